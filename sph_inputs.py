@@ -1,0 +1,228 @@
+"""Seeded synthetic inputs for the photoionization source evaluation.
+
+This module is shared by the FP64 oracle (``oracle/``), the tests and
+``bench.py``.  It holds no part of the method's arithmetic: it only draws
+random numbers and lays out the emission field ``q`` and the electric-field
+magnitude ``|E|`` on a uniform cell-centred grid (paper Section 4, uniform
+mesh over the box ``[0,x_d] x [0,y_d] x [0,z_d]``).
+
+Conventions
+-----------
+* Cell ``n = i + nx*(j + ny*k)`` (x fastest) has centre
+  ``origin + h*(i+1/2, j+1/2, k+1/2)`` in cm.
+* Every field is produced in FP64 and rounded once to FP32, so the oracle and
+  the GPU path read bit-identical inputs.
+* Random numbers come from SplitMix64 (Steele, Lea and Flood 2014): the n-th
+  draw of a stream seeded with ``seed`` is ``mix(seed + (n+1)*0x9E3779B97F4A7C15)``
+  and the uniform deviate is ``(x >> 11) * 2**-53``; draws are taken in
+  linear-index order.
+* Emission peak ``I0 = 1e26 m^-3 s^-1 = 1e20 cm^-3 s^-1``.
+* ``source_scale`` is the factor that turns ``q`` into the emission term of
+  Eq. Ifun: ``xi * p_q/(p + p_q)`` with the config's combined ``xi = 0.06``
+  (= the paper's ``xi * omega/alpha = 0.1*0.6``) and ``p_q = 30`` Torr.
+* ``pO2 = p * 150/760`` (the paper's air ratio).
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+I0 = 1.0e20          # cm^-3 s^-1
+CHI_MIN = 0.035      # cm^-1 Torr^-1  (Eq. gfun)
+CHI_MAX = 2.0        # cm^-1 Torr^-1  (Eq. gfun)
+P_Q = 30.0           # Torr
+XI_EFF = 0.06        # xi * omega/alpha
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws ``offset .. offset+n-1`` of the SplitMix64 stream ``seed`` (uint64)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + idx * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """U[0,1) deviates in FP64 from the SplitMix64 stream."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic snapshot on a uniform grid (all lengths in cm)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    origin: tuple
+    p_torr: float
+    pO2_torr: float
+    q: np.ndarray                 # float32[nx*ny*nz], emission shape (x fastest)
+    emag: np.ndarray | None       # float32[nx*ny*nz], |E| in kV/cm, or None
+    source_scale: float           # I = source_scale * q
+    i_frac: float = 0.0           # 0 selects every cell as a source
+    e_frac: float = 0.0
+    e_applied: float = 0.0
+    targets_all: bool = True      # True: every cell is a target (emag unused)
+    leaf_size: int = 64
+    seed: int = 0
+    chi_min: float = CHI_MIN
+    chi_max: float = CHI_MAX
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def centres(self):
+        """FP64 cell-centre coordinate arrays (X, Y, Z), each shaped (nz, ny, nx)."""
+        return _grid(self.nx, self.ny, self.nz, self.h, self.origin)
+
+
+def _grid(nx, ny, nz, h, origin=(0.0, 0.0, 0.0)):
+    x = origin[0] + h * (np.arange(nx, dtype=np.float64) + 0.5)
+    y = origin[1] + h * (np.arange(ny, dtype=np.float64) + 0.5)
+    z = origin[2] + h * (np.arange(nz, dtype=np.float64) + 0.5)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")   # shaped (nz, ny, nx): x fastest
+    return X, Y, Z
+
+
+def pO2_of(p_torr: float) -> float:
+    return p_torr * 150.0 / 760.0
+
+
+def scale_of(p_torr: float) -> float:
+    return XI_EFF * P_Q / (p_torr + P_Q)
+
+
+def streamer_emission(X, Y, Z, head, sigma_head, chan_len, chan_radius,
+                      chan_level=1e-2, cloud=None):
+    """Gaussian head plus a Gaussian-profile channel behind it (head points -z).
+
+    ``head`` = (x, y, z) of the head centre; the channel occupies
+    ``z in [z_head, z_head + chan_len]`` on the axis through the head with
+    radial profile ``chan_level * exp(-rho^2/chan_radius^2)``.  ``cloud`` =
+    (centre, radius, level) adds a spherical Gaussian.  Peak value 1 (times I0).
+    """
+    hx, hy, hz = head
+    r2 = (X - hx) ** 2 + (Y - hy) ** 2 + (Z - hz) ** 2
+    q = np.exp(-r2 / sigma_head ** 2)
+    rho2 = (X - hx) ** 2 + (Y - hy) ** 2
+    inside = (Z >= hz) & (Z <= hz + chan_len)
+    q = q + np.where(inside, chan_level * np.exp(-rho2 / chan_radius ** 2), 0.0)
+    if cloud is not None:
+        (cx, cy, cz), crad, clev = cloud
+        q = q + clev * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / crad ** 2)
+    return q
+
+
+def streamer_efield(X, Y, Z, head, sigma_head, chan_len, chan_radius,
+                    e_background=30.0, e_head=150.0, e_chan=30.0):
+    """|E| (kV/cm) of a synthetic streamer: background + charged ball + charged segment.
+
+    * background ``(0, 0, -e_background)``;
+    * a uniformly charged ball of radius ``sigma_head`` at the head whose
+      surface field is ``e_head`` (linear inside, inverse-square outside);
+    * a uniformly charged segment on the channel axis from ``z_head`` to
+      ``z_head + chan_len`` with Plummer softening ``chan_radius``, its line
+      density set so that the radial field at ``rho = chan_radius`` at
+      mid-channel is ``e_chan``.
+    """
+    hx, hy, hz = head
+    dx, dy, dz = X - hx, Y - hy, Z - hz
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    R = sigma_head
+    rs = np.maximum(r, 1e-300)
+    fball = np.where(r < R, e_head * r / R, e_head * (R / rs) ** 2) / rs
+    ex = fball * dx
+    ey = fball * dy
+    ez = fball * dz - e_background
+    a = chan_radius
+    L = chan_len
+    z1, z2 = hz, hz + L
+    k_lam = e_chan * 2.0 * a * np.sqrt(2.0 * a * a + L * L / 4.0) / L
+    rho2 = dx * dx + dy * dy
+    b2 = rho2 + a * a
+    u1 = Z - z1
+    u2 = Z - z2
+    s1 = np.sqrt(b2 + u1 * u1)
+    s2 = np.sqrt(b2 + u2 * u2)
+    erho_over_rho = k_lam / b2 * (u1 / s1 - u2 / s2)
+    ex = ex + erho_over_rho * dx
+    ey = ey + erho_over_rho * dy
+    ez = ez + k_lam * (1.0 / s2 - 1.0 / s1)
+    return np.sqrt(ex * ex + ey * ey + ez * ez)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float64).astype(np.float32).ravel()
+
+
+def plain_gaussian(n=24, seed=1000, noise=1e-3, p_torr=760.0, box=0.2, sigma=0.02):
+    """Plain direct-quadrature case: n^3 cells in a ``box`` cm cube, Gaussian + noise.
+
+    ``q = exp(-|r-r0|^2/sigma^2) + noise*U[0,1)`` in units of I0, r0 at the
+    box centre (a cell corner for even n); every cell is a source and a target.
+    """
+    h = box / n
+    X, Y, Z = _grid(n, n, n, h)
+    c = box / 2
+    q = np.exp(-((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2) / sigma ** 2)
+    q = q + noise * uniform01(seed, n ** 3).reshape(q.shape)
+    return Problem("plain_gaussian_%d" % n, n, n, n, h, (0.0, 0.0, 0.0), p_torr,
+                   pO2_of(p_torr), _f32(q * I0), None, scale_of(p_torr), seed=seed)
+
+
+def streamer(n=128, box=1.0, p_torr=760.0, chan_len=0.5, i_frac=0.0, e_frac=0.1,
+             e_applied=0.0, targets_all=True, leaf_size=64, seed=1001,
+             sigma_head=0.015, chan_radius=0.02, with_efield=True, head=None,
+             cloud=None, name=None):
+    """Streamer-shaped emission (Gaussian head + channel) in an n^3 grid over a ``box`` cube.
+
+    Head at (box/2, box/2, box/2 - chan_len/2) unless ``head`` is given; the
+    channel runs ``chan_len`` cm towards +z.  ``|E|`` from :func:`streamer_efield`.
+    """
+    h = box / n
+    X, Y, Z = _grid(n, n, n, h)
+    if head is None:
+        head = (box / 2, box / 2, box / 2 - chan_len / 2)
+    q = streamer_emission(X, Y, Z, head, sigma_head, chan_len, chan_radius, cloud=cloud)
+    em = None
+    if with_efield:
+        em = _f32(streamer_efield(X, Y, Z, head, sigma_head, chan_len, chan_radius))
+    return Problem(name or "streamer_%d" % n, n, n, n, h, (0.0, 0.0, 0.0), p_torr,
+                   pO2_of(p_torr), _f32(q * I0), em, scale_of(p_torr), i_frac=i_frac,
+                   e_frac=e_frac, e_applied=e_applied, targets_all=targets_all,
+                   leaf_size=leaf_size, seed=seed)
+
+
+def config_c0():
+    """24^3 plain direct quadrature in a 2 mm cube at 760 Torr, all cells source and target."""
+    return plain_gaussian(24, seed=1000)
+
+
+def config_c1(n=128):
+    """FMM without adaptivity: 128^3 streamer in a 1 cm cube at 760 Torr, all cells."""
+    return streamer(n=n, box=1.0, p_torr=760.0, chan_len=0.5, i_frac=0.0,
+                    targets_all=True, seed=1001, with_efield=False,
+                    name="streamer_%d_full" % n)
+
+
+def config_c2(n=256, p_torr=760.0, e_frac=0.1, e_applied=0.0):
+    """Adaptive FMM: 256^3 streamer in a 1 cm cube, sources I >= 1e-4 max I,
+    targets |E| >= e_applied + e_frac*(max|E| - e_applied)."""
+    return streamer(n=n, box=1.0, p_torr=p_torr, chan_len=0.5, i_frac=1e-4,
+                    e_frac=e_frac, e_applied=e_applied, targets_all=False, seed=1002,
+                    name="streamer_%d_adaptive_p%d" % (n, int(p_torr)))
+
+
+def random_mask(n_cells: int, frac: float, seed: int) -> np.ndarray:
+    """uint8 mask with each cell set with probability ``frac`` (SplitMix64 stream)."""
+    return (uniform01(seed, n_cells) < frac).astype(np.uint8)

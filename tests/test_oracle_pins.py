@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a
+high-precision evaluation of Eq. gfun written as the paper prints it (a
+difference of exponentials, not the expm1 form the oracle uses), textbook
+special functions, adaptive quadrature, photon conservation, the continuum
+Eq. integral for a spherical source, symmetry invariants, an extended-precision
+brute force and an FFT convolution.  A dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sph_inputs as si
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper_consts():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        return json.load(f)
+
+
+def _ab(pO2):
+    c = _paper_consts()
+    return oracle.alpha_beta(pO2, c["chi_min"]["value"], c["chi_max"]["value"])
+
+
+# --------------------------------------------------------------------------- kernel
+@pytest.mark.parametrize("pO2", [150.0, 75.0, 15.0, 160.0, 10.0])
+def test_G_matches_eq_gfun_in_50_digits(pO2):
+    """Eq. gfun evaluated as printed (difference of exponentials) with mpmath."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    c = _paper_consts()
+    chi_min, chi_max = c["chi_min"]["value"], c["chi_max"]["value"]
+    a, b = oracle.alpha_beta(pO2, chi_min, chi_max)
+    for R in np.logspace(-6, 0.5, 41):
+        Rm = mp.mpf(float(R))
+        p = mp.mpf(pO2)
+        g_over_p = (mp.e ** (-mp.mpf(chi_min) * p * Rm) - mp.e ** (-mp.mpf(chi_max) * p * Rm)) / (
+            p * Rm * mp.log(mp.mpf(chi_max) / mp.mpf(chi_min)))
+        ref = g_over_p * p / (4 * mp.pi * Rm ** 2)
+        got = oracle.G(R, a, b)
+        assert abs(got / float(ref) - 1.0) < 2e-14, (R, got, float(ref))
+
+
+def test_G_small_R_limit():
+    """g(r) -> p_O2 (chi_max - chi_min)/ln(chi_max/chi_min) as r -> 0 (Eq. gfun)."""
+    a, b = _ab(150.0)
+    R = 1e-12
+    g = oracle.G(R, a, b) * 4 * math.pi * R * R
+    # next term of the expansion is -(a + b) R / 2 ~ 1.5e-10 here
+    assert abs(g / ((b - a) / math.log(b / a)) - 1) < 1e-9
+
+
+def test_photon_conservation():
+    """int_0^inf 4 pi r^2 G(r) dr = int (e^-ar - e^-br)/(L r) dr = ln(b/a)/L = 1."""
+    import scipy.integrate as sint
+    for pO2 in (150.0, 15.0):
+        a, b = _ab(pO2)
+        f = lambda r: 4 * math.pi * r * r * oracle.G(r, a, b)
+        tot = 0.0
+        edges = [0.0, 1e-4, 1e-3, 1e-2, 0.1, 1.0, 10.0, 100.0, 1e4]
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            v, _ = sint.quad(f, max(lo, 1e-300), hi, epsabs=0, epsrel=1e-13, limit=500)
+            tot += v
+        assert abs(tot - 1.0) < 1e-9, tot
+
+
+# --------------------------------------------------------------------------- E1 / self
+@pytest.mark.parametrize("x", [1e-10, 1e-4, 0.03, 0.5, 0.999, 1.0, 1.001, 2.5, 7.0, 30.0, 300.0])
+def test_E1_against_scipy_and_mpmath(x):
+    import scipy.special as ss
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    ref = float(mp.e1(mp.mpf(x)))
+    assert abs(oracle.E1(x) / ref - 1) < 5e-15
+    assert abs(ss.exp1(x) / ref - 1) < 1e-13
+
+
+@pytest.mark.parametrize("h,pO2", [(0.2 / 24, 150.0), (1 / 256, 150.0), (1 / 256, 15.0), (0.05, 150.0), (1e-4, 75.0)])
+def test_self_integral_against_quadrature(h, pO2):
+    """Ball of one cell's volume: int_0^a (e^-ar - e^-br)/(L r) dr by Gauss-Kronrod."""
+    import scipy.integrate as sint
+    a_, b_ = _ab(pO2)
+    L = math.log(b_ / a_)
+    a = h * (3 / (4 * math.pi)) ** (1 / 3)
+    f = lambda r: (-math.expm1(-(b_ - a_) * r) * math.exp(-a_ * r)) / (L * r) if r > 0 else (b_ - a_) / L
+    ref, _ = sint.quad(f, 0, a, epsabs=0, epsrel=1e-13, limit=200)
+    got = oracle.self_integral(h, a_, b_)
+    assert abs(got / ref - 1) < 1e-12, (got, ref)
+
+
+def test_self_integral_small_radius_limit():
+    a_, b_ = _ab(150.0)
+    h = 1e-7
+    a = h * (3 / (4 * math.pi)) ** (1 / 3)
+    assert abs(oracle.self_integral(h, a_, b_) / ((b_ - a_) * a / math.log(b_ / a_)) - 1) < 1e-4
+
+
+# --------------------------------------------------------------------------- selection
+def test_selection_threshold_edges():
+    """Section 3 rules: '>=' at the exact threshold; i_frac = 0 keeps every cell;
+    max|q| <= 0 with i_frac > 0 selects nothing; explicit mask wins."""
+    q = np.array([4.0, 1.0, 0.5, 0.25, 2.0, 0.0], np.float32)
+    J, T = oracle.select(q, i_frac=0.125)           # thr = 0.5 exactly
+    assert J.tolist() == [0, 1, 2, 4]
+    assert T.tolist() == list(range(6))
+    J, _ = oracle.select(q, i_frac=0.0)
+    assert J.tolist() == list(range(6))
+    J, _ = oracle.select(np.zeros(5, np.float32), i_frac=0.1)
+    assert J.size == 0
+    J, _ = oracle.select(-np.ones(5, np.float32), i_frac=0.1)
+    assert J.size == 0
+    e = np.array([1.0, 5.0, 3.0, 2.0, 9.0, 4.0], np.float32)
+    # thr = 1 + 0.5 (9 - 1) = 5 exactly
+    _, T = oracle.select(q, emag=e, i_frac=0.125, e_frac=0.5, e_applied=1.0)
+    assert T.tolist() == [1, 4]
+    m = np.array([0, 1, 0, 0, 1, 1], np.uint8)
+    _, T = oracle.select(q, emag=e, mask=m)
+    assert T.tolist() == [1, 4, 5]
+
+
+def test_selection_comparison_is_fp64():
+    """Threshold formed in FP64: a value just below the FP64 threshold but equal in FP32 is excluded."""
+    qmax = np.float32(3.0)
+    frac = 1.0 / 3.0 + 1e-12          # thr = 1.000000000003 in FP64
+    q = np.array([qmax, np.float32(1.0)], np.float32)
+    J, _ = oracle.select(q, i_frac=frac)
+    assert J.tolist() == [0]
+
+
+# --------------------------------------------------------------------------- the sum
+def test_point_source_against_mpmath():
+    """One nonzero cell: S(t) = I_h G(R) with I_h = scale*q*h^3 (Eq. summation), and
+    the source cell itself gets I * (ball integral)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    nx, ny, nz, h = 7, 5, 6, 0.013
+    a, b = _ab(150.0)
+    q = np.zeros(nx * ny * nz, np.float32)
+    s = 3 + nx * (2 + ny * 4)
+    q[s] = 2.5e19
+    scale = 0.01
+    J = np.arange(nx * ny * nz, dtype=np.int32)
+    T = J.copy()
+    S = oracle.sph(nx, ny, nz, h, a, b, q, scale, J, T)
+    L = mp.log(mp.mpf(b) / mp.mpf(a))
+    for t in range(nx * ny * nz):
+        it, jt, kt = t % nx, (t // nx) % ny, t // (nx * ny)
+        if t == s:
+            continue
+        R = mp.mpf(h) * mp.sqrt((it - 3) ** 2 + (jt - 2) ** 2 + (kt - 4) ** 2)
+        ref = (mp.e ** (-a * R) - mp.e ** (-b * R)) / (4 * mp.pi * L * R ** 3) * scale * mp.mpf(float(q[s])) * mp.mpf(h) ** 3
+        assert abs(S[t] / float(ref) - 1) < 1e-13
+    assert abs(S[s] / (scale * float(q[s]) * oracle.self_integral(h, a, b)) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 4)])
+def test_brute_force_extended_precision(dims):
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    h = 0.01
+    a, b = _ab(150.0)
+    q = (si.uniform01(7, n) * 1e20).astype(np.float32)
+    J = np.arange(n, dtype=np.int32)
+    T = np.arange(n, dtype=np.int32)
+    S = oracle.sph(nx, ny, nz, h, a, b, q, 0.002, J, T)
+    ref = oracle.sph_longdouble(nx, ny, nz, h, a, b, q, 0.002, J, T, 1, oracle.self_integral(h, a, b))
+    assert np.max(np.abs(S / ref - 1)) < 1e-13
+
+
+def test_reciprocity():
+    """G is symmetric, so <a, S[b]> = <b, S[a]> with J = T = all (no self term)."""
+    nx, ny, nz, h = 9, 8, 7, 0.02
+    n = nx * ny * nz
+    A, B = _ab(75.0)
+    qa = si.uniform01(11, n).astype(np.float32)
+    qb = si.uniform01(12, n).astype(np.float32)
+    J = np.arange(n, dtype=np.int32)
+    Sa = oracle.sph(nx, ny, nz, h, A, B, qa, 1.0, J, J, self_mode=0)
+    Sb = oracle.sph(nx, ny, nz, h, A, B, qb, 1.0, J, J, self_mode=0)
+    lhs = float(np.dot(qa.astype(np.float64), Sb))
+    rhs = float(np.dot(qb.astype(np.float64), Sa))
+    assert abs(lhs / rhs - 1) < 1e-13
+
+
+def test_translation_bit_identical():
+    """Shifting sources and targets by whole cells leaves every S bit-identical."""
+    nx, ny, nz, h = 12, 10, 9, 0.01
+    A, B = _ab(150.0)
+    q = np.zeros((nz, ny, nx), np.float32)
+    blob = (si.uniform01(21, 5 * 4 * 3).reshape(3, 4, 5) * 1e18).astype(np.float32)
+    q[1:4, 2:6, 1:6] = blob
+    q2 = np.zeros_like(q)
+    q2[4:7, 5:9, 6:11] = blob                      # shift (dx, dy, dz) = (5, 3, 3)
+    J1 = np.flatnonzero(q.ravel()).astype(np.int32)
+    J2 = np.flatnonzero(q2.ravel()).astype(np.int32)
+    t1 = np.array([0 + nx * (0 + ny * 0), 2 + nx * (6 + ny * 4), 5 + nx * (6 + ny * 5)], np.int32)
+    ti, tj, tk = t1 % nx, (t1 // nx) % ny, t1 // (nx * ny)
+    t2 = ((ti + 5) + nx * ((tj + 3) + ny * (tk + 3))).astype(np.int32)
+    S1 = oracle.sph(nx, ny, nz, h, A, B, q.ravel(), 1.0, J1, t1)
+    S2 = oracle.sph(nx, ny, nz, h, A, B, q2.ravel(), 1.0, J2, t2)
+    assert np.array_equal(S1, S2)
+
+
+def test_linearity_and_mirror_symmetry():
+    nx = ny = nz = 8
+    h = 0.015
+    n = nx * ny * nz
+    A, B = _ab(150.0)
+    J = np.arange(n, dtype=np.int32)
+    q1 = si.uniform01(31, n).astype(np.float32)
+    q2 = si.uniform01(32, n).astype(np.float32)
+    S1 = oracle.sph(nx, ny, nz, h, A, B, q1, 1.0, J, J)
+    S2 = oracle.sph(nx, ny, nz, h, A, B, q2, 1.0, J, J)
+    q3 = (q1.astype(np.float64) * 0.5 + q2.astype(np.float64) * 0.25).astype(np.float32)
+    S3 = oracle.sph(nx, ny, nz, h, A, B, q3, 1.0, J, J)
+    # q3 is q1/2 + q2/4 exactly only up to FP32 rounding of q3: compare against that
+    ref = 0.5 * S1 + 0.25 * S2
+    assert np.max(np.abs(S3 - ref) / ref) < 2e-7
+    S4 = oracle.sph(nx, ny, nz, h, A, B, q1, 0.5, J, J)
+    assert np.max(np.abs(S4 - 0.5 * S1) / S1) < 1e-15
+    qm = q1.reshape(nz, ny, nx)[:, :, ::-1].ravel().copy()
+    Sm = oracle.sph(nx, ny, nz, h, A, B, qm, 1.0, J, J)
+    assert np.max(np.abs(Sm.reshape(nz, ny, nx)[:, :, ::-1].ravel() / S1 - 1)) < 1e-13
+
+
+@pytest.mark.parametrize("dims,frac", [((16, 12, 10), 1e-2), ((20, 20, 20), 0.0)])
+def test_fft_convolution_agrees(dims, frac):
+    """Same discrete sum as an FFT convolution (independent algorithm)."""
+    nx, ny, nz = dims
+    h = 0.2 / nx
+    A, B = _ab(150.0)
+    p = si.plain_gaussian(nx, seed=5, box=0.2, sigma=0.03)
+    q = p.q[: nx * ny * nz] if (ny, nz) != (nx, nx) else p.q
+    q = np.asarray(q[: nx * ny * nz], np.float32)
+    J, T = oracle.select(q, i_frac=frac)
+    S = oracle.sph(nx, ny, nz, h, A, B, q, 1.0, J, T)
+    F = oracle.fft_convolution(nx, ny, nz, h, A, B, q, 1.0, J)[T]
+    assert oracle.rel_l2(F, S) < 1e-12
+    assert np.max(np.abs(F - S)) < 1e-11 * S.max()
+
+
+# --------------------------------------------------------------------------- continuum limits
+def _radial_case(n, box, sigma, rmin, rmax, pO2=150.0, self_mode=1):
+    A, B = _ab(pO2)
+    c = box / 2
+    h = box / n
+    X, Y, Z = si._grid(n, n, n, h)
+    q = np.exp(-((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2) / sigma ** 2).astype(np.float32).ravel()
+    J = np.flatnonzero(q > 0).astype(np.int32)
+    jj = kk = n // 2             # the centre lies on a cell corner: take the row just above it
+    ii = np.arange(n)
+    xs, ys, zs = (ii + 0.5) * h, (jj + 0.5) * h, (kk + 0.5) * h
+    r = np.sqrt((xs - c) ** 2 + (ys - c) ** 2 + (zs - c) ** 2)
+    sel = (r >= rmin) & (r <= rmax) & (xs > c)
+    T = (ii[sel] + n * (jj + n * kk)).astype(np.int32)
+    S = oracle.sph(n, n, n, h, A, B, q, 1.0, J, T, self_mode=self_mode)
+    Iq = lambda rho: math.exp(-rho * rho / sigma ** 2)
+    ref = np.array([oracle.radial_reference(float(rr), Iq, A, B, 10 * sigma) for rr in r[sel]])
+    return float(np.max(np.abs(S / ref - 1)))
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+def test_converges_to_radial_integral_far_from_source():
+    """A spherical Gaussian: Eq. integral reduces to a 1D radial integral.  Where the
+    emission has died out (r >= 5 sigma) the midpoint sum of Eq. summation is an
+    accurate quadrature of it (smooth integrand)."""
+    e24 = _radial_case(24, 0.3, 0.02, 5 * 0.02, 7.5 * 0.02)
+    e48 = _radial_case(48, 0.3, 0.02, 5 * 0.02, 7.5 * 0.02)
+    assert e24 < 1e-7, e24
+    assert e48 < 1e-8, e48
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+def test_self_term_inside_source():
+    """Inside the source the cell's own contribution (ball of one cell's volume)
+    carries most of the near-singular integral: with it the sum approaches the
+    continuum as h -> 0; without it the error is many times larger."""
+    box, sigma = 0.3, 0.03
+    with_self = [_radial_case(n, box, sigma, 0.0, sigma) for n in (24, 48)]
+    without = [_radial_case(n, box, sigma, 0.0, sigma, self_mode=0) for n in (24, 48)]
+    assert with_self[1] < with_self[0] < 0.06, with_self
+    assert with_self[0] * 5 < without[0] and with_self[1] * 5 < without[1], (with_self, without)
+
+
+def test_truncated_gaussian_far_field_deficit():
+    """Dropping sources below f*max (Eq. sourcepct) removes the Gaussian mass fraction
+    erfc(u) + 2u/sqrt(pi) e^{-u^2}, u = sqrt(ln 1/f); far away, S drops by that fraction."""
+    nx = ny = 40
+    nz = 200
+    h = 0.01
+    sigma = 0.06
+    A, B = _ab(15.0)
+    X, Y, Z = si._grid(nx, ny, nz, h)
+    c = (0.2, 0.2, 0.3)
+    q = np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / sigma ** 2).astype(np.float32).ravel()
+    Jall = np.flatnonzero(q > 0).astype(np.int32)
+    T = np.array([nx // 2 + nx * (ny // 2 + ny * k) for k in (160, 180, 199)], np.int32)
+    Sall = oracle.sph(nx, ny, nz, h, A, B, q, 1.0, Jall, T)
+    for f in (1e-2, 1e-1):
+        Jf, _ = oracle.select(q, i_frac=f)
+        Sf = oracle.sph(nx, ny, nz, h, A, B, q, 1.0, Jf, T)
+        drop = 1 - Sf / Sall
+        u = math.sqrt(math.log(1 / f))
+        expect = math.erfc(u) + 2 * u / math.sqrt(math.pi) * math.exp(-u * u)
+        assert np.all(np.abs(drop / expect - 1) < 0.03), (f, drop, expect)
