@@ -1,0 +1,330 @@
+"""Benchmark: S_ph targets/s of the adaptive FMM on one GB300 (or N replicas).
+
+Workload (default): the 256^3 adaptive streamer case -- a 1 cm cube at 760 Torr,
+Gaussian head + channel emission, sources with I >= 1e-4 max I, targets with
+|E| >= 0.1 max|E| -- evaluated through the C ABI (eval_sph) with inputs resident
+in device memory.  One step = one full evaluation: selection, octree and lists,
+upward pass, M2L, downward pass, leaves.  L2 is flushed (256 MiB write) between
+timed steps; each step is timed with CUDA events on the library's stream.
+
+Printed: one JSON line (rank 0) with value = targets/s summed over ranks,
+e2e = the same through eval_sph_host (host buffers, copies inside the timed
+region), roofline of the dominant kernel, the FP32 direct sum on the same GPU,
+accuracy against the FP64 oracle on sampled targets, and the CPU oracle baseline.
+
+``--impl reference`` times the FP64 CPU oracle (the plain direct quadrature) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sph_inputs as si  # noqa: E402
+
+MUFU_PER_SM_CLK = 16          # SFU (MUFU) results per SM per clock on sm_100-class parts
+MUFU_PER_EVAL = 3             # rsqrt + 2 x ex2 per kernel evaluation
+NSM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid edge (cells)")
+    ap.add_argument("--p", type=float, default=760.0, help="pressure (Torr)")
+    ap.add_argument("--m2l", default="f32", choices=["f32", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(args):
+    return si.config_c2(n=args.n, p_torr=args.p)
+
+
+def workload_cfg(p, args):
+    return {"workload": "streamer %d^3 in 1 cm, %g Torr, sources I>=1e-4*max, targets |E|>=0.1*max|E|"
+                        % (args.n, args.p),
+            "grid": [p.nx, p.ny, p.nz], "pressure_torr": args.p, "i_frac": p.i_frac, "e_frac": p.e_frac,
+            "leaf_size": p.leaf_size, "m2l": args.m2l, "l2_flush_between_steps": True,
+            "inputs_resident_in_hbm": True}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def leaf_evals(tree, nt_total):
+    """Algorithmic kernel evaluations of the leaf kernel (L2P + M2P + P2P pairs)."""
+    lev = tree["level"]
+    nt = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
+    ns = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
+    leaf = tree["leaf"]
+    l2p = int(np.sum(nt[leaf & (lev >= 2)]) * 152)
+    W = tree["W"]
+    m2p = int(np.sum(nt[W[:, 0]]) * 152) if len(W) else 0
+    U = tree["U"]
+    p2p = int(np.sum(nt[U[:, 0]] * ns[U[:, 1]])) if len(U) else 0
+    return l2p, m2p, p2p
+
+
+def oracle_sample(p, J, T, seconds, seed=5):
+    """Time the FP64 oracle on a bounded random sample of targets; returns (targets/s, sample, cores)."""
+    import oracle
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    rng = np.random.default_rng(seed)
+    n0 = max(8, min(T.size, 64))
+    samp = np.sort(rng.choice(T, size=n0, replace=False))
+    t0 = time.perf_counter()
+    oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+    dt = time.perf_counter() - t0
+    n1 = int(min(T.size, max(n0, n0 * seconds / max(dt, 1e-3))))
+    samp = np.sort(rng.choice(T, size=n1, replace=False))
+    t0 = time.perf_counter()
+    oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+    dt = time.perf_counter() - t0
+    return n1 / dt, n1, dt, oracle.num_threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = workload(args)
+    J, T = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    per_step = []
+    nsamp = 0
+    for k in range(args.warmup + args.steps):
+        rate, n1, dt, cores = oracle_sample(p, J, T, max(1.0, min(args.cpu_seconds, 120.0 / (args.steps + args.warmup))),
+                                            seed=100 + k)
+        if k >= args.warmup:
+            per_step.append(rate)
+            nsamp = n1
+    v = statistics.median(per_step)
+    line = {"impl": "reference", "metric": "S_ph targets/s", "value": v, "unit": "targets/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T.size / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_cfg(p, args),
+            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d random targets of %d per step (FP64 direct sum over all %d sources), "
+                                       "extrapolated to targets/s" % (nsamp, T.size, J.size)},
+            "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_2112_10059_gb300 as sph
+
+    p = workload(args)
+    dev = torch.device("cuda", local)
+    q = torch.from_numpy(p.q).to(dev)
+    em = torch.from_numpy(p.emag).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sph.Context(local, stream)
+    sph.set_grid(ctx, p.nx, p.ny, p.nz, p.h, p.pO2_torr, p.chi_min, p.chi_max)
+    sph.set_sources(ctx, q, p.source_scale)
+    sph.set_targets(ctx, emag=em)
+    prec = sph.M2L_BF16X3 if args.m2l == "bf16x3" else sph.M2L_F32
+    sph.set_criteria(ctx, p.i_frac, p.e_frac, p.e_applied, 1, p.leaf_size, prec)
+    out = torch.empty(p.ncell, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(3, args.warmup)):
+        sph.eval_sph(ctx, out)
+    torch.cuda.synchronize()
+    _, st0 = sph.eval_sph(ctx, out, stats=True)
+    nt = int(st0.n_targets)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    leaf_ms, step_stats = [], []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            _, st = sph.eval_sph(ctx, out, stats=True)
+            ev[k][1].record(stream)
+            leaf_ms.append(st.ms_near)
+            step_stats.append(st.as_dict())
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nt * world / (ms * 1e-3)
+
+    # e2e through the host-buffer entry point
+    qh = p.q
+    eh = p.emag
+    sh = np.empty(p.ncell, np.float32)
+    sph.eval_sph_host(ctx, qh, eh, out=sh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne2e = max(3, min(args.steps, 5))
+    for _ in range(ne2e):
+        sph.eval_sph_host(ctx, qh, eh, out=sh)
+    e2e_s = (time.perf_counter() - t0) / ne2e
+    # restore device inputs
+    sph.set_sources(ctx, q, p.source_scale)
+    sph.set_targets(ctx, emag=em)
+
+    # roofline of the dominant kernel (the leaf kernel: L2P + M2P + P2P kernel evaluations)
+    tree = sph.get_tree(ctx)
+    l2p, m2p, p2p = leaf_evals(tree, nt)
+    evals = l2p + m2p + p2p
+    leaf_avg = sum(leaf_ms) / len(leaf_ms)
+    clocks = clk.summary()
+    f_mhz = clocks["sm_mhz"] or 1920.0
+    peak_evals = NSM * MUFU_PER_SM_CLK * f_mhz * 1e6 / MUFU_PER_EVAL
+    achieved = evals / (leaf_avg * 1e-3)
+
+    # FP32 direct sum on the same GPU over the same selected sets
+    direct = None
+    if not args.no_direct:
+        d = sph.eval_direct(ctx, fp64=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d = sph.eval_direct(ctx, fp64=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms = e0.elapsed_time(e1)
+        direct = {"targets_per_s": nt / (dms * 1e-3), "ms": dms, "pairs": int(st0.n_sources) * nt,
+                  "fmm_speedup": (nt / (ms * 1e-3)) / (nt / (dms * 1e-3))}
+
+    # accuracy on sampled targets against the FP64 oracle
+    import oracle
+    J, T = sph.get_selection(ctx)
+    rng = np.random.default_rng(1)
+    samp = np.sort(rng.choice(T, size=min(T.size, 400), replace=False))
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+    S = out.cpu().numpy().astype(np.float64)[samp]
+    acc = {"rel_l2_sampled": oracle.rel_l2(S, ref), "max_rel_sampled": oracle.max_rel(S, ref, 1e-3),
+           "n_sampled_targets": int(samp.size)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n1, dt, cores = oracle_sample(p, J, T, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "targets/s", "cores": cores, "kind": "oracle",
+               "sample": "%d random targets of %d (FP64 direct sum over all %d sources) in %.1f s"
+                         % (n1, T.size, J.size, dt)}
+
+    if rank == 0:
+        last = step_stats[-1]
+        line = {"metric": "S_ph targets/s", "value": value, "unit": "targets/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.m2l == "f32" else "f32+bf16x3",
+                "data": "synthetic", "config": workload_cfg(p, args),
+                "e2e": {"value": nt * world / e2e_s, "unit": "targets/s",
+                        "h2d_bytes_per_step": int(qh.nbytes + eh.nbytes), "d2h_bytes_per_step": int(sh.nbytes)},
+                "roofline": {"bound": "alu", "kernel": "k_leaf", "achieved": achieved, "peak": peak_evals,
+                             "unit": "kernel-evals/s", "frac": achieved / peak_evals, "traffic": None,
+                             "peak_basis": "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz,
+                             "evals_per_launch": evals, "l2p": l2p, "m2p": m2p, "p2p": p2p,
+                             "ms_per_launch": leaf_avg},
+                "clocks": clocks, "gpu_launches": None,
+                "phases_ms": {k: last[k] for k in ("ms_select", "ms_tree", "ms_upward", "ms_m2l", "ms_near",
+                                                   "ms_total")},
+                "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
+                                                "max_level")},
+                "direct_fp32": direct, "accuracy": acc, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

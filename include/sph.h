@@ -1,0 +1,158 @@
+/*
+ * sph.h -- C ABI of libsph: the photoionization source S_ph of the Zheleznyak
+ * integral model evaluated on one GPU by an adaptive kernel-independent fast
+ * multipole method (Lin & Zhuang, "Adaptive Strategies to Fast Multipole
+ * Method in Photoionization Calculations").
+ *
+ * What is computed (paper Section 2.1, Eq. integral / Eq. Ifun / Eq. gfun, and
+ * Section 2.4, Eq. summation):
+ *   S_ph(x_t) = sum_{s in J, s != t} G(|x_t - y_s|) I_h(y_s) + [t in J] I(x_t) * Gself
+ *   G(R)      = (e^{-alpha R} - e^{-beta R}) / (4 pi L R^3),
+ *   alpha = chi_min p_O2, beta = chi_max p_O2, L = ln(chi_max/chi_min),
+ *   I = source_scale * q,  I_h = I * h^3 (cell volume),
+ *   Gself = integral of G over the ball with one cell's volume
+ *         = 1 - (E1(alpha a) - E1(beta a))/L,  a = h (3/(4 pi))^(1/3)   (self_mode 1)
+ * over the source set J and the target set T chosen by the adaptive
+ * strategies of Section 3 (Eq. summationI, Eq. sourcepct, the Section 5
+ * electric-field rule):
+ *   J = { n : q[n] >= i_frac * max_n q }      (i_frac == 0: every cell)
+ *   T = { n : |E|[n] >= e_applied + e_frac (max|E| - e_applied) },
+ *       or { n : mask[n] != 0 }, or every cell.
+ * Every threshold comparison is made in FP64 on the FP32 inputs.
+ * The far field is approximated through the hierarchy of Section 2.4
+ * (Eq. nearfar, Eq. s2l, Figure fmulloc); the near field is summed exactly.
+ *
+ * Grid: nx*ny*nz cells of edge h (cm); cell n = i + nx*(j + ny*k) (x fastest)
+ * has centre origin + h*(i+1/2, j+1/2, k+1/2).  nx, ny, nz <= 1024.
+ *
+ * Conventions for every call:
+ *  - Return value: SPH_OK (0) or a negative sph_status.  Nothing throws or
+ *    aborts; sph_last_error() gives a one-line message for the last failure.
+ *  - Pointers named *_dev are device pointers on the context's device; they
+ *    are borrowed, never freed, and must stay valid until the work queued on
+ *    the context's stream has finished.  Pointers named *_host are host memory.
+ *  - All work is queued on the stream given to sph_create (NULL = legacy
+ *    default stream).  eval_* calls may synchronise that stream internally
+ *    (tree sizes are data dependent); they return after the result is queued.
+ *  - A CUDA error poisons the context: every later call returns SPH_ECUDA.
+ *  - One context per host thread; contexts are independent.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum sph_status {
+    SPH_OK = 0,
+    SPH_EINVAL = -1,     /* bad argument (detected on the host before any work is queued) */
+    SPH_ENOMEM = -2,     /* device allocation failed */
+    SPH_ECUDA = -3,      /* CUDA runtime error (context is poisoned) */
+    SPH_ESTATE = -4,     /* call order: grid / sources / targets / criteria not set */
+    SPH_ECAPACITY = -5,  /* a size exceeds a fixed capacity of this call */
+    SPH_ETIMEOUT = -6,   /* a bounded device wait gave up */
+    SPH_EINTERNAL = -7
+} sph_status;
+
+/* Arithmetic of the far-field translation M2L (Section 2.4 far interactions). */
+enum {
+    SPH_M2L_F32 = 0,     /* FP32 SIMT */
+    SPH_M2L_BF16X3 = 1   /* tensor cores: BF16 hi/lo split, 3 products, FP32 accumulate */
+};
+
+/* Per-call statistics (host struct, optional). */
+typedef struct sph_stats {
+    int64_t n_sources;         /* |J| */
+    int64_t n_targets;         /* |T| */
+    int32_t depth;             /* D: the grid is embedded in a 2^D cube of cells */
+    int32_t max_level;         /* deepest level that holds a box */
+    int64_t n_boxes;
+    int64_t n_leaves;
+    int64_t n_u, n_v, n_w, n_x;/* interaction-list pairs */
+    float ms_select, ms_tree, ms_upward, ms_m2l, ms_downward, ms_near, ms_total; /* GPU ms (0 unless timing on) */
+} sph_stats;
+
+/* Create a context on CUDA device `device`, queuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = default stream).  *out receives the handle. */
+int sph_create(sph_ctx **out, int device, void *cuda_stream);
+/* Release every device buffer the context owns.  NULL is accepted. */
+void sph_destroy(sph_ctx *ctx);
+/* Message for the last failed call on this context (never NULL). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Grid and gas (Section 4 uniform mesh; Eq. gfun coefficients).
+ * nx, ny, nz in [1, 1024]; h > 0 (cm); pO2 > 0 (Torr);
+ * 0 < chi_min < chi_max (cm^-1 Torr^-1).  origin_cm may be NULL (= 0,0,0);
+ * it only shifts coordinates and does not change S_ph. */
+int set_grid(sph_ctx *ctx, int nx, int ny, int nz, const double origin_cm[3], double h_cm,
+             double pO2_torr, double chi_min, double chi_max);
+
+/* Emission field q (float[nx*ny*nz], device, x fastest) and the scale that
+ * turns it into I of Eq. Ifun: I = source_scale * q (source_scale > 0).
+ * Cells with NaN q are never selected. */
+int set_sources(sph_ctx *ctx, const float *q_dev, double source_scale);
+
+/* Target rule input: |E| (float[nx*ny*nz], device) for the electric-field
+ * rule, or an explicit mask (uint8[nx*ny*nz], device, nonzero = target).
+ * At most one may be non-NULL; both NULL makes every cell a target. */
+int set_targets(sph_ctx *ctx, const float *emag_dev, const uint8_t *mask_dev);
+
+/* Adaptive criteria (Section 3) and method options.
+ * i_frac in [0,1] (0: every cell is a source); e_frac in [0,1];
+ * e_applied in the units of |E|; self_mode 0 (no self term) or 1 (ball);
+ * leaf_size in [1, 4096] (the octree splits a box holding more sources or
+ * more targets than this; 0 = 64); m2l_precision one of SPH_M2L_*. */
+int set_criteria(sph_ctx *ctx, double i_frac, double e_frac, double e_applied,
+                 int self_mode, int leaf_size, int m2l_precision);
+
+/* Evaluate S_ph by the adaptive FMM into s_dev (float[nx*ny*nz], device):
+ * S_ph at every target, 0 at every other cell.  stats may be NULL. */
+int eval_sph(sph_ctx *ctx, float *s_dev, sph_stats *stats);
+
+/* Same evaluation with host buffers: copies q (and |E| or the mask, as set
+ * by the last set_targets call's kind: pass the matching host array, or NULL
+ * for "every cell") to context-owned device memory, evaluates, and copies S
+ * back to s_host.  Host pointers need not be pinned. */
+int eval_sph_host(sph_ctx *ctx, const float *q_host, const float *emag_host,
+                  const uint8_t *mask_host, float *s_host, sph_stats *stats);
+
+/* Direct sum of Eq. summation over the same selected sets (no FMM):
+ * fp64 == 0 writes float[nx*ny*nz] in FP32 arithmetic, fp64 == 1 writes
+ * double[nx*ny*nz] in FP64 arithmetic.  0 at non-targets. */
+int eval_direct(sph_ctx *ctx, int fp64, void *s_dev);
+
+/* Selected sets of the last eval: canonical ascending linear indices.
+ * Call with NULL arrays to get the counts; then with arrays of that size.
+ * Synchronises the stream. */
+int sph_get_selection(sph_ctx *ctx, int32_t *src_host, int64_t *n_src,
+                      int32_t *trg_host, int64_t *n_trg);
+
+/* Octree of the last eval.  Call with tree == NULL fields to read the counts
+ * (n_boxes, n_u, n_v, n_w, n_x); then with arrays of those sizes.  Boxes are
+ * ordered by (level, Morton key); pairs are (target box, source box).
+ * Synchronises the stream. */
+typedef struct sph_tree_view {
+    int64_t n_boxes, n_u, n_v, n_w, n_x;
+    int32_t depth;
+    int32_t *level;        /* [n_boxes] */
+    uint32_t *key;         /* [n_boxes] Morton key at its level: x bit 3b, y 3b+1, z 3b+2 */
+    int32_t *src_begin, *src_end, *trg_begin, *trg_end;  /* [n_boxes] ranges in Morton-sorted points */
+    int32_t *parent;       /* [n_boxes], -1 for the root */
+    uint8_t *is_leaf;      /* [n_boxes] */
+    int32_t *u_pairs, *v_pairs, *w_pairs, *x_pairs;      /* [2*n] (target box, source box) */
+} sph_tree_view;
+int sph_get_tree(sph_ctx *ctx, sph_tree_view *tree);
+
+/* Library version string. */
+const char *sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,275 @@
+"""Python binding of libsph (C ABI in include/sph.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+kernels of ``libsph.so``.  Device buffers are PyTorch CUDA tensors (torch is
+used for device memory and streams); host buffers are numpy arrays.  The
+library is loaded on first use and the import fails loudly if it is missing
+or was not built: there is no CPU fallback.
+
+The functions keep the C names: :func:`set_grid`, :func:`set_sources`,
+:func:`set_targets`, :func:`set_criteria`, :func:`eval_sph`,
+:func:`eval_sph_host`, :func:`eval_direct`, plus :class:`Context` and the
+introspection calls :func:`get_selection` / :func:`get_tree`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "eval_sph",
+           "eval_sph_host", "eval_direct", "get_selection", "get_tree", "load", "SphError",
+           "M2L_F32", "M2L_BF16X3", "Stats"]
+
+M2L_F32 = 0
+M2L_BF16X3 = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsph.so")
+_lib = None
+_lock = threading.Lock()
+
+_STATUS = {0: "SPH_OK", -1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ESTATE",
+           -5: "SPH_ECAPACITY", -6: "SPH_ETIMEOUT", -7: "SPH_EINTERNAL"}
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("max_level", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("n_w", ctypes.c_int64),
+                ("n_x", ctypes.c_int64), ("ms_select", ctypes.c_float), ("ms_tree", ctypes.c_float),
+                ("ms_upward", ctypes.c_float), ("ms_m2l", ctypes.c_float), ("ms_downward", ctypes.c_float),
+                ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TreeView(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int64), ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64),
+                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("level", ctypes.c_void_p), ("key", ctypes.c_void_p), ("src_begin", ctypes.c_void_p),
+                ("src_end", ctypes.c_void_p), ("trg_begin", ctypes.c_void_p), ("trg_end", ctypes.c_void_p),
+                ("parent", ctypes.c_void_p), ("is_leaf", ctypes.c_void_p), ("u_pairs", ctypes.c_void_p),
+                ("v_pairs", ctypes.c_void_p), ("w_pairs", ctypes.c_void_p), ("x_pairs", ctypes.c_void_p)]
+
+
+EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
+           "set_criteria", "eval_sph", "eval_sph_host", "eval_direct", "sph_get_selection",
+           "sph_get_tree", "sph_version"]
+
+
+def load(path: str | None = None):
+    """Load libsph.so (built by ``paper_2112_10059_gb300.build``).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError("libsph.so not built at %s: run __graft_entry__.build()" % p)
+        lib = ctypes.CDLL(p)
+        V, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        lib.sph_create.argtypes = [ctypes.POINTER(V), I, V]
+        lib.sph_destroy.argtypes = [V]
+        lib.sph_destroy.restype = None
+        lib.sph_last_error.argtypes = [V]
+        lib.sph_last_error.restype = ctypes.c_char_p
+        lib.set_grid.argtypes = [V, I, I, I, V, D, D, D, D]
+        lib.set_sources.argtypes = [V, V, D]
+        lib.set_targets.argtypes = [V, V, V]
+        lib.set_criteria.argtypes = [V, D, D, D, I, I, I]
+        lib.eval_sph.argtypes = [V, V, V]
+        lib.eval_sph_host.argtypes = [V, V, V, V, V, V]
+        lib.eval_direct.argtypes = [V, I, V]
+        lib.sph_get_selection.argtypes = [V, V, ctypes.POINTER(I64), V, ctypes.POINTER(I64)]
+        lib.sph_get_tree.argtypes = [V, ctypes.POINTER(TreeView)]
+        lib.sph_version.restype = ctypes.c_char_p
+        for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "eval_sph",
+                  "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
+            getattr(lib, f).restype = I
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor, or None."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous array")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """Owns one ``sph_ctx``: device memory, operator cache and the last tree."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.sph_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise SphError(rc, "sph_create failed")
+        self.h = h
+        self.nx = self.ny = self.nz = 0
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.sph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise SphError(rc, self.lib.sph_last_error(self.h).decode())
+        return rc
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny * self.nz
+
+
+def set_grid(ctx: Context, nx, ny, nz, h, pO2, chi_min=0.035, chi_max=2.0, origin=(0.0, 0.0, 0.0)):
+    org = (ctypes.c_double * 3)(*origin)
+    ctx._ck(ctx.lib.set_grid(ctx.h, int(nx), int(ny), int(nz), ctypes.cast(org, ctypes.c_void_p),
+                             float(h), float(pO2), float(chi_min), float(chi_max)))
+    ctx.nx, ctx.ny, ctx.nz = int(nx), int(ny), int(nz)
+
+
+def set_sources(ctx: Context, q, source_scale):
+    """q: float32 CUDA tensor of nx*ny*nz cells (kept alive by the context)."""
+    ctx._keep = [k for k in ctx._keep if k[0] != "q"] + [("q", q)]
+    ctx._ck(ctx.lib.set_sources(ctx.h, _ptr(q), float(source_scale)))
+
+
+def set_targets(ctx: Context, emag=None, mask=None):
+    ctx._keep = [k for k in ctx._keep if k[0] not in ("e", "m")] + [("e", emag), ("m", mask)]
+    ctx._ck(ctx.lib.set_targets(ctx.h, _ptr(emag), _ptr(mask)))
+
+
+def set_criteria(ctx: Context, i_frac=0.0, e_frac=0.0, e_applied=0.0, self_mode=1, leaf_size=64,
+                 m2l_precision=M2L_F32):
+    ctx._ck(ctx.lib.set_criteria(ctx.h, float(i_frac), float(e_frac), float(e_applied), int(self_mode),
+                                 int(leaf_size), int(m2l_precision)))
+
+
+def eval_sph(ctx: Context, out=None, stats: bool = False):
+    """S_ph on the grid (float32 CUDA tensor, 0 at non-targets).  Returns (out, Stats|None)."""
+    import torch
+    if out is None:
+        out = torch.empty(ctx.ncell, dtype=torch.float32, device="cuda:%d" % ctx.device)
+    st = Stats() if stats else None
+    ctx._ck(ctx.lib.eval_sph(ctx.h, _ptr(out), ctypes.byref(st) if st is not None else None))
+    return out, st
+
+
+def eval_sph_host(ctx: Context, q, emag=None, mask=None, out=None, stats: bool = False):
+    """Host-buffer evaluation: numpy in, numpy out (copies inside the call)."""
+    if out is None:
+        out = np.empty(ctx.ncell, np.float32)
+    st = Stats() if stats else None
+    ctx._ck(ctx.lib.eval_sph_host(ctx.h, _hptr(q), _hptr(emag), _hptr(mask), _hptr(out),
+                                  ctypes.byref(st) if st is not None else None))
+    return out, st
+
+
+def eval_direct(ctx: Context, fp64=False, out=None):
+    """Direct sum over the selected sets; float32 (or float64 with fp64=True) CUDA tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(ctx.ncell, dtype=torch.float64 if fp64 else torch.float32,
+                          device="cuda:%d" % ctx.device)
+    ctx._ck(ctx.lib.eval_direct(ctx.h, 1 if fp64 else 0, _ptr(out)))
+    return out
+
+
+def get_selection(ctx: Context):
+    """(J, T): selected source and target linear indices of the last eval, ascending int32."""
+    ns = ctypes.c_int64()
+    nt = ctypes.c_int64()
+    ctx._ck(ctx.lib.sph_get_selection(ctx.h, None, ctypes.byref(ns), None, ctypes.byref(nt)))
+    J = np.empty(ns.value, np.int32)
+    T = np.empty(nt.value, np.int32)
+    ctx._ck(ctx.lib.sph_get_selection(ctx.h, _hptr(J), ctypes.byref(ns), _hptr(T), ctypes.byref(nt)))
+    return J, T
+
+
+def get_tree(ctx: Context):
+    """Octree and lists of the last eval as numpy arrays (pairs sorted (target box, source box))."""
+    tv = TreeView()
+    ctx._ck(ctx.lib.sph_get_tree(ctx.h, ctypes.byref(tv)))
+    nb = tv.n_boxes
+    out = dict(depth=tv.depth, level=np.empty(nb, np.int32), key=np.empty(nb, np.uint32),
+               src_begin=np.empty(nb, np.int32), src_end=np.empty(nb, np.int32),
+               trg_begin=np.empty(nb, np.int32), trg_end=np.empty(nb, np.int32),
+               parent=np.empty(nb, np.int32), leaf=np.empty(nb, np.uint8),
+               U=np.empty((tv.n_u, 2), np.int32), V=np.empty((tv.n_v, 2), np.int32),
+               W=np.empty((tv.n_w, 2), np.int32), X=np.empty((tv.n_x, 2), np.int32))
+    if nb == 0:
+        out["leaf"] = out["leaf"].astype(bool)
+        return out
+    tv.level = _hptr(out["level"])
+    tv.key = _hptr(out["key"])
+    tv.src_begin = _hptr(out["src_begin"])
+    tv.src_end = _hptr(out["src_end"])
+    tv.trg_begin = _hptr(out["trg_begin"])
+    tv.trg_end = _hptr(out["trg_end"])
+    tv.parent = _hptr(out["parent"])
+    tv.is_leaf = _hptr(out["leaf"])
+    tv.u_pairs = _hptr(out["U"])
+    tv.v_pairs = _hptr(out["V"])
+    tv.w_pairs = _hptr(out["W"])
+    tv.x_pairs = _hptr(out["X"])
+    ctx._ck(ctx.lib.sph_get_tree(ctx.h, ctypes.byref(tv)))
+    out["leaf"] = out["leaf"].astype(bool)
+    return out
+
+
+def solve(problem, ctx: Context | None = None, m2l_precision=M2L_F32, leaf_size=None, stats=False,
+          mask=None):
+    """Convenience: evaluate S_ph for a ``sph_inputs.Problem`` (inputs copied to the GPU)."""
+    import torch
+    ctx = ctx or Context(0)
+    set_grid(ctx, problem.nx, problem.ny, problem.nz, problem.h, problem.pO2_torr,
+             problem.chi_min, problem.chi_max, problem.origin)
+    q = torch.from_numpy(problem.q).cuda()
+    set_sources(ctx, q, problem.source_scale)
+    if mask is not None:
+        set_targets(ctx, mask=torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).cuda())
+    elif problem.targets_all or problem.emag is None:
+        set_targets(ctx)
+    else:
+        set_targets(ctx, emag=torch.from_numpy(problem.emag).cuda())
+    set_criteria(ctx, problem.i_frac, problem.e_frac, problem.e_applied, 1,
+                 leaf_size or problem.leaf_size, m2l_precision)
+    out, st = eval_sph(ctx, stats=stats)
+    return ctx, out, st

@@ -1,0 +1,236 @@
+// Selection of sources and targets (paper Section 3: Eq. summationI, Eq. sourcepct,
+// and the electric-field target rule of Section 5) as a GPU stream compaction
+// that emits the selected cells directly in Morton order.
+//
+// Pass 1 (k_grid_max): max q and max |E| over all cells (NaN ignored).
+// Pass 2 (k_select_count): per 16^3 brick (a Morton-contiguous key range),
+//         count selected sources / targets.
+// Pass 3 (k_scan_bricks): exclusive scan of the brick counts.
+// Pass 4 (k_select_emit): per brick, re-evaluate the rules, rank the cells in
+//         Morton order inside the brick and write key, packed (i,j,k) and, for
+//         sources, q (consumers scale it to I_h = source_scale * q * h^3).
+// The rules compare in FP64: (double)q >= i_frac * (double)qmax.
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ unsigned f2ord(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void k_grid_max(const float *__restrict__ q, const float *__restrict__ e, int64_t n,
+                           unsigned *__restrict__ out /* [2] ordered-uint maxima */) {
+    float mq = -INFINITY, me = -INFINITY;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (q) { float v = __ldg(q + i); if (v == v) mq = fmaxf(mq, v); }
+        if (e) { float v = __ldg(e + i); if (v == v) me = fmaxf(me, v); }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+        me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+    }
+    __shared__ float sq[32], se[32];
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sq[w] = mq; se[w] = me; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        mq = l < nw ? sq[l] : -INFINITY;
+        me = l < nw ? se[l] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+            me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+        }
+        if (l == 0) {
+            if (q) atomicMax(out + 0, f2ord(mq));
+            if (e) atomicMax(out + 1, f2ord(me));
+        }
+    }
+}
+
+struct SelRule {
+    int nx, ny, nz;
+    int brick_edge_log2;   // brick edge = 2^b (<= 16)
+    int src_all;           // i_frac == 0
+    double i_frac;
+    int trg_mode;          // 0 all, 1 |E| rule, 2 mask
+    double e_frac, e_app;
+};
+
+// Evaluate both rules for cell (x,y,z); returns bit0 = source, bit1 = target.
+__device__ __forceinline__ int sel_bits(const SelRule &r, const float *q, const float *e,
+                                        const uint8_t *mask, int x, int y, int z,
+                                        double thr_q, double thr_e, bool qpos, float &qv) {
+    if (x >= r.nx || y >= r.ny || z >= r.nz) return 0;
+    int64_t lin = (int64_t)x + (int64_t)r.nx * ((int64_t)y + (int64_t)r.ny * z);
+    qv = __ldg(q + lin);
+    int b = 0;
+    if (r.src_all) b |= 1;
+    else if (qpos && (double)qv >= thr_q) b |= 1;
+    if (r.trg_mode == 0) b |= 2;
+    else if (r.trg_mode == 1) { float ev = __ldg(e + lin); if ((double)ev >= thr_e) b |= 2; }
+    else { if (__ldg(mask + lin)) b |= 2; }
+    return b;
+}
+
+__device__ __forceinline__ void thresholds(const SelRule &r, const unsigned *maxes, double &thr_q,
+                                           double &thr_e, bool &qpos) {
+    float qmax = ord2f(maxes[0]);
+    float emax = ord2f(maxes[1]);
+    qpos = qmax > 0.0f;
+    thr_q = r.i_frac * (double)qmax;
+    thr_e = r.e_app + r.e_frac * ((double)emax - r.e_app);
+}
+
+// One CTA per brick; blockDim.x = 512; brick of up to 16^3 cells, 8 cells per thread
+// in Morton order (thread t owns local keys 8t .. 8t+7).
+template <bool EMIT>
+__global__ void __launch_bounds__(512) k_select_brick(
+        SelRule r, const float *__restrict__ q, const float *__restrict__ e,
+        const uint8_t *__restrict__ mask, const unsigned *__restrict__ maxes,
+        int *__restrict__ cnt_s, int *__restrict__ cnt_t,            // [nbricks] (count pass)
+        const int *__restrict__ off_s, const int *__restrict__ off_t,// [nbricks] (emit pass)
+        uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc, float *__restrict__ src_q,
+        uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc) {
+    const int b = r.brick_edge_log2;
+    const int ncell = 1 << (3 * b);
+    const uint32_t brick = blockIdx.x;
+    uint32_t bx, by, bz;
+    demorton3(brick, bx, by, bz);
+    const int x0 = bx << b, y0 = by << b, z0 = bz << b;
+    double thr_q, thr_e;
+    bool qpos;
+    thresholds(r, maxes, thr_q, thr_e, qpos);
+
+    int my_bits[8];
+    float my_q[8];
+    int ns = 0, nt = 0;
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;   // 8 for a 16^3 brick, fewer for small grids
+    for (int u = 0; u < per; ++u) {
+        int lk = threadIdx.x * per + u;
+        my_bits[u] = 0;
+        my_q[u] = 0.0f;
+        if (lk < ncell && x0 < r.nx && y0 < r.ny && z0 < r.nz) {
+            uint32_t lx, ly, lz;
+            demorton3((uint32_t)lk, lx, ly, lz);
+            float qv = 0.0f;
+            my_bits[u] = sel_bits(r, q, e, mask, x0 + lx, y0 + ly, z0 + lz, thr_q, thr_e, qpos, qv);
+            my_q[u] = qv;
+        }
+        ns += my_bits[u] & 1;
+        nt += (my_bits[u] >> 1) & 1;
+    }
+    // block exclusive scan of (ns, nt) in thread order
+    __shared__ int ws[16], wt[16];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int is = ns, it = nt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int a = __shfl_up_sync(0xffffffffu, is, o);
+        int c = __shfl_up_sync(0xffffffffu, it, o);
+        if (lane >= o) { is += a; it += c; }
+    }
+    if (lane == 31) { ws[w] = is; wt[w] = it; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int a = lane < nw ? ws[lane] : 0;
+        int c = lane < nw ? wt[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int a2 = __shfl_up_sync(0xffffffffu, a, o);
+            int c2 = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) { a += a2; c += c2; }
+        }
+        if (lane < 16) { ws[lane] = a; wt[lane] = c; }
+    }
+    __syncthreads();
+    int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
+    int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
+    if (!EMIT) {
+        if (threadIdx.x == blockDim.x - 1) {
+            cnt_s[brick] = base_s + ns;
+            cnt_t[brick] = base_t + nt;
+        }
+        return;
+    }
+    int ps = off_s[brick] + base_s, pt = off_t[brick] + base_t;
+    for (int u = 0; u < per; ++u) {
+        int lk = threadIdx.x * per + u;
+        if (!my_bits[u]) continue;
+        uint32_t lx, ly, lz;
+        demorton3((uint32_t)lk, lx, ly, lz);
+        uint32_t key = (brick << (3 * b)) | (uint32_t)lk;
+        uint32_t pc = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
+        if (my_bits[u] & 1) {
+            src_key[ps] = key;
+            src_pc[ps] = pc;
+            src_q[ps] = my_q[u];
+            ++ps;
+        }
+        if (my_bits[u] & 2) {
+            trg_key[pt] = key;
+            trg_pc[pt] = pc;
+            ++pt;
+        }
+    }
+}
+
+// Exclusive scan of two int arrays of length n by one CTA of 1024 threads; totals
+// written to tot[0], tot[1].
+__global__ void __launch_bounds__(1024) k_scan2(const int *__restrict__ a, const int *__restrict__ b,
+                                                int *__restrict__ oa, int *__restrict__ ob, int n,
+                                                int *__restrict__ tot) {
+    __shared__ int sa[1024], sb[1024];
+    int per = (n + 1023) / 1024;
+    int beg = threadIdx.x * per, end = min(n, beg + per);
+    int ra = 0, rb = 0;
+    for (int i = beg; i < end; ++i) { ra += a[i]; rb += b[i]; }
+    sa[threadIdx.x] = ra;
+    sb[threadIdx.x] = rb;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int va = threadIdx.x >= o ? sa[threadIdx.x - o] : 0;
+        int vb = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
+        __syncthreads();
+        sa[threadIdx.x] += va;
+        sb[threadIdx.x] += vb;
+        __syncthreads();
+    }
+    int xa = sa[threadIdx.x] - ra, xb = sb[threadIdx.x] - rb;
+    for (int i = beg; i < end; ++i) {
+        oa[i] = xa; xa += a[i];
+        ob[i] = xb; xb += b[i];
+    }
+    if (threadIdx.x == 1023) { tot[0] = sa[1023]; tot[1] = sb[1023]; }
+}
+
+int select_launch(const SelectArgs &A, cudaStream_t st) {
+    int b = A.brick_log2;
+    int nbr = 1 << (3 * (A.D - b));
+    SelRule r;
+    r.nx = A.nx; r.ny = A.ny; r.nz = A.nz;
+    r.brick_edge_log2 = b;
+    r.src_all = A.i_frac == 0.0;
+    r.i_frac = A.i_frac;
+    r.trg_mode = A.mask ? 2 : (A.emag ? 1 : 0);
+    r.e_frac = A.e_frac;
+    r.e_app = A.e_app;
+    int64_t n = (int64_t)A.nx * A.ny * A.nz;
+    cudaMemsetAsync(A.maxes, 0, 2 * sizeof(unsigned), st);
+    int gm = (int)((n + 255) / 256);
+    if (gm > 152 * 16) gm = 152 * 16;
+    k_grid_max<<<gm, 256, 0, st>>>(r.src_all ? nullptr : A.q, r.trg_mode == 1 ? A.emag : nullptr, n, A.maxes);
+    k_select_brick<false><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    k_scan2<<<1, 1024, 0, st>>>(A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
+    k_select_brick<true><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
+                                              A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
+                                              A.trg_key, A.trg_pc);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace sph

@@ -1,0 +1,694 @@
+// C ABI of libsph (declared in include/sph.h): argument checks, context-owned
+// device memory, the operator cache and the orchestration of one evaluation.
+//
+// One evaluation (eval_sph) queues, on the context's stream:
+//   selection (Section 3)        -> Morton-ordered source / target points
+//   octree + U/V/W/X lists       -> Section 2.4 hierarchy
+//   operators (cached)           -> FP64 pseudo-inverses, FP32 translations
+//   upward pass (P2M, M2M)       -> upward equivalent densities (Eq. s2l)
+//   downward pass (M2L, P2L, DC2E, L2L)
+//   leaves (L2P, M2P, P2P)       -> S_ph at every target, 0 elsewhere
+// Box and list counts are data dependent: the host reads them back three times
+// (after selection, after the tree, after list counting) to size buffers and grids.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sph_kernels.cuh"
+#include "../../include/sph.h"
+
+using namespace sph;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct sph_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool poisoned = false;
+    std::string err;
+    // grid / gas
+    bool grid_set = false;
+    int nx = 0, ny = 0, nz = 0, D = 0;
+    double origin[3] = {0, 0, 0};
+    double h = 0, pO2 = 0, chi_min = 0, chi_max = 0, alpha = 0, beta = 0;
+    // inputs
+    bool src_set = false, trg_set = false, crit_set = false;
+    const float *q = nullptr;
+    double source_scale = 0;
+    const float *emag = nullptr;
+    const uint8_t *mask = nullptr;
+    double i_frac = 0, e_frac = 0, e_app = 0;
+    int self_mode = 1, leaf_size = 64, m2l_prec = SPH_M2L_F32;
+    // results of the last eval
+    int64_t ns = 0, nt = 0;
+    int nboxes = 0, Lmax = 0;
+    std::vector<int> lvl_count, lvl_base;
+    int list_tot[4] = {0, 0, 0, 0};
+    bool have_tree = false;
+    // buffers
+    DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
+    DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
+    DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
+    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_wsrc, b_xsrc;
+    DevBuf b_ueq, b_dchk, b_deq;
+    DevBuf o_work, o_uc, o_dc, o_m2m, o_l2l, o_m2l, o_m2lbf, o_slot, o_surf, o_self;
+    DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
+    int *pinned = nullptr;       // small pinned host buffer for read-backs
+    // operator cache key
+    bool ops_valid = false;
+    int ops_D = -1, ops_L = -1;
+    double ops_h = 0, ops_a = 0, ops_b = 0, ops_eps = 0;
+    bool ops_bf = false;
+    double self_int = 0;
+    double pinv_eps = 1e-9;
+};
+
+namespace {
+
+int fail(sph_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(sph_ctx *c, cudaError_t e, const char *where) {
+    c->poisoned = true;
+    return fail(c, SPH_ECUDA, "CUDA error in %s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+int ensure(sph_ctx *c, DevBuf &b, size_t bytes) {
+    if (bytes <= b.cap && b.p) return SPH_OK;
+    if (b.p) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream sync before realloc");
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, SPH_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return SPH_OK;
+}
+
+#define ENS(buf, bytes)                                  \
+    do {                                                 \
+        int r_ = ensure(c, (buf), (bytes));              \
+        if (r_ != SPH_OK) return r_;                     \
+    } while (0)
+
+template <class T>
+T *P(DevBuf &b) { return (T *)b.p; }
+
+int depth_of(int nx, int ny, int nz) {
+    int m = std::max(nx, std::max(ny, nz)), D = 0;
+    while ((1 << D) < m) ++D;
+    return D;
+}
+
+int check_ready(sph_ctx *c) {
+    if (!c) return SPH_EINVAL;
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned by an earlier CUDA error");
+    if (!c->grid_set) return fail(c, SPH_ESTATE, "set_grid has not been called");
+    if (!c->src_set) return fail(c, SPH_ESTATE, "set_sources has not been called");
+    if (!c->trg_set) return fail(c, SPH_ESTATE, "set_targets has not been called");
+    if (!c->crit_set) return fail(c, SPH_ESTATE, "set_criteria has not been called");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return SPH_OK;
+}
+
+KParams make_kp(const sph_ctx *c) {
+    KParams k;
+    const double log2e = 1.4426950408889634;
+    double L = std::log(c->beta / c->alpha);
+    k.a2 = (float)(c->alpha * log2e);
+    k.b2 = (float)((c->beta - c->alpha) * log2e);
+    k.bma = (float)(c->beta - c->alpha);
+    k.C = (float)(1.0 / (4.0 * M_PI * L));
+    k.h = (float)c->h;
+    k.gself = (float)(c->self_int / (c->h * c->h * c->h));
+    return k;
+}
+
+// Selection into Morton-ordered point arrays; reads back (Ns, Nt).
+int run_select(sph_ctx *c) {
+    const int D = c->D;
+    const int b = std::min(4, D);
+    const int64_t nbr = 1ll << (3 * (D - b));
+    const int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
+    ENS(c->b_maxes, 2 * sizeof(unsigned));
+    ENS(c->b_cnt, 2 * nbr * sizeof(int));
+    ENS(c->b_off, 2 * nbr * sizeof(int));
+    ENS(c->b_tot, 16 * sizeof(int));
+    ENS(c->b_skey, ncell * sizeof(uint32_t));
+    ENS(c->b_spc, ncell * sizeof(uint32_t));
+    ENS(c->b_sq, ncell * sizeof(float));
+    ENS(c->b_tkey, ncell * sizeof(uint32_t));
+    ENS(c->b_tpc, ncell * sizeof(uint32_t));
+    SelectArgs A;
+    A.nx = c->nx; A.ny = c->ny; A.nz = c->nz; A.D = D; A.brick_log2 = b;
+    A.q = c->q; A.emag = c->emag; A.mask = c->mask;
+    A.i_frac = c->i_frac; A.e_frac = c->e_frac; A.e_app = c->e_app;
+    A.maxes = P<unsigned>(c->b_maxes);
+    A.cnt_s = P<int>(c->b_cnt); A.cnt_t = A.cnt_s + nbr;
+    A.off_s = P<int>(c->b_off); A.off_t = A.off_s + nbr;
+    A.totals = P<int>(c->b_tot);
+    A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
+    A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
+    if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned, A.totals, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->ns = c->pinned[0];
+    c->nt = c->pinned[1];
+    return SPH_OK;
+}
+
+TreeDev tree_dev(sph_ctx *c) {
+    TreeDev T;
+    T.box_at = P<int>(c->b_boxat);
+    T.lvl_base = P<int>(c->b_lvl);
+    T.lvl_count = T.lvl_base + 16;
+    T.b_level = P<int>(c->b_level);
+    T.b_key = P<uint32_t>(c->b_key);
+    T.b_sb = P<int>(c->b_sb); T.b_se = P<int>(c->b_se);
+    T.b_tb = P<int>(c->b_tb); T.b_te = P<int>(c->b_te);
+    T.b_parent = P<int>(c->b_parent);
+    T.b_leaf = P<uint8_t>(c->b_leaf);
+    return T;
+}
+
+ListDev list_dev(sph_ctx *c) {
+    ListDev L;
+    int nb = std::max(c->nboxes, 1);
+    int *cnt = P<int>(c->b_lcnt), *off = P<int>(c->b_loff);
+    L.u_cnt = cnt; L.v_cnt = cnt + nb; L.w_cnt = cnt + 2 * nb; L.x_cnt = cnt + 3 * nb;
+    L.u_off = off; L.v_off = off + (nb + 1); L.w_off = off + 2 * (nb + 1); L.x_off = off + 3 * (nb + 1);
+    L.u_src = P<int>(c->b_usrc); L.v_src = P<int>(c->b_vsrc); L.w_src = P<int>(c->b_wsrc);
+    L.x_src = P<int>(c->b_xsrc);
+    L.v_oc = P<short>(c->b_vocs);
+    return L;
+}
+
+int run_tree(sph_ctx *c) {
+    const int D = c->D;
+    int S = c->leaf_size;
+    int k = 0;
+    while (k < 4 && (1ll << (3 * (k + 1))) <= S) ++k;
+    const int Lmax = std::max(0, D - k);
+    c->Lmax = Lmax;
+    const int64_t dense_total = dense_off(Lmax + 1);
+    const int64_t top = 1ll << (3 * Lmax);
+    ENS(c->b_boxat, dense_total * sizeof(int));
+    ENS(c->b_flag, top * sizeof(int));
+    ENS(c->b_pos, top * sizeof(int));
+    ENS(c->b_rng, top * sizeof(int4));
+    ENS(c->b_scan, scan_tmp_ints((int)std::max<int64_t>(top, 4 * (dense_total + 1))) * sizeof(int) + 64);
+    ENS(c->b_lvl, 32 * sizeof(int));
+    const int64_t cap = dense_total;   // every slot of every level could hold a box
+    ENS(c->b_level, cap * sizeof(int));
+    ENS(c->b_key, cap * sizeof(uint32_t));
+    ENS(c->b_sb, cap * sizeof(int)); ENS(c->b_se, cap * sizeof(int));
+    ENS(c->b_tb, cap * sizeof(int)); ENS(c->b_te, cap * sizeof(int));
+    ENS(c->b_parent, cap * sizeof(int));
+    ENS(c->b_leaf, cap);
+    TreeArgs A;
+    A.T = tree_dev(c);
+    A.ns = (int)c->ns; A.nt = (int)c->nt; A.S = S; A.D = D; A.Lmax = Lmax;
+    A.skey = P<uint32_t>(c->b_skey); A.tkey = P<uint32_t>(c->b_tkey);
+    A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos); A.rng = P<int4>(c->b_rng);
+    A.scan_tmp = P<int>(c->b_scan);
+    tree_build_launch(A, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->lvl_count.assign(Lmax + 1, 0);
+    c->lvl_base.assign(Lmax + 1, 0);
+    int tot = 0;
+    for (int l = 0; l <= Lmax; ++l) {
+        c->lvl_count[l] = c->pinned[16 + l];
+        c->lvl_base[l] = tot;
+        tot += c->lvl_count[l];
+    }
+    c->nboxes = tot;
+    // lists
+    int nb = std::max(tot, 1);
+    ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
+    ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
+    ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
+    ListDev L = list_dev(c);
+    int *ltot = P<int>(c->b_tot) + 4;
+    lists_count_launch(A.T, L, tot, D, Lmax, P<int>(c->b_scan), ltot, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned, ltot, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 4; ++i) c->list_tot[i] = c->pinned[i];
+    ENS(c->b_usrc, std::max(1, c->list_tot[0]) * sizeof(int));
+    ENS(c->b_vsrc, std::max(1, c->list_tot[1]) * sizeof(int));
+    ENS(c->b_vocs, std::max(1, c->list_tot[1]) * sizeof(short));
+    ENS(c->b_wsrc, std::max(1, c->list_tot[2]) * sizeof(int));
+    ENS(c->b_xsrc, std::max(1, c->list_tot[3]) * sizeof(int));
+    L = list_dev(c);
+    lists_fill_launch(A.T, L, tot, D, Lmax, ltot, c->stream);
+    CK(cudaGetLastError());
+    c->have_tree = true;
+    return SPH_OK;
+}
+
+int run_ops(sph_ctx *c) {
+    bool want_bf = c->m2l_prec == SPH_M2L_BF16X3;
+    if (c->ops_valid && c->ops_D == c->D && c->ops_L >= c->Lmax && c->ops_h == c->h && c->ops_a == c->alpha &&
+        c->ops_b == c->beta && c->ops_eps == c->pinv_eps && (c->ops_bf || !want_bf))
+        return SPH_OK;
+    const int L = c->Lmax;
+    const size_t PP2 = (size_t)SPH_PP * SPH_PP;
+    ENS(c->o_work, ops_work_doubles(L) * sizeof(double));
+    ENS(c->o_uc, (L + 1) * PP2 * sizeof(float));
+    ENS(c->o_dc, (L + 1) * PP2 * sizeof(float));
+    ENS(c->o_m2m, (L + 1) * 8 * PP2 * sizeof(float));
+    ENS(c->o_l2l, (L + 1) * 8 * PP2 * sizeof(float));
+    ENS(c->o_m2l, (L + 1) * 316 * PP2 * sizeof(float));
+    if (want_bf) ENS(c->o_m2lbf, (L + 1) * 316 * 2 * PP2 * sizeof(uint16_t));
+    ENS(c->o_slot, 343 * sizeof(short));
+    ENS(c->o_surf, 160 * 4 * sizeof(float));
+    ENS(c->o_self, 4 * sizeof(double));
+    OpsBuildArgs A;
+    A.D = c->D; A.Lmax = L; A.h = c->h; A.alpha = c->alpha; A.beta = c->beta; A.eps = c->pinv_eps;
+    A.work = P<double>(c->o_work);
+    A.ops.uc2e_t = P<float>(c->o_uc); A.ops.dc2e_t = P<float>(c->o_dc);
+    A.ops.m2m_t = P<float>(c->o_m2m); A.ops.l2l_t = P<float>(c->o_l2l);
+    A.ops.m2l_t = P<float>(c->o_m2l);
+    A.ops.m2l_bf = want_bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
+    A.ops.slot_of_code = P<short>(c->o_slot);
+    A.ops.surf = P<float>(c->o_surf);
+    A.ops.self_int = P<double>(c->o_self);
+    if (ops_build(A, c->stream) != 0) CK(cudaGetLastError());
+    double si = 0;
+    CK(cudaMemcpyAsync(&si, A.ops.self_int, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->self_int = si;
+    c->ops_valid = true;
+    c->ops_D = c->D; c->ops_L = L; c->ops_h = c->h; c->ops_a = c->alpha; c->ops_b = c->beta;
+    c->ops_eps = c->pinv_eps;
+    c->ops_bf = want_bf;
+    return SPH_OK;
+}
+
+OpsDev ops_dev(sph_ctx *c) {
+    OpsDev O;
+    O.uc2e_t = P<float>(c->o_uc); O.dc2e_t = P<float>(c->o_dc);
+    O.m2m_t = P<float>(c->o_m2m); O.l2l_t = P<float>(c->o_l2l);
+    O.m2l_t = P<float>(c->o_m2l);
+    O.m2l_bf = c->ops_bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
+    O.slot_of_code = P<short>(c->o_slot);
+    O.surf = P<float>(c->o_surf);
+    O.self_int = P<double>(c->o_self);
+    return O;
+}
+
+struct PhaseTimer {
+    cudaEvent_t ev[8];
+    bool on = false;
+    int n = 0;
+    void start(bool enable, cudaStream_t st) {
+        on = enable;
+        if (!on) return;
+        for (auto &e : ev) cudaEventCreate(&e);
+        n = 0;
+        mark(st);
+    }
+    void mark(cudaStream_t st) {
+        if (on && n < 8) cudaEventRecord(ev[n++], st);
+    }
+    float ms(int a, int b) {
+        float m = 0;
+        if (on && b < n) cudaEventElapsedTime(&m, ev[a], ev[b]);
+        return m;
+    }
+    ~PhaseTimer() {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
+    PhaseTimer tm;
+    tm.start(stats != nullptr, c->stream);
+    int r = run_select(c);
+    if (r) return r;
+    tm.mark(c->stream);   // 1
+    if ((int64_t)c->nx * c->ny * c->nz > 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
+    }
+    if (c->nt == 0) {
+        c->have_tree = false;
+        if (stats) {
+            memset(stats, 0, sizeof *stats);
+            stats->n_sources = c->ns;
+            stats->depth = c->D;
+        }
+        return SPH_OK;
+    }
+    r = run_tree(c);
+    if (r) return r;
+    tm.mark(c->stream);   // 2
+    r = run_ops(c);
+    if (r) return r;
+    const int nb = c->nboxes;
+    const size_t vb = (size_t)std::max(nb, 1) * SPH_PP * sizeof(float);
+    ENS(c->b_ueq, vb);
+    ENS(c->b_dchk, vb);
+    ENS(c->b_deq, vb);
+    CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
+    FmmDev F;
+    F.T = tree_dev(c);
+    F.L = list_dev(c);
+    F.O = ops_dev(c);
+    F.src_pc = P<uint32_t>(c->b_spc);
+    F.trg_pc = P<uint32_t>(c->b_tpc);
+    F.src_q = P<float>(c->b_sq);
+    F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
+    F.kp = make_kp(c);
+    F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
+    F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk); F.deq = P<float>(c->b_deq);
+    tm.mark(c->stream);   // 3
+    for (int l = c->Lmax; l >= 2; --l) fmm_upward_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+    tm.mark(c->stream);   // 4
+    for (int l = 2; l <= c->Lmax; ++l) {
+        fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
+        if (c->list_tot[3] > 0) fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+        fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+    }
+    tm.mark(c->stream);   // 5
+    fmm_leaf(F, nb, c->leaf_size, out, c->stream);
+    tm.mark(c->stream);   // 6
+    CK(cudaGetLastError());
+    if (stats) {
+        CK(cudaStreamSynchronize(c->stream));
+        memset(stats, 0, sizeof *stats);
+        stats->n_sources = c->ns;
+        stats->n_targets = c->nt;
+        stats->depth = c->D;
+        int ml = 0;
+        for (int l = 0; l <= c->Lmax; ++l)
+            if (c->lvl_count[l] > 0) ml = l;
+        stats->max_level = ml;
+        stats->n_boxes = nb;
+        stats->n_u = c->list_tot[0]; stats->n_v = c->list_tot[1];
+        stats->n_w = c->list_tot[2]; stats->n_x = c->list_tot[3];
+        stats->ms_select = tm.ms(0, 1);
+        stats->ms_tree = tm.ms(1, 2);
+        stats->ms_upward = tm.ms(3, 4);
+        stats->ms_m2l = tm.ms(4, 5);
+        stats->ms_downward = 0;
+        stats->ms_near = tm.ms(5, 6);
+        stats->ms_total = tm.ms(0, 6);
+    }
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sph_version(void) { return "libsph 0.1 (sm_103a)"; }
+
+int sph_create(sph_ctx **out, int device, void *cuda_stream) {
+    if (!out) return SPH_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return SPH_EINVAL;
+    }
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return SPH_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SPH_ECUDA;
+    }
+    if (const char *e = getenv("SPH_PINV_EPS")) c->pinv_eps = atof(e);
+    *out = c;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
+                     &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
+                     &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
+                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_wsrc, &c->b_xsrc,
+                     &c->b_ueq, &c->b_dchk, &c->b_deq, &c->o_work, &c->o_uc, &c->o_dc, &c->o_m2m, &c->o_l2l,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_slot, &c->o_surf, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->h_s};
+    for (DevBuf *b : all)
+        if (b->p) cudaFree(b->p);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+}
+
+const char *sph_last_error(const sph_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int set_grid(sph_ctx *c, int nx, int ny, int nz, const double origin_cm[3], double h_cm, double pO2_torr,
+             double chi_min, double chi_max) {
+    if (!c) return SPH_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024)
+        return fail(c, SPH_EINVAL, "grid dimensions must be in [1, 1024], got %d x %d x %d", nx, ny, nz);
+    if (!(h_cm > 0) || !std::isfinite(h_cm)) return fail(c, SPH_EINVAL, "h must be positive and finite");
+    if (!(pO2_torr > 0) || !std::isfinite(pO2_torr)) return fail(c, SPH_EINVAL, "pO2 must be positive");
+    if (!(chi_min > 0) || !(chi_max > chi_min) || !std::isfinite(chi_max))
+        return fail(c, SPH_EINVAL, "need 0 < chi_min < chi_max");
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->D = depth_of(nx, ny, nz);
+    for (int i = 0; i < 3; ++i) c->origin[i] = origin_cm ? origin_cm[i] : 0.0;
+    c->h = h_cm; c->pO2 = pO2_torr; c->chi_min = chi_min; c->chi_max = chi_max;
+    c->alpha = chi_min * pO2_torr;
+    c->beta = chi_max * pO2_torr;
+    c->grid_set = true;
+    c->have_tree = false;
+    return SPH_OK;
+}
+
+int set_sources(sph_ctx *c, const float *q_dev, double source_scale) {
+    if (!c) return SPH_EINVAL;
+    if (!q_dev) return fail(c, SPH_EINVAL, "q_dev is NULL");
+    if (!(source_scale > 0) || !std::isfinite(source_scale))
+        return fail(c, SPH_EINVAL, "source_scale must be positive and finite");
+    c->q = q_dev;
+    c->source_scale = source_scale;
+    c->src_set = true;
+    return SPH_OK;
+}
+
+int set_targets(sph_ctx *c, const float *emag_dev, const uint8_t *mask_dev) {
+    if (!c) return SPH_EINVAL;
+    if (emag_dev && mask_dev) return fail(c, SPH_EINVAL, "give |E| or a mask, not both");
+    c->emag = emag_dev;
+    c->mask = mask_dev;
+    c->trg_set = true;
+    return SPH_OK;
+}
+
+int set_criteria(sph_ctx *c, double i_frac, double e_frac, double e_applied, int self_mode, int leaf_size,
+                 int m2l_precision) {
+    if (!c) return SPH_EINVAL;
+    if (!(i_frac >= 0 && i_frac <= 1)) return fail(c, SPH_EINVAL, "i_frac must be in [0, 1]");
+    if (!(e_frac >= 0 && e_frac <= 1)) return fail(c, SPH_EINVAL, "e_frac must be in [0, 1]");
+    if (!std::isfinite(e_applied)) return fail(c, SPH_EINVAL, "e_applied must be finite");
+    if (self_mode != 0 && self_mode != 1) return fail(c, SPH_EINVAL, "self_mode must be 0 or 1");
+    if (leaf_size == 0) leaf_size = 64;
+    if (leaf_size < 1 || leaf_size > 4096) return fail(c, SPH_EINVAL, "leaf_size must be in [1, 4096]");
+    if (m2l_precision != SPH_M2L_F32 && m2l_precision != SPH_M2L_BF16X3)
+        return fail(c, SPH_EINVAL, "unknown m2l_precision %d", m2l_precision);
+    c->i_frac = i_frac; c->e_frac = e_frac; c->e_app = e_applied;
+    c->self_mode = self_mode; c->leaf_size = leaf_size; c->m2l_prec = m2l_precision;
+    c->crit_set = true;
+    return SPH_OK;
+}
+
+int eval_sph(sph_ctx *c, float *s_dev, sph_stats *stats) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!s_dev) return fail(c, SPH_EINVAL, "s_dev is NULL");
+    return run_fmm(c, s_dev, stats);
+}
+
+int eval_sph_host(sph_ctx *c, const float *q_host, const float *emag_host, const uint8_t *mask_host,
+                  float *s_host, sph_stats *stats) {
+    if (!c) return SPH_EINVAL;
+    if (!q_host || !s_host) return fail(c, SPH_EINVAL, "q_host and s_host must be non-NULL");
+    if (emag_host && mask_host) return fail(c, SPH_EINVAL, "give |E| or a mask, not both");
+    if (!c->grid_set) return fail(c, SPH_ESTATE, "set_grid has not been called");
+    if (!c->crit_set) return fail(c, SPH_ESTATE, "set_criteria has not been called");
+    if (c->source_scale <= 0) return fail(c, SPH_ESTATE, "set_sources has not been called (source_scale)");
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned by an earlier CUDA error");
+    CK(cudaSetDevice(c->device));
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    ENS(c->h_q, n * sizeof(float));
+    ENS(c->h_s, n * sizeof(float));
+    CK(cudaMemcpyAsync(c->h_q.p, q_host, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    const float *e = nullptr;
+    const uint8_t *m = nullptr;
+    if (emag_host) {
+        ENS(c->h_e, n * sizeof(float));
+        CK(cudaMemcpyAsync(c->h_e.p, emag_host, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        e = P<float>(c->h_e);
+    } else if (mask_host) {
+        ENS(c->h_m, n);
+        CK(cudaMemcpyAsync(c->h_m.p, mask_host, n, cudaMemcpyHostToDevice, c->stream));
+        m = P<uint8_t>(c->h_m);
+    }
+    c->q = P<float>(c->h_q);
+    c->src_set = true;
+    c->emag = e;
+    c->mask = m;
+    c->trg_set = true;
+    int r = run_fmm(c, P<float>(c->h_s), stats);
+    if (r) return r;
+    CK(cudaMemcpyAsync(s_host, c->h_s.p, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+int eval_direct(sph_ctx *c, int fp64, void *s_dev) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!s_dev) return fail(c, SPH_EINVAL, "s_dev is NULL");
+    if (fp64 != 0 && fp64 != 1) return fail(c, SPH_EINVAL, "fp64 must be 0 or 1");
+    r = run_select(c);
+    if (r) return r;
+    // the self term needs the ball integral: computed with the operators' precompute
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    CK(cudaMemsetAsync(s_dev, 0, n * (fp64 ? sizeof(double) : sizeof(float)), c->stream));
+    if (!c->ops_valid || c->ops_h != c->h || c->ops_a != c->alpha || c->ops_b != c->beta) {
+        c->Lmax = 0;   // only the self integral is needed
+        r = run_ops(c);
+        if (r) return r;
+    }
+    DirectArgs A;
+    A.src_pc = P<uint32_t>(c->b_spc);
+    A.src_q = P<float>(c->b_sq);
+    A.wscale = (float)(c->source_scale * c->h * c->h * c->h);
+    A.ns = (int)c->ns;
+    A.trg_pc = P<uint32_t>(c->b_tpc);
+    A.nt = (int)c->nt;
+    A.kp = make_kp(c);
+    double L = std::log(c->beta / c->alpha);
+    A.kp64.alpha = c->alpha; A.kp64.bma = c->beta - c->alpha; A.kp64.C = 1.0 / (4.0 * M_PI * L);
+    A.kp64.h = c->h; A.kp64.vol = c->h * c->h * c->h; A.kp64.scale = c->source_scale;
+    A.kp64.self_int = c->self_int;
+    A.self_mode = c->self_mode; A.nx = c->nx; A.ny = c->ny; A.fp64 = fp64;
+    A.out = s_dev;
+    if (direct_launch(A, c->stream) != 0) CK(cudaGetLastError());
+    return SPH_OK;
+}
+
+int sph_get_selection(sph_ctx *c, int32_t *src_host, int64_t *n_src, int32_t *trg_host, int64_t *n_trg) {
+    if (!c) return SPH_EINVAL;
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned");
+    if (n_src) *n_src = c->ns;
+    if (n_trg) *n_trg = c->nt;
+    if (!src_host && !trg_host) return SPH_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    auto fetch = [&](DevBuf &pcb, int64_t n, int32_t *dst) -> int {
+        std::vector<uint32_t> pc(n);
+        if (n) {
+            cudaError_t e = cudaMemcpy(pc.data(), pcb.p, n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(c, e, "selection read-back");
+        }
+        for (int64_t i = 0; i < n; ++i)
+            dst[i] = pc_i(pc[i]) + c->nx * (pc_j(pc[i]) + c->ny * pc_k(pc[i]));
+        std::sort(dst, dst + n);
+        return SPH_OK;
+    };
+    if (src_host) { int r = fetch(c->b_spc, c->ns, src_host); if (r) return r; }
+    if (trg_host) { int r = fetch(c->b_tpc, c->nt, trg_host); if (r) return r; }
+    return SPH_OK;
+}
+
+int sph_get_tree(sph_ctx *c, sph_tree_view *tv) {
+    if (!c || !tv) return SPH_EINVAL;
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned");
+    if (!c->have_tree) return fail(c, SPH_ESTATE, "no tree: run eval_sph first");
+    tv->n_boxes = c->nboxes;
+    tv->n_u = c->list_tot[0]; tv->n_v = c->list_tot[1]; tv->n_w = c->list_tot[2]; tv->n_x = c->list_tot[3];
+    tv->depth = c->D;
+    if (!tv->level) return SPH_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    const int nb = c->nboxes;
+    auto get = [&](void *dst, DevBuf &b, size_t bytes) -> int {
+        if (!dst || !bytes) return SPH_OK;
+        cudaError_t e = cudaMemcpy(dst, b.p, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "tree read-back");
+        return SPH_OK;
+    };
+    int r = 0;
+    if ((r = get(tv->level, c->b_level, nb * sizeof(int)))) return r;
+    if ((r = get(tv->key, c->b_key, nb * sizeof(uint32_t)))) return r;
+    if ((r = get(tv->src_begin, c->b_sb, nb * sizeof(int)))) return r;
+    if ((r = get(tv->src_end, c->b_se, nb * sizeof(int)))) return r;
+    if ((r = get(tv->trg_begin, c->b_tb, nb * sizeof(int)))) return r;
+    if ((r = get(tv->trg_end, c->b_te, nb * sizeof(int)))) return r;
+    if ((r = get(tv->parent, c->b_parent, nb * sizeof(int)))) return r;
+    if ((r = get(tv->is_leaf, c->b_leaf, nb))) return r;
+    ListDev L = list_dev(c);
+    std::vector<int> off((size_t)nb + 1), src;
+    auto pairs = [&](const int *doff, const int *dsrc, int tot, int32_t *dst) -> int {
+        if (!dst) return SPH_OK;
+        cudaError_t e = cudaMemcpy(off.data(), doff, (nb + 1) * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "list read-back");
+        src.resize(std::max(tot, 1));
+        if (tot) {
+            e = cudaMemcpy(src.data(), dsrc, tot * sizeof(int), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(c, e, "list read-back");
+        }
+        std::vector<std::pair<int, int>> pr;
+        pr.reserve(tot);
+        for (int b = 0; b < nb; ++b)
+            for (int k = off[b]; k < off[b + 1]; ++k) pr.emplace_back(b, src[k]);
+        std::sort(pr.begin(), pr.end());
+        for (size_t k = 0; k < pr.size(); ++k) {
+            dst[2 * k] = pr[k].first;
+            dst[2 * k + 1] = pr[k].second;
+        }
+        return SPH_OK;
+    };
+    if ((r = pairs(L.u_off, L.u_src, c->list_tot[0], tv->u_pairs))) return r;
+    if ((r = pairs(L.v_off, L.v_src, c->list_tot[1], tv->v_pairs))) return r;
+    if ((r = pairs(L.w_off, L.w_src, c->list_tot[2], tv->w_pairs))) return r;
+    if ((r = pairs(L.x_off, L.x_src, c->list_tot[3], tv->x_pairs))) return r;
+    return SPH_OK;
+}
+
+}  // extern "C"

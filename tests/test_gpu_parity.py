@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+* selection index sets and the octree with its U/V/W/X lists: bit-exact;
+* direct sum FP64: max relative error <= 1e-12; FP32: rel-L2 <= 1e-5;
+* adaptive FMM: rel-L2 <= 1e-3 over the targets and max-rel <= 1e-2 on targets
+  with S > 1e-3 max S (the accuracy gate), 0 at every non-target cell.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import sph_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-3
+MAX_REL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2112_10059_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sph):
+    return sph.Context(0)
+
+
+def _check_fmm(S, ref, T, label=""):
+    S = np.asarray(S, np.float64)
+    e2 = oracle.rel_l2(S[T], ref)
+    em = oracle.max_rel(S[T], ref, 1e-3)
+    assert e2 <= REL_L2, "%s rel-L2 %.3e" % (label, e2)
+    assert em <= MAX_REL, "%s max-rel %.3e" % (label, em)
+    others = np.ones(S.size, bool)
+    others[T] = False
+    assert np.all(S[others] == 0.0), label
+    return e2, em
+
+
+def _problems():
+    return [
+        si.config_c0(),
+        si.streamer(n=48, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.3, targets_all=False, leaf_size=32,
+                    sigma_head=0.02, chan_radius=0.02, seed=11, name="s48"),
+        si.streamer(n=40, box=0.4, chan_len=0.2, i_frac=1e-4, targets_all=True, leaf_size=16,
+                    sigma_head=0.015, chan_radius=0.015, seed=12, name="s40_leaf16"),
+    ]
+
+
+@pytest.mark.parametrize("pi", range(3))
+def test_selection_bit_exact(sph, ctx, pi):
+    p = _problems()[pi]
+    sph.solve(p, ctx)
+    J, T = sph.get_selection(ctx)
+    Jo, To = oracle.select(p.q, None if p.targets_all else p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    assert np.array_equal(J, Jo)
+    assert np.array_equal(T, To)
+
+
+def test_selection_threshold_ties_and_mask(sph, ctx):
+    import torch
+    n = 16
+    q = np.zeros(n ** 3, np.float32)
+    q[:100] = 0.5
+    q[100:200] = 0.25          # exactly i_frac * max with i_frac = 0.125, max = 2
+    q[200:300] = np.nextafter(np.float32(0.25), np.float32(0))
+    q[5000] = 2.0
+    q[6000] = np.float32(np.nan)
+    mask = (si.uniform01(3, n ** 3) < 0.2).astype(np.uint8)
+    sph.set_grid(ctx, n, n, n, 0.01, 150.0)
+    sph.set_sources(ctx, torch.from_numpy(q).cuda(), 1.0)
+    sph.set_targets(ctx, mask=torch.from_numpy(mask).cuda())
+    sph.set_criteria(ctx, 0.125, 0.0, 0.0, 1, 8)
+    sph.eval_sph(ctx)
+    J, T = sph.get_selection(ctx)
+    Jo, To = oracle.select(q, None, mask, 0.125)
+    assert np.array_equal(J, Jo) and np.array_equal(T, To)
+    assert 150 in J and 250 not in J and 6000 not in J
+
+
+@pytest.mark.parametrize("case", [(16, 16, 16, 0.05, 0.3, 8, 2), (12, 9, 7, 0.2, 0.1, 4, 3),
+                                  (20, 10, 13, 0.5, 0.02, 6, 5), (32, 32, 32, 0.02, 0.5, 16, 9)])
+def test_tree_bit_exact(sph, ctx, case):
+    import torch
+    nx, ny, nz, fs, ft, S, seed = case
+    n = nx * ny * nz
+    J = np.flatnonzero(si.uniform01(seed, n) < fs).astype(np.int32)
+    T = np.flatnonzero(si.uniform01(seed + 100, n) < ft).astype(np.int32)
+    q = np.zeros(n, np.float32)
+    q[J] = 1.0
+    mask = np.zeros(n, np.uint8)
+    mask[T] = 1
+    sph.set_grid(ctx, nx, ny, nz, 0.01, 150.0)
+    sph.set_sources(ctx, torch.from_numpy(q).cuda(), 1.0)
+    sph.set_targets(ctx, mask=torch.from_numpy(mask).cuda())
+    sph.set_criteria(ctx, 0.5, 0.0, 0.0, 1, S)
+    sph.eval_sph(ctx)
+    g = sph.get_tree(ctx)
+    o = oracle.octree(nx, ny, nz, J, T, S)
+    assert g["depth"] == o["depth"]
+    for k in ("level", "key", "src_begin", "src_end", "trg_begin", "trg_end", "parent"):
+        assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
+    assert np.array_equal(g["leaf"], o["leaf"])
+    for k in ("U", "V", "W", "X"):
+        assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
+
+
+def test_direct_fp64_and_fp32_c0(sph, ctx):
+    p = si.config_c0()
+    sph.solve(p, ctx)
+    ref, J, T = oracle.sph_problem(p)
+    d64 = sph.eval_direct(ctx, fp64=True).cpu().numpy()
+    assert np.max(np.abs(d64[T] / ref - 1)) < 1e-12
+    d32 = sph.eval_direct(ctx, fp64=False).cpu().numpy().astype(np.float64)
+    assert oracle.rel_l2(d32[T], ref) < 1e-5
+    assert oracle.max_rel(d32[T], ref, 0.0) < 1e-4
+
+
+@pytest.mark.parametrize("pi", range(3))
+def test_fmm_small(sph, ctx, pi):
+    p = _problems()[pi]
+    _, out, st = sph.solve(p, ctx, stats=True)
+    ref, J, T = oracle.sph_problem(p)
+    _check_fmm(out.cpu().numpy(), ref, T, p.name)
+
+
+@pytest.mark.parametrize("p_torr", [76.0, 380.0, 760.0])
+def test_fmm_pressures(sph, ctx, p_torr):
+    p = si.streamer(n=64, box=1.0, p_torr=p_torr, chan_len=0.5, i_frac=1e-4, e_frac=0.1, targets_all=False,
+                    seed=21, name="s64_p%d" % p_torr)
+    _, out, st = sph.solve(p, ctx, stats=True)
+    ref, J, T = oracle.sph_problem(p)
+    _check_fmm(out.cpu().numpy(), ref, T, p.name)
+
+
+def test_fmm_nonpow2_grid_with_mask(sph, ctx):
+    import torch
+    nx, ny, nz = 40, 24, 33
+    h = 0.01
+    X, Y, Z = si._grid(nx, ny, nz, h)
+    q = np.exp(-((X - 0.2) ** 2 + (Y - 0.12) ** 2 + (Z - 0.15) ** 2) / 0.03 ** 2)
+    q = (q * 1e20).astype(np.float32).ravel()
+    mask = (si.uniform01(44, q.size) < 0.3).astype(np.uint8)
+    sph.set_grid(ctx, nx, ny, nz, h, 150.0)
+    sph.set_sources(ctx, torch.from_numpy(q).cuda(), 2e-3)
+    sph.set_targets(ctx, mask=torch.from_numpy(mask).cuda())
+    sph.set_criteria(ctx, 1e-3, 0, 0, 1, 12)
+    out, _ = sph.eval_sph(ctx)
+    a, b = oracle.alpha_beta(150.0, 0.035, 2.0)
+    J, T = oracle.select(q, None, mask, 1e-3)
+    ref = oracle.sph(nx, ny, nz, h, a, b, q, 2e-3, J, T)
+    _check_fmm(out.cpu().numpy(), ref, T, "nonpow2")
+
+
+def test_empty_sets(sph, ctx):
+    import torch
+    n = 16
+    sph.set_grid(ctx, n, n, n, 0.01, 150.0)
+    q = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    sph.set_sources(ctx, q, 1.0)
+    sph.set_targets(ctx)
+    sph.set_criteria(ctx, 0.1, 0, 0, 1, 8)      # max q = 0 -> no sources
+    out, st = sph.eval_sph(ctx, stats=True)
+    assert st.n_sources == 0 and float(out.abs().max()) == 0.0
+    q[7] = 1.0
+    sph.set_targets(ctx, mask=torch.zeros(n ** 3, dtype=torch.uint8, device="cuda"))
+    out, st = sph.eval_sph(ctx, stats=True)
+    assert st.n_targets == 0 and float(out.abs().max()) == 0.0
+
+
+def test_host_buffers_match_device(sph, ctx):
+    p = _problems()[1]
+    _, out, _ = sph.solve(p, ctx)
+    dev = out.cpu().numpy()
+    host, _ = sph.eval_sph_host(ctx, p.q, p.emag)
+    assert np.array_equal(dev, host)
+
+
+def test_argument_errors(sph):
+    c = sph.Context(0)
+    with pytest.raises(sph.SphError) as e:
+        sph.eval_sph(c)
+    assert e.value.code == -4
+    with pytest.raises(sph.SphError) as e:
+        sph.set_grid(c, 0, 4, 4, 0.01, 150.0)
+    assert e.value.code == -1
+    with pytest.raises(sph.SphError):
+        sph.set_grid(c, 4, 4, 4, 0.01, 150.0, chi_min=2.0, chi_max=1.0)
+    sph.set_grid(c, 4, 4, 4, 0.01, 150.0)
+    with pytest.raises(sph.SphError):
+        sph.set_criteria(c, 1.5)
+    with pytest.raises(sph.SphError):
+        sph.set_criteria(c, 0.1, leaf_size=5000)
