@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="grid edge (cells)")
     ap.add_argument("--p", type=float, default=760.0, help="pressure (Torr)")
     ap.add_argument("--m2l", default="f32", choices=["f32", "bf16x3"])
+    ap.add_argument("--order", type=int, default=5, help="Chebyshev order of the far field")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -62,7 +63,8 @@ def workload_cfg(p, args):
     return {"workload": "streamer %d^3 in 1 cm, %g Torr, sources I>=1e-4*max, targets |E|>=0.1*max|E|"
                         % (args.n, args.p),
             "grid": [p.nx, p.ny, p.nz], "pressure_torr": args.p, "i_frac": p.i_frac, "e_frac": p.e_frac,
-            "leaf_size": p.leaf_size, "m2l": args.m2l, "l2_flush_between_steps": True,
+            "leaf_size": p.leaf_size, "m2l": args.m2l, "far_field": "chebyshev order %d" % args.order,
+            "l2_flush_between_steps": True,
             "inputs_resident_in_hbm": True}
 
 
@@ -123,15 +125,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def leaf_evals(tree, nt_total):
-    """Algorithmic kernel evaluations of the leaf kernel (L2P + M2P + P2P pairs)."""
+def leaf_evals(tree, nt_total, nnode):
+    """Work of the leaf kernel: L2P interpolation MACs, M2P and P2P kernel evaluations."""
     lev = tree["level"]
     nt = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
     ns = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
     leaf = tree["leaf"]
-    l2p = int(np.sum(nt[leaf & (lev >= 2)]) * 152)
+    l2p = int(np.sum(nt[leaf & (lev >= 2)]) * nnode)
     W = tree["W"]
-    m2p = int(np.sum(nt[W[:, 0]]) * 152) if len(W) else 0
+    m2p = int(np.sum(nt[W[:, 0]]) * nnode) if len(W) else 0
     U = tree["U"]
     p2p = int(np.sum(nt[U[:, 0]] * ns[U[:, 1]])) if len(U) else 0
     return l2p, m2p, p2p
@@ -212,6 +214,7 @@ def main():
     sph.set_targets(ctx, emag=em)
     prec = sph.M2L_BF16X3 if args.m2l == "bf16x3" else sph.M2L_F32
     sph.set_criteria(ctx, p.i_frac, p.e_frac, p.e_applied, 1, p.leaf_size, prec)
+    sph.set_far_field(ctx, sph.FAR_CHEBYSHEV, args.order)
     out = torch.empty(p.ncell, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -262,8 +265,8 @@ def main():
 
     # roofline of the dominant kernel (the leaf kernel: L2P + M2P + P2P kernel evaluations)
     tree = sph.get_tree(ctx)
-    l2p, m2p, p2p = leaf_evals(tree, nt)
-    evals = l2p + m2p + p2p
+    l2p, m2p, p2p = leaf_evals(tree, nt, args.order ** 3)
+    evals = m2p + p2p
     leaf_avg = sum(leaf_ms) / len(leaf_ms)
     clocks = clk.summary()
     f_mhz = clocks["sm_mhz"] or 1920.0
@@ -315,7 +318,7 @@ def main():
                              "peak_basis": "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz,
                              "evals_per_launch": evals, "l2p": l2p, "m2p": m2p, "p2p": p2p,
                              "ms_per_launch": leaf_avg},
-                "clocks": clocks, "gpu_launches": None,
+                "clocks": clocks, "gpu_launches": int(sum(x["n_launches"] for x in step_stats)),
                 "phases_ms": {k: last[k] for k in ("ms_select", "ms_tree", "ms_upward", "ms_m2l", "ms_near",
                                                    "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",

@@ -66,6 +66,14 @@ enum {
     SPH_M2L_BF16X3 = 1   /* tensor cores: BF16 hi/lo split, 3 products, FP32 accumulate */
 };
 
+/* Far-field representation of a box (Section 2.4: artificial source points
+ * with artificial intensities that reproduce its far interactions, Eq. s2l). */
+enum {
+    SPH_FAR_CHEBYSHEV = 0,  /* order^3 tensor Chebyshev nodes, intensities by anterpolation (default, order 5) */
+    SPH_FAR_SURFACE = 1     /* equivalent / check surfaces of Figure fmulloc, order points per cube
+                               edge, intensities by the least-squares solve of Eq. s2l (FP64 SVD) */
+};
+
 /* Per-call statistics (host struct, optional). */
 typedef struct sph_stats {
     int64_t n_sources;         /* |J| */
@@ -76,6 +84,8 @@ typedef struct sph_stats {
     int64_t n_leaves;
     int64_t n_u, n_v, n_w, n_x;/* interaction-list pairs */
     float ms_select, ms_tree, ms_upward, ms_m2l, ms_downward, ms_near, ms_total; /* GPU ms (0 unless timing on) */
+    int64_t n_launches;        /* kernels launched by this eval (operator precompute excluded) */
+    int32_t far_method, far_order;
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -110,6 +120,11 @@ int set_targets(sph_ctx *ctx, const float *emag_dev, const uint8_t *mask_dev);
  * more targets than this; 0 = 64); m2l_precision one of SPH_M2L_*. */
 int set_criteria(sph_ctx *ctx, double i_frac, double e_frac, double e_applied,
                  int self_mode, int leaf_size, int m2l_precision);
+
+/* Far-field representation and its order (see SPH_FAR_*): Chebyshev order in
+ * [2, 8] (p^3 nodes per box), surface order in [3, 10] (points per cube edge).
+ * Default: SPH_FAR_CHEBYSHEV, 5.  Takes effect at the next eval. */
+int sph_set_far_field(sph_ctx *ctx, int method, int order);
 
 /* Evaluate S_ph by the adaptive FMM into s_dev (float[nx*ny*nz], device):
  * S_ph at every target, 0 at every other cell.  stats may be NULL. */

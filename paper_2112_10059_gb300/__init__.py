@@ -19,7 +19,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "eval_sph",
+__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "eval_sph",
            "eval_sph_host", "eval_direct", "get_selection", "get_tree", "load", "SphError",
            "M2L_F32", "M2L_BF16X3", "Stats"]
 
@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("n_w", ctypes.c_int64),
                 ("n_x", ctypes.c_int64), ("ms_select", ctypes.c_float), ("ms_tree", ctypes.c_float),
                 ("ms_upward", ctypes.c_float), ("ms_m2l", ctypes.c_float), ("ms_downward", ctypes.c_float),
-                ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
+                ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -63,8 +64,11 @@ class TreeView(ctypes.Structure):
 
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
-           "set_criteria", "eval_sph", "eval_sph_host", "eval_direct", "sph_get_selection",
-           "sph_get_tree", "sph_version"]
+           "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_host", "eval_direct",
+           "sph_get_selection", "sph_get_tree", "sph_version"]
+
+FAR_CHEBYSHEV = 0
+FAR_SURFACE = 1
 
 
 def load(path: str | None = None):
@@ -87,13 +91,14 @@ def load(path: str | None = None):
         lib.set_sources.argtypes = [V, V, D]
         lib.set_targets.argtypes = [V, V, V]
         lib.set_criteria.argtypes = [V, D, D, D, I, I, I]
+        lib.sph_set_far_field.argtypes = [V, I, I]
         lib.eval_sph.argtypes = [V, V, V]
         lib.eval_sph_host.argtypes = [V, V, V, V, V, V]
         lib.eval_direct.argtypes = [V, I, V]
         lib.sph_get_selection.argtypes = [V, V, ctypes.POINTER(I64), V, ctypes.POINTER(I64)]
         lib.sph_get_tree.argtypes = [V, ctypes.POINTER(TreeView)]
         lib.sph_version.restype = ctypes.c_char_p
-        for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "eval_sph",
+        for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
                   "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I
         _lib = lib
@@ -180,6 +185,11 @@ def set_criteria(ctx: Context, i_frac=0.0, e_frac=0.0, e_applied=0.0, self_mode=
                  m2l_precision=M2L_F32):
     ctx._ck(ctx.lib.set_criteria(ctx.h, float(i_frac), float(e_frac), float(e_applied), int(self_mode),
                                  int(leaf_size), int(m2l_precision)))
+
+
+def set_far_field(ctx: Context, method=FAR_CHEBYSHEV, order=5):
+    """Far-field representation: FAR_CHEBYSHEV (order p, p^3 nodes) or FAR_SURFACE (order = points per edge)."""
+    ctx._ck(ctx.lib.sph_set_far_field(ctx.h, int(method), int(order)))
 
 
 def eval_sph(ctx: Context, out=None, stats: bool = False):

@@ -1,29 +1,30 @@
 // Upward pass, far-field translations, downward pass and the per-leaf
-// evaluation (near field + local expansion) of the kernel-independent FMM
+// evaluation (near field + far field) of the kernel-independent FMM
 // (paper Section 2.4: Eq. nearfar, Eq. s2l and the recursive hierarchy).
 //
-// Surface vectors (check potentials, equivalent densities) are rows of 160
-// floats (152 used) per box.  Matrices are stored transposed ([col][row]) so a
-// CTA with one thread per output row reads each column coalesced.
-//
+// Every box carries two state vectors of n values (rows padded to npad): u_B
+// from the sources inside B and d_B from the sources far from B (see OpsDev for
+// their meaning under FAR_CHEB / FAR_SURFACE).
 //   k_upward     level l, boxes with sources:
-//                  leaf  -> P2M: upward check potential by direct kernel sums
-//                           over the box's sources, then UC2E;
-//                  other -> M2M: sum over children of (UC2E M2M-kernel) ueq_child.
-//   k_m2l_simt   level l, target boxes with a V list: dchk += M2L_o ueq_A (FP32 SIMT).
-//   k_p2l        X list: dchk += kernel sums from the sources of coarser leaves.
-//   k_down       level l: deq = DC2E dchk + (DC2E L2L-kernel) deq_parent.
-//   k_leaf       leaves with targets: S(t) = L2P(deq) + M2P over W + P2P over U
-//                (+ the self term), written to the dense output.
+//                  leaf  -> P2M: FAR_CHEB    u_B[m] = sum_s S_m(y_s) w_s  (anterpolation)
+//                                FAR_SURFACE u_B[i] = sum_s G(|x_i - y_s|) w_s (check potential)
+//                  other -> M2M: u_B = sum over children c of M2M_c u_c.
+//   k_m2l_simt   level l, target boxes with a V list: d_B += M2L_o u_A (FP32 SIMT).
+//   k_p2l        X list: d_B[i] += sum over the coarser leaf's sources of G(|x_i - y_s|) w_s.
+//   k_down       level l >= 3: d_B += L2L_c d_parent.
+//   k_leaf       leaves with targets: S(t) = L2P + M2P over W + P2P over U (+ self term),
+//                written to the dense output.
+//                  L2P: FAR_CHEB    sum_m S_m(x_t) d_B[m] (interpolation);
+//                       FAR_SURFACE E_l[cell of t] . d_B, or FP64 for leaves too coarse for a table.
+//                  M2P: FAR_CHEB    sum_m G(|x_t - y_m^A|) u_A[m];
+//                       FAR_SURFACE FP64 equivalent density of A, then FP64 kernel sums.
+// CTAs of the box kernels have 2 * npad threads: thread t owns state row t % npad
+// and half (t / npad) of the reduction, so each matrix column is read coalesced.
 #include "sph_kernels.cuh"
 
 namespace sph {
 
-constexpr int PPAD = SPH_PP;
-constexpr int P = SPH_P;
-constexpr int NSLOT = 316;
-
-// Position of cell (i,j,k) relative to the centre of box (level l, coords bx,by,bz), in cm.
+// Position of cell (i,j,k) relative to the centre of box (coords bx,by,bz, edge size cells), in cm.
 // Box centre in half-cell units: 2*b*size + size; cell centre: 2*i + 1.
 __device__ __forceinline__ void rel_cell(int i, int j, int k, int bx, int by, int bz, int size, float hh,
                                          float &x, float &y, float &z) {
@@ -38,62 +39,90 @@ __device__ __forceinline__ void box_coords(const TreeDev &T, int b, int &x, int 
     x = (int)ux; y = (int)uy; z = (int)uz;
 }
 
+// 1D Chebyshev Lagrange basis values S_k(x), k < p, of the nodes t[] (FP32).
+__device__ __forceinline__ void cheb_basis(int p, const float *t, float x, float *S) {
+    for (int k = 0; k < p; ++k) {
+        float v = 1.f;
+        for (int j = 0; j < p; ++j)
+            if (j != k) v *= (x - t[j]) / (t[k] - t[j]);
+        S[k] = v;
+    }
+}
+
 // ------------------------------------------------------------------ upward
-// blockDim = 320: thread t handles surface point t % 160 and half (t / 160) of the sources.
-__global__ void __launch_bounds__(320) k_upward(FmmDev F, int level, int box_begin, int box_count) {
+constexpr int UT = 256;   // sources per shared tile
+
+__global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, int box_begin, int box_count) {
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     const TreeDev &T = F.T;
     int sb = T.b_sb[b], se = T.b_se[b];
     if (se <= sb) return;
-    __shared__ float vec[PPAD];
-    __shared__ float part[2][PPAD];
-    __shared__ uint32_t spc[256];
-    __shared__ float sw[256];
-    const int tid = threadIdx.x, pt = tid % PPAD, half = tid / PPAD;
+    const int n = F.O.n, np = F.O.npad;
+    __shared__ float vec[MAXPAD];
+    __shared__ float part[2][MAXPAD];
+    __shared__ uint32_t spc[UT];
+    __shared__ float sw[UT];
+    __shared__ float bas[UT][3][8];
+    __shared__ float tcheb[8];
+    const int tid = threadIdx.x, pt = tid % np, half = tid / np;
     const int size = 1 << (F.D - level);
     const float w = F.kp.h * size * 0.5f;
-    float *ueq = F.ueq + (size_t)b * PPAD;
+    const float hh = 0.5f * F.kp.h;
+    float *u = F.ueq + (size_t)b * np;
     if (T.b_leaf[b]) {
         int bx, by, bz;
         box_coords(T, b, bx, by, bz);
+        const bool cheb = F.O.method == FAR_CHEB;
+        const int p = F.O.order;
+        if (cheb && tid < p) tcheb[tid] = F.O.cheb_t[tid];
         float sx = 0, sy = 0, sz = 0;
-        if (pt < P) {
-            sx = (float)R_UC * w * F.O.surf[4 * pt + 0];
-            sy = (float)R_UC * w * F.O.surf[4 * pt + 1];
-            sz = (float)R_UC * w * F.O.surf[4 * pt + 2];
+        int ia = 0, ib = 0, ic = 0;
+        if (pt < n) {
+            if (cheb) {
+                ia = pt % p; ib = (pt / p) % p; ic = pt / (p * p);
+            } else {
+                sx = (float)F.O.r.uc * w * F.O.nodes[4 * pt + 0];
+                sy = (float)F.O.r.uc * w * F.O.nodes[4 * pt + 1];
+                sz = (float)F.O.r.uc * w * F.O.nodes[4 * pt + 2];
+            }
         }
         float acc = 0.f;
-        const float hh = 0.5f * F.kp.h;
-        for (int s0 = sb; s0 < se; s0 += 256) {
-            int m = min(256, se - s0);
+        const float iw = 1.0f / w;
+        for (int s0 = sb; s0 < se; s0 += UT) {
+            int m = min(UT, se - s0);
             __syncthreads();
-            for (int u = tid; u < m; u += blockDim.x) {
-                spc[u] = F.src_pc[s0 + u];
-                sw[u] = F.src_q[s0 + u] * F.wscale;
+            for (int v = tid; v < m; v += blockDim.x) {
+                uint32_t pc = F.src_pc[s0 + v];
+                spc[v] = pc;
+                sw[v] = F.src_q[s0 + v] * F.wscale;
+                if (cheb) {
+                    float x, y, z;
+                    rel_cell(pc_i(pc), pc_j(pc), pc_k(pc), bx, by, bz, size, hh, x, y, z);
+                    cheb_basis(p, tcheb, x * iw, bas[v][0]);
+                    cheb_basis(p, tcheb, y * iw, bas[v][1]);
+                    cheb_basis(p, tcheb, z * iw, bas[v][2]);
+                }
             }
             __syncthreads();
-            if (pt < P) {
-                for (int u = half; u < m; u += 2) {
-                    uint32_t p = spc[u];
-                    float x, y, z;
-                    rel_cell(pc_i(p), pc_j(p), pc_k(p), bx, by, bz, size, hh, x, y, z);
-                    float dx = sx - x, dy = sy - y, dz = sz - z;
-                    acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), sw[u], acc);
+            if (pt < n) {
+                if (cheb) {
+                    for (int v = half; v < m; v += 2)
+                        acc = fmaf(bas[v][0][ia] * bas[v][1][ib] * bas[v][2][ic], sw[v], acc);
+                } else {
+                    for (int v = half; v < m; v += 2) {
+                        uint32_t pc = spc[v];
+                        float x, y, z;
+                        rel_cell(pc_i(pc), pc_j(pc), pc_k(pc), bx, by, bz, size, hh, x, y, z);
+                        float dx = sx - x, dy = sy - y, dz = sz - z;
+                        acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), sw[v], acc);
+                    }
                 }
             }
         }
         part[half][pt] = acc;
         __syncthreads();
-        if (tid < PPAD) vec[tid] = tid < P ? part[0][tid] + part[1][tid] : 0.f;
-        __syncthreads();
-        // ueq = UC2E * check
-        const float *M = F.O.uc2e_t + (size_t)level * PPAD * PPAD;
-        float a0 = 0.f;
-        for (int j = half; j < P; j += 2) a0 = fmaf(M[j * PPAD + pt], vec[j], a0);
-        part[half][pt] = a0;
-        __syncthreads();
-        if (tid < PPAD) ueq[tid] = tid < P ? part[0][tid] + part[1][tid] : 0.f;
+        if (tid < np) u[tid] = tid < n ? part[0][tid] + part[1][tid] : 0.f;
     } else {
         // M2M from the children (level + 1)
         float acc = 0.f;
@@ -103,145 +132,166 @@ __global__ void __launch_bounds__(320) k_upward(FmmDev F, int level, int box_beg
             int C = bat[ck + c];
             if (C < 0 || T.b_se[C] <= T.b_sb[C]) continue;   // uniform across the CTA
             __syncthreads();
-            if (tid < PPAD) vec[tid] = F.ueq[(size_t)C * PPAD + tid];
+            if (tid < np) vec[tid] = F.ueq[(size_t)C * np + tid];
             __syncthreads();
-            const float *M = F.O.m2m_t + ((size_t)level * 8 + c) * PPAD * PPAD;
-            for (int j = half; j < P; j += 2) acc = fmaf(M[j * PPAD + pt], vec[j], acc);
+            const float *M = F.O.m2m_t + ((size_t)level * 8 + c) * np * np;
+            for (int j = half; j < n; j += 2) acc = fmaf(M[(size_t)j * np + pt], vec[j], acc);
         }
         part[half][pt] = acc;
         __syncthreads();
-        if (tid < PPAD) ueq[tid] = tid < P ? part[0][tid] + part[1][tid] : 0.f;
+        if (tid < np) u[tid] = tid < n ? part[0][tid] + part[1][tid] : 0.f;
     }
 }
 
 void fmm_upward_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
-    k_upward<<<box_count, 320, 0, st>>>(F, level, box_begin, box_count);
+    k_upward<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
-__global__ void __launch_bounds__(320) k_m2l_simt(FmmDev F, int level, int box_begin, int box_count) {
+__global__ void __launch_bounds__(2 * MAXPAD) k_m2l_simt(FmmDev F, int level, int box_begin, int box_count) {
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     int v0 = F.L.v_off[b], v1 = F.L.v_off[b + 1];
     if (v1 <= v0) return;
-    __shared__ float vec[PPAD];
-    __shared__ float part[2][PPAD];
-    const int tid = threadIdx.x, pt = tid % PPAD, half = tid / PPAD;
-    const float *Mlev = F.O.m2l_t + (size_t)level * NSLOT * PPAD * PPAD;
+    const int n = F.O.n, np = F.O.npad;
+    __shared__ float vec[MAXPAD];
+    __shared__ float part[2][MAXPAD];
+    const int tid = threadIdx.x, pt = tid % np, half = tid / np;
+    const float *Mlev = F.O.m2l_t + (size_t)level * NSLOT * np * np;
     float acc = 0.f;
     for (int v = v0; v < v1; ++v) {
         int A = F.L.v_src[v];
         int slot = F.O.slot_of_code[F.L.v_oc[v]];
         __syncthreads();
-        if (tid < PPAD) vec[tid] = F.ueq[(size_t)A * PPAD + tid];
+        if (tid < np) vec[tid] = F.ueq[(size_t)A * np + tid];
         __syncthreads();
-        const float *M = Mlev + (size_t)slot * PPAD * PPAD;
-        for (int j = half; j < P; j += 2) acc = fmaf(M[j * PPAD + pt], vec[j], acc);
+        const float *M = Mlev + (size_t)slot * np * np;
+        for (int j = half; j < n; j += 2) acc = fmaf(M[(size_t)j * np + pt], vec[j], acc);
     }
     part[half][pt] = acc;
     __syncthreads();
-    if (tid < P) F.dchk[(size_t)b * PPAD + tid] += part[0][tid] + part[1][tid];
+    if (tid < n) F.dchk[(size_t)b * np + tid] += part[0][tid] + part[1][tid];
 }
 
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
     (void)m2l_prec;
-    k_m2l_simt<<<box_count, 320, 0, st>>>(F, level, box_begin, box_count);
+    k_m2l_simt<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ P2L (X list)
-__global__ void __launch_bounds__(320) k_p2l(FmmDev F, int level, int box_begin, int box_count) {
+__global__ void __launch_bounds__(2 * MAXPAD) k_p2l(FmmDev F, int level, int box_begin, int box_count) {
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     int x0 = F.L.x_off[b], x1 = F.L.x_off[b + 1];
     if (x1 <= x0) return;
-    __shared__ uint32_t spc[256];
-    __shared__ float sw[256];
-    __shared__ float part[2][PPAD];
-    const int tid = threadIdx.x, pt = tid % PPAD, half = tid / PPAD;
+    const int n = F.O.n, np = F.O.npad;
+    __shared__ uint32_t spc[UT];
+    __shared__ float sw[UT];
+    __shared__ float part[2][MAXPAD];
+    const int tid = threadIdx.x, pt = tid % np, half = tid / np;
     const int size = 1 << (F.D - level);
     const float w = F.kp.h * size * 0.5f;
     const float hh = 0.5f * F.kp.h;
+    const float rad = F.O.method == FAR_CHEB ? w : (float)F.O.r.dc * w;
     int bx, by, bz;
     box_coords(F.T, b, bx, by, bz);
     float cx = 0, cy = 0, cz = 0;
-    if (pt < P) {
-        cx = (float)R_DC * w * F.O.surf[4 * pt + 0];
-        cy = (float)R_DC * w * F.O.surf[4 * pt + 1];
-        cz = (float)R_DC * w * F.O.surf[4 * pt + 2];
+    if (pt < n) {
+        cx = rad * F.O.nodes[4 * pt + 0];
+        cy = rad * F.O.nodes[4 * pt + 1];
+        cz = rad * F.O.nodes[4 * pt + 2];
     }
     float acc = 0.f;
     for (int x = x0; x < x1; ++x) {
         int A = F.L.x_src[x];
         int sb = F.T.b_sb[A], se = F.T.b_se[A];
-        for (int s0 = sb; s0 < se; s0 += 256) {
-            int m = min(256, se - s0);
+        for (int s0 = sb; s0 < se; s0 += UT) {
+            int m = min(UT, se - s0);
             __syncthreads();
-            for (int u = tid; u < m; u += blockDim.x) {
-                spc[u] = F.src_pc[s0 + u];
-                sw[u] = F.src_q[s0 + u] * F.wscale;
+            for (int v = tid; v < m; v += blockDim.x) {
+                spc[v] = F.src_pc[s0 + v];
+                sw[v] = F.src_q[s0 + v] * F.wscale;
             }
             __syncthreads();
-            if (pt < P) {
-                for (int u = half; u < m; u += 2) {
-                    uint32_t p = spc[u];
+            if (pt < n) {
+                for (int v = half; v < m; v += 2) {
+                    uint32_t pc = spc[v];
                     float sx, sy, sz;
-                    rel_cell(pc_i(p), pc_j(p), pc_k(p), bx, by, bz, size, hh, sx, sy, sz);
+                    rel_cell(pc_i(pc), pc_j(pc), pc_k(pc), bx, by, bz, size, hh, sx, sy, sz);
                     float dx = cx - sx, dy = cy - sy, dz = cz - sz;
-                    acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), sw[u], acc);
+                    acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), sw[v], acc);
                 }
             }
         }
     }
     part[half][pt] = acc;
     __syncthreads();
-    if (tid < P) F.dchk[(size_t)b * PPAD + tid] += part[0][tid] + part[1][tid];
+    if (tid < n) F.dchk[(size_t)b * np + tid] += part[0][tid] + part[1][tid];
 }
 
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
-    k_p2l<<<box_count, 320, 0, st>>>(F, level, box_begin, box_count);
+    k_p2l<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
 }
 
-// ------------------------------------------------------------------ downward: DC2E + L2L
-__global__ void __launch_bounds__(320) k_down(FmmDev F, int level, int box_begin, int box_count) {
+// ------------------------------------------------------------------ downward: L2L
+__global__ void __launch_bounds__(2 * MAXPAD) k_down(FmmDev F, int level, int box_begin, int box_count) {
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     const TreeDev &T = F.T;
     if (T.b_te[b] <= T.b_tb[b]) return;
-    __shared__ float vchk[PPAD], vpar[PPAD];
-    __shared__ float part[2][PPAD];
-    const int tid = threadIdx.x, pt = tid % PPAD, half = tid / PPAD;
     int parent = T.b_parent[b];
-    bool has_parent = level >= 3 && parent >= 0;
-    if (tid < PPAD) {
-        vchk[tid] = F.dchk[(size_t)b * PPAD + tid];
-        vpar[tid] = has_parent ? F.deq[(size_t)parent * PPAD + tid] : 0.f;
-    }
+    if (level < 3 || parent < 0) return;
+    const int n = F.O.n, np = F.O.npad;
+    __shared__ float vpar[MAXPAD];
+    __shared__ float part[2][MAXPAD];
+    const int tid = threadIdx.x, pt = tid % np, half = tid / np;
+    if (tid < np) vpar[tid] = F.dchk[(size_t)parent * np + tid];
     __syncthreads();
-    const float *Md = F.O.dc2e_t + (size_t)level * PPAD * PPAD;
+    int c = (int)(T.b_key[b] & 7u);
+    const float *Ml = F.O.l2l_t + ((size_t)level * 8 + c) * np * np;
     float acc = 0.f;
-    for (int j = half; j < P; j += 2) acc = fmaf(Md[j * PPAD + pt], vchk[j], acc);
-    if (has_parent) {
-        int c = (int)(T.b_key[b] & 7u);
-        const float *Ml = F.O.l2l_t + ((size_t)level * 8 + c) * PPAD * PPAD;
-        for (int j = half; j < P; j += 2) acc = fmaf(Ml[j * PPAD + pt], vpar[j], acc);
-    }
+    for (int j = half; j < n; j += 2) acc = fmaf(Ml[(size_t)j * np + pt], vpar[j], acc);
     part[half][pt] = acc;
     __syncthreads();
-    if (tid < PPAD) F.deq[(size_t)b * PPAD + tid] = tid < P ? part[0][tid] + part[1][tid] : 0.f;
+    if (tid < n) F.dchk[(size_t)b * np + tid] += part[0][tid] + part[1][tid];
 }
 
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
-    if (box_count <= 0 || level < 2) return;
-    k_down<<<box_count, 320, 0, st>>>(F, level, box_begin, box_count);
+    if (box_count <= 0 || level < 3) return;
+    k_down<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ leaves
-// One CTA (128 threads) per box; thread t handles targets t, t+128, ... of the box.
-constexpr int LT = 128;
+constexpr int LT = 128;   // threads per leaf CTA
 constexpr int LS = 512;   // sources per shared tile
+
+// eq[i] = sum_k pinv[i][k] chk[k] in FP64 (pinv row-major n x n); all LT threads, ends synchronised.
+__device__ __forceinline__ void equiv64(const double *__restrict__ pinv, const float *__restrict__ chk, int n,
+                                        double *eq) {
+    for (int i = threadIdx.x; i < n; i += LT) {
+        double a = 0.0;
+        for (int k = 0; k < n; ++k) a = fma(pinv[(size_t)i * n + k], (double)chk[k], a);
+        eq[i] = a;
+    }
+    __syncthreads();
+}
+
+// sum_j G(|x - r u_j|) eq[j] in FP64, x relative to the surface centre.
+__device__ __forceinline__ double eval64(const double *eq, int n, float r, float x, float y, float z, const FmmDev &F,
+                                         const float4 *sv) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double dx = (double)x - (double)r * sv[j].x;
+        double dy = (double)y - (double)r * sv[j].y;
+        double dz = (double)z - (double)r * sv[j].z;
+        double R = sqrt(dx * dx + dy * dy + dz * dz);
+        s = fma(g64(R, F.alpha, F.beta, F.C64), eq[j], s);
+    }
+    return s;
+}
 
 __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__restrict__ out) {
     int b = blockIdx.x;
@@ -249,14 +299,23 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
     if (!T.b_leaf[b]) return;
     int tb = T.b_tb[b], te = T.b_te[b];
     if (te <= tb) return;
+    const int n = F.O.n, np = F.O.npad;
+    const bool cheb = F.O.method == FAR_CHEB;
+    const int p = F.O.order;
     const int level = T.b_level[b];
     const int size = 1 << (F.D - level);
     const float hh = 0.5f * F.kp.h;
     int bx, by, bz;
     box_coords(T, b, bx, by, bz);
-    __shared__ float4 sv[PPAD];          // equivalent points (x, y, z, density)
+    __shared__ float4 sv[MAXPAD];                  // unit node positions
+    __shared__ __align__(16) float sd[MAXPAD];     // a state vector
+    __shared__ double sd64[MAXPAD];
     __shared__ uint32_t spc[LS];
     __shared__ float sw[LS];
+    __shared__ float tcheb[8];
+    for (int j = threadIdx.x; j < np; j += LT)
+        sv[j] = make_float4(F.O.nodes[4 * j], F.O.nodes[4 * j + 1], F.O.nodes[4 * j + 2], 0.f);
+    if (cheb && threadIdx.x < p) tcheb[threadIdx.x] = F.O.cheb_t[threadIdx.x];
 
     for (int t0 = tb; t0 < te; t0 += LT) {
         int t = t0 + threadIdx.x;
@@ -266,24 +325,52 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
         float tx, ty, tz;
         rel_cell(ti, tj, tk, bx, by, bz, size, hh, tx, ty, tz);
         float acc = 0.f;
-        // L2P: downward equivalent density of this box (levels >= 2)
+        // ---- L2P (levels >= 2)
         if (level >= 2) {
             const float w = F.kp.h * size * 0.5f;
             __syncthreads();
-            for (int j = threadIdx.x; j < P; j += LT) {
-                sv[j] = make_float4((float)R_DE * w * F.O.surf[4 * j + 0], (float)R_DE * w * F.O.surf[4 * j + 1],
-                                    (float)R_DE * w * F.O.surf[4 * j + 2], F.deq[(size_t)b * PPAD + j]);
-            }
-            __syncthreads();
-            if (act) {
-                for (int j = 0; j < P; ++j) {
-                    float4 e = sv[j];
-                    float dx = tx - e.x, dy = ty - e.y, dz = tz - e.z;
-                    acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), e.w, acc);
+            if (cheb) {
+                for (int j = threadIdx.x; j < np; j += LT) sd[j] = F.dchk[(size_t)b * np + j];
+                __syncthreads();
+                if (act) {
+                    float Sx[8], Sy[8], Sz[8];
+                    const float iw = 1.0f / w;
+                    cheb_basis(p, tcheb, tx * iw, Sx);
+                    cheb_basis(p, tcheb, ty * iw, Sy);
+                    cheb_basis(p, tcheb, tz * iw, Sz);
+                    for (int c = 0; c < p; ++c) {
+                        float zc = 0.f;
+                        for (int bb = 0; bb < p; ++bb) {
+                            const float *row = sd + p * (bb + p * c);
+                            float r = 0.f;
+                            for (int a = 0; a < p; ++a) r = fmaf(Sx[a], row[a], r);
+                            zc = fmaf(Sy[bb], r, zc);
+                        }
+                        acc = fmaf(Sz[c], zc, acc);
+                    }
+                }
+            } else {
+                const long long eo = F.O.e_off[level];
+                if (eo >= 0) {
+                    for (int j = threadIdx.x; j < np; j += LT) sd[j] = F.dchk[(size_t)b * np + j];
+                    __syncthreads();
+                    if (act) {
+                        int lx = ti - bx * size, ly = tj - by * size, lz = tk - bz * size;
+                        const float4 *row =
+                            (const float4 *)(F.O.e_tab + eo + (size_t)(lx + size * (ly + size * lz)) * np);
+                        const float4 *d4 = (const float4 *)sd;
+                        for (int j = 0; j < np / 4; ++j) {
+                            float4 a = __ldg(row + j), v = d4[j];
+                            acc = fmaf(a.x, v.x, fmaf(a.y, v.y, fmaf(a.z, v.z, fmaf(a.w, v.w, acc))));
+                        }
+                    }
+                } else {
+                    equiv64(F.O.dc64 + (size_t)level * F.O.pinv_stride, F.dchk + (size_t)b * np, n, sd64);
+                    if (act) acc += (float)eval64(sd64, n, (float)F.O.r.de * w, tx, ty, tz, F, sv);
                 }
             }
         }
-        // M2P over the W list: upward equivalent densities of finer boxes
+        // ---- M2P over the W list (finer boxes A not adjacent to this leaf)
         for (int wv = F.L.w_off[b]; wv < F.L.w_off[b + 1]; ++wv) {
             int A = F.L.w_src[wv];
             int al = T.b_level[A];
@@ -291,24 +378,24 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
             int ax, ay, az;
             box_coords(T, A, ax, ay, az);
             const float aw = F.kp.h * asz * 0.5f;
-            // target position relative to A's centre
             float rx, ry, rz;
             rel_cell(ti, tj, tk, ax, ay, az, asz, hh, rx, ry, rz);
             __syncthreads();
-            for (int j = threadIdx.x; j < P; j += LT) {
-                sv[j] = make_float4((float)R_UE * aw * F.O.surf[4 * j + 0], (float)R_UE * aw * F.O.surf[4 * j + 1],
-                                    (float)R_UE * aw * F.O.surf[4 * j + 2], F.ueq[(size_t)A * PPAD + j]);
-            }
-            __syncthreads();
-            if (act) {
-                for (int j = 0; j < P; ++j) {
-                    float4 e = sv[j];
-                    float dx = rx - e.x, dy = ry - e.y, dz = rz - e.z;
-                    acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), e.w, acc);
+            if (cheb) {
+                for (int j = threadIdx.x; j < np; j += LT) sd[j] = F.ueq[(size_t)A * np + j];
+                __syncthreads();
+                if (act) {
+                    for (int j = 0; j < n; ++j) {
+                        float dx = rx - aw * sv[j].x, dy = ry - aw * sv[j].y, dz = rz - aw * sv[j].z;
+                        acc = fmaf(g_of_r2(dx * dx + dy * dy + dz * dz, F.kp), sd[j], acc);
+                    }
                 }
+            } else {
+                equiv64(F.O.uc64 + (size_t)al * F.O.pinv_stride, F.ueq + (size_t)A * np, n, sd64);
+                if (act) acc += (float)eval64(sd64, n, (float)F.O.r.ue * aw, rx, ry, rz, F, sv);
             }
         }
-        // P2P over the U list (near field, Eq. nearfar), with the self term
+        // ---- P2P over the U list (near field, Eq. nearfar), with the self term
         for (int uv = F.L.u_off[b]; uv < F.L.u_off[b + 1]; ++uv) {
             int A = F.L.u_src[uv];
             int sb = T.b_sb[A], se = T.b_se[A];
@@ -322,8 +409,8 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
                 __syncthreads();
                 if (act) {
                     for (int u = 0; u < m; ++u) {
-                        uint32_t p = spc[u];
-                        int di = ti - pc_i(p), dj = tj - pc_j(p), dk = tk - pc_k(p);
+                        uint32_t pc = spc[u];
+                        int di = ti - pc_i(pc), dj = tj - pc_j(pc), dk = tk - pc_k(pc);
                         int d2 = di * di + dj * dj + dk * dk;
                         float g = d2 ? g_of_cells(d2, F.kp) : (F.self_mode ? F.kp.gself : 0.f);
                         acc = fmaf(g, sw[u], acc);

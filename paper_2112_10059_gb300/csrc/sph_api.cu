@@ -4,9 +4,9 @@
 // One evaluation (eval_sph) queues, on the context's stream:
 //   selection (Section 3)        -> Morton-ordered source / target points
 //   octree + U/V/W/X lists       -> Section 2.4 hierarchy
-//   operators (cached)           -> FP64 pseudo-inverses, FP32 translations
-//   upward pass (P2M, M2M)       -> upward equivalent densities (Eq. s2l)
-//   downward pass (M2L, P2L, DC2E, L2L)
+//   operators (cached)           -> FP64 pseudo-inverses folded into FP32 translations
+//   upward pass (P2M, M2M)       -> upward check potentials (Eq. s2l right-hand sides)
+//   downward pass (M2L, P2L, L2L)-> downward check potentials
 //   leaves (L2P, M2P, P2P)       -> S_ph at every target, 0 elsewhere
 // Box and list counts are data dependent: the host reads them back three times
 // (after selection, after the tree, after list counting) to size buffers and grids.
@@ -56,13 +56,14 @@ struct sph_ctx {
     std::vector<int> lvl_count, lvl_base;
     int list_tot[4] = {0, 0, 0, 0};
     bool have_tree = false;
+    int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
     DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_wsrc, b_xsrc;
-    DevBuf b_ueq, b_dchk, b_deq;
-    DevBuf o_work, o_uc, o_dc, o_m2m, o_l2l, o_m2l, o_m2lbf, o_slot, o_surf, o_self;
+    DevBuf b_ueq, b_dchk;
+    DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
     // operator cache key
@@ -71,7 +72,12 @@ struct sph_ctx {
     double ops_h = 0, ops_a = 0, ops_b = 0, ops_eps = 0;
     bool ops_bf = false;
     double self_int = 0;
-    double pinv_eps = 1e-9;
+    double pinv_eps = 1e-5;
+    Radii radii = RADII_DEFAULT;
+    Radii ops_r = {0, 0, 0, 0};
+    int far_method = FAR_CHEB, far_order = 5;
+    int ops_method = -1, ops_order = -1;
+    int npad() const { return pad16(far_n(far_method, far_order)); }
 };
 
 namespace {
@@ -183,6 +189,7 @@ int run_select(sph_ctx *c) {
     A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
     A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
+    c->launches += 4;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->ns = c->pinned[0];
@@ -245,6 +252,7 @@ int run_tree(sph_ctx *c) {
     A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos); A.rng = P<int4>(c->b_rng);
     A.scan_tmp = P<int>(c->b_scan);
     tree_build_launch(A, c->stream);
+    c->launches += 1 + 5 * Lmax;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -276,38 +284,54 @@ int run_tree(sph_ctx *c) {
     ENS(c->b_xsrc, std::max(1, c->list_tot[3]) * sizeof(int));
     L = list_dev(c);
     lists_fill_launch(A.T, L, tot, D, Lmax, ltot, c->stream);
+    if (tot > 0) c->launches += 15;
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
 }
 
+void fill_ops(sph_ctx *c, OpsDev &O, int D, int L, bool bf) {
+    O.method = c->far_method;
+    O.order = c->far_order;
+    O.n = far_n(c->far_method, c->far_order);
+    O.npad = pad16(O.n);
+    O.e_tab = P<float>(c->o_etab);
+    O.r = c->radii;
+    O.m2m_t = P<float>(c->o_m2m); O.l2l_t = P<float>(c->o_l2l);
+    O.m2l_t = P<float>(c->o_m2l);
+    O.m2l_bf = bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
+    O.slot_of_code = P<short>(c->o_slot);
+    O.nodes = P<float>(c->o_surf);
+    O.cheb_t = P<float>(c->o_cheb);
+    O.self_int = P<double>(c->o_self);
+    ops_layout(D, L, P<double>(c->o_work), O);
+}
+
 int run_ops(sph_ctx *c) {
     bool want_bf = c->m2l_prec == SPH_M2L_BF16X3;
     if (c->ops_valid && c->ops_D == c->D && c->ops_L >= c->Lmax && c->ops_h == c->h && c->ops_a == c->alpha &&
-        c->ops_b == c->beta && c->ops_eps == c->pinv_eps && (c->ops_bf || !want_bf))
+        c->ops_b == c->beta && c->ops_eps == c->pinv_eps && (c->ops_bf || !want_bf) &&
+        c->ops_method == c->far_method && c->ops_order == c->far_order &&
+        c->ops_r.ue == c->radii.ue && c->ops_r.uc == c->radii.uc && c->ops_r.dc == c->radii.dc &&
+        c->ops_r.de == c->radii.de)
         return SPH_OK;
     const int L = c->Lmax;
-    const size_t PP2 = (size_t)SPH_PP * SPH_PP;
-    ENS(c->o_work, ops_work_doubles(L) * sizeof(double));
-    ENS(c->o_uc, (L + 1) * PP2 * sizeof(float));
-    ENS(c->o_dc, (L + 1) * PP2 * sizeof(float));
+    const int n = far_n(c->far_method, c->far_order), np = pad16(n);
+    const size_t PP2 = (size_t)np * np;
+    ENS(c->o_work, ops_work_doubles(c->far_method, n, L) * sizeof(double));
+    ENS(c->o_etab, ops_etab_floats(c->far_method, np, c->D, L) * sizeof(float));
     ENS(c->o_m2m, (L + 1) * 8 * PP2 * sizeof(float));
     ENS(c->o_l2l, (L + 1) * 8 * PP2 * sizeof(float));
     ENS(c->o_m2l, (L + 1) * 316 * PP2 * sizeof(float));
     if (want_bf) ENS(c->o_m2lbf, (L + 1) * 316 * 2 * PP2 * sizeof(uint16_t));
     ENS(c->o_slot, 343 * sizeof(short));
-    ENS(c->o_surf, 160 * 4 * sizeof(float));
+    ENS(c->o_surf, (size_t)np * 4 * sizeof(float));
+    ENS(c->o_cheb, 16 * sizeof(float));
     ENS(c->o_self, 4 * sizeof(double));
     OpsBuildArgs A;
     A.D = c->D; A.Lmax = L; A.h = c->h; A.alpha = c->alpha; A.beta = c->beta; A.eps = c->pinv_eps;
     A.work = P<double>(c->o_work);
-    A.ops.uc2e_t = P<float>(c->o_uc); A.ops.dc2e_t = P<float>(c->o_dc);
-    A.ops.m2m_t = P<float>(c->o_m2m); A.ops.l2l_t = P<float>(c->o_l2l);
-    A.ops.m2l_t = P<float>(c->o_m2l);
-    A.ops.m2l_bf = want_bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
-    A.ops.slot_of_code = P<short>(c->o_slot);
-    A.ops.surf = P<float>(c->o_surf);
-    A.ops.self_int = P<double>(c->o_self);
+    fill_ops(c, A.ops, c->D, L, want_bf);
     if (ops_build(A, c->stream) != 0) CK(cudaGetLastError());
     double si = 0;
     CK(cudaMemcpyAsync(&si, A.ops.self_int, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -317,18 +341,16 @@ int run_ops(sph_ctx *c) {
     c->ops_D = c->D; c->ops_L = L; c->ops_h = c->h; c->ops_a = c->alpha; c->ops_b = c->beta;
     c->ops_eps = c->pinv_eps;
     c->ops_bf = want_bf;
+    c->ops_r = c->radii;
+    c->ops_method = c->far_method;
+    c->ops_order = c->far_order;
     return SPH_OK;
 }
 
 OpsDev ops_dev(sph_ctx *c) {
     OpsDev O;
-    O.uc2e_t = P<float>(c->o_uc); O.dc2e_t = P<float>(c->o_dc);
-    O.m2m_t = P<float>(c->o_m2m); O.l2l_t = P<float>(c->o_l2l);
-    O.m2l_t = P<float>(c->o_m2l);
-    O.m2l_bf = c->ops_bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
-    O.slot_of_code = P<short>(c->o_slot);
-    O.surf = P<float>(c->o_surf);
-    O.self_int = P<double>(c->o_self);
+    fill_ops(c, O, c->ops_D, c->ops_L, c->ops_bf);
+    O.r = c->ops_r;
     return O;
 }
 
@@ -360,6 +382,7 @@ struct PhaseTimer {
 int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     PhaseTimer tm;
     tm.start(stats != nullptr, c->stream);
+    c->launches = 0;
     int r = run_select(c);
     if (r) return r;
     tm.mark(c->stream);   // 1
@@ -372,6 +395,7 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
             memset(stats, 0, sizeof *stats);
             stats->n_sources = c->ns;
             stats->depth = c->D;
+            stats->n_launches = c->launches;
         }
         return SPH_OK;
     }
@@ -381,10 +405,9 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     r = run_ops(c);
     if (r) return r;
     const int nb = c->nboxes;
-    const size_t vb = (size_t)std::max(nb, 1) * SPH_PP * sizeof(float);
+    const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_deq, vb);
     CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
     FmmDev F;
     F.T = tree_dev(c);
@@ -396,17 +419,27 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
     F.kp = make_kp(c);
     F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
-    F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk); F.deq = P<float>(c->b_deq);
+    F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
+    F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
     tm.mark(c->stream);   // 3
-    for (int l = c->Lmax; l >= 2; --l) fmm_upward_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+    for (int l = c->Lmax; l >= 2; --l) {
+        fmm_upward_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+        c->launches += c->lvl_count[l] > 0;
+    }
     tm.mark(c->stream);   // 4
     for (int l = 2; l <= c->Lmax; ++l) {
         fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
-        if (c->list_tot[3] > 0) fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+        c->launches += c->lvl_count[l] > 0;
+        if (c->list_tot[3] > 0) {
+            fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+            c->launches += c->lvl_count[l] > 0;
+        }
         fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+        c->launches += l >= 3 && c->lvl_count[l] > 0;
     }
     tm.mark(c->stream);   // 5
     fmm_leaf(F, nb, c->leaf_size, out, c->stream);
+    c->launches += nb > 0;
     tm.mark(c->stream);   // 6
     CK(cudaGetLastError());
     if (stats) {
@@ -429,6 +462,9 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         stats->ms_downward = 0;
         stats->ms_near = tm.ms(5, 6);
         stats->ms_total = tm.ms(0, 6);
+        stats->n_launches = c->launches;
+        stats->far_method = c->far_method;
+        stats->far_order = c->far_order;
     }
     return SPH_OK;
 }
@@ -457,6 +493,14 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
         return SPH_ECUDA;
     }
     if (const char *e = getenv("SPH_PINV_EPS")) c->pinv_eps = atof(e);
+    if (const char *e = getenv("SPH_FAR")) {
+        int m, o;
+        if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }
+    }
+    if (const char *e = getenv("SPH_RADII")) {
+        Radii r;
+        if (sscanf(e, "%lf,%lf,%lf,%lf", &r.ue, &r.uc, &r.dc, &r.de) == 4) c->radii = r;
+    }
     *out = c;
     return SPH_OK;
 }
@@ -469,8 +513,8 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_wsrc, &c->b_xsrc,
-                     &c->b_ueq, &c->b_dchk, &c->b_deq, &c->o_work, &c->o_uc, &c->o_dc, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_slot, &c->o_surf, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);
@@ -517,6 +561,21 @@ int set_targets(sph_ctx *c, const float *emag_dev, const uint8_t *mask_dev) {
     c->emag = emag_dev;
     c->mask = mask_dev;
     c->trg_set = true;
+    return SPH_OK;
+}
+
+int sph_set_far_field(sph_ctx *c, int method, int order) {
+    if (!c) return SPH_EINVAL;
+    if (method == SPH_FAR_CHEBYSHEV) {
+        if (order < 2 || order > 8) return fail(c, SPH_EINVAL, "Chebyshev order must be in [2, 8]");
+        c->far_method = FAR_CHEB;
+    } else if (method == SPH_FAR_SURFACE) {
+        if (order < 3 || order > 10) return fail(c, SPH_EINVAL, "surface points per edge must be in [3, 10]");
+        c->far_method = FAR_SURFACE;
+    } else {
+        return fail(c, SPH_EINVAL, "unknown far-field method %d", method);
+    }
+    c->far_order = order;
     return SPH_OK;
 }
 

@@ -4,8 +4,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#define SPH_P 152        // points on an equivalent / check surface (6 per cube edge)
-#define SPH_PP 160       // padded row length of a surface vector (multiple of 16)
+#ifndef SPH_NP
+#define SPH_NP 6         // surface lattice points per cube edge
+#endif
+// points on an equivalent / check surface: NP^3 - (NP-2)^3 (152 for NP = 6)
+#define SPH_P (SPH_NP * SPH_NP * SPH_NP - (SPH_NP - 2) * (SPH_NP - 2) * (SPH_NP - 2))
+// padded row length of a surface vector (multiple of 16)
+#define SPH_PP ((SPH_P + 15) / 16 * 16)
 #define SPH_NOFF 343     // 7^3 relative offsets of same-level boxes (316 used by M2L)
 
 // ---------------------------------------------------------------- Morton codes
@@ -102,20 +107,21 @@ __device__ __forceinline__ float g_of_cells(int d2, const KParams &k) {
     return g_of_r2(r2, k);
 }
 
-// Unit surface point m (0..151) of the 6x6x6 lattice on [-1,1]^3 that lies on
-// the cube's surface; lattice coordinate values -1, -0.6, -0.2, 0.2, 0.6, 1.
+// Unit surface point m (0..P-1) of the NP x NP x NP lattice on [-1,1]^3 that
+// lies on the cube's surface; lattice coordinates -1 + 2a/(NP-1).
 // Order: lexicographic in (a, b, c) = lattice indices along (x, y, z), skipping interior points.
 __host__ __device__ __forceinline__ void surf_unit(int m, float &x, float &y, float &z) {
+    const int n = SPH_NP;
     int cnt = 0;
-    for (int a = 0; a < 6; ++a)
-        for (int b = 0; b < 6; ++b)
-            for (int c = 0; c < 6; ++c) {
-                bool surf = (a == 0 || a == 5 || b == 0 || b == 5 || c == 0 || c == 5);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            for (int c = 0; c < n; ++c) {
+                bool surf = (a == 0 || a == n - 1 || b == 0 || b == n - 1 || c == 0 || c == n - 1);
                 if (!surf) continue;
                 if (cnt == m) {
-                    x = -1.0f + 0.4f * a;
-                    y = -1.0f + 0.4f * b;
-                    z = -1.0f + 0.4f * c;
+                    x = -1.0f + 2.0f * a / (n - 1);
+                    y = -1.0f + 2.0f * b / (n - 1);
+                    z = -1.0f + 2.0f * c / (n - 1);
                     return;
                 }
                 ++cnt;
@@ -123,4 +129,7 @@ __host__ __device__ __forceinline__ void surf_unit(int m, float &x, float &y, fl
     x = y = z = 0.0f;
 }
 
-#define SPH_CUDA_CHECK_LAUNCH() (cudaGetLastError())
+// FP64 kernel G(R) (operator precompute and the rare FP64 evaluation paths).
+__device__ __forceinline__ double g64(double R, double alpha, double beta, double C) {
+    return C * exp(-alpha * R) * (-expm1(-(beta - alpha) * R)) / (R * R * R);
+}

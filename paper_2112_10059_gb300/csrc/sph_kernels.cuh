@@ -75,29 +75,64 @@ void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, in
                        cudaStream_t st);
 
 // ---------------------------------------------------------------- operators
-// Surface radii in units of the box half-width.
-constexpr double R_UE = 1.05, R_UC = 2.95, R_DC = 1.05, R_DE = 2.95;
+// Far-field representation of a box (Section 2.4: artificial source points
+// with artificial intensities reproduce the far interactions, Eq. s2l):
+//   FAR_CHEB    : the artificial points are the p^3 tensor Chebyshev nodes of
+//                 the box; intensities by Chebyshev anterpolation (default);
+//   FAR_SURFACE : equivalent / check surfaces of Figure fmulloc (NP points
+//                 per cube edge), intensities by the least-squares solve of
+//                 Eq. s2l (FP64 truncated SVD).
+enum FarMethod { FAR_CHEB = 0, FAR_SURFACE = 1 };
+constexpr int MAXPAD = 512;          // largest padded state length (p <= 8, NP <= 10)
+constexpr int NSLOT = 316;           // M2L offsets o in [-3,3]^3 \ [-1,1]^3
+constexpr int ETAB_MAX_EDGE = 16;    // surface L2P tables for leaf boxes of edge <= 16 cells
 
+// Surface radii in units of the box half-width: upward equivalent / check,
+// downward check / equivalent.
+struct Radii {
+    double ue, uc, dc, de;
+};
+constexpr Radii RADII_DEFAULT = {1.05, 2.95, 1.05, 2.95};
+
+__host__ __device__ __forceinline__ int far_n(int method, int order) {
+    return method == FAR_CHEB ? order * order * order
+                              : order * order * order - (order - 2) * (order - 2) * (order - 2);
+}
+__host__ __device__ __forceinline__ int pad16(int n) { return (n + 15) / 16 * 16; }
+
+// State vectors (length n, rows padded to npad) per box:
+//   FAR_CHEB:    u_B = anterpolated source weights at B's nodes,
+//                d_B = far-field potential at B's nodes (interpolated to targets);
+//   FAR_SURFACE: u_B = upward check potential, d_B = downward check potential
+//                (every pseudo-inverse folded into the operators in FP64).
+// Matrices are stored FP32 transposed ([col][row], npad x npad) so a CTA with
+// one thread per output row reads them coalesced.
 struct OpsDev {
-    // per level l (index l), FP32, transposed ([col][row]) so that threads over rows coalesce
-    float *uc2e_t;    // [L][PP][PP]
-    float *dc2e_t;    // [L][PP][PP]
-    float *m2m_t;     // [L][8][PP][PP]  child (level l+1) ueq -> parent (level l) ueq
-    float *l2l_t;     // [L][8][PP][PP]  parent (level l-1) deq -> child (level l) deq
-    float *m2l_t;     // [L][316][PP][PP] source ueq -> target dcheck, [slot][j][i]
-    uint16_t *m2l_bf; // [L][316][2][PP][PP] BF16 hi / lo, [slot][part][i][k] (row i = check point, K-major)
-    short *slot_of_code;   // [343] -> 0..315 or -1
-    float *surf;      // [152][4] unit surface points (x, y, z, 0)
+    int method, order, n, npad;
+    float *m2m_t;     // [L][8][npad][npad]  u_child(l+1, c) -> u_parent(l)
+    float *l2l_t;     // [L][8][npad][npad]  d_parent(l-1) -> d_child(l, c)
+    float *m2l_t;     // [L][316][npad][npad] u_A -> d_B (A at offset o from B)
+    uint16_t *m2l_bf; // [L][316][2][npad][npad] BF16 hi / lo of m2l, [slot][part][i][k] (K-major rows)
+    float *e_tab;     // FAR_SURFACE L2P tables, per level [edge^3][npad] row-major
+    long long e_off[16];          // float offset of level l's table in e_tab, -1 if none
+    const double *uc64, *dc64;    // FAR_SURFACE FP64 UC2E_l / DC2E_l (row-major n x n), + l * pinv_stride
+    long long pinv_stride;
+    short *slot_of_code;  // [343] -> 0..315 or -1
+    float *nodes;     // [npad][4] unit node positions: Chebyshev nodes in [-1,1]^3 or unit surface points
+    float *cheb_t;    // [order] 1D Chebyshev nodes cos((2k+1) pi / (2p))
     double *self_int; // [1]
+    Radii r;
 };
 struct OpsBuildArgs {
     int D, Lmax;
     double h, alpha, beta, eps;
-    double *work;      // FP64 scratch
+    double *work;      // FP64 scratch; keeps UC2E_l / DC2E_l after the build (FAR_SURFACE)
     OpsDev ops;
 };
 int ops_build(const OpsBuildArgs &A, cudaStream_t st);
-size_t ops_work_doubles(int Lmax);
+size_t ops_work_doubles(int method, int n, int Lmax);
+size_t ops_etab_floats(int method, int npad, int D, int Lmax);
+void ops_layout(int D, int Lmax, double *work, OpsDev &O);   // e_off, uc64, dc64, pinv_stride
 
 // ---------------------------------------------------------------- FMM passes
 struct FmmDev {
@@ -108,8 +143,9 @@ struct FmmDev {
     const float *src_q;
     float wscale;
     KParams kp;
+    double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
     int D, nx, ny, self_mode;
-    float *ueq, *dchk, *deq;   // [nboxes][PP]
+    float *ueq, *dchk;   // [nboxes][PP]: upward / downward check potentials u_B, d_B
 };
 void fmm_upward_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
