@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid edge (cells)")
     ap.add_argument("--p", type=float, default=760.0, help="pressure (Torr)")
-    ap.add_argument("--m2l", default="f32", choices=["f32", "bf16x3"])
+    ap.add_argument("--m2l", default="bf16x3", choices=["f32", "bf16x3"])
     ap.add_argument("--order", type=int, default=5, help="Chebyshev order of the far field")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
@@ -125,18 +125,60 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def leaf_evals(tree, nt_total, nnode):
-    """Work of the leaf kernel: L2P interpolation MACs, M2P and P2P kernel evaluations."""
+def measured_peaks():
+    """Measured peaks of this GPU pool (HBM copy GB/s, dense BF16 TFLOP/s), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks):
+    """Achieved vs peak per phase kernel.  Work is ALGORITHMIC (what the method needs), not executed:
+      m2l  (tensor): 2 n^2 flops per V pair, n = order^3 (the BF16 x3 split executes 3 x 128^2 x 2);
+      l2l  (tensor): 2 n^2 flops per child box with targets below level 2;
+      l2p  (FP32 FMA): 2 n flops per target in a leaf with an interpolation table;
+      near (MUFU):  P2P pairs + M2P evaluations (3 MUFU each: rsqrt + 2 x ex2);
+      select (HBM): 8 B per cell read (q and |E|) + 12 B per selected point written."""
+    n = args.order ** 3
+    mean = lambda k: statistics.mean(x[k] for x in step_stats)
     lev = tree["level"]
-    nt = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
-    ns = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
-    leaf = tree["leaf"]
-    l2p = int(np.sum(nt[leaf & (lev >= 2)]) * nnode)
-    W = tree["W"]
-    m2p = int(np.sum(nt[W[:, 0]]) * nnode) if len(W) else 0
-    U = tree["U"]
-    p2p = int(np.sum(nt[U[:, 0]] * ns[U[:, 1]])) if len(U) else 0
-    return l2p, m2p, p2p
+    ntb = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
+    nsb = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
+    n_child = int(np.sum((lev >= 3) & (ntb > 0)))
+    nV = len(tree["V"])
+    U, W = tree["U"], tree["W"]
+    p2p = int(np.sum(ntb[U[:, 0]] * nsb[U[:, 1]])) if len(U) else 0
+    m2p = int(np.sum(ntb[W[:, 0]]) * n) if len(W) else 0
+    fp32_peak = NSM * 128 * 2 * f_mhz * 1e6 / 1e12          # TFLOP/s: 128 FP32 lanes x FMA
+    mufu_peak = NSM * MUFU_PER_SM_CLK * f_mhz * 1e6 / MUFU_PER_EVAL
+    tc = args.m2l == "bf16x3"
+    tpk = peaks["bf16_tflops"]
+    out = {}
+
+    def add(name, kernel, bound, work, unit_work, ms, peak, unit, basis):
+        ach = work / (ms * 1e-3) if ms > 0 else 0.0
+        scale = 1e12 if unit == "TFLOP/s" else (1e9 if unit == "GB/s" else 1.0)
+        out[name] = {"kernel": kernel, "bound": bound, "achieved": ach / scale, "peak": peak, "unit": unit,
+                     "frac": (ach / scale) / peak if peak else None, "traffic": None, "ms_per_launch": ms,
+                     "work_per_launch": work, "work_unit": unit_work, "peak_basis": basis}
+
+    add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
+        mean("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
+        ("measured dense BF16 %.1f TFLOP/s (%s)" % (tpk, peaks["source"])) if tc else "FP32 FMA 152 SMs")
+    add("l2l", "k_l2l_tc" if tc else "k_l2l_gemm", "tensor" if tc else "alu", 2.0 * n * n * n_child, "flop",
+        mean("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
+    add("l2p", "k_l2p_gemm", "alu", 2.0 * n * nt, "flop", mean("ms_l2p"), fp32_peak, "TFLOP/s",
+        "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % f_mhz)
+    add("near", "k_leaf", "alu", float(p2p + m2p), "kernel-evals", mean("ms_near"), mufu_peak, "evals/s",
+        "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz)
+    add("select", "k_select_brick", "hbm", 8.0 * ncell + 12.0 * (ns + nt), "bytes", mean("ms_select"),
+        peaks["hbm_gbs"], "GB/s", "measured HBM copy %.0f GB/s (%s)" % (peaks["hbm_gbs"], peaks["source"]))
+    return out
 
 
 def oracle_sample(p, J, T, seconds, seed=5):
@@ -225,7 +267,7 @@ def main():
     nt = int(st0.n_targets)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    leaf_ms, step_stats = [], []
+    step_stats = []
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -235,7 +277,6 @@ def main():
             ev[k][0].record(stream)
             _, st = sph.eval_sph(ctx, out, stats=True)
             ev[k][1].record(stream)
-            leaf_ms.append(st.ms_near)
             step_stats.append(st.as_dict())
         torch.cuda.synchronize()
     if dist is not None:
@@ -263,15 +304,13 @@ def main():
     sph.set_sources(ctx, q, p.source_scale)
     sph.set_targets(ctx, emag=em)
 
-    # roofline of the dominant kernel (the leaf kernel: L2P + M2P + P2P kernel evaluations)
+    # rooflines of the kernels, from the library's CUDA-event phase timers (averages over the timed steps)
     tree = sph.get_tree(ctx)
-    l2p, m2p, p2p = leaf_evals(tree, nt, args.order ** 3)
-    evals = m2p + p2p
-    leaf_avg = sum(leaf_ms) / len(leaf_ms)
     clocks = clk.summary()
     f_mhz = clocks["sm_mhz"] or 1920.0
-    peak_evals = NSM * MUFU_PER_SM_CLK * f_mhz * 1e6 / MUFU_PER_EVAL
-    achieved = evals / (leaf_avg * 1e-3)
+    peaks = measured_peaks()
+    roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, f_mhz, peaks)
+    dominant = max(roof, key=lambda k: roof[k]["ms_per_launch"])
 
     # FP32 direct sum on the same GPU over the same selected sets
     direct = None
@@ -313,14 +352,12 @@ def main():
                 "data": "synthetic", "config": workload_cfg(p, args),
                 "e2e": {"value": nt * world / e2e_s, "unit": "targets/s",
                         "h2d_bytes_per_step": int(qh.nbytes + eh.nbytes), "d2h_bytes_per_step": int(sh.nbytes)},
-                "roofline": {"bound": "alu", "kernel": "k_leaf", "achieved": achieved, "peak": peak_evals,
-                             "unit": "kernel-evals/s", "frac": achieved / peak_evals, "traffic": None,
-                             "peak_basis": "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz,
-                             "evals_per_launch": evals, "l2p": l2p, "m2p": m2p, "p2p": p2p,
-                             "ms_per_launch": leaf_avg},
+                "roofline": dict(roof[dominant], phase=dominant),
+                "rooflines": roof,
                 "clocks": clocks, "gpu_launches": int(sum(x["n_launches"] for x in step_stats)),
-                "phases_ms": {k: last[k] for k in ("ms_select", "ms_tree", "ms_upward", "ms_m2l", "ms_near",
-                                                   "ms_total")},
+                "phases_ms": {k: statistics.mean(x[k] for x in step_stats)
+                              for k in ("ms_select", "ms_tree", "ms_upward", "ms_vpairs", "ms_m2l", "ms_l2l",
+                                        "ms_l2p", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
                 "direct_fp32": direct, "accuracy": acc, "cpu_baseline": cpu}

@@ -83,7 +83,11 @@ typedef struct sph_stats {
     int64_t n_boxes;
     int64_t n_leaves;
     int64_t n_u, n_v, n_w, n_x;/* interaction-list pairs */
-    float ms_select, ms_tree, ms_upward, ms_m2l, ms_downward, ms_near, ms_total; /* GPU ms (0 unless timing on) */
+    /* GPU milliseconds per phase, from CUDA events on the context's stream (filled when
+     * stats is non-NULL): selection; tree + lists; upward pass (P2M, M2M); grouping of the
+     * V pairs by offset; M2L; L2L (+ P2L); table L2P; leaf kernel (near field, M2P and
+     * the remaining L2P); whole eval. */
+    float ms_select, ms_tree, ms_upward, ms_vpairs, ms_m2l, ms_l2l, ms_l2p, ms_near, ms_total;
     int64_t n_launches;        /* kernels launched by this eval (operator precompute excluded) */
     int32_t far_method, far_order;
 } sph_stats;

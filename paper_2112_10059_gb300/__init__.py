@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("max_level", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("n_w", ctypes.c_int64),
                 ("n_x", ctypes.c_int64), ("ms_select", ctypes.c_float), ("ms_tree", ctypes.c_float),
-                ("ms_upward", ctypes.c_float), ("ms_m2l", ctypes.c_float), ("ms_downward", ctypes.c_float),
+                ("ms_upward", ctypes.c_float), ("ms_vpairs", ctypes.c_float), ("ms_m2l", ctypes.c_float),
+                ("ms_l2l", ctypes.c_float), ("ms_l2p", ctypes.c_float),
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
                 ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32)]
 

@@ -304,6 +304,9 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
     const int p = F.O.order;
     const int level = T.b_level[b];
     const int size = 1 << (F.D - level);
+    // a table L2P (k_l2p_gemm) already wrote S for this leaf: add the near field only
+    const bool l2p_done = F.leaf_l2p_done && cheb && level >= 2 && F.O.e_off[level] >= 0;
+    if (l2p_done && F.L.u_off[b] == F.L.u_off[b + 1] && F.L.w_off[b] == F.L.w_off[b + 1]) return;
     const float hh = 0.5f * F.kp.h;
     int bx, by, bz;
     box_coords(T, b, bx, by, bz);
@@ -313,9 +316,22 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
     __shared__ uint32_t spc[LS];
     __shared__ float sw[LS];
     __shared__ float tcheb[8];
+    __shared__ float ctab[16][8];                  // Chebyshev basis at the cell positions of one axis
     for (int j = threadIdx.x; j < np; j += LT)
         sv[j] = make_float4(F.O.nodes[4 * j], F.O.nodes[4 * j + 1], F.O.nodes[4 * j + 2], 0.f);
     if (cheb && threadIdx.x < p) tcheb[threadIdx.x] = F.O.cheb_t[threadIdx.x];
+    if (cheb && level >= 2 && size <= 16) {
+        __syncthreads();
+        // unit coordinate of cell l along an axis: (2 l + 1 - size) / size
+        for (int e = threadIdx.x; e < size * p; e += LT) {
+            int l = e / p, a = e % p;
+            float x = (float)(2 * l + 1 - size) / (float)size;
+            float v = 1.f;
+            for (int j = 0; j < p; ++j)
+                if (j != a) v *= (x - tcheb[j]) / (tcheb[a] - tcheb[j]);
+            ctab[l][a] = v;
+        }
+    }
 
     for (int t0 = tb; t0 < te; t0 += LT) {
         int t = t0 + threadIdx.x;
@@ -326,7 +342,7 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
         rel_cell(ti, tj, tk, bx, by, bz, size, hh, tx, ty, tz);
         float acc = 0.f;
         // ---- L2P (levels >= 2)
-        if (level >= 2) {
+        if (level >= 2 && !l2p_done) {
             const float w = F.kp.h * size * 0.5f;
             __syncthreads();
             if (cheb) {
@@ -334,10 +350,19 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
                 __syncthreads();
                 if (act) {
                     float Sx[8], Sy[8], Sz[8];
-                    const float iw = 1.0f / w;
-                    cheb_basis(p, tcheb, tx * iw, Sx);
-                    cheb_basis(p, tcheb, ty * iw, Sy);
-                    cheb_basis(p, tcheb, tz * iw, Sz);
+                    if (size <= 16) {   // cell centres sit at size fixed positions per axis: table
+                        const int lx = ti - bx * size, ly = tj - by * size, lz = tk - bz * size;
+                        for (int a = 0; a < p; ++a) {
+                            Sx[a] = ctab[lx][a];
+                            Sy[a] = ctab[ly][a];
+                            Sz[a] = ctab[lz][a];
+                        }
+                    } else {
+                        const float iw = 1.0f / w;
+                        cheb_basis(p, tcheb, tx * iw, Sx);
+                        cheb_basis(p, tcheb, ty * iw, Sy);
+                        cheb_basis(p, tcheb, tz * iw, Sz);
+                    }
                     for (int c = 0; c < p; ++c) {
                         float zc = 0.f;
                         for (int bb = 0; bb < p; ++bb) {
@@ -418,7 +443,10 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
                 }
             }
         }
-        if (act) out[(int64_t)ti + (int64_t)F.nx * ((int64_t)tj + (int64_t)F.ny * tk)] = acc;
+        if (act) {
+            float *o = out + (int64_t)ti + (int64_t)F.nx * ((int64_t)tj + (int64_t)F.ny * tk);
+            *o = l2p_done ? *o + acc : acc;
+        }
     }
 }
 

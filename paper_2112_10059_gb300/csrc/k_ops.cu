@@ -109,6 +109,21 @@ __global__ void k_cheb_m2m_l2l(int order, int n, int npad, float *__restrict__ m
     l2l_t[base + (size_t)pn * npad + ch] = (float)v;
 }
 
+// Chebyshev L2P table of a box of edge e cells: out[k * rows + m] = S_k(cell m), m the
+// local Morton index of the cell, unit coordinate (2 l + 1 - e) / e per axis.
+__global__ void k_cheb_etab(int order, int e, int n, float *__restrict__ out) {
+    int rows = e * e * e;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * n) return;
+    int m = idx / n, k = idx % n;
+    uint32_t lx, ly, lz;
+    demorton3((uint32_t)m, lx, ly, lz);
+    int a = k % order, b = (k / order) % order, c = k / (order * order);
+    double v = lagrange64(order, a, (2.0 * lx + 1 - e) / e) * lagrange64(order, b, (2.0 * ly + 1 - e) / e) *
+               lagrange64(order, c, (2.0 * lz + 1 - e) / e);
+    out[(size_t)k * rows + m] = (float)v;
+}
+
 // Kernel matrix K[i][j] = G(|t_i - s_j|), t_i = ct + rt * u_i, s_j = cs + rs * u_j (cm).
 struct MatSpec {
     double ct[3], rt, cs[3], rs;
@@ -269,20 +284,6 @@ __global__ void k_kmat_cells64(int e, int n, double hh, double rs, const float *
     out[idx] = g64(sqrt(dx * dx + dy * dy + dz * dz), alpha, beta, C);
 }
 
-// M2L of one level, FP32 [slot][j][i] -> BF16 hi/lo [slot][part][i][k].
-__global__ void k_m2l_split_bf16(const float *__restrict__ m2l_t, uint16_t *__restrict__ bf, int npad) {
-    int slot = blockIdx.y;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= npad * npad) return;
-    int i = e / npad, k = e % npad;
-    float g = m2l_t[(size_t)slot * npad * npad + (size_t)k * npad + i];
-    __nv_bfloat16 hi = __float2bfloat16_rn(g);
-    __nv_bfloat16 lo = __float2bfloat16_rn(g - __bfloat162float(hi));
-    size_t base = (size_t)slot * 2 * npad * npad;
-    bf[base + (size_t)i * npad + k] = __bfloat16_as_ushort(hi);
-    bf[base + (size_t)npad * npad + (size_t)i * npad + k] = __bfloat16_as_ushort(lo);
-}
-
 // Ball integral of G (self term): int_0^a (e^{-alpha r} - e^{-beta r}) / (L r) dr by composite
 // Simpson on the smooth integrand (its value at r = 0 is (beta - alpha)/L), 2^14 panels.
 __global__ void k_self_int(double a, double alpha, double beta, double *out) {
@@ -324,7 +325,6 @@ static int edge_of(int D, int l) { return 1 << (D - l); }
 
 size_t ops_etab_floats(int method, int npad, int D, int Lmax) {
     size_t s = npad;
-    if (method != FAR_SURFACE) return s;
     for (int l = 2; l <= Lmax; ++l) {
         int e = edge_of(D, l);
         if (e <= ETAB_MAX_EDGE) s += (size_t)e * e * e * npad;
@@ -336,7 +336,6 @@ void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
     for (int l = 0; l < 16; ++l) O.e_off[l] = -1;
     O.uc64 = O.dc64 = nullptr;
     O.pinv_stride = 0;
-    if (O.method != FAR_SURFACE) return;
     long long off = 0;
     for (int l = 2; l <= Lmax && l < 16; ++l) {
         int e = edge_of(D, l);
@@ -345,6 +344,7 @@ void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
             off += (long long)e * e * e * O.npad;
         }
     }
+    if (O.method != FAR_SURFACE) return;
     const size_t nn = (size_t)O.n * O.n;
     O.pinv_stride = (long long)(BLK * nn);
     O.uc64 = work + 2 * nn;
@@ -389,6 +389,13 @@ static int build_cheb(const OpsBuildArgs &A, cudaStream_t st, double C) {
             m.out_t = O.m2l_t + ((size_t)l * NSLOT + slot) * pp;
             ms.push_back(m);
         }
+    }
+    // L2P interpolation tables (rows beyond n of the padded K dimension stay zero)
+    cudaMemsetAsync(O.e_tab, 0, sizeof(float) * ops_etab_floats(O.method, np, A.D, A.Lmax), st);
+    for (int l = 2; l <= A.Lmax; ++l) {
+        if (O.e_off[l] < 0) continue;
+        int e = 1 << (A.D - l);
+        k_cheb_etab<<<(e * e * e * n + 255) / 256, 256, 0, st>>>(O.order, e, n, O.e_tab + O.e_off[l]);
     }
     if (!ms.empty()) {
         MatSpec *dms = (MatSpec *)A.work;
@@ -510,7 +517,8 @@ static int build_surface(const OpsBuildArgs &A, cudaStream_t st, double C) {
         k_kmat<<<dim3((n * n + 255) / 256, NSLOT), 256, 0, st>>>(dm2l + k, O.nodes, n, np, A.alpha, A.beta, C);
         k_gemm64<<<dim3((n + 15) / 16, (n + 15) / 16, NSLOT), 256, 0, st>>>(dgm + k, n, np);
     }
-    // L2P tables
+    // L2P tables (padding columns must read as zero)
+    cudaMemsetAsync(O.e_tab, 0, sizeof(float) * ops_etab_floats(O.method, np, A.D, A.Lmax), st);
     GemmSpec *dge = dgm + gm.size() + 2;
     int ne = 0;
     for (int l = L0; l <= L1; ++l) {
@@ -536,11 +544,10 @@ int ops_build(const OpsBuildArgs &A, cudaStream_t st) {
     if (A.Lmax >= 2) {
         if (O.method == FAR_CHEB) build_cheb(A, st, C);
         else build_surface(A, st, C);
-        if (O.m2l_bf)
-            for (int l = 2; l <= A.Lmax; ++l)
-                k_m2l_split_bf16<<<dim3((O.npad * O.npad + 255) / 256, NSLOT), 256, 0, st>>>(
-                    O.m2l_t + (size_t)l * NSLOT * O.npad * O.npad,
-                    O.m2l_bf + (size_t)l * NSLOT * 2 * O.npad * O.npad, O.npad);
+        if (O.m2l_img && tc_supported(O)) {
+            make_images(O.m2l_t, O.npad, (A.Lmax + 1) * NSLOT, O.m2l_img, st);
+            make_images(O.l2l_t, O.npad, (A.Lmax + 1) * 8, O.l2l_img, st);
+        }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

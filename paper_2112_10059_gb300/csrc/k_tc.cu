@@ -1,0 +1,279 @@
+// Far-field translations on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// M2L (paper Section 2.4, far interactions through the hierarchy) and L2L are
+// dense contractions of 128 x 128 operators with gathered state vectors:
+//     D[i][j] = sum_k Op[i][k] X[k][j],   X[:, j] = state row of box j.
+// Split-precision BF16: Op = Op_hi + Op_lo, X = X_hi + X_lo (each BF16), and
+//     D ~ Op_hi X_hi + Op_hi X_lo + Op_lo X_hi
+// accumulated in FP32 in tensor memory (TMEM); the dropped Op_lo X_lo term is
+// ~2^-16 relative, so the product keeps about 16 significant bits.
+//
+// One CTA (128 threads, one warpgroup) per tile of 64 columns:
+//   * thread 0 loads the operator's two 32 KiB BF16 images (pre-swizzled in
+//     global memory, see k_make_image) with bulk async copies on an mbarrier;
+//   * all threads gather the 64 FP32 state rows, split them into BF16 hi / lo
+//     and store them K-major with the 128-byte swizzle;
+//   * thread 0 issues 3 x 8 tcgen05.mma (M = 128, N = 64, K = 16 each) into a
+//     64-column TMEM accumulator and commits to a second mbarrier;
+//   * warp w reads TMEM lanes 32w..32w+31 (rows i) and adds the result into the
+//     destination boxes' downward state (atomically for M2L, whose targets
+//     receive many tiles; plainly for L2L, whose children are unique).
+// Every wait is bounded; on expiry the tile records an error code and still
+// releases its TMEM.
+#include "sph_kernels.cuh"
+#include "tc_sm103.cuh"
+
+namespace sph {
+
+constexpr int TCM = 128, TCN = 64, TCK = 128;
+constexpr uint32_t A_BYTES = TCM * TCK * 2;        // one BF16 operator image (32 KiB)
+constexpr uint32_t B_BYTES = TCN * TCK * 2;        // one BF16 gathered tile (16 KiB)
+constexpr uint32_t TC_TAIL = 32 + 2 * TCN * 4;                     // 2 mbarriers, TMEM address, column indices
+// dynamic shared memory: up to 1008 bytes of padding to the 1024-byte aligned base, the
+// four operand tiles, then the tail
+constexpr uint32_t TC_SMEM = 1024 + 2 * A_BYTES + 2 * B_BYTES + TC_TAIL;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+// Operator (FP32, transposed [k][i], stride np) -> BF16 hi / lo images, K-major SW128.
+__global__ void k_make_image(const float *__restrict__ opT, int np, uint16_t *__restrict__ img) {
+    const float *src = opT + (size_t)blockIdx.y * np * np;
+    uint16_t *hi = img + (size_t)blockIdx.y * 2 * (A_BYTES / 2);
+    uint16_t *lo = hi + A_BYTES / 2;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= TCM * TCK) return;
+    int i = e / TCK, k = e % TCK;
+    float v = (i < np && k < np) ? src[(size_t)k * np + i] : 0.f;
+    uint16_t h, l;
+    tc::split_bf16(v, h, l);
+    uint32_t off = tc::sw128_offset(i, k, TCM) / 2;
+    hi[off] = h;
+    lo[off] = l;
+}
+
+void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st) {
+    if (count <= 0) return;
+    k_make_image<<<dim3((TCM * TCK + 255) / 256, count), 256, 0, st>>>(opT, np, img);
+}
+
+struct TcSmem {
+    uint8_t *a_hi, *a_lo, *b_hi, *b_lo;
+    uint64_t *bar_a, *bar_mma;
+    uint32_t *tmem_base;
+    int *col_src, *col_dst;
+};
+
+__device__ __forceinline__ TcSmem carve(uint8_t *raw) {
+    uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+    p = (p + 1023) & ~(uintptr_t)1023;
+    uint8_t *b = reinterpret_cast<uint8_t *>(p);
+    TcSmem s;
+    s.a_hi = b;
+    s.a_lo = b + A_BYTES;
+    s.b_hi = b + 2 * A_BYTES;
+    s.b_lo = b + 2 * A_BYTES + B_BYTES;
+    uint8_t *tail = b + 2 * A_BYTES + 2 * B_BYTES;
+    s.bar_a = reinterpret_cast<uint64_t *>(tail);
+    s.bar_mma = reinterpret_cast<uint64_t *>(tail + 8);
+    s.tmem_base = reinterpret_cast<uint32_t *>(tail + 16);
+    s.col_src = reinterpret_cast<int *>(tail + 32);
+    s.col_dst = s.col_src + TCN;      // ends at tail + TC_TAIL <= raw + TC_SMEM
+    return s;
+}
+
+// Gather the FP32 state rows col_src[j] (row stride np) into the BF16 hi / lo B tiles.
+__device__ __forceinline__ void gather_split(const TcSmem &s, const float *__restrict__ state, int np) {
+    for (int e = threadIdx.x; e < TCN * (TCK / 4); e += blockDim.x) {
+        int j = e / (TCK / 4), q = e % (TCK / 4);
+        int src = s.col_src[j];
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src >= 0 && 4 * q < np) v = *reinterpret_cast<const float4 *>(state + (size_t)src * np + 4 * q);
+        uint16_t h0, l0, h1, l1, h2, l2, h3, l3;
+        tc::split_bf16(v.x, h0, l0);
+        tc::split_bf16(v.y, h1, l1);
+        tc::split_bf16(v.z, h2, l2);
+        tc::split_bf16(v.w, h3, l3);
+        uint32_t off = tc::sw128_offset(j, 4 * q, TCN);
+        uint2 hv = make_uint2((uint32_t)h0 | ((uint32_t)h1 << 16), (uint32_t)h2 | ((uint32_t)h3 << 16));
+        uint2 lv = make_uint2((uint32_t)l0 | ((uint32_t)l1 << 16), (uint32_t)l2 | ((uint32_t)l3 << 16));
+        *reinterpret_cast<uint2 *>(s.b_hi + off) = hv;
+        *reinterpret_cast<uint2 *>(s.b_lo + off) = lv;
+    }
+}
+
+// Issue the 3 x 8 MMAs of one tile (thread 0 only).
+__device__ __forceinline__ void issue_mmas(const TcSmem &s, uint32_t tmem) {
+    const uint32_t idesc = tc::idesc_bf16_f32(TCM, TCN);
+    const uint32_t a_hi = tc::smem_u32(s.a_hi), a_lo = tc::smem_u32(s.a_lo);
+    const uint32_t b_hi = tc::smem_u32(s.b_hi), b_lo = tc::smem_u32(s.b_lo);
+#pragma unroll
+    for (int ks = 0; ks < TCK / 16; ++ks) {
+        uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+        uint32_t bo = tc::sw128_offset(0, 16 * ks, TCN);
+        tc::mma_bf16(tmem, tc::sdesc_sw128(a_hi + ao), tc::sdesc_sw128(b_hi + bo), idesc, ks > 0);
+        tc::mma_bf16(tmem, tc::sdesc_sw128(a_hi + ao), tc::sdesc_sw128(b_lo + bo), idesc, 1);
+        tc::mma_bf16(tmem, tc::sdesc_sw128(a_lo + ao), tc::sdesc_sw128(b_hi + bo), idesc, 1);
+    }
+    tc::mma_commit(tc::smem_u32(s.bar_mma));
+}
+
+// The common body: operator image `img` (hi followed by lo), columns already in smem.
+// Adds D into out[col_dst[j] * np + i] (atomically if `atomic`).  Returns false on a timeout.
+__device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__restrict__ img,
+                                          const float *__restrict__ state, float *__restrict__ out, int np,
+                                          int n, bool atomic, int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        tc::mbar_expect_tx(tc::smem_u32(s.bar_a), 2 * A_BYTES);
+        tc::bulk_g2s(tc::smem_u32(s.a_hi), img, A_BYTES, tc::smem_u32(s.bar_a));
+        tc::bulk_g2s(tc::smem_u32(s.a_lo), img + A_BYTES / 2, A_BYTES, tc::smem_u32(s.bar_a));
+    }
+    gather_split(s, state, np);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    const uint32_t tmem = *s.tmem_base;
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        int ok = tc::mbar_wait_bounded(tc::smem_u32(s.bar_a), 0, WAIT_LIMIT);
+        if (ok) {
+            tc::fence_after_sync();
+            issue_mmas(s, tmem);
+        } else {
+            atomicOr(err, 1);
+            tc::mbar_wait_bounded(tc::smem_u32(s.bar_a), 0, WAIT_LIMIT);   // let the copies land
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    if (!tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT)) {
+        atomicOr(err, 2);
+        tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);     // let the MMAs finish
+        return;
+    }
+    tc::fence_after_sync();
+    const int i = warp * 32 + lane;   // TMEM lane = operator row
+#pragma unroll
+    for (int c0 = 0; c0 < TCN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (i < n) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                int d = s.col_dst[c0 + j];
+                if (d < 0) continue;
+                float *o = out + (size_t)d * np + i;
+                if (atomic) atomicAdd(o, v[j]);
+                else *o += v[j];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_setup(const TcSmem &s) {
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(tc::smem_u32(s.tmem_base), TCN);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_u32(s.bar_a), 1);
+        tc::mbar_init(tc::smem_u32(s.bar_mma), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ void tile_teardown(const TcSmem &s) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(*s.tmem_base, TCN);
+}
+
+// ---------------------------------------------------------------- M2L over offset-grouped V pairs
+__global__ void __launch_bounds__(128) k_m2l_tc(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
+                                                int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    const int tile = blockIdx.x;
+    if (tile >= Pd.tile_off[Pd.nkeys]) return;
+    TcSmem s = carve(smem_raw);
+    __shared__ int s_key;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = Pd.nkeys;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (Pd.tile_off[mid] <= tile) lo = mid; else hi = mid;
+        }
+        s_key = lo;
+    }
+    tile_setup(s);
+    const int key = s_key;
+    const int p0 = Pd.off[key] + (tile - Pd.tile_off[key]) * TCN;
+    const int p1 = min(p0 + TCN, Pd.off[key + 1]);
+    if (threadIdx.x < TCN) {
+        int q = p0 + threadIdx.x;
+        s.col_src[threadIdx.x] = q < p1 ? Pd.src[q] : -1;
+        s.col_dst[threadIdx.x] = q < p1 ? Pd.trg[q] : -1;
+    }
+    __syncthreads();
+    const uint16_t *img = images + (size_t)key * (2 * A_BYTES / 2);
+    tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err);
+    tile_teardown(s);
+}
+
+// ---------------------------------------------------------------- L2L for one level
+__global__ void __launch_bounds__(128) k_l2l_tc(FmmDev F, int level, int parent_begin, int parent_count,
+                                                const uint16_t *__restrict__ images, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem s = carve(smem_raw);
+    const int t0 = blockIdx.x * TCN;
+    const int c = blockIdx.y;
+    const TreeDev &T = F.T;
+    int any = 0;
+    if (threadIdx.x < TCN) {
+        int p = parent_begin + t0 + threadIdx.x;
+        int P = -1, C = -1;
+        if (t0 + (int)threadIdx.x < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) {
+            int ch = T.box_at[dense_off(level) + ((T.b_key[p] << 3) | (uint32_t)c)];
+            if (ch >= 0 && T.b_te[ch] > T.b_tb[ch]) { P = p; C = ch; }
+        }
+        any = C >= 0;
+        s.col_src[threadIdx.x] = P;
+        s.col_dst[threadIdx.x] = C;
+    }
+    if (!__syncthreads_or(any)) return;
+    tile_setup(s);
+    const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
+    tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err);
+    tile_teardown(s);
+}
+
+bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
+
+size_t tc_image_elems(int count) { return (size_t)count * 2 * (A_BYTES / 2); }
+
+void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st) {
+    if (nV <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        attr = true;
+    }
+    int grid = (nV + TCN - 1) / TCN + Pd.nkeys;
+    k_m2l_tc<<<grid, 128, TC_SMEM, st>>>(F, Pd, images, err);
+}
+
+void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
+                      int *err, cudaStream_t st) {
+    if (parent_count <= 0 || level < 3) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        attr = true;
+    }
+    dim3 grid((parent_count + TCN - 1) / TCN, 8);
+    k_l2l_tc<<<grid, 128, TC_SMEM, st>>>(F, level, parent_begin, parent_count, images, err);
+}
+
+}  // namespace sph

@@ -313,6 +313,7 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                         if (A >= 0 && T.b_se[A] > T.b_sb[A]) {
                             if (FILL) {
                                 L.v_src[pV] = A;
+                                L.v_trg[pV] = b;
                                 L.v_oc[pV] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
                             }
                             ++pV; ++nV;

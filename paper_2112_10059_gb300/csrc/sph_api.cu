@@ -57,13 +57,16 @@ struct sph_ctx {
     int list_tot[4] = {0, 0, 0, 0};
     bool have_tree = false;
     int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
+    bool translate_per_box = false;   // one CTA per box for M2L / L2L instead of the batched GEMMs
+    bool tc_used = false;             // this eval ran the tensor-core translations
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
-    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_wsrc, b_xsrc;
+    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pairs;
     DevBuf b_ueq, b_dchk;
-    DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_slot, o_surf, o_cheb, o_self;
+    DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
+    DevBuf b_err;                // device error flags of the tensor-core tiles
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
     // operator cache key
@@ -220,6 +223,7 @@ ListDev list_dev(sph_ctx *c) {
     L.u_src = P<int>(c->b_usrc); L.v_src = P<int>(c->b_vsrc); L.w_src = P<int>(c->b_wsrc);
     L.x_src = P<int>(c->b_xsrc);
     L.v_oc = P<short>(c->b_vocs);
+    L.v_trg = P<int>(c->b_vtrg);
     return L;
 }
 
@@ -280,6 +284,7 @@ int run_tree(sph_ctx *c) {
     ENS(c->b_usrc, std::max(1, c->list_tot[0]) * sizeof(int));
     ENS(c->b_vsrc, std::max(1, c->list_tot[1]) * sizeof(int));
     ENS(c->b_vocs, std::max(1, c->list_tot[1]) * sizeof(short));
+    ENS(c->b_vtrg, std::max(1, c->list_tot[1]) * sizeof(int));
     ENS(c->b_wsrc, std::max(1, c->list_tot[2]) * sizeof(int));
     ENS(c->b_xsrc, std::max(1, c->list_tot[3]) * sizeof(int));
     L = list_dev(c);
@@ -299,7 +304,9 @@ void fill_ops(sph_ctx *c, OpsDev &O, int D, int L, bool bf) {
     O.r = c->radii;
     O.m2m_t = P<float>(c->o_m2m); O.l2l_t = P<float>(c->o_l2l);
     O.m2l_t = P<float>(c->o_m2l);
-    O.m2l_bf = bf ? P<uint16_t>(c->o_m2lbf) : nullptr;
+    const bool img = bf && O.npad == 128;
+    O.m2l_img = img ? P<uint16_t>(c->o_m2lbf) : nullptr;
+    O.l2l_img = img ? P<uint16_t>(c->o_l2lbf) : nullptr;
     O.slot_of_code = P<short>(c->o_slot);
     O.nodes = P<float>(c->o_surf);
     O.cheb_t = P<float>(c->o_cheb);
@@ -323,7 +330,10 @@ int run_ops(sph_ctx *c) {
     ENS(c->o_m2m, (L + 1) * 8 * PP2 * sizeof(float));
     ENS(c->o_l2l, (L + 1) * 8 * PP2 * sizeof(float));
     ENS(c->o_m2l, (L + 1) * 316 * PP2 * sizeof(float));
-    if (want_bf) ENS(c->o_m2lbf, (L + 1) * 316 * 2 * PP2 * sizeof(uint16_t));
+    if (want_bf && np == 128) {
+        ENS(c->o_m2lbf, tc_image_elems((L + 1) * 316) * sizeof(uint16_t));
+        ENS(c->o_l2lbf, tc_image_elems((L + 1) * 8) * sizeof(uint16_t));
+    }
     ENS(c->o_slot, 343 * sizeof(short));
     ENS(c->o_surf, (size_t)np * 4 * sizeof(float));
     ENS(c->o_cheb, 16 * sizeof(float));
@@ -355,7 +365,7 @@ OpsDev ops_dev(sph_ctx *c) {
 }
 
 struct PhaseTimer {
-    cudaEvent_t ev[8];
+    cudaEvent_t ev[16];
     bool on = false;
     int n = 0;
     void start(bool enable, cudaStream_t st) {
@@ -366,8 +376,15 @@ struct PhaseTimer {
         mark(st);
     }
     void mark(cudaStream_t st) {
-        if (on && n < 8) cudaEventRecord(ev[n++], st);
+        if (on && n < 16) cudaEventRecord(ev[n++], st);
     }
+    void mark_at(int k, cudaStream_t st) {   // record event k (events between may stay unrecorded)
+        if (on && k < 16) {
+            cudaEventRecord(ev[k], st);
+            n = k + 1;
+        }
+    }
+    bool rec[16] = {};
     float ms(int a, int b) {
         float m = 0;
         if (on && b < n) cudaEventElapsedTime(&m, ev[a], ev[b]);
@@ -383,9 +400,16 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     PhaseTimer tm;
     tm.start(stats != nullptr, c->stream);
     c->launches = 0;
+    // a timeout recorded by the previous eval's tensor-core tiles surfaces here (after its sync)
+    if (c->tc_used && c->pinned[48] != 0) {
+        c->tc_used = false;
+        return fail(c, SPH_ETIMEOUT, "a tensor-core tile of the previous eval gave up waiting (code %d)",
+                    c->pinned[48]);
+    }
+    c->tc_used = false;
     int r = run_select(c);
     if (r) return r;
-    tm.mark(c->stream);   // 1
+    tm.mark_at(1, c->stream);
     if ((int64_t)c->nx * c->ny * c->nz > 0) {
         CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
     }
@@ -401,7 +425,7 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     }
     r = run_tree(c);
     if (r) return r;
-    tm.mark(c->stream);   // 2
+    tm.mark_at(2, c->stream);
     r = run_ops(c);
     if (r) return r;
     const int nb = c->nboxes;
@@ -415,35 +439,94 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     F.O = ops_dev(c);
     F.src_pc = P<uint32_t>(c->b_spc);
     F.trg_pc = P<uint32_t>(c->b_tpc);
+    F.trg_key = P<uint32_t>(c->b_tkey);
+    F.leaf_l2p_done = 0;
     F.src_q = P<float>(c->b_sq);
     F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
     F.kp = make_kp(c);
     F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
     F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
     F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
-    tm.mark(c->stream);   // 3
+    tm.mark_at(3, c->stream);
     for (int l = c->Lmax; l >= 2; --l) {
         fmm_upward_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
         c->launches += c->lvl_count[l] > 0;
     }
-    tm.mark(c->stream);   // 4
-    for (int l = 2; l <= c->Lmax; ++l) {
-        fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
-        c->launches += c->lvl_count[l] > 0;
-        if (c->list_tot[3] > 0) {
-            fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+    tm.mark_at(4, c->stream);
+    const bool per_box = c->translate_per_box;
+    if (per_box) {
+        tm.mark_at(5, c->stream);
+        tm.mark_at(6, c->stream);
+        for (int l = 2; l <= c->Lmax; ++l) {
+            fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
             c->launches += c->lvl_count[l] > 0;
+            if (c->list_tot[3] > 0) {
+                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+                c->launches += c->lvl_count[l] > 0;
+            }
+            fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+            c->launches += l >= 3 && c->lvl_count[l] > 0;
         }
-        fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
-        c->launches += l >= 3 && c->lvl_count[l] > 0;
+    } else {
+        // every M2L (all levels) and P2L first, then L2L top-down: d_child += L2L d_parent
+        // needs the parent's d complete, which holds once the level above is done.
+        const int nV = c->list_tot[1];
+        const int nkeys = (c->Lmax + 1) * NSLOT;
+        ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1)) * sizeof(int));
+        ENS(c->b_scan, scan_tmp_ints(nkeys + 1) * sizeof(int) + 64);
+        PairsDev Pd;
+        int *pb = P<int>(c->b_pairs);
+        Pd.nkeys = nkeys;
+        Pd.cnt = pb; Pd.off = pb + nkeys; Pd.cursor = pb + 2 * nkeys + 1;
+        Pd.tile_cnt = pb + 3 * nkeys + 1; Pd.tile_off = pb + 4 * nkeys + 1;
+        Pd.total_tiles = pb + 5 * nkeys + 2;
+        Pd.trg = pb + 5 * nkeys + 8; Pd.src = Pd.trg + std::max(nV, 1);
+        vpairs_build(F, Pd, nV, P<int>(c->b_scan), c->stream);
+        c->launches += 8 + (nV > 0 ? 2 : 0);
+        tm.mark_at(5, c->stream);
+        const bool tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr;
+        ENS(c->b_err, 16 * sizeof(int));
+        int *err = P<int>(c->b_err);
+        if (tc) {
+            CK(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+            fmm_m2l_tc(F, Pd, nV, F.O.m2l_img, err, c->stream);
+        } else {
+            fmm_m2l_pairs(F, Pd, nV, c->m2l_prec, c->stream);
+        }
+        c->launches += nV > 0;
+        tm.mark_at(6, c->stream);
+        for (int l = 2; l <= c->Lmax; ++l)
+            if (c->list_tot[3] > 0) {
+                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+                c->launches += c->lvl_count[l] > 0;
+            }
+        for (int l = 3; l <= c->Lmax; ++l) {
+            if (tc) fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
+            else fmm_l2l_gemm_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], c->stream);
+            c->launches += c->lvl_count[l - 1] > 0;
+        }
+        if (tc) CK(cudaMemcpyAsync(c->pinned + 48, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        c->tc_used = tc;
     }
-    tm.mark(c->stream);   // 5
+    tm.mark_at(7, c->stream);
+    if (!per_box && F.O.method == FAR_CHEB) {
+        for (int l = 2; l <= c->Lmax; ++l) {
+            if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
+                fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                ++c->launches;
+            }
+        }
+        F.leaf_l2p_done = 1;
+    }
+    tm.mark_at(8, c->stream);
     fmm_leaf(F, nb, c->leaf_size, out, c->stream);
     c->launches += nb > 0;
-    tm.mark(c->stream);   // 6
+    tm.mark_at(9, c->stream);
     CK(cudaGetLastError());
     if (stats) {
         CK(cudaStreamSynchronize(c->stream));
+        if (c->tc_used && c->pinned[48] != 0)
+            return fail(c, SPH_ETIMEOUT, "a tensor-core tile gave up waiting (code %d)", c->pinned[48]);
         memset(stats, 0, sizeof *stats);
         stats->n_sources = c->ns;
         stats->n_targets = c->nt;
@@ -458,10 +541,12 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         stats->ms_select = tm.ms(0, 1);
         stats->ms_tree = tm.ms(1, 2);
         stats->ms_upward = tm.ms(3, 4);
-        stats->ms_m2l = tm.ms(4, 5);
-        stats->ms_downward = 0;
-        stats->ms_near = tm.ms(5, 6);
-        stats->ms_total = tm.ms(0, 6);
+        stats->ms_vpairs = tm.ms(4, 5);
+        stats->ms_m2l = tm.ms(5, 6);
+        stats->ms_l2l = tm.ms(6, 7);
+        stats->ms_l2p = tm.ms(7, 8);
+        stats->ms_near = tm.ms(8, 9);
+        stats->ms_total = tm.ms(0, 9);
         stats->n_launches = c->launches;
         stats->far_method = c->far_method;
         stats->far_order = c->far_order;
@@ -493,6 +578,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
         return SPH_ECUDA;
     }
     if (const char *e = getenv("SPH_PINV_EPS")) c->pinv_eps = atof(e);
+    if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
         if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }
@@ -512,9 +598,9 @@ void sph_destroy(sph_ctx *c) {
     DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
-                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_wsrc, &c->b_xsrc,
+                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);

@@ -68,6 +68,7 @@ struct ListDev {
     int *u_off, *v_off, *w_off, *x_off;     // [nboxes+1]
     int *u_src, *v_src, *w_src, *x_src;
     short *v_oc;                            // offset code (ox+3) + 7(oy+3) + 49(oz+3)
+    int *v_trg;                             // target box of each V entry
 };
 void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
                         int *totals, cudaStream_t st);
@@ -112,8 +113,10 @@ struct OpsDev {
     float *m2m_t;     // [L][8][npad][npad]  u_child(l+1, c) -> u_parent(l)
     float *l2l_t;     // [L][8][npad][npad]  d_parent(l-1) -> d_child(l, c)
     float *m2l_t;     // [L][316][npad][npad] u_A -> d_B (A at offset o from B)
-    uint16_t *m2l_bf; // [L][316][2][npad][npad] BF16 hi / lo of m2l, [slot][part][i][k] (K-major rows)
-    float *e_tab;     // FAR_SURFACE L2P tables, per level [edge^3][npad] row-major
+    uint16_t *m2l_img;    // [L][316] BF16 hi / lo images of M2L for the tensor cores (npad == 128)
+    uint16_t *l2l_img;    // [L][8]   BF16 hi / lo images of L2L
+    float *e_tab;     // L2P tables per level: FAR_SURFACE [edge^3][npad] row-major (cells in linear order);
+                      // FAR_CHEB [npad][edge^3] (cells in local Morton order)
     long long e_off[16];          // float offset of level l's table in e_tab, -1 if none
     const double *uc64, *dc64;    // FAR_SURFACE FP64 UC2E_l / DC2E_l (row-major n x n), + l * pinv_stride
     long long pinv_stride;
@@ -139,8 +142,9 @@ struct FmmDev {
     TreeDev T;
     ListDev L;
     OpsDev O;
-    const uint32_t *src_pc, *trg_pc;
+    const uint32_t *src_pc, *trg_pc, *trg_key;
     const float *src_q;
+    int leaf_l2p_done;   // 1: k_leaf adds near-field terms only where a table L2P already wrote S
     float wscale;
     KParams kp;
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
@@ -152,5 +156,26 @@ void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_leaf(const FmmDev &F, int nboxes, int leaf_cap, float *out_dense, cudaStream_t st);
+void fmm_m2l_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
+// V pairs grouped by (level, offset slot): built once per tree, then one M2L launch for all levels.
+struct PairsDev {
+    int nkeys;            // (Lmax + 1) * 316
+    int *cnt, *off;       // [nkeys], [nkeys + 1]
+    int *cursor;          // [nkeys]
+    int *tile_cnt, *tile_off;   // [nkeys], [nkeys + 1]
+    int *trg, *src;       // [nV]
+    int *total_tiles;     // [1]
+};
+void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cudaStream_t st);
+void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cudaStream_t st);
+// tensor-core (tcgen05, BF16 x3) translations; require npad == 128
+bool tc_supported(const OpsDev &O);
+size_t tc_image_elems(int count);
+void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st);
+void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st);
+void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
+                      int *err, cudaStream_t st);
+void fmm_l2l_gemm_level(const FmmDev &F, int level, int parent_begin, int parent_count, cudaStream_t st);
+void fmm_l2p_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st);
 
 }  // namespace sph

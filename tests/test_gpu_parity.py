@@ -189,6 +189,38 @@ def test_surface_far_field(sph, pi):
     c.close()
 
 
+def test_batched_translations_match_per_box(sph, monkeypatch):
+    """The batched gathered-GEMM M2L / L2L give the same field as one CTA per box."""
+    p = _problems()[1]
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SPH_TRANSLATE_PER_BOX", flag)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c)
+        outs.append(out.cpu().numpy().astype(np.float64))
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs[1][T], outs[0][T]) < 1e-6
+
+
+@pytest.mark.parametrize("pi", [0, 1, 2])
+def test_tensor_core_translations(sph, pi):
+    """M2L / L2L on the tensor cores (tcgen05, BF16 hi/lo split, 3 products, FP32 accumulate)
+    agree with the FP32 SIMT translations to ~1e-5 and pass the oracle gate."""
+    p = _problems()[pi]
+    ref, J, T = oracle.sph_problem(p)
+    c32 = sph.Context(0)
+    _, o32, _ = sph.solve(p, c32, m2l_precision=sph.M2L_F32)
+    ctc = sph.Context(0)
+    _, otc, st = sph.solve(p, ctc, m2l_precision=sph.M2L_BF16X3, stats=True)
+    a = o32.cpu().numpy().astype(np.float64)
+    b = otc.cpu().numpy().astype(np.float64)
+    assert oracle.rel_l2(b[T], a[T]) < 2e-5
+    _check_fmm(b, ref, T, p.name + " bf16x3")
+    c32.close()
+    ctc.close()
+
+
 def test_empty_sets(sph, ctx):
     import torch
     n = 16
@@ -210,7 +242,10 @@ def test_host_buffers_match_device(sph, ctx):
     _, out, _ = sph.solve(p, ctx)
     dev = out.cpu().numpy()
     host, _ = sph.eval_sph_host(ctx, p.q, p.emag)
-    assert np.array_equal(dev, host)
+    # M2L contributions are scatter-added with atomics, so the summation order (and the
+    # last bits) may differ between two evaluations
+    assert np.array_equal(dev == 0, host == 0)
+    assert np.max(np.abs(host - dev)) <= 1e-5 * np.max(np.abs(dev))
 
 
 def test_argument_errors(sph):
