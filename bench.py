@@ -56,7 +56,7 @@ def parse():
 
 
 def workload(args):
-    return si.config_c2(n=args.n, p_torr=args.p)
+    return si.streamer_adaptive(n=args.n, p_torr=args.p)
 
 
 def workload_cfg(p, args):

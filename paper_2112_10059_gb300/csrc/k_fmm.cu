@@ -52,9 +52,7 @@ __device__ __forceinline__ void cheb_basis(int p, const float *t, float x, float
 // ------------------------------------------------------------------ upward
 constexpr int UT = 256;   // sources per shared tile
 
-__global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, int box_begin, int box_count) {
-    int b = box_begin + blockIdx.x;
-    if (blockIdx.x >= box_count) return;
+__device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
     const TreeDev &T = F.T;
     int sb = T.b_sb[b], se = T.b_se[b];
     if (se <= sb) return;
@@ -143,9 +141,47 @@ __global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, int 
     }
 }
 
-void fmm_upward_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
+// CTAs walk the compact list of this level's boxes that hold sources.
+__global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, const int *__restrict__ list,
+                                                       const int *__restrict__ count) {
+    const int cnt = *count;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        upward_box(F, level, list[i]);
+        __syncthreads();
+    }
+}
+
+void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
+                      cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
-    k_upward<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
+    int grid = box_count < 152 * 8 ? box_count : 152 * 8;
+    k_upward<<<grid, 2 * F.O.npad, 0, st>>>(F, level, list, count);
+}
+
+// Compact work lists: per level the boxes with sources (stored in the level's box range),
+// and the leaves that the leaf kernel has to visit (any without a table L2P, or with a
+// U or W list).
+__global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
+                             int *__restrict__ leaf_list, int *__restrict__ leaf_cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nboxes) return;
+    const TreeDev &T = F.T;
+    int l = T.b_level[b];
+    if (l >= 2 && T.b_se[b] > T.b_sb[b]) {
+        int i = atomicAdd(src_cnt + l, 1);
+        src_list[T.lvl_base[l] + i] = b;
+    }
+    if (T.b_leaf[b] && T.b_te[b] > T.b_tb[b]) {
+        bool l2p_done = F.leaf_l2p_done && F.O.method == FAR_CHEB && l >= 2 && F.O.e_off[l] >= 0;
+        bool need = !l2p_done || F.L.u_off[b] != F.L.u_off[b + 1] || F.L.w_off[b] != F.L.w_off[b + 1];
+        if (need) leaf_list[atomicAdd(leaf_cnt, 1)] = b;
+    }
+}
+
+void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
+                    cudaStream_t st) {
+    if (nboxes <= 0) return;
+    k_work_lists<<<(nboxes + 255) / 256, 256, 0, st>>>(F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
@@ -293,8 +329,7 @@ __device__ __forceinline__ double eval64(const double *eq, int n, float r, float
     return s;
 }
 
-__global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__restrict__ out) {
-    int b = blockIdx.x;
+__device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restrict__ out) {
     const TreeDev &T = F.T;
     if (!T.b_leaf[b]) return;
     int tb = T.b_tb[b], te = T.b_te[b];
@@ -450,10 +485,20 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, int nboxes, float *__rest
     }
 }
 
-void fmm_leaf(const FmmDev &F, int nboxes, int leaf_cap, float *out_dense, cudaStream_t st) {
+// CTAs walk the compact list of leaves that need this kernel.
+__global__ void __launch_bounds__(LT) k_leaf(FmmDev F, const int *__restrict__ list, const int *__restrict__ count,
+                                             float *__restrict__ out) {
+    const int cnt = *count;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        leaf_box(F, list[i], out);
+        __syncthreads();
+    }
+}
+
+void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {
     if (nboxes <= 0) return;
-    (void)leaf_cap;
-    k_leaf<<<nboxes, LT, 0, st>>>(F, nboxes, out_dense);
+    int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
+    k_leaf<<<grid, LT, 0, st>>>(F, list, count, out_dense);
 }
 
 }  // namespace sph

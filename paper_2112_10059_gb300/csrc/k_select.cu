@@ -87,8 +87,9 @@ __device__ __forceinline__ void thresholds(const SelRule &r, const unsigned *max
     thr_e = r.e_app + r.e_frac * ((double)emax - r.e_app);
 }
 
-// One CTA per brick; blockDim.x = 512; brick of up to 16^3 cells, 8 cells per thread
-// in Morton order (thread t owns local keys 8t .. 8t+7).
+// One CTA per brick; blockDim.x = 512; brick of up to 16^3 cells.  The brick is read
+// row by row (coalesced) into shared memory at local Morton positions; then thread t
+// owns local keys 8t .. 8t+7, so a block scan in thread order is a scan in Morton order.
 template <bool EMIT>
 __global__ void __launch_bounds__(512) k_select_brick(
         SelRule r, const float *__restrict__ q, const float *__restrict__ e,
@@ -107,21 +108,28 @@ __global__ void __launch_bounds__(512) k_select_brick(
     bool qpos;
     thresholds(r, maxes, thr_q, thr_e, qpos);
 
+    // stage the brick: coalesced loads in linear (x fastest) order, rule bits and q
+    // stored at the cell's local Morton index
+    __shared__ uint8_t s_bits[4096];
+    __shared__ float s_q[4096];
+    const int edge = 1 << b;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        int lx = c & (edge - 1), ly = (c >> b) & (edge - 1), lz = c >> (2 * b);
+        uint32_t lk = morton3((uint32_t)lx, (uint32_t)ly, (uint32_t)lz);
+        float qv = 0.0f;
+        int bits = sel_bits(r, q, e, mask, x0 + lx, y0 + ly, z0 + lz, thr_q, thr_e, qpos, qv);
+        s_bits[lk] = (uint8_t)bits;
+        s_q[lk] = qv;
+    }
+    __syncthreads();
     int my_bits[8];
     float my_q[8];
     int ns = 0, nt = 0;
     const int per = (ncell + blockDim.x - 1) / blockDim.x;   // 8 for a 16^3 brick, fewer for small grids
     for (int u = 0; u < per; ++u) {
         int lk = threadIdx.x * per + u;
-        my_bits[u] = 0;
-        my_q[u] = 0.0f;
-        if (lk < ncell && x0 < r.nx && y0 < r.ny && z0 < r.nz) {
-            uint32_t lx, ly, lz;
-            demorton3((uint32_t)lk, lx, ly, lz);
-            float qv = 0.0f;
-            my_bits[u] = sel_bits(r, q, e, mask, x0 + lx, y0 + ly, z0 + lz, thr_q, thr_e, qpos, qv);
-            my_q[u] = qv;
-        }
+        my_bits[u] = lk < ncell ? s_bits[lk] : 0;
+        my_q[u] = lk < ncell ? s_q[lk] : 0.0f;
         ns += my_bits[u] & 1;
         nt += (my_bits[u] >> 1) & 1;
     }

@@ -16,8 +16,9 @@
 //   * thread 0 issues 3 x 8 tcgen05.mma (M = 128, N = 64, K = 16 each) into a
 //     64-column TMEM accumulator and commits to a second mbarrier;
 //   * warp w reads TMEM lanes 32w..32w+31 (rows i) and adds the result into the
-//     destination boxes' downward state (atomically for M2L, whose targets
-//     receive many tiles; plainly for L2L, whose children are unique).
+//     destination boxes' downward state with global reductions (red.add): M2L
+//     targets receive many tiles, and for L2L a reduction avoids a dependent
+//     DRAM read per element.
 // Every wait is bounded; on expiry the tile records an error code and still
 // releases its TMEM.
 #include "sph_kernels.cuh"
@@ -161,9 +162,10 @@ __device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__res
             for (int j = 0; j < 16; ++j) {
                 int d = s.col_dst[c0 + j];
                 if (d < 0) continue;
-                float *o = out + (size_t)d * np + i;
-                if (atomic) atomicAdd(o, v[j]);
-                else *o += v[j];
+                // reductions (fire and forget) in both cases; `atomic` only documents whether
+                // several tiles may add into the same element
+                (void)atomic;
+                atomicAdd(out + (size_t)d * np + i, v[j]);
             }
         }
     }
@@ -246,6 +248,162 @@ __global__ void __launch_bounds__(128) k_l2l_tc(FmmDev F, int level, int parent_
     const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
     tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err);
     tile_teardown(s);
+}
+
+// ---------------------------------------------------------------- L2L, all 8 children per CTA
+// 64 parents per CTA; their downward states are gathered once (B tile), and the 8 child
+// operators stream through two 64 KiB image buffers: image c + 2 is loaded into the
+// buffer of image c as soon as the MMAs reading it have completed.  Child c accumulates
+// into TMEM columns [64c, 64c + 64), all 512 columns of the SM's tensor memory.
+constexpr uint32_t L8_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + 64 + 9 * TCN * 4;
+
+__global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent_begin, int parent_count,
+                                                 const uint16_t *__restrict__ images, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uintptr_t pa = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
+    uint8_t *base = reinterpret_cast<uint8_t *>(pa);
+    uint8_t *abuf[2] = {base, base + 2 * A_BYTES};        // each: hi (32 KiB) then lo (32 KiB)
+    TcSmem s;
+    s.a_hi = abuf[0];
+    s.a_lo = abuf[0] + A_BYTES;
+    s.b_hi = base + 4 * A_BYTES;
+    s.b_lo = s.b_hi + B_BYTES;
+    uint8_t *tail = s.b_lo + B_BYTES;
+    uint64_t *bar_a = reinterpret_cast<uint64_t *>(tail);          // [2]
+    uint64_t *bar_free = bar_a + 2;                                 // [2]
+    s.bar_mma = bar_a + 4;
+    s.tmem_base = reinterpret_cast<uint32_t *>(tail + 40);
+    s.col_src = reinterpret_cast<int *>(tail + 64);
+    int *dst = s.col_src + TCN;                                     // [8][TCN]
+    s.col_dst = dst;
+    const int t0 = blockIdx.x * TCN;
+    const TreeDev &T = F.T;
+    const int np = F.O.npad, n = F.O.n;
+    int any = 0;
+    if (threadIdx.x < TCN) {
+        int p = parent_begin + t0 + threadIdx.x;
+        int P = -1;
+        if (t0 + (int)threadIdx.x < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
+        for (int c = 0; c < 8; ++c) {
+            int C = -1;
+            if (P >= 0) {
+                int ch = T.box_at[dense_off(level) + ((T.b_key[P] << 3) | (uint32_t)c)];
+                if (ch >= 0 && T.b_te[ch] > T.b_tb[ch]) C = ch;
+            }
+            dst[c * TCN + threadIdx.x] = C;
+            any |= C >= 0;
+        }
+        s.col_src[threadIdx.x] = P;
+    }
+    if (!__syncthreads_or(any)) return;
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(tc::smem_u32(s.tmem_base), 512);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(tc::smem_u32(bar_a + k), 1);
+            tc::mbar_init(tc::smem_u32(bar_free + k), 1);
+        }
+        tc::mbar_init(tc::smem_u32(s.bar_mma), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint16_t *img0 = images + (size_t)level * 8 * (2 * A_BYTES / 2);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_expect_tx(tc::smem_u32(bar_a + k), 2 * A_BYTES);
+            tc::bulk_g2s(tc::smem_u32(abuf[k]), img0 + (size_t)k * (2 * A_BYTES / 2), 2 * A_BYTES,
+                         tc::smem_u32(bar_a + k));
+        }
+    }
+    gather_split(s, F.dchk, np);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    const uint32_t tmem = *s.tmem_base;
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        int issued[2] = {1, 1}, landed[2] = {0, 0};   // image loads per buffer
+        const uint32_t idesc = tc::idesc_bf16_f32(TCM, TCN);
+        const uint32_t b_hi = tc::smem_u32(s.b_hi), b_lo = tc::smem_u32(s.b_lo);
+        for (int c = 0; c < 8 && ok; ++c) {
+            const int k = c & 1;
+            ok = tc::mbar_wait_bounded(tc::smem_u32(bar_a + k), (c >> 1) & 1, WAIT_LIMIT);
+            if (!ok) break;
+            ++landed[k];
+            tc::fence_after_sync();
+            const uint32_t a_hi = tc::smem_u32(abuf[k]), a_lo = a_hi + A_BYTES;
+            const uint32_t d = tmem + (uint32_t)(c * TCN);
+#pragma unroll
+            for (int ks = 0; ks < TCK / 16; ++ks) {
+                uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+                uint32_t bo = tc::sw128_offset(0, 16 * ks, TCN);
+                tc::mma_bf16(d, tc::sdesc_sw128(a_hi + ao), tc::sdesc_sw128(b_hi + bo), idesc, ks > 0);
+                tc::mma_bf16(d, tc::sdesc_sw128(a_hi + ao), tc::sdesc_sw128(b_lo + bo), idesc, 1);
+                tc::mma_bf16(d, tc::sdesc_sw128(a_lo + ao), tc::sdesc_sw128(b_hi + bo), idesc, 1);
+            }
+            tc::mma_commit(tc::smem_u32(bar_free + k));
+            if (c + 2 < 8) {
+                ok = tc::mbar_wait_bounded(tc::smem_u32(bar_free + k), (c >> 1) & 1, WAIT_LIMIT);
+                if (!ok) break;
+                tc::mbar_expect_tx(tc::smem_u32(bar_a + k), 2 * A_BYTES);
+                tc::bulk_g2s(tc::smem_u32(abuf[k]), img0 + (size_t)(c + 2) * (2 * A_BYTES / 2), 2 * A_BYTES,
+                             tc::smem_u32(bar_a + k));
+                ++issued[k];
+            }
+        }
+        tc::mma_commit(tc::smem_u32(s.bar_mma));   // tracks every MMA issued so far
+        if (!ok) {
+            atomicOr(err, 4);
+            // let this CTA's own copies and MMAs finish before its memory is released
+            for (int k = 0; k < 2; ++k)
+                if (issued[k] > landed[k])
+                    tc::mbar_wait_bounded(tc::smem_u32(bar_a + k), (issued[k] - 1) & 1, WAIT_LIMIT);
+            tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    bool done = ok_s && tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);
+    if (ok_s && !done) atomicOr(err, 8);
+    if (done) {
+        tc::fence_after_sync();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int i = warp * 32 + lane;
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int c0 = 0; c0 < TCN; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * TCN + c0), v);
+                if (i < n) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        int C = dst[c * TCN + c0 + j];
+                        // a reduction, not a load-add-store: no dependent DRAM round trip per element
+                        if (C >= 0) atomicAdd(F.dchk + (size_t)C * np + i, v[j]);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 512);
+}
+
+void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
+                       int *err, cudaStream_t st) {
+    if (parent_count <= 0 || level < 3) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
+        attr = true;
+    }
+    k_l2l_tc8<<<(parent_count + TCN - 1) / TCN, 128, L8_SMEM, st>>>(F, level, parent_begin, parent_count, images,
+                                                                     err);
 }
 
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }

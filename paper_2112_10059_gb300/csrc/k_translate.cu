@@ -94,7 +94,7 @@ __device__ __forceinline__ void scatter_add(float *__restrict__ out, int np, int
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             int i = i0 + ty * 8 + r;
-            if (i < n) out[(size_t)d * np + i] += acc[r][cc];
+            if (i < n) atomicAdd(out + (size_t)d * np + i, acc[r][cc]);   // reduction: no dependent load
         }
     }
 }

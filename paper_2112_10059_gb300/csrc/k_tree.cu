@@ -244,6 +244,7 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                         if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
                         int A = lookup(T, l, qx, qy, qz);
                         if (A >= 0) {
+                            if (T.b_se[A] <= T.b_sb[A]) continue;   // no sources anywhere below A
                             if (T.b_leaf[A]) {
                                 if (T.b_se[A] > T.b_sb[A]) {
                                     if (FILL) L.u_src[pU] = A;
@@ -300,8 +301,43 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                 ++pU; ++nU;
             }
         }
-        // ---- V
+        // ---- X, and whether any box adjacent to the parent holds sources (else V is empty)
+        bool parent_near_src = false;
         if (l >= 2) {
+            int cx = B.x >> 1, cy = B.y >> 1, cz = B.z >> 1;
+            int found[27];
+            int nf = 0;
+            int n = 1 << (l - 1);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int qx = cx + dx, qy = cy + dy, qz = cz + dz;
+                        if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
+                        for (int m = l - 1; m >= 0; --m) {
+                            int sh = l - 1 - m;
+                            int Am = lookup(T, m, qx >> sh, qy >> sh, qz >> sh);
+                            if (Am >= 0) {
+                                bool hs = T.b_se[Am] > T.b_sb[Am];
+                                if (m == l - 1) parent_near_src |= hs;
+                                if (T.b_leaf[Am] && hs) {
+                                    BoxGeom G = geom_of(T, Am);
+                                    if (!adjacent(G, B, D)) {
+                                        bool dup = false;
+                                        for (int u = 0; u < nf; ++u) dup |= found[u] == Am;
+                                        if (!dup) found[nf++] = Am;
+                                    }
+                                }
+                                break;
+                            }
+                        }
+                    }
+            for (int u = 0; u < nf; ++u) {
+                if (FILL) L.x_src[pX] = found[u];
+                ++pX; ++nX;
+            }
+        }
+        // ---- V (children of the parent's neighbours that hold sources)
+        if (l >= 2 && parent_near_src) {
             int px = (B.x >> 1) << 1, py = (B.y >> 1) << 1, pz = (B.z >> 1) << 1;
             for (int dz = -2; dz <= 3; ++dz)
                 for (int dy = -2; dy <= 3; ++dy)
@@ -319,38 +355,6 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                             ++pV; ++nV;
                         }
                     }
-        }
-        // ---- X
-        if (l >= 2) {
-            int cx = B.x >> 1, cy = B.y >> 1, cz = B.z >> 1;
-            int found[27];
-            int nf = 0;
-            int n = 1 << (l - 1);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-                        if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
-                        for (int m = l - 1; m >= 0; --m) {
-                            int sh = l - 1 - m;
-                            int Am = lookup(T, m, qx >> sh, qy >> sh, qz >> sh);
-                            if (Am >= 0) {
-                                if (T.b_leaf[Am] && T.b_se[Am] > T.b_sb[Am]) {
-                                    BoxGeom G = geom_of(T, Am);
-                                    if (!adjacent(G, B, D)) {
-                                        bool dup = false;
-                                        for (int u = 0; u < nf; ++u) dup |= found[u] == Am;
-                                        if (!dup) found[nf++] = Am;
-                                    }
-                                }
-                                break;
-                            }
-                        }
-                    }
-            for (int u = 0; u < nf; ++u) {
-                if (FILL) L.x_src[pX] = found[u];
-                ++pX; ++nX;
-            }
         }
     }
     if (!FILL) {

@@ -59,6 +59,7 @@ struct sph_ctx {
     int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
     bool translate_per_box = false;   // one CTA per box for M2L / L2L instead of the batched GEMMs
     bool tc_used = false;             // this eval ran the tensor-core translations
+    bool l2l_eight = true;            // tensor-core L2L: all 8 children per CTA (else one child per CTA)
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -67,6 +68,7 @@ struct sph_ctx {
     DevBuf b_ueq, b_dchk;
     DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf b_err;                // device error flags of the tensor-core tiles
+    DevBuf b_work;               // compact work lists: sources per level, leaves for the leaf kernel
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
     // operator cache key
@@ -447,13 +449,19 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
     F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
     F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
+    const bool per_box = c->translate_per_box;
+    F.leaf_l2p_done = (!per_box && F.O.method == FAR_CHEB) ? 1 : 0;
+    ENS(c->b_work, (2 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    int *w_src = P<int>(c->b_work), *w_leaf = w_src + std::max(nb, 1), *w_cnt = w_leaf + std::max(nb, 1);
+    CK(cudaMemsetAsync(w_cnt, 0, 64 * sizeof(int), c->stream));
+    fmm_work_lists(F, nb, w_src, w_cnt, w_leaf, w_cnt + 32, c->stream);
+    c->launches += nb > 0;
     tm.mark_at(3, c->stream);
     for (int l = c->Lmax; l >= 2; --l) {
-        fmm_upward_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+        fmm_upward_level(F, l, c->lvl_count[l], w_src + c->lvl_base[l], w_cnt + l, c->stream);
         c->launches += c->lvl_count[l] > 0;
     }
     tm.mark_at(4, c->stream);
-    const bool per_box = c->translate_per_box;
     if (per_box) {
         tm.mark_at(5, c->stream);
         tm.mark_at(6, c->stream);
@@ -501,7 +509,10 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
                 c->launches += c->lvl_count[l] > 0;
             }
         for (int l = 3; l <= c->Lmax; ++l) {
-            if (tc) fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
+            if (tc && c->l2l_eight)
+                fmm_l2l_tc8_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
+            else if (tc)
+                fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
             else fmm_l2l_gemm_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], c->stream);
             c->launches += c->lvl_count[l - 1] > 0;
         }
@@ -509,17 +520,16 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         c->tc_used = tc;
     }
     tm.mark_at(7, c->stream);
-    if (!per_box && F.O.method == FAR_CHEB) {
+    if (F.leaf_l2p_done) {
         for (int l = 2; l <= c->Lmax; ++l) {
             if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
                 fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
                 ++c->launches;
             }
         }
-        F.leaf_l2p_done = 1;
     }
     tm.mark_at(8, c->stream);
-    fmm_leaf(F, nb, c->leaf_size, out, c->stream);
+    fmm_leaf(F, nb, w_leaf, w_cnt + 32, out, c->stream);
     c->launches += nb > 0;
     tm.mark_at(9, c->stream);
     CK(cudaGetLastError());
@@ -579,6 +589,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     }
     if (const char *e = getenv("SPH_PINV_EPS")) c->pinv_eps = atof(e);
     if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
+    if (const char *e = getenv("SPH_L2L_ONE_CHILD")) c->l2l_eight = atoi(e) == 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
         if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }
@@ -600,7 +611,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);

@@ -151,11 +151,14 @@ struct FmmDev {
     int D, nx, ny, self_mode;
     float *ueq, *dchk;   // [nboxes][PP]: upward / downward check potentials u_B, d_B
 };
-void fmm_upward_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
+void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
+                      cudaStream_t st);
+void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
+                    cudaStream_t st);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
-void fmm_leaf(const FmmDev &F, int nboxes, int leaf_cap, float *out_dense, cudaStream_t st);
+void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st);
 void fmm_m2l_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 // V pairs grouped by (level, offset slot): built once per tree, then one M2L launch for all levels.
 struct PairsDev {
@@ -175,6 +178,8 @@ void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st);
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
                       int *err, cudaStream_t st);
+void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
+                       int *err, cudaStream_t st);
 void fmm_l2l_gemm_level(const FmmDev &F, int level, int parent_begin, int parent_count, cudaStream_t st);
 void fmm_l2p_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st);
 

@@ -203,19 +203,19 @@ def streamer(n=128, box=1.0, p_torr=760.0, chan_len=0.5, i_frac=0.0, e_frac=0.1,
                    leaf_size=leaf_size, seed=seed)
 
 
-def config_c0():
+def plain_24():
     """24^3 plain direct quadrature in a 2 mm cube at 760 Torr, all cells source and target."""
     return plain_gaussian(24, seed=1000)
 
 
-def config_c1(n=128):
+def streamer_full(n=128):
     """FMM without adaptivity: 128^3 streamer in a 1 cm cube at 760 Torr, all cells."""
     return streamer(n=n, box=1.0, p_torr=760.0, chan_len=0.5, i_frac=0.0,
                     targets_all=True, seed=1001, with_efield=False,
                     name="streamer_%d_full" % n)
 
 
-def config_c2(n=256, p_torr=760.0, e_frac=0.1, e_applied=0.0):
+def streamer_adaptive(n=256, p_torr=760.0, e_frac=0.1, e_applied=0.0):
     """Adaptive FMM: 256^3 streamer in a 1 cm cube, sources I >= 1e-4 max I,
     targets |E| >= e_applied + e_frac*(max|E| - e_applied)."""
     return streamer(n=n, box=1.0, p_torr=p_torr, chan_len=0.5, i_frac=1e-4,

@@ -44,7 +44,7 @@ def _check_fmm(S, ref, T, label=""):
 
 def _problems():
     return [
-        si.config_c0(),
+        si.plain_24(),
         si.streamer(n=48, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.3, targets_all=False, leaf_size=32,
                     sigma_head=0.02, chan_radius=0.02, seed=11, name="s48"),
         si.streamer(n=40, box=0.4, chan_len=0.2, i_frac=1e-4, targets_all=True, leaf_size=16,
@@ -111,7 +111,7 @@ def test_tree_bit_exact(sph, ctx, case):
 
 
 def test_direct_fp64_and_fp32_c0(sph, ctx):
-    p = si.config_c0()
+    p = si.plain_24()
     sph.solve(p, ctx)
     ref, J, T = oracle.sph_problem(p)
     d64 = sph.eval_direct(ctx, fp64=True).cpu().numpy()
@@ -219,6 +219,22 @@ def test_tensor_core_translations(sph, pi):
     _check_fmm(b, ref, T, p.name + " bf16x3")
     c32.close()
     ctc.close()
+
+
+def test_l2l_eight_children_per_cta(sph, monkeypatch):
+    """Tensor-core L2L with all 8 child operators streamed through one CTA equals the
+    one-child-per-CTA kernel (same products, different scheduling)."""
+    p = _problems()[2]
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SPH_L2L_ONE_CHILD", flag)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        outs.append(out.cpu().numpy().astype(np.float64))
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs[1][T], outs[0][T]) < 1e-6
+    _check_fmm(outs[1], ref, T, "l2l8")
 
 
 def test_empty_sets(sph, ctx):
