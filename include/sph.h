@@ -168,6 +168,29 @@ typedef struct sph_tree_view {
 } sph_tree_view;
 int sph_get_tree(sph_ctx *ctx, sph_tree_view *tree);
 
+/* Selection without any device allocation (the paper has no counterpart: this is a
+ * convenience of the library for callers that cannot allocate device memory while
+ * they run -- e.g. an application that owns all device memory through its own
+ * allocator or budget, or code running where an allocation would synchronise or is
+ * forbidden).  It performs the same source / target selection as eval_sph (same
+ * rules, same Morton-ordered output) but takes every output from the caller and
+ * keeps its scratch in one fixed static device array inside the library.
+ *   device, cuda_stream: CUDA device and stream (cudaStream_t, NULL = default);
+ *   nx, ny, nz in [1, 512] (larger grids: SPH_ECAPACITY, nothing queued);
+ *   q_dev, emag_dev / mask_dev, i_frac, e_frac, e_applied: as set_sources /
+ *   set_targets / set_criteria (at most one of emag_dev, mask_dev non-NULL);
+ *   outputs (device, each with room for nx*ny*nz entries): src_key_dev, src_pc_dev
+ *   (packed i | j<<10 | k<<20), src_q_dev, trg_key_dev, trg_pc_dev, in Morton order;
+ *   counts_dev: int32[2] receives (number of sources, number of targets).
+ * The work is queued on cuda_stream; results are valid once it completes.  All calls
+ * share the library's scratch array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The first call for a device looks up the array's device
+ * address; make it before any stream capture.  Never calls cudaMalloc or cudaFree. */
+int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny, int nz, const float *q_dev,
+                       const float *emag_dev, const uint8_t *mask_dev, double i_frac, double e_frac,
+                       double e_applied, uint32_t *src_key_dev, uint32_t *src_pc_dev, float *src_q_dev,
+                       uint32_t *trg_key_dev, uint32_t *trg_pc_dev, int32_t *counts_dev);
+
 /* Library version string. */
 const char *sph_version(void);
 

@@ -66,7 +66,7 @@ class TreeView(ctypes.Structure):
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
            "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_host", "eval_direct",
-           "sph_get_selection", "sph_get_tree", "sph_version"]
+           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version"]
 
 FAR_CHEBYSHEV = 0
 FAR_SURFACE = 1
@@ -99,6 +99,8 @@ def load(path: str | None = None):
         lib.sph_get_selection.argtypes = [V, V, ctypes.POINTER(I64), V, ctypes.POINTER(I64)]
         lib.sph_get_tree.argtypes = [V, ctypes.POINTER(TreeView)]
         lib.sph_version.restype = ctypes.c_char_p
+        lib.sph_select_noalloc.argtypes = [I, V, I, I, I, V, V, V, D, D, D, V, V, V, V, V, V]
+        lib.sph_select_noalloc.restype = I
         for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
                   "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I
