@@ -3,6 +3,9 @@
 // that emits the selected cells directly in Morton order.
 //
 // Pass 1 (k_grid_max): max q and max |E| over all cells (NaN ignored).
+// Default: k_select_onepass (below) does count, offsets and emit in one pass over the
+// grid with a decoupled look-back across bricks.  The two-pass form that follows is kept
+// as a reference:
 // Pass 2 (k_select_count): per 16^3 brick (a Morton-contiguous key range),
 //         count selected sources / targets.
 // Pass 3 (k_scan_bricks): exclusive scan of the brick counts.
@@ -216,6 +219,175 @@ __global__ void __launch_bounds__(1024) k_scan2(const int *__restrict__ a, const
     if (threadIdx.x == 1023) { tot[0] = sa[1023]; tot[1] = sb[1023]; }
 }
 
+// ---------------------------------------------------------------- one-pass selection
+// Exact FP32 equivalent of the FP64 rule (double)v >= thr: the smallest float f with
+// (double)f >= thr, so that v >= f decides every finite v exactly as the FP64 compare.
+__device__ __forceinline__ float ge_threshold_f32(double thr) {
+    float f = __double2float_rd(thr);          // (double)f <= thr
+    if ((double)f < thr) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Look-back state of one brick: status in bits 62-63 (0 none, 1 own counts, 2 inclusive
+// prefix), source count in bits 31-61, target count in bits 0-30.
+__device__ __forceinline__ unsigned long long pack_state(unsigned st, unsigned ns, unsigned nt) {
+    return ((unsigned long long)st << 62) | ((unsigned long long)ns << 31) | (unsigned long long)nt;
+}
+
+constexpr unsigned LOOKBACK_LIMIT = 1u << 22;
+
+// One pass over the grid: each CTA takes the next brick in dispatch order (ticket), reads
+// it row by row, evaluates both rules, ranks its cells in Morton order, finds its output
+// offset by decoupled look-back over the preceding bricks, and writes its points.
+__global__ void __launch_bounds__(512) k_select_onepass(
+        SelRule r, const float *__restrict__ q, const float *__restrict__ e, const uint8_t *__restrict__ mask,
+        const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
+        int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
+        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc) {
+    __shared__ int s_brick;
+    __shared__ float s_thr_q, s_thr_e;
+    __shared__ int s_qpos;
+    __shared__ uint8_t s_bits[4096];
+    __shared__ float s_q[4096];
+    __shared__ int ws[16], wt[16];
+    __shared__ unsigned s_pre_s, s_pre_t;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_brick = (int)atomicAdd(ticket, 1u);
+        double thr_q, thr_e;
+        bool qpos;
+        thresholds(r, maxes, thr_q, thr_e, qpos);
+        s_thr_q = ge_threshold_f32(thr_q);
+        s_thr_e = ge_threshold_f32(thr_e);
+        s_qpos = qpos;
+    }
+    __syncthreads();
+    const int brick = s_brick;
+    const int b = r.brick_edge_log2;
+    const int ncell = 1 << (3 * b);
+    const int edge = 1 << b;
+    uint32_t bx, by, bz;
+    demorton3((uint32_t)brick, bx, by, bz);
+    const int x0 = bx << b, y0 = by << b, z0 = bz << b;
+    const float thr_q = s_thr_q, thr_e = s_thr_e;
+    const bool qpos = s_qpos;
+    // stage in linear (x fastest) order: coalesced rows, byte-wise conflict-free stores
+    for (int c = tid; c < ncell; c += blockDim.x) {
+        int lx = c & (edge - 1), ly = (c >> b) & (edge - 1), lz = c >> (2 * b);
+        int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        int bits = 0;
+        float qv = 0.f;
+        if (x < r.nx && y < r.ny && z < r.nz) {
+            uint32_t lin = (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z);
+            qv = __ldg(q + lin);
+            if (r.src_all || (qpos && qv >= thr_q)) bits |= 1;
+            if (r.trg_mode == 0) bits |= 2;
+            else if (r.trg_mode == 1) { if (__ldg(e + lin) >= thr_e) bits |= 2; }
+            else if (__ldg(mask + lin)) bits |= 2;
+        }
+        s_bits[c] = (uint8_t)bits;
+        s_q[c] = qv;
+    }
+    __syncthreads();
+    int my_bits[8];
+    float my_q[8];
+    int ns = 0, nt = 0;
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    for (int u = 0; u < per; ++u) {
+        int lk = tid * per + u;
+        my_bits[u] = 0;
+        my_q[u] = 0.f;
+        if (lk < ncell) {
+            uint32_t lx, ly, lz;
+            demorton3((uint32_t)lk, lx, ly, lz);
+            int c = (int)(lx + ((ly + (lz << b)) << b));
+            my_bits[u] = s_bits[c];
+            my_q[u] = s_q[c];
+        }
+        ns += my_bits[u] & 1;
+        nt += (my_bits[u] >> 1) & 1;
+    }
+    // block exclusive scan of (ns, nt)
+    int lane = tid & 31, w = tid >> 5;
+    int is = ns, it = nt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int a = __shfl_up_sync(0xffffffffu, is, o);
+        int c = __shfl_up_sync(0xffffffffu, it, o);
+        if (lane >= o) { is += a; it += c; }
+    }
+    if (lane == 31) { ws[w] = is; wt[w] = it; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int a = lane < nw ? ws[lane] : 0;
+        int c = lane < nw ? wt[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int a2 = __shfl_up_sync(0xffffffffu, a, o);
+            int c2 = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) { a += a2; c += c2; }
+        }
+        if (lane < 16) { ws[lane] = a; wt[lane] = c; }
+    }
+    __syncthreads();
+    const int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
+    const int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
+    if (tid == 0) {
+        const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
+        unsigned pre_s = 0, pre_t = 0;
+        if (brick == 0) {
+            atomicExch(state + brick, pack_state(2u, agg_s, agg_t));
+        } else {
+            atomicExch(state + brick, pack_state(1u, agg_s, agg_t));
+            bool failed = false;
+            for (int j = brick - 1; j >= 0; --j) {
+                unsigned long long v = 0;
+                unsigned stt = 0;
+                for (unsigned k = 0; k < LOOKBACK_LIMIT; ++k) {
+                    v = *((volatile unsigned long long *)(state + j));
+                    stt = (unsigned)(v >> 62);
+                    if (stt != 0) break;
+                    __nanosleep(64);
+                }
+                if (stt == 0) { failed = true; break; }
+                pre_s += (unsigned)((v >> 31) & 0x7FFFFFFFu);
+                pre_t += (unsigned)(v & 0x7FFFFFFFu);
+                if (stt == 2) break;
+            }
+            if (failed) atomicOr(totals + 2, 1);
+            atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
+        }
+        s_pre_s = pre_s;
+        s_pre_t = pre_t;
+        if (brick == nbr - 1) {
+            __threadfence();
+            bool bad = atomicOr(totals + 2, 0) != 0;
+            totals[0] = bad ? -1 : (int)(pre_s + agg_s);
+            totals[1] = bad ? -1 : (int)(pre_t + agg_t);
+        }
+    }
+    __syncthreads();
+    int ps = (int)s_pre_s + base_s, pt = (int)s_pre_t + base_t;
+    for (int u = 0; u < per; ++u) {
+        int lk = tid * per + u;
+        if (!my_bits[u]) continue;
+        uint32_t lx, ly, lz;
+        demorton3((uint32_t)lk, lx, ly, lz);
+        uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)lk;
+        uint32_t pc = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
+        if (my_bits[u] & 1) {
+            src_key[ps] = key;
+            src_pc[ps] = pc;
+            src_q[ps] = my_q[u];
+            ++ps;
+        }
+        if (my_bits[u] & 2) {
+            trg_key[pt] = key;
+            trg_pc[pt] = pc;
+            ++pt;
+        }
+    }
+}
+
 int select_launch(const SelectArgs &A, cudaStream_t st) {
     int b = A.brick_log2;
     int nbr = 1 << (3 * (A.D - b));
@@ -232,12 +404,23 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     int gm = (int)((n + 255) / 256);
     if (gm > 152 * 16) gm = 152 * 16;
     k_grid_max<<<gm, 256, 0, st>>>(r.src_all ? nullptr : A.q, r.trg_mode == 1 ? A.emag : nullptr, n, A.maxes);
-    k_select_brick<false><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
-                                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-    k_scan2<<<1, 1024, 0, st>>>(A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
-    k_select_brick<true><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
-                                              A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
-                                              A.trg_key, A.trg_pc);
+    if (A.two_pass) {
+        k_select_brick<false><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        k_scan2<<<1, 1024, 0, st>>>(A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
+        k_select_brick<true><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
+                                                  A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
+                                                  A.trg_key, A.trg_pc);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    // one pass: the look-back states live in cnt_s .. cnt_t (2 ints per brick), the ticket in off_s[0]
+    unsigned long long *state = reinterpret_cast<unsigned long long *>(A.cnt_s);
+    unsigned *ticket = reinterpret_cast<unsigned *>(A.off_s);
+    cudaMemsetAsync(state, 0, sizeof(unsigned long long) * nbr, st);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
+    k_select_onepass<<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
+                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

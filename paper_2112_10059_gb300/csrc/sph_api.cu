@@ -60,6 +60,7 @@ struct sph_ctx {
     bool translate_per_box = false;   // one CTA per box for M2L / L2L instead of the batched GEMMs
     bool tc_used = false;             // this eval ran the tensor-core translations
     bool l2l_eight = true;            // tensor-core L2L: all 8 children per CTA (else one child per CTA)
+    int select_two_pass = 0;          // 1: two-pass selection instead of the one-pass look-back
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -188,6 +189,7 @@ int run_select(sph_ctx *c) {
     A.q = c->q; A.emag = c->emag; A.mask = c->mask;
     A.i_frac = c->i_frac; A.e_frac = c->e_frac; A.e_app = c->e_app;
     A.maxes = P<unsigned>(c->b_maxes);
+    A.two_pass = c->select_two_pass;
     A.cnt_s = P<int>(c->b_cnt); A.cnt_t = A.cnt_s + nbr;
     A.off_s = P<int>(c->b_off); A.off_t = A.off_s + nbr;
     A.totals = P<int>(c->b_tot);
@@ -195,8 +197,10 @@ int run_select(sph_ctx *c) {
     A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
     c->launches += 4;
-    CK(cudaMemcpyAsync(c->pinned, A.totals, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->pinned[0] < 0 || c->pinned[1] < 0 || (!A.two_pass && c->pinned[2] != 0))
+        return fail(c, SPH_ETIMEOUT, "selection look-back gave up waiting for a preceding brick");
     c->ns = c->pinned[0];
     c->nt = c->pinned[1];
     return SPH_OK;
@@ -590,6 +594,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_PINV_EPS")) c->pinv_eps = atof(e);
     if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2L_ONE_CHILD")) c->l2l_eight = atoi(e) == 0;
+    if (const char *e = getenv("SPH_SELECT_TWO_PASS")) c->select_two_pass = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
         if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }

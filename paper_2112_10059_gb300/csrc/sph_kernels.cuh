@@ -21,7 +21,8 @@ struct SelectArgs {
     double i_frac, e_frac, e_app;
     unsigned *maxes;                 // [2]
     int *cnt_s, *cnt_t, *off_s, *off_t;   // [nbricks]
-    int *totals;                     // [2] Ns, Nt
+    int *totals;                     // [3] Ns, Nt, error flag (look-back gave up)
+    int two_pass = 0;                // 1: count pass + scan + emit pass instead of the one-pass kernel
     uint32_t *src_key, *src_pc, *trg_key, *trg_pc;
     float *src_q;
 };
