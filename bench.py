@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-snapshot batched evaluation")
+    ap.add_argument("--batch-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -182,21 +184,23 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks):
 
 
 def oracle_sample(p, J, T, seconds, seed=5):
-    """Time the FP64 oracle on a bounded random sample of targets; returns (targets/s, sample, cores)."""
+    """Time the FP64 oracle on a bounded random sample of targets; returns (targets/s, sample, seconds, cores).
+
+    The sample grows geometrically until one timed run lasts at least half of ``seconds``
+    (or covers every target), so that thread start-up does not dominate the figure.
+    """
     import oracle
     a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
     rng = np.random.default_rng(seed)
-    n0 = max(8, min(T.size, 64))
-    samp = np.sort(rng.choice(T, size=n0, replace=False))
-    t0 = time.perf_counter()
-    oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
-    dt = time.perf_counter() - t0
-    n1 = int(min(T.size, max(n0, n0 * seconds / max(dt, 1e-3))))
-    samp = np.sort(rng.choice(T, size=n1, replace=False))
-    t0 = time.perf_counter()
-    oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
-    dt = time.perf_counter() - t0
-    return n1 / dt, n1, dt, oracle.num_threads()
+    n1 = max(8, min(T.size, 64))
+    while True:
+        samp = np.sort(rng.choice(T, size=n1, replace=False))
+        t0 = time.perf_counter()
+        oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds or n1 >= T.size:
+            return n1 / dt, n1, dt, oracle.num_threads()
+        n1 = int(min(T.size, max(2 * n1, n1 * 0.8 * seconds / max(dt, 1e-3))))
 
 
 def run_reference(args, rank):
@@ -224,6 +228,89 @@ def run_reference(args, rank):
                                        "extrapolated to targets/s" % (nsamp, T.size, J.size)},
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_batch(sph, torch, dev, stream, args, prec):
+    """24 independent snapshots through eval_sph_batch (autotuned leaf sizes), against the same
+    snapshots evaluated one eval_sph call at a time on per-snapshot contexts."""
+    import oracle
+    probs = si.snapshot_batch(24)
+    bps = [sph.BatchProblem.from_problem(p, device=dev) for p in probs]
+    ctx = sph.Context(dev.index or 0, stream)
+    sph.set_criteria(ctx, 0.0, 0.0, 0.0, 1, 0, prec)
+    sph.set_far_field(ctx, sph.FAR_CHEBYSHEV, args.order)
+    t0 = time.perf_counter()
+    sph.eval_sph_batch(ctx, bps)          # first call: autotuner measurements, operator builds
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(2):
+        sph.eval_sph_batch(ctx, bps)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    wall, dev_ms, nt = [], [], 0
+    for k in range(max(1, args.batch_steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        _, st = sph.eval_sph_batch(ctx, bps, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t0)
+        dev_ms.append(e0.elapsed_time(e1))
+        nt = int(st.n_targets)
+        launches = int(st.n_launches)
+    # the same snapshots one call at a time (each on its own context, leaf sizes fixed to the tuned ones)
+    seq_ctx = []
+    for p, bp in zip(probs, bps):
+        c = sph.Context(dev.index or 0, stream)
+        sph.set_grid(c, p.nx, p.ny, p.nz, p.h, p.pO2_torr, p.chi_min, p.chi_max)
+        sph.set_sources(c, bp.q, p.source_scale)
+        sph.set_targets(c, emag=bp.emag)
+        sph.set_criteria(c, p.i_frac, p.e_frac, p.e_applied, 1, 0, prec)
+        sph.set_far_field(c, sph.FAR_CHEBYSHEV, args.order)
+        seq_ctx.append(c)
+    outs = [torch.empty_like(bp.out) for bp in bps]
+    leaf = {}
+    for i, c in enumerate(seq_ctx):
+        _, st1 = sph.eval_sph(c, outs[i], stats=True)
+        leaf[probs[i].name] = int(st1.leaf_size)
+    torch.cuda.synchronize()
+    seq = []
+    for k in range(max(1, args.batch_steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, c in enumerate(seq_ctx):
+            sph.eval_sph(c, outs[i])
+        torch.cuda.synchronize()
+        seq.append(time.perf_counter() - t0)
+    same = max(float((o - bp.out).norm() / max(bp.out.norm(), 1e-30)) for o, bp in zip(outs, bps))
+    # accuracy of the batch on sampled targets of the three smallest snapshots
+    rng = np.random.default_rng(3)
+    errs = []
+    for i in sorted(range(len(probs)), key=lambda i: probs[i].ncell)[:3]:
+        p = probs[i]
+        J, T = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+        if T.size == 0:
+            continue
+        samp = np.sort(rng.choice(T, size=min(T.size, 200), replace=False))
+        a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+        ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+        S = bps[i].out.cpu().numpy().astype(np.float64)[samp]
+        errs.append(oracle.rel_l2(S, ref))
+    bw, bd, sq = statistics.median(wall), statistics.median(dev_ms), statistics.median(seq)
+    for c in seq_ctx:
+        c.close()
+    ctx.close()
+    return {"workload": "24 streamer snapshots, grids %s, pressures %s Torr, i_frac 1e-5..1e-3, e_frac 0.05..0.2, "
+                        "seed 1003" % (sorted({p.nx for p in probs}), sorted({int(p.p_torr) for p in probs})),
+            "value": nt / bw, "unit": "targets/s", "ms_per_batch_wall": 1e3 * bw, "ms_per_batch_gpu": bd,
+            "n_targets": nt, "gpu_launches": launches, "graph_captured": True,
+            "sequential_ms_wall": 1e3 * sq, "speedup_vs_sequential": sq / bw,
+            "max_rel_diff_vs_sequential": same, "first_call_s": first_s, "leaf_sizes": leaf,
+            "rel_l2_sampled_smallest3": errs, "l2_flush": "256 MiB write before each batch"}
 
 
 def main():
@@ -337,6 +424,10 @@ def main():
     acc = {"rel_l2_sampled": oracle.rel_l2(S, ref), "max_rel_sampled": oracle.max_rel(S, ref, 1e-3),
            "n_sampled_targets": int(samp.size)}
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(sph, torch, dev, stream, args, prec)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, n1, dt, cores = oracle_sample(p, J, T, args.cpu_seconds)
@@ -360,7 +451,7 @@ def main():
                                         "ms_l2p", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
-                "direct_fp32": direct, "accuracy": acc, "cpu_baseline": cpu}
+                "direct_fp32": direct, "accuracy": acc, "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -90,6 +90,7 @@ typedef struct sph_stats {
     float ms_select, ms_tree, ms_upward, ms_vpairs, ms_m2l, ms_l2l, ms_l2p, ms_near, ms_total;
     int64_t n_launches;        /* kernels launched by this eval (operator precompute excluded) */
     int32_t far_method, far_order;
+    int32_t leaf_size;         /* leaf size of the tree (set_criteria's, or the autotuner's choice) */
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -120,8 +121,10 @@ int set_targets(sph_ctx *ctx, const float *emag_dev, const uint8_t *mask_dev);
 /* Adaptive criteria (Section 3) and method options.
  * i_frac in [0,1] (0: every cell is a source); e_frac in [0,1];
  * e_applied in the units of |E|; self_mode 0 (no self term) or 1 (ball);
- * leaf_size in [1, 4096] (the octree splits a box holding more sources or
- * more targets than this; 0 = 64); m2l_precision one of SPH_M2L_*. */
+ * leaf_size in [0, 4096]: the octree splits a box holding more sources or more
+ * targets than this; 0 = autotune (the first eval of each problem shape times the
+ * candidates 32, 64 and 512 and keeps the fastest for the life of the context);
+ * m2l_precision one of SPH_M2L_*. */
 int set_criteria(sph_ctx *ctx, double i_frac, double e_frac, double e_applied,
                  int self_mode, int leaf_size, int m2l_precision);
 
@@ -133,6 +136,30 @@ int sph_set_far_field(sph_ctx *ctx, int method, int order);
 /* Evaluate S_ph by the adaptive FMM into s_dev (float[nx*ny*nz], device):
  * S_ph at every target, 0 at every other cell.  stats may be NULL. */
 int eval_sph(sph_ctx *ctx, float *s_dev, sph_stats *stats);
+
+/* One snapshot of a batch: its own grid, gas, fields, thresholds and output. */
+typedef struct sph_problem {
+    int nx, ny, nz;                 /* [1, 1024] */
+    double h_cm, pO2_torr;          /* > 0 */
+    double chi_min, chi_max;        /* 0 < chi_min < chi_max */
+    const float *q_dev;             /* float[nx*ny*nz], device */
+    double source_scale;            /* > 0 */
+    const float *emag_dev;          /* float[nx*ny*nz] or NULL */
+    const uint8_t *mask_dev;        /* uint8[nx*ny*nz] or NULL (at most one of emag/mask) */
+    double i_frac, e_frac, e_applied;
+    float *s_dev;                   /* output float[nx*ny*nz], device; 0 at non-targets */
+} sph_problem;
+
+/* Evaluate n independent snapshots (SURVEY's batching row; the paper evaluates S_ph twice per
+ * time step of a streamer simulation, Section 5).  Method options (self term, leaf size or
+ * autotune, M2L arithmetic, far field) come from the context's set_criteria /
+ * sph_set_far_field; the grid, fields and thresholds from each problem.  The snapshots'
+ * phases are interleaved so the whole batch needs three host synchronisations, and their
+ * FMM passes run concurrently on per-snapshot streams, captured into one CUDA graph.
+ * Inputs must be ready on the context's stream; outputs are complete on it when the
+ * queued work finishes.  stats (optional) sums counts over the batch; ms_total is the
+ * batch's GPU time.  Each snapshot slot keeps its own buffers and operator cache. */
+int eval_sph_batch(sph_ctx *ctx, int n, const sph_problem *problems, sph_stats *stats);
 
 /* Same evaluation with host buffers: copies q (and |E| or the mask, as set
  * by the last set_targets call's kind: pass the matching host array, or NULL

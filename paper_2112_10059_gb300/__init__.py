@@ -20,8 +20,8 @@ import threading
 import numpy as np
 
 __all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "eval_sph",
-           "eval_sph_host", "eval_direct", "get_selection", "get_tree", "load", "SphError",
-           "M2L_F32", "M2L_BF16X3", "Stats"]
+           "eval_sph_host", "eval_direct", "eval_sph_batch", "BatchProblem", "get_selection", "get_tree", "load",
+           "SphError", "M2L_F32", "M2L_BF16X3", "Stats"]
 
 M2L_F32 = 0
 M2L_BF16X3 = 1
@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("ms_upward", ctypes.c_float), ("ms_vpairs", ctypes.c_float), ("ms_m2l", ctypes.c_float),
                 ("ms_l2l", ctypes.c_float), ("ms_l2p", ctypes.c_float),
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
-                ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32)]
+                ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,8 +64,17 @@ class TreeView(ctypes.Structure):
                 ("v_pairs", ctypes.c_void_p), ("w_pairs", ctypes.c_void_p), ("x_pairs", ctypes.c_void_p)]
 
 
+class Problem(ctypes.Structure):
+    """Mirror of ``sph_problem`` (one snapshot of a batch)."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h_cm", ctypes.c_double),
+                ("pO2_torr", ctypes.c_double), ("chi_min", ctypes.c_double), ("chi_max", ctypes.c_double),
+                ("q_dev", ctypes.c_void_p), ("source_scale", ctypes.c_double), ("emag_dev", ctypes.c_void_p),
+                ("mask_dev", ctypes.c_void_p), ("i_frac", ctypes.c_double), ("e_frac", ctypes.c_double),
+                ("e_applied", ctypes.c_double), ("s_dev", ctypes.c_void_p)]
+
+
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
-           "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_host", "eval_direct",
+           "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
            "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version"]
 
 FAR_CHEBYSHEV = 0
@@ -94,6 +103,7 @@ def load(path: str | None = None):
         lib.set_criteria.argtypes = [V, D, D, D, I, I, I]
         lib.sph_set_far_field.argtypes = [V, I, I]
         lib.eval_sph.argtypes = [V, V, V]
+        lib.eval_sph_batch.argtypes = [V, I, ctypes.POINTER(Problem), V]
         lib.eval_sph_host.argtypes = [V, V, V, V, V, V]
         lib.eval_direct.argtypes = [V, I, V]
         lib.sph_get_selection.argtypes = [V, V, ctypes.POINTER(I64), V, ctypes.POINTER(I64)]
@@ -102,7 +112,7 @@ def load(path: str | None = None):
         lib.sph_select_noalloc.argtypes = [I, V, I, I, I, V, V, V, D, D, D, V, V, V, V, V, V]
         lib.sph_select_noalloc.restype = I
         for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
-                  "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
+                  "eval_sph_batch", "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I
         _lib = lib
         return lib
@@ -205,6 +215,55 @@ def eval_sph(ctx: Context, out=None, stats: bool = False):
     return out, st
 
 
+class BatchProblem:
+    """One snapshot for :func:`eval_sph_batch`: grid, gas, CUDA-tensor fields and thresholds."""
+
+    def __init__(self, nx, ny, nz, h, pO2, q, source_scale, emag=None, mask=None, i_frac=0.0, e_frac=0.0,
+                 e_applied=0.0, chi_min=0.035, chi_max=2.0, out=None):
+        import torch
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.h, self.pO2, self.chi_min, self.chi_max = float(h), float(pO2), float(chi_min), float(chi_max)
+        self.q, self.emag, self.mask = q, emag, mask
+        self.source_scale = float(source_scale)
+        self.i_frac, self.e_frac, self.e_applied = float(i_frac), float(e_frac), float(e_applied)
+        if out is None:
+            out = torch.empty(self.nx * self.ny * self.nz, dtype=torch.float32, device=q.device)
+        self.out = out
+
+    @classmethod
+    def from_problem(cls, problem, device="cuda", mask=None):
+        """From a ``sph_inputs.Problem`` (fields copied to the device)."""
+        import torch
+        q = torch.from_numpy(problem.q).to(device)
+        emag = None
+        m = None
+        if mask is not None:
+            m = torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).to(device)
+        elif not (problem.targets_all or problem.emag is None):
+            emag = torch.from_numpy(problem.emag).to(device)
+        return cls(problem.nx, problem.ny, problem.nz, problem.h, problem.pO2_torr, q, problem.source_scale,
+                   emag=emag, mask=m, i_frac=problem.i_frac, e_frac=problem.e_frac, e_applied=problem.e_applied,
+                   chi_min=problem.chi_min, chi_max=problem.chi_max)
+
+    def c_struct(self):
+        return Problem(self.nx, self.ny, self.nz, self.h, self.pO2, self.chi_min, self.chi_max,
+                       _ptr(self.q), self.source_scale, _ptr(self.emag), _ptr(self.mask), self.i_frac,
+                       self.e_frac, self.e_applied, _ptr(self.out))
+
+
+def eval_sph_batch(ctx: Context, problems, stats: bool = False):
+    """S_ph for every snapshot of ``problems`` (list of :class:`BatchProblem`) in one call.
+
+    Method options (self term, leaf size -- 0 autotunes --, M2L arithmetic, far field)
+    come from ``set_criteria`` / ``set_far_field`` on ``ctx``.  Returns (list of outputs,
+    Stats|None); the outputs are each problem's ``out`` tensor.
+    """
+    arr = (Problem * max(len(problems), 1))(*[p.c_struct() for p in problems])
+    st = Stats() if stats else None
+    ctx._ck(ctx.lib.eval_sph_batch(ctx.h, len(problems), arr, ctypes.byref(st) if st is not None else None))
+    return [p.out for p in problems], st
+
+
 def eval_sph_host(ctx: Context, q, emag=None, mask=None, out=None, stats: bool = False):
     """Host-buffer evaluation: numpy in, numpy out (copies inside the call)."""
     if out is None:
@@ -283,6 +342,6 @@ def solve(problem, ctx: Context | None = None, m2l_precision=M2L_F32, leaf_size=
     else:
         set_targets(ctx, emag=torch.from_numpy(problem.emag).cuda())
     set_criteria(ctx, problem.i_frac, problem.e_frac, problem.e_applied, 1,
-                 leaf_size or problem.leaf_size, m2l_precision)
+                 problem.leaf_size if leaf_size is None else leaf_size, m2l_precision)
     out, st = eval_sph(ctx, stats=stats)
     return ctx, out, st

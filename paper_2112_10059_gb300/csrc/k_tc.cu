@@ -34,6 +34,7 @@ constexpr uint32_t TC_TAIL = 32 + 2 * TCN * 4;                     // 2 mbarrier
 // four operand tiles, then the tail
 constexpr uint32_t TC_SMEM = 1024 + 2 * A_BYTES + 2 * B_BYTES + TC_TAIL;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
+void tc_init_attributes();
 
 // Operator (FP32, transposed [k][i], stride np) -> BF16 hi / lo images, K-major SW128.
 __global__ void k_make_image(const float *__restrict__ opT, int np, uint16_t *__restrict__ img) {
@@ -397,27 +398,29 @@ __global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent
 void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
                        int *err, cudaStream_t st) {
     if (parent_count <= 0 || level < 3) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
-        attr = true;
-    }
+    tc_init_attributes();
     k_l2l_tc8<<<(parent_count + TCN - 1) / TCN, 128, L8_SMEM, st>>>(F, level, parent_begin, parent_count, images,
                                                                      err);
 }
 
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
 
+// Opt in to the dynamic shared memory of the tensor-core kernels (host-side, once;
+// called before any launch so that launches can be captured into a graph).
+void tc_init_attributes() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
+    done = true;
+}
+
 size_t tc_image_elems(int count) { return (size_t)count * 2 * (A_BYTES / 2); }
 
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st) {
     if (nV <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        attr = true;
-    }
+    tc_init_attributes();
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;
     k_m2l_tc<<<grid, 128, TC_SMEM, st>>>(F, Pd, images, err);
 }
@@ -425,11 +428,7 @@ void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *ima
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
                       int *err, cudaStream_t st) {
     if (parent_count <= 0 || level < 3) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        attr = true;
-    }
+    tc_init_attributes();
     dim3 grid((parent_count + TCN - 1) / TCN, 8);
     k_l2l_tc<<<grid, 128, TC_SMEM, st>>>(F, level, parent_begin, parent_count, images, err);
 }

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "sph_kernels.cuh"
@@ -50,6 +51,16 @@ struct sph_ctx {
     const uint8_t *mask = nullptr;
     double i_frac = 0, e_frac = 0, e_app = 0;
     int self_mode = 1, leaf_size = 64, m2l_prec = SPH_M2L_F32;
+    int leaf_eff = 64;                // leaf size of the current tree (leaf_size, or the autotuner's choice)
+    std::map<std::string, int> tune_cache;
+    sph_ctx *tune_owner = nullptr;    // batch slots share their parent's autotuner cache
+    // batches: one sub-context (own stream, buffers, operator cache) per snapshot slot
+    std::vector<sph_ctx *> subs;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<cudaEvent_t> events;
+    bool batch_graph = true;
     // results of the last eval
     int64_t ns = 0, nt = 0;
     int nboxes = 0, Lmax = 0;
@@ -170,7 +181,8 @@ KParams make_kp(const sph_ctx *c) {
 }
 
 // Selection into Morton-ordered point arrays; reads back (Ns, Nt).
-int run_select(sph_ctx *c) {
+// ------------------------------------------------------------------ selection
+int select_queue(sph_ctx *c) {
     const int D = c->D;
     const int b = std::min(4, D);
     const int64_t nbr = 1ll << (3 * (D - b));
@@ -196,14 +208,25 @@ int run_select(sph_ctx *c) {
     A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
     A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
-    c->launches += 4;
+    c->launches += 2;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (c->pinned[0] < 0 || c->pinned[1] < 0 || (!A.two_pass && c->pinned[2] != 0))
+    return SPH_OK;
+}
+
+// after the stream has been synchronised
+int select_read(sph_ctx *c) {
+    if (c->pinned[0] < 0 || c->pinned[1] < 0 || (!c->select_two_pass && c->pinned[2] != 0))
         return fail(c, SPH_ETIMEOUT, "selection look-back gave up waiting for a preceding brick");
     c->ns = c->pinned[0];
     c->nt = c->pinned[1];
     return SPH_OK;
+}
+
+int run_select(sph_ctx *c) {
+    int r = select_queue(c);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    return select_read(c);
 }
 
 TreeDev tree_dev(sph_ctx *c) {
@@ -233,9 +256,12 @@ ListDev list_dev(sph_ctx *c) {
     return L;
 }
 
-int run_tree(sph_ctx *c) {
+// ------------------------------------------------------------------ tree and lists
+// pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
+// [44..48) list totals, [48] tensor-core error flags
+int tree_queue(sph_ctx *c) {
     const int D = c->D;
-    int S = c->leaf_size;
+    int S = c->leaf_eff;
     int k = 0;
     while (k < 4 && (1ll << (3 * (k + 1))) <= S) ++k;
     const int Lmax = std::max(0, D - k);
@@ -264,41 +290,60 @@ int run_tree(sph_ctx *c) {
     tree_build_launch(A, c->stream);
     c->launches += 1 + 5 * Lmax;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return SPH_OK;
+}
+
+// after a sync: level counts -> box count; queue the list counting
+int tree_read_count(sph_ctx *c) {
+    const int Lmax = c->Lmax;
     c->lvl_count.assign(Lmax + 1, 0);
     c->lvl_base.assign(Lmax + 1, 0);
     int tot = 0;
     for (int l = 0; l <= Lmax; ++l) {
-        c->lvl_count[l] = c->pinned[16 + l];
+        c->lvl_count[l] = c->pinned[8 + 16 + l];
         c->lvl_base[l] = tot;
         tot += c->lvl_count[l];
     }
     c->nboxes = tot;
-    // lists
     int nb = std::max(tot, 1);
     ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
     ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
     ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
-    lists_count_launch(A.T, L, tot, D, Lmax, P<int>(c->b_scan), ltot, c->stream);
+    lists_count_launch(tree_dev(c), L, tot, c->D, Lmax, P<int>(c->b_scan), ltot, c->stream);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned, ltot, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < 4; ++i) c->list_tot[i] = c->pinned[i];
+    CK(cudaMemcpyAsync(c->pinned + 44, ltot, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return SPH_OK;
+}
+
+// after a sync: list totals -> buffers; queue the list fill
+int lists_fill(sph_ctx *c) {
+    for (int i = 0; i < 4; ++i) c->list_tot[i] = c->pinned[44 + i];
     ENS(c->b_usrc, std::max(1, c->list_tot[0]) * sizeof(int));
     ENS(c->b_vsrc, std::max(1, c->list_tot[1]) * sizeof(int));
     ENS(c->b_vocs, std::max(1, c->list_tot[1]) * sizeof(short));
     ENS(c->b_vtrg, std::max(1, c->list_tot[1]) * sizeof(int));
     ENS(c->b_wsrc, std::max(1, c->list_tot[2]) * sizeof(int));
     ENS(c->b_xsrc, std::max(1, c->list_tot[3]) * sizeof(int));
-    L = list_dev(c);
-    lists_fill_launch(A.T, L, tot, D, Lmax, ltot, c->stream);
-    if (tot > 0) c->launches += 15;
+    ListDev L = list_dev(c);
+    int *ltot = P<int>(c->b_tot) + 4;
+    lists_fill_launch(tree_dev(c), L, c->nboxes, c->D, c->Lmax, ltot, c->stream);
+    if (c->nboxes > 0) c->launches += 15;
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
+}
+
+int run_tree(sph_ctx *c) {
+    int r = tree_queue(c);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    r = tree_read_count(c);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    return lists_fill(c);
 }
 
 void fill_ops(sph_ctx *c, OpsDev &O, int D, int L, bool bf) {
@@ -402,18 +447,247 @@ struct PhaseTimer {
     }
 };
 
-int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
-    PhaseTimer tm;
-    tm.start(stats != nullptr, c->stream);
-    c->launches = 0;
-    // a timeout recorded by the previous eval's tensor-core tiles surfaces here (after its sync)
+// ------------------------------------------------------------------ FMM passes
+struct PassState {
+    FmmDev F;
+    int *w_src = nullptr, *w_leaf = nullptr, *w_cnt = nullptr;
+    PairsDev Pd;
+    int *err = nullptr;
+    bool tc = false;
+};
+
+// Every buffer the passes need (so that fmm_queue allocates nothing and can be captured).
+int fmm_prepare(sph_ctx *c, PassState &S) {
+    const int nb = c->nboxes;
+    const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
+    ENS(c->b_ueq, vb);
+    ENS(c->b_dchk, vb);
+    ENS(c->b_work, (2 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    const int nV = c->list_tot[1];
+    const int nkeys = (c->Lmax + 1) * NSLOT;
+    ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1)) * sizeof(int));
+    ENS(c->b_scan, scan_tmp_ints(nkeys + 1) * sizeof(int) + 64);
+    ENS(c->b_err, 16 * sizeof(int));
+    FmmDev &F = S.F;
+    F.T = tree_dev(c);
+    F.L = list_dev(c);
+    F.O = ops_dev(c);
+    F.src_pc = P<uint32_t>(c->b_spc);
+    F.trg_pc = P<uint32_t>(c->b_tpc);
+    F.trg_key = P<uint32_t>(c->b_tkey);
+    F.src_q = P<float>(c->b_sq);
+    F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
+    F.kp = make_kp(c);
+    F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
+    F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
+    F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
+    F.leaf_l2p_done = (!c->translate_per_box && F.O.method == FAR_CHEB) ? 1 : 0;
+    S.w_src = P<int>(c->b_work);
+    S.w_leaf = S.w_src + std::max(nb, 1);
+    S.w_cnt = S.w_leaf + std::max(nb, 1);
+    int *pb = P<int>(c->b_pairs);
+    PairsDev &Pd = S.Pd;
+    Pd.nkeys = nkeys;
+    Pd.cnt = pb; Pd.off = pb + nkeys; Pd.cursor = pb + 2 * nkeys + 1;
+    Pd.tile_cnt = pb + 3 * nkeys + 1; Pd.tile_off = pb + 4 * nkeys + 1;
+    Pd.total_tiles = pb + 5 * nkeys + 2;
+    Pd.trg = pb + 5 * nkeys + 8; Pd.src = Pd.trg + std::max(nV, 1);
+    S.err = P<int>(c->b_err);
+    S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
+    tc_init_attributes();
+    return SPH_OK;
+}
+
+// Queue the passes on c->stream: memsets and kernels only (no allocation, no sync).
+int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
+    FmmDev &F = S.F;
+    const int nb = c->nboxes;
+    const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
+    CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
+    CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
+    fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, c->stream);
+    c->launches += nb > 0;
+    if (tm) tm->mark_at(3, c->stream);
+    for (int l = c->Lmax; l >= 2; --l) {
+        fmm_upward_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, c->stream);
+        c->launches += c->lvl_count[l] > 0;
+    }
+    if (tm) tm->mark_at(4, c->stream);
+    if (c->translate_per_box) {
+        if (tm) { tm->mark_at(5, c->stream); tm->mark_at(6, c->stream); }
+        for (int l = 2; l <= c->Lmax; ++l) {
+            fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
+            c->launches += c->lvl_count[l] > 0;
+            if (c->list_tot[3] > 0) {
+                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+                c->launches += c->lvl_count[l] > 0;
+            }
+            fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+            c->launches += l >= 3 && c->lvl_count[l] > 0;
+        }
+    } else {
+        // every M2L (all levels) and P2L first, then L2L top-down: d_child += L2L d_parent
+        // needs the parent's d complete, which holds once the level above is done.
+        const int nV = c->list_tot[1];
+        vpairs_build(F, S.Pd, nV, P<int>(c->b_scan), c->stream);
+        c->launches += 8 + (nV > 0 ? 2 : 0);
+        if (tm) tm->mark_at(5, c->stream);
+        if (S.tc) {
+            CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));
+            fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream);
+        } else {
+            fmm_m2l_pairs(F, S.Pd, nV, c->m2l_prec, c->stream);
+        }
+        c->launches += nV > 0;
+        if (tm) tm->mark_at(6, c->stream);
+        for (int l = 2; l <= c->Lmax; ++l)
+            if (c->list_tot[3] > 0) {
+                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
+                c->launches += c->lvl_count[l] > 0;
+            }
+        for (int l = 3; l <= c->Lmax; ++l) {
+            if (S.tc && c->l2l_eight)
+                fmm_l2l_tc8_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, S.err, c->stream);
+            else if (S.tc)
+                fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, S.err, c->stream);
+            else fmm_l2l_gemm_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], c->stream);
+            c->launches += c->lvl_count[l - 1] > 0;
+        }
+        if (S.tc) CK(cudaMemcpyAsync(c->pinned + 48, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        c->tc_used = S.tc;
+    }
+    if (tm) tm->mark_at(7, c->stream);
+    if (F.leaf_l2p_done) {
+        for (int l = 2; l <= c->Lmax; ++l) {
+            if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
+                fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                ++c->launches;
+            }
+        }
+    }
+    if (tm) tm->mark_at(8, c->stream);
+    fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
+    c->launches += nb > 0;
+    if (tm) tm->mark_at(9, c->stream);
+    CK(cudaGetLastError());
+    return SPH_OK;
+}
+
+// Surfaces a timeout recorded by the previous eval's tensor-core tiles (read back after its sync).
+int check_previous_tc(sph_ctx *c) {
     if (c->tc_used && c->pinned[48] != 0) {
         c->tc_used = false;
         return fail(c, SPH_ETIMEOUT, "a tensor-core tile of the previous eval gave up waiting (code %d)",
                     c->pinned[48]);
     }
     c->tc_used = false;
-    int r = run_select(c);
+    return SPH_OK;
+}
+
+void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
+    memset(stats, 0, sizeof *stats);
+    stats->n_sources = c->ns;
+    stats->n_targets = c->nt;
+    stats->depth = c->D;
+    int ml = 0;
+    for (int l = 0; l < (int)c->lvl_count.size(); ++l)
+        if (c->lvl_count[l] > 0) ml = l;
+    stats->max_level = ml;
+    stats->n_boxes = c->nboxes;
+    stats->n_u = c->list_tot[0]; stats->n_v = c->list_tot[1];
+    stats->n_w = c->list_tot[2]; stats->n_x = c->list_tot[3];
+    if (tm) {
+        stats->ms_select = tm->ms(0, 1);
+        stats->ms_tree = tm->ms(1, 2);
+        stats->ms_upward = tm->ms(3, 4);
+        stats->ms_vpairs = tm->ms(4, 5);
+        stats->ms_m2l = tm->ms(5, 6);
+        stats->ms_l2l = tm->ms(6, 7);
+        stats->ms_l2p = tm->ms(7, 8);
+        stats->ms_near = tm->ms(8, 9);
+        stats->ms_total = tm->ms(0, 9);
+    }
+    stats->n_launches = c->launches;
+    stats->far_method = c->far_method;
+    stats->far_order = c->far_order;
+    stats->leaf_size = c->leaf_eff;
+}
+
+// tree + operators + passes for the current selection (used by eval and by the autotuner)
+int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm) {
+    int r = run_tree(c);
+    if (r) return r;
+    if (tm) tm->mark_at(2, c->stream);
+    r = run_ops(c);
+    if (r) return r;
+    PassState S;
+    r = fmm_prepare(c, S);
+    if (r) return r;
+    return fmm_queue(c, S, out, tm);
+}
+
+// Problem class of the autotuner's cache: grid shape, far-field form and arithmetic, and the
+// selected set sizes and kernel decay length on a log2 scale (the quantities that move the
+// near/far balance); snapshots of one class share the measured leaf size.
+std::string tune_key(const sph_ctx *c) {
+    auto lg = [](double v) { return v > 0 ? (int)std::lround(std::log2(v)) : -99; };
+    char buf[256];
+    snprintf(buf, sizeof buf, "%d,%d,%d|%d,%d,%d|%d,%d|%d", c->nx, c->ny, c->nz, c->far_method, c->far_order,
+             c->m2l_prec, lg((double)c->ns), lg((double)c->nt), lg(2.0 * c->beta * c->h));
+    return buf;
+}
+
+// Leaf size by measurement: each candidate's tree, lists and passes are timed with CUDA
+// events on the context's stream (the operator build is excluded: it is cached); the
+// fastest is kept per problem class (tune_key) for the life of the context.
+int autotune_leaf(sph_ctx *c, float *out) {
+    const std::string key = tune_key(c);
+    std::map<std::string, int> &cache = c->tune_owner ? c->tune_owner->tune_cache : c->tune_cache;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        c->leaf_eff = it->second;
+        return SPH_OK;
+    }
+    static const int cands[] = {32, 64, 128, 512};
+    float best_ms = 1e30f;
+    int best = 64;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const size_t out_bytes = sizeof(float) * (size_t)c->nx * c->ny * c->nz;
+    for (int S : cands) {
+        c->leaf_eff = S;
+        int r = fmm_after_select(c, out, nullptr);   // builds and caches this candidate's operators
+        if (r) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+        float tot = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, c->stream));
+            r = fmm_after_select(c, out, nullptr);
+            if (r) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (tot < best_ms) { best_ms = tot; best = S; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the trial passes accumulated into out: clear it for the real evaluation
+    CK(cudaMemsetAsync(out, 0, out_bytes, c->stream));
+    cache[key] = best;
+    c->leaf_eff = best;
+    return SPH_OK;
+}
+
+int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
+    PhaseTimer tm;
+    tm.start(stats != nullptr, c->stream);
+    c->launches = 0;
+    int r = check_previous_tc(c);
+    if (r) return r;
+    r = run_select(c);
     if (r) return r;
     tm.mark_at(1, c->stream);
     if ((int64_t)c->nx * c->ny * c->nz > 0) {
@@ -429,141 +703,242 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         }
         return SPH_OK;
     }
-    r = run_tree(c);
-    if (r) return r;
-    tm.mark_at(2, c->stream);
-    r = run_ops(c);
-    if (r) return r;
-    const int nb = c->nboxes;
-    const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
-    ENS(c->b_ueq, vb);
-    ENS(c->b_dchk, vb);
-    CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
-    FmmDev F;
-    F.T = tree_dev(c);
-    F.L = list_dev(c);
-    F.O = ops_dev(c);
-    F.src_pc = P<uint32_t>(c->b_spc);
-    F.trg_pc = P<uint32_t>(c->b_tpc);
-    F.trg_key = P<uint32_t>(c->b_tkey);
-    F.leaf_l2p_done = 0;
-    F.src_q = P<float>(c->b_sq);
-    F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
-    F.kp = make_kp(c);
-    F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
-    F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
-    F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
-    const bool per_box = c->translate_per_box;
-    F.leaf_l2p_done = (!per_box && F.O.method == FAR_CHEB) ? 1 : 0;
-    ENS(c->b_work, (2 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
-    int *w_src = P<int>(c->b_work), *w_leaf = w_src + std::max(nb, 1), *w_cnt = w_leaf + std::max(nb, 1);
-    CK(cudaMemsetAsync(w_cnt, 0, 64 * sizeof(int), c->stream));
-    fmm_work_lists(F, nb, w_src, w_cnt, w_leaf, w_cnt + 32, c->stream);
-    c->launches += nb > 0;
-    tm.mark_at(3, c->stream);
-    for (int l = c->Lmax; l >= 2; --l) {
-        fmm_upward_level(F, l, c->lvl_count[l], w_src + c->lvl_base[l], w_cnt + l, c->stream);
-        c->launches += c->lvl_count[l] > 0;
-    }
-    tm.mark_at(4, c->stream);
-    if (per_box) {
-        tm.mark_at(5, c->stream);
-        tm.mark_at(6, c->stream);
-        for (int l = 2; l <= c->Lmax; ++l) {
-            fmm_m2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->m2l_prec, c->stream);
-            c->launches += c->lvl_count[l] > 0;
-            if (c->list_tot[3] > 0) {
-                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
-                c->launches += c->lvl_count[l] > 0;
-            }
-            fmm_down_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
-            c->launches += l >= 3 && c->lvl_count[l] > 0;
-        }
+    if (c->leaf_size == 0) {
+        r = autotune_leaf(c, out);
+        if (r) return r;
     } else {
-        // every M2L (all levels) and P2L first, then L2L top-down: d_child += L2L d_parent
-        // needs the parent's d complete, which holds once the level above is done.
-        const int nV = c->list_tot[1];
-        const int nkeys = (c->Lmax + 1) * NSLOT;
-        ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1)) * sizeof(int));
-        ENS(c->b_scan, scan_tmp_ints(nkeys + 1) * sizeof(int) + 64);
-        PairsDev Pd;
-        int *pb = P<int>(c->b_pairs);
-        Pd.nkeys = nkeys;
-        Pd.cnt = pb; Pd.off = pb + nkeys; Pd.cursor = pb + 2 * nkeys + 1;
-        Pd.tile_cnt = pb + 3 * nkeys + 1; Pd.tile_off = pb + 4 * nkeys + 1;
-        Pd.total_tiles = pb + 5 * nkeys + 2;
-        Pd.trg = pb + 5 * nkeys + 8; Pd.src = Pd.trg + std::max(nV, 1);
-        vpairs_build(F, Pd, nV, P<int>(c->b_scan), c->stream);
-        c->launches += 8 + (nV > 0 ? 2 : 0);
-        tm.mark_at(5, c->stream);
-        const bool tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr;
-        ENS(c->b_err, 16 * sizeof(int));
-        int *err = P<int>(c->b_err);
-        if (tc) {
-            CK(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-            fmm_m2l_tc(F, Pd, nV, F.O.m2l_img, err, c->stream);
-        } else {
-            fmm_m2l_pairs(F, Pd, nV, c->m2l_prec, c->stream);
-        }
-        c->launches += nV > 0;
-        tm.mark_at(6, c->stream);
-        for (int l = 2; l <= c->Lmax; ++l)
-            if (c->list_tot[3] > 0) {
-                fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
-                c->launches += c->lvl_count[l] > 0;
-            }
-        for (int l = 3; l <= c->Lmax; ++l) {
-            if (tc && c->l2l_eight)
-                fmm_l2l_tc8_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
-            else if (tc)
-                fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, err, c->stream);
-            else fmm_l2l_gemm_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], c->stream);
-            c->launches += c->lvl_count[l - 1] > 0;
-        }
-        if (tc) CK(cudaMemcpyAsync(c->pinned + 48, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        c->tc_used = tc;
+        c->leaf_eff = c->leaf_size;
     }
-    tm.mark_at(7, c->stream);
-    if (F.leaf_l2p_done) {
-        for (int l = 2; l <= c->Lmax; ++l) {
-            if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
-                fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
-                ++c->launches;
-            }
-        }
-    }
-    tm.mark_at(8, c->stream);
-    fmm_leaf(F, nb, w_leaf, w_cnt + 32, out, c->stream);
-    c->launches += nb > 0;
-    tm.mark_at(9, c->stream);
-    CK(cudaGetLastError());
+    r = fmm_after_select(c, out, &tm);
+    if (r) return r;
     if (stats) {
         CK(cudaStreamSynchronize(c->stream));
         if (c->tc_used && c->pinned[48] != 0)
             return fail(c, SPH_ETIMEOUT, "a tensor-core tile gave up waiting (code %d)", c->pinned[48]);
+        fill_stats(c, stats, &tm);
+    }
+    return SPH_OK;
+}
+
+sph_ctx *make_sub(sph_ctx *parent) {
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return nullptr;
+    c->device = parent->device;
+    c->tune_owner = parent;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return nullptr;
+    }
+    c->own_stream = true;
+    if (cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(c->stream);
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || p.nx > 1024 || p.ny > 1024 || p.nz > 1024) return SPH_EINVAL;
+    if (!(p.h_cm > 0) || !(p.pO2_torr > 0) || !(p.chi_min > 0) || !(p.chi_max > p.chi_min)) return SPH_EINVAL;
+    if (!p.q_dev || !p.s_dev || !(p.source_scale > 0)) return SPH_EINVAL;
+    if (p.emag_dev && p.mask_dev) return SPH_EINVAL;
+    if (!(p.i_frac >= 0 && p.i_frac <= 1) || !(p.e_frac >= 0 && p.e_frac <= 1)) return SPH_EINVAL;
+    sub->nx = p.nx; sub->ny = p.ny; sub->nz = p.nz;
+    sub->D = depth_of(p.nx, p.ny, p.nz);
+    sub->h = p.h_cm; sub->pO2 = p.pO2_torr; sub->chi_min = p.chi_min; sub->chi_max = p.chi_max;
+    sub->alpha = p.chi_min * p.pO2_torr;
+    sub->beta = p.chi_max * p.pO2_torr;
+    sub->grid_set = true;
+    sub->q = p.q_dev; sub->source_scale = p.source_scale; sub->src_set = true;
+    sub->emag = p.emag_dev; sub->mask = p.mask_dev; sub->trg_set = true;
+    sub->i_frac = p.i_frac; sub->e_frac = p.e_frac; sub->e_app = p.e_applied;
+    sub->self_mode = parent->self_mode; sub->leaf_size = parent->leaf_size; sub->m2l_prec = parent->m2l_prec;
+    sub->crit_set = true;
+    sub->far_method = parent->far_method; sub->far_order = parent->far_order;
+    sub->radii = parent->radii; sub->pinv_eps = parent->pinv_eps;
+    sub->translate_per_box = parent->translate_per_box; sub->l2l_eight = parent->l2l_eight;
+    sub->select_two_pass = parent->select_two_pass;
+    sub->launches = 0;
+    return SPH_OK;
+}
+
+int sub_fail(sph_ctx *c, sph_ctx *sub, int code, int i) {
+    return fail(c, code, "snapshot %d: %s", i, sub->err.c_str());
+}
+
+cudaEvent_t batch_event(sph_ctx *c, size_t k) {
+    while (c->events.size() <= k) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        c->events.push_back(e);
+    }
+    return c->events[k];
+}
+
+int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
+    while ((int)c->subs.size() < n) {
+        sph_ctx *sub = make_sub(c);
+        if (!sub) return fail(c, SPH_ENOMEM, "cannot create the context of batch slot %d", (int)c->subs.size());
+        c->subs.push_back(sub);
+    }
+    for (int i = 0; i < n; ++i) {
+        int r = configure_sub(c->subs[i], c, probs[i]);
+        if (r) return fail(c, r, "snapshot %d: invalid problem", i);
+    }
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (stats) {
+        CK(cudaEventCreate(&t0));
+        CK(cudaEventCreate(&t1));
+        CK(cudaEventRecord(t0, c->stream));
+    }
+    // fork: the snapshots' streams wait for the inputs queued on the context's stream
+    cudaEvent_t fork = batch_event(c, 0);
+    if (!fork) return fail(c, SPH_ECUDA, "event creation failed");
+    CK(cudaEventRecord(fork, c->stream));
+    for (int i = 0; i < n; ++i) CK(cudaStreamWaitEvent(c->subs[i]->stream, fork, 0));
+    // phase 1: selection of every snapshot, one synchronisation
+    for (int i = 0; i < n; ++i) {
+        sph_ctx *sub = c->subs[i];
+        int r = check_previous_tc(sub);
+        if (!r) r = select_queue(sub);
+        if (r) return sub_fail(c, sub, r, i);
+        size_t cells = (size_t)sub->nx * sub->ny * sub->nz;
+        CK(cudaMemsetAsync(probs[i].s_dev, 0, cells * sizeof(float), sub->stream));
+    }
+    for (int i = 0; i < n; ++i) {
+        sph_ctx *sub = c->subs[i];
+        CK(cudaStreamSynchronize(sub->stream));
+        int r = select_read(sub);
+        if (r) return sub_fail(c, sub, r, i);
+    }
+    // leaf sizes (autotuned shapes run their candidates here, once per shape)
+    std::vector<int> live;
+    for (int i = 0; i < n; ++i) {
+        sph_ctx *sub = c->subs[i];
+        if (sub->nt == 0) { sub->have_tree = false; continue; }
+        live.push_back(i);
+        if (sub->leaf_size == 0) {
+            int r = autotune_leaf(sub, probs[i].s_dev);
+            if (r) return sub_fail(c, sub, r, i);
+        } else {
+            sub->leaf_eff = sub->leaf_size;
+        }
+    }
+    // phases 2-3: trees, list counts, list fills -- two more synchronisations
+    for (int i : live) {
+        int r = tree_queue(c->subs[i]);
+        if (r) return sub_fail(c, c->subs[i], r, i);
+    }
+    for (int i : live) {
+        CK(cudaStreamSynchronize(c->subs[i]->stream));
+        int r = tree_read_count(c->subs[i]);
+        if (r) return sub_fail(c, c->subs[i], r, i);
+    }
+    for (int i : live) {
+        CK(cudaStreamSynchronize(c->subs[i]->stream));
+        int r = lists_fill(c->subs[i]);
+        if (!r) r = run_ops(c->subs[i]);
+        if (r) return sub_fail(c, c->subs[i], r, i);
+    }
+    std::vector<PassState> ps(n);
+    for (int i : live) {
+        int r = fmm_prepare(c->subs[i], ps[i]);
+        if (r) return sub_fail(c, c->subs[i], r, i);
+    }
+    // phase 4: the FMM passes of every snapshot, concurrently, as one graph
+    bool graph = c->batch_graph && !live.empty();
+    if (graph) {
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(c->cap_stream));
+        // the capture stream starts after the context's stream and every snapshot's pending work
+        cudaEvent_t pre = batch_event(c, 1);
+        CK(cudaEventRecord(pre, c->stream));
+        CK(cudaStreamWaitEvent(c->cap_stream, pre, 0));
+        for (size_t k = 0; k < live.size(); ++k) {
+            cudaEvent_t e = batch_event(c, 2 + k);
+            CK(cudaEventRecord(e, c->subs[live[k]]->stream));
+            CK(cudaStreamWaitEvent(c->cap_stream, e, 0));
+        }
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaEvent_t cf = batch_event(c, 2 + live.size());
+        int r = SPH_OK;
+        if (cudaEventRecord(cf, c->cap_stream) != cudaSuccess) r = SPH_ECUDA;
+        for (size_t k = 0; k < live.size() && !r; ++k) {
+            sph_ctx *sub = c->subs[live[k]];
+            if (cudaStreamWaitEvent(sub->stream, cf, 0) != cudaSuccess) { r = SPH_ECUDA; break; }
+            r = fmm_queue(sub, ps[live[k]], probs[live[k]].s_dev, nullptr);
+            cudaEvent_t j = batch_event(c, 3 + live.size() + k);
+            if (!r && (cudaEventRecord(j, sub->stream) != cudaSuccess ||
+                       cudaStreamWaitEvent(c->cap_stream, j, 0) != cudaSuccess))
+                r = SPH_ECUDA;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+        if (r || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(c, SPH_ECUDA, "batch graph capture failed");
+        }
+        // same topology as the previous batch (the usual case): update the executable in place
+        bool updated = false;
+        if (c->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+        }
+        cudaError_t ei = updated ? cudaSuccess : cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return cuda_fail(c, ei, "cudaGraphInstantiate");
+        }
+        CK(cudaGraphLaunch(c->gexec, c->cap_stream));
+        cudaEvent_t done = batch_event(c, 3 + 2 * live.size());
+        CK(cudaEventRecord(done, c->cap_stream));
+        CK(cudaStreamWaitEvent(c->stream, done, 0));
+    } else {
+        for (int i : live) {
+            int r = fmm_queue(c->subs[i], ps[i], probs[i].s_dev, nullptr);
+            if (r) return sub_fail(c, c->subs[i], r, i);
+        }
+    }
+    // join every snapshot stream back into the context's stream
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t e = batch_event(c, 4 + 2 * live.size() + i);
+        CK(cudaEventRecord(e, c->subs[i]->stream));
+        CK(cudaStreamWaitEvent(c->stream, e, 0));
+    }
+    if (stats) {
+        CK(cudaEventRecord(t1, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
         memset(stats, 0, sizeof *stats);
-        stats->n_sources = c->ns;
-        stats->n_targets = c->nt;
-        stats->depth = c->D;
-        int ml = 0;
-        for (int l = 0; l <= c->Lmax; ++l)
-            if (c->lvl_count[l] > 0) ml = l;
-        stats->max_level = ml;
-        stats->n_boxes = nb;
-        stats->n_u = c->list_tot[0]; stats->n_v = c->list_tot[1];
-        stats->n_w = c->list_tot[2]; stats->n_x = c->list_tot[3];
-        stats->ms_select = tm.ms(0, 1);
-        stats->ms_tree = tm.ms(1, 2);
-        stats->ms_upward = tm.ms(3, 4);
-        stats->ms_vpairs = tm.ms(4, 5);
-        stats->ms_m2l = tm.ms(5, 6);
-        stats->ms_l2l = tm.ms(6, 7);
-        stats->ms_l2p = tm.ms(7, 8);
-        stats->ms_near = tm.ms(8, 9);
-        stats->ms_total = tm.ms(0, 9);
-        stats->n_launches = c->launches;
+        for (int i = 0; i < n; ++i) {
+            sph_ctx *sub = c->subs[i];
+            if (sub->tc_used && sub->pinned[48] != 0)
+                return fail(c, SPH_ETIMEOUT, "snapshot %d: a tensor-core tile gave up waiting", i);
+            stats->n_sources += sub->ns;
+            stats->n_targets += sub->nt;
+            stats->n_boxes += sub->nboxes;
+            stats->n_u += sub->list_tot[0]; stats->n_v += sub->list_tot[1];
+            stats->n_w += sub->list_tot[2]; stats->n_x += sub->list_tot[3];
+            stats->n_launches += sub->launches;
+            stats->depth = std::max(stats->depth, sub->D);
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        stats->ms_total = ms;
         stats->far_method = c->far_method;
         stats->far_order = c->far_order;
+        stats->leaf_size = c->leaf_size;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
     }
     return SPH_OK;
 }
@@ -595,6 +970,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2L_ONE_CHILD")) c->l2l_eight = atoi(e) == 0;
     if (const char *e = getenv("SPH_SELECT_TWO_PASS")) c->select_two_pass = atoi(e) != 0;
+    if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
         if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }
@@ -611,6 +987,12 @@ void sph_destroy(sph_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (sph_ctx *sub : c->subs) sph_destroy(sub);
+    c->subs.clear();
     DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
@@ -621,6 +1003,7 @@ void sph_destroy(sph_ctx *c) {
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -688,8 +1071,7 @@ int set_criteria(sph_ctx *c, double i_frac, double e_frac, double e_applied, int
     if (!(e_frac >= 0 && e_frac <= 1)) return fail(c, SPH_EINVAL, "e_frac must be in [0, 1]");
     if (!std::isfinite(e_applied)) return fail(c, SPH_EINVAL, "e_applied must be finite");
     if (self_mode != 0 && self_mode != 1) return fail(c, SPH_EINVAL, "self_mode must be 0 or 1");
-    if (leaf_size == 0) leaf_size = 64;
-    if (leaf_size < 1 || leaf_size > 4096) return fail(c, SPH_EINVAL, "leaf_size must be in [1, 4096]");
+    if (leaf_size < 0 || leaf_size > 4096) return fail(c, SPH_EINVAL, "leaf_size must be in [0, 4096] (0: autotune)");
     if (m2l_precision != SPH_M2L_F32 && m2l_precision != SPH_M2L_BF16X3)
         return fail(c, SPH_EINVAL, "unknown m2l_precision %d", m2l_precision);
     c->i_frac = i_frac; c->e_frac = e_frac; c->e_app = e_applied;
@@ -703,6 +1085,19 @@ int eval_sph(sph_ctx *c, float *s_dev, sph_stats *stats) {
     if (r) return r;
     if (!s_dev) return fail(c, SPH_EINVAL, "s_dev is NULL");
     return run_fmm(c, s_dev, stats);
+}
+
+int eval_sph_batch(sph_ctx *c, int n, const sph_problem *problems, sph_stats *stats) {
+    if (!c) return SPH_EINVAL;
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned by an earlier CUDA error");
+    if (n < 0 || (n > 0 && !problems)) return fail(c, SPH_EINVAL, "bad batch");
+    if (!c->crit_set) return fail(c, SPH_ESTATE, "set_criteria has not been called");
+    if (n == 0) {
+        if (stats) memset(stats, 0, sizeof *stats);
+        return SPH_OK;
+    }
+    CK(cudaSetDevice(c->device));
+    return run_batch(c, n, problems, stats);
 }
 
 int eval_sph_host(sph_ctx *c, const float *q_host, const float *emag_host, const uint8_t *mask_host,

@@ -174,6 +174,7 @@ void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cu
 void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cudaStream_t st);
 // tensor-core (tcgen05, BF16 x3) translations; require npad == 128
 bool tc_supported(const OpsDev &O);
+void tc_init_attributes();
 size_t tc_image_elems(int count);
 void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st);
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st);

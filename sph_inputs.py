@@ -223,6 +223,29 @@ def streamer_adaptive(n=256, p_torr=760.0, e_frac=0.1, e_applied=0.0):
                     name="streamer_%d_adaptive_p%d" % (n, int(p_torr)))
 
 
+def snapshot_batch(count=24, seed=1003, sizes=(64, 96, 128, 192, 256), pressures=(76.0, 380.0, 760.0)):
+    """Independent streamer snapshots for batched evaluation, drawn from one SplitMix64 stream.
+
+    Per snapshot: grid n^3 with n from ``sizes``, a 1 cm cube, channel length
+    U[0.1, 0.8] cm, pressure from ``pressures``, source threshold i_frac
+    log-uniform in [1e-5, 1e-3], target threshold e_frac U[0.05, 0.2], head
+    position jittered by up to 0.5 mm in x and y.
+    """
+    u = uniform01(seed, 8 * count).reshape(count, 8)
+    out = []
+    for k in range(count):
+        n = int(sizes[min(int(u[k, 0] * len(sizes)), len(sizes) - 1)])
+        chan = 0.1 + 0.7 * float(u[k, 1])
+        p = float(pressures[min(int(u[k, 2] * len(pressures)), len(pressures) - 1)])
+        i_frac = float(10.0 ** (-5.0 + 2.0 * u[k, 3]))
+        e_frac = 0.05 + 0.15 * float(u[k, 4])
+        head = (0.5 + 0.1 * (u[k, 5] - 0.5), 0.5 + 0.1 * (u[k, 6] - 0.5), 0.5 - chan / 2.0)
+        out.append(streamer(n=n, box=1.0, p_torr=p, chan_len=chan, i_frac=i_frac, e_frac=e_frac,
+                            targets_all=False, seed=seed * 1000 + k, head=head,
+                            name="snap%02d_n%d_p%d" % (k, n, int(p))))
+    return out
+
+
 def random_mask(n_cells: int, frac: float, seed: int) -> np.ndarray:
     """uint8 mask with each cell set with probability ``frac`` (SplitMix64 stream)."""
     return (uniform01(seed, n_cells) < frac).astype(np.uint8)
