@@ -75,7 +75,12 @@ class Problem(ctypes.Structure):
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
            "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
-           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version"]
+           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version",
+           # learned surrogate (include/sph_nn.h)
+           "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
+           "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads", "sph_nn_forward", "sph_nn_backward",
+           "sph_nn_adam", "sph_nn_train_step", "sph_nn_make_inputs", "sph_nn_make_target", "sph_pool_avg",
+           "sph_nn_conv3d", "sph_nn_conv3d_wgrad"]
 
 FAR_CHEBYSHEV = 0
 FAR_SURFACE = 1
@@ -111,6 +116,30 @@ def load(path: str | None = None):
         lib.sph_version.restype = ctypes.c_char_p
         lib.sph_select_noalloc.argtypes = [I, V, I, I, I, V, V, V, D, D, D, V, V, V, V, V, V]
         lib.sph_select_noalloc.restype = I
+        PD, PF = ctypes.POINTER(ctypes.c_double), ctypes.c_float
+        lib.sph_nn_create.argtypes = [ctypes.POINTER(V), I, V, I, I]
+        lib.sph_nn_destroy.argtypes = [V]
+        lib.sph_nn_destroy.restype = None
+        lib.sph_nn_last_error.argtypes = [V]
+        lib.sph_nn_last_error.restype = ctypes.c_char_p
+        lib.sph_nn_num_params.restype = I64
+        lib.sph_nn_init.argtypes = [V, ctypes.c_uint64]
+        lib.sph_nn_set_params.argtypes = [V, V, I64]
+        lib.sph_nn_get_params.argtypes = [V, V, I64]
+        lib.sph_nn_get_grads.argtypes = [V, V, I64]
+        lib.sph_nn_forward.argtypes = [V, I, V, V]
+        lib.sph_nn_backward.argtypes = [V, I, V, V, PD]
+        lib.sph_nn_adam.argtypes = [V, PF, PF, PF, PF]
+        lib.sph_nn_train_step.argtypes = [V, I, V, V, PF, PD]
+        lib.sph_nn_make_inputs.argtypes = [V, I, I, V, V, V, V]
+        lib.sph_nn_make_target.argtypes = [V, I, I, V, V, V]
+        lib.sph_pool_avg.argtypes = [I, V, I, I, V, V]
+        lib.sph_nn_conv3d.argtypes = [I, V, I, I, I, I, I, V, V, V, V, V, I, V]
+        lib.sph_nn_conv3d_wgrad.argtypes = [I, V, I, I, I, I, V, V, V]
+        for f in ("sph_nn_create", "sph_nn_init", "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads",
+                  "sph_nn_forward", "sph_nn_backward", "sph_nn_adam", "sph_nn_train_step", "sph_nn_make_inputs",
+                  "sph_nn_make_target", "sph_pool_avg", "sph_nn_conv3d", "sph_nn_conv3d_wgrad"):
+            getattr(lib, f).restype = I
         for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
                   "eval_sph_batch", "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I

@@ -127,6 +127,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void *src, ui
                  : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (generic proxy); src_bytes = 0 writes zeros and
+// reads nothing.  Completion is tracked per thread with commit / wait groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst_saddr, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst_saddr), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// FP32 -> BF16, round to nearest even
+__device__ __forceinline__ uint16_t f2bf(float x) {
+    uint32_t u = __float_as_uint(x);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
 // split an FP32 value into BF16 hi + lo (x ~ hi + lo to ~16 bits)
 __device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
     uint32_t u = __float_as_uint(x);

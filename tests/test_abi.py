@@ -1,4 +1,4 @@
-"""The C ABI library loads and exports every entry point include/sph.h declares (no GPU needed)."""
+"""The C ABI library loads and exports every entry point include/*.h declares (no GPU needed)."""
 import ctypes
 import os
 import re
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "sph.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*([a-z_][a-z_0-9]*)\s*\(", txt, flags=re.M)
     return sorted(set(names))
