@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-snapshot batched evaluation")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip training and judging the learned surrogate")
+    ap.add_argument("--sur-samples", type=int, default=2000, help="FMM solves in the surrogate's training set")
+    ap.add_argument("--sur-epochs", type=int, default=10)
     return ap.parse_args()
 
 
@@ -313,6 +316,118 @@ def run_batch(sph, torch, dev, stream, args, prec):
             "rel_l2_sampled_smallest3": errs, "l2_flush": "256 MiB write before each batch"}
 
 
+def run_surrogate(sph, torch, dev, stream, args, peaks):
+    """Learned surrogate at 256^3 -> 64^3 in the 1.5 cm cube: training set from the adaptive FMM,
+    training by the library's BF16 kernels, then the judged evaluation of the streamer-and-cloud
+    configuration against the FMM alone."""
+    from paper_2112_10059_gb300 import surrogate as sur
+    nf, f = 256, 4
+    D = nf // f
+    B = 4
+    net = sur.Net(edge=D, max_batch=B, seed=11)
+    t0 = time.perf_counter()
+    X, T = sur.training_set(net, args.sur_samples, nf, f, first=0)
+    gen_s = time.perf_counter() - t0
+    Xv, Tv = sur.training_set(net, 16, nf, f, first=100000)
+    before = sur.validation_loss(net, Xv, Tv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = sur.train(net, X, T, epochs=args.sur_epochs, batch=B, lr=1e-3, lr_final=1e-4, X_val=Xv, T_val=Tv)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    steps = args.sur_epochs * (args.sur_samples // B)
+    # one training step and one forward pass timed alone (CUDA events on the network's stream)
+    xb, tb = X[:B].reshape(-1), T[:B].reshape(-1)
+    for _ in range(3):
+        net.backward(xb, tb, B)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        net.backward(xb, tb, B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 5
+    y = net.forward(xb, B)
+    e0.record(stream)
+    for _ in range(5):
+        net.forward(xb, B, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    # prediction error on held-out geometries: network vs the coarse estimate alone
+    en, ec = [], []
+    for i in range(0, 16, B):
+        yy = net.forward(Xv[i:i + B].reshape(-1), B).cpu().numpy().reshape(B, -1, 2)
+        tt = Tv[i:i + B].cpu().numpy().reshape(B, -1)
+        en.append(np.abs(np.expm1(yy[..., 0] - tt)))
+        ec.append(np.abs(np.expm1(-tt)))
+    en, ec = np.concatenate(en).ravel(), np.concatenate(ec).ravel()
+    # the streamer-and-cloud configuration: full FMM vs the judged surrogate
+    p = si.streamer_cloud(nf)
+    q = torch.from_numpy(p.q).to(dev)
+    em = torch.from_numpy(p.emag).to(dev)
+    full = sph.Context(dev.index or 0, stream)
+    sph.set_grid(full, nf, nf, nf, p.h, p.pO2_torr, p.chi_min, p.chi_max)
+    sph.set_sources(full, q, p.source_scale)
+    sph.set_targets(full)
+    sph.set_criteria(full, p.i_frac, 0.0, 0.0, 1, p.leaf_size, sph.M2L_BF16X3)
+    S = torch.empty(nf ** 3, dtype=torch.float32, device=dev)
+    pooled = torch.empty(D ** 3, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sph.eval_sph(full, S)
+        sur.pool_avg(S, nf, f, pooled)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        sph.eval_sph(full, S)
+        sur.pool_avg(S, nf, f, pooled)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1) / 5
+    truth = pooled.cpu().numpy().astype(np.float64)
+    ctx = sph.Context(dev.index or 0, stream)
+    sph.set_grid(ctx, nf, nf, nf, p.h, p.pO2_torr, p.chi_min, p.chi_max)
+    sph.set_sources(ctx, q, p.source_scale)
+    sph.set_targets(ctx, emag=em)
+    sph.set_criteria(ctx, p.i_frac, 0.0, 0.0, 1, p.leaf_size, sph.M2L_BF16X3)
+    judged = []
+    for tol in (1e-3, 1e-2):
+        for use in (True, False):
+            for _ in range(2):
+                o, st = sur.evaluate(ctx, net, f, tol=tol, samples=2, seed=7, use_net=use)
+            o = o.cpu().numpy().astype(np.float64)
+            rel = np.abs(o - truth) / truth
+            judged.append({"tol": tol, "network": use, "fallback_blocks": st.n_fallback, "blocks": st.n_blocks,
+                           "judged_fail": st.n_judged_fail, "predicted_fail": st.n_predicted_fail,
+                           "rel_l2": float(np.linalg.norm(o - truth) / np.linalg.norm(truth)),
+                           "max_rel": float(rel.max()), "ms": st.ms_total,
+                           "ms_parts": {"coarse": st.ms_coarse, "network": st.ms_net, "judge": st.ms_judge,
+                                        "fallback": st.ms_fallback}})
+    full.close()
+    ctx.close()
+    peak = peaks.get("bf16_tflops", 1947.8)
+    fl_step = sur.train_flops(D, B)
+    fl_fwd = sur.forward_flops(D, B)
+    return {"workload": "256^3 streamer + plasma cloud, 1.5 cm, 760 Torr; 4^3 pooling to 64^3; training set "
+                        "%d seeded random geometries (FMM solves), %d epochs, batch %d" % (args.sur_samples,
+                                                                                         args.sur_epochs, B),
+            "params": int(net.P), "generate_s": gen_s, "train_s": train_s, "train_steps": steps,
+            "val_loss_before": before, "val_loss_after": hist[-1][2], "train_loss_last": hist[-1][1],
+            "pred_err_network": {"mean": float(en.mean()), "median": float(np.median(en)),
+                                 "p90": float(np.percentile(en, 90)), "frac_below_1e-3": float((en < 1e-3).mean())},
+            "pred_err_coarse_only": {"mean": float(ec.mean()), "median": float(np.median(ec)),
+                                     "p90": float(np.percentile(ec, 90)),
+                                     "frac_below_1e-3": float((ec < 1e-3).mean())},
+            "train_step_ms": step_ms, "forward_ms": fwd_ms,
+            "conv_roofline": {"bound": "tensor", "achieved_train": fl_step / (step_ms * 1e-3) / 1e12,
+                              "achieved_forward": fl_fwd / (fwd_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                              "frac_train": fl_step / (step_ms * 1e-3) / 1e12 / peak,
+                              "frac_forward": fl_fwd / (fwd_ms * 1e-3) / 1e12 / peak,
+                              "work": "2*27*Cin*Cout flop per voxel per convolution (%.1f GF forward, %.1f GF per "
+                                      "training step)" % (fl_fwd / 1e9, fl_step / 1e9)},
+            "full_fmm_ms": full_ms, "judged": judged}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -428,6 +543,10 @@ def main():
     if not args.no_batch:
         batch = run_batch(sph, torch, dev, stream, args, prec)
 
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = run_surrogate(sph, torch, dev, stream, args, measured_peaks())
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, n1, dt, cores = oracle_sample(p, J, T, args.cpu_seconds)
@@ -451,7 +570,7 @@ def main():
                                         "ms_l2p", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
-                "direct_fp32": direct, "accuracy": acc, "batch": batch, "cpu_baseline": cpu}
+                "direct_fp32": direct, "accuracy": acc, "batch": batch, "surrogate": surrogate, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -14,9 +14,10 @@
  *   level 3 (D/8):      c30 32->32, c31 32->32 = b3
  *   up (nearest) + s2 -> c22 32->32;  up + s1 -> c12 32->32;  up -> c02 32->16, + s0
  *   c03 16->16 = f;  head (1x1x1, FP32, no ReLU): [r, e] = Wh f + bh
- * Input x: BF16 [B][D][D][D][16] channels-last (x fastest, then y, z, batch); channels 0-2
- * are the log-normalised pooled source, the normalised pooled |E| and the log-normalised
- * coarse FMM estimate (sph_nn_make_inputs), the rest zero.  Output y: FP32 [B][D^3][2]:
+ * Input x: BF16 [B][D][D][D][16] channels-last (x fastest, then y, z, batch); channels 0-3
+ * are the log-normalised pooled source, the normalised pooled |E|, the log-normalised
+ * coarse FMM estimate and the log-normalised largest fine-cell source in each coarse cell
+ * (sph_nn_make_inputs), the rest zero.  Output y: FP32 [B][D^3][2]:
  * r = predicted ln(S_fine_pooled / S_coarse), e = predicted ln |error of r|.
  * D is a power of two, 8 <= D <= 256.
  *
@@ -25,7 +26,7 @@
  * then head w [2][16], b [2].
  *
  * Loss of a training batch with target t (FP32 [B][D^3]):
- *   L = mean (r - t)^2 + 0.1 * mean (e - ln(|r - t| + 1e-4))^2   (inner |r - t| constant).
+ *   L = mean (r - t)^2 + 0.01 * mean (e - ln(|r - t| + 1e-4))^2   (inner |r - t| constant).
  *
  * Conventions as in sph.h: status codes sph_status, *_dev device pointers on the
  * network's device (borrowed), *_host host pointers, all work on the stream given to
@@ -52,7 +53,8 @@ void sph_nn_destroy(sph_nn *net);
 const char *sph_nn_last_error(const sph_nn *net);
 int64_t sph_nn_num_params(void);
 
-/* He-normal weights from a SplitMix64 stream of `seed`, zero biases, small head. */
+/* He-normal weights from a SplitMix64 stream of `seed`, zero biases, small head weights,
+ * error-head bias ln(1e-2). */
 int sph_nn_init(sph_nn *net, uint64_t seed);
 /* Copy the flat FP32 parameters in / out (n must equal sph_nn_num_params()); set_params
  * also resets the Adam state. */
@@ -96,6 +98,34 @@ int sph_nn_conv3d(int device, void *cuda_stream, int mode, int C, int N, int edg
  * input x [nvox][C] and the pre-activation gradient dz [nvox][N]. */
 int sph_nn_conv3d_wgrad(int device, void *cuda_stream, int C, int N, int edge, int batch, const uint16_t *x_dev,
                         const uint16_t *dz_dev, float *dw_dev);
+
+/* ---- Surrogate evaluation with the FMM as judge and fallback ----
+ * On the context's grid (cubic, n = factor * D with D the network's edge), sources and
+ * criteria (i_frac selects the sources on both grids; the |E| field given to set_targets,
+ * if any, is only a network input):
+ *   1. S_c: the FMM on the coarse grid D^3 (cell edge factor * h) with the factor^3-pooled
+ *      source, every coarse cell a target;
+ *   2. S_pred = S_c * exp(r), r from the network (use_net = 0: S_pred = S_c);
+ *   3. judge: the FMM on the fine grid at the factor^3 cells of `samples_per_block` seeded
+ *      coarse voxels in every block of 8^3 coarse voxels; a block fails if S_pred differs
+ *      from the pooled fine value by more than tol (relative) at any sample, or (use_net)
+ *      if the error head predicts more than tol anywhere in it;
+ *   4. fallback: the FMM on every fine cell of the failing blocks, pooled.
+ * coarse_out_dev (FP32 [D^3]) receives the pooled-fine-grid estimate of S_ph: S_pred in
+ * passing blocks, the pooled FMM in failing ones.  Synchronises the context's stream. */
+typedef struct sph_surrogate_stats {
+    int32_t n_blocks;             /* (D/8)^3 */
+    int32_t n_fallback;           /* blocks evaluated by the fallback */
+    int32_t n_judged_fail;        /* blocks failed by the judge's samples */
+    int32_t n_predicted_fail;     /* blocks failed by the error head */
+    int64_t n_judge_targets;      /* fine cells evaluated by the judge */
+    int64_t n_fallback_targets;   /* fine cells evaluated by the fallback */
+    float judged_max_err;         /* largest sampled relative error of S_pred */
+    float ms_coarse, ms_net, ms_judge, ms_fallback, ms_total;
+} sph_surrogate_stats;
+
+int eval_sph_surrogate(sph_ctx *ctx, sph_nn *net, int factor, double tol, int samples_per_block, uint64_t seed,
+                       int use_net, float *coarse_out_dev, sph_surrogate_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -37,7 +37,7 @@ from __future__ import annotations
 
 import numpy as np
 
-LAMBDA = 0.1
+LAMBDA = 0.01
 EPS = 1e-4
 
 # (name, in channels, out channels, level)

@@ -80,7 +80,7 @@ EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sourc
            "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
            "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads", "sph_nn_forward", "sph_nn_backward",
            "sph_nn_adam", "sph_nn_train_step", "sph_nn_make_inputs", "sph_nn_make_target", "sph_pool_avg",
-           "sph_nn_conv3d", "sph_nn_conv3d_wgrad"]
+           "sph_nn_conv3d", "sph_nn_conv3d_wgrad", "eval_sph_surrogate"]
 
 FAR_CHEBYSHEV = 0
 FAR_SURFACE = 1
@@ -136,9 +136,10 @@ def load(path: str | None = None):
         lib.sph_pool_avg.argtypes = [I, V, I, I, V, V]
         lib.sph_nn_conv3d.argtypes = [I, V, I, I, I, I, I, V, V, V, V, V, I, V]
         lib.sph_nn_conv3d_wgrad.argtypes = [I, V, I, I, I, I, V, V, V]
+        lib.eval_sph_surrogate.argtypes = [V, V, I, D, I, ctypes.c_uint64, I, V, V]
         for f in ("sph_nn_create", "sph_nn_init", "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads",
                   "sph_nn_forward", "sph_nn_backward", "sph_nn_adam", "sph_nn_train_step", "sph_nn_make_inputs",
-                  "sph_nn_make_target", "sph_pool_avg", "sph_nn_conv3d", "sph_nn_conv3d_wgrad"):
+                  "sph_nn_make_target", "sph_pool_avg", "sph_nn_conv3d", "sph_nn_conv3d_wgrad", "eval_sph_surrogate"):
             getattr(lib, f).restype = I
         for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
                   "eval_sph_batch", "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):

@@ -628,40 +628,57 @@ __global__ void k_pool_avg_f32(const float *__restrict__ fine, int nf, int f, fl
     coarse[p] = s / (float)(f * f * f);
 }
 
-__global__ void k_max3(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ c,
-                       size_t n, unsigned *maxbits) {
-    float ma = 0.f, mb = 0.f, mc = 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        ma = fmaxf(ma, a[i]);
-        if (b) mb = fmaxf(mb, b[i]);
-        mc = fmaxf(mc, c[i]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ma = fmaxf(ma, __shfl_down_sync(0xffffffffu, ma, o));
-        mb = fmaxf(mb, __shfl_down_sync(0xffffffffu, mb, o));
-        mc = fmaxf(mc, __shfl_down_sync(0xffffffffu, mc, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(maxbits, __float_as_uint(ma));
-        atomicMax(maxbits + 1, __float_as_uint(mb));
-        atomicMax(maxbits + 2, __float_as_uint(mc));
-    }
+__global__ void k_pool_max_f32(const float *__restrict__ fine, int nf, int f, float *__restrict__ coarse) {
+    const int nc = nf / f;
+    const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (p >= (size_t)nc * nc * nc) return;
+    const int x = (int)(p % nc), y = (int)((p / nc) % nc), z = (int)(p / ((size_t)nc * nc));
+    float s = 0.f;
+    for (int k = 0; k < f; ++k)
+        for (int j = 0; j < f; ++j) {
+            const float *row = fine + ((size_t)(z * f + k) * nf + (y * f + j)) * nf + x * f;
+            for (int i = 0; i < f; ++i) s = fmaxf(s, row[i]);
+        }
+    coarse[p] = s;
 }
 
-// channel 0: log10(I / max I + 1e-8) / 8 + 1; channel 1: |E| / max |E|;
-// channel 2: ln(S / max S + 1e-12) / ln(1e12) + 1; channels 3..15 zero
+// maxima of up to four non-negative fields (b, d may be null) as float bits
+__global__ void k_max4(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ c,
+                       const float *__restrict__ d, size_t n, unsigned *maxbits) {
+    float m[4] = {0.f, 0.f, 0.f, 0.f};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        m[0] = fmaxf(m[0], a[i]);
+        if (b) m[1] = fmaxf(m[1], b[i]);
+        m[2] = fmaxf(m[2], c[i]);
+        if (d) m[3] = fmaxf(m[3], d[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[k] = fmaxf(m[k], __shfl_down_sync(0xffffffffu, m[k], o));
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 4; ++k) atomicMax(maxbits + k, __float_as_uint(m[k]));
+}
+
+// channel 0: log10(I / max I + 1e-8) / 8 + 1 (I averaged over the coarse cell); channel 1:
+// |E| / max |E|; channel 2: ln(S / max S + 1e-12) / ln(1e12) + 1 (coarse FMM estimate);
+// channel 3: as channel 0 for the largest fine-cell I in the coarse cell (sub-cell peak);
+// channels 4..15 zero
 __global__ void k_make_inputs(const float *__restrict__ I, const float *__restrict__ E, const float *__restrict__ S,
-                              const unsigned *__restrict__ maxbits, uint16_t *__restrict__ x, size_t n) {
+                              const float *__restrict__ Imax, const unsigned *__restrict__ maxbits,
+                              uint16_t *__restrict__ x, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float mi = __uint_as_float(maxbits[0]), me = __uint_as_float(maxbits[1]), ms = __uint_as_float(maxbits[2]);
+    const float mx = __uint_as_float(maxbits[3]);
     float f[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) f[c] = 0.f;
     f[0] = mi > 0.f ? fmaxf(0.f, log10f(I[i] / mi + 1e-8f) * 0.125f + 1.f) : 0.f;
     f[1] = (E && me > 0.f) ? E[i] / me : 0.f;
     f[2] = ms > 0.f ? fmaxf(0.f, logf(S[i] / ms + 1e-12f) / 27.631021f + 1.f) : 0.f;
+    f[3] = (Imax && mx > 0.f) ? fmaxf(0.f, log10f(Imax[i] / mx + 1e-8f) * 0.125f + 1.f) : 0.f;
     *reinterpret_cast<uint4 *>(x + i * 16) = pack8(f);
     *reinterpret_cast<uint4 *>(x + i * 16 + 8) = pack8(f + 8);
 }
@@ -678,16 +695,169 @@ void pool_avg_f32(const float *fine, int n_fine, int f, float *coarse, cudaStrea
     const size_t nc = (size_t)(n_fine / f);
     if (nc) k_pool_avg_f32<<<blocks_for(nc * nc * nc), 256, 0, st>>>(fine, n_fine, f, coarse);
 }
-void max3(const float *a, const float *b, const float *c, size_t n, unsigned *maxbits, cudaStream_t st) {
-    cudaMemsetAsync(maxbits, 0, 3 * sizeof(unsigned), st);
-    if (n) k_max3<<<304, 256, 0, st>>>(a, b, c, n, maxbits);
+void pool_max_f32(const float *fine, int n_fine, int f, float *coarse, cudaStream_t st) {
+    const size_t nc = (size_t)(n_fine / f);
+    if (nc) k_pool_max_f32<<<blocks_for(nc * nc * nc), 256, 0, st>>>(fine, n_fine, f, coarse);
 }
-void make_inputs(const float *I, const float *E, const float *S, const unsigned *maxbits, uint16_t *x, size_t n,
-                 cudaStream_t st) {
-    if (n) k_make_inputs<<<blocks_for(n), 256, 0, st>>>(I, E, S, maxbits, x, n);
+void max4(const float *a, const float *b, const float *c, const float *d, size_t n, unsigned *maxbits,
+          cudaStream_t st) {
+    cudaMemsetAsync(maxbits, 0, 4 * sizeof(unsigned), st);
+    if (n) k_max4<<<304, 256, 0, st>>>(a, b, c, d, n, maxbits);
+}
+void make_inputs(const float *I, const float *E, const float *S, const float *Imax, const unsigned *maxbits,
+                 uint16_t *x, size_t n, cudaStream_t st) {
+    if (n) k_make_inputs<<<blocks_for(n), 256, 0, st>>>(I, E, S, Imax, maxbits, x, n);
 }
 void make_target(const float *S_true, const float *S_base, float *t, size_t n, cudaStream_t st) {
     if (n) k_make_target<<<blocks_for(n), 256, 0, st>>>(S_true, S_base, t, n);
+}
+
+
+// ---------------------------------------------------------------- judge and fallback
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int block_of(int v, int lgD) {
+    const int D = 1 << lgD, dm = D - 1, nb = D / JUDGE_BLOCK;
+    const int x = v & dm, y = (v >> lgD) & dm, z = v >> (2 * lgD);
+    return ((z / JUDGE_BLOCK) * nb + y / JUDGE_BLOCK) * nb + x / JUDGE_BLOCK;
+}
+
+// coarse voxel j (0..511) of block b
+__device__ __forceinline__ int voxel_in_block(int b, int j, int lgD) {
+    const int D = 1 << lgD, nb = D / JUDGE_BLOCK;
+    const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+    const int x = bx * JUDGE_BLOCK + (j & 7), y = by * JUDGE_BLOCK + ((j >> 3) & 7), z = bz * JUDGE_BLOCK + (j >> 6);
+    return (z * D + y) * D + x;
+}
+
+__device__ __forceinline__ size_t fine_cell(int v, int lgD, int f, int a) {
+    const int D = 1 << lgD, dm = D - 1, n = D * f;
+    const int x = v & dm, y = (v >> lgD) & dm, z = v >> (2 * lgD);
+    const int ax = a % f, ay = (a / f) % f, az = a / (f * f);
+    return ((size_t)(z * f + az) * n + (y * f + ay)) * n + (x * f + ax);
+}
+
+__global__ void k_apply_residual(const float *__restrict__ Sc, const float *__restrict__ y, int use_net,
+                                 float *__restrict__ Sp, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) Sp[i] = use_net ? Sc[i] * expf(y[2 * i]) : Sc[i];
+}
+
+__global__ void k_block_pred_err(const float *__restrict__ y, int lgD, float *__restrict__ pe, int nblocks) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    float m = 0.f;
+    for (int j = 0; j < JUDGE_BLOCK * JUDGE_BLOCK * JUDGE_BLOCK; ++j)
+        m = fmaxf(m, expf(y[2 * (size_t)voxel_in_block(b, j, lgD) + 1]));
+    pe[b] = m;
+}
+
+__global__ void k_judge_pick(int lgD, int f, uint64_t seed, int samples, uint8_t *__restrict__ mask,
+                             int *__restrict__ sample_vox, int nblocks) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nblocks * samples) return;
+    const int b = e / samples, s = e % samples;
+    const int j = (int)(mix64(seed ^ ((uint64_t)e * 0xD1B54A32D192ED03ull)) & 511u);
+    const int v = voxel_in_block(b, j, lgD);
+    sample_vox[e] = v;
+    for (int a = 0; a < f * f * f; ++a) mask[fine_cell(v, lgD, f, a)] = 1;
+    (void)s;
+}
+
+__global__ void k_judge_err(const float *__restrict__ Sf, const float *__restrict__ Sp,
+                            const int *__restrict__ sample_vox, int lgD, int f, int samples, float *__restrict__ err,
+                            int nblocks) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    float m = 0.f;
+    for (int s = 0; s < samples; ++s) {
+        const int v = sample_vox[b * samples + s];
+        float acc = 0.f;
+        for (int a = 0; a < f * f * f; ++a) acc += Sf[fine_cell(v, lgD, f, a)];
+        acc /= (float)(f * f * f);
+        const float rel = acc > 0.f ? fabsf(Sp[v] - acc) / acc : (Sp[v] != 0.f ? INFINITY : 0.f);
+        m = fmaxf(m, rel);
+    }
+    err[b] = m;
+}
+
+__global__ void k_fallback_flags(const float *__restrict__ err, const float *__restrict__ pe, int use_pred,
+                                 float tol, int nblocks, int *__restrict__ flags, unsigned *counts) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const bool jf = !(err[b] <= tol);
+    const bool pf = use_pred && !(pe[b] <= tol);
+    flags[b] = (jf || pf) ? 1 : 0;
+    if (jf || pf) atomicAdd(counts, 1u);
+    if (jf) atomicAdd(counts + 1, 1u);
+    if (pf) atomicAdd(counts + 2, 1u);
+    atomicMax(counts + 3, __float_as_uint(fminf(err[b], 3.0e38f)));
+}
+
+__global__ void k_fallback_mask(const int *__restrict__ flags, int lgD, int f, uint8_t *__restrict__ mask) {
+    const int D = 1 << lgD, n = D * f;
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)n * n * n) return;
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
+    const int v = ((z / f) * D + y / f) * D + x / f;
+    mask[i] = (uint8_t)flags[block_of(v, lgD)];
+}
+
+__global__ void k_combine(const float *__restrict__ Sp, const float *__restrict__ Sf, const int *__restrict__ flags,
+                          int lgD, int f, float *__restrict__ out) {
+    const int D = 1 << lgD;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D * D * D) return;
+    if (!flags[block_of(v, lgD)]) {
+        out[v] = Sp[v];
+        return;
+    }
+    float acc = 0.f;
+    for (int a = 0; a < f * f * f; ++a) acc += Sf[fine_cell(v, lgD, f, a)];
+    out[v] = acc / (float)(f * f * f);
+}
+
+static int nblocks_of(int lgD) {
+    const int nb = (1 << lgD) / JUDGE_BLOCK;
+    return nb * nb * nb;
+}
+
+void apply_residual(const float *Sc, const float *y, int use_net, float *Sp, size_t n, cudaStream_t st) {
+    if (n) k_apply_residual<<<blocks_for(n), 256, 0, st>>>(Sc, y, use_net, Sp, n);
+}
+void block_pred_err(const float *y, int lgD, float *pe, cudaStream_t st) {
+    const int nb = nblocks_of(lgD);
+    k_block_pred_err<<<blocks_for(nb, 128), 128, 0, st>>>(y, lgD, pe, nb);
+}
+void judge_mask(int lgD, int factor, uint64_t seed, int samples, uint8_t *mask, int *sample_vox, cudaStream_t st) {
+    const size_t n = (size_t)(factor << lgD);
+    cudaMemsetAsync(mask, 0, n * n * n, st);
+    const int nb = nblocks_of(lgD);
+    k_judge_pick<<<blocks_for((size_t)nb * samples, 128), 128, 0, st>>>(lgD, factor, seed, samples, mask, sample_vox,
+                                                                      nb);
+}
+void judge_err(const float *Sf, const float *Sp, const int *sample_vox, int lgD, int factor, int samples, float *err,
+               cudaStream_t st) {
+    const int nb = nblocks_of(lgD);
+    k_judge_err<<<blocks_for(nb, 128), 128, 0, st>>>(Sf, Sp, sample_vox, lgD, factor, samples, err, nb);
+}
+void fallback_flags(const float *err, const float *pe, int use_pred, float tol, int nblocks, int *flags,
+                    unsigned *counts, cudaStream_t st) {
+    cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned), st);
+    k_fallback_flags<<<blocks_for(nblocks, 128), 128, 0, st>>>(err, pe, use_pred, tol, nblocks, flags, counts);
+}
+void fallback_mask(const int *flags, int lgD, int factor, uint8_t *mask, cudaStream_t st) {
+    const size_t n = (size_t)(factor << lgD);
+    k_fallback_mask<<<blocks_for(n * n * n), 256, 0, st>>>(flags, lgD, factor, mask);
+}
+void combine(const float *Sp, const float *Sf, const int *flags, int lgD, int factor, float *out, cudaStream_t st) {
+    const size_t n = (size_t)1 << (3 * lgD);
+    k_combine<<<blocks_for(n), 256, 0, st>>>(Sp, Sf, flags, lgD, factor, out);
 }
 
 }  // namespace nn

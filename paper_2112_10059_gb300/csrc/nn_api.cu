@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/sph_nn.h"
+#include "nn_internal.h"
 #include "nn_kernels.cuh"
 
 using namespace sph::nn;
@@ -24,7 +25,7 @@ const LayerSpec LAYERS[12] = {{"c00", 16, 16, 0}, {"c01", 16, 16, 0}, {"c10", 16
                               {"c22", 32, 32, 2}, {"c12", 32, 32, 1}, {"c02", 32, 16, 0}, {"c03", 16, 16, 0}};
 enum { C00, C01, C10, C11, C20, C21, C30, C31, C22, C12, C02, C03, NLAYER };
 constexpr int HEAD_W = 32, HEAD_N = 34;
-constexpr float LOSS_LAMBDA = 0.1f, LOSS_EPS = 1e-4f;
+constexpr float LOSS_LAMBDA = 0.01f, LOSS_EPS = 1e-4f;
 
 int64_t count_params() {
     int64_t n = 0;
@@ -243,6 +244,10 @@ double normal(uint64_t &s) {
 
 }  // namespace
 
+int sph::nn::net_edge(const sph_nn *n) { return n ? n->edge : 0; }
+cudaStream_t sph::nn::net_stream(const sph_nn *n) { return n ? n->stream : nullptr; }
+const char *sph::nn::net_error(const sph_nn *n) { return n ? n->err.c_str() : ""; }
+
 extern "C" {
 
 int64_t sph_nn_num_params(void) { return count_params(); }
@@ -315,7 +320,7 @@ int sph_nn_create(sph_nn **out, int device, void *stream, int edge, int max_batc
     A(n->g_p2, V3 * 32); A(n->g_s2, V2 * 32); A(n->g_a20, V2 * 32); A(n->g_p1, V2 * 32); A(n->g_s1, V1 * 32);
     A(n->g_a10, V1 * 32); A(n->g_p0, V1 * 16); A(n->g_s0, V0 * 16); A(n->g_a00, V0 * 16);
     if (!r) {
-        n->scratch_n = 2 * (size_t)edge * edge * edge;
+        n->scratch_n = 3 * (size_t)edge * edge * edge;
         A(n->scratch, n->scratch_n);
     }
     if (r) {
@@ -373,13 +378,14 @@ int sph_nn_init(sph_nn *n, uint64_t seed) {
         const double sd = std::sqrt(2.0 / (NTAPS * S.ci));
         const size_t nw = (size_t)S.co * NTAPS * S.ci;
         for (size_t i = 0; i < nw; ++i) {
-            // first layer: channels >= 3 carry no input; keep their weights zero
+            // first layer: channels >= 4 carry no input; keep their weights zero
             const int c = (int)(i % S.ci);
             const double w = normal(s) * sd;
-            h[n->p_off[L] + i] = (L == C00 && c >= 3) ? 0.f : (float)w;
+            h[n->p_off[L] + i] = (L == C00 && c >= 4) ? 0.f : (float)w;
         }
     }
     for (int i = 0; i < HEAD_W; ++i) h[n->head_off + i] = (float)(normal(s) * 0.25 * 0.1);
+    h[n->head_off + HEAD_W + 1] = -4.6f;     // error head starts near ln(1e-2)
     return sph_nn_set_params(n, h.data(), n->P);
 }
 
@@ -436,11 +442,12 @@ int sph_nn_make_inputs(sph_nn *n, int nf, int factor, const float *I, const floa
     if (n->poisoned) return SPH_ECUDA;
     NCK(cudaSetDevice(n->device));
     const size_t nc = (size_t)n->edge * n->edge * n->edge;
-    float *Ic = n->scratch, *Ec = E ? n->scratch + nc : nullptr;
+    float *Ic = n->scratch, *Im = n->scratch + nc, *Ec = E ? n->scratch + 2 * nc : nullptr;
     pool_avg_f32(I, nf, factor, Ic, n->stream);
+    pool_max_f32(I, nf, factor, Im, n->stream);
     if (E) pool_avg_f32(E, nf, factor, Ec, n->stream);
-    max3(Ic, Ec, S, nc, n->maxbits, n->stream);
-    make_inputs(Ic, Ec, S, n->maxbits, x, nc, n->stream);
+    max4(Ic, Ec, S, Im, nc, n->maxbits, n->stream);
+    make_inputs(Ic, Ec, S, Im, n->maxbits, x, nc, n->stream);
     NCK(cudaGetLastError());
     return SPH_OK;
 }

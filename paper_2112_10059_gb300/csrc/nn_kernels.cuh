@@ -78,10 +78,34 @@ void f32_to_bf16(const float *in, uint16_t *out, size_t n, cudaStream_t st);
 
 // coarse inputs of the network from pooled fields
 void pool_avg_f32(const float *fine, int n_fine, int f, float *coarse, cudaStream_t st);
-void max3(const float *a, const float *b, const float *c, size_t n, unsigned *maxbits, cudaStream_t st);
-void make_inputs(const float *I, const float *E, const float *S, const unsigned *maxbits, uint16_t *x, size_t n,
-                 cudaStream_t st);
+void pool_max_f32(const float *fine, int n_fine, int f, float *coarse, cudaStream_t st);
+void max4(const float *a, const float *b, const float *c, const float *d, size_t n, unsigned *maxbits,
+          cudaStream_t st);
+void make_inputs(const float *I, const float *E, const float *S, const float *Imax, const unsigned *maxbits,
+                 uint16_t *x, size_t n, cudaStream_t st);
 void make_target(const float *S_true, const float *S_base, float *t, size_t n, cudaStream_t st);
 
+}  // namespace nn
+}  // namespace sph
+
+namespace sph {
+namespace nn {
+// ---- judge and fallback of the surrogate (single sample, coarse grid D = 1 << lgD, blocks of
+// 8^3 coarse voxels, fine grid n = factor * D)
+constexpr int JUDGE_BLOCK = 8;
+// S_pred = S_coarse * exp(r) (use_net) or S_coarse
+void apply_residual(const float *Sc, const float *y, int use_net, float *Sp, size_t n, cudaStream_t st);
+// per block: max over its voxels of exp(e) (the error head's estimate of |ln S_pred - ln S|)
+void block_pred_err(const float *y, int lgD, float *pe, cudaStream_t st);
+// mark `samples` seeded coarse voxels per block: their factor^3 fine cells in mask (cleared here)
+void judge_mask(int lgD, int factor, uint64_t seed, int samples, uint8_t *mask, int *sample_vox, cudaStream_t st);
+// per block: max relative error of S_pred against the pooled fine S at the sampled voxels
+void judge_err(const float *Sf, const float *Sp, const int *sample_vox, int lgD, int factor, int samples, float *err,
+               cudaStream_t st);
+// flags[b] = err > tol || (use_pred && pe > tol); counts: fallback, judged fail, predicted fail, max err bits
+void fallback_flags(const float *err, const float *pe, int use_pred, float tol, int nblocks, int *flags,
+                    unsigned *counts, cudaStream_t st);
+void fallback_mask(const int *flags, int lgD, int factor, uint8_t *mask, cudaStream_t st);
+void combine(const float *Sp, const float *Sf, const int *flags, int lgD, int factor, float *out, cudaStream_t st);
 }  // namespace nn
 }  // namespace sph

@@ -20,7 +20,10 @@
 #include <vector>
 
 #include "sph_kernels.cuh"
+#include "nn_internal.h"
+#include "nn_kernels.cuh"
 #include "../../include/sph.h"
+#include "../../include/sph_nn.h"
 
 using namespace sph;
 
@@ -61,6 +64,9 @@ struct sph_ctx {
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaEvent_t> events;
     bool batch_graph = true;
+    // surrogate evaluation: coarse and fine sub-contexts on this context's stream, buffers
+    sph_ctx *sur_coarse = nullptr, *sur_fine = nullptr;
+    DevBuf s_qc, s_Sc, s_y, s_Sp, s_x, s_Sf, s_mask, s_svox, s_err, s_pe, s_flags, s_counts;
     // results of the last eval
     int64_t ns = 0, nt = 0;
     int nboxes = 0, Lmax = 0;
@@ -720,20 +726,25 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     return SPH_OK;
 }
 
-sph_ctx *make_sub(sph_ctx *parent) {
+// A sub-context of `parent`: its own stream (batch slots) or the parent's (shared_stream).
+sph_ctx *make_sub(sph_ctx *parent, bool shared_stream = false) {
     sph_ctx *c = new (std::nothrow) sph_ctx();
     if (!c) return nullptr;
     c->device = parent->device;
     c->tune_owner = parent;
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return nullptr;
+    if (shared_stream) {
+        c->stream = parent->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return nullptr;
+        }
+        c->own_stream = true;
     }
-    c->own_stream = true;
     if (cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        cudaStreamDestroy(c->stream);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
         return nullptr;
     }
@@ -943,9 +954,135 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
     return SPH_OK;
 }
 
+int run_surrogate(sph_ctx *c, sph_nn *net, int factor, double tol, int samples, uint64_t seed, int use_net,
+                  float *out, sph_surrogate_stats *st) {
+    const int D = nn::net_edge(net);
+    int lgD = 0;
+    while ((1 << lgD) < D) ++lgD;
+    if (D < nn::JUDGE_BLOCK || (1 << lgD) != D) return fail(c, SPH_EINVAL, "network edge must be a power of two >= 8");
+    if (c->nx != c->ny || c->nx != c->nz || c->nx != factor * D)
+        return fail(c, SPH_EINVAL, "grid must be cubic with edge factor * %d", D);
+    const int n = c->nx;
+    const size_t nf = (size_t)n * n * n, nc = (size_t)D * D * D;
+    const int nbl = (D / nn::JUDGE_BLOCK) * (D / nn::JUDGE_BLOCK) * (D / nn::JUDGE_BLOCK);
+    ENS(c->s_qc, nc * sizeof(float));
+    ENS(c->s_Sc, nc * sizeof(float));
+    ENS(c->s_y, 2 * nc * sizeof(float));
+    ENS(c->s_Sp, nc * sizeof(float));
+    ENS(c->s_x, 16 * nc * sizeof(uint16_t));
+    ENS(c->s_Sf, nf * sizeof(float));
+    ENS(c->s_mask, nf);
+    ENS(c->s_svox, (size_t)nbl * samples * sizeof(int));
+    ENS(c->s_err, nbl * sizeof(float));
+    ENS(c->s_pe, nbl * sizeof(float));
+    ENS(c->s_flags, nbl * sizeof(int));
+    ENS(c->s_counts, 4 * sizeof(unsigned));
+    if (!c->sur_coarse) c->sur_coarse = make_sub(c, true);
+    if (!c->sur_fine) c->sur_fine = make_sub(c, true);
+    if (!c->sur_coarse || !c->sur_fine) return fail(c, SPH_ENOMEM, "cannot create the surrogate's sub-contexts");
+    cudaStream_t s = c->stream;
+    cudaEvent_t ev[5];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    CK(cudaEventRecord(ev[0], s));
+    // 1. coarse FMM on the pooled source
+    nn::pool_avg_f32(c->q, n, factor, P<float>(c->s_qc), s);
+    sph_problem pc;
+    pc.nx = pc.ny = pc.nz = D;
+    pc.h_cm = c->h * factor; pc.pO2_torr = c->pO2; pc.chi_min = c->chi_min; pc.chi_max = c->chi_max;
+    pc.q_dev = P<float>(c->s_qc); pc.source_scale = c->source_scale;
+    pc.emag_dev = nullptr; pc.mask_dev = nullptr;
+    pc.i_frac = c->i_frac; pc.e_frac = 0; pc.e_applied = 0;
+    pc.s_dev = P<float>(c->s_Sc);
+    int r = configure_sub(c->sur_coarse, c, pc);
+    if (!r) r = run_fmm(c->sur_coarse, P<float>(c->s_Sc), nullptr);
+    if (r) return fail(c, r, "coarse FMM: %s", c->sur_coarse->err.c_str());
+    CK(cudaEventRecord(ev[1], s));
+    // 2. network
+    if (use_net) {
+        cudaStream_t ns = nn::net_stream(net);
+        if (ns != s) {
+            CK(cudaStreamWaitEvent(ns, ev[1], 0));
+        }
+        r = sph_nn_make_inputs(net, n, factor, c->q, c->emag, P<float>(c->s_Sc), P<uint16_t>(c->s_x));
+        if (!r) r = sph_nn_forward(net, 1, P<uint16_t>(c->s_x), P<float>(c->s_y));
+        if (r) return fail(c, r, "network: %s", nn::net_error(net));
+        if (ns != s) {
+            CK(cudaEventRecord(ev[2], ns));
+            CK(cudaStreamWaitEvent(s, ev[2], 0));
+        }
+        nn::block_pred_err(P<float>(c->s_y), lgD, P<float>(c->s_pe), s);
+    }
+    nn::apply_residual(P<float>(c->s_Sc), P<float>(c->s_y), use_net, P<float>(c->s_Sp), nc, s);
+    CK(cudaEventRecord(ev[2], s));
+    // 3. judge: the FMM at the sampled voxels' fine cells
+    nn::judge_mask(lgD, factor, seed, samples, P<uint8_t>(c->s_mask), P<int>(c->s_svox), s);
+    sph_problem pf = pc;
+    pf.nx = pf.ny = pf.nz = n;
+    pf.h_cm = c->h;
+    pf.q_dev = c->q;
+    pf.mask_dev = P<uint8_t>(c->s_mask);
+    pf.s_dev = P<float>(c->s_Sf);
+    r = configure_sub(c->sur_fine, c, pf);
+    if (!r) r = run_fmm(c->sur_fine, P<float>(c->s_Sf), nullptr);
+    if (r) return fail(c, r, "judge FMM: %s", c->sur_fine->err.c_str());
+    const int64_t judge_nt = c->sur_fine->nt;
+    nn::judge_err(P<float>(c->s_Sf), P<float>(c->s_Sp), P<int>(c->s_svox), lgD, factor, samples,
+                  P<float>(c->s_err), s);
+    nn::fallback_flags(P<float>(c->s_err), P<float>(c->s_pe), use_net, (float)tol, nbl, P<int>(c->s_flags),
+                       P<unsigned>(c->s_counts), s);
+    CK(cudaEventRecord(ev[3], s));
+    // 4. fallback: every fine cell of the failing blocks
+    nn::fallback_mask(P<int>(c->s_flags), lgD, factor, P<uint8_t>(c->s_mask), s);
+    r = run_fmm(c->sur_fine, P<float>(c->s_Sf), nullptr);
+    if (r) return fail(c, r, "fallback FMM: %s", c->sur_fine->err.c_str());
+    const int64_t fb_nt = c->sur_fine->nt;
+    nn::combine(P<float>(c->s_Sp), P<float>(c->s_Sf), P<int>(c->s_flags), lgD, factor, out, s);
+    CK(cudaEventRecord(ev[4], s));
+    unsigned cnt[4];
+    CK(cudaMemcpyAsync(cnt, c->s_counts.p, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    if (st) {
+        memset(st, 0, sizeof *st);
+        st->n_blocks = nbl;
+        st->n_fallback = (int)cnt[0];
+        st->n_judged_fail = (int)cnt[1];
+        st->n_predicted_fail = (int)cnt[2];
+        float mx;
+        memcpy(&mx, &cnt[3], sizeof mx);
+        st->judged_max_err = mx;
+        st->n_judge_targets = judge_nt;
+        st->n_fallback_targets = fb_nt;
+        cudaEventElapsedTime(&st->ms_coarse, ev[0], ev[1]);
+        cudaEventElapsedTime(&st->ms_net, ev[1], ev[2]);
+        cudaEventElapsedTime(&st->ms_judge, ev[2], ev[3]);
+        cudaEventElapsedTime(&st->ms_fallback, ev[3], ev[4]);
+        cudaEventElapsedTime(&st->ms_total, ev[0], ev[4]);
+    }
+    return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int eval_sph_surrogate(sph_ctx *c, sph_nn *net, int factor, double tol, int samples_per_block, uint64_t seed,
+                       int use_net, float *out, sph_surrogate_stats *stats) {
+    if (!c) return SPH_EINVAL;
+    if (c->poisoned) return fail(c, SPH_ECUDA, "context poisoned by an earlier CUDA error");
+    if (!net || !out || factor < 1 || !(tol > 0) || samples_per_block < 1 || samples_per_block > 64)
+        return fail(c, SPH_EINVAL, "bad surrogate arguments");
+    if (!c->grid_set || !c->src_set || !c->crit_set) return fail(c, SPH_ESTATE, "grid, sources and criteria must be set");
+    CK(cudaSetDevice(c->device));
+    return run_surrogate(c, net, factor, tol, samples_per_block, seed, use_net ? 1 : 0, out, stats);
+}
+
 
 const char *sph_version(void) { return "libsph 0.1 (sm_103a)"; }
 
@@ -993,6 +1130,8 @@ void sph_destroy(sph_ctx *c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (sph_ctx *sub : c->subs) sph_destroy(sub);
     c->subs.clear();
+    if (c->sur_coarse) sph_destroy(c->sur_coarse);
+    if (c->sur_fine) sph_destroy(c->sur_fine);
     DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,

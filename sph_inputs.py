@@ -102,29 +102,38 @@ def scale_of(p_torr: float) -> float:
     return XI_EFF * P_Q / (p_torr + P_Q)
 
 
+def _xp_ops(xp):
+    """(exp, sqrt, where, maximum-with-scalar) for numpy or torch arrays."""
+    if xp is np:
+        return np.exp, np.sqrt, np.where, np.maximum
+    return xp.exp, xp.sqrt, xp.where, lambda a, b: xp.clamp(a, min=b)
+
+
 def streamer_emission(X, Y, Z, head, sigma_head, chan_len, chan_radius,
-                      chan_level=1e-2, cloud=None):
+                      chan_level=1e-2, cloud=None, xp=np):
     """Gaussian head plus a Gaussian-profile channel behind it (head points -z).
 
     ``head`` = (x, y, z) of the head centre; the channel occupies
     ``z in [z_head, z_head + chan_len]`` on the axis through the head with
     radial profile ``chan_level * exp(-rho^2/chan_radius^2)``.  ``cloud`` =
     (centre, radius, level) adds a spherical Gaussian.  Peak value 1 (times I0).
+    ``xp``: numpy (default) or torch, for arrays of either.
     """
+    exp, _, where, _ = _xp_ops(xp)
     hx, hy, hz = head
     r2 = (X - hx) ** 2 + (Y - hy) ** 2 + (Z - hz) ** 2
-    q = np.exp(-r2 / sigma_head ** 2)
+    q = exp(-r2 / sigma_head ** 2)
     rho2 = (X - hx) ** 2 + (Y - hy) ** 2
     inside = (Z >= hz) & (Z <= hz + chan_len)
-    q = q + np.where(inside, chan_level * np.exp(-rho2 / chan_radius ** 2), 0.0)
+    q = q + where(inside, chan_level * exp(-rho2 / chan_radius ** 2), 0.0 * rho2)
     if cloud is not None:
         (cx, cy, cz), crad, clev = cloud
-        q = q + clev * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / crad ** 2)
+        q = q + clev * exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / crad ** 2)
     return q
 
 
 def streamer_efield(X, Y, Z, head, sigma_head, chan_len, chan_radius,
-                    e_background=30.0, e_head=150.0, e_chan=30.0):
+                    e_background=30.0, e_head=150.0, e_chan=30.0, xp=np):
     """|E| (kV/cm) of a synthetic streamer: background + charged ball + charged segment.
 
     * background ``(0, 0, -e_background)``;
@@ -135,30 +144,31 @@ def streamer_efield(X, Y, Z, head, sigma_head, chan_len, chan_radius,
       density set so that the radial field at ``rho = chan_radius`` at
       mid-channel is ``e_chan``.
     """
+    _, sqrt, where, maximum = _xp_ops(xp)
     hx, hy, hz = head
     dx, dy, dz = X - hx, Y - hy, Z - hz
-    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    r = sqrt(dx * dx + dy * dy + dz * dz)
     R = sigma_head
-    rs = np.maximum(r, 1e-300)
-    fball = np.where(r < R, e_head * r / R, e_head * (R / rs) ** 2) / rs
+    rs = maximum(r, 1e-300)
+    fball = where(r < R, e_head * r / R, e_head * (R / rs) ** 2) / rs
     ex = fball * dx
     ey = fball * dy
     ez = fball * dz - e_background
     a = chan_radius
     L = chan_len
     z1, z2 = hz, hz + L
-    k_lam = e_chan * 2.0 * a * np.sqrt(2.0 * a * a + L * L / 4.0) / L
+    k_lam = e_chan * 2.0 * a * float(np.sqrt(2.0 * a * a + L * L / 4.0)) / L
     rho2 = dx * dx + dy * dy
     b2 = rho2 + a * a
     u1 = Z - z1
     u2 = Z - z2
-    s1 = np.sqrt(b2 + u1 * u1)
-    s2 = np.sqrt(b2 + u2 * u2)
+    s1 = sqrt(b2 + u1 * u1)
+    s2 = sqrt(b2 + u2 * u2)
     erho_over_rho = k_lam / b2 * (u1 / s1 - u2 / s2)
     ex = ex + erho_over_rho * dx
     ey = ey + erho_over_rho * dy
     ez = ez + k_lam * (1.0 / s2 - 1.0 / s1)
-    return np.sqrt(ex * ex + ey * ey + ez * ez)
+    return sqrt(ex * ex + ey * ey + ez * ez)
 
 
 def _f32(a):
@@ -244,6 +254,49 @@ def snapshot_batch(count=24, seed=1003, sizes=(64, 96, 128, 192, 256), pressures
                             targets_all=False, seed=seed * 1000 + k, head=head,
                             name="snap%02d_n%d_p%d" % (k, n, int(p))))
     return out
+
+
+def streamer_cloud(n=256, box=1.5, p_torr=760.0, i_frac=1e-4, seed=1004):
+    """Streamer head approaching a plasma cloud: n^3 grid in a 1.5 cm cube at 760 Torr.
+
+    Head (sigma 0.15 mm) at (0.75, 0.75, 0.6) cm with its channel up to z = 1.1 cm; a
+    spherical Gaussian cloud of radius 1 mm and level 1e-3 I0 centred 3 mm ahead of the
+    head, at (0.75, 0.75, 0.3) cm.  Every cell is a target.
+    """
+    return streamer(n=n, box=box, p_torr=p_torr, chan_len=0.5, i_frac=i_frac, targets_all=True,
+                    seed=seed, head=(0.75, 0.75, 0.6), cloud=((0.75, 0.75, 0.3), 0.1, 1e-3),
+                    name="streamer_cloud_%d" % n)
+
+
+def cloud_geometry(k, seed=1005):
+    """Seeded random streamer-and-cloud geometry k (training set of the surrogate), 1.5 cm cube.
+
+    Head at (0.75 +- 0.1, 0.75 +- 0.1, U[0.45, 0.75]) cm, sigma U[0.10, 0.25] mm, channel
+    length U[2, 6] mm and radius U[0.15, 0.3] mm; cloud U[2, 4] mm ahead of the head (-z),
+    radius U[0.5, 1.5] mm, level 10^U[-4, -2.5].
+    """
+    u = uniform01(seed * 7919 + k, 10)
+    head = (0.75 + 0.2 * (u[0] - 0.5), 0.75 + 0.2 * (u[1] - 0.5), 0.45 + 0.3 * u[2])
+    cz = head[2] - (0.2 + 0.2 * u[6])
+    return dict(head=head, sigma_head=0.010 + 0.015 * u[3], chan_len=0.2 + 0.4 * u[4],
+                chan_radius=0.015 + 0.015 * u[5],
+                cloud=((head[0], head[1], cz), 0.05 + 0.1 * u[7], 10.0 ** (-4.0 + 1.5 * u[8])))
+
+
+def fields_torch(n, box, geom, device="cuda", with_efield=True):
+    """Emission shape q and |E| (float32 tensors on ``device``, x fastest) of a geometry dict
+    from :func:`cloud_geometry`, computed in float64 by the same formulas as the numpy path."""
+    import torch
+    h = box / n
+    ax = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) * h
+    Z, Y, X = torch.meshgrid(ax, ax, ax, indexing="ij")
+    q = streamer_emission(X, Y, Z, geom["head"], geom["sigma_head"], geom["chan_len"], geom["chan_radius"],
+                          cloud=geom.get("cloud"), xp=torch)
+    em = None
+    if with_efield:
+        em = streamer_efield(X, Y, Z, geom["head"], geom["sigma_head"], geom["chan_len"], geom["chan_radius"],
+                             xp=torch).float().reshape(-1).contiguous()
+    return (q * I0).float().reshape(-1).contiguous(), em
 
 
 def random_mask(n_cells: int, frac: float, seed: int) -> np.ndarray:
