@@ -162,7 +162,8 @@ void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list
 // and the leaves that the leaf kernel has to visit (any without a table L2P, or with a
 // U or W list).
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
-                             int *__restrict__ leaf_list, int *__restrict__ leaf_cnt) {
+                             int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
+                             int *__restrict__ p2p_cnt) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
     const TreeDev &T = F.T;
@@ -172,16 +173,22 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
         src_list[T.lvl_base[l] + i] = b;
     }
     if (T.b_leaf[b] && T.b_te[b] > T.b_tb[b]) {
-        bool l2p_done = F.leaf_l2p_done && F.O.method == FAR_CHEB && l >= 2 && F.O.e_off[l] >= 0;
-        bool need = !l2p_done || F.L.u_off[b] != F.L.u_off[b + 1] || F.L.w_off[b] != F.L.w_off[b + 1];
+        bool l2p_done = F.leaf_l2p_done && F.O.method == FAR_CHEB && l >= 2 && (F.O.e_off[l] >= 0 || F.l2p_sep);
+        bool has_u = F.L.u_off[b] != F.L.u_off[b + 1];
+        bool has_w = F.L.w_off[b] != F.L.w_off[b + 1];
+        // the separate near-field kernel takes U and (Chebyshev far field) W lists
+        bool w_sep = F.p2p_separate && F.O.method == FAR_CHEB;
+        bool need = !l2p_done || ((has_u || has_w) && !F.p2p_separate) || (has_w && !w_sep);
         if (need) leaf_list[atomicAdd(leaf_cnt, 1)] = b;
+        if (F.p2p_separate && (has_u || (has_w && w_sep))) p2p_list[atomicAdd(p2p_cnt, 1)] = b;
     }
 }
 
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    cudaStream_t st) {
+                    int *p2p_list, int *p2p_cnt, cudaStream_t st) {
     if (nboxes <= 0) return;
-    k_work_lists<<<(nboxes + 255) / 256, 256, 0, st>>>(F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt);
+    k_work_lists<<<(nboxes + 255) / 256, 256, 0, st>>>(F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
+                                                       p2p_cnt);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
@@ -340,8 +347,11 @@ __device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restri
     const int level = T.b_level[b];
     const int size = 1 << (F.D - level);
     // a table L2P (k_l2p_gemm) already wrote S for this leaf: add the near field only
-    const bool l2p_done = F.leaf_l2p_done && cheb && level >= 2 && F.O.e_off[level] >= 0;
-    if (l2p_done && F.L.u_off[b] == F.L.u_off[b + 1] && F.L.w_off[b] == F.L.w_off[b + 1]) return;
+    const bool l2p_done = F.leaf_l2p_done && cheb && level >= 2 && (F.O.e_off[level] >= 0 || F.l2p_sep);
+    const bool do_u = !F.p2p_separate;
+    const bool do_w = !(F.p2p_separate && cheb);     // the near-field kernel takes Chebyshev M2P
+    if (l2p_done && (!do_u || F.L.u_off[b] == F.L.u_off[b + 1]) && (!do_w || F.L.w_off[b] == F.L.w_off[b + 1]))
+        return;
     const float hh = 0.5f * F.kp.h;
     int bx, by, bz;
     box_coords(T, b, bx, by, bz);
@@ -431,7 +441,7 @@ __device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restri
             }
         }
         // ---- M2P over the W list (finer boxes A not adjacent to this leaf)
-        for (int wv = F.L.w_off[b]; wv < F.L.w_off[b + 1]; ++wv) {
+        for (int wv = F.L.w_off[b]; do_w && wv < F.L.w_off[b + 1]; ++wv) {
             int A = F.L.w_src[wv];
             int al = T.b_level[A];
             int asz = 1 << (F.D - al);
@@ -456,7 +466,7 @@ __device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restri
             }
         }
         // ---- P2P over the U list (near field, Eq. nearfar), with the self term
-        for (int uv = F.L.u_off[b]; uv < F.L.u_off[b + 1]; ++uv) {
+        for (int uv = F.L.u_off[b]; do_u && uv < F.L.u_off[b + 1]; ++uv) {
             int A = F.L.u_src[uv];
             int sb = T.b_sb[A], se = T.b_se[A];
             for (int s0 = sb; s0 < se; s0 += LS) {
@@ -493,6 +503,276 @@ __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, const int *__restrict__ l
         leaf_box(F, list[i], out);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------- L2P by tensor-product stages
+// Chebyshev far field, leaves without an interpolation table (edge e > 16 cells): with the
+// 1D Lagrange basis S_a(x) of the box's cell centres along each axis,
+//     S(x, y, z) = sum_c S_c(z) sum_b S_b(y) sum_a S_a(x) d[a + p (b + p c)]
+// is evaluated in three contractions held in shared memory: T1[c][b][x] (p^2 e), T2 for a
+// band of Y rows, T2[c][y][x] (p Y e), then 5 (= p) multiply-adds per cell, written in
+// coalesced x rows.  A box is split over CTAs by z slabs (grid.y).  Cells outside the
+// grid are skipped; a partly selected box writes only where the target mask is set.
+constexpr int SEP_SLAB = 16;
+constexpr int SEP_T2_FLOATS = 16384;   // 64 KiB band of T2
+
+__host__ int sep_band_rows(int p, int e) {
+    int Y = SEP_T2_FLOATS / (p * e);
+    return Y < 1 ? 1 : (Y > e ? e : Y);
+}
+size_t sep_smem_bytes(int p, int np, int e) {
+    return sizeof(float) * ((size_t)np + (size_t)p * e + (size_t)p * p * e + (size_t)p * sep_band_rows(p, e) * e);
+}
+
+__global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, int box_begin, int box_count, int band,
+                                                 float *__restrict__ out) {
+    extern __shared__ float sm[];
+    const int p = F.O.order, n = F.O.n, np = F.O.npad;
+    const int e = 1 << (F.D - level);
+    float *sd = sm;                         // [np]
+    float *Sb = sd + np;                    // [p][e]
+    float *T1 = Sb + p * e;                 // [p*p][e]: (c, b) x
+    float *T2 = T1 + p * p * e;             // [p][band][e]
+    __shared__ float tch[8];
+    const int tid = threadIdx.x;
+    const int z0 = blockIdx.y * SEP_SLAB, z1 = min(e, z0 + SEP_SLAB);
+    if (tid < p) tch[tid] = F.O.cheb_t[tid];
+    for (int i = blockIdx.x; i < box_count; i += gridDim.x) {
+        const int b = box_begin + i;
+        const TreeDev &T = F.T;
+        if (!T.b_leaf[b] || T.b_te[b] <= T.b_tb[b] || z0 >= e) continue;   // uniform over the CTA
+        const bool full = T.b_te[b] - T.b_tb[b] == e * e * e;
+        uint32_t ux, uy, uz;
+        demorton3(T.b_key[b], ux, uy, uz);
+        const int bx = (int)ux * e, by = (int)uy * e, bz = (int)uz * e;
+        __syncthreads();
+        for (int j = tid; j < n; j += blockDim.x) sd[j] = F.dchk[(size_t)b * np + j];
+        for (int j = tid; j < p * e; j += blockDim.x) {
+            const int a = j / e, x = j % e;
+            const float u = (float)(2 * x + 1 - e) / (float)e;
+            float v = 1.f;
+            for (int k = 0; k < p; ++k)
+                if (k != a) v *= (u - tch[k]) / (tch[a] - tch[k]);
+            Sb[j] = v;
+        }
+        __syncthreads();
+        for (int j = tid; j < p * p * e; j += blockDim.x) {
+            const int x = j % e, cb = j / e;
+            const float *row = sd + p * cb;
+            float acc = 0.f;
+            for (int a = 0; a < p; ++a) acc = fmaf(row[a], Sb[a * e + x], acc);
+            T1[j] = acc;
+        }
+        for (int y0 = 0; y0 < e; y0 += band) {
+            const int ny = min(band, e - y0);
+            __syncthreads();
+            for (int j = tid; j < p * ny * e; j += blockDim.x) {
+                const int x = j % e, yy = (j / e) % ny, c = j / (e * ny);
+                float acc = 0.f;
+                for (int bb = 0; bb < p; ++bb) acc = fmaf(T1[(c * p + bb) * e + x], Sb[bb * e + y0 + yy], acc);
+                T2[(c * band + yy) * e + x] = acc;
+            }
+            __syncthreads();
+            const int cells = (z1 - z0) * ny * e;
+            for (int j = tid; j < cells; j += blockDim.x) {
+                const int x = j % e, yy = (j / e) % ny, z = z0 + j / (e * ny);
+                const int gx = bx + x, gy = by + y0 + yy, gz = bz + z;
+                if (gx >= F.nx || gy >= F.ny || gz >= F.nz) continue;
+                const int64_t o = (int64_t)gx + (int64_t)F.nx * ((int64_t)gy + (int64_t)F.ny * gz);
+                if (!full && !F.tmask[o]) continue;
+                float acc = 0.f;
+                for (int c = 0; c < p; ++c) acc = fmaf(T2[(c * band + yy) * e + x], Sb[c * e + z], acc);
+                out[o] = acc;
+            }
+        }
+    }
+}
+
+void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st) {
+    if (box_count <= 0 || level < 2) return;
+    const int e = 1 << (F.D - level), p = F.O.order;
+    const int band = sep_band_rows(p, e);
+    const size_t smem = sep_smem_bytes(p, F.O.npad, e);
+    const int zs = (e + SEP_SLAB - 1) / SEP_SLAB;
+    int gx = box_count < 152 * 4 ? box_count : 152 * 4;
+    k_l2p_sep<<<dim3(gx, zs), 256, smem, st>>>(F, level, box_begin, box_count, band, out);
+}
+
+// Shared-memory opt-in of the FMM kernels that may need more than 48 KiB (host, once, before
+// any launch that could be captured into a graph).  k_l2p_sep needs at most
+// 4 * (512 + 8 * 256 + 64 * 256 + 16384) bytes = 141 KiB (order <= 8, edge <= 256).
+void fmm_init_attributes() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_l2p_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    done = true;
+}
+
+// ---------------------------------------------------------------- near field (U and W lists), warp-tiled
+// One CTA (4 warps) per leaf of the list.  Point sources are staged in shared memory in
+// rounds of up to P2P_CAP: the sources of the leaf's U-list boxes (P2P, Eq. nearfar), then the
+// Chebyshev nodes of its W-list boxes with their upward weights (M2P).  A staged point holds
+// its position in cell units (cell (i, j, k) at (i, j, k)) and its weight pre-multiplied by
+// C / h^3, so that with s = |offset| in cells
+//     G(R) * w = w' e^{-alpha h s} (1 - e^{-(beta - alpha) h s}) / s^3.
+// A warp owns 32 of the leaf's targets (one per lane) and a share of the staged points,
+// read with broadcast loads.  Small leaves (one or two chunks of 32 targets) split the points
+// across 4 or 2 warps; every target's sum is added once per warp.  TAYLOR = false when
+// (beta - alpha) h >= 0.5: then 1 - e^{-x} needs no series at any distance >= 1 cell.
+constexpr int P2P_WARPS = 4;
+constexpr int P2P_CAP = 1536;        // staged points per round (24 KiB)
+constexpr int P2P_MAXU = 128;        // list entries handled per pass over the box table
+
+struct P2PConst {
+    float k1, k2;        // alpha h log2(e), (beta - alpha) h log2(e)
+    float bma_h;         // (beta - alpha) h
+    float wself;         // G_self h^3 / C  (self term, in the scaled weight units)
+};
+
+template <bool TAYLOR>
+__device__ __forceinline__ float p2p_sum(const float4 *__restrict__ pts, int lo, int hi, float tx, float ty,
+                                         float tz, const P2PConst &K) {
+    float a = 0.f;
+#pragma unroll 4
+    for (int j = lo; j < hi; ++j) {
+        const float4 sp = pts[j];
+        const float dx = tx - sp.x, dy = ty - sp.y, dz = tz - sp.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rs = rsqrt_approx(fmaxf(d2, 1e-12f));
+        const float sdist = d2 * rs;
+        const float e1 = ex2_approx(-K.k1 * sdist);
+        const float em = TAYLOR ? one_minus_exp_neg(K.bma_h * sdist, K.k2 * sdist) : 1.f - ex2_approx(-K.k2 * sdist);
+        const float g = d2 > 0.f ? e1 * em * (rs * rs * rs) : K.wself;
+        a = fmaf(g, sp.w, a);
+    }
+    return a;
+}
+
+template <bool TAYLOR>
+__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
+                                                         const int *__restrict__ count, float *__restrict__ out,
+                                                         P2PConst K) {
+    __shared__ float4 stage[P2P_CAP];
+    __shared__ int ub[P2P_MAXU], un[P2P_MAXU], uo[P2P_MAXU + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cnt = *count;
+    const TreeDev &T = F.T;
+    const float h = F.kp.h;
+    const float wsc = F.wscale * F.kp.C / (h * h * h);          // source weight -> scaled weight
+    const float usc = F.kp.C / (h * h * h);                     // upward weight -> scaled weight
+    const int n = F.O.n, np = F.O.npad;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int b = list[i];
+        const int tb = T.b_tb[b], te = T.b_te[b];
+        const int nch = (te - tb + 31) >> 5;
+        const int G = nch >= P2P_WARPS ? 1 : P2P_WARPS / nch;     // warps sharing a target chunk
+        const int groups = P2P_WARPS / G;
+        const int k = warp % G;
+        float acc[2] = {0.f, 0.f};        // the first two chunks of this warp; further chunks flush per round
+        // pass 0: U list (point sources); pass 1: W list (Chebyshev nodes of the W boxes)
+        const int passes = F.O.method == FAR_CHEB ? 2 : 1;     // the surface form keeps M2P in k_leaf
+        for (int pass = 0; pass < passes; ++pass) {
+            const int l0 = pass == 0 ? F.L.u_off[b] : F.L.w_off[b];
+            const int l1 = pass == 0 ? F.L.u_off[b + 1] : F.L.w_off[b + 1];
+            for (int ub0 = l0; ub0 < l1; ub0 += P2P_MAXU) {
+                const int nu = min(P2P_MAXU, l1 - ub0);
+                __syncthreads();
+                if (tid < nu) {
+                    const int A = pass == 0 ? F.L.u_src[ub0 + tid] : F.L.w_src[ub0 + tid];
+                    if (pass == 0) {
+                        const int sb = T.b_sb[A];
+                        ub[tid] = sb;
+                        un[tid] = T.b_se[A] - sb;
+                    } else {
+                        ub[tid] = A;
+                        un[tid] = n;
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int o = 0;
+                    for (int j = 0; j < nu; ++j) {
+                        uo[j] = o;
+                        o += un[j];
+                    }
+                    uo[nu] = o;
+                }
+                __syncthreads();
+                const int total = uo[nu];
+                for (int r0 = 0; r0 < total; r0 += P2P_CAP) {
+                    const int rn = min(P2P_CAP, total - r0);
+                    __syncthreads();
+                    for (int j = 0; j < nu; ++j) {
+                        const int lo = max(uo[j], r0), hi = min(uo[j + 1], r0 + rn);
+                        if (lo >= hi) continue;
+                        if (pass == 0) {
+                            for (int s = lo + tid; s < hi; s += blockDim.x) {
+                                const int si = ub[j] + (s - uo[j]);
+                                const uint32_t pc = __ldg(F.src_pc + si);
+                                stage[s - r0] = make_float4((float)pc_i(pc), (float)pc_j(pc), (float)pc_k(pc),
+                                                            __ldg(F.src_q + si) * wsc);
+                            }
+                        } else {
+                            const int A = ub[j];
+                            const int asz = 1 << (F.D - T.b_level[A]);
+                            uint32_t ax, ay, az;
+                            demorton3(T.b_key[A], ax, ay, az);
+                            const float half = 0.5f * (float)asz;
+                            const float cx = (float)ax * asz + half - 0.5f, cy = (float)ay * asz + half - 0.5f,
+                                        cz = (float)az * asz + half - 0.5f;
+                            for (int s = lo + tid; s < hi; s += blockDim.x) {
+                                const int m = s - uo[j];
+                                stage[s - r0] = make_float4(cx + half * F.O.nodes[4 * m], cy + half * F.O.nodes[4 * m + 1],
+                                                            cz + half * F.O.nodes[4 * m + 2],
+                                                            F.ueq[(size_t)A * np + m] * usc);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    const int per = (rn + G - 1) / G;
+                    const int s_lo = k * per, s_hi = min(rn, s_lo + per);
+                    int slot = 0;
+                    for (int c = warp / G; c < nch; c += groups, ++slot) {
+                        const int t = tb + c * 32 + lane;
+                        const uint32_t tp = t < te ? F.trg_pc[t] : 0u;
+                        const float a = p2p_sum<TAYLOR>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
+                                                        (float)pc_k(tp), K);
+                        if (slot < 2) acc[slot] += a;
+                        else if (t < te)
+                            atomicAdd(out + (int64_t)pc_i(tp) +
+                                          (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
+                                      a);
+                    }
+                }
+            }
+        }
+        int slot = 0;
+        for (int c = warp / G; c < nch && slot < 2; c += groups, ++slot) {
+            const int t = tb + c * 32 + lane;
+            if (t >= te) continue;
+            const uint32_t tp = F.trg_pc[t];
+            atomicAdd(out + (int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
+                      acc[slot]);
+        }
+    }
+}
+
+void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st) {
+    if (nboxes <= 0) return;
+    const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
+    const float log2e = 1.4426950408889634f;
+    P2PConst K;
+    const float h = F.kp.h;
+    K.k1 = F.kp.a2 * h;                       // a2 = alpha log2(e)
+    K.k2 = F.kp.b2 * h;                       // b2 = (beta - alpha) log2(e)
+    K.bma_h = F.kp.bma * h;
+    K.wself = F.self_mode ? F.kp.gself * h * h * h / F.kp.C : 0.f;
+    (void)log2e;
+    // the self weight multiplies the scaled weight w' = w C / h^3: g_self w = (g_self h^3 / C) w'
+    if (K.bma_h >= 0.5f)
+        k_p2p<false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    else
+        k_p2p<true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {

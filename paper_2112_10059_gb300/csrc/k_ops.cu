@@ -332,8 +332,28 @@ size_t ops_etab_floats(int method, int npad, int D, int Lmax) {
     return s;
 }
 
+size_t ops_l2p_img_elems(int D, int Lmax) {
+    size_t s = 0;
+    for (int l = 2; l <= Lmax && l < 16; ++l) {
+        int e = edge_of(D, l);
+        if (e <= ETAB_MAX_EDGE) s += l2p_image_elems(e);
+    }
+    return s;
+}
+
 void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
     for (int l = 0; l < 16; ++l) O.e_off[l] = -1;
+    for (int l = 0; l < 16; ++l) O.l2p_off[l] = -1;
+    if (O.method == FAR_CHEB && O.l2p_img) {
+        long long off = 0;
+        for (int l = 2; l <= Lmax && l < 16; ++l) {
+            int e = edge_of(D, l);
+            if (e <= ETAB_MAX_EDGE) {
+                O.l2p_off[l] = off;
+                off += (long long)l2p_image_elems(e);
+            }
+        }
+    }
     O.uc64 = O.dc64 = nullptr;
     O.pinv_stride = 0;
     long long off = 0;
@@ -547,6 +567,11 @@ int ops_build(const OpsBuildArgs &A, cudaStream_t st) {
         if (O.m2l_img && tc_supported(O)) {
             make_images(O.m2l_t, O.npad, (A.Lmax + 1) * NSLOT, O.m2l_img, st);
             make_images(O.l2l_t, O.npad, (A.Lmax + 1) * 8, O.l2l_img, st);
+        }
+        if (O.l2p_img && O.method == FAR_CHEB && tc_supported(O)) {
+            for (int l = 2; l <= A.Lmax && l < 16; ++l)
+                if (O.e_off[l] >= 0 && O.l2p_off[l] >= 0)
+                    make_l2p_images(O.e_tab + O.e_off[l], edge_of(A.D, l), O.n, O.l2p_img + O.l2p_off[l], st);
         }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -28,10 +28,40 @@ __device__ __forceinline__ float ord2f(unsigned u) {
 __global__ void k_grid_max(const float *__restrict__ q, const float *__restrict__ e, int64_t n,
                            unsigned *__restrict__ out /* [2] ordered-uint maxima */) {
     float mq = -INFINITY, me = -INFINITY;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        if (q) { float v = __ldg(q + i); if (v == v) mq = fmaxf(mq, v); }
-        if (e) { float v = __ldg(e + i); if (v == v) me = fmaxf(me, v); }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // aligned float4 body (cudaMalloc'd inputs), four loads in flight per array and thread
+    const int64_t n4 = ((reinterpret_cast<uintptr_t>(q ? q : e) & 15) == 0 &&
+                        (!q || !e || (reinterpret_cast<uintptr_t>(e) & 15) == 0)) ? n / 4 : 0;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q), *e4 = reinterpret_cast<const float4 *>(e);
+    auto fold = [](float m, float4 v) {
+        if (v.x == v.x) m = fmaxf(m, v.x);
+        if (v.y == v.y) m = fmaxf(m, v.y);
+        if (v.z == v.z) m = fmaxf(m, v.z);
+        if (v.w == v.w) m = fmaxf(m, v.w);
+        return m;
+    };
+    int64_t i = tid;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (q) a[u] = __ldg(q4 + i + u * stride);
+            if (e) b[u] = __ldg(e4 + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (q) mq = fold(mq, a[u]);
+            if (e) me = fold(me, b[u]);
+        }
+    }
+    for (; i < n4; i += stride) {
+        if (q) mq = fold(mq, __ldg(q4 + i));
+        if (e) me = fold(me, __ldg(e4 + i));
+    }
+    for (int64_t j = 4 * n4 + tid; j < n; j += stride) {
+        if (q) { float v = __ldg(q + j); if (v == v) mq = fmaxf(mq, v); }
+        if (e) { float v = __ldg(e + j); if (v == v) me = fmaxf(me, v); }
     }
     for (int o = 16; o > 0; o >>= 1) {
         mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
@@ -100,7 +130,7 @@ __global__ void __launch_bounds__(512) k_select_brick(
         int *__restrict__ cnt_s, int *__restrict__ cnt_t,            // [nbricks] (count pass)
         const int *__restrict__ off_s, const int *__restrict__ off_t,// [nbricks] (emit pass)
         uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc, float *__restrict__ src_q,
-        uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc) {
+        uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc, uint8_t *__restrict__ tmask) {
     const int b = r.brick_edge_log2;
     const int ncell = 1 << (3 * b);
     const uint32_t brick = blockIdx.x;
@@ -123,6 +153,9 @@ __global__ void __launch_bounds__(512) k_select_brick(
         int bits = sel_bits(r, q, e, mask, x0 + lx, y0 + ly, z0 + lz, thr_q, thr_e, qpos, qv);
         s_bits[lk] = (uint8_t)bits;
         s_q[lk] = qv;
+        if (EMIT && tmask && x0 + lx < r.nx && y0 + ly < r.ny && z0 + lz < r.nz)
+            tmask[(int64_t)(x0 + lx) + (int64_t)r.nx * ((int64_t)(y0 + ly) + (int64_t)r.ny * (z0 + lz))] =
+                (uint8_t)(bits >> 1);
     }
     __syncthreads();
     int my_bits[8];
@@ -243,7 +276,8 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         SelRule r, const float *__restrict__ q, const float *__restrict__ e, const uint8_t *__restrict__ mask,
         const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
         int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
-        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc) {
+        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
+        uint8_t *__restrict__ tmask) {
     __shared__ int s_brick;
     __shared__ float s_thr_q, s_thr_e;
     __shared__ int s_qpos;
@@ -271,22 +305,39 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     const int x0 = bx << b, y0 = by << b, z0 = bz << b;
     const float thr_q = s_thr_q, thr_e = s_thr_e;
     const bool qpos = s_qpos;
-    // stage in linear (x fastest) order: coalesced rows, byte-wise conflict-free stores
-    for (int c = tid; c < ncell; c += blockDim.x) {
-        int lx = c & (edge - 1), ly = (c >> b) & (edge - 1), lz = c >> (2 * b);
-        int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-        int bits = 0;
-        float qv = 0.f;
-        if (x < r.nx && y < r.ny && z < r.nz) {
-            uint32_t lin = (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z);
-            qv = __ldg(q + lin);
-            if (r.src_all || (qpos && qv >= thr_q)) bits |= 1;
-            if (r.trg_mode == 0) bits |= 2;
-            else if (r.trg_mode == 1) { if (__ldg(e + lin) >= thr_e) bits |= 2; }
-            else if (__ldg(mask + lin)) bits |= 2;
+    // stage in linear (x fastest) order: coalesced rows, byte-wise conflict-free stores.
+    // All loads of a thread are issued before any is used (up to 8 cells per thread).
+    {
+        constexpr int U = 8;
+        float qv[U], ev[U];
+        uint32_t lin[U];
+        bool in[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = tid + u * (int)blockDim.x;
+            const int lx = c & (edge - 1), ly = (c >> b) & (edge - 1), lz = c >> (2 * b);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            in[u] = c < ncell && x < r.nx && y < r.ny && z < r.nz;
+            lin[u] = in[u] ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
+            qv[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
+            ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
+            if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
         }
-        s_bits[c] = (uint8_t)bits;
-        s_q[c] = qv;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = tid + u * (int)blockDim.x;
+            if (c >= ncell) break;
+            int bits = 0;
+            if (in[u]) {
+                if (r.src_all || (qpos && qv[u] >= thr_q)) bits |= 1;
+                if (r.trg_mode == 0) bits |= 2;
+                else if (r.trg_mode == 1) { if (ev[u] >= thr_e) bits |= 2; }
+                else if (ev[u] != 0.f) bits |= 2;
+                if (tmask) tmask[lin[u]] = (uint8_t)(bits >> 1);
+            }
+            s_bits[c] = (uint8_t)bits;
+            s_q[c] = qv[u];
+        }
     }
     __syncthreads();
     int my_bits[8];
@@ -331,38 +382,60 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __syncthreads();
     const int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
     const int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
-    if (tid == 0) {
+    // decoupled look-back by warp 0: 32 predecessor states per round, the nearest inclusive
+    // one ends the walk
+    if (w == 0) {
         const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
         unsigned pre_s = 0, pre_t = 0;
         if (brick == 0) {
-            atomicExch(state + brick, pack_state(2u, agg_s, agg_t));
+            if (lane == 0) atomicExch(state + brick, pack_state(2u, agg_s, agg_t));
         } else {
-            atomicExch(state + brick, pack_state(1u, agg_s, agg_t));
+            if (lane == 0) atomicExch(state + brick, pack_state(1u, agg_s, agg_t));
             bool failed = false;
-            for (int j = brick - 1; j >= 0; --j) {
+            for (int j = brick - 1; j >= 0; j -= 32) {
+                const int idx = j - lane;
                 unsigned long long v = 0;
-                unsigned stt = 0;
+                unsigned stt = 2;                  // before brick 0: an inclusive zero
+                // every lane runs the same number of polls (the exit test is warp-uniform)
                 for (unsigned k = 0; k < LOOKBACK_LIMIT; ++k) {
-                    v = *((volatile unsigned long long *)(state + j));
-                    stt = (unsigned)(v >> 62);
-                    if (stt != 0) break;
+                    if (idx >= 0) {
+                        v = *((volatile unsigned long long *)(state + idx));
+                        stt = (unsigned)(v >> 62);
+                    }
+                    if (__all_sync(0xffffffffu, stt != 0)) break;
                     __nanosleep(64);
                 }
-                if (stt == 0) { failed = true; break; }
-                pre_s += (unsigned)((v >> 31) & 0x7FFFFFFFu);
-                pre_t += (unsigned)(v & 0x7FFFFFFFu);
-                if (stt == 2) break;
+                if (!__all_sync(0xffffffffu, stt != 0)) {
+                    failed = true;
+                    break;
+                }
+                const unsigned incl = __ballot_sync(0xffffffffu, stt == 2u);
+                const int stop = incl ? __ffs(incl) - 1 : 31;    // nearest inclusive predecessor
+                unsigned cs = (lane <= stop && idx >= 0) ? (unsigned)((v >> 31) & 0x7FFFFFFFu) : 0u;
+                unsigned ct = (lane <= stop && idx >= 0) ? (unsigned)(v & 0x7FFFFFFFu) : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                    ct += __shfl_xor_sync(0xffffffffu, ct, o);
+                }
+                pre_s += cs;
+                pre_t += ct;
+                if (incl) break;
             }
-            if (failed) atomicOr(totals + 2, 1);
-            atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
+            if (lane == 0) {
+                if (failed) atomicOr(totals + 2, 1);
+                atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
+            }
         }
-        s_pre_s = pre_s;
-        s_pre_t = pre_t;
-        if (brick == nbr - 1) {
-            __threadfence();
-            bool bad = atomicOr(totals + 2, 0) != 0;
-            totals[0] = bad ? -1 : (int)(pre_s + agg_s);
-            totals[1] = bad ? -1 : (int)(pre_t + agg_t);
+        if (lane == 0) {
+            s_pre_s = pre_s;
+            s_pre_t = pre_t;
+            if (brick == nbr - 1) {
+                __threadfence();
+                bool bad = atomicOr(totals + 2, 0) != 0;
+                totals[0] = bad ? -1 : (int)(pre_s + agg_s);
+                totals[1] = bad ? -1 : (int)(pre_t + agg_t);
+            }
         }
     }
     __syncthreads();
@@ -401,16 +474,19 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     r.e_app = A.e_app;
     int64_t n = (int64_t)A.nx * A.ny * A.nz;
     cudaMemsetAsync(A.maxes, 0, 2 * sizeof(unsigned), st);
-    int gm = (int)((n + 255) / 256);
-    if (gm > 152 * 16) gm = 152 * 16;
-    k_grid_max<<<gm, 256, 0, st>>>(r.src_all ? nullptr : A.q, r.trg_mode == 1 ? A.emag : nullptr, n, A.maxes);
+    int gm = (int)((n / 4 + 255) / 256);
+    if (gm > 152 * 8) gm = 152 * 8;
+    if (gm < 1) gm = 1;
+    const float *gq = r.src_all ? nullptr : A.q, *ge = r.trg_mode == 1 ? A.emag : nullptr;
+    if (gq || ge) k_grid_max<<<gm, 256, 0, st>>>(gq, ge, n, A.maxes);
     if (A.two_pass) {
         k_select_brick<false><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
-                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr);
         k_scan2<<<1, 1024, 0, st>>>(A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
         k_select_brick<true><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
                                                   A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
-                                                  A.trg_key, A.trg_pc);
+                                                  A.trg_key, A.trg_pc, A.tmask);
         return cudaGetLastError() == cudaSuccess ? 0 : -1;
     }
     // one pass: the look-back states live in cnt_s .. cnt_t (2 ints per brick), the ticket in off_s[0]
@@ -420,7 +496,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
     k_select_onepass<<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
-                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc);
+                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

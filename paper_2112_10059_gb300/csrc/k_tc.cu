@@ -83,23 +83,50 @@ __device__ __forceinline__ TcSmem carve(uint8_t *raw) {
 }
 
 // Gather the FP32 state rows col_src[j] (row stride np) into the BF16 hi / lo B tiles.
-__device__ __forceinline__ void gather_split(const TcSmem &s, const float *__restrict__ state, int np) {
-    for (int e = threadIdx.x; e < TCN * (TCK / 4); e += blockDim.x) {
-        int j = e / (TCK / 4), q = e % (TCK / 4);
-        int src = s.col_src[j];
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (src >= 0 && 4 * q < np) v = *reinterpret_cast<const float4 *>(state + (size_t)src * np + 4 * q);
-        uint16_t h0, l0, h1, l1, h2, l2, h3, l3;
-        tc::split_bf16(v.x, h0, l0);
-        tc::split_bf16(v.y, h1, l1);
-        tc::split_bf16(v.z, h2, l2);
-        tc::split_bf16(v.w, h3, l3);
-        uint32_t off = tc::sw128_offset(j, 4 * q, TCN);
-        uint2 hv = make_uint2((uint32_t)h0 | ((uint32_t)h1 << 16), (uint32_t)h2 | ((uint32_t)h3 << 16));
-        uint2 lv = make_uint2((uint32_t)l0 | ((uint32_t)l1 << 16), (uint32_t)l2 | ((uint32_t)l3 << 16));
-        *reinterpret_cast<uint2 *>(s.b_hi + off) = hv;
-        *reinterpret_cast<uint2 *>(s.b_lo + off) = lv;
+// Split 4 FP32 values into BF16 hi / lo and store them at element (row, k0..k0+3) of two
+// K-major SW128 tiles with `rows` rows.
+__device__ __forceinline__ void put_split4(uint8_t *hi, uint8_t *lo, int row, int k0, int rows, const float4 &v) {
+    uint16_t h0, l0, h1, l1, h2, l2, h3, l3;
+    tc::split_bf16(v.x, h0, l0);
+    tc::split_bf16(v.y, h1, l1);
+    tc::split_bf16(v.z, h2, l2);
+    tc::split_bf16(v.w, h3, l3);
+    const uint32_t off = tc::sw128_offset(row, k0, rows);
+    *reinterpret_cast<uint2 *>(hi + off) =
+        make_uint2((uint32_t)h0 | ((uint32_t)h1 << 16), (uint32_t)h2 | ((uint32_t)h3 << 16));
+    *reinterpret_cast<uint2 *>(lo + off) =
+        make_uint2((uint32_t)l0 | ((uint32_t)l1 << 16), (uint32_t)l2 | ((uint32_t)l3 << 16));
+}
+
+// Gather `rows` FP32 state rows (index list `idx`, -1 = zero row; row stride np) into BF16
+// hi / lo K-major SW128 tiles.  Loads are issued eight at a time per thread before any is
+// converted, so a thread has eight row segments in flight instead of one.
+__device__ __forceinline__ void gather_rows_split(uint8_t *hi, uint8_t *lo, const int *idx, int rows,
+                                                  const float *__restrict__ state, int np) {
+    constexpr int Q = TCK / 4;   // float4 per row
+    const int total = rows * Q;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < total) {
+                const int j = e / Q, q = e % Q;
+                const int src = idx[j];
+                if (src >= 0 && 4 * q < np) v[u] = __ldg(reinterpret_cast<const float4 *>(state + (size_t)src * np) + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < total) put_split4(hi, lo, e / Q, 4 * (e % Q), rows, v[u]);
+        }
     }
+}
+
+__device__ __forceinline__ void gather_split(const TcSmem &s, const float *__restrict__ state, int np) {
+    gather_rows_split(s.b_hi, s.b_lo, s.col_src, TCN, state, np);
 }
 
 // Issue the 3 x 8 MMAs of one tile (thread 0 only).
@@ -403,6 +430,173 @@ void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_
                                                                      err);
 }
 
+// ---------------------------------------------------------------- L2P on the tensor cores
+// S(cell c of leaf B) = sum_k E_l[c][k] d_B[k] for every leaf of one level, as
+//     D[box][cell] = sum_k d[box][k] E[cell][k]    (M = 128 boxes, N = up to 64 cells, K = 128)
+// with BF16 hi / lo splits of both operands (3 products).  The table of a level is stored
+// as images of N cells each (lexicographic order inside the box, x fastest), ready for a
+// bulk copy into shared memory.  One CTA gathers 128 boxes' d once and loops over the
+// level's cell tiles; thread r (TMEM lane r) writes box r's cells.  A box whose every cell
+// is a target is written whole; a partly selected box writes where the target mask is set.
+constexpr uint32_t L2P_A = TCM * TCK * 2;               // 32 KiB: 128 boxes x 128 coefficients
+constexpr uint32_t L2P_B = 64 * TCK * 2;                // 16 KiB: up to 64 cells x 128
+constexpr uint32_t L2P_SMEM = 1024 + 2 * L2P_A + 2 * L2P_B + 64 + 2 * TCM * 4;
+
+__global__ void k_l2p_image(const float *__restrict__ etab, int e, int n, int N, int ntiles, uint16_t *img) {
+    const int rows = e * e * e;
+    const size_t total = (size_t)ntiles * N * TCK;
+    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int t = (int)(idx / ((size_t)N * TCK));
+    const int rem = (int)(idx % ((size_t)N * TCK));
+    const int j = rem / TCK, k = rem % TCK;
+    const int c = t * N + j;
+    float v = 0.f;
+    if (c < rows && k < n) {
+        const uint32_t lx = c % e, ly = (c / e) % e, lz = c / (e * e);
+        v = etab[(size_t)k * rows + morton3(lx, ly, lz)];
+    }
+    uint16_t hi, lo;
+    tc::split_bf16(v, hi, lo);
+    uint16_t *base = img + (size_t)t * 2 * N * TCK;
+    const uint32_t off = tc::sw128_offset(j, k, N) / 2;
+    base[off] = hi;
+    base[(size_t)N * TCK + off] = lo;
+}
+
+__host__ __device__ int l2p_tile_n(int e) {
+    const int rows = e * e * e;
+    const int r16 = (rows + 15) / 16 * 16;
+    return r16 < 64 ? r16 : 64;
+}
+
+void make_l2p_images(const float *etab, int e, int n, uint16_t *img, cudaStream_t st) {
+    const int N = l2p_tile_n(e), ntiles = (e * e * e + N - 1) / N;
+    const size_t total = (size_t)ntiles * N * TCK;
+    k_l2p_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(etab, e, n, N, ntiles, img);
+}
+
+size_t l2p_image_elems(int e) {
+    const int N = l2p_tile_n(e), ntiles = (e * e * e + N - 1) / N;
+    return (size_t)ntiles * 2 * N * TCK;
+}
+
+__global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_begin, int box_count,
+                                                const uint16_t *__restrict__ img, float *__restrict__ out,
+                                                int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *a_hi = base, *a_lo = base + L2P_A, *b_hi = base + 2 * L2P_A, *b_lo = b_hi + L2P_B;
+    uint8_t *tail = base + 2 * L2P_A + 2 * L2P_B;
+    uint64_t *bar_b = reinterpret_cast<uint64_t *>(tail);
+    uint64_t *bar_mma = bar_b + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tail + 16);
+    int *ok_s = reinterpret_cast<int *>(tail + 20);
+    int *sbox = reinterpret_cast<int *>(tail + 64);
+    int *sfull = sbox + TCM;
+    const TreeDev &T = F.T;
+    const int r = threadIdx.x, warp = r >> 5;
+    const int e = 1 << (F.D - level), rows = e * e * e;
+    const int N = l2p_tile_n(e), ntiles = (rows + N - 1) / N;
+    const int i = blockIdx.x * TCM + r;
+    const int b = box_begin + i;
+    bool ok = false;
+    if (i < box_count) ok = T.b_leaf[b] && T.b_te[b] > T.b_tb[b];
+    sbox[r] = ok ? b : -1;
+    sfull[r] = ok && (T.b_te[b] - T.b_tb[b] == rows);
+    if (!__syncthreads_or(ok)) return;
+    if (r < 32) {
+        tc::tmem_alloc(tc::smem_u32(tslot), 64);
+        tc::tmem_relinquish();
+    }
+    if (r == 0) {
+        tc::mbar_init(tc::smem_u32(bar_b), 1);
+        tc::mbar_init(tc::smem_u32(bar_mma), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // A: the 128 boxes' d (FP32 [npad]) split into BF16 hi / lo, K-major SW128
+    gather_rows_split(a_hi, a_lo, sbox, TCM, F.dchk, F.O.npad);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int bb = sbox[r];
+    const bool full = sfull[r] != 0;
+    int bx = 0, by = 0, bz = 0;
+    if (bb >= 0) {
+        uint32_t ux, uy, uz;
+        demorton3(T.b_key[bb], ux, uy, uz);
+        bx = (int)ux * e; by = (int)uy * e; bz = (int)uz * e;
+    }
+    const uint32_t idesc = tc::idesc_bf16_f32(TCM, N);
+    const bool vec4 = full && (e % 4) == 0 && (F.nx % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    const uint32_t sa_hi = tc::smem_u32(a_hi), sa_lo = tc::smem_u32(a_lo);
+    const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = tc::smem_u32(b_lo);
+    const uint32_t bbytes = (uint32_t)N * TCK * 2;
+    for (int t = 0; t < ntiles; ++t) {
+        if (r == 0) {
+            const uint16_t *src = img + (size_t)t * 2 * N * TCK;
+            tc::mbar_expect_tx(tc::smem_u32(bar_b), 2 * bbytes);
+            tc::bulk_g2s(sb_hi, src, bbytes, tc::smem_u32(bar_b));
+            tc::bulk_g2s(sb_lo, src + (size_t)N * TCK, bbytes, tc::smem_u32(bar_b));
+            int good = tc::mbar_wait_bounded(tc::smem_u32(bar_b), t & 1, WAIT_LIMIT);
+            if (good) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int ks = 0; ks < TCK / 16; ++ks) {
+                    const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+                    const uint32_t bo = tc::sw128_offset(0, 16 * ks, N);
+                    tc::mma_bf16(tmem, tc::sdesc_sw128(sa_hi + ao), tc::sdesc_sw128(sb_hi + bo), idesc, ks > 0);
+                    tc::mma_bf16(tmem, tc::sdesc_sw128(sa_hi + ao), tc::sdesc_sw128(sb_lo + bo), idesc, 1);
+                    tc::mma_bf16(tmem, tc::sdesc_sw128(sa_lo + ao), tc::sdesc_sw128(sb_hi + bo), idesc, 1);
+                }
+                tc::mma_commit(tc::smem_u32(bar_mma));
+                good = tc::mbar_wait_bounded(tc::smem_u32(bar_mma), t & 1, WAIT_LIMIT);
+                if (!good) {
+                    atomicOr(err, 8);
+                    tc::mbar_wait_bounded(tc::smem_u32(bar_mma), t & 1, WAIT_LIMIT);
+                }
+            } else {
+                atomicOr(err, 4);
+                tc::mbar_wait_bounded(tc::smem_u32(bar_b), t & 1, WAIT_LIMIT);
+            }
+            *ok_s = good;
+        }
+        __syncthreads();
+        if (!*ok_s) break;
+        tc::fence_after_sync();
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (bb < 0) continue;
+            if (vec4) {   // whole box, rows of 4k cells: one 16-byte store per 4 cells of a row
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const int c = t * N + c0 + j;
+                    if (c >= rows) break;
+                    const int x = bx + c % e, y = by + (c / e) % e, z = bz + c / (e * e);
+                    const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                    *reinterpret_cast<float4 *>(out + o) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                continue;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = t * N + c0 + j;
+                if (c >= rows) break;
+                const int x = bx + c % e, y = by + (c / e) % e, z = bz + c / (e * e);
+                if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
+                const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                if (full || F.tmask[o]) out[o] = v[j];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (r < 32) tc::tmem_dealloc(tmem, 64);
+}
+
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
 
 // Opt in to the dynamic shared memory of the tensor-core kernels (host-side, once;
@@ -413,10 +607,19 @@ void tc_init_attributes() {
     cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
+    cudaFuncSetAttribute(k_l2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2P_SMEM);
     done = true;
 }
 
 size_t tc_image_elems(int count) { return (size_t)count * 2 * (A_BYTES / 2); }
+
+void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, int *err,
+                      cudaStream_t st) {
+    if (box_count <= 0 || level < 2 || F.O.l2p_off[level] < 0) return;
+    tc_init_attributes();
+    k_l2p_tc<<<(box_count + TCM - 1) / TCM, 128, L2P_SMEM, st>>>(F, level, box_begin, box_count,
+                                                                 F.O.l2p_img + F.O.l2p_off[level], out, err);
+}
 
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st) {
     if (nV <= 0) return;

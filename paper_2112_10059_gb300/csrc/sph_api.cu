@@ -78,6 +78,9 @@ struct sph_ctx {
     bool tc_used = false;             // this eval ran the tensor-core translations
     bool l2l_eight = true;            // tensor-core L2L: all 8 children per CTA (else one child per CTA)
     int select_two_pass = 0;          // 1: two-pass selection instead of the one-pass look-back
+    bool p2p_in_leaf = false;         // near field inside the leaf kernel (reference form)
+    bool l2p_simt = false;            // FP32 SIMT L2P even when the tensor-core images exist
+    bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -86,7 +89,9 @@ struct sph_ctx {
     DevBuf b_ueq, b_dchk;
     DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf b_err;                // device error flags of the tensor-core tiles
-    DevBuf b_work;               // compact work lists: sources per level, leaves for the leaf kernel
+    DevBuf b_work;               // compact work lists: sources per level, leaves for the leaf and P2P kernels
+    DevBuf b_tmask;              // [ncell] 1 at targets (written by the selection)
+    DevBuf o_l2pimg;             // BF16 images of the L2P tables (tensor-core L2P)
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
     // operator cache key
@@ -202,6 +207,7 @@ int select_queue(sph_ctx *c) {
     ENS(c->b_sq, ncell * sizeof(float));
     ENS(c->b_tkey, ncell * sizeof(uint32_t));
     ENS(c->b_tpc, ncell * sizeof(uint32_t));
+    ENS(c->b_tmask, ncell);
     SelectArgs A;
     A.nx = c->nx; A.ny = c->ny; A.nz = c->nz; A.D = D; A.brick_log2 = b;
     A.q = c->q; A.emag = c->emag; A.mask = c->mask;
@@ -213,6 +219,7 @@ int select_queue(sph_ctx *c) {
     A.totals = P<int>(c->b_tot);
     A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
     A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
+    A.tmask = P<uint8_t>(c->b_tmask);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
     c->launches += 2;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -364,6 +371,7 @@ void fill_ops(sph_ctx *c, OpsDev &O, int D, int L, bool bf) {
     const bool img = bf && O.npad == 128;
     O.m2l_img = img ? P<uint16_t>(c->o_m2lbf) : nullptr;
     O.l2l_img = img ? P<uint16_t>(c->o_l2lbf) : nullptr;
+    O.l2p_img = (img && c->far_method == FAR_CHEB) ? P<uint16_t>(c->o_l2pimg) : nullptr;
     O.slot_of_code = P<short>(c->o_slot);
     O.nodes = P<float>(c->o_surf);
     O.cheb_t = P<float>(c->o_cheb);
@@ -390,6 +398,7 @@ int run_ops(sph_ctx *c) {
     if (want_bf && np == 128) {
         ENS(c->o_m2lbf, tc_image_elems((L + 1) * 316) * sizeof(uint16_t));
         ENS(c->o_l2lbf, tc_image_elems((L + 1) * 8) * sizeof(uint16_t));
+        if (c->far_method == FAR_CHEB) ENS(c->o_l2pimg, (ops_l2p_img_elems(c->D, L) + 64) * sizeof(uint16_t));
     }
     ENS(c->o_slot, 343 * sizeof(short));
     ENS(c->o_surf, (size_t)np * 4 * sizeof(float));
@@ -456,7 +465,7 @@ struct PhaseTimer {
 // ------------------------------------------------------------------ FMM passes
 struct PassState {
     FmmDev F;
-    int *w_src = nullptr, *w_leaf = nullptr, *w_cnt = nullptr;
+    int *w_src = nullptr, *w_leaf = nullptr, *w_p2p = nullptr, *w_cnt = nullptr;
     PairsDev Pd;
     int *err = nullptr;
     bool tc = false;
@@ -468,7 +477,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_work, (2 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    ENS(c->b_work, (3 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     const int nV = c->list_tot[1];
     const int nkeys = (c->Lmax + 1) * NSLOT;
     ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1)) * sizeof(int));
@@ -484,13 +493,17 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     F.src_q = P<float>(c->b_sq);
     F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
     F.kp = make_kp(c);
-    F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.self_mode = c->self_mode;
+    F.D = c->D; F.nx = c->nx; F.ny = c->ny; F.nz = c->nz; F.self_mode = c->self_mode;
     F.ueq = P<float>(c->b_ueq); F.dchk = P<float>(c->b_dchk);
     F.alpha = c->alpha; F.beta = c->beta; F.C64 = 1.0 / (4.0 * M_PI * std::log(c->beta / c->alpha));
     F.leaf_l2p_done = (!c->translate_per_box && F.O.method == FAR_CHEB) ? 1 : 0;
+    F.p2p_separate = c->p2p_in_leaf ? 0 : 1;
+    F.l2p_sep = (F.leaf_l2p_done && F.O.method == FAR_CHEB && !c->l2p_simt) ? 1 : 0;
+    F.tmask = P<uint8_t>(c->b_tmask);
     S.w_src = P<int>(c->b_work);
     S.w_leaf = S.w_src + std::max(nb, 1);
-    S.w_cnt = S.w_leaf + std::max(nb, 1);
+    S.w_p2p = S.w_leaf + std::max(nb, 1);
+    S.w_cnt = S.w_p2p + std::max(nb, 1);
     int *pb = P<int>(c->b_pairs);
     PairsDev &Pd = S.Pd;
     Pd.nkeys = nkeys;
@@ -501,6 +514,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
     tc_init_attributes();
+    fmm_init_attributes();
     return SPH_OK;
 }
 
@@ -511,7 +525,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
     CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
-    fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, c->stream);
+    fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 33, c->stream);
     c->launches += nb > 0;
     if (tm) tm->mark_at(3, c->stream);
     for (int l = c->Lmax; l >= 2; --l) {
@@ -564,16 +578,28 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     }
     if (tm) tm->mark_at(7, c->stream);
     if (F.leaf_l2p_done) {
+        const bool l2p_tc = S.tc && F.O.l2p_img != nullptr && !c->l2p_simt;
+        if (l2p_tc) CK(cudaMemsetAsync(S.err + 1, 0, sizeof(int), c->stream));
         for (int l = 2; l <= c->Lmax; ++l) {
             if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
-                fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                if (l2p_tc) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
+                else fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                ++c->launches;
+            } else if (c->lvl_count[l] > 0 && F.l2p_sep) {
+                fmm_l2p_sep_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
                 ++c->launches;
             }
         }
+        if (l2p_tc) CK(cudaMemcpyAsync(c->pinned + 49, S.err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        c->l2p_tc_used = l2p_tc;
     }
     if (tm) tm->mark_at(8, c->stream);
     fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
     c->launches += nb > 0;
+    if (F.p2p_separate) {
+        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 33, out, c->stream);
+        c->launches += nb > 0;
+    }
     if (tm) tm->mark_at(9, c->stream);
     CK(cudaGetLastError());
     return SPH_OK;
@@ -581,12 +607,11 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
 
 // Surfaces a timeout recorded by the previous eval's tensor-core tiles (read back after its sync).
 int check_previous_tc(sph_ctx *c) {
-    if (c->tc_used && c->pinned[48] != 0) {
-        c->tc_used = false;
-        return fail(c, SPH_ETIMEOUT, "a tensor-core tile of the previous eval gave up waiting (code %d)",
-                    c->pinned[48]);
-    }
+    const int code = (c->tc_used ? c->pinned[48] : 0) | (c->l2p_tc_used ? c->pinned[49] : 0);
     c->tc_used = false;
+    c->l2p_tc_used = false;
+    if (code != 0)
+        return fail(c, SPH_ETIMEOUT, "a tensor-core tile of the previous eval gave up waiting (code %d)", code);
     return SPH_OK;
 }
 
@@ -719,8 +744,9 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     if (r) return r;
     if (stats) {
         CK(cudaStreamSynchronize(c->stream));
-        if (c->tc_used && c->pinned[48] != 0)
-            return fail(c, SPH_ETIMEOUT, "a tensor-core tile gave up waiting (code %d)", c->pinned[48]);
+        if ((c->tc_used && c->pinned[48] != 0) || (c->l2p_tc_used && c->pinned[49] != 0))
+            return fail(c, SPH_ETIMEOUT, "a tensor-core tile gave up waiting (code %d)",
+                        c->pinned[48] | c->pinned[49]);
         fill_stats(c, stats, &tm);
     }
     return SPH_OK;
@@ -772,6 +798,8 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->radii = parent->radii; sub->pinv_eps = parent->pinv_eps;
     sub->translate_per_box = parent->translate_per_box; sub->l2l_eight = parent->l2l_eight;
     sub->select_two_pass = parent->select_two_pass;
+    sub->p2p_in_leaf = parent->p2p_in_leaf;
+    sub->l2p_simt = parent->l2p_simt;
     sub->launches = 0;
     return SPH_OK;
 }
@@ -932,7 +960,7 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
         memset(stats, 0, sizeof *stats);
         for (int i = 0; i < n; ++i) {
             sph_ctx *sub = c->subs[i];
-            if (sub->tc_used && sub->pinned[48] != 0)
+            if ((sub->tc_used && sub->pinned[48] != 0) || (sub->l2p_tc_used && sub->pinned[49] != 0))
                 return fail(c, SPH_ETIMEOUT, "snapshot %d: a tensor-core tile gave up waiting", i);
             stats->n_sources += sub->ns;
             stats->n_targets += sub->nt;
@@ -1107,6 +1135,8 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2L_ONE_CHILD")) c->l2l_eight = atoi(e) == 0;
     if (const char *e = getenv("SPH_SELECT_TWO_PASS")) c->select_two_pass = atoi(e) != 0;
+    if (const char *e = getenv("SPH_P2P_IN_LEAF")) c->p2p_in_leaf = atoi(e) != 0;
+    if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
@@ -1138,7 +1168,8 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
-                     &c->h_s};
+                     &c->h_s, &c->b_tmask, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
+                     &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);
     if (c->pinned) cudaFreeHost(c->pinned);

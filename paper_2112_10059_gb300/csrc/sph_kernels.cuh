@@ -25,6 +25,7 @@ struct SelectArgs {
     int two_pass = 0;                // 1: count pass + scan + emit pass instead of the one-pass kernel
     uint32_t *src_key, *src_pc, *trg_key, *trg_pc;
     float *src_q;
+    uint8_t *tmask = nullptr;        // optional [nx*ny*nz]: 1 where the cell is a target
 };
 int select_launch(const SelectArgs &A, cudaStream_t st);
 
@@ -119,6 +120,8 @@ struct OpsDev {
     float *e_tab;     // L2P tables per level: FAR_SURFACE [edge^3][npad] row-major (cells in linear order);
                       // FAR_CHEB [npad][edge^3] (cells in local Morton order)
     long long e_off[16];          // float offset of level l's table in e_tab, -1 if none
+    uint16_t *l2p_img;            // FAR_CHEB: BF16 hi / lo images of the tables for the tensor-core L2P
+    long long l2p_off[16];        // element offset of level l's images in l2p_img, -1 if none
     const double *uc64, *dc64;    // FAR_SURFACE FP64 UC2E_l / DC2E_l (row-major n x n), + l * pinv_stride
     long long pinv_stride;
     short *slot_of_code;  // [343] -> 0..315 or -1
@@ -136,7 +139,8 @@ struct OpsBuildArgs {
 int ops_build(const OpsBuildArgs &A, cudaStream_t st);
 size_t ops_work_doubles(int method, int n, int Lmax);
 size_t ops_etab_floats(int method, int npad, int D, int Lmax);
-void ops_layout(int D, int Lmax, double *work, OpsDev &O);   // e_off, uc64, dc64, pinv_stride
+void ops_layout(int D, int Lmax, double *work, OpsDev &O);   // e_off, l2p_off, uc64, dc64, pinv_stride
+size_t ops_l2p_img_elems(int D, int Lmax);                  // BF16 elements of every level's L2P images
 
 // ---------------------------------------------------------------- FMM passes
 struct FmmDev {
@@ -146,20 +150,33 @@ struct FmmDev {
     const uint32_t *src_pc, *trg_pc, *trg_key;
     const float *src_q;
     int leaf_l2p_done;   // 1: k_leaf adds near-field terms only where a table L2P already wrote S
+    int p2p_separate;    // 1: the U-list near field runs in k_p2p (after k_leaf), not in k_leaf
+    int l2p_sep;         // 1: leaves without a table get their L2P from k_l2p_sep (before k_leaf)
+    const uint8_t *tmask;   // [nx*ny*nz] 1 at targets (tensor-core L2P of partly selected leaves)
     float wscale;
     KParams kp;
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
-    int D, nx, ny, self_mode;
+    int D, nx, ny, nz, self_mode;
     float *ueq, *dchk;   // [nboxes][PP]: upward / downward check potentials u_B, d_B
 };
 void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
                       cudaStream_t st);
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    cudaStream_t st);
+                    int *p2p_list, int *p2p_cnt, cudaStream_t st);
+// near field over the U lists of the leaves in p2p_list (adds into out)
+void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st);
+// tensor-core L2P (FAR_CHEB, images present): writes S at the targets of the level's leaves
+void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, int *err,
+                      cudaStream_t st);
+__host__ __device__ int l2p_tile_n(int edge);
+void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st);
+void fmm_init_attributes();
+size_t l2p_image_elems(int edge);
+void make_l2p_images(const float *etab, int edge, int n, uint16_t *img, cudaStream_t st);
 void fmm_m2l_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 // V pairs grouped by (level, offset slot): built once per tree, then one M2L launch for all levels.
 struct PairsDev {

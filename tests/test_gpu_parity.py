@@ -174,6 +174,87 @@ def test_fmm_nonpow2_grid_with_mask(sph, ctx):
     _check_fmm(out.cpu().numpy(), ref, T, "nonpow2")
 
 
+def test_nonpow2_grid_with_mask_tensor_cores(sph):
+    """Tensor-core translations and L2P on a grid whose leaf boxes overhang its faces and
+    whose targets are a random subset (partly selected leaves go through the target mask)."""
+    import torch
+    nx, ny, nz = 40, 24, 33
+    h = 0.01
+    X, Y, Z = si._grid(nx, ny, nz, h)
+    q = np.exp(-((X - 0.2) ** 2 + (Y - 0.12) ** 2 + (Z - 0.15) ** 2) / 0.03 ** 2)
+    q = (q * 1e20).astype(np.float32).ravel()
+    mask = (si.uniform01(45, q.size) < 0.3).astype(np.uint8)
+    outs = []
+    for prec in (sph.M2L_F32, sph.M2L_BF16X3):
+        c = sph.Context(0)
+        sph.set_grid(c, nx, ny, nz, h, 150.0)
+        sph.set_sources(c, torch.from_numpy(q).cuda(), 2e-3)
+        sph.set_targets(c, mask=torch.from_numpy(mask).cuda())
+        sph.set_criteria(c, 1e-3, 0, 0, 1, 8, prec)
+        out, _ = sph.eval_sph(c)
+        outs.append(out.cpu().numpy().astype(np.float64))
+        c.close()
+    a, b = oracle.alpha_beta(150.0, 0.035, 2.0)
+    J, T = oracle.select(q, None, mask, 1e-3)
+    ref = oracle.sph(nx, ny, nz, h, a, b, q, 2e-3, J, T)
+    _check_fmm(outs[1], ref, T, "nonpow2 tensor cores")
+    assert oracle.rel_l2(outs[1][T], outs[0][T]) < 3e-5
+
+
+@pytest.mark.parametrize("pi", [1, 2])
+def test_tensor_core_l2p_and_separate_near_field(sph, monkeypatch, pi):
+    """The tensor-core L2P equals the FP32 table L2P to BF16x3 accuracy, and the warp-tiled
+    near-field kernel equals the near field summed inside the leaf kernel (same terms,
+    another order)."""
+    p = _problems()[pi]
+    outs = {}
+    for name, env in (("default", {}), ("l2p_simt", {"SPH_L2P_SIMT": "1"}), ("p2p_in_leaf", {"SPH_P2P_IN_LEAF": "1"})):
+        for k in ("SPH_L2P_SIMT", "SPH_P2P_IN_LEAF"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        outs[name] = out.cpu().numpy().astype(np.float64)
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs["default"][T], outs["p2p_in_leaf"][T]) < 1e-6
+    assert oracle.rel_l2(outs["default"][T], outs["l2p_simt"][T]) < 3e-5
+    others = np.ones(outs["default"].size, bool)
+    others[T] = False
+    assert np.all(outs["default"][others] == 0)
+    _check_fmm(outs["default"], ref, T, p.name)
+
+
+def test_separable_l2p_for_coarse_leaves(sph, monkeypatch):
+    """128^3 with sources only near a streamer head and targets where |E| is large: many
+    targets sit in coarse leaves (edge 32 cells, no interpolation table), evaluated by the
+    tensor-product L2P; equal to the per-target evaluation inside the leaf kernel and within
+    the gate on sampled targets."""
+    p = si.streamer(n=128, box=1.0, chan_len=0.3, i_frac=1e-3, targets_all=True, leaf_size=64, seed=31,
+                    name="s128_coarse")
+    mask = si.random_mask(p.ncell, 2e-3, 32)       # sparse targets: leaves stay coarse
+    outs = {}
+    for name, env in (("default", {}), ("in_leaf", {"SPH_L2P_SIMT": "1"})):
+        monkeypatch.delenv("SPH_L2P_SIMT", raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        c = sph.Context(0)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True, mask=mask)
+        outs[name] = out.cpu().numpy().astype(np.float64)
+        tree = sph.get_tree(c)
+        c.close()
+    lv = tree["level"][tree["leaf"] & (tree["trg_end"] > tree["trg_begin"])]
+    assert (lv <= tree["depth"] - 5).any()          # some leaves have edge >= 32
+    assert oracle.rel_l2(outs["default"], outs["in_leaf"]) < 3e-5
+    J, T = oracle.select(p.q, None, mask, p.i_frac)
+    samp = np.sort(np.random.default_rng(4).choice(T, min(3000, T.size), replace=False))
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+    assert oracle.rel_l2(outs["default"][samp], ref) < REL_L2
+    assert oracle.max_rel(outs["default"][samp], ref, 1e-3) < MAX_REL
+
+
 @pytest.mark.parametrize("pi", [0, 1, 2])
 def test_chebyshev_order_convergence(sph, pi):
     """The far-field error falls steadily with the Chebyshev order (4 -> 7)."""
