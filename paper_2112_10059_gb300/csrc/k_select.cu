@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __shared__ uint8_t s_bits[4096];
     __shared__ float s_q[4096];
     __shared__ int ws[16], wt[16];
-    __shared__ unsigned s_pre_s, s_pre_t;
+    __shared__ unsigned rs[16], rt[16];
+    __shared__ int s_stop;
+    __shared__ uint32_t st_pc[4096];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_brick = (int)atomicAdd(ticket, 1u);
@@ -382,64 +384,75 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __syncthreads();
     const int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
     const int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
-    // decoupled look-back by warp 0: 32 predecessor states per round, the nearest inclusive
-    // one ends the walk
-    if (w == 0) {
-        const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
-        unsigned pre_s = 0, pre_t = 0;
-        if (brick == 0) {
-            if (lane == 0) atomicExch(state + brick, pack_state(2u, agg_s, agg_t));
-        } else {
-            if (lane == 0) atomicExch(state + brick, pack_state(1u, agg_s, agg_t));
-            bool failed = false;
-            for (int j = brick - 1; j >= 0; j -= 32) {
-                const int idx = j - lane;
-                unsigned long long v = 0;
-                unsigned stt = 2;                  // before brick 0: an inclusive zero
-                // every lane runs the same number of polls (the exit test is warp-uniform)
-                for (unsigned k = 0; k < LOOKBACK_LIMIT; ++k) {
-                    if (idx >= 0) {
-                        v = *((volatile unsigned long long *)(state + idx));
-                        stt = (unsigned)(v >> 62);
-                    }
-                    if (__all_sync(0xffffffffu, stt != 0)) break;
-                    __nanosleep(64);
-                }
-                if (!__all_sync(0xffffffffu, stt != 0)) {
-                    failed = true;
-                    break;
-                }
-                const unsigned incl = __ballot_sync(0xffffffffu, stt == 2u);
-                const int stop = incl ? __ffs(incl) - 1 : 31;    // nearest inclusive predecessor
-                unsigned cs = (lane <= stop && idx >= 0) ? (unsigned)((v >> 31) & 0x7FFFFFFFu) : 0u;
-                unsigned ct = (lane <= stop && idx >= 0) ? (unsigned)(v & 0x7FFFFFFFu) : 0u;
+    // decoupled look-back by the whole block: 512 predecessor states per round (every
+    // brick in flight is within a round or two); the nearest inclusive state ends the walk
+    const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
+    if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, agg_s, agg_t));
+    unsigned pre_s = 0, pre_t = 0;
+    bool failed = false;
+    for (int j = brick - 1; j >= 0; j -= (int)blockDim.x) {
+        const int idx = j - tid;
+        unsigned long long v = 0;
+        unsigned stt = 2;                          // before brick 0: an inclusive zero
+        bool ready = false;
+        for (unsigned k = 0; k < LOOKBACK_LIMIT; ++k) {
+            if (idx >= 0) {
+                v = *((volatile unsigned long long *)(state + idx));
+                stt = (unsigned)(v >> 62);
+            }
+            if (__syncthreads_and(stt != 0)) {
+                ready = true;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!ready) {                              // uniform: every thread saw the same vote
+            failed = true;
+            break;
+        }
+        if (tid == 0) s_stop = (int)blockDim.x;
+        __syncthreads();
+        if (stt == 2u) atomicMin(&s_stop, tid);
+        __syncthreads();
+        const int stop = s_stop;
+        unsigned cs = (tid <= stop && idx >= 0) ? (unsigned)((v >> 31) & 0x7FFFFFFFu) : 0u;
+        unsigned ct = (tid <= stop && idx >= 0) ? (unsigned)(v & 0x7FFFFFFFu) : 0u;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    cs += __shfl_xor_sync(0xffffffffu, cs, o);
-                    ct += __shfl_xor_sync(0xffffffffu, ct, o);
-                }
-                pre_s += cs;
-                pre_t += ct;
-                if (incl) break;
-            }
-            if (lane == 0) {
-                if (failed) atomicOr(totals + 2, 1);
-                atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            ct += __shfl_xor_sync(0xffffffffu, ct, o);
         }
         if (lane == 0) {
-            s_pre_s = pre_s;
-            s_pre_t = pre_t;
-            if (brick == nbr - 1) {
-                __threadfence();
-                bool bad = atomicOr(totals + 2, 0) != 0;
-                totals[0] = bad ? -1 : (int)(pre_s + agg_s);
-                totals[1] = bad ? -1 : (int)(pre_t + agg_t);
-            }
+            rs[w] = cs;
+            rt[w] = ct;
+        }
+        __syncthreads();
+        unsigned sum_s = 0, sum_t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sum_s += rs[k];
+            sum_t += rt[k];
+        }
+        pre_s += sum_s;
+        pre_t += sum_t;
+        __syncthreads();                           // rs / rt / s_stop reused by the next round
+        if (stop < (int)blockDim.x) break;
+    }
+    if (tid == 0) {
+        if (brick > 0) {
+            if (failed) atomicOr(totals + 2, 1);
+            atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
+        }
+        if (brick == nbr - 1) {
+            __threadfence();
+            bool bad = atomicOr(totals + 2, 0) != 0;
+            totals[0] = bad ? -1 : (int)(pre_s + agg_s);
+            totals[1] = bad ? -1 : (int)(pre_t + agg_t);
         }
     }
-    __syncthreads();
-    int ps = (int)s_pre_s + base_s, pt = (int)s_pre_t + base_t;
+    // targets: staged at their brick-local rank (in the space of s_q, read above), then
+    // written out by consecutive threads; sources (few) go straight out
+    uint32_t *st_key = reinterpret_cast<uint32_t *>(s_q);
+    int ps = (int)pre_s + base_s, lt = base_t;
     for (int u = 0; u < per; ++u) {
         int lk = tid * per + u;
         if (!my_bits[u]) continue;
@@ -454,10 +467,15 @@ __global__ void __launch_bounds__(512) k_select_onepass(
             ++ps;
         }
         if (my_bits[u] & 2) {
-            trg_key[pt] = key;
-            trg_pc[pt] = pc;
-            ++pt;
+            st_key[lt] = key;
+            st_pc[lt] = pc;
+            ++lt;
         }
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)agg_t; i += blockDim.x) {
+        trg_key[pre_t + i] = st_key[i];
+        trg_pc[pre_t + i] = st_pc[i];
     }
 }
 

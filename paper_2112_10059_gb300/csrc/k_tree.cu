@@ -124,70 +124,150 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
     return lo;
 }
 
-__global__ void k_tree_root(TreeDev T, int ns, int nt, int S, int D) {
+// Point ranges of every dense slot of every level in one pass over the Morton-sorted keys:
+// point i opens the range of its slot at level l when point i-1 lies in another slot of
+// that level, and closes it when point i+1 does.  Untouched slots keep [0, 0).
+__global__ void k_tree_ranges(int n, const uint32_t *__restrict__ key, int D, int Lmax, int *__restrict__ beg,
+                              int *__restrict__ end) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = key[i];
+    // two keys fall in different slots of level l iff their highest differing bit b (0-based)
+    // satisfies b >= 3 (D - l), i.e. for every l >= D - b / 3; only those levels are written
+    auto first_level = [&](uint32_t other) {
+        const int b = 31 - __clz(k ^ other);
+        const int l0 = D - b / 3;
+        return l0 < 0 ? 0 : l0;
+    };
+    const int lb = i == 0 ? 0 : first_level(key[i - 1]);
+    const int le = i + 1 == n ? 0 : first_level(key[i + 1]);
+    for (int l = lb; l <= Lmax; ++l) beg[dense_off(l) + (k >> (3 * (D - l)))] = i;
+    for (int l = le; l <= Lmax; ++l) end[dense_off(l) + (k >> (3 * (D - l)))] = i + 1;
+}
+
+__device__ __forceinline__ int level_of_slot(int64_t s, int Lmax) {
+    int l = 0;
+    while (l < Lmax && s >= dense_off(l + 1)) ++l;
+    return l;
+}
+
+// A slot holds a box iff it has points and its parent was split (ns > S or nt > S at a
+// level < D).  Point counts only shrink from parent to child, so a split parent implies
+// that every ancestor was split as well.
+__global__ void k_tree_exists(int64_t nslot, int Lmax, int D, int S, const int *__restrict__ rsb,
+                              const int *__restrict__ rse, const int *__restrict__ rtb, const int *__restrict__ rte,
+                              int *__restrict__ flag) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslot) return;
+    const int l = level_of_slot(s, Lmax);
+    const int ns = rse[s] - rsb[s], nt = rte[s] - rtb[s];
     bool ex = ns + nt > 0;
-    T.box_at[0] = ex ? 0 : -1;
-    T.lvl_base[0] = 0;
-    T.lvl_count[0] = ex ? 1 : 0;
-    if (ex) {
-        T.b_level[0] = 0;
-        T.b_key[0] = 0;
-        T.b_sb[0] = 0; T.b_se[0] = ns;
-        T.b_tb[0] = 0; T.b_te[0] = nt;
-        T.b_parent[0] = -1;
-        T.b_leaf[0] = !(0 < D && (ns > S || nt > S));
+    if (ex && l > 0) {
+        const int64_t ps = dense_off(l - 1) + ((s - dense_off(l)) >> 3);
+        const int pns = rse[ps] - rsb[ps], pnt = rte[ps] - rtb[ps];
+        ex = (l - 1 < D) && (pns > S || pnt > S);
     }
+    flag[s] = ex ? 1 : 0;
 }
 
-__global__ void k_tree_flags(TreeDev T, int level, int D, const uint32_t *__restrict__ skey,
-                             const uint32_t *__restrict__ tkey, int *__restrict__ flag,
-                             int4 *__restrict__ rng) {
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nslot = 1ll << (3 * level);
-    if (m >= nslot) return;
-    const int *pat = T.box_at + dense_off(level - 1);
-    int pb = pat[m >> 3];
-    if (pb < 0 || T.b_leaf[pb]) { flag[m] = 0; return; }
-    int shift = 3 * (D - level);
-    uint32_t lo = (uint32_t)m << shift;          // keys < 2^30, so lo + 2^shift fits
-    uint32_t hi = lo + (1u << shift);
-    int sb = lower_bound_u32(skey, T.b_sb[pb], T.b_se[pb], lo);
-    int se = lower_bound_u32(skey, sb, T.b_se[pb], hi);
-    int tb = lower_bound_u32(tkey, T.b_tb[pb], T.b_te[pb], lo);
-    int te = lower_bound_u32(tkey, tb, T.b_te[pb], hi);
-    flag[m] = (se > sb || te > tb) ? 1 : 0;
-    rng[m] = make_int4(sb, se, tb, te);
-}
-
-__global__ void k_tree_emit(TreeDev T, int level, int D, int S, const int *__restrict__ flag,
-                            const int *__restrict__ pos, const int4 *__restrict__ rng) {
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nslot = 1ll << (3 * level);
-    int base = T.lvl_base[level - 1] + T.lvl_count[level - 1];
-    if (m == 0) T.lvl_base[level] = base;
-    if (m >= nslot) return;
-    int *bat = T.box_at + dense_off(level);
-    if (!flag[m]) { bat[m] = -1; return; }
-    int idx = base + pos[m];
-    bat[m] = idx;
-    int4 r = rng[m];
-    T.b_level[idx] = level;
+// Boxes in (level, key) order: box index = exclusive scan of the existence flags.
+__global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S, const int *__restrict__ flag,
+                                const int *__restrict__ pos, const int *__restrict__ rsb,
+                                const int *__restrict__ rse, const int *__restrict__ rtb,
+                                const int *__restrict__ rte, const int *__restrict__ total,
+                                const uint32_t *__restrict__ skey, int ns, const uint32_t *__restrict__ tkey, int nt) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= Lmax) {       // level table (threads 0..Lmax)
+        const int l = (int)s;
+        const int b0 = pos[dense_off(l)];
+        const int b1 = l < Lmax ? pos[dense_off(l + 1)] : *total;
+        T.lvl_base[l] = b0;
+        T.lvl_count[l] = b1 - b0;
+    }
+    if (s >= nslot) return;
+    if (!flag[s]) {
+        T.box_at[s] = -1;
+        return;
+    }
+    const int l = level_of_slot(s, Lmax);
+    const int64_t m = s - dense_off(l);
+    const int idx = pos[s];
+    T.box_at[s] = idx;
+    int sb = rsb[s], se = rse[s], tb = rtb[s], te = rte[s];
+    // an empty range starts where the slot's first key would be inserted
+    const uint32_t lo = (uint32_t)m << (3 * (D - l));
+    if (se == sb) sb = se = lower_bound_u32(skey, 0, ns, lo);
+    if (te == tb) tb = te = lower_bound_u32(tkey, 0, nt, lo);
+    T.b_level[idx] = l;
     T.b_key[idx] = (uint32_t)m;
-    T.b_sb[idx] = r.x; T.b_se[idx] = r.y;
-    T.b_tb[idx] = r.z; T.b_te[idx] = r.w;
-    T.b_parent[idx] = T.box_at[dense_off(level - 1) + (m >> 3)];
-    int ns = r.y - r.x, nt = r.w - r.z;
-    T.b_leaf[idx] = !(level < D && (ns > S || nt > S));
+    T.b_sb[idx] = sb; T.b_se[idx] = se;
+    T.b_tb[idx] = tb; T.b_te[idx] = te;
+    T.b_parent[idx] = l > 0 ? pos[dense_off(l - 1) + (m >> 3)] : -1;
+    T.b_leaf[idx] = !(l < D && (se - sb > S || te - tb > S));
+}
+
+// occ[s] = 1 if the slot's region holds a source point, or lies inside a leaf that holds
+// sources (the deepest existing box over the slot); levels 0..Lmax-1.
+__global__ void k_src_occ(TreeDev T, int64_t nslot, int Lmax, const int *__restrict__ rsb,
+                          const int *__restrict__ rse, uint8_t *__restrict__ occ) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslot) return;
+    uint8_t o = rse[s] > rsb[s];
+    if (!o) {
+        int l = level_of_slot(s, Lmax);
+        int64_t m = s - dense_off(l);
+        for (; l >= 0; --l, m >>= 3) {
+            const int B = T.box_at[dense_off(l) + m];
+            if (B >= 0) {
+                o = T.b_leaf[B] && T.b_se[B] > T.b_sb[B];
+                break;
+            }
+        }
+    }
+    occ[s] = o;
+}
+
+__global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ occ, uint8_t *__restrict__ near) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslot) return;
+    const int l = level_of_slot(s, Lmax);
+    const uint32_t m = (uint32_t)(s - dense_off(l));
+    uint32_t x, y, z;
+    demorton3(m, x, y, z);
+    const int n = 1 << l;
+    uint8_t v = 0;
+    for (int dz = -1; dz <= 1 && !v; ++dz)
+        for (int dy = -1; dy <= 1 && !v; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qx = (int)x + dx, qy = (int)y + dy, qz = (int)z + dz;
+                if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
+                if (occ[dense_off(l) + morton3(qx, qy, qz)]) {
+                    v = 1;
+                    break;
+                }
+            }
+    near[s] = v;
 }
 
 void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
-    k_tree_root<<<1, 1, 0, st>>>(A.T, A.ns, A.nt, A.S, A.D);
-    for (int l = 1; l <= A.Lmax; ++l) {
-        int64_t nslot = 1ll << (3 * l);
-        int grid = (int)((nslot + 255) / 256);
-        k_tree_flags<<<grid, 256, 0, st>>>(A.T, l, A.D, A.skey, A.tkey, A.flag, A.rng);
-        scan_exclusive(A.flag, A.pos, (int)nslot, A.T.lvl_count + l, A.scan_tmp, st);
-        k_tree_emit<<<grid, 256, 0, st>>>(A.T, l, A.D, A.S, A.flag, A.pos, A.rng);
+    const int64_t nslot = dense_off(A.Lmax + 1);
+    cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
+    cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
+    cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
+    cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
+    if (A.ns > 0) k_tree_ranges<<<(A.ns + 255) / 256, 256, 0, st>>>(A.ns, A.skey, A.D, A.Lmax, A.rsb, A.rse);
+    if (A.nt > 0) k_tree_ranges<<<(A.nt + 255) / 256, 256, 0, st>>>(A.nt, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
+    const int grid = (int)((nslot + 255) / 256);
+    k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
+    int *total = A.pos + nslot;
+    scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st);
+    k_tree_emit_all<<<grid, 256, 0, st>>>(A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
+                                          A.rte, total, A.skey, A.ns, A.tkey, A.nt);
+    const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
+    if (npar > 0 && A.occ && A.near) {
+        const int g2 = (int)((npar + 255) / 256);
+        k_src_occ<<<g2, 256, 0, st>>>(A.T, npar, A.Lmax - 1, A.rsb, A.rse, A.occ);
+        k_src_near<<<g2, 256, 0, st>>>(npar, A.Lmax - 1, A.occ, A.near);
     }
 }
 
@@ -228,6 +308,12 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
     int pU = 0, pV = 0, pW = 0, pX = 0;
     if (FILL) { pU = L.u_off[b]; pV = L.v_off[b]; pW = L.w_off[b]; pX = L.x_off[b]; }
     int nt = T.b_te[b] - T.b_tb[b];
+    if (nt > 0) {
+        BoxGeom B = geom_of(T, b);
+        const int l = B.level;
+        // nothing with sources anywhere around the parent: every list is empty
+        if (l >= 1 && T.near && !T.near[dense_off(l - 1) + morton3(B.x >> 1, B.y >> 1, B.z >> 1)]) nt = 0;
+    }
     if (nt > 0) {
         BoxGeom B = geom_of(T, b);
         const int l = B.level;

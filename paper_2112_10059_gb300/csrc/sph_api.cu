@@ -91,6 +91,7 @@ struct sph_ctx {
     DevBuf b_err;                // device error flags of the tensor-core tiles
     DevBuf b_work;               // compact work lists: sources per level, leaves for the leaf and P2P kernels
     DevBuf b_tmask;              // [ncell] 1 at targets (written by the selection)
+    DevBuf b_near;               // tree: source occupancy and its 3x3x3 dilation per dense slot
     DevBuf o_l2pimg;             // BF16 images of the L2P tables (tensor-core L2P)
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
@@ -253,6 +254,7 @@ TreeDev tree_dev(sph_ctx *c) {
     T.b_tb = P<int>(c->b_tb); T.b_te = P<int>(c->b_te);
     T.b_parent = P<int>(c->b_parent);
     T.b_leaf = P<uint8_t>(c->b_leaf);
+    T.near = c->Lmax >= 1 ? P<uint8_t>(c->b_near) + dense_off(c->Lmax + 1) : nullptr;
     return T;
 }
 
@@ -280,12 +282,12 @@ int tree_queue(sph_ctx *c) {
     const int Lmax = std::max(0, D - k);
     c->Lmax = Lmax;
     const int64_t dense_total = dense_off(Lmax + 1);
-    const int64_t top = 1ll << (3 * Lmax);
     ENS(c->b_boxat, dense_total * sizeof(int));
-    ENS(c->b_flag, top * sizeof(int));
-    ENS(c->b_pos, top * sizeof(int));
-    ENS(c->b_rng, top * sizeof(int4));
-    ENS(c->b_scan, scan_tmp_ints((int)std::max<int64_t>(top, 4 * (dense_total + 1))) * sizeof(int) + 64);
+    ENS(c->b_flag, dense_total * sizeof(int));
+    ENS(c->b_pos, (dense_total + 1) * sizeof(int));
+    ENS(c->b_rng, 4 * dense_total * sizeof(int));
+    ENS(c->b_near, 2 * dense_total + 16);
+    ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
     ENS(c->b_lvl, 32 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
     ENS(c->b_level, cap * sizeof(int));
@@ -298,10 +300,12 @@ int tree_queue(sph_ctx *c) {
     A.T = tree_dev(c);
     A.ns = (int)c->ns; A.nt = (int)c->nt; A.S = S; A.D = D; A.Lmax = Lmax;
     A.skey = P<uint32_t>(c->b_skey); A.tkey = P<uint32_t>(c->b_tkey);
-    A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos); A.rng = P<int4>(c->b_rng);
+    A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos);
+    A.rsb = P<int>(c->b_rng); A.rse = A.rsb + dense_total; A.rtb = A.rse + dense_total; A.rte = A.rtb + dense_total;
+    A.occ = P<uint8_t>(c->b_near); A.near = A.occ + dense_total;
     A.scan_tmp = P<int>(c->b_scan);
     tree_build_launch(A, c->stream);
-    c->launches += 1 + 5 * Lmax;
+    c->launches += 7;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
@@ -1168,7 +1172,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
-                     &c->h_s, &c->b_tmask, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
+                     &c->h_s, &c->b_tmask, &c->b_near, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);

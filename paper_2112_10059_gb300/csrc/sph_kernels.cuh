@@ -52,13 +52,17 @@ struct TreeDev {
     uint32_t *b_key;
     int *b_sb, *b_se, *b_tb, *b_te, *b_parent;
     uint8_t *b_leaf;
+    // near[s], slots of levels 0..Lmax-1: a source point, or a leaf holding sources, lies in
+    // the 3x3x3 slots around s.  If not, every list of every child of s is empty.
+    const uint8_t *near;
 };
 struct TreeArgs {
     TreeDev T;
     int ns, nt, S, D, Lmax;
     const uint32_t *skey, *tkey;
-    int *flag, *pos;     // dense scratch, 8^Lmax
-    int4 *rng;           // dense scratch, 8^Lmax
+    int *flag, *pos;     // dense scratch over every level's slots, dense_off(Lmax + 1) (+1 for pos)
+    int *rsb, *rse, *rtb, *rte;   // dense point ranges of every slot of every level
+    uint8_t *occ, *near;          // dense over levels 0..Lmax-1: source occupancy and its 3x3x3 dilation
     int *scan_tmp;
 };
 void tree_build_launch(const TreeArgs &A, cudaStream_t st);
