@@ -588,8 +588,128 @@ __global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, int box_be
     }
 }
 
+// Small leaves (edge e <= 8): one warp per box, the same three contractions in the warp's own
+// shared slots, outputs as float4 runs along x for whole boxes (e a multiple of 4 and x rows
+// 16-byte aligned), per cell otherwise.
+constexpr int SEPW_WARPS = 8;
+constexpr int SEPW_MAXE = 8;
+constexpr int SEPW_MAXP = 6;           // orders up to 6 (n <= 216, npad <= 224)
+constexpr int SEPW_NP = 224;
+
+__global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int level, int box_begin,
+                                                                   int box_count, float *__restrict__ out) {
+    __shared__ float Sb[SEPW_MAXP * SEPW_MAXE];                                  // [p][e]
+    __shared__ __align__(16) float sd[SEPW_WARPS][SEPW_NP];
+    __shared__ float T1[SEPW_WARPS][SEPW_MAXP * SEPW_MAXP * SEPW_MAXE];          // [p*p][e]
+    __shared__ float T2[SEPW_WARPS][SEPW_MAXP * SEPW_MAXE * SEPW_MAXE];          // [p][e][e]
+    __shared__ float tch[8];
+    const int p = F.O.order, n = F.O.n, np = F.O.npad;
+    const int e = 1 << (F.D - level);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < p) tch[threadIdx.x] = F.O.cheb_t[threadIdx.x];
+    __syncthreads();
+    for (int j = threadIdx.x; j < p * e; j += blockDim.x) {
+        const int a = j / e, x = j % e;
+        const float u = (float)(2 * x + 1 - e) / (float)e;
+        float v = 1.f;
+        for (int k = 0; k < p; ++k)
+            if (k != a) v *= (u - tch[k]) / (tch[a] - tch[k]);
+        Sb[j] = v;
+    }
+    __syncthreads();
+    const TreeDev &T = F.T;
+    const bool rows4 = (e % 4) == 0 && (F.nx % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    int le = 0;
+    while ((1 << le) < e) ++le;
+    const int em = e - 1;
+    float *d = sd[warp], *t1 = T1[warp], *t2 = T2[warp];
+    // the next box's d is fetched into registers while the current box is evaluated
+    const int stride = gridDim.x * SEPW_WARPS;
+    int i = blockIdx.x * SEPW_WARPS + warp;
+    float4 nd[2];
+    auto fetch = [&](int ii, float4 *r) {
+        if (ii < box_count) {
+            const float *src = F.dchk + (size_t)(box_begin + ii) * np;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int j = 4 * lane + 128 * k;
+                r[k] = j < np ? __ldg(reinterpret_cast<const float4 *>(src + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    fetch(i, nd);
+    for (; i < box_count; i += stride) {
+        const int b = box_begin + i;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int j = 4 * lane + 128 * k;
+            if (j < np) *reinterpret_cast<float4 *>(d + j) = nd[k];
+        }
+        fetch(i + stride, nd);
+        const bool use = T.b_leaf[b] && T.b_te[b] > T.b_tb[b];
+        const bool full = use && T.b_te[b] - T.b_tb[b] == e * e * e;
+        uint32_t ux, uy, uz;
+        demorton3(T.b_key[b], ux, uy, uz);
+        const int bx = (int)ux * e, by = (int)uy * e, bz = (int)uz * e;
+        __syncwarp();
+        if (use) {
+            for (int j = lane; j < p * p * e; j += 32) {
+                const int x = j & em, cb = j >> le;
+                const float *row = d + p * cb;
+                float acc = 0.f;
+                for (int a = 0; a < p; ++a) acc = fmaf(row[a], Sb[a * e + x], acc);
+                t1[j] = acc;
+            }
+            __syncwarp();
+            for (int j = lane; j < p * e * e; j += 32) {
+                const int x = j & em, y = (j >> le) & em, c = j >> (2 * le);
+                float acc = 0.f;
+                for (int bb = 0; bb < p; ++bb) acc = fmaf(t1[(c * p + bb) * e + x], Sb[bb * e + y], acc);
+                t2[j] = acc;
+            }
+            __syncwarp();
+            if (full && rows4) {
+                for (int r = lane; r < (e * e * e) >> 2; r += 32) {
+                    const int c4 = r << 2;
+                    const int x = c4 & em, y = (c4 >> le) & em, z = c4 >> (2 * le);
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float acc = 0.f;
+                        for (int c = 0; c < p; ++c) acc = fmaf(t2[(c * e + y) * e + x + u], Sb[c * e + z], acc);
+                        v[u] = acc;
+                    }
+                    const int64_t o =
+                        (int64_t)(bx + x) + (int64_t)F.nx * ((int64_t)(by + y) + (int64_t)F.ny * (bz + z));
+                    *reinterpret_cast<float4 *>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            } else {
+                for (int j = lane; j < e * e * e; j += 32) {
+                    const int x = j & em, y = (j >> le) & em, z = j >> (2 * le);
+                    const int gx = bx + x, gy = by + y, gz = bz + z;
+                    if (gx >= F.nx || gy >= F.ny || gz >= F.nz) continue;
+                    const int64_t o = (int64_t)gx + (int64_t)F.nx * ((int64_t)gy + (int64_t)F.ny * gz);
+                    if (!full && !F.tmask[o]) continue;
+                    float acc = 0.f;
+                    for (int c = 0; c < p; ++c) acc = fmaf(t2[(c * e + y) * e + x], Sb[c * e + z], acc);
+                    out[o] = acc;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    (void)n;
+}
+
 void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
+    if ((1 << (F.D - level)) <= SEPW_MAXE && F.O.order <= SEPW_MAXP && F.O.npad <= SEPW_NP) {
+        const int per = SEPW_WARPS;
+        int grid = (box_count + per - 1) / per;
+        if (grid > 152 * 8) grid = 152 * 8;
+        k_l2p_sep_small<<<grid, SEPW_WARPS * 32, 0, st>>>(F, level, box_begin, box_count, out);
+        return;
+    }
     const int e = 1 << (F.D - level), p = F.O.order;
     const int band = sep_band_rows(p, e);
     const size_t smem = sep_smem_bytes(p, F.O.npad, e);

@@ -81,6 +81,7 @@ struct sph_ctx {
     bool p2p_in_leaf = false;         // near field inside the leaf kernel (reference form)
     bool l2p_simt = false;            // FP32 SIMT L2P even when the tensor-core images exist
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
+    bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -570,7 +571,10 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                 c->launches += c->lvl_count[l] > 0;
             }
         for (int l = 3; l <= c->Lmax; ++l) {
-            if (S.tc && c->l2l_eight)
+            // 8 children per CTA where that still gives every SM a CTA; one child per CTA (8x the
+            // CTAs, 1/8 of the serial work each) for the small upper levels
+            const bool few = (c->lvl_count[l - 1] + 63) / 64 < 152;
+            if (S.tc && c->l2l_eight && !few)
                 fmm_l2l_tc8_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, S.err, c->stream);
             else if (S.tc)
                 fmm_l2l_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], F.O.l2l_img, S.err, c->stream);
@@ -582,11 +586,19 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     }
     if (tm) tm->mark_at(7, c->stream);
     if (F.leaf_l2p_done) {
+        // default: the interpolation table on the tensor cores for leaves of edge 4 (the bulk of
+        // a fine tree; measured faster there), the tensor-product (separable) form elsewhere.
+        // SPH_L2P_TC=1: tables on the tensor cores at every level; SPH_L2P_SIMT=1: FP32 tables.
         const bool l2p_tc = S.tc && F.O.l2p_img != nullptr && !c->l2p_simt;
+        const bool sep_all = F.l2p_sep && !c->l2p_tc_tables;
         if (l2p_tc) CK(cudaMemsetAsync(S.err + 1, 0, sizeof(int), c->stream));
         for (int l = 2; l <= c->Lmax; ++l) {
-            if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
-                if (l2p_tc) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
+            const bool tc_here = l2p_tc && (c->l2p_tc_tables || (1 << (c->D - l)) == 4);
+            if (c->lvl_count[l] > 0 && sep_all && !tc_here) {
+                fmm_l2p_sep_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                ++c->launches;
+            } else if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
+                if (tc_here) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
                 else fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
                 ++c->launches;
             } else if (c->lvl_count[l] > 0 && F.l2p_sep) {
@@ -804,6 +816,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->select_two_pass = parent->select_two_pass;
     sub->p2p_in_leaf = parent->p2p_in_leaf;
     sub->l2p_simt = parent->l2p_simt;
+    sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->launches = 0;
     return SPH_OK;
 }
@@ -1141,6 +1154,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_SELECT_TWO_PASS")) c->select_two_pass = atoi(e) != 0;
     if (const char *e = getenv("SPH_P2P_IN_LEAF")) c->p2p_in_leaf = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
+    if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;

@@ -202,14 +202,15 @@ def test_nonpow2_grid_with_mask_tensor_cores(sph):
 
 
 @pytest.mark.parametrize("pi", [1, 2])
-def test_tensor_core_l2p_and_separate_near_field(sph, monkeypatch, pi):
-    """The tensor-core L2P equals the FP32 table L2P to BF16x3 accuracy, and the warp-tiled
-    near-field kernel equals the near field summed inside the leaf kernel (same terms,
-    another order)."""
+def test_l2p_forms_and_separate_near_field(sph, monkeypatch, pi):
+    """The three L2P forms agree: tensor-product (default), interpolation tables in FP32, and
+    tables on the tensor cores (BF16x3); and the warp-tiled near-field kernel equals the near
+    field summed inside the leaf kernel (same terms, another order)."""
     p = _problems()[pi]
     outs = {}
-    for name, env in (("default", {}), ("l2p_simt", {"SPH_L2P_SIMT": "1"}), ("p2p_in_leaf", {"SPH_P2P_IN_LEAF": "1"})):
-        for k in ("SPH_L2P_SIMT", "SPH_P2P_IN_LEAF"):
+    for name, env in (("default", {}), ("l2p_simt", {"SPH_L2P_SIMT": "1"}), ("l2p_tc", {"SPH_L2P_TC": "1"}),
+                      ("p2p_in_leaf", {"SPH_P2P_IN_LEAF": "1"})):
+        for k in ("SPH_L2P_SIMT", "SPH_L2P_TC", "SPH_P2P_IN_LEAF"):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)
@@ -219,7 +220,8 @@ def test_tensor_core_l2p_and_separate_near_field(sph, monkeypatch, pi):
         c.close()
     ref, J, T = oracle.sph_problem(p)
     assert oracle.rel_l2(outs["default"][T], outs["p2p_in_leaf"][T]) < 1e-6
-    assert oracle.rel_l2(outs["default"][T], outs["l2p_simt"][T]) < 3e-5
+    assert oracle.rel_l2(outs["default"][T], outs["l2p_simt"][T]) < 1e-5
+    assert oracle.rel_l2(outs["default"][T], outs["l2p_tc"][T]) < 3e-5
     others = np.ones(outs["default"].size, bool)
     others[T] = False
     assert np.all(outs["default"][others] == 0)
