@@ -281,12 +281,10 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __shared__ int s_brick;
     __shared__ float s_thr_q, s_thr_e;
     __shared__ int s_qpos;
-    __shared__ uint8_t s_bits[4096];
-    __shared__ float s_q[4096];
     __shared__ int ws[16], wt[16];
     __shared__ unsigned rs[16], rt[16];
     __shared__ int s_stop;
-    __shared__ uint32_t st_pc[4096];
+    __shared__ uint32_t st_key[4096], st_pc[4096];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_brick = (int)atomicAdd(ticket, 1u);
@@ -301,62 +299,47 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     const int brick = s_brick;
     const int b = r.brick_edge_log2;
     const int ncell = 1 << (3 * b);
-    const int edge = 1 << b;
     uint32_t bx, by, bz;
     demorton3((uint32_t)brick, bx, by, bz);
     const int x0 = bx << b, y0 = by << b, z0 = bz << b;
     const float thr_q = s_thr_q, thr_e = s_thr_e;
     const bool qpos = s_qpos;
-    // stage in linear (x fastest) order: coalesced rows, byte-wise conflict-free stores.
-    // All loads of a thread are issued before any is used (up to 8 cells per thread).
+    // Thread t owns the brick's local Morton keys 8t .. 8t+7: a 2x2x2 micro-cube, so the
+    // 8 cells follow from one decode; its loads are all issued before any is used (a warp's
+    // cells form an 8x8x4 block, whose rows the L1 serves sector by sector).
+    int my_bits[8];
+    float my_q[8];
+    uint32_t mx, my, mz;
+    demorton3((uint32_t)(8 * tid), mx, my, mz);
     {
-        constexpr int U = 8;
-        float qv[U], ev[U];
-        uint32_t lin[U];
-        bool in[U];
+        float ev[8];
+        uint32_t lin[8];
+        bool in[8];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = tid + u * (int)blockDim.x;
-            const int lx = c & (edge - 1), ly = (c >> b) & (edge - 1), lz = c >> (2 * b);
-            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            in[u] = c < ncell && x < r.nx && y < r.ny && z < r.nz;
+        for (int u = 0; u < 8; ++u) {
+            const int x = x0 + (int)mx + (u & 1), y = y0 + (int)my + ((u >> 1) & 1), z = z0 + (int)mz + (u >> 2);
+            in[u] = 8 * tid + u < ncell && x < r.nx && y < r.ny && z < r.nz;
             lin[u] = in[u] ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
-            qv[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
+            my_q[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
             ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
             if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = tid + u * (int)blockDim.x;
-            if (c >= ncell) break;
+        for (int u = 0; u < 8; ++u) {
             int bits = 0;
             if (in[u]) {
-                if (r.src_all || (qpos && qv[u] >= thr_q)) bits |= 1;
+                if (r.src_all || (qpos && my_q[u] >= thr_q)) bits |= 1;
                 if (r.trg_mode == 0) bits |= 2;
                 else if (r.trg_mode == 1) { if (ev[u] >= thr_e) bits |= 2; }
                 else if (ev[u] != 0.f) bits |= 2;
                 if (tmask) tmask[lin[u]] = (uint8_t)(bits >> 1);
             }
-            s_bits[c] = (uint8_t)bits;
-            s_q[c] = qv[u];
+            my_bits[u] = bits;
         }
     }
-    __syncthreads();
-    int my_bits[8];
-    float my_q[8];
     int ns = 0, nt = 0;
-    const int per = (ncell + blockDim.x - 1) / blockDim.x;
-    for (int u = 0; u < per; ++u) {
-        int lk = tid * per + u;
-        my_bits[u] = 0;
-        my_q[u] = 0.f;
-        if (lk < ncell) {
-            uint32_t lx, ly, lz;
-            demorton3((uint32_t)lk, lx, ly, lz);
-            int c = (int)(lx + ((ly + (lz << b)) << b));
-            my_bits[u] = s_bits[c];
-            my_q[u] = s_q[c];
-        }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
         ns += my_bits[u] & 1;
         nt += (my_bits[u] >> 1) & 1;
     }
@@ -451,15 +434,13 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     }
     // targets: staged at their brick-local rank (in the space of s_q, read above), then
     // written out by consecutive threads; sources (few) go straight out
-    uint32_t *st_key = reinterpret_cast<uint32_t *>(s_q);
     int ps = (int)pre_s + base_s, lt = base_t;
-    for (int u = 0; u < per; ++u) {
-        int lk = tid * per + u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int lk = 8 * tid + u;
         if (!my_bits[u]) continue;
-        uint32_t lx, ly, lz;
-        demorton3((uint32_t)lk, lx, ly, lz);
-        uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)lk;
-        uint32_t pc = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
+        const uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)lk;
+        const uint32_t pc = pack_ijk(x0 + mx + (u & 1), y0 + my + ((u >> 1) & 1), z0 + mz + (u >> 2));
         if (my_bits[u] & 1) {
             src_key[ps] = key;
             src_pc[ps] = pc;
