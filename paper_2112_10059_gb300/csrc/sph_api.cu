@@ -64,6 +64,8 @@ struct sph_ctx {
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaEvent_t> events;
     bool batch_graph = true;
+    bool eval_graph = true;             // single evaluations: FMM passes as one captured graph
+    cudaGraphExec_t eval_gexec = nullptr;
     // surrogate evaluation: coarse and fine sub-contexts on this context's stream, buffers
     sph_ctx *sur_coarse = nullptr, *sur_fine = nullptr;
     DevBuf s_qc, s_Sc, s_y, s_Sp, s_x, s_Sf, s_mask, s_svox, s_err, s_pe, s_flags, s_counts;
@@ -451,7 +453,11 @@ struct PhaseTimer {
     }
     void mark_at(int k, cudaStream_t st) {   // record event k (events between may stay unrecorded)
         if (on && k < 16) {
-            cudaEventRecord(ev[k], st);
+            // inside a graph capture the record must become an event-record node of the graph
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(st, &cs);
+            if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal);
+            else cudaEventRecord(ev[k], st);
             n = k + 1;
         }
     }
@@ -660,6 +666,43 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
     stats->leaf_size = c->leaf_eff;
 }
 
+// The passes queued as one CUDA graph: captured on the context's private capture stream (the
+// caller's stream may be the legacy default stream, which cannot be captured) and launched on
+// the caller's stream; the executable is updated in place while the topology repeats.
+int fmm_queue_graph(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t eb = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int r = eb == cudaSuccess ? fmm_queue(c, S, out, tm) : SPH_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = eb == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : eb;
+    c->stream = user;
+    if (r || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return r ? r : cuda_fail(c, ee, "capture of the FMM passes");
+    }
+    bool updated = false;
+    if (c->eval_gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(c->eval_gexec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->eval_gexec);
+            c->eval_gexec = nullptr;
+        }
+    }
+    cudaError_t ei = updated ? cudaSuccess : cudaGraphInstantiate(&c->eval_gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->eval_gexec = nullptr;
+        return cuda_fail(c, ei, "cudaGraphInstantiate (FMM passes)");
+    }
+    CK(cudaGraphLaunch(c->eval_gexec, c->stream));
+    return SPH_OK;
+}
+
 // tree + operators + passes for the current selection (used by eval and by the autotuner)
 int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm) {
     int r = run_tree(c);
@@ -670,7 +713,7 @@ int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm) {
     PassState S;
     r = fmm_prepare(c, S);
     if (r) return r;
-    return fmm_queue(c, S, out, tm);
+    return c->eval_graph ? fmm_queue_graph(c, S, out, tm) : fmm_queue(c, S, out, tm);
 }
 
 // Problem class of the autotuner's cache: grid shape, far-field form and arithmetic, and the
@@ -1156,6 +1199,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
+    if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {
         int m, o;
         if (sscanf(e, "%d,%d", &m, &o) == 2) { c->far_method = m; c->far_order = o; }
@@ -1174,6 +1218,7 @@ void sph_destroy(sph_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->eval_gexec) cudaGraphExecDestroy(c->eval_gexec);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (sph_ctx *sub : c->subs) sph_destroy(sub);
