@@ -142,19 +142,28 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks):
-    """Achieved vs peak per phase kernel.  Work is ALGORITHMIC (what the method needs), not executed:
+# DRAM bytes (read + write) per launch of the selection kernels from one ncu capture
+# (profiles/k_select_onepass_streamer256_adaptive.md, profiles/k_grid_max_streamer256_adaptive.md);
+# valid for the 256^3 adaptive workload and the kernels as profiled there.
+NCU_TRAFFIC = {"select": (134.320640 + 104.982784 + 134.236928 + 3.904512) * 1e6}
+
+
+def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_headline=True):
+    """Achieved vs peak per phase.  Work is ALGORITHMIC (what the method needs), not executed:
       m2l  (tensor): 2 n^2 flops per V pair, n = order^3 (the BF16 x3 split executes 3 x 128^2 x 2);
       l2l  (tensor): 2 n^2 flops per child box with targets below level 2;
-      l2p  (FP32 FMA): 2 n flops per target in a leaf with an interpolation table;
+      l2p  (HBM): the leaves' local expansions read (npad x 4 B per leaf with targets) + S written (4 B per target);
       near (MUFU):  P2P pairs + M2P evaluations (3 MUFU each: rsqrt + 2 x ex2);
-      select (HBM): 8 B per cell read (q and |E|) + 12 B per selected point written."""
+      select (HBM): 8 B per cell read twice (maxima, then the rules: q and |E|) + 8 B per target and
+                    12 B per source written + 1 B per cell of target mask."""
     n = args.order ** 3
+    npad = (n + 15) // 16 * 16
     mean = lambda k: statistics.mean(x[k] for x in step_stats)
     lev = tree["level"]
     ntb = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
     nsb = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
     n_child = int(np.sum((lev >= 3) & (ntb > 0)))
+    n_leaf_t = int(np.sum(tree["leaf"] & (ntb > 0) & (lev >= 2)))
     nV = len(tree["V"])
     U, W = tree["U"], tree["W"]
     p2p = int(np.sum(ntb[U[:, 0]] * nsb[U[:, 1]])) if len(U) else 0
@@ -163,26 +172,29 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks):
     mufu_peak = NSM * MUFU_PER_SM_CLK * f_mhz * 1e6 / MUFU_PER_EVAL
     tc = args.m2l == "bf16x3"
     tpk = peaks["bf16_tflops"]
+    hbm = peaks["hbm_gbs"]
+    hbm_basis = "measured HBM copy %.0f GB/s (%s)" % (hbm, peaks["source"])
     out = {}
 
-    def add(name, kernel, bound, work, unit_work, ms, peak, unit, basis):
+    def add(name, kernel, bound, work, unit_work, ms, peak, unit, basis, traffic=None):
         ach = work / (ms * 1e-3) if ms > 0 else 0.0
         scale = 1e12 if unit == "TFLOP/s" else (1e9 if unit == "GB/s" else 1.0)
         out[name] = {"kernel": kernel, "bound": bound, "achieved": ach / scale, "peak": peak, "unit": unit,
-                     "frac": (ach / scale) / peak if peak else None, "traffic": None, "ms_per_launch": ms,
+                     "frac": (ach / scale) / peak if peak else None, "traffic": traffic, "ms_per_launch": ms,
                      "work_per_launch": work, "work_unit": unit_work, "peak_basis": basis}
 
     add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
         mean("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
         ("measured dense BF16 %.1f TFLOP/s (%s)" % (tpk, peaks["source"])) if tc else "FP32 FMA 152 SMs")
-    add("l2l", "k_l2l_tc" if tc else "k_l2l_gemm", "tensor" if tc else "alu", 2.0 * n * n * n_child, "flop",
-        mean("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
-    add("l2p", "k_l2p_gemm", "alu", 2.0 * n * nt, "flop", mean("ms_l2p"), fp32_peak, "TFLOP/s",
-        "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % f_mhz)
-    add("near", "k_leaf", "alu", float(p2p + m2p), "kernel-evals", mean("ms_near"), mufu_peak, "evals/s",
+    add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", "tensor" if tc else "alu", 2.0 * n * n * n_child,
+        "flop", mean("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
+    add("l2p", "k_l2p_tc + k_l2p_sep_small + k_l2p_sep" if tc else "k_l2p_sep_small + k_l2p_sep", "hbm",
+        4.0 * npad * n_leaf_t + 4.0 * nt, "bytes", mean("ms_l2p"), hbm, "GB/s", hbm_basis)
+    add("near", "k_p2p", "alu", float(p2p + m2p), "kernel-evals", mean("ms_near"), mufu_peak, "evals/s",
         "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz)
-    add("select", "k_select_brick", "hbm", 8.0 * ncell + 12.0 * (ns + nt), "bytes", mean("ms_select"),
-        peaks["hbm_gbs"], "GB/s", "measured HBM copy %.0f GB/s (%s)" % (peaks["hbm_gbs"], peaks["source"]))
+    add("select", "k_grid_max + k_select_onepass", "hbm", 16.0 * ncell + 8.0 * nt + 12.0 * ns + 1.0 * ncell,
+        "bytes", mean("ms_select"), hbm, "GB/s", hbm_basis,
+        traffic=NCU_TRAFFIC["select"] if workload_is_headline else None)
     return out
 
 
@@ -517,7 +529,8 @@ def main():
     clocks = clk.summary()
     f_mhz = clocks["sm_mhz"] or 1920.0
     peaks = measured_peaks()
-    roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, f_mhz, peaks)
+    roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, f_mhz, peaks,
+                     workload_is_headline=(args.n == 256 and args.p == 760.0 and args.order == 5))
     dominant = max(roof, key=lambda k: roof[k]["ms_per_launch"])
 
     # FP32 direct sum on the same GPU over the same selected sets
