@@ -228,14 +228,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
     if (tile >= Pd.tile_off[Pd.nkeys]) return;
     TcSmem s = carve(smem_raw);
     __shared__ int s_key;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = Pd.nkeys;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (Pd.tile_off[mid] <= tile) lo = mid; else hi = mid;
-        }
-        s_key = lo;
-    }
+    if (threadIdx.x == 0) s_key = Pd.tile_key[tile];
     tile_setup(s);
     const int key = s_key;
     const int p0 = Pd.off[key] + (tile - Pd.tile_off[key]) * TCN;
@@ -249,6 +242,220 @@ __global__ void __launch_bounds__(128) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
     const uint16_t *img = images + (size_t)key * (2 * A_BYTES / 2);
     tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err);
     tile_teardown(s);
+}
+
+// ---------------------------------------------------------------- M2L, persistent and pipelined
+// One CTA per SM walks a contiguous range of tiles (tiles of one (level, offset) group are
+// consecutive, so the operator image is reused while the group lasts).  Per tile i:
+//   (a) the FP32 source rows of tile i, copied by cp.async during tile i-1, have landed;
+//   (b) MMA(i-1) has completed (the B tile and its TMEM accumulator are free / ready);
+//   (c) the rows are split into the BF16 hi / lo B tile;
+//   (d, e) tile i+1's pair indices are read and its rows start to stream in (cp.async);
+//   (f) thread 0 issues MMA(i) into accumulator i % 2 and, if tile i+1 needs another
+//       operator, its image into the other A buffer;
+//   (g) all threads add accumulator (i-1) % 2 into the targets (reductions),
+// so the epilogue of one tile runs under the MMAs and loads of the next.  Pair metadata
+// rotates through three slots (i+1 is written while i-1 is still being scattered).
+constexpr uint32_t PIPE_RAW = TCN * TCK * 4;       // 64 rows x 128 FP32
+constexpr uint32_t PIPE_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + PIPE_RAW + 64 + 6 * TCN * 4 + 64;
+
+__device__ __forceinline__ void m2l_tile_range(const PairsDev &Pd, int key, int tile, int &p0, int &p1) {
+    p0 = Pd.off[key] + (tile - Pd.tile_off[key]) * TCN;
+    p1 = min(p0 + TCN, Pd.off[key + 1]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
+                                                        int *err) {
+    const int T = Pd.tile_off[Pd.nkeys];
+    const int chunk = (T + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * chunk, t_end = min(T, t_begin + chunk);
+    if (t_begin >= t_end) return;                  // uniform, before any allocation
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *abuf[2] = {base, base + 2 * A_BYTES};
+    uint8_t *b_hi = base + 4 * A_BYTES, *b_lo = b_hi + B_BYTES;
+    float *raw = reinterpret_cast<float *>(b_lo + B_BYTES);
+    uint8_t *tail = reinterpret_cast<uint8_t *>(raw) + PIPE_RAW;
+    uint64_t *bar_a = reinterpret_cast<uint64_t *>(tail);       // [2]
+    uint64_t *bar_mma = bar_a + 2;                              // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 4);
+    int *ctl = reinterpret_cast<int *>(tslot + 1);              // [0] error, [1] next key, [2] next aslot
+    int *msrc = reinterpret_cast<int *>(tail + 64);             // [3][TCN]
+    int *mdst = msrc + 3 * TCN;                                 // [3][TCN]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int np = F.O.npad, n = F.O.n;
+    if (tid < 32) {
+        tc::tmem_alloc(tc::smem_u32(tslot), 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(tc::smem_u32(bar_a + k), 1);
+            tc::mbar_init(tc::smem_u32(bar_mma + k), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int key = 0, lo = 0, hi = Pd.nkeys;
+        while (hi - lo > 1) {                      // key of the first tile
+            const int mid = (lo + hi) >> 1;
+            if (Pd.tile_off[mid] <= t_begin) lo = mid; else hi = mid;
+        }
+        key = lo;
+        ctl[0] = 0;
+        ctl[1] = key;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    // thread-0 state of the image buffers
+    int a_loads[2] = {0, 0}, a_landed[2] = {0, 0};
+    int cur_key = ctl[1], cur_slot = 0;
+    auto fill_meta = [&](int tile, int key, int ms) {
+        if (tid < TCN) {
+            int p0, p1;
+            m2l_tile_range(Pd, key, tile, p0, p1);
+            const int q = p0 + tid;
+            msrc[ms * TCN + tid] = q < p1 ? Pd.src[q] : -1;
+            mdst[ms * TCN + tid] = q < p1 ? Pd.trg[q] : -1;
+        }
+    };
+    auto issue_raw = [&](int ms) {
+        for (int e = tid; e < TCN * (TCK / 4); e += 128) {
+            const int row = e >> 5, q = e & 31;
+            const int src = msrc[ms * TCN + row];
+            const float *g = src >= 0 && 4 * q < np ? F.ueq + (size_t)src * np + 4 * q : F.ueq;
+            tc::cp_async16(tc::smem_u32(raw + row * TCK + 4 * q), g, (src >= 0 && 4 * q < np) ? 16u : 0u);
+        }
+        tc::cp_async_commit();
+    };
+    auto epilogue = [&](int i) {
+        const int ms = i % 3;
+        const uint32_t col = (uint32_t)((i & 1) * TCN);
+        const int row = warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < TCN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)c0, v);
+            if (row < n) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int d = mdst[ms * TCN + c0 + j];
+                    if (d >= 0) atomicAdd(F.dchk + (size_t)d * np + row, v[j]);
+                }
+            }
+        }
+    };
+    // prologue: tile t_begin's metadata, rows and image
+    fill_meta(t_begin, cur_key, 0);
+    __syncthreads();
+    issue_raw(0);
+    if (tid == 0) {
+        tc::mbar_expect_tx(tc::smem_u32(bar_a), 2 * A_BYTES);
+        tc::bulk_g2s(tc::smem_u32(abuf[0]), images + (size_t)cur_key * (2 * A_BYTES / 2), 2 * A_BYTES,
+                     tc::smem_u32(bar_a));
+        a_loads[0] = 1;
+    }
+    const int ntile = t_end - t_begin;
+    const uint32_t idesc = tc::idesc_bf16_f32(TCM, TCN);
+    int done_epi = -1;
+    for (int i = 0; i < ntile; ++i) {
+        const int t = t_begin + i;
+        // (a) rows of tile i landed (every thread's copies)
+        tc::cp_async_wait<0>();
+        // (b) MMA(i-1) complete
+        if (tid == 0 && i >= 1) {
+            if (!tc::mbar_wait_bounded(tc::smem_u32(bar_mma + ((i - 1) & 1)), ((i - 1) >> 1) & 1, WAIT_LIMIT))
+                ctl[0] |= 2;
+        }
+        __syncthreads();
+        if (ctl[0]) break;
+        tc::fence_after_sync();
+        // (c) split the rows into the B tile
+        for (int e = tid; e < TCN * (TCK / 4); e += 128) {
+            const int row = e >> 5, q = e & 31;
+            put_split4(b_hi, b_lo, row, 4 * q, TCN, *reinterpret_cast<const float4 *>(raw + row * TCK + 4 * q));
+        }
+        tc::fence_proxy_async_smem();
+        // (d) next tile's key and metadata
+        if (tid == 0 && i + 1 < ntile) {
+            int k = cur_key;
+            while (Pd.tile_off[k + 1] <= t + 1) ++k;
+            ctl[1] = k;
+        }
+        __syncthreads();
+        const int next_key = ctl[1];
+        if (i + 1 < ntile) fill_meta(t + 1, next_key, (i + 1) % 3);
+        __syncthreads();
+        // (e) rows of tile i+1 start streaming into the raw buffer (free: converted above)
+        if (i + 1 < ntile) issue_raw((i + 1) % 3);
+        // (f) MMA(i), and the image of tile i+1 if its operator differs
+        if (tid == 0) {
+            int ok = 1;
+            if (a_landed[cur_slot] < a_loads[cur_slot]) {
+                ok = tc::mbar_wait_bounded(tc::smem_u32(bar_a + cur_slot), (a_loads[cur_slot] - 1) & 1, WAIT_LIMIT);
+                a_landed[cur_slot] = a_loads[cur_slot];
+            }
+            if (ok) {
+                tc::fence_after_sync();
+                const uint32_t ahi = tc::smem_u32(abuf[cur_slot]), alo = ahi + A_BYTES;
+                const uint32_t bhi = tc::smem_u32(b_hi), blo = tc::smem_u32(b_lo);
+                const uint32_t d = tmem + (uint32_t)((i & 1) * TCN);
+#pragma unroll
+                for (int ks = 0; ks < TCK / 16; ++ks) {
+                    const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+                    const uint32_t bo = tc::sw128_offset(0, 16 * ks, TCN);
+                    tc::mma_bf16(d, tc::sdesc_sw128(ahi + ao), tc::sdesc_sw128(bhi + bo), idesc, ks > 0);
+                    tc::mma_bf16(d, tc::sdesc_sw128(ahi + ao), tc::sdesc_sw128(blo + bo), idesc, 1);
+                    tc::mma_bf16(d, tc::sdesc_sw128(alo + ao), tc::sdesc_sw128(bhi + bo), idesc, 1);
+                }
+                tc::mma_commit(tc::smem_u32(bar_mma + (i & 1)));
+                if (i + 1 < ntile && next_key != cur_key) {
+                    // the other buffer's last reader was tile i-1 or earlier, complete at (b)
+                    const int o = cur_slot ^ 1;
+                    tc::mbar_expect_tx(tc::smem_u32(bar_a + o), 2 * A_BYTES);
+                    tc::bulk_g2s(tc::smem_u32(abuf[o]), images + (size_t)next_key * (2 * A_BYTES / 2),
+                                 2 * A_BYTES, tc::smem_u32(bar_a + o));
+                    ++a_loads[o];
+                    cur_slot = o;
+                }
+            } else {
+                ctl[0] |= 1;
+            }
+            cur_key = next_key;
+        }
+        // (g) scatter tile i-1 while MMA(i) runs
+        if (i >= 1) {
+            epilogue(i - 1);
+            done_epi = i - 1;
+        }
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    // last tile: wait for its MMAs, then scatter it
+    const int last = ntile - 1;
+    if (tid == 0 && !ctl[0]) {
+        if (!tc::mbar_wait_bounded(tc::smem_u32(bar_mma + (last & 1)), (last >> 1) & 1, WAIT_LIMIT)) ctl[0] |= 2;
+    }
+    __syncthreads();
+    if (!ctl[0] && done_epi < last) {
+        tc::fence_after_sync();
+        epilogue(last);
+    }
+    if (ctl[0] && tid == 0) {
+        atomicOr(err, ctl[0]);
+        // let this CTA's copies and MMAs finish before its memory is released
+        for (int k = 0; k < 2; ++k)
+            if (a_landed[k] < a_loads[k])
+                tc::mbar_wait_bounded(tc::smem_u32(bar_a + k), (a_loads[k] - 1) & 1, WAIT_LIMIT);
+        for (int k = 0; k < 2 && k <= last; ++k) {
+            const int i_last = last - ((last - k) & 1);      // last tile that used accumulator k
+            tc::mbar_wait_bounded(tc::smem_u32(bar_mma + (i_last & 1)), (i_last >> 1) & 1, WAIT_LIMIT);
+        }
+    }
+    tc::cp_async_wait<0>();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem, 128);
 }
 
 // ---------------------------------------------------------------- L2L for one level
@@ -608,6 +815,7 @@ void tc_init_attributes() {
     cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
     cudaFuncSetAttribute(k_l2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2P_SMEM);
+    cudaFuncSetAttribute(k_m2l_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PIPE_SMEM);
     done = true;
 }
 
@@ -621,9 +829,14 @@ void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, 
                                                                  F.O.l2p_img + F.O.l2p_off[level], out, err);
 }
 
-void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st) {
+void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
+                bool pipelined) {
     if (nV <= 0) return;
     tc_init_attributes();
+    if (pipelined) {
+        k_m2l_tc_pipe<<<152, 128, PIPE_SMEM, st>>>(F, Pd, images, err);
+        return;
+    }
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;
     k_m2l_tc<<<grid, 128, TC_SMEM, st>>>(F, Pd, images, err);
 }

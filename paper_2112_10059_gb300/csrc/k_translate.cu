@@ -221,6 +221,13 @@ __global__ void k_vpairs_close(PairsDev Pd, const int *tot_pairs, const int *tot
     }
 }
 
+// tile -> key table (tiles of a key are consecutive)
+__global__ void k_vpairs_tile_keys(PairsDev Pd) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Pd.nkeys) return;
+    for (int t = Pd.tile_off[k]; t < Pd.tile_off[k] + Pd.tile_cnt[k]; ++t) Pd.tile_key[t] = k;
+}
+
 void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cudaStream_t st) {
     cudaMemsetAsync(Pd.cnt, 0, sizeof(int) * Pd.nkeys, st);
     cudaMemsetAsync(Pd.cursor, 0, sizeof(int) * Pd.nkeys, st);
@@ -230,6 +237,7 @@ void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cu
     k_vpairs_tiles<<<(Pd.nkeys + 255) / 256, 256, 0, st>>>(Pd);
     scan_exclusive(Pd.tile_cnt, Pd.tile_off, Pd.nkeys, Pd.total_tiles, scan_tmp, st);
     k_vpairs_close<<<1, 32, 0, st>>>(Pd, Pd.total_tiles + 1, Pd.total_tiles);
+    k_vpairs_tile_keys<<<(Pd.nkeys + 255) / 256, 256, 0, st>>>(Pd);
 }
 
 // One CTA per tile of up to 64 V pairs sharing (level, offset): d_B += M2L_{l,o} u_A, scatter-added.
@@ -242,14 +250,7 @@ __global__ void __launch_bounds__(256) k_m2l_pairs(FmmDev F, PairsDev Pd) {
     const int np = F.O.npad, n = F.O.n;
     const int tile = blockIdx.x;
     if (tile >= Pd.tile_off[Pd.nkeys]) return;
-    if (tid == 0) {   // key with tile_off[key] <= tile < tile_off[key + 1]
-        int lo = 0, hi = Pd.nkeys;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (Pd.tile_off[mid] <= tile) lo = mid; else hi = mid;
-        }
-        s_key = lo;
-    }
+    if (tid == 0) s_key = Pd.tile_key[tile];
     __syncthreads();
     const int key = s_key;
     const int level = key / NSLOT, slot = key % NSLOT;

@@ -84,6 +84,7 @@ struct sph_ctx {
     bool l2p_simt = false;            // FP32 SIMT L2P even when the tensor-core images exist
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
+    bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -491,7 +492,8 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     ENS(c->b_work, (3 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     const int nV = c->list_tot[1];
     const int nkeys = (c->Lmax + 1) * NSLOT;
-    ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1)) * sizeof(int));
+    const size_t max_tiles = (size_t)std::max(nV, 1) / 64 + nkeys + 1;
+    ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1) + max_tiles) * sizeof(int));
     ENS(c->b_scan, scan_tmp_ints(nkeys + 1) * sizeof(int) + 64);
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
@@ -522,6 +524,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     Pd.tile_cnt = pb + 3 * nkeys + 1; Pd.tile_off = pb + 4 * nkeys + 1;
     Pd.total_tiles = pb + 5 * nkeys + 2;
     Pd.trg = pb + 5 * nkeys + 8; Pd.src = Pd.trg + std::max(nV, 1);
+    Pd.tile_key = Pd.src + std::max(nV, 1);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
     tc_init_attributes();
@@ -565,7 +568,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         if (tm) tm->mark_at(5, c->stream);
         if (S.tc) {
             CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));
-            fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream);
+            fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream, c->m2l_pipe);
         } else {
             fmm_m2l_pairs(F, S.Pd, nV, c->m2l_prec, c->stream);
         }
@@ -860,6 +863,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->p2p_in_leaf = parent->p2p_in_leaf;
     sub->l2p_simt = parent->l2p_simt;
     sub->l2p_tc_tables = parent->l2p_tc_tables;
+    sub->m2l_pipe = parent->m2l_pipe;
     sub->launches = 0;
     return SPH_OK;
 }
@@ -1198,6 +1202,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_P2P_IN_LEAF")) c->p2p_in_leaf = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
+    if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {

@@ -190,6 +190,7 @@ struct PairsDev {
     int *tile_cnt, *tile_off;   // [nkeys], [nkeys + 1]
     int *trg, *src;       // [nV]
     int *total_tiles;     // [1]
+    int *tile_key;        // [nV / 64 + nkeys]: key of every tile (one load instead of a search per CTA)
 };
 void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cudaStream_t st);
 void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cudaStream_t st);
@@ -198,7 +199,8 @@ bool tc_supported(const OpsDev &O);
 void tc_init_attributes();
 size_t tc_image_elems(int count);
 void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st);
-void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st);
+void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
+                bool pipelined = false);
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
                       int *err, cudaStream_t st);
 void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,

@@ -321,6 +321,23 @@ def test_tensor_core_translations(sph, pi):
     ctc.close()
 
 
+@pytest.mark.parametrize("pi", [1, 2])
+def test_pipelined_m2l_matches_per_tile(sph, monkeypatch, pi):
+    """The persistent pipelined tensor-core M2L equals the one-CTA-per-tile kernel (same
+    products; only the order of the reductions into the targets differs)."""
+    p = _problems()[pi]
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("SPH_M2L_PIPE", flag)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        outs.append(out.cpu().numpy().astype(np.float64))
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs[1][T], outs[0][T]) < 1e-6
+    _check_fmm(outs[1], ref, T, "m2l pipelined")
+
+
 def test_l2l_eight_children_per_cta(sph, monkeypatch):
     """Tensor-core L2L with all 8 child operators streamed through one CTA equals the
     one-child-per-CTA kernel (same products, different scheduling)."""
