@@ -91,6 +91,7 @@ typedef struct sph_stats {
     int64_t n_launches;        /* kernels launched by this eval (operator precompute excluded) */
     int32_t far_method, far_order;
     int32_t leaf_size;         /* leaf size of the tree (set_criteria's, or the autotuner's choice) */
+    int32_t near_table;        /* 1 if the near field used the table form */
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -122,8 +123,8 @@ int set_targets(sph_ctx *ctx, const float *emag_dev, const uint8_t *mask_dev);
  * i_frac in [0,1] (0: every cell is a source); e_frac in [0,1];
  * e_applied in the units of |E|; self_mode 0 (no self term) or 1 (ball);
  * leaf_size in [0, 4096]: the octree splits a box holding more sources or more
- * targets than this; 0 = autotune (the first eval of each problem shape times the
- * candidates 32, 64 and 512 and keeps the fastest for the life of the context);
+ * targets than this; 0 = autotune (the first eval of each problem class times the
+ * candidates 32, 64, 128 and 512 and keeps the fastest for the life of the context);
  * m2l_precision one of SPH_M2L_*. */
 int set_criteria(sph_ctx *ctx, double i_frac, double e_frac, double e_applied,
                  int self_mode, int leaf_size, int m2l_precision);
@@ -132,6 +133,14 @@ int set_criteria(sph_ctx *ctx, double i_frac, double e_frac, double e_applied,
  * [2, 8] (p^3 nodes per box), surface order in [3, 10] (points per cube edge).
  * Default: SPH_FAR_CHEBYSHEV, 5.  Takes effect at the next eval. */
 int sph_set_far_field(sph_ctx *ctx, int method, int order);
+
+/* Near field (Eq. nearfar, the exact part): SPH_NEAR_EXP evaluates the kernel with its
+ * exponentials for every source-target pair (default); SPH_NEAR_TABLE reads G for the integer
+ * squared cell offsets below 4096 from a table built per evaluation with the same arithmetic
+ * (uniform grids make every offset an integer); SPH_NEAR_AUTO times both on the first eval
+ * of each problem class and keeps the faster.  Takes effect at the next eval. */
+enum { SPH_NEAR_EXP = 0, SPH_NEAR_TABLE = 1, SPH_NEAR_AUTO = 2 };
+int sph_set_near_field(sph_ctx *ctx, int mode);
 
 /* Evaluate S_ph by the adaptive FMM into s_dev (float[nx*ny*nz], device):
  * S_ph at every target, 0 at every other cell.  stats may be NULL. */

@@ -19,7 +19,8 @@ import threading
 
 import numpy as np
 
-__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "eval_sph",
+__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "set_near_field",
+           "eval_sph",
            "eval_sph_host", "eval_direct", "eval_sph_batch", "BatchProblem", "get_selection", "get_tree", "load",
            "SphError", "M2L_F32", "M2L_BF16X3", "Stats"]
 
@@ -49,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("ms_upward", ctypes.c_float), ("ms_vpairs", ctypes.c_float), ("ms_m2l", ctypes.c_float),
                 ("ms_l2l", ctypes.c_float), ("ms_l2p", ctypes.c_float),
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
-                ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32)]
+                ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("near_table", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,7 +76,7 @@ class Problem(ctypes.Structure):
 
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
-           "set_criteria", "sph_set_far_field", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
+           "set_criteria", "sph_set_far_field", "sph_set_near_field", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
            "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version",
            # learned surrogate (include/sph_nn.h)
            "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
@@ -84,6 +86,7 @@ EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sourc
 
 FAR_CHEBYSHEV = 0
 FAR_SURFACE = 1
+NEAR_EXP, NEAR_TABLE, NEAR_AUTO = 0, 1, 2
 
 
 def load(path: str | None = None):
@@ -107,6 +110,7 @@ def load(path: str | None = None):
         lib.set_targets.argtypes = [V, V, V]
         lib.set_criteria.argtypes = [V, D, D, D, I, I, I]
         lib.sph_set_far_field.argtypes = [V, I, I]
+        lib.sph_set_near_field.argtypes = [V, I]
         lib.eval_sph.argtypes = [V, V, V]
         lib.eval_sph_batch.argtypes = [V, I, ctypes.POINTER(Problem), V]
         lib.eval_sph_host.argtypes = [V, V, V, V, V, V]
@@ -141,7 +145,8 @@ def load(path: str | None = None):
                   "sph_nn_forward", "sph_nn_backward", "sph_nn_adam", "sph_nn_train_step", "sph_nn_make_inputs",
                   "sph_nn_make_target", "sph_pool_avg", "sph_nn_conv3d", "sph_nn_conv3d_wgrad", "eval_sph_surrogate"):
             getattr(lib, f).restype = I
-        for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field", "eval_sph",
+        for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field",
+                  "sph_set_near_field", "eval_sph",
                   "eval_sph_batch", "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I
         _lib = lib
@@ -233,6 +238,12 @@ def set_criteria(ctx: Context, i_frac=0.0, e_frac=0.0, e_applied=0.0, self_mode=
 def set_far_field(ctx: Context, method=FAR_CHEBYSHEV, order=5):
     """Far-field representation: FAR_CHEBYSHEV (order p, p^3 nodes) or FAR_SURFACE (order = points per edge)."""
     ctx._ck(ctx.lib.sph_set_far_field(ctx.h, int(method), int(order)))
+
+
+def set_near_field(ctx: Context, mode=NEAR_EXP):
+    """Near-field form: NEAR_EXP (kernel evaluated per pair), NEAR_TABLE (table of G over the
+    integer squared cell offsets), NEAR_AUTO (timed on the first eval of a problem class)."""
+    ctx._ck(ctx.lib.sph_set_near_field(ctx.h, int(mode)))
 
 
 def eval_sph(ctx: Context, out=None, stats: bool = False):

@@ -749,30 +749,54 @@ struct P2PConst {
     float wself;         // G_self h^3 / C  (self term, in the scaled weight units)
 };
 
+// the scaled kernel g(s^2) of the near-field sum (see above); d2 > 0
 template <bool TAYLOR>
+__device__ __forceinline__ float p2p_g(float d2, const P2PConst &K) {
+    const float rs = rsqrt_approx(fmaxf(d2, 1e-12f));
+    const float sdist = d2 * rs;
+    const float e1 = ex2_approx(-K.k1 * sdist);
+    const float em = TAYLOR ? one_minus_exp_neg(K.bma_h * sdist, K.k2 * sdist) : 1.f - ex2_approx(-K.k2 * sdist);
+    return e1 * em * (rs * rs * rs);
+}
+
+// TABLE: the offsets of point sources are integers; g is read from the shared-memory table
+// for d2 < GTAB_N (values computed by p2p_g itself, so the sums are the same).
+template <bool TAYLOR, bool TABLE>
 __device__ __forceinline__ float p2p_sum(const float4 *__restrict__ pts, int lo, int hi, float tx, float ty,
-                                         float tz, const P2PConst &K) {
+                                         float tz, const P2PConst &K, const float *__restrict__ tab) {
     float a = 0.f;
 #pragma unroll 4
     for (int j = lo; j < hi; ++j) {
         const float4 sp = pts[j];
         const float dx = tx - sp.x, dy = ty - sp.y, dz = tz - sp.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rs = rsqrt_approx(fmaxf(d2, 1e-12f));
-        const float sdist = d2 * rs;
-        const float e1 = ex2_approx(-K.k1 * sdist);
-        const float em = TAYLOR ? one_minus_exp_neg(K.bma_h * sdist, K.k2 * sdist) : 1.f - ex2_approx(-K.k2 * sdist);
-        const float g = d2 > 0.f ? e1 * em * (rs * rs * rs) : K.wself;
+        float g;
+        if (TABLE) {
+            const int di = (int)d2;
+            g = di < GTAB_N ? tab[di] : p2p_g<TAYLOR>(d2, K);
+        } else {
+            const float gv = p2p_g<TAYLOR>(d2, K);      // computed for every pair, then selected
+            g = d2 > 0.f ? gv : K.wself;
+        }
         a = fmaf(g, sp.w, a);
     }
     return a;
 }
 
 template <bool TAYLOR>
+__global__ void k_near_table(P2PConst K, float *tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < GTAB_N) tab[i] = i == 0 ? K.wself : p2p_g<TAYLOR>((float)i, K);
+}
+
+template <bool TAYLOR, bool TABLE>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
                                                          const int *__restrict__ count, float *__restrict__ out,
                                                          P2PConst K) {
     __shared__ float4 stage[P2P_CAP];
+    __shared__ float tab[TABLE ? GTAB_N : 1];
+    if (TABLE)
+        for (int j = threadIdx.x; j < GTAB_N; j += blockDim.x) tab[j] = F.gtab[j];
     __shared__ int ub[P2P_MAXU], un[P2P_MAXU], uo[P2P_MAXU + 1];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cnt = *count;
@@ -855,8 +879,14 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                     for (int c = warp / G; c < nch; c += groups, ++slot) {
                         const int t = tb + c * 32 + lane;
                         const uint32_t tp = t < te ? F.trg_pc[t] : 0u;
-                        const float a = p2p_sum<TAYLOR>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
-                                                        (float)pc_k(tp), K);
+                        // W-list nodes (pass 1) sit off the lattice: the exp form
+                        float a;
+                        if (TABLE && pass == 0)
+                            a = p2p_sum<TAYLOR, true>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
+                                                      (float)pc_k(tp), K, tab);
+                        else
+                            a = p2p_sum<TAYLOR, false>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
+                                                       (float)pc_k(tp), K, tab);
                         if (slot < 2) acc[slot] += a;
                         else if (t < te)
                             atomicAdd(out + (int64_t)pc_i(tp) +
@@ -877,22 +907,32 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
     }
 }
 
-void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st) {
-    if (nboxes <= 0) return;
-    const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
-    const float log2e = 1.4426950408889634f;
+static P2PConst p2p_const(const FmmDev &F) {
     P2PConst K;
     const float h = F.kp.h;
     K.k1 = F.kp.a2 * h;                       // a2 = alpha log2(e)
     K.k2 = F.kp.b2 * h;                       // b2 = (beta - alpha) log2(e)
     K.bma_h = F.kp.bma * h;
-    K.wself = F.self_mode ? F.kp.gself * h * h * h / F.kp.C : 0.f;
-    (void)log2e;
     // the self weight multiplies the scaled weight w' = w C / h^3: g_self w = (g_self h^3 / C) w'
-    if (K.bma_h >= 0.5f)
-        k_p2p<false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
-    else
-        k_p2p<true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    K.wself = F.self_mode ? F.kp.gself * h * h * h / F.kp.C : 0.f;
+    return K;
+}
+
+void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st) {
+    const P2PConst K = p2p_const(F);
+    if (K.bma_h >= 0.5f) k_near_table<false><<<(GTAB_N + 255) / 256, 256, 0, st>>>(K, gtab);
+    else k_near_table<true><<<(GTAB_N + 255) / 256, 256, 0, st>>>(K, gtab);
+}
+
+void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st) {
+    if (nboxes <= 0) return;
+    const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
+    const P2PConst K = p2p_const(F);
+    const bool taylor = K.bma_h < 0.5f, table = F.gtab != nullptr;
+    if (!taylor && !table) k_p2p<false, false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    else if (taylor && !table) k_p2p<true, false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    else if (!taylor) k_p2p<false, true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    else k_p2p<true, true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {

@@ -85,6 +85,9 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    int near_mode = SPH_NEAR_EXP;     // requested near-field form
+    bool near_table = false;          // resolved for the current evaluation
+    DevBuf b_gtab;
     // buffers
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
@@ -513,6 +516,11 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     F.p2p_separate = c->p2p_in_leaf ? 0 : 1;
     F.l2p_sep = (F.leaf_l2p_done && F.O.method == FAR_CHEB && !c->l2p_simt) ? 1 : 0;
     F.tmask = P<uint8_t>(c->b_tmask);
+    F.gtab = nullptr;
+    if (c->near_table && F.p2p_separate) {
+        ENS(c->b_gtab, GTAB_N * sizeof(float));
+        F.gtab = P<float>(c->b_gtab);
+    }
     S.w_src = P<int>(c->b_work);
     S.w_leaf = S.w_src + std::max(nb, 1);
     S.w_p2p = S.w_leaf + std::max(nb, 1);
@@ -622,6 +630,10 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
     c->launches += nb > 0;
     if (F.p2p_separate) {
+        if (F.gtab) {
+            fmm_near_table(F, const_cast<float *>(F.gtab), c->stream);
+            ++c->launches;
+        }
         fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 33, out, c->stream);
         c->launches += nb > 0;
     }
@@ -667,6 +679,7 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
     stats->far_method = c->far_method;
     stats->far_order = c->far_order;
     stats->leaf_size = c->leaf_eff;
+    stats->near_table = c->near_table ? 1 : 0;
 }
 
 // The passes queued as one CUDA graph: captured on the context's private capture stream (the
@@ -774,6 +787,56 @@ int autotune_leaf(sph_ctx *c, float *out) {
     return SPH_OK;
 }
 
+// Near-field form for this evaluation: fixed, or (SPH_NEAR_AUTO) the faster of the two,
+// timed like the leaf size and cached per problem class.
+int resolve_near(sph_ctx *c, float *out) {
+    if (c->near_mode != SPH_NEAR_AUTO) {
+        c->near_table = c->near_mode == SPH_NEAR_TABLE;
+        return SPH_OK;
+    }
+    const std::string key = tune_key(c) + "|near|" + std::to_string(c->leaf_eff);
+    std::map<std::string, int> &cache = c->tune_owner ? c->tune_owner->tune_cache : c->tune_cache;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        c->near_table = it->second != 0;
+        return SPH_OK;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int choice = 0;
+    for (int table = 0; table < 2; ++table) {
+        c->near_table = table != 0;
+        int r = fmm_after_select(c, out, nullptr);
+        float tot = 0.f;
+        for (int rep = 0; rep < 2 && !r; ++rep) {
+            CK(cudaEventRecord(e0, c->stream));
+            r = fmm_after_select(c, out, nullptr);
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (r) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r;
+        }
+        if (tot < best) {
+            best = tot;
+            choice = table;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
+    cache[key] = choice;
+    c->near_table = choice != 0;
+    return SPH_OK;
+}
+
 int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     PhaseTimer tm;
     tm.start(stats != nullptr, c->stream);
@@ -802,6 +865,8 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     } else {
         c->leaf_eff = c->leaf_size;
     }
+    r = resolve_near(c, out);
+    if (r) return r;
     r = fmm_after_select(c, out, &tm);
     if (r) return r;
     if (stats) {
@@ -864,6 +929,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_simt = parent->l2p_simt;
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
+    sub->near_mode = parent->near_mode;
     sub->launches = 0;
     return SPH_OK;
 }
@@ -928,6 +994,10 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
             if (r) return sub_fail(c, sub, r, i);
         } else {
             sub->leaf_eff = sub->leaf_size;
+        }
+        {
+            int r = resolve_near(sub, probs[i].s_dev);
+            if (r) return sub_fail(c, sub, r, i);
         }
     }
     // phases 2-3: trees, list counts, list fills -- two more synchronisations
@@ -1236,7 +1306,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
-                     &c->h_s, &c->b_tmask, &c->b_near, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
+                     &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);
@@ -1323,6 +1393,14 @@ int eval_sph(sph_ctx *c, float *s_dev, sph_stats *stats) {
     if (r) return r;
     if (!s_dev) return fail(c, SPH_EINVAL, "s_dev is NULL");
     return run_fmm(c, s_dev, stats);
+}
+
+int sph_set_near_field(sph_ctx *c, int mode) {
+    if (!c) return SPH_EINVAL;
+    if (mode != SPH_NEAR_EXP && mode != SPH_NEAR_TABLE && mode != SPH_NEAR_AUTO)
+        return fail(c, SPH_EINVAL, "near-field mode must be SPH_NEAR_EXP, SPH_NEAR_TABLE or SPH_NEAR_AUTO");
+    c->near_mode = mode;
+    return SPH_OK;
 }
 
 int eval_sph_batch(sph_ctx *c, int n, const sph_problem *problems, sph_stats *stats) {

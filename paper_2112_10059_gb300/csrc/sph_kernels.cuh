@@ -157,6 +157,7 @@ struct FmmDev {
     int p2p_separate;    // 1: the U-list near field runs in k_p2p (after k_leaf), not in k_leaf
     int l2p_sep;         // 1: leaves without a table get their L2P from k_l2p_sep (before k_leaf)
     const uint8_t *tmask;   // [nx*ny*nz] 1 at targets (tensor-core L2P of partly selected leaves)
+    const float *gtab;      // optional near-field table: g(d2) for integer squared offsets d2 < GTAB_N
     float wscale;
     KParams kp;
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
@@ -179,6 +180,8 @@ void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, 
 __host__ __device__ int l2p_tile_n(int edge);
 void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st);
 void fmm_init_attributes();
+constexpr int GTAB_N = 4096;           // table of the scaled kernel for squared cell offsets 0 .. 4095
+void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st);
 size_t l2p_image_elems(int edge);
 void make_l2p_images(const float *etab, int edge, int n, uint16_t *img, cudaStream_t st);
 void fmm_m2l_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);

@@ -400,3 +400,60 @@ def test_argument_errors(sph):
         sph.set_far_field(c, sph.FAR_CHEBYSHEV, 9)
     with pytest.raises(sph.SphError):
         sph.set_far_field(c, 7, 5)
+
+
+def test_demand_oriented_targets_line_and_section(sph):
+    """Strategy 2 as a demand (Section 4): targets on a cross-section and a line only."""
+    import torch
+    p = si.streamer(n=64, box=0.5, chan_len=0.25, i_frac=1e-3, targets_all=True, leaf_size=32, seed=41,
+                    name="s64_demand")
+    n = p.nx
+    mask = np.zeros((n, n, n), np.uint8)            # (z, y, x)
+    mask[n // 2, :, :] = 1                          # cross-section z = const
+    mask[:, n // 2, n // 2] = 1                     # line along z through the centre
+    mask = mask.ravel()
+    c = sph.Context(0)
+    _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, mask=mask, stats=True)
+    J, T = oracle.select(p.q, None, mask, p.i_frac)
+    assert st.n_targets == T.size == n * n + n - 1
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, *oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max), p.q,
+                     p.source_scale, J, T)
+    _check_fmm(out.cpu().numpy(), ref, T, "demand line + section")
+
+
+def test_applied_field_target_rule(sph):
+    """Section 5 target rule with an applied field: |E| >= E_app + e_frac (max|E| - E_app)."""
+    p = si.streamer(n=48, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.005, e_applied=50.0,
+                    targets_all=False, leaf_size=32, seed=42, name="s48_eapp")
+    c = sph.Context(0)
+    _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+    J, T = sph.get_selection(c)
+    Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    assert np.array_equal(J, Jo) and np.array_equal(T, To)
+    assert 0 < T.size < p.ncell
+    ref, _, _ = oracle.sph_problem(p)
+    _check_fmm(out.cpu().numpy(), ref, T, "applied field rule")
+
+
+@pytest.mark.parametrize("pi", [1, 2])
+def test_near_field_table_equals_exp(sph, pi):
+    """The tabulated near field (integer squared offsets) gives the exp form's sums: the table
+    holds the same kernel values; only reduction order may differ."""
+    p = _problems()[pi]
+    outs = {}
+    for mode in (sph.NEAR_EXP, sph.NEAR_TABLE, sph.NEAR_AUTO):
+        c = sph.Context(0)
+        sph.set_near_field(c, mode)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+        outs[mode] = (out.cpu().numpy().astype(np.float64), st.near_table)
+        if mode == sph.NEAR_AUTO:
+            _, out2, st2 = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+            assert st2.near_table == st.near_table          # cached choice
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert outs[sph.NEAR_EXP][1] == 0 and outs[sph.NEAR_TABLE][1] == 1
+    assert oracle.rel_l2(outs[sph.NEAR_TABLE][0][T], outs[sph.NEAR_EXP][0][T]) < 1e-6
+    assert oracle.rel_l2(outs[sph.NEAR_AUTO][0][T], outs[sph.NEAR_EXP][0][T]) < 1e-6
+    _check_fmm(outs[sph.NEAR_TABLE][0], ref, T, "near table")
+    with pytest.raises(sph.SphError):
+        sph.set_near_field(sph.Context(0), 7)
