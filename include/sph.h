@@ -92,6 +92,7 @@ typedef struct sph_stats {
     int32_t far_method, far_order;
     int32_t leaf_size;         /* leaf size of the tree (set_criteria's, or the autotuner's choice) */
     int32_t near_table;        /* 1 if the near field used the table form */
+    int64_t n_w_skipped;       /* (target, W box) pairs skipped by strategy 3 (sph_set_skip_ratio) */
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -141,6 +142,15 @@ int sph_set_far_field(sph_ctx *ctx, int method, int order);
  * of each problem class and keeps the faster.  Takes effect at the next eval. */
 enum { SPH_NEAR_EXP = 0, SPH_NEAR_TABLE = 1, SPH_NEAR_AUTO = 2 };
 int sph_set_near_field(sph_ctx *ctx, int mode);
+
+/* Strategy 3 of Section 3 (third approach): after the far field, the leaf itself and the
+ * leaves adjacent to it have been summed for a target, the non-adjacent near boxes (W list,
+ * Chebyshev far field) are skipped for that target when their bounded contribution
+ * G(d_min) * sum of their I_h is below r_s times that estimate (d_min: distance from the
+ * target cell to the box's nearest cell).  r_s in [0, 1); 0 (default) turns it off; the paper
+ * uses 1e-4 in its streamer simulations (Section 5).  Applies to leaves with at most 256
+ * targets. */
+int sph_set_skip_ratio(sph_ctx *ctx, double r_s);
 
 /* Evaluate S_ph by the adaptive FMM into s_dev (float[nx*ny*nz], device):
  * S_ph at every target, 0 at every other cell.  stats may be NULL. */

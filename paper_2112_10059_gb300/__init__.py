@@ -19,7 +19,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "set_near_field",
+__all__ = ["Context", "set_grid", "set_sources", "set_targets", "set_criteria", "set_far_field", "set_near_field", "set_skip_ratio",
            "eval_sph",
            "eval_sph_host", "eval_direct", "eval_sph_batch", "BatchProblem", "get_selection", "get_tree", "load",
            "SphError", "M2L_F32", "M2L_BF16X3", "Stats"]
@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("ms_l2l", ctypes.c_float), ("ms_l2p", ctypes.c_float),
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
                 ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
-                ("near_table", ctypes.c_int32)]
+                ("near_table", ctypes.c_int32), ("n_w_skipped", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,7 +76,7 @@ class Problem(ctypes.Structure):
 
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
-           "set_criteria", "sph_set_far_field", "sph_set_near_field", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
+           "set_criteria", "sph_set_far_field", "sph_set_near_field", "sph_set_skip_ratio", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
            "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version",
            # learned surrogate (include/sph_nn.h)
            "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
@@ -111,6 +111,7 @@ def load(path: str | None = None):
         lib.set_criteria.argtypes = [V, D, D, D, I, I, I]
         lib.sph_set_far_field.argtypes = [V, I, I]
         lib.sph_set_near_field.argtypes = [V, I]
+        lib.sph_set_skip_ratio.argtypes = [V, D]
         lib.eval_sph.argtypes = [V, V, V]
         lib.eval_sph_batch.argtypes = [V, I, ctypes.POINTER(Problem), V]
         lib.eval_sph_host.argtypes = [V, V, V, V, V, V]
@@ -146,7 +147,7 @@ def load(path: str | None = None):
                   "sph_nn_make_target", "sph_pool_avg", "sph_nn_conv3d", "sph_nn_conv3d_wgrad", "eval_sph_surrogate"):
             getattr(lib, f).restype = I
         for f in ("sph_create", "set_grid", "set_sources", "set_targets", "set_criteria", "sph_set_far_field",
-                  "sph_set_near_field", "eval_sph",
+                  "sph_set_near_field", "sph_set_skip_ratio", "eval_sph",
                   "eval_sph_batch", "eval_sph_host", "eval_direct", "sph_get_selection", "sph_get_tree"):
             getattr(lib, f).restype = I
         _lib = lib
@@ -244,6 +245,11 @@ def set_near_field(ctx: Context, mode=NEAR_EXP):
     """Near-field form: NEAR_EXP (kernel evaluated per pair), NEAR_TABLE (table of G over the
     integer squared cell offsets), NEAR_AUTO (timed on the first eval of a problem class)."""
     ctx._ck(ctx.lib.sph_set_near_field(ctx.h, int(mode)))
+
+
+def set_skip_ratio(ctx: Context, r_s=0.0):
+    """Strategy 3: skip W boxes whose bounded share of a target's S_ph is below r_s (0 = off)."""
+    ctx._ck(ctx.lib.sph_set_skip_ratio(ctx.h, float(r_s)))
 
 
 def eval_sph(ctx: Context, out=None, stats: bool = False):

@@ -795,6 +795,9 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                                                          P2PConst K) {
     __shared__ float4 stage[P2P_CAP];
     __shared__ float tab[TABLE ? GTAB_N : 1];
+    __shared__ int4 ubox[P2P_MAXU];        // W boxes: lowest cell corner, edge (strategy 3)
+    __shared__ float uwt[P2P_MAXU];        // W boxes: total scaled weight
+    __shared__ float usum[P2P_WARPS * 2][32];   // U-list sums per (chunk, lane) (strategy 3)
     if (TABLE)
         for (int j = threadIdx.x; j < GTAB_N; j += blockDim.x) tab[j] = F.gtab[j];
     __shared__ int ub[P2P_MAXU], un[P2P_MAXU], uo[P2P_MAXU + 1];
@@ -815,9 +818,31 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
         float acc[2] = {0.f, 0.f};        // the first two chunks of this warp; further chunks flush per round
         // pass 0: U list (point sources); pass 1: W list (Chebyshev nodes of the W boxes)
         const int passes = F.O.method == FAR_CHEB ? 2 : 1;     // the surface form keeps M2P in k_leaf
+        // strategy 3 applies to leaves whose every chunk stays in this warp's two sum slots
+        const bool skip3 = F.r_s > 0.f && nch <= 2 * groups && F.L.w_off[b + 1] > F.L.w_off[b];
+        float sest[2] = {0.f, 0.f};
         for (int pass = 0; pass < passes; ++pass) {
             const int l0 = pass == 0 ? F.L.u_off[b] : F.L.w_off[b];
             const int l1 = pass == 0 ? F.L.u_off[b + 1] : F.L.w_off[b + 1];
+            if (pass == 1 && skip3) {
+                // S_est = far field already in out (L2P) + the leaf's whole U-list sum
+                __syncthreads();
+                for (int j = tid; j < P2P_WARPS * 2 * 32; j += blockDim.x) (&usum[0][0])[j] = 0.f;
+                __syncthreads();
+                int sl = 0;
+                for (int c = warp / G; c < nch && sl < 2; c += groups, ++sl) atomicAdd(&usum[c][lane], acc[sl]);
+                __syncthreads();
+                sl = 0;
+                for (int c = warp / G; c < nch && sl < 2; c += groups, ++sl) {
+                    const int t = tb + c * 32 + lane;
+                    float far = 0.f;
+                    if (t < te) {
+                        const uint32_t tp = F.trg_pc[t];
+                        far = out[(int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp))];
+                    }
+                    sest[sl] = far + usum[c][lane];
+                }
+            }
             for (int ub0 = l0; ub0 < l1; ub0 += P2P_MAXU) {
                 const int nu = min(P2P_MAXU, l1 - ub0);
                 __syncthreads();
@@ -830,6 +855,15 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                     } else {
                         ub[tid] = A;
                         un[tid] = n;
+                        if (F.r_s > 0.f) {
+                            const int asz = 1 << (F.D - T.b_level[A]);
+                            uint32_t ax, ay, az;
+                            demorton3(T.b_key[A], ax, ay, az);
+                            ubox[tid] = make_int4((int)ax * asz, (int)ay * asz, (int)az * asz, asz);
+                            float wsum = 0.f;
+                            for (int m = 0; m < n; ++m) wsum += F.ueq[(size_t)A * np + m];
+                            uwt[tid] = wsum * usc;
+                        }
                     }
                 }
                 __syncthreads();
@@ -879,6 +913,35 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                     for (int c = warp / G; c < nch; c += groups, ++slot) {
                         const int t = tb + c * 32 + lane;
                         const uint32_t tp = t < te ? F.trg_pc[t] : 0u;
+                        if (pass == 1 && skip3) {
+                            // W box by W box: a lane drops box j when G(d_min) * sum(I_h) < r_s * S_est
+                            const int tx = pc_i(tp), ty = pc_j(tp), tz = pc_k(tp);
+                            float a = 0.f;
+                            unsigned long long skipped = 0;
+                            for (int j = 0; j < nu; ++j) {
+                                const int lo = max(uo[j] - r0, s_lo), hi = min(uo[j + 1] - r0, s_hi);
+                                if (lo >= hi) continue;
+                                const int4 bx = ubox[j];
+                                const int ex = max(0, max(bx.x - tx, tx - (bx.x + bx.w - 1)));
+                                const int ey = max(0, max(bx.y - ty, ty - (bx.y + bx.w - 1)));
+                                const int ez = max(0, max(bx.z - tz, tz - (bx.z + bx.w - 1)));
+                                const float d2 = (float)(ex * ex + ey * ey + ez * ez);
+                                const bool drop = t < te && p2p_g<TAYLOR>(fmaxf(d2, 1.f), K) * uwt[j] <
+                                                                 F.r_s * sest[slot < 2 ? slot : 1];
+                                skipped += drop;
+                                if (__all_sync(0xffffffffu, drop || t >= te)) continue;
+                                const float part = p2p_sum<TAYLOR, false>(stage, lo, hi, (float)tx, (float)ty,
+                                                                          (float)tz, K, tab);
+                                if (!drop) a += part;
+                            }
+                            if (skipped && F.skip_count) atomicAdd(F.skip_count, skipped);
+                            if (slot < 2) acc[slot] += a;
+                            else if (t < te)
+                                atomicAdd(out + (int64_t)pc_i(tp) +
+                                              (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
+                                          a);
+                            continue;
+                        }
                         // W-list nodes (pass 1) sit off the lattice: the exp form
                         float a;
                         if (TABLE && pass == 0)

@@ -86,6 +86,8 @@ struct sph_ctx {
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     int near_mode = SPH_NEAR_EXP;     // requested near-field form
+    double r_s = 0.0;                 // strategy 3 ratio (0: off)
+    DevBuf b_skip;
     bool near_table = false;          // resolved for the current evaluation
     DevBuf b_gtab;
     // buffers
@@ -517,6 +519,9 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     F.l2p_sep = (F.leaf_l2p_done && F.O.method == FAR_CHEB && !c->l2p_simt) ? 1 : 0;
     F.tmask = P<uint8_t>(c->b_tmask);
     F.gtab = nullptr;
+    F.r_s = (float)c->r_s;
+    ENS(c->b_skip, 2 * sizeof(unsigned long long));
+    F.skip_count = P<unsigned long long>(c->b_skip);
     if (c->near_table && F.p2p_separate) {
         ENS(c->b_gtab, GTAB_N * sizeof(float));
         F.gtab = P<float>(c->b_gtab);
@@ -630,6 +635,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
     c->launches += nb > 0;
     if (F.p2p_separate) {
+        CK(cudaMemsetAsync(F.skip_count, 0, sizeof(unsigned long long), c->stream));
         if (F.gtab) {
             fmm_near_table(F, const_cast<float *>(F.gtab), c->stream);
             ++c->launches;
@@ -680,6 +686,11 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
     stats->far_order = c->far_order;
     stats->leaf_size = c->leaf_eff;
     stats->near_table = c->near_table ? 1 : 0;
+    if (c->b_skip.p) {
+        unsigned long long k = 0;
+        if (cudaMemcpy(&k, c->b_skip.p, sizeof k, cudaMemcpyDeviceToHost) == cudaSuccess) stats->n_w_skipped = (int64_t)k;
+        else cudaGetLastError();
+    }
 }
 
 // The passes queued as one CUDA graph: captured on the context's private capture stream (the
@@ -930,6 +941,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
     sub->near_mode = parent->near_mode;
+    sub->r_s = parent->r_s;
     sub->launches = 0;
     return SPH_OK;
 }
@@ -1306,7 +1318,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
-                     &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
+                     &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)
         if (b->p) cudaFree(b->p);
@@ -1393,6 +1405,13 @@ int eval_sph(sph_ctx *c, float *s_dev, sph_stats *stats) {
     if (r) return r;
     if (!s_dev) return fail(c, SPH_EINVAL, "s_dev is NULL");
     return run_fmm(c, s_dev, stats);
+}
+
+int sph_set_skip_ratio(sph_ctx *c, double r_s) {
+    if (!c) return SPH_EINVAL;
+    if (!(r_s >= 0.0 && r_s < 1.0)) return fail(c, SPH_EINVAL, "r_s must be in [0, 1)");
+    c->r_s = r_s;
+    return SPH_OK;
 }
 
 int sph_set_near_field(sph_ctx *c, int mode) {

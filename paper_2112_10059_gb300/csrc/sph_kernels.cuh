@@ -158,6 +158,8 @@ struct FmmDev {
     int l2p_sep;         // 1: leaves without a table get their L2P from k_l2p_sep (before k_leaf)
     const uint8_t *tmask;   // [nx*ny*nz] 1 at targets (tensor-core L2P of partly selected leaves)
     const float *gtab;      // optional near-field table: g(d2) for integer squared offsets d2 < GTAB_N
+    float r_s;              // strategy 3 (skip W boxes whose bounded share is below r_s S_est); 0 = off
+    unsigned long long *skip_count;   // (target, W box) pairs skipped by strategy 3
     float wscale;
     KParams kp;
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths

@@ -457,3 +457,32 @@ def test_near_field_table_equals_exp(sph, pi):
     _check_fmm(outs[sph.NEAR_TABLE][0], ref, T, "near table")
     with pytest.raises(sph.SphError):
         sph.set_near_field(sph.Context(0), 7)
+
+
+@pytest.mark.parametrize("r_s", [1e-4, 1e-2])
+def test_strategy3_skips_within_its_bound(sph, r_s):
+    """Strategy 3 (Section 3): a W box is dropped for a target only when G(d_min) times its
+    total I_h is below r_s times the target's estimate (far field + own and adjacent leaves),
+    so the result moves by less than r_s times the number of W boxes of the leaf, relatively.
+    r_s = 0 changes nothing."""
+    p = _problems()[1]                          # the W/X-heavy case
+    res = {}
+    for rs in (0.0, r_s):
+        c = sph.Context(0)
+        sph.set_skip_ratio(c, rs)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+        res[rs] = (out.cpu().numpy().astype(np.float64), st.n_w_skipped)
+        tree = sph.get_tree(c)
+        c.close()
+    S0, S1 = res[0.0][0], res[r_s][0]
+    assert res[0.0][1] == 0
+    W = tree["W"]
+    assert len(W) > 0
+    nmax = int(np.bincount(W[:, 0]).max())
+    T = np.flatnonzero(S0 != 0)
+    rel = np.abs(S1[T] - S0[T]) / S0[T]
+    assert rel.max() <= nmax * r_s, (rel.max(), nmax, res[r_s][1])
+    if r_s >= 1e-2:
+        assert res[r_s][1] > 0
+    with pytest.raises(sph.SphError):
+        sph.set_skip_ratio(sph.Context(0), -1.0)
