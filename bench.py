@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-snapshot batched evaluation")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and judging the learned surrogate")
+    ap.add_argument("--sweep", action="store_true",
+                    help="Section 4.3 trade-off: FMM time and E_V against the full FP64 sum for I_pct 1e-4 .. 1e-1")
     ap.add_argument("--sur-samples", type=int, default=2000, help="FMM solves in the surrogate's training set")
     ap.add_argument("--sur-epochs", type=int, default=10)
     return ap.parse_args()
@@ -440,6 +442,35 @@ def run_surrogate(sph, torch, dev, stream, args, peaks):
             "full_fmm_ms": full_ms, "judged": judged}
 
 
+def run_sweep(sph, torch, dev, stream, args):
+    """I_pct trade-off (Eq. sourcepct): a spherical Gaussian (sigma = 8 cells, every cell a
+    target) in a 2:2:1 box (128 x 128 x 64) and an elongated box (32 x 32 x 176), at pO2 = 150
+    and 10 Torr.  Per I_pct: FMM step time (CUDA events, library timer) and E_V, the relative
+    L2 error over 2000 sampled targets against the FP64 sum over every cell."""
+    import oracle
+    rows = []
+    for shape in ((128, 128, 64), (32, 32, 176)):
+        for po2 in (150.0, 10.0):
+            p = si.gaussian_box(*shape, sigma_cells=8.0, h=1.25e-3, pO2_torr=po2)
+            a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+            samp = np.sort(np.random.default_rng(11).choice(p.ncell, 2000, replace=False)).astype(np.int32)
+            full = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale,
+                              np.arange(p.ncell, dtype=np.int32), samp)
+            for f in (0.0, 1e-4, 1e-3, 1e-2, 1e-1):
+                p.i_frac = f
+                c = sph.Context(dev.index or 0, stream)
+                ctx_, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+                ms = []
+                for _ in range(3):
+                    _, st = sph.eval_sph(c, out, stats=True)
+                    ms.append(st.ms_total)
+                S = out.cpu().numpy().astype(np.float64)[samp]
+                rows.append({"box": list(shape), "pO2_torr": po2, "I_pct": f, "n_sources": int(st.n_sources),
+                             "ms": statistics.median(ms), "E_V_percent": 100.0 * oracle.rel_l2(S, full)})
+                c.close()
+    return rows
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -562,6 +593,8 @@ def main():
     if not args.no_batch:
         batch = run_batch(sph, torch, dev, stream, args, prec)
 
+    sweep = run_sweep(sph, torch, dev, stream, args) if args.sweep else None
+
     surrogate = None
     if not args.no_surrogate:
         surrogate = run_surrogate(sph, torch, dev, stream, args, measured_peaks())
@@ -589,7 +622,7 @@ def main():
                                         "ms_l2p", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
-                "direct_fp32": direct, "accuracy": acc, "batch": batch, "surrogate": surrogate, "cpu_baseline": cpu}
+                "direct_fp32": direct, "accuracy": acc, "batch": batch, "surrogate": surrogate, "sweep": sweep, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

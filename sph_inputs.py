@@ -299,6 +299,19 @@ def fields_torch(n, box, geom, device="cuda", with_efield=True):
     return (q * I0).float().reshape(-1).contiguous(), em
 
 
+def gaussian_box(nx, ny, nz, sigma_cells=8.0, h=1.25e-3, pO2_torr=150.0, center=None, name=None):
+    """One spherical Gaussian emission exp(-|r - r0|^2 / sigma^2), sigma = sigma_cells * h, in an
+    nx x ny x nz box of cell edge h (cm), r0 the box centre unless given; every cell a target.
+    The pressure is given through the O2 partial pressure (Section 4.2 form)."""
+    X, Y, Z = _grid(nx, ny, nz, h)
+    sig = sigma_cells * h
+    c = center if center is not None else (nx * h / 2, ny * h / 2, nz * h / 2)
+    q = np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / sig ** 2)
+    p_torr = pO2_torr * 760.0 / 150.0
+    return Problem(name or "gaussian_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, h, (0.0, 0.0, 0.0), p_torr, pO2_torr,
+                   _f32(q * I0), None, scale_of(p_torr), targets_all=True, leaf_size=64)
+
+
 def random_mask(n_cells: int, frac: float, seed: int) -> np.ndarray:
     """uint8 mask with each cell set with probability ``frac`` (SplitMix64 stream)."""
     return (uniform01(seed, n_cells) < frac).astype(np.uint8)
