@@ -237,6 +237,16 @@ int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny, int nz, co
                        double e_applied, uint32_t *src_key_dev, uint32_t *src_pc_dev, float *src_q_dev,
                        uint32_t *trg_key_dev, uint32_t *trg_pc_dev, int32_t *counts_dev);
 
+/* Exclusive prefix sum of int32 counts: the building block that numbers the octree's boxes
+ * (scan of the per-slot existence flags of Section 2.4's adaptive tree) and lays out the
+ * interaction lists (scan of the per-box list lengths) -- the same one-launch device scan
+ * the tree phase runs.  out_dev[i] = sum_{j<i} in_dev[j] (int32, wrapping), *total_dev =
+ * sum of all n.  in_dev, out_dev: device int32[n], distinct; total_dev: device int32[1];
+ * 0 <= n < 2^31.  Allocates its scratch and synchronises the stream.  SPH_ETIMEOUT if a
+ * tile gave up waiting for its predecessors (the results are then not valid). */
+int sph_scan_i32(int device, void *cuda_stream, int64_t n, const int32_t *in_dev, int32_t *out_dev,
+                 int32_t *total_dev);
+
 /* Library version string. */
 const char *sph_version(void);
 

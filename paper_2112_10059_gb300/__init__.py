@@ -77,7 +77,7 @@ class Problem(ctypes.Structure):
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
            "set_criteria", "sph_set_far_field", "sph_set_near_field", "sph_set_skip_ratio", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
-           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_version",
+           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_scan_i32", "sph_version",
            # learned surrogate (include/sph_nn.h)
            "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
            "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads", "sph_nn_forward", "sph_nn_backward",
@@ -121,6 +121,8 @@ def load(path: str | None = None):
         lib.sph_version.restype = ctypes.c_char_p
         lib.sph_select_noalloc.argtypes = [I, V, I, I, I, V, V, V, D, D, D, V, V, V, V, V, V]
         lib.sph_select_noalloc.restype = I
+        lib.sph_scan_i32.argtypes = [I, V, I64, V, V, V]
+        lib.sph_scan_i32.restype = I
         PD, PF = ctypes.POINTER(ctypes.c_double), ctypes.c_float
         lib.sph_nn_create.argtypes = [ctypes.POINTER(V), I, V, I, I]
         lib.sph_nn_destroy.argtypes = [V]
@@ -371,6 +373,23 @@ def get_tree(ctx: Context):
     ctx._ck(ctx.lib.sph_get_tree(ctx.h, ctypes.byref(tv)))
     out["leaf"] = out["leaf"].astype(bool)
     return out
+
+
+def scan_i32(x):
+    """Exclusive prefix sum of a CUDA int32 tensor through the library's device scan:
+    (out, total) with out[i] = sum of x[:i] (int32 wrap-around) and total = sum of x."""
+    import torch
+    lib = load()
+    if x.dtype != torch.int32:
+        raise ValueError("expected an int32 tensor")
+    out = torch.empty_like(x)
+    total = torch.empty(1, dtype=torch.int32, device=x.device)
+    st = torch.cuda.current_stream(x.device)
+    rc = lib.sph_scan_i32(int(x.device.index or 0), ctypes.c_void_p(st.cuda_stream), x.numel(), _ptr(x),
+                          _ptr(out), _ptr(total))
+    if rc != 0:
+        raise SphError(rc, "sph_scan_i32 failed")
+    return out, int(total.item())
 
 
 def solve(problem, ctx: Context | None = None, m2l_precision=M2L_F32, leaf_size=None, stats=False,

@@ -1,15 +1,15 @@
-// Morton octree over the selected points and its interaction lists
-// (paper Section 2.4: "each leaf cube contains no more than a prescribed number
-// of points"; Eq. nearfar's near / far split; the recursive far-field hierarchy).
+// Morton octree over the selected points and its interaction lists (Section 2.4: leaves
+// bounded in point count, the near / far split of Eq. nearfar, the recursive far-field
+// hierarchy).
 //
-// Build: the grid is embedded in a 2^D cube of cells.  Level l has a dense
-// array box_at[l][key] (8^l entries, -1 = no box) so every neighbour lookup is
-// one load.  Level by level (top-down):
-//   k_tree_flags  : for every child slot of a split parent, binary-search the
-//                   Morton-sorted point keys for the child's [begin, end) ranges;
+// Build: the grid is embedded in a 2^D cube of cells.  Level l has a dense array
+// box_at[l][key] (8^l entries, -1 = no box), so every neighbour lookup is one load.
+//   k_tree_ranges : one pass over the Morton-sorted keys gives every dense slot of every
+//                   level its [begin, end) point range (sources and targets);
+//   k_tree_exists : a slot holds a box iff it has points and its parent was split;
 //   scan          : exclusive scan of the existence flags -> canonical index
 //                   (boxes ordered by (level, key));
-//   k_tree_emit   : write the compact box records and box_at[l].
+//   k_tree_emit_all : the compact box records, box_at and the per-slot source flag.
 // A box splits iff it holds more than S sources or more than S targets and its
 // level is below D.  All of it is integer arithmetic, so the tree is
 // bit-identical to the oracle's.
@@ -19,100 +19,182 @@
 //   V: same level >= 2, parents adjacent, A not adjacent to B; offset code kept;
 //   W: B leaf, A finer with sources, parent(A) adjacent to B, A not adjacent;
 //   X: A leaf with sources, coarser than B, A adjacent to parent(B), not to B.
-// k_lists<false> counts, a scan gives CSR offsets, k_lists<true> fills.
+// k_lists<false> counts, one scan gives the four CSR offset arrays, k_lists<true> fills.
 #include "sph_kernels.cuh"
 
 namespace sph {
 
 // ------------------------------------------------------------ device-wide scan
-constexpr int SCAN_T = 1024, SCAN_PER = 4, SCAN_TILE = SCAN_T * SCAN_PER;
+// One launch per scan (up to four arrays of the same length at once, blockIdx.y).  A CTA
+// scans a tile of SCAN_TILE ints staged through shared memory; tiles find their offset by
+// decoupled look-back in ticket order (state word: 2-bit status | 32-bit value), or, for
+// short arrays, one CTA per array walks every tile with a running carry.
+constexpr int SCAN_T = 1024, SCAN_PER = 8, SCAN_TILE = SCAN_T * SCAN_PER;
+constexpr int SCAN_SMALL = 4 * SCAN_TILE;          // one CTA per array up to this length
+constexpr unsigned SCAN_WAIT_LIMIT = 1u << 20;
+constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62;
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int *__restrict__ in, int n, int *__restrict__ bsum) {
-    int base = blockIdx.x * SCAN_TILE;
-    int s = 0;
+struct ScanSet {
+    const int *in[4];
+    int *out[4];
+    int *total[4];
+};
+
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
+// Exclusive scan of one tile staged through shared memory: returns the tile's sum (every
+// thread), leaves the thread's exclusive prefix in *pre and its SCAN_PER elements in v.
+__device__ __forceinline__ int tile_scan(const int *__restrict__ in, int base, int n, int *sh, int *ws,
+                                         int (&v)[SCAN_PER], int *pre) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
     for (int u = 0; u < SCAN_PER; ++u) {
-        int i = base + u * SCAN_T + threadIdx.x;
-        if (i < n) s += in[i];
+        const int i = u * SCAN_T + tid;
+        sh[spad(i)] = base + i < n ? in[base + i] : 0;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ int ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        s = ws[threadIdx.x];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) bsum[blockIdx.x] = s;
-    }
-}
-
-// exclusive scan of bsum[0..nb) in place by one CTA; total -> *total
-__global__ void __launch_bounds__(SCAN_T) k_scan_top(int *__restrict__ bsum, int nb, int *__restrict__ total) {
-    __shared__ int sh[SCAN_T];
-    int per = (nb + SCAN_T - 1) / SCAN_T;
-    int beg = threadIdx.x * per, end = min(nb, beg + per);
-    int r = 0;
-    for (int i = beg; i < end; ++i) r += bsum[i];
-    sh[threadIdx.x] = r;
-    __syncthreads();
-    for (int o = 1; o < SCAN_T; o <<= 1) {
-        int v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int x = sh[threadIdx.x] - r;
-    for (int i = beg; i < end; ++i) { int v = bsum[i]; bsum[i] = x; x += v; }
-    if (threadIdx.x == SCAN_T - 1 && total) *total = sh[SCAN_T - 1];
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_final(const int *__restrict__ in, int *__restrict__ out, int n,
-                                                       const int *__restrict__ bsum) {
-    __shared__ int ws[32];
-    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
-    int v[SCAN_PER];
     int s = 0;
+#pragma unroll
     for (int u = 0; u < SCAN_PER; ++u) {
-        int i = base + u;
-        v[u] = i < n ? in[i] : 0;
+        v[u] = sh[spad(tid * SCAN_PER + u)];
         s += v[u];
     }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int inc = s;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += t;
     }
     if (lane == 31) ws[w] = inc;
     __syncthreads();
     if (w == 0) {
         int t = ws[lane];
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, t, o);
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
         ws[lane] = t;
     }
     __syncthreads();
-    int x = bsum[blockIdx.x] + (w ? ws[w - 1] : 0) + inc - s;
+    *pre = (w ? ws[w - 1] : 0) + inc - s;
+    return ws[31];
+}
+
+// The tile's exclusive prefixes (offset x added) written back through shared memory, coalesced.
+__device__ __forceinline__ void tile_store(int *__restrict__ out, int base, int n, int *sh, const int (&v)[SCAN_PER],
+                                           int x) {
+    const int tid = threadIdx.x;
+    __syncthreads();
+#pragma unroll
     for (int u = 0; u < SCAN_PER; ++u) {
-        int i = base + u;
-        if (i < n) out[i] = x;
+        sh[spad(tid * SCAN_PER + u)] = x;
         x += v[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SCAN_PER; ++u) {
+        const int i = u * SCAN_T + tid;
+        if (base + i < n) out[base + i] = sh[spad(i)];
     }
 }
 
-size_t scan_tmp_ints(int n) { return (size_t)(n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+__global__ void __launch_bounds__(SCAN_T) k_scan_small(ScanSet S, int n) {
+    __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
+    __shared__ int ws[32];
+    const int a = blockIdx.y;
+    int carry = 0;
+    for (int base = 0; base < n; base += SCAN_TILE) {
+        int v[SCAN_PER], pre;
+        const int sum = tile_scan(S.in[a], base, n, sh, ws, v, &pre);
+        tile_store(S.out[a], base, n, sh, v, carry + pre);
+        carry += sum;
+        __syncthreads();      // ws / sh are reused by the next tile
+    }
+    if (threadIdx.x == 0) *S.total[a] = carry;
+}
 
-// out[i] = sum_{j<i} in[j]; *total = sum (device).  tmp: scan_tmp_ints(n) ints.
-void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st) {
+// state: per array ntiles + 1 words (the last one is the ticket), zeroed before the launch.
+// A tile that gives up waiting for a predecessor counts it as zero (its prefixes stay in
+// [0, true prefix], so indices derived from them stay in bounds) and sets bit 0 of *err.
+__global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int ntiles,
+                                                         unsigned long long *__restrict__ state, int *err) {
+    __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
+    __shared__ int ws[32];
+    __shared__ int s_tile, s_pre;
+    const int a = blockIdx.y, tid = threadIdx.x;
+    unsigned long long *st = state + (size_t)a * (ntiles + 1);
+    if (tid == 0) s_tile = (int)atomicAdd(st + ntiles, 1ull);
+    __syncthreads();
+    const int tile = s_tile, base = tile * SCAN_TILE;
+    int v[SCAN_PER], pre;
+    const int sum = tile_scan(S.in[a], base, n, sh, ws, v, &pre);
+    if (tid < 32) {
+        if (tid == 0) atomicExch(st + tile, (tile == 0 ? ST_INC : ST_AGG) | (unsigned)sum);
+        __syncwarp();
+        // warp 0 walks back 32 predecessors at a time; the nearest inclusive state ends the walk
+        unsigned run = 0;
+        bool gave_up = false;
+        for (int j = tile - 1; j >= 0; j -= 32) {
+            const int idx = j - tid;
+            unsigned long long w = ST_INC;   // before tile 0: an inclusive zero
+            unsigned k = 0;
+            for (; k < SCAN_WAIT_LIMIT; ++k) {
+                if (idx >= 0) w = *((volatile unsigned long long *)(st + idx));
+                if (__all_sync(0xffffffffu, (w >> 62) != 0)) break;
+                __nanosleep(32);
+            }
+            if (k == SCAN_WAIT_LIMIT) {
+                gave_up = true;
+                break;
+            }
+            const unsigned inc_mask = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+            const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+            unsigned c = (tid <= stop && idx >= 0) ? (unsigned)w : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            run += c;
+            if (inc_mask) break;
+        }
+        if (tid == 0) {
+            if (gave_up && err) atomicOr(err, 1);
+            if (tile > 0) atomicExch(st + tile, ST_INC | (unsigned)(run + (unsigned)sum));
+            s_pre = (int)run;
+            if (tile == ntiles - 1) *S.total[a] = (int)run + sum;
+        }
+    }
+    __syncthreads();
+    tile_store(S.out[a], base, n, sh, v, s_pre + pre);
+}
+
+size_t scan_tmp_ints(int n) {
+    const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return 2 * 4 * ((size_t)ntiles + 1) + 16;
+}
+
+// out_k[i] = sum_{j<i} in_k[j]; *total_k = sum (device), for k <= 4 arrays of length n.
+// tmp: scan_tmp_ints(n) ints, 8-byte aligned; err (optional): bit 0 set if a look-back gave up.
+void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cudaStream_t st) {
     if (n <= 0) {
-        cudaMemsetAsync(total, 0, sizeof(int), st);
+        for (int a = 0; a < k; ++a) cudaMemsetAsync(S.total[a], 0, sizeof(int), st);
         return;
     }
-    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<nb, SCAN_T, 0, st>>>(in, n, tmp);
-    k_scan_top<<<1, SCAN_T, 0, st>>>(tmp, nb, total);
-    k_scan_final<<<nb, SCAN_T, 0, st>>>(in, out, n, tmp);
+    if (n <= SCAN_SMALL) {
+        k_scan_small<<<dim3(1, k), SCAN_T, 0, st>>>(S, n);
+        return;
+    }
+    const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    unsigned long long *state = reinterpret_cast<unsigned long long *>(tmp);
+    cudaMemsetAsync(state, 0, sizeof(unsigned long long) * k * (ntiles + 1), st);
+    k_scan_onepass<<<dim3(ntiles, k), SCAN_T, 0, st>>>(S, n, ntiles, state, err);
+}
+
+void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err) {
+    ScanSet S{};
+    S.in[0] = in;
+    S.out[0] = out;
+    S.total[0] = total;
+    scan_exclusive_multi(S, 1, n, tmp, err, st);
 }
 
 // ------------------------------------------------------------ tree build
@@ -127,22 +209,68 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
 // Point ranges of every dense slot of every level in one pass over the Morton-sorted keys:
 // point i opens the range of its slot at level l when point i-1 lies in another slot of
 // that level, and closes it when point i+1 does.  Untouched slots keep [0, 0).
-__global__ void k_tree_ranges(int n, const uint32_t *__restrict__ key, int D, int Lmax, int *__restrict__ beg,
-                              int *__restrict__ end) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t k = key[i];
+// Four keys per thread (one 16-byte load), neighbours through warp shuffles.  A key whose
+// finest slot (level Lmax) matches both neighbours' -- all but about one in 8^(D-Lmax) --
+// costs a few integer operations; the boundary writes are queued in shared memory and
+// carried out by the whole block, so that no warp runs them one lane at a time.
+constexpr int RANGE_PER = 4, RANGE_T = 256;
+
+__global__ void __launch_bounds__(RANGE_T) k_tree_ranges(int n, const uint32_t *__restrict__ key, int D, int Lmax,
+                                                         int *__restrict__ beg, int *__restrict__ end) {
+    __shared__ uint32_t task_key[2 * RANGE_PER * RANGE_T];
+    __shared__ int task_val[2 * RANGE_PER * RANGE_T];
+    __shared__ uint8_t task_lvl[2 * RANGE_PER * RANGE_T];   // first level | 0x80 for an end
+    __shared__ int ntask;
+    const int t = blockIdx.x * RANGE_T + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long i0 = (long long)t * RANGE_PER;
+    if (threadIdx.x == 0) ntask = 0;
+    uint32_t k[RANGE_PER];
+    if (i0 + RANGE_PER <= n) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(key + i0);
+        k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < RANGE_PER; ++u) k[u] = i0 + u < n ? key[i0 + u] : 0u;
+    }
+    // every lane takes part in the shuffles; lanes past the end only supply values nobody uses
+    uint32_t prev = __shfl_up_sync(0xffffffffu, k[RANGE_PER - 1], 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+    if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? key[i0 - 1] : 0u;
+    if (lane == 31) next = (i0 + RANGE_PER < n) ? key[i0 + RANGE_PER] : 0u;
+    __syncthreads();
+    const int fine = 3 * (D - Lmax);
     // two keys fall in different slots of level l iff their highest differing bit b (0-based)
-    // satisfies b >= 3 (D - l), i.e. for every l >= D - b / 3; only those levels are written
-    auto first_level = [&](uint32_t other) {
-        const int b = 31 - __clz(k ^ other);
-        const int l0 = D - b / 3;
-        return l0 < 0 ? 0 : l0;
-    };
-    const int lb = i == 0 ? 0 : first_level(key[i - 1]);
-    const int le = i + 1 == n ? 0 : first_level(key[i + 1]);
-    for (int l = lb; l <= Lmax; ++l) beg[dense_off(l) + (k >> (3 * (D - l)))] = i;
-    for (int l = le; l <= Lmax; ++l) end[dense_off(l) + (k >> (3 * (D - l)))] = i + 1;
+    // satisfies b >= 3 (D - l), i.e. for every l >= D - b / 3
+    auto first_level = [&](uint32_t x, uint32_t o) { return max(0, D - (31 - __clz(x ^ o)) / 3); };
+#pragma unroll
+    for (int u = 0; u < RANGE_PER; ++u) {
+        const long long i = i0 + u;
+        if (i >= n) break;
+        const uint32_t p = u == 0 ? prev : k[u - 1];
+        const uint32_t q = u == RANGE_PER - 1 ? next : k[u + 1];
+        if (i == 0 || ((k[u] ^ p) >> fine) != 0) {
+            const int s = atomicAdd(&ntask, 1);
+            task_key[s] = k[u];
+            task_val[s] = (int)i;
+            task_lvl[s] = (uint8_t)(i == 0 ? 0 : first_level(k[u], p));
+        }
+        if (i + 1 == n || ((k[u] ^ q) >> fine) != 0) {
+            const int s = atomicAdd(&ntask, 1);
+            task_key[s] = k[u];
+            task_val[s] = (int)i + 1;
+            task_lvl[s] = (uint8_t)(0x80 | (i + 1 == n ? 0 : first_level(k[u], q)));
+        }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < ntask; s += RANGE_T) {
+        const uint32_t kk = task_key[s];
+        const int val = task_val[s];
+        const int l0 = task_lvl[s] & 0x7f;
+        int *out = (task_lvl[s] & 0x80) ? end : beg;
+        int64_t off = dense_off(l0);
+        for (int l = l0; l <= Lmax; ++l, off = 8 * off + 1) out[off + (kk >> (3 * (D - l)))] = val;
+    }
 }
 
 __device__ __forceinline__ int level_of_slot(int64_t s, int Lmax) {
@@ -175,7 +303,8 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
                                 const int *__restrict__ pos, const int *__restrict__ rsb,
                                 const int *__restrict__ rse, const int *__restrict__ rtb,
                                 const int *__restrict__ rte, const int *__restrict__ total,
-                                const uint32_t *__restrict__ skey, int ns, const uint32_t *__restrict__ tkey, int nt) {
+                                const uint32_t *__restrict__ skey, int ns, const uint32_t *__restrict__ tkey, int nt,
+                                uint8_t *__restrict__ vsrc) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= Lmax) {       // level table (threads 0..Lmax)
         const int l = (int)s;
@@ -187,6 +316,7 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
     if (s >= nslot) return;
     if (!flag[s]) {
         T.box_at[s] = -1;
+        vsrc[s] = 0;
         return;
     }
     const int l = level_of_slot(s, Lmax);
@@ -204,6 +334,7 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
     T.b_tb[idx] = tb; T.b_te[idx] = te;
     T.b_parent[idx] = l > 0 ? pos[dense_off(l - 1) + (m >> 3)] : -1;
     T.b_leaf[idx] = !(l < D && (se - sb > S || te - tb > S));
+    vsrc[s] = se > sb;
 }
 
 // occ[s] = 1 if the slot's region holds a source point, or lies inside a leaf that holds
@@ -255,14 +386,15 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
     cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
     cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
-    if (A.ns > 0) k_tree_ranges<<<(A.ns + 255) / 256, 256, 0, st>>>(A.ns, A.skey, A.D, A.Lmax, A.rsb, A.rse);
-    if (A.nt > 0) k_tree_ranges<<<(A.nt + 255) / 256, 256, 0, st>>>(A.nt, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
+    constexpr int RB = RANGE_T * RANGE_PER;
+    if (A.ns > 0) k_tree_ranges<<<(A.ns + RB - 1) / RB, RANGE_T, 0, st>>>(A.ns, A.skey, A.D, A.Lmax, A.rsb, A.rse);
+    if (A.nt > 0) k_tree_ranges<<<(A.nt + RB - 1) / RB, RANGE_T, 0, st>>>(A.nt, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
     k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
-    scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st);
+    scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);
     k_tree_emit_all<<<grid, 256, 0, st>>>(A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
-                                          A.rte, total, A.skey, A.ns, A.tkey, A.nt);
+                                          A.rte, total, A.skey, A.ns, A.tkey, A.nt, A.vsrc);
     const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
     if (npar > 0 && A.occ && A.near) {
         const int g2 = (int)((npar + 255) / 256);
@@ -328,14 +460,14 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                         int qx = B.x + dx, qy = B.y + dy, qz = B.z + dz;
                         int n = 1 << l;
                         if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
-                        int A = lookup(T, l, qx, qy, qz);
+                        const uint32_t m = morton3(qx, qy, qz);
+                        const int A = T.box_at[dense_off(l) + m];
+                        const bool hs_a = T.vsrc[dense_off(l) + m];
                         if (A >= 0) {
-                            if (T.b_se[A] <= T.b_sb[A]) continue;   // no sources anywhere below A
+                            if (!hs_a) continue;   // no sources anywhere below A
                             if (T.b_leaf[A]) {
-                                if (T.b_se[A] > T.b_sb[A]) {
-                                    if (FILL) L.u_src[pU] = A;
-                                    ++pU; ++nU;
-                                }
+                                if (FILL) L.u_src[pU] = A;
+                                ++pU; ++nU;
                             } else {
                                 int sp = 0;
                                 // push children of the colleague
@@ -369,10 +501,11 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                             }
                         } else {
                             for (int m = l - 1; m >= 0; --m) {
-                                int sh = l - m;
-                                int Am = lookup(T, m, qx >> sh, qy >> sh, qz >> sh);
+                                const int sh = l - m;
+                                const int64_t sl = dense_off(m) + morton3(qx >> sh, qy >> sh, qz >> sh);
+                                const int Am = T.box_at[sl];
                                 if (Am >= 0) {
-                                    if (T.b_leaf[Am] && T.b_se[Am] > T.b_sb[Am]) {
+                                    if (T.vsrc[sl] && T.b_leaf[Am]) {
                                         bool dup = false;
                                         for (int u = 0; u < ncoarse; ++u) dup |= coarse[u] == Am;
                                         if (!dup) coarse[ncoarse++] = Am;
@@ -400,12 +533,13 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                         int qx = cx + dx, qy = cy + dy, qz = cz + dz;
                         if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
                         for (int m = l - 1; m >= 0; --m) {
-                            int sh = l - 1 - m;
-                            int Am = lookup(T, m, qx >> sh, qy >> sh, qz >> sh);
+                            const int sh = l - 1 - m;
+                            const int64_t sl = dense_off(m) + morton3(qx >> sh, qy >> sh, qz >> sh);
+                            const int Am = T.box_at[sl];
+                            const bool hs = T.vsrc[sl];
                             if (Am >= 0) {
-                                bool hs = T.b_se[Am] > T.b_sb[Am];
                                 if (m == l - 1) parent_near_src |= hs;
-                                if (T.b_leaf[Am] && hs) {
+                                if (hs && T.b_leaf[Am]) {
                                     BoxGeom G = geom_of(T, Am);
                                     if (!adjacent(G, B, D)) {
                                         bool dup = false;
@@ -422,25 +556,41 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
                 ++pX; ++nX;
             }
         }
-        // ---- V (children of the parent's neighbours that hold sources)
+        // ---- V (children of the parent's neighbours that hold sources): 6^3 candidates around
+        // the parent, minus the 3^3 adjacent to B; one byte per candidate slot decides
         if (l >= 2 && parent_near_src) {
-            int px = (B.x >> 1) << 1, py = (B.y >> 1) << 1, pz = (B.z >> 1) << 1;
-            for (int dz = -2; dz <= 3; ++dz)
-                for (int dy = -2; dy <= 3; ++dy)
-                    for (int dx = -2; dx <= 3; ++dx) {
-                        int qx = px + dx, qy = py + dy, qz = pz + dz;
-                        int ox = qx - B.x, oy = qy - B.y, oz = qz - B.z;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                        int A = lookup(T, l, qx, qy, qz);
-                        if (A >= 0 && T.b_se[A] > T.b_sb[A]) {
+            const int n = 1 << l;
+            const int px = B.x & ~1, py = B.y & ~1, pz = B.z & ~1;
+            const uint8_t *vs = T.vsrc + dense_off(l);
+            const int *ba = T.box_at + dense_off(l);
+            uint32_t sx[6];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) sx[d] = spread3((uint32_t)(px - 2 + d));
+            for (int dz = 0; dz < 6; ++dz) {
+                const int qz = pz - 2 + dz, oz = qz - B.z;
+                if (qz < 0 || qz >= n) continue;
+                const uint32_t mz = spread3((uint32_t)qz) << 2;
+                for (int dy = 0; dy < 6; ++dy) {
+                    const int qy = py - 2 + dy, oy = qy - B.y;
+                    if (qy < 0 || qy >= n) continue;
+                    const bool near_yz = abs(oy) <= 1 && abs(oz) <= 1;
+                    const uint32_t myz = (spread3((uint32_t)qy) << 1) | mz;
+#pragma unroll
+                    for (int dx = 0; dx < 6; ++dx) {
+                        const int qx = px - 2 + dx, ox = qx - B.x;
+                        if (qx < 0 || qx >= n || (near_yz && abs(ox) <= 1)) continue;
+                        const uint32_t m = sx[dx] | myz;
+                        if (vs[m]) {
                             if (FILL) {
-                                L.v_src[pV] = A;
+                                L.v_src[pV] = ba[m];
                                 L.v_trg[pV] = b;
                                 L.v_oc[pV] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
                             }
                             ++pV; ++nV;
                         }
                     }
+                }
+            }
         }
     }
     if (!FILL) {
@@ -449,16 +599,17 @@ __global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
 }
 
 void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
-                        int *totals /* device [4] */, cudaStream_t st) {
+                        int *totals /* device [4] */, int *err, cudaStream_t st) {
     if (nboxes <= 0) {
         cudaMemsetAsync(totals, 0, 4 * sizeof(int), st);
         return;
     }
     k_lists<false><<<(nboxes + 127) / 128, 128, 0, st>>>(T, L, nboxes, D, Lmax);
-    scan_exclusive(L.u_cnt, L.u_off, nboxes, totals + 0, scan_tmp, st);
-    scan_exclusive(L.v_cnt, L.v_off, nboxes, totals + 1, scan_tmp, st);
-    scan_exclusive(L.w_cnt, L.w_off, nboxes, totals + 2, scan_tmp, st);
-    scan_exclusive(L.x_cnt, L.x_off, nboxes, totals + 3, scan_tmp, st);
+    ScanSet S{};
+    S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;
+    S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
+    for (int a = 0; a < 4; ++a) S.total[a] = totals + a;
+    scan_exclusive_multi(S, 4, nboxes, scan_tmp, err, st);
 }
 
 __global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ totals) {

@@ -264,6 +264,7 @@ TreeDev tree_dev(sph_ctx *c) {
     T.b_parent = P<int>(c->b_parent);
     T.b_leaf = P<uint8_t>(c->b_leaf);
     T.near = c->Lmax >= 1 ? P<uint8_t>(c->b_near) + dense_off(c->Lmax + 1) : nullptr;
+    T.vsrc = P<uint8_t>(c->b_near) + 2 * dense_off(c->Lmax + 1);
     return T;
 }
 
@@ -282,7 +283,7 @@ ListDev list_dev(sph_ctx *c) {
 
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
-// [44..48) list totals, [48] tensor-core error flags
+// [43] scan give-up flag, [44..48) list totals, [48] tensor-core error flags
 int tree_queue(sph_ctx *c) {
     const int D = c->D;
     int S = c->leaf_eff;
@@ -295,7 +296,7 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_flag, dense_total * sizeof(int));
     ENS(c->b_pos, (dense_total + 1) * sizeof(int));
     ENS(c->b_rng, 4 * dense_total * sizeof(int));
-    ENS(c->b_near, 2 * dense_total + 16);
+    ENS(c->b_near, 3 * dense_total + 16);
     ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
     ENS(c->b_lvl, 32 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
@@ -311,41 +312,49 @@ int tree_queue(sph_ctx *c) {
     A.skey = P<uint32_t>(c->b_skey); A.tkey = P<uint32_t>(c->b_tkey);
     A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos);
     A.rsb = P<int>(c->b_rng); A.rse = A.rsb + dense_total; A.rtb = A.rse + dense_total; A.rte = A.rtb + dense_total;
-    A.occ = P<uint8_t>(c->b_near); A.near = A.occ + dense_total;
+    A.occ = P<uint8_t>(c->b_near); A.near = A.occ + dense_total; A.vsrc = A.occ + 2 * dense_total;
     A.scan_tmp = P<int>(c->b_scan);
+    A.err = P<int>(c->b_tot) + 3;
+    CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
-    c->launches += 7;
+    // ranges (sources, targets), existence flags, scan, emit, source occupancy and its dilation
+    c->launches += (A.ns > 0) + (A.nt > 0) + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 43, A.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
 // after a sync: level counts -> box count; queue the list counting
 int tree_read_count(sph_ctx *c) {
     const int Lmax = c->Lmax;
+    if (c->pinned[43] != 0) return fail(c, SPH_ETIMEOUT, "the tree scan gave up waiting for a preceding tile");
     c->lvl_count.assign(Lmax + 1, 0);
     c->lvl_base.assign(Lmax + 1, 0);
-    int tot = 0;
+    int64_t tot = 0;
     for (int l = 0; l <= Lmax; ++l) {
         c->lvl_count[l] = c->pinned[8 + 16 + l];
-        c->lvl_base[l] = tot;
+        if (c->lvl_count[l] < 0) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
+        c->lvl_base[l] = (int)tot;
         tot += c->lvl_count[l];
     }
-    c->nboxes = tot;
-    int nb = std::max(tot, 1);
+    if (tot > dense_off(Lmax + 1)) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
+    c->nboxes = (int)tot;
+    int nb = std::max(c->nboxes, 1);
     ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
     ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
     ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
-    lists_count_launch(tree_dev(c), L, tot, c->D, Lmax, P<int>(c->b_scan), ltot, c->stream);
+    lists_count_launch(tree_dev(c), L, c->nboxes, c->D, Lmax, P<int>(c->b_scan), ltot, ltot - 1, c->stream);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned + 44, ltot, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
 // after a sync: list totals -> buffers; queue the list fill
 int lists_fill(sph_ctx *c) {
+    if (c->pinned[43] != 0) return fail(c, SPH_ETIMEOUT, "a list scan gave up waiting for a preceding tile");
     for (int i = 0; i < 4; ++i) c->list_tot[i] = c->pinned[44 + i];
     ENS(c->b_usrc, std::max(1, c->list_tot[0]) * sizeof(int));
     ENS(c->b_vsrc, std::max(1, c->list_tot[1]) * sizeof(int));
@@ -356,7 +365,7 @@ int lists_fill(sph_ctx *c) {
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
     lists_fill_launch(tree_dev(c), L, c->nboxes, c->D, c->Lmax, ltot, c->stream);
-    if (c->nboxes > 0) c->launches += 15;
+    if (c->nboxes > 0) c->launches += 4;   // one scan, close, fill
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
@@ -577,7 +586,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         // needs the parent's d complete, which holds once the level above is done.
         const int nV = c->list_tot[1];
         vpairs_build(F, S.Pd, nV, P<int>(c->b_scan), c->stream);
-        c->launches += 8 + (nV > 0 ? 2 : 0);
+        c->launches += 5 + (nV > 0 ? 2 : 0);
         if (tm) tm->mark_at(5, c->stream);
         if (S.tc) {
             CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));
@@ -1257,6 +1266,38 @@ int eval_sph_surrogate(sph_ctx *c, sph_nn *net, int factor, double tol, int samp
     return run_surrogate(c, net, factor, tol, samples_per_block, seed, use_net ? 1 : 0, out, stats);
 }
 
+
+int sph_scan_i32(int device, void *cuda_stream, int64_t n, const int32_t *in_dev, int32_t *out_dev,
+                 int32_t *total_dev) {
+    if (n < 0 || n > INT32_MAX || !total_dev || (n > 0 && (!in_dev || !out_dev))) return SPH_EINVAL;
+    if (n > 0 && in_dev == out_dev) return SPH_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ECUDA;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t nt = scan_tmp_ints((int)n);
+    int *tmp = nullptr;
+    if (cudaMalloc(&tmp, (nt + 2) * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ENOMEM;
+    }
+    int *err = tmp + nt;
+    int herr = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        scan_exclusive(in_dev, out_dev, (int)n, total_dev, tmp, st, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ECUDA;
+    }
+    return herr ? SPH_ETIMEOUT : SPH_OK;
+}
 
 const char *sph_version(void) { return "libsph 0.1 (sm_103a)"; }
 

@@ -55,6 +55,8 @@ struct TreeDev {
     // near[s], slots of levels 0..Lmax-1: a source point, or a leaf holding sources, lies in
     // the 3x3x3 slots around s.  If not, every list of every child of s is empty.
     const uint8_t *near;
+    // vsrc[s], every slot of every level: a box exists at s and holds sources
+    const uint8_t *vsrc;
 };
 struct TreeArgs {
     TreeDev T;
@@ -63,11 +65,13 @@ struct TreeArgs {
     int *flag, *pos;     // dense scratch over every level's slots, dense_off(Lmax + 1) (+1 for pos)
     int *rsb, *rse, *rtb, *rte;   // dense point ranges of every slot of every level
     uint8_t *occ, *near;          // dense over levels 0..Lmax-1: source occupancy and its 3x3x3 dilation
+    uint8_t *vsrc;                // dense over levels 0..Lmax: box exists and holds sources
     int *scan_tmp;
+    int *err = nullptr;           // bit 0 set if a scan's look-back gave up waiting
 };
 void tree_build_launch(const TreeArgs &A, cudaStream_t st);
 size_t scan_tmp_ints(int n);
-void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st);
+void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err = nullptr);
 
 struct ListDev {
     int *u_cnt, *v_cnt, *w_cnt, *x_cnt;     // [nboxes]
@@ -77,7 +81,7 @@ struct ListDev {
     int *v_trg;                             // target box of each V entry
 };
 void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
-                        int *totals, cudaStream_t st);
+                        int *totals, int *err, cudaStream_t st);
 void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, const int *totals,
                        cudaStream_t st);
 

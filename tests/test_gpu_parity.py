@@ -127,6 +127,20 @@ def test_tree_bit_exact(sph, ctx, case):
         assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
 
 
+@pytest.mark.parametrize("n", [0, 1, 1000, 32768, 32769, 8192 * 37 + 5, 3_000_001])
+def test_device_scan_exact(sph, n):
+    """The one-launch device scan that numbers the boxes and lays out the lists equals the
+    running sum, on both of its paths (one CTA per array up to 32768 elements, look-back
+    across tiles above)."""
+    import torch
+    u = si.uniform01(900 + n % 97, max(n, 1))[:n]
+    x = np.where(u < 0.3, 0, (u * 400).astype(np.int32)).astype(np.int32)   # runs of zeros, as flags have
+    out, total = sph.scan_i32(torch.from_numpy(x).cuda())
+    ref = np.concatenate([[0], np.cumsum(x, dtype=np.int64)])
+    assert total == ref[-1]
+    assert np.array_equal(out.cpu().numpy().astype(np.int64), ref[:-1])
+
+
 def test_direct_fp64_and_fp32_c0(sph, ctx):
     p = si.plain_24()
     sph.solve(p, ctx)
