@@ -332,18 +332,26 @@ size_t ops_etab_floats(int method, int npad, int D, int Lmax) {
     return s;
 }
 
+// level whose boxes have edge 4 and get the composed L2L + L2P images, or -1
+static int l2pc_level(int D, int Lmax) {
+    const int l = D - 2;
+    return (l >= 3 && l <= Lmax && l < 16 && 4 <= ETAB_MAX_EDGE) ? l : -1;
+}
+
 size_t ops_l2p_img_elems(int D, int Lmax) {
     size_t s = 0;
     for (int l = 2; l <= Lmax && l < 16; ++l) {
         int e = edge_of(D, l);
         if (e <= ETAB_MAX_EDGE) s += l2p_image_elems(e);
     }
+    if (l2pc_level(D, Lmax) >= 0) s += 8 * l2p_image_elems(4);
     return s;
 }
 
 void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
     for (int l = 0; l < 16; ++l) O.e_off[l] = -1;
     for (int l = 0; l < 16; ++l) O.l2p_off[l] = -1;
+    O.l2pc_off = -1;
     if (O.method == FAR_CHEB && O.l2p_img) {
         long long off = 0;
         for (int l = 2; l <= Lmax && l < 16; ++l) {
@@ -353,6 +361,7 @@ void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
                 off += (long long)l2p_image_elems(e);
             }
         }
+        if (l2pc_level(D, Lmax) >= 0) O.l2pc_off = off;
     }
     O.uc64 = O.dc64 = nullptr;
     O.pinv_stride = 0;
@@ -555,6 +564,21 @@ static int build_surface(const OpsBuildArgs &A, cudaStream_t st, double C) {
     return 0;
 }
 
+// Composed L2L + L2P tables of a child box of edge 4 (FP64 sums of the FP32 operators):
+//   C_c[k][cell] = sum_i E[i][cell] L2L_c[i][k]
+// E in the L2P table layout [i][cell] (cells of the 4^3 box in local Morton order), L2L_c as
+// stored ([k][i], stride npad), output in the L2P table layout, one [npad][64] block per child.
+__global__ void k_l2p_compose(const float *__restrict__ etab, const float *__restrict__ l2l, int n, int npad,
+                              float *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * n * 64) return;
+    const int cell = idx % 64, k = (idx / 64) % n, c = idx / (64 * n);
+    const float *L = l2l + (size_t)c * npad * npad + (size_t)k * npad;
+    double v = 0.0;
+    for (int i = 0; i < n; ++i) v += (double)etab[(size_t)i * 64 + cell] * (double)L[i];
+    out[(size_t)c * npad * 64 + (size_t)k * 64 + cell] = (float)v;
+}
+
 int ops_build(const OpsBuildArgs &A, cudaStream_t st) {
     const OpsDev &O = A.ops;
     const double C = 1.0 / (4.0 * 3.14159265358979323846 * log(A.beta / A.alpha));
@@ -572,6 +596,19 @@ int ops_build(const OpsBuildArgs &A, cudaStream_t st) {
             for (int l = 2; l <= A.Lmax && l < 16; ++l)
                 if (O.e_off[l] >= 0 && O.l2p_off[l] >= 0)
                     make_l2p_images(O.e_tab + O.e_off[l], edge_of(A.D, l), O.n, O.l2p_img + O.l2p_off[l], st);
+            const int lc = l2pc_level(A.D, A.Lmax);
+            if (lc >= 0 && O.l2pc_off >= 0 && O.e_off[lc] >= 0) {
+                // composed tables [8][npad][64] in the FP64 work array (used as FP32 scratch: the
+                // Chebyshev build keeps nothing there), then their images
+                float *comp = reinterpret_cast<float *>(A.work);
+                const int total = 8 * O.n * 64;
+                k_l2p_compose<<<(total + 255) / 256, 256, 0, st>>>(O.e_tab + O.e_off[lc],
+                                                                    O.l2l_t + (size_t)lc * 8 * O.npad * O.npad,
+                                                                    O.n, O.npad, comp);
+                for (int c = 0; c < 8; ++c)
+                    make_l2p_images(comp + (size_t)c * O.npad * 64, 4, O.n,
+                                    O.l2p_img + O.l2pc_off + (size_t)c * l2p_image_elems(4), st);
+            }
         }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -804,6 +804,233 @@ __global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_beg
     if (r < 32) tc::tmem_dealloc(tmem, 64);
 }
 
+// ---------------------------------------------------------------- L2L + L2P, deepest level
+// Where every box of the level is a leaf of edge 4, the last L2L and the L2P compose: for
+// child c of parent P (cells j of the child, coefficients k)
+//     S(j) = sum_k E[j][k] d_c[k] + sum_k (E L2L_c)[j][k] d_P[k],
+// d_c the child's own local terms (M2L, P2L: its L2L never runs), d_P the parent's complete
+// local expansion.  One CTA takes 128 parents (M = 128, TMEM lane = parent) and all 8
+// children: child c accumulates its 64 cells in TMEM columns [64c, 64c + 64) from two K = 128
+// contractions (parent x composed table, child x table), BF16 hi / lo x3.  Software pipeline
+// per child: the MMAs of child c run while the 256 threads hold child c+1's rows in flight
+// (16 loads each) and write child c's cells; then the rows are split into the operand tile
+// and child c+1's composed table arrives by a bulk copy.
+constexpr uint32_t LP_A = TCM * TCK * 2;               // 32 KiB: 128 rows x 128 coefficients
+constexpr uint32_t LP_B = 64 * TCK * 2;                // 16 KiB: 64 cells x 128 coefficients
+constexpr int LP_T = 256;
+constexpr int LP_V = TCM * (TCK / 4) / LP_T;           // float4 row segments per thread per tile (16)
+constexpr uint32_t LP_SMEM = 1024 + 4 * LP_A + 4 * LP_B + 64 + 17 * TCM * 4;
+
+// rows idx[0..128) of the FP32 state (-1: zero row), 16 float4 per thread, all in flight at once
+__device__ __forceinline__ void lp_load(float4 (&v)[LP_V], const int *idx, const float *__restrict__ state, int np) {
+#pragma unroll
+    for (int u = 0; u < LP_V; ++u) {
+        const int e = threadIdx.x + u * LP_T, j = e / (TCK / 4), q = e % (TCK / 4);
+        const int src = idx[j];
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src >= 0 && 4 * q < np) v[u] = __ldg(reinterpret_cast<const float4 *>(state + (size_t)src * np) + q);
+    }
+}
+__device__ __forceinline__ void lp_store(uint8_t *hi, uint8_t *lo, const float4 (&v)[LP_V]) {
+#pragma unroll
+    for (int u = 0; u < LP_V; ++u) {
+        const int e = threadIdx.x + u * LP_T;
+        put_split4(hi, lo, e / (TCK / 4), 4 * (e % (TCK / 4)), TCM, v[u]);
+    }
+}
+
+__global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int parent_begin, int parent_count,
+                                                     const uint16_t *__restrict__ img_e,
+                                                     const uint16_t *__restrict__ img_c, float *__restrict__ out,
+                                                     int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *ap_hi = base, *ap_lo = base + LP_A, *ac_hi = base + 2 * LP_A, *ac_lo = base + 3 * LP_A;
+    uint8_t *e_hi = base + 4 * LP_A, *e_lo = e_hi + LP_B, *t_hi = e_lo + LP_B, *t_lo = t_hi + LP_B;
+    uint8_t *tail = t_lo + LP_B;
+    uint64_t *bar_e = reinterpret_cast<uint64_t *>(tail);
+    uint64_t *bar_t = bar_e + 1;
+    uint64_t *bar_mma = bar_e + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tail + 24);
+    int *ok_s = reinterpret_cast<int *>(tail + 28);
+    int *spar = reinterpret_cast<int *>(tail + 64);         // [128] parent box or -1
+    int *sch = spar + TCM;                                  // [8][128] child box or -1
+    int *sfull = sch + 8 * TCM;                             // [8][128] child has every cell as target
+    const TreeDev &T = F.T;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int np = F.O.npad;
+    const size_t img_elems = (size_t)2 * 64 * TCK;          // one image: hi then lo
+    int any = 0;
+    if (tid < TCM) {
+        const int i = blockIdx.x * TCM + tid;
+        const int p = parent_begin + i;
+        int P = -1;
+        if (i < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
+        spar[tid] = P;
+        for (int c = 0; c < 8; ++c) {
+            int C = -1, full = 0;
+            if (P >= 0) {
+                const int ch = T.box_at[dense_off(level) + ((T.b_key[P] << 3) | (uint32_t)c)];
+                if (ch >= 0 && T.b_leaf[ch] && T.b_te[ch] > T.b_tb[ch]) {
+                    C = ch;
+                    full = T.b_te[ch] - T.b_tb[ch] == 64;
+                }
+            }
+            sch[c * TCM + tid] = C;
+            sfull[c * TCM + tid] = full;
+            any |= C >= 0;
+        }
+    }
+    if (!__syncthreads_or(any)) return;
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tslot), 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) tc::mbar_init(tc::smem_u32(bar_e + k), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *ok_s = 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    // thread 0's record of what is in flight, for a clean exit after a timeout
+    int t_issued = 0, t_landed = 0, m_issued = 0, m_done = 0;
+    bool e_landed = false;
+    if (tid == 0) {
+        tc::mbar_expect_tx(tc::smem_u32(bar_e), 2 * LP_B);
+        tc::bulk_g2s(tc::smem_u32(e_hi), img_e, LP_B, tc::smem_u32(bar_e));
+        tc::bulk_g2s(tc::smem_u32(e_lo), img_e + LP_B / 2, LP_B, tc::smem_u32(bar_e));
+        tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
+        tc::bulk_g2s(tc::smem_u32(t_hi), img_c, LP_B, tc::smem_u32(bar_t));
+        tc::bulk_g2s(tc::smem_u32(t_lo), img_c + LP_B / 2, LP_B, tc::smem_u32(bar_t));
+        t_issued = 1;
+    }
+    float4 v[LP_V];
+    lp_load(v, spar, F.dchk, np);
+    lp_store(ap_hi, ap_lo, v);
+    lp_load(v, sch, F.dchk, np);
+    lp_store(ac_hi, ac_lo, v);
+    const uint32_t idesc = tc::idesc_bf16_f32(TCM, 64);
+    const int q = warp & 3, r = q * 32 + lane;              // TMEM lane quadrant, parent row
+    const bool vec_ok = (F.nx % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int c = 0; c < 8; ++c) {
+        // (a) operand tiles of child c are in shared memory: MMAs (thread 0)
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && *ok_s) {
+            bool ok = e_landed || tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
+            e_landed = ok;
+            ok = ok && tc::mbar_wait_bounded(tc::smem_u32(bar_t), c & 1, WAIT_LIMIT);
+            if (ok) {
+                ++t_landed;
+                tc::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(64 * c);
+                const uint32_t aph = tc::smem_u32(ap_hi), apl = tc::smem_u32(ap_lo);
+                const uint32_t ach = tc::smem_u32(ac_hi), acl = tc::smem_u32(ac_lo);
+                const uint32_t th = tc::smem_u32(t_hi), tl = tc::smem_u32(t_lo);
+                const uint32_t eh = tc::smem_u32(e_hi), el = tc::smem_u32(e_lo);
+#pragma unroll
+                for (int ks = 0; ks < TCK / 16; ++ks) {
+                    const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+                    const uint32_t bo = tc::sw128_offset(0, 16 * ks, 64);
+                    tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(th + bo), idesc, ks > 0);
+                    tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(tl + bo), idesc, 1);
+                    tc::mma_bf16(d, tc::sdesc_sw128(apl + ao), tc::sdesc_sw128(th + bo), idesc, 1);
+                    tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                    tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
+                    tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                }
+                tc::mma_commit(tc::smem_u32(bar_mma));
+                ++m_issued;
+            } else {
+                atomicOr(err, 4);
+                *ok_s = 0;
+            }
+        }
+        // (b) child c+1's rows in flight while the MMAs run
+        if (c + 1 < 8) lp_load(v, sch + (c + 1) * TCM, F.dchk, np);
+        // (c) MMAs of child c complete: its accumulator is final, the child tile and the table
+        //     buffer are free; child c+1's table starts streaming in
+        if (tid == 0 && *ok_s) {
+            if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), c & 1, WAIT_LIMIT)) {
+                ++m_done;
+                if (c + 1 < 8) {
+                    tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
+                    const uint16_t *src = img_c + (size_t)(c + 1) * img_elems;
+                    tc::bulk_g2s(tc::smem_u32(t_hi), src, LP_B, tc::smem_u32(bar_t));
+                    tc::bulk_g2s(tc::smem_u32(t_lo), src + LP_B / 2, LP_B, tc::smem_u32(bar_t));
+                    ++t_issued;
+                }
+            } else {
+                atomicOr(err, 8);
+                *ok_s = 0;
+            }
+        }
+        __syncthreads();
+        if (!*ok_s) break;
+        tc::fence_after_sync();
+        // (d) child c's cells: warps w and w + 4 share TMEM lanes 32 (w % 4) .. and take half
+        //     of the 64 columns each
+        {
+            const int C = sch[c * TCM + r];
+            const bool full = sfull[c * TCM + r] != 0;
+            int bx = 0, by = 0, bz = 0;
+            if (C >= 0) {
+                uint32_t ux, uy, uz;
+                demorton3(T.b_key[C], ux, uy, uz);
+                bx = (int)ux * 4; by = (int)uy * 4; bz = (int)uz * 4;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c0 = 32 * (warp >> 2) + 16 * h;
+                float w[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * c + c0), w);
+                if (C < 0) continue;
+                if (full && vec_ok) {   // whole box: one 16-byte store per row of 4 cells
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        const int cell = c0 + j;
+                        const int y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                        const int64_t o = (int64_t)bx + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                        *reinterpret_cast<float4 *>(out + o) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int cell = c0 + j;
+                    const int x = bx + (cell & 3), y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                    if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
+                    const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                    if (full || F.tmask[o]) out[o] = w[j];
+                }
+            }
+        }
+        // (e) child c+1's operand tile
+        if (c + 1 < 8) lp_store(ac_hi, ac_lo, v);
+    }
+    if (tid == 0 && !*ok_s) {
+        // let this CTA's own copies and MMAs finish before its memory is released
+        if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
+        if (t_issued > t_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_issued - 1) & 1, WAIT_LIMIT);
+        if (m_issued > m_done) tc::mbar_wait_bounded(tc::smem_u32(bar_mma), (m_issued - 1) & 1, WAIT_LIMIT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, float *out, int *err,
+                       cudaStream_t st) {
+    if (parent_count <= 0 || level < 3 || F.O.l2pc_off < 0 || F.O.l2p_off[level] < 0) return;
+    tc_init_attributes();
+    k_l2lp_tc<<<(parent_count + TCM - 1) / TCM, LP_T, LP_SMEM, st>>>(F, level, parent_begin, parent_count,
+                                                                     F.O.l2p_img + F.O.l2p_off[level],
+                                                                     F.O.l2p_img + F.O.l2pc_off, out, err);
+}
+
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
 
 // Opt in to the dynamic shared memory of the tensor-core kernels (host-side, once;
@@ -815,6 +1042,7 @@ void tc_init_attributes() {
     cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
     cudaFuncSetAttribute(k_l2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2P_SMEM);
+    cudaFuncSetAttribute(k_l2lp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);
     cudaFuncSetAttribute(k_m2l_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PIPE_SMEM);
     done = true;
 }

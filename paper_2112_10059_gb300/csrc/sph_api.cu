@@ -85,6 +85,7 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    bool l2lp_fused = true;           // deepest level of edge-4 leaves: L2L and L2P in one tensor-core kernel
     int near_mode = SPH_NEAR_EXP;     // requested near-field form
     double r_s = 0.0;                 // strategy 3 ratio (0: off)
     DevBuf b_skip;
@@ -569,6 +570,9 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         c->launches += c->lvl_count[l] > 0;
     }
     if (tm) tm->mark_at(4, c->stream);
+    // the last L2L and the L2P of the deepest level fused (every box there a leaf of edge 4)
+    const bool fused = S.tc && c->l2lp_fused && F.leaf_l2p_done && F.O.l2p_img != nullptr && !c->l2p_simt &&
+                       F.O.l2pc_off >= 0 && c->Lmax >= 3 && c->Lmax == c->D - 2 && F.O.l2p_off[c->Lmax] >= 0;
     if (c->translate_per_box) {
         if (tm) { tm->mark_at(5, c->stream); tm->mark_at(6, c->stream); }
         for (int l = 2; l <= c->Lmax; ++l) {
@@ -601,7 +605,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                 fmm_p2l_level(F, l, c->lvl_base[l], c->lvl_count[l], c->stream);
                 c->launches += c->lvl_count[l] > 0;
             }
-        for (int l = 3; l <= c->Lmax; ++l) {
+        for (int l = 3; l <= c->Lmax - (fused ? 1 : 0); ++l) {
             // 8 children per CTA where that still gives every SM a CTA; one child per CTA (8x the
             // CTAs, 1/8 of the serial work each) for the small upper levels
             const bool few = (c->lvl_count[l - 1] + 63) / 64 < 152;
@@ -624,6 +628,13 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         const bool sep_all = F.l2p_sep && !c->l2p_tc_tables;
         if (l2p_tc) CK(cudaMemsetAsync(S.err + 1, 0, sizeof(int), c->stream));
         for (int l = 2; l <= c->Lmax; ++l) {
+            if (fused && l == c->Lmax) {
+                if (c->lvl_count[l - 1] > 0) {
+                    fmm_l2lp_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], out, S.err + 1, c->stream);
+                    ++c->launches;
+                }
+                continue;
+            }
             const bool tc_here = l2p_tc && (c->l2p_tc_tables || (1 << (c->D - l)) == 4);
             if (c->lvl_count[l] > 0 && sep_all && !tc_here) {
                 fmm_l2p_sep_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
@@ -949,6 +960,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_simt = parent->l2p_simt;
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
+    sub->l2lp_fused = parent->l2lp_fused;
     sub->near_mode = parent->near_mode;
     sub->r_s = parent->r_s;
     sub->launches = 0;
@@ -1326,6 +1338,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
+    if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {

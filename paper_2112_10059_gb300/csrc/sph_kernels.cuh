@@ -130,6 +130,10 @@ struct OpsDev {
     long long e_off[16];          // float offset of level l's table in e_tab, -1 if none
     uint16_t *l2p_img;            // FAR_CHEB: BF16 hi / lo images of the tables for the tensor-core L2P
     long long l2p_off[16];        // element offset of level l's images in l2p_img, -1 if none
+    // FAR_CHEB, leaves of edge 4 at level D-2: images of the 8 composed tables E L2L_c (the L2L
+    // from the parent into child c followed by the child's L2P), at this element offset in
+    // l2p_img; -1 if not built
+    long long l2pc_off;
     const double *uc64, *dc64;    // FAR_SURFACE FP64 UC2E_l / DC2E_l (row-major n x n), + l * pinv_stride
     long long pinv_stride;
     short *slot_of_code;  // [343] -> 0..315 or -1
@@ -149,6 +153,7 @@ size_t ops_work_doubles(int method, int n, int Lmax);
 size_t ops_etab_floats(int method, int npad, int D, int Lmax);
 void ops_layout(int D, int Lmax, double *work, OpsDev &O);   // e_off, l2p_off, uc64, dc64, pinv_stride
 size_t ops_l2p_img_elems(int D, int Lmax);                  // BF16 elements of every level's L2P images
+                                                            // (and the composed L2L + L2P images)
 
 // ---------------------------------------------------------------- FMM passes
 struct FmmDev {
@@ -181,6 +186,10 @@ void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cud
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st);
 // tensor-core L2P (FAR_CHEB, images present): writes S at the targets of the level's leaves
+// L2L into the leaves of edge 4 at `level` fused with their L2P (tensor cores); every box at
+// `level` must be a leaf (level == Lmax).  Replaces fmm_l2l_*_level(level) and the L2P of `level`.
+void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, float *out, int *err,
+                       cudaStream_t st);
 void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, int *err,
                       cudaStream_t st);
 __host__ __device__ int l2p_tile_n(int edge);

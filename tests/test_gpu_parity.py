@@ -242,6 +242,48 @@ def test_l2p_forms_and_separate_near_field(sph, monkeypatch, pi):
     _check_fmm(outs["default"], ref, T, p.name)
 
 
+@pytest.mark.parametrize("case", ["all", "efrac_ragged", "mask"])
+def test_fused_l2l_l2p_deepest_level(sph, monkeypatch, case):
+    """Leaf size 64: every box of the deepest level is a leaf of edge 4, and one tensor-core
+    kernel applies the parent's local expansion through the composed tables (L2L into the
+    child, then its L2P) and the child's own terms through the L2P table.  Equal to the
+    separate L2L and L2P kernels, zero outside the targets, within the oracle gate; ragged
+    grid (boxes overhanging the grid) and partly selected leaves included."""
+    mask = None
+    if case == "all":
+        p = si.streamer(n=48, box=0.5, chan_len=0.25, i_frac=1e-3, targets_all=True, leaf_size=64,
+                        sigma_head=0.02, chan_radius=0.02, seed=41, name="s48_leaf64")
+    elif case == "efrac_ragged":
+        p = si.streamer(n=54, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.05, targets_all=False, leaf_size=64,
+                        sigma_head=0.02, chan_radius=0.02, seed=42, name="s54_leaf64")
+    else:
+        p = si.streamer(n=48, box=0.5, chan_len=0.25, i_frac=1e-3, targets_all=True, leaf_size=64,
+                        sigma_head=0.02, chan_radius=0.02, seed=43, name="s48_mask")
+        mask = si.random_mask(p.ncell, 0.4, 44)
+    outs, stats = {}, {}
+    for name, env in (("fused", {}), ("separate", {"SPH_L2LP_FUSED": "0"})):
+        monkeypatch.delenv("SPH_L2LP_FUSED", raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        c = sph.Context(0)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True, mask=mask)
+        outs[name] = out.cpu().numpy().astype(np.float64)
+        stats[name] = st
+        c.close()
+    assert stats["fused"].max_level == stats["fused"].depth - 2          # the fused kernel's case
+    if mask is None:
+        ref, J, T = oracle.sph_problem(p)
+    else:
+        T = np.flatnonzero(mask)
+    assert oracle.rel_l2(outs["fused"][T], outs["separate"][T]) < 3e-5
+    assert oracle.max_rel(outs["fused"][T], outs["separate"][T], 1e-3) < 3e-4
+    others = np.ones(outs["fused"].size, bool)
+    others[T] = False
+    assert np.all(outs["fused"][others] == 0)
+    if mask is None:
+        _check_fmm(outs["fused"], ref, T, p.name)
+
+
 def test_separable_l2p_for_coarse_leaves(sph, monkeypatch):
     """128^3 with sources only near a streamer head and targets where |E| is large: many
     targets sit in coarse leaves (edge 32 cells, no interpolation table), evaluated by the
