@@ -153,19 +153,28 @@ NCU_TRAFFIC = {"select": (134.320640 + 104.982784 + 134.236928 + 3.904512) * 1e6
 def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_headline=True):
     """Achieved vs peak per phase.  Work is ALGORITHMIC (what the method needs), not executed:
       m2l  (tensor): 2 n^2 flops per V pair, n = order^3 (the BF16 x3 split executes 3 x 128^2 x 2);
-      l2l  (tensor): 2 n^2 flops per child box with targets below level 2;
-      l2p  (HBM): the leaves' local expansions read (npad x 4 B per leaf with targets) + S written (4 B per target);
+      l2l  (tensor): 2 n^2 flops per child box with targets below level 2 (levels the separate
+                     L2L kernels run: all but the deepest one when that level is fused);
+      l2lp (HBM): fused L2L + L2P of the deepest level: the parents' and the leaves' local
+                  expansions read (npad x 4 B each) + S written (4 B per target of those leaves);
+      l2p  (HBM): the other leaves' local expansions read (npad x 4 B per leaf with targets) + S
+                  written (4 B per target);
       near (MUFU):  P2P pairs + M2P evaluations (3 MUFU each: rsqrt + 2 x ex2);
       select (HBM): 8 B per cell read twice (maxima, then the rules: q and |E|) + 8 B per target and
                     12 B per source written + 1 B per cell of target mask."""
     n = args.order ** 3
     npad = (n + 15) // 16 * 16
     mean = lambda k: statistics.mean(x[k] for x in step_stats)
+    fused = all(x["l2lp_fused"] for x in step_stats)
     lev = tree["level"]
     ntb = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
     nsb = (tree["src_end"] - tree["src_begin"]).astype(np.int64)
-    n_child = int(np.sum((lev >= 3) & (ntb > 0)))
-    n_leaf_t = int(np.sum(tree["leaf"] & (ntb > 0) & (lev >= 2)))
+    lmax = int(lev.max()) if lev.size else 0
+    deep = (lev == lmax) if fused else np.zeros(lev.size, bool)
+    n_child = int(np.sum((lev >= 3) & (ntb > 0) & ~deep))
+    leaf_t = tree["leaf"] & (ntb > 0) & (lev >= 2)
+    n_leaf_t = int(np.sum(leaf_t & ~deep))
+    nt_other = int(np.sum(ntb[leaf_t & ~deep]))
     nV = len(tree["V"])
     U, W = tree["U"], tree["W"]
     p2p = int(np.sum(ntb[U[:, 0]] * nsb[U[:, 1]])) if len(U) else 0
@@ -190,8 +199,15 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_h
         ("measured dense BF16 %.1f TFLOP/s (%s)" % (tpk, peaks["source"])) if tc else "FP32 FMA 152 SMs")
     add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", "tensor" if tc else "alu", 2.0 * n * n * n_child,
         "flop", mean("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
-    add("l2p", "k_l2p_tc + k_l2p_sep_small + k_l2p_sep" if tc else "k_l2p_sep_small + k_l2p_sep", "hbm",
-        4.0 * npad * n_leaf_t + 4.0 * nt, "bytes", mean("ms_l2p"), hbm, "GB/s", hbm_basis)
+    ms_lp = mean("ms_l2lp") if fused else 0.0
+    if fused:
+        n_par = int(np.sum((lev == lmax - 1) & ~tree["leaf"] & (ntb > 0)))
+        n_deep = int(np.sum(leaf_t & deep))
+        nt_deep = int(np.sum(ntb[leaf_t & deep]))
+        add("l2lp", "k_l2lp_tc", "hbm", 4.0 * npad * (n_par + n_deep) + 4.0 * nt_deep, "bytes", ms_lp, hbm,
+            "GB/s", hbm_basis, traffic=NCU_TRAFFIC.get("l2lp") if workload_is_headline else None)
+    add("l2p", ("k_l2p_tc + " if tc and not fused else "") + "k_l2p_sep_small + k_l2p_sep", "hbm",
+        4.0 * npad * n_leaf_t + 4.0 * nt_other, "bytes", mean("ms_l2p") - ms_lp, hbm, "GB/s", hbm_basis)
     add("near", "k_p2p", "alu", float(p2p + m2p), "kernel-evals", mean("ms_near"), mufu_peak, "evals/s",
         "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz)
     add("select", "k_grid_max + k_select_onepass", "hbm", 16.0 * ncell + 8.0 * nt + 12.0 * ns + 1.0 * ncell,
@@ -619,7 +635,7 @@ def main():
                 "clocks": clocks, "gpu_launches": int(step_stats[-1]["n_launches"]) * args.steps,
                 "phases_ms": {k: statistics.mean(x[k] for x in step_stats)
                               for k in ("ms_select", "ms_tree", "ms_upward", "ms_vpairs", "ms_m2l", "ms_l2l",
-                                        "ms_l2p", "ms_near", "ms_total")},
+                                        "ms_l2p", "ms_l2lp", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
                 "direct_fp32": direct, "accuracy": acc, "batch": batch, "surrogate": surrogate, "sweep": sweep, "cpu_baseline": cpu}

@@ -93,6 +93,8 @@ typedef struct sph_stats {
     int32_t leaf_size;         /* leaf size of the tree (set_criteria's, or the autotuner's choice) */
     int32_t near_table;        /* 1 if the near field used the table form */
     int64_t n_w_skipped;       /* (target, W box) pairs skipped by strategy 3 (sph_set_skip_ratio) */
+    int32_t l2lp_fused;        /* 1 if the deepest level's L2L and L2P ran as one kernel (leaves of edge 4) */
+    float ms_l2lp;             /* its GPU milliseconds (inside ms_l2p), 0 if not fused */
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`

@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("ms_l2l", ctypes.c_float), ("ms_l2p", ctypes.c_float),
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
                 ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
-                ("near_table", ctypes.c_int32), ("n_w_skipped", ctypes.c_int64)]
+                ("near_table", ctypes.c_int32), ("n_w_skipped", ctypes.c_int64), ("l2lp_fused", ctypes.c_int32),
+                ("ms_l2lp", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -86,16 +86,18 @@ __device__ __forceinline__ TcSmem carve(uint8_t *raw) {
 // Split 4 FP32 values into BF16 hi / lo and store them at element (row, k0..k0+3) of two
 // K-major SW128 tiles with `rows` rows.
 __device__ __forceinline__ void put_split4(uint8_t *hi, uint8_t *lo, int row, int k0, int rows, const float4 &v) {
-    uint16_t h0, l0, h1, l1, h2, l2, h3, l3;
-    tc::split_bf16(v.x, h0, l0);
-    tc::split_bf16(v.y, h1, l1);
-    tc::split_bf16(v.z, h2, l2);
-    tc::split_bf16(v.w, h3, l3);
+    // cvt.rn.bf16x2 rounds two values to nearest even at once (first operand to the upper
+    // half); the residuals x - hi are exact in FP32 and rounded the same way
+    uint32_t h01, h23, l01, l23;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h01) : "f"(v.y), "f"(v.x));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h23) : "f"(v.w), "f"(v.z));
+    const float r0 = v.x - __uint_as_float(h01 << 16), r1 = v.y - __uint_as_float(h01 & 0xFFFF0000u);
+    const float r2 = v.z - __uint_as_float(h23 << 16), r3 = v.w - __uint_as_float(h23 & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l01) : "f"(r1), "f"(r0));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l23) : "f"(r3), "f"(r2));
     const uint32_t off = tc::sw128_offset(row, k0, rows);
-    *reinterpret_cast<uint2 *>(hi + off) =
-        make_uint2((uint32_t)h0 | ((uint32_t)h1 << 16), (uint32_t)h2 | ((uint32_t)h3 << 16));
-    *reinterpret_cast<uint2 *>(lo + off) =
-        make_uint2((uint32_t)l0 | ((uint32_t)l1 << 16), (uint32_t)l2 | ((uint32_t)l3 << 16));
+    *reinterpret_cast<uint2 *>(hi + off) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2 *>(lo + off) = make_uint2(l01, l23);
 }
 
 // Gather `rows` FP32 state rows (index list `idx`, -1 = zero row; row stride np) into BF16

@@ -86,6 +86,7 @@ struct sph_ctx {
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     bool l2lp_fused = true;           // deepest level of edge-4 leaves: L2L and L2P in one tensor-core kernel
+    bool l2lp_used = false;           // the last eval ran the fused kernel
     int near_mode = SPH_NEAR_EXP;     // requested near-field form
     double r_s = 0.0;                 // strategy 3 ratio (0: off)
     DevBuf b_skip;
@@ -465,7 +466,10 @@ struct PhaseTimer {
         mark(st);
     }
     void mark(cudaStream_t st) {
-        if (on && n < 16) cudaEventRecord(ev[n++], st);
+        if (on && n < 16) {
+            rec[n] = true;
+            cudaEventRecord(ev[n++], st);
+        }
     }
     void mark_at(int k, cudaStream_t st) {   // record event k (events between may stay unrecorded)
         if (on && k < 16) {
@@ -474,13 +478,14 @@ struct PhaseTimer {
             cudaStreamIsCapturing(st, &cs);
             if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal);
             else cudaEventRecord(ev[k], st);
-            n = k + 1;
+            rec[k] = true;
+            n = std::max(n, k + 1);
         }
     }
     bool rec[16] = {};
-    float ms(int a, int b) {
+    float ms(int a, int b) {     // 0 unless both events were recorded in this eval
         float m = 0;
-        if (on && b < n) cudaEventElapsedTime(&m, ev[a], ev[b]);
+        if (on && a < 16 && b < 16 && rec[a] && rec[b]) cudaEventElapsedTime(&m, ev[a], ev[b]);
         return m;
     }
     ~PhaseTimer() {
@@ -573,6 +578,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     // the last L2L and the L2P of the deepest level fused (every box there a leaf of edge 4)
     const bool fused = S.tc && c->l2lp_fused && F.leaf_l2p_done && F.O.l2p_img != nullptr && !c->l2p_simt &&
                        F.O.l2pc_off >= 0 && c->Lmax >= 3 && c->Lmax == c->D - 2 && F.O.l2p_off[c->Lmax] >= 0;
+    c->l2lp_used = fused && c->lvl_count[c->Lmax - 1] > 0;
     if (c->translate_per_box) {
         if (tm) { tm->mark_at(5, c->stream); tm->mark_at(6, c->stream); }
         for (int l = 2; l <= c->Lmax; ++l) {
@@ -630,7 +636,9 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         for (int l = 2; l <= c->Lmax; ++l) {
             if (fused && l == c->Lmax) {
                 if (c->lvl_count[l - 1] > 0) {
+                    if (tm) tm->mark_at(10, c->stream);
                     fmm_l2lp_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], out, S.err + 1, c->stream);
+                    if (tm) tm->mark_at(11, c->stream);
                     ++c->launches;
                 }
                 continue;
@@ -700,12 +708,14 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
         stats->ms_l2p = tm->ms(7, 8);
         stats->ms_near = tm->ms(8, 9);
         stats->ms_total = tm->ms(0, 9);
+        stats->ms_l2lp = tm->ms(10, 11);
     }
     stats->n_launches = c->launches;
     stats->far_method = c->far_method;
     stats->far_order = c->far_order;
     stats->leaf_size = c->leaf_eff;
     stats->near_table = c->near_table ? 1 : 0;
+    stats->l2lp_fused = c->l2lp_used ? 1 : 0;
     if (c->b_skip.p) {
         unsigned long long k = 0;
         if (cudaMemcpy(&k, c->b_skip.p, sizeof k, cudaMemcpyDeviceToHost) == cudaSuccess) stats->n_w_skipped = (int64_t)k;
