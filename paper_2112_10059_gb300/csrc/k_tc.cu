@@ -917,6 +917,43 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     const uint32_t idesc = tc::idesc_bf16_f32(TCM, 64);
     const int q = warp & 3, r = q * 32 + lane;              // TMEM lane quadrant, parent row
     const bool vec_ok = (F.nx % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    // child c's cells: warps w and w + 4 share TMEM lanes 32 (w % 4) .. and take half of
+    // the 64 columns each
+    auto epilogue = [&](int c) {
+        const int C = sch[c * TCM + r];
+        const bool full = sfull[c * TCM + r] != 0;
+        int bx = 0, by = 0, bz = 0;
+        if (C >= 0) {
+            uint32_t ux, uy, uz;
+            demorton3(T.b_key[C], ux, uy, uz);
+            bx = (int)ux * 4; by = (int)uy * 4; bz = (int)uz * 4;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = 32 * (warp >> 2) + 16 * h;
+            float w[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * c + c0), w);
+            if (C < 0) continue;
+            if (full && vec_ok) {   // whole box: one 16-byte store per row of 4 cells
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const int cell = c0 + j;
+                    const int y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                    const int64_t o = (int64_t)bx + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                    *reinterpret_cast<float4 *>(out + o) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+                }
+                continue;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int cell = c0 + j;
+                const int x = bx + (cell & 3), y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
+                const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                if (full || F.tmask[o]) out[o] = w[j];
+            }
+        }
+    };
     for (int c = 0; c < 8; ++c) {
         // (a) operand tiles of child c are in shared memory: MMAs (thread 0)
         tc::fence_proxy_async_smem();
@@ -951,10 +988,11 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                 *ok_s = 0;
             }
         }
-        // (b) child c+1's rows in flight while the MMAs run
+        // (b) child c+1's rows in flight and child c-1's cells written while the MMAs run
         if (c + 1 < 8) lp_load(v, sch + (c + 1) * TCM, F.dchk, np);
-        // (c) MMAs of child c complete: its accumulator is final, the child tile and the table
-        //     buffer are free; child c+1's table starts streaming in
+        if (c > 0) epilogue(c - 1);
+        // (c) MMAs of child c complete: its accumulator is final (written in the next round),
+        //     the child tile and the table buffer are free; child c+1's table streams in
         if (tid == 0 && *ok_s) {
             if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), c & 1, WAIT_LIMIT)) {
                 ++m_done;
@@ -973,46 +1011,10 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
         __syncthreads();
         if (!*ok_s) break;
         tc::fence_after_sync();
-        // (d) child c's cells: warps w and w + 4 share TMEM lanes 32 (w % 4) .. and take half
-        //     of the 64 columns each
-        {
-            const int C = sch[c * TCM + r];
-            const bool full = sfull[c * TCM + r] != 0;
-            int bx = 0, by = 0, bz = 0;
-            if (C >= 0) {
-                uint32_t ux, uy, uz;
-                demorton3(T.b_key[C], ux, uy, uz);
-                bx = (int)ux * 4; by = (int)uy * 4; bz = (int)uz * 4;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c0 = 32 * (warp >> 2) + 16 * h;
-                float w[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * c + c0), w);
-                if (C < 0) continue;
-                if (full && vec_ok) {   // whole box: one 16-byte store per row of 4 cells
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4) {
-                        const int cell = c0 + j;
-                        const int y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
-                        const int64_t o = (int64_t)bx + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-                        *reinterpret_cast<float4 *>(out + o) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int cell = c0 + j;
-                    const int x = bx + (cell & 3), y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
-                    if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
-                    const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-                    if (full || F.tmask[o]) out[o] = w[j];
-                }
-            }
-        }
         // (e) child c+1's operand tile
         if (c + 1 < 8) lp_store(ac_hi, ac_lo, v);
     }
+    if (*ok_s) epilogue(7);
     if (tid == 0 && !*ok_s) {
         // let this CTA's own copies and MMAs finish before its memory is released
         if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
