@@ -312,17 +312,41 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     uint32_t mx, my, mz;
     demorton3((uint32_t)(8 * tid), mx, my, mz);
     {
+        // cell u of the micro-cube sits at (mx + (u & 1), my + ((u >> 1) & 1), mz + (u >> 2)):
+        // the pairs (u, u + 1), u even, are x-neighbours at an even x, read as one float2 when
+        // the row pitch and the arrays allow it
+        const bool vec2 = (r.nx & 1) == 0 && (reinterpret_cast<uintptr_t>(q) & 7) == 0 &&
+                          (r.trg_mode != 1 || (reinterpret_cast<uintptr_t>(e) & 7) == 0);
         float ev[8];
         uint32_t lin[8];
         bool in[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int x = x0 + (int)mx + (u & 1), y = y0 + (int)my + ((u >> 1) & 1), z = z0 + (int)mz + (u >> 2);
-            in[u] = 8 * tid + u < ncell && x < r.nx && y < r.ny && z < r.nz;
-            lin[u] = in[u] ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
-            my_q[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
-            ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
-            if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
+        for (int v2 = 0; v2 < 4; ++v2) {
+            const int u0 = 2 * v2;
+            const int x = x0 + (int)mx, y = y0 + (int)my + (v2 & 1), z = z0 + (int)mz + (v2 >> 1);
+            const bool row = 8 * tid + u0 < ncell && y < r.ny && z < r.nz;
+            in[u0] = row && x < r.nx;
+            in[u0 + 1] = row && x + 1 < r.nx;
+            const uint32_t l0 = row ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
+            lin[u0] = l0;
+            lin[u0 + 1] = l0 + 1;
+            if (vec2 && in[u0 + 1] && r.trg_mode != 2) {
+                const float2 a = __ldg(reinterpret_cast<const float2 *>(q + l0));
+                my_q[u0] = a.x;
+                my_q[u0 + 1] = a.y;
+                float2 c = make_float2(0.f, 0.f);
+                if (r.trg_mode == 1) c = __ldg(reinterpret_cast<const float2 *>(e + l0));
+                ev[u0] = c.x;
+                ev[u0 + 1] = c.y;
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int u = u0 + h;
+                    my_q[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
+                    ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
+                    if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -332,9 +356,21 @@ __global__ void __launch_bounds__(512) k_select_onepass(
                 if (r.trg_mode == 0) bits |= 2;
                 else if (r.trg_mode == 1) { if (ev[u] >= thr_e) bits |= 2; }
                 else if (ev[u] != 0.f) bits |= 2;
-                if (tmask) tmask[lin[u]] = (uint8_t)(bits >> 1);
             }
             my_bits[u] = bits;
+        }
+        if (tmask) {
+#pragma unroll
+            for (int v2 = 0; v2 < 4; ++v2) {
+                const int u0 = 2 * v2;
+                if (vec2 && in[u0 + 1]) {      // even index: one 2-byte store
+                    *reinterpret_cast<uint16_t *>(tmask + lin[u0]) =
+                        (uint16_t)((my_bits[u0] >> 1) | ((my_bits[u0 + 1] >> 1) << 8));
+                } else {
+                    if (in[u0]) tmask[lin[u0]] = (uint8_t)(my_bits[u0] >> 1);
+                    if (in[u0 + 1]) tmask[lin[u0 + 1]] = (uint8_t)(my_bits[u0 + 1] >> 1);
+                }
+            }
         }
     }
     int ns = 0, nt = 0;

@@ -62,6 +62,19 @@ def test_selection_bit_exact(sph, ctx, pi):
     assert np.array_equal(T, To)
 
 
+@pytest.mark.parametrize("n", [45, 46])
+def test_selection_bit_exact_row_pitch(sph, ctx, n):
+    """Odd and even row pitch: the selection reads x-pairs as one 8-byte load only where the
+    pitch keeps them aligned, cell by cell elsewhere; both give the oracle's sets."""
+    p = si.streamer(n=n, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.3, targets_all=False, leaf_size=32,
+                    sigma_head=0.02, chan_radius=0.02, seed=50 + n, name="s%d" % n)
+    sph.solve(p, ctx)
+    J, T = sph.get_selection(ctx)
+    Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    assert np.array_equal(J, Jo)
+    assert np.array_equal(T, To)
+
+
 def test_selection_threshold_ties_and_mask(sph, ctx):
     import torch
     n = 16
