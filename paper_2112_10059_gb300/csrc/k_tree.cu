@@ -19,7 +19,8 @@
 //   V: same level >= 2, parents adjacent, A not adjacent to B; offset code kept;
 //   W: B leaf, A finer with sources, parent(A) adjacent to B, A not adjacent;
 //   X: A leaf with sources, coarser than B, A adjacent to parent(B), not to B.
-// k_lists<false> counts, one scan gives the four CSR offset arrays, k_lists<true> fills.
+// k_lists_classify + k_lists_warp<false> count, one scan gives the four CSR offset arrays,
+// k_lists_warp<true> fills.
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -432,171 +433,191 @@ __device__ __forceinline__ int lookup(const TreeDev &T, int level, int x, int y,
     return T.box_at[dense_off(level) + morton3(x, y, z)];
 }
 
-template <bool FILL>
-__global__ void k_lists(TreeDev T, ListDev L, int nboxes, int D, int Lmax) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+// Lists in two steps.  k_lists_classify (thread per box) finds the boxes that can have an
+// entry -- targets, and sources somewhere around the parent -- and queues them (any order:
+// every box writes only its own CSR range); the others get empty lists.  k_lists_warp
+// then takes one queued box per warp: the 27 neighbour slots of U / W and of X one per
+// lane, the 216 V candidates 32 at a time, entries placed in slot order by warp prefix
+// sums, so every list comes out exactly as a serial walk of the slots would write it.
+__global__ void k_lists_classify(TreeDev T, ListDev L, int nboxes) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
-    int nU = 0, nV = 0, nW = 0, nX = 0;
-    int pU = 0, pV = 0, pW = 0, pX = 0;
-    if (FILL) { pU = L.u_off[b]; pV = L.v_off[b]; pW = L.w_off[b]; pX = L.x_off[b]; }
-    int nt = T.b_te[b] - T.b_tb[b];
-    if (nt > 0) {
-        BoxGeom B = geom_of(T, b);
-        const int l = B.level;
+    bool heavy = false;
+    if (T.b_te[b] > T.b_tb[b]) {
+        const int l = T.b_level[b];
         // nothing with sources anywhere around the parent: every list is empty
-        if (l >= 1 && T.near && !T.near[dense_off(l - 1) + morton3(B.x >> 1, B.y >> 1, B.z >> 1)]) nt = 0;
+        heavy = !(l >= 1 && T.near && !T.near[dense_off(l - 1) + (T.b_key[b] >> 3)]);
     }
-    if (nt > 0) {
+    if (heavy) {
+        L.heavy[atomicAdd(L.nheavy, 1)] = b;
+    } else {
+        L.u_cnt[b] = 0; L.v_cnt[b] = 0; L.w_cnt[b] = 0; L.x_cnt[b] = 0;
+    }
+}
+
+// Descendants of a split colleague A of leaf B: adjacent leaves with sources join U, the
+// first non-adjacent boxes with sources join W (depth first, children in key order).
+template <bool FILL>
+__device__ __noinline__ void lists_descend(const TreeDev &T, const ListDev &L, const BoxGeom &B, int D, int A,
+                                           int pu, int pw, int &cu, int &cw) {
+    int stk[128];
+    int sp = 0;
+    const uint32_t ck = T.b_key[A] << 3;
+    for (int c = 0; c < 8; ++c) {
+        const int C = T.box_at[dense_off(B.level + 1) + ck + c];
+        if (C >= 0) stk[sp++] = C;
+    }
+    while (sp > 0) {
+        const int Dn = stk[--sp];
+        const BoxGeom G = geom_of(T, Dn);
+        const bool hs = T.b_se[Dn] > T.b_sb[Dn];
+        if (adjacent(G, B, D)) {
+            if (T.b_leaf[Dn]) {
+                if (hs) {
+                    if (FILL) L.u_src[pu + cu] = Dn;
+                    ++cu;
+                }
+            } else if (sp + 8 <= 128) {
+                const uint32_t k2 = T.b_key[Dn] << 3;
+                for (int c = 0; c < 8; ++c) {
+                    const int C = T.box_at[dense_off(G.level + 1) + k2 + c];
+                    if (C >= 0) stk[sp++] = C;
+                }
+            }
+        } else if (hs) {
+            if (FILL) L.w_src[pw + cw] = Dn;
+            ++cw;
+        }
+    }
+}
+
+// Deepest existing box over slot (qx, qy, qz) of level lq, searched from level lq - 1 up;
+// its index if it is a leaf with sources, else -1.
+__device__ __forceinline__ int coarse_leaf_src(const TreeDev &T, int lq, int qx, int qy, int qz) {
+    for (int m = lq - 1; m >= 0; --m) {
+        const int sh = lq - m;
+        const int64_t sl = dense_off(m) + morton3(qx >> sh, qy >> sh, qz >> sh);
+        const int Am = T.box_at[sl];
+        if (Am >= 0) return (T.vsrc[sl] && T.b_leaf[Am]) ? Am : -1;
+    }
+    return -1;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, int D) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nh = *L.nheavy;
+    for (int h = wid; h < nh; h += nw) {
+        const int b = L.heavy[h];
         BoxGeom B = geom_of(T, b);
         const int l = B.level;
-        // ---- U and W (B leaf)
+        int pU = 0, pV = 0, pW = 0, pX = 0;
+        if (FILL) { pU = L.u_off[b]; pV = L.v_off[b]; pW = L.w_off[b]; pX = L.x_off[b]; }
+        int nU = 0, nV = 0, nW = 0, nX = 0;
+        // ---- U and W (B leaf): lane t < 27 takes slot t (z, then y, then x)
         if (T.b_leaf[b]) {
-            int coarse[27];
-            int ncoarse = 0;
-            int stk[128];
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int qx = B.x + dx, qy = B.y + dy, qz = B.z + dz;
-                        int n = 1 << l;
-                        if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
-                        const uint32_t m = morton3(qx, qy, qz);
-                        const int A = T.box_at[dense_off(l) + m];
-                        const bool hs_a = T.vsrc[dense_off(l) + m];
-                        if (A >= 0) {
-                            if (!hs_a) continue;   // no sources anywhere below A
-                            if (T.b_leaf[A]) {
-                                if (FILL) L.u_src[pU] = A;
-                                ++pU; ++nU;
-                            } else {
-                                int sp = 0;
-                                // push children of the colleague
-                                uint32_t ck = T.b_key[A] << 3;
-                                for (int c = 0; c < 8; ++c) {
-                                    int C = T.box_at[dense_off(l + 1) + ck + c];
-                                    if (C >= 0) stk[sp++] = C;
-                                }
-                                while (sp > 0) {
-                                    int Dn = stk[--sp];
-                                    BoxGeom G = geom_of(T, Dn);
-                                    bool hs = T.b_se[Dn] > T.b_sb[Dn];
-                                    if (adjacent(G, B, D)) {
-                                        if (T.b_leaf[Dn]) {
-                                            if (hs) {
-                                                if (FILL) L.u_src[pU] = Dn;
-                                                ++pU; ++nU;
-                                            }
-                                        } else if (sp + 8 <= 128) {
-                                            uint32_t k2 = T.b_key[Dn] << 3;
-                                            for (int c = 0; c < 8; ++c) {
-                                                int C = T.box_at[dense_off(G.level + 1) + k2 + c];
-                                                if (C >= 0) stk[sp++] = C;
-                                            }
-                                        }
-                                    } else if (hs) {
-                                        if (FILL) L.w_src[pW] = Dn;
-                                        ++pW; ++nW;
-                                    }
-                                }
-                            }
-                        } else {
-                            for (int m = l - 1; m >= 0; --m) {
-                                const int sh = l - m;
-                                const int64_t sl = dense_off(m) + morton3(qx >> sh, qy >> sh, qz >> sh);
-                                const int Am = T.box_at[sl];
-                                if (Am >= 0) {
-                                    if (T.vsrc[sl] && T.b_leaf[Am]) {
-                                        bool dup = false;
-                                        for (int u = 0; u < ncoarse; ++u) dup |= coarse[u] == Am;
-                                        if (!dup) coarse[ncoarse++] = Am;
-                                    }
-                                    break;
-                                }
-                            }
-                        }
-                    }
-            for (int u = 0; u < ncoarse; ++u) {
-                if (FILL) L.u_src[pU] = coarse[u];
-                ++pU; ++nU;
+            const int n = 1 << l;
+            const int qx = B.x + lane % 3 - 1, qy = B.y + (lane / 3) % 3 - 1, qz = B.z + lane / 9 - 1;
+            const bool inr = lane < 27 && qx >= 0 && qy >= 0 && qz >= 0 && qx < n && qy < n && qz < n;
+            int A = -1, mode = 0;          // 1 leaf colleague, 2 split colleague, 3 no box at this level
+            if (inr) {
+                const int64_t sl = dense_off(l) + morton3(qx, qy, qz);
+                A = T.box_at[sl];
+                if (A < 0) mode = 3;
+                else if (T.vsrc[sl]) mode = T.b_leaf[A] ? 1 : 2;
             }
+            int cu = mode == 1, cw = 0, coarse = -1;
+            if (mode == 2) lists_descend<false>(T, L, B, D, A, 0, 0, cu, cw);
+            if (mode == 3) coarse = coarse_leaf_src(T, l, qx, qy, qz);
+            int eu = cu, ew = cw;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a = __shfl_up_sync(0xffffffffu, eu, o), c = __shfl_up_sync(0xffffffffu, ew, o);
+                if (lane >= o) { eu += a; ew += c; }
+            }
+            const int tu = __shfl_sync(0xffffffffu, eu, 31), tw = __shfl_sync(0xffffffffu, ew, 31);
+            eu -= cu;
+            ew -= cw;
+            if (FILL) {
+                if (mode == 1) L.u_src[pU + eu] = A;
+                if (mode == 2) {
+                    int du = 0, dw = 0;
+                    lists_descend<true>(T, L, B, D, A, pU + eu, pW + ew, du, dw);
+                }
+            }
+            // leaves covering missing slots: once each, in order of first appearance, after the rest
+            const unsigned same = __match_any_sync(0xffffffffu, coarse);
+            const bool rep = coarse >= 0 && (__ffs(same) - 1) == lane;
+            const unsigned repm = __ballot_sync(0xffffffffu, rep);
+            if (FILL && rep) L.u_src[pU + tu + __popc(repm & lt)] = coarse;
+            nU = tu + __popc(repm);
+            nW = tw;
         }
-        // ---- X, and whether any box adjacent to the parent holds sources (else V is empty)
+        // ---- X (leaves with sources adjacent to the parent, not to B), and whether any box
+        // adjacent to the parent holds sources (else V is empty)
         bool parent_near_src = false;
         if (l >= 2) {
-            int cx = B.x >> 1, cy = B.y >> 1, cz = B.z >> 1;
-            int found[27];
-            int nf = 0;
-            int n = 1 << (l - 1);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-                        if (qx < 0 || qy < 0 || qz < 0 || qx >= n || qy >= n || qz >= n) continue;
-                        for (int m = l - 1; m >= 0; --m) {
-                            const int sh = l - 1 - m;
-                            const int64_t sl = dense_off(m) + morton3(qx >> sh, qy >> sh, qz >> sh);
-                            const int Am = T.box_at[sl];
-                            const bool hs = T.vsrc[sl];
-                            if (Am >= 0) {
-                                if (m == l - 1) parent_near_src |= hs;
-                                if (hs && T.b_leaf[Am]) {
-                                    BoxGeom G = geom_of(T, Am);
-                                    if (!adjacent(G, B, D)) {
-                                        bool dup = false;
-                                        for (int u = 0; u < nf; ++u) dup |= found[u] == Am;
-                                        if (!dup) found[nf++] = Am;
-                                    }
-                                }
-                                break;
-                            }
-                        }
-                    }
-            for (int u = 0; u < nf; ++u) {
-                if (FILL) L.x_src[pX] = found[u];
-                ++pX; ++nX;
+            const int n = 1 << (l - 1);
+            const int qx = (B.x >> 1) + lane % 3 - 1, qy = (B.y >> 1) + (lane / 3) % 3 - 1, qz = (B.z >> 1) + lane / 9 - 1;
+            const bool inr = lane < 27 && qx >= 0 && qy >= 0 && qz >= 0 && qx < n && qy < n && qz < n;
+            int cand = -1;
+            bool hs = false;
+            if (inr) {
+                const int64_t sl = dense_off(l - 1) + morton3(qx, qy, qz);
+                const int Am = T.box_at[sl];
+                if (Am >= 0) {
+                    hs = T.vsrc[sl];
+                    if (hs && T.b_leaf[Am]) cand = Am;
+                } else {
+                    cand = coarse_leaf_src(T, l - 1, qx, qy, qz);
+                }
+                if (cand >= 0 && adjacent(geom_of(T, cand), B, D)) cand = -1;
             }
+            parent_near_src = __any_sync(0xffffffffu, hs);
+            const unsigned same = __match_any_sync(0xffffffffu, cand);
+            const bool rep = cand >= 0 && (__ffs(same) - 1) == lane;
+            const unsigned repm = __ballot_sync(0xffffffffu, rep);
+            if (FILL && rep) L.x_src[pX + __popc(repm & lt)] = cand;
+            nX = __popc(repm);
         }
-        // ---- V (children of the parent's neighbours that hold sources): 6^3 candidates around
-        // the parent, minus the 3^3 adjacent to B; one byte per candidate slot decides
+        // ---- V: the 6^3 candidates around the parent minus the 3^3 adjacent to B, 32 at a time
         if (l >= 2 && parent_near_src) {
             const int n = 1 << l;
             const int px = B.x & ~1, py = B.y & ~1, pz = B.z & ~1;
             const uint8_t *vs = T.vsrc + dense_off(l);
             const int *ba = T.box_at + dense_off(l);
-            uint32_t sx[6];
 #pragma unroll
-            for (int d = 0; d < 6; ++d) sx[d] = spread3((uint32_t)(px - 2 + d));
-            for (int dz = 0; dz < 6; ++dz) {
-                const int qz = pz - 2 + dz, oz = qz - B.z;
-                if (qz < 0 || qz >= n) continue;
-                const uint32_t mz = spread3((uint32_t)qz) << 2;
-                for (int dy = 0; dy < 6; ++dy) {
-                    const int qy = py - 2 + dy, oy = qy - B.y;
-                    if (qy < 0 || qy >= n) continue;
-                    const bool near_yz = abs(oy) <= 1 && abs(oz) <= 1;
-                    const uint32_t myz = (spread3((uint32_t)qy) << 1) | mz;
-#pragma unroll
-                    for (int dx = 0; dx < 6; ++dx) {
-                        const int qx = px - 2 + dx, ox = qx - B.x;
-                        if (qx < 0 || qx >= n || (near_yz && abs(ox) <= 1)) continue;
-                        const uint32_t m = sx[dx] | myz;
-                        if (vs[m]) {
-                            if (FILL) {
-                                L.v_src[pV] = ba[m];
-                                L.v_trg[pV] = b;
-                                L.v_oc[pV] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
-                            }
-                            ++pV; ++nV;
-                        }
-                    }
+            for (int k = 0; k < 7; ++k) {
+                const int c = 32 * k + lane;
+                const int qx = px - 2 + c % 6, qy = py - 2 + (c / 6) % 6, qz = pz - 2 + c / 36;
+                const int ox = qx - B.x, oy = qy - B.y, oz = qz - B.z;
+                uint32_t m = 0;
+                bool hit = false;
+                if (c < 216 && qx >= 0 && qy >= 0 && qz >= 0 && qx < n && qy < n && qz < n &&
+                    !(abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1)) {
+                    m = morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz);
+                    hit = vs[m] != 0;
                 }
+                const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                if (FILL && hit) {
+                    const int pos = pV + nV + __popc(hm & lt);
+                    L.v_src[pos] = ba[m];
+                    L.v_trg[pos] = b;
+                    L.v_oc[pos] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
+                }
+                nV += __popc(hm);
             }
         }
-    }
-    if (!FILL) {
-        L.u_cnt[b] = nU; L.v_cnt[b] = nV; L.w_cnt[b] = nW; L.x_cnt[b] = nX;
+        if (!FILL && lane == 0) {
+            L.u_cnt[b] = nU; L.v_cnt[b] = nV; L.w_cnt[b] = nW; L.x_cnt[b] = nX;
+        }
     }
 }
+
+constexpr int LISTS_WARP_GRID = 152 * 8;
 
 void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
                         int *totals /* device [4] */, int *err, cudaStream_t st) {
@@ -604,7 +625,9 @@ void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, i
         cudaMemsetAsync(totals, 0, 4 * sizeof(int), st);
         return;
     }
-    k_lists<false><<<(nboxes + 127) / 128, 128, 0, st>>>(T, L, nboxes, D, Lmax);
+    cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
+    k_lists_classify<<<(nboxes + 255) / 256, 256, 0, st>>>(T, L, nboxes);
+    k_lists_warp<false><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, D);
     ScanSet S{};
     S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;
     S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
@@ -625,7 +648,7 @@ void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, in
                        const int *totals, cudaStream_t st) {
     if (nboxes <= 0) return;
     k_close_offsets<<<1, 32, 0, st>>>(L, nboxes, totals);
-    k_lists<true><<<(nboxes + 127) / 128, 128, 0, st>>>(T, L, nboxes, D, Lmax);
+    k_lists_warp<true><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, D);
 }
 
 }  // namespace sph

@@ -96,7 +96,7 @@ struct sph_ctx {
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
-    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pairs;
+    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pairs, b_heavy;
     DevBuf b_ueq, b_dchk;
     DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf b_err;                // device error flags of the tensor-core tiles
@@ -280,6 +280,8 @@ ListDev list_dev(sph_ctx *c) {
     L.x_src = P<int>(c->b_xsrc);
     L.v_oc = P<short>(c->b_vocs);
     L.v_trg = P<int>(c->b_vtrg);
+    L.heavy = P<int>(c->b_heavy);
+    L.nheavy = P<int>(c->b_tot) + 8;
     return L;
 }
 
@@ -345,6 +347,7 @@ int tree_read_count(sph_ctx *c) {
     int nb = std::max(c->nboxes, 1);
     ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
     ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
+    ENS(c->b_heavy, (size_t)nb * sizeof(int));
     ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
@@ -367,7 +370,7 @@ int lists_fill(sph_ctx *c) {
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
     lists_fill_launch(tree_dev(c), L, c->nboxes, c->D, c->Lmax, ltot, c->stream);
-    if (c->nboxes > 0) c->launches += 4;   // one scan, close, fill
+    if (c->nboxes > 0) c->launches += 5;   // classify, count, one scan, close, fill
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
@@ -1379,7 +1382,7 @@ void sph_destroy(sph_ctx *c) {
     DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
-                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs,
+                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs, &c->b_heavy,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,

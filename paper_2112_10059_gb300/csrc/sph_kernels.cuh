@@ -79,6 +79,7 @@ struct ListDev {
     int *u_src, *v_src, *w_src, *x_src;
     short *v_oc;                            // offset code (ox+3) + 7(oy+3) + 49(oz+3)
     int *v_trg;                             // target box of each V entry
+    int *heavy, *nheavy;                    // boxes that can have list entries ([nboxes]), their count
 };
 void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
                         int *totals, int *err, cudaStream_t st);
