@@ -182,11 +182,12 @@ __device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__res
         return;
     }
     tc::fence_after_sync();
-    const int i = warp * 32 + lane;   // TMEM lane = operator row
-#pragma unroll
-    for (int c0 = 0; c0 < TCN; c0 += 16) {
+    // warp w reads TMEM lanes 32 (w % 4) ..; with 8 warps, w and w + 4 take half the columns each
+    const int q = warp & 3, i = q * 32 + lane;   // TMEM lane = operator row
+    const int cw = TCN / ((int)blockDim.x / 128), cbeg = (warp >> 2) * cw;
+    for (int c0 = cbeg; c0 < cbeg + cw; c0 += 16) {
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         if (i < n) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -223,7 +224,7 @@ __device__ __forceinline__ void tile_teardown(const TcSmem &s) {
 }
 
 // ---------------------------------------------------------------- M2L over offset-grouped V pairs
-__global__ void __launch_bounds__(128) k_m2l_tc(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
+__global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
                                                 int *err) {
     extern __shared__ uint8_t smem_raw[];
     const int tile = blockIdx.x;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
 }
 
 // ---------------------------------------------------------------- L2L for one level
-__global__ void __launch_bounds__(128) k_l2l_tc(FmmDev F, int level, int parent_begin, int parent_count,
+__global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_begin, int parent_count,
                                                 const uint16_t *__restrict__ images, int *err) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem s = carve(smem_raw);
@@ -1070,7 +1071,7 @@ void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *ima
         return;
     }
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;
-    k_m2l_tc<<<grid, 128, TC_SMEM, st>>>(F, Pd, images, err);
+    k_m2l_tc<<<grid, 256, TC_SMEM, st>>>(F, Pd, images, err);
 }
 
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
@@ -1078,7 +1079,7 @@ void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_c
     if (parent_count <= 0 || level < 3) return;
     tc_init_attributes();
     dim3 grid((parent_count + TCN - 1) / TCN, 8);
-    k_l2l_tc<<<grid, 128, TC_SMEM, st>>>(F, level, parent_begin, parent_count, images, err);
+    k_l2l_tc<<<grid, 256, TC_SMEM, st>>>(F, level, parent_begin, parent_count, images, err);
 }
 
 }  // namespace sph
