@@ -191,54 +191,53 @@ __global__ void __launch_bounds__(256) k_l2l_gemm(FmmDev F, int level, int paren
 }
 
 // ---------------------------------------------------------------- V pairs grouped by offset
-// key = level * 316 + slot.  Within a key the pair order is whatever the atomic
-// cursor gives; every pair is present exactly once.
-__global__ void k_vpairs_count(FmmDev F, PairsDev Pd, int nV) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nV) return;
-    int key = F.T.b_level[F.L.v_trg[e]] * NSLOT + F.O.slot_of_code[F.L.v_oc[e]];
-    atomicAdd(Pd.cnt + key, 1);
-}
-
-__global__ void k_vpairs_fill(FmmDev F, PairsDev Pd, int nV) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nV) return;
-    int key = F.T.b_level[F.L.v_trg[e]] * NSLOT + F.O.slot_of_code[F.L.v_oc[e]];
-    int pos = Pd.off[key] + atomicAdd(Pd.cursor + key, 1);
-    Pd.trg[pos] = F.L.v_trg[e];
-    Pd.src[pos] = F.L.v_src[e];
-}
-
-__global__ void k_vpairs_tiles(PairsDev Pd) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < Pd.nkeys) Pd.tile_cnt[k] = (Pd.cnt[k] + TN - 1) / TN;
-}
-
-__global__ void k_vpairs_close(PairsDev Pd, const int *tot_pairs, const int *tot_tiles) {
-    if (threadIdx.x == 0) {
-        Pd.off[Pd.nkeys] = *tot_pairs;
-        Pd.tile_off[Pd.nkeys] = *tot_tiles;
+// key = level * 316 + slot.  The list kernels count the pairs per key, scan the counts and
+// place every pair in its key's range (any order within a key).  One CTA then cuts every
+// key's range into tiles of TN pairs: tile counts, their exclusive scan (the tile offsets),
+// the closing offsets and the key of every tile.
+__global__ void __launch_bounds__(1024) k_vpairs_finish(PairsDev Pd) {
+    __shared__ int ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int per = (Pd.nkeys + 1023) / 1024;
+    const int k0 = min(tid * per, Pd.nkeys), k1 = min(k0 + per, Pd.nkeys);
+    int s = 0;
+    for (int k = k0; k < k1; ++k) {
+        const int t = (Pd.cnt[k] + TN - 1) / TN;
+        Pd.tile_cnt[k] = t;
+        s += t;
+    }
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int y = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    int x = (w ? ws[w - 1] : 0) + inc - s;
+    for (int k = k0; k < k1; ++k) {
+        Pd.tile_off[k] = x;
+        for (int t = 0; t < Pd.tile_cnt[k]; ++t) Pd.tile_key[x + t] = k;
+        x += Pd.tile_cnt[k];
+    }
+    if (tid == 1023) {
+        Pd.tile_off[Pd.nkeys] = ws[31];
+        Pd.total_tiles[0] = ws[31];
+        Pd.off[Pd.nkeys] = Pd.total_tiles[1];
     }
 }
 
-// tile -> key table (tiles of a key are consecutive)
-__global__ void k_vpairs_tile_keys(PairsDev Pd) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= Pd.nkeys) return;
-    for (int t = Pd.tile_off[k]; t < Pd.tile_off[k] + Pd.tile_cnt[k]; ++t) Pd.tile_key[t] = k;
-}
-
-void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cudaStream_t st) {
-    cudaMemsetAsync(Pd.cnt, 0, sizeof(int) * Pd.nkeys, st);
-    cudaMemsetAsync(Pd.cursor, 0, sizeof(int) * Pd.nkeys, st);
-    if (nV > 0) k_vpairs_count<<<(nV + 255) / 256, 256, 0, st>>>(F, Pd, nV);
-    scan_exclusive(Pd.cnt, Pd.off, Pd.nkeys, Pd.total_tiles + 1, scan_tmp, st);
-    if (nV > 0) k_vpairs_fill<<<(nV + 255) / 256, 256, 0, st>>>(F, Pd, nV);
-    k_vpairs_tiles<<<(Pd.nkeys + 255) / 256, 256, 0, st>>>(Pd);
-    scan_exclusive(Pd.tile_cnt, Pd.tile_off, Pd.nkeys, Pd.total_tiles, scan_tmp, st);
-    k_vpairs_close<<<1, 32, 0, st>>>(Pd, Pd.total_tiles + 1, Pd.total_tiles);
-    k_vpairs_tile_keys<<<(Pd.nkeys + 255) / 256, 256, 0, st>>>(Pd);
-}
+void vpairs_finish(const PairsDev &Pd, cudaStream_t st) { k_vpairs_finish<<<1, 1024, 0, st>>>(Pd); }
 
 // One CTA per tile of up to 64 V pairs sharing (level, offset): d_B += M2L_{l,o} u_A, scatter-added.
 __global__ void __launch_bounds__(256) k_m2l_pairs(FmmDev F, PairsDev Pd) {

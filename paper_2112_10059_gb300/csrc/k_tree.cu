@@ -504,7 +504,7 @@ __device__ __forceinline__ int coarse_leaf_src(const TreeDev &T, int lq, int qx,
 }
 
 template <bool FILL>
-__global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, int D) {
+__global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, PairsDev Pd, int D) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -602,11 +602,21 @@ __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, int D)
                     hit = vs[m] != 0;
                 }
                 const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                if (FILL && hit) {
-                    const int pos = pV + nV + __popc(hm & lt);
-                    L.v_src[pos] = ba[m];
-                    L.v_trg[pos] = b;
-                    L.v_oc[pos] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
+                if (hit) {
+                    const int key = l * NSLOT + m2l_slot(ox, oy, oz);
+                    if (FILL) {
+                        const int pos = pV + nV + __popc(hm & lt);
+                        const int A = ba[m];
+                        L.v_src[pos] = A;
+                        L.v_trg[pos] = b;
+                        L.v_oc[pos] = (short)((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3));
+                        // the pair in its (level, offset) bucket, in any order within the bucket
+                        const int q = Pd.off[key] + atomicAdd(Pd.cursor + key, 1);
+                        Pd.trg[q] = b;
+                        Pd.src[q] = A;
+                    } else {
+                        atomicAdd(Pd.cnt + key, 1);
+                    }
                 }
                 nV += __popc(hm);
             }
@@ -619,20 +629,21 @@ __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, int D)
 
 constexpr int LISTS_WARP_GRID = 152 * 8;
 
-void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
-                        int *totals /* device [4] */, int *err, cudaStream_t st) {
+void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
+                        int *scan_tmp, int *totals /* device [4] */, int *err, cudaStream_t st) {
     if (nboxes <= 0) {
         cudaMemsetAsync(totals, 0, 4 * sizeof(int), st);
         return;
     }
     cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
     k_lists_classify<<<(nboxes + 255) / 256, 256, 0, st>>>(T, L, nboxes);
-    k_lists_warp<false><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, D);
+    k_lists_warp<false><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, Pd, D);
     ScanSet S{};
     S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;
     S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
     for (int a = 0; a < 4; ++a) S.total[a] = totals + a;
     scan_exclusive_multi(S, 4, nboxes, scan_tmp, err, st);
+    scan_exclusive(Pd.cnt, Pd.off, Pd.nkeys, Pd.total_tiles + 1, scan_tmp, st, err);
 }
 
 __global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ totals) {
@@ -644,11 +655,12 @@ __global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ t
     }
 }
 
-void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax,
+void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
                        const int *totals, cudaStream_t st) {
     if (nboxes <= 0) return;
     k_close_offsets<<<1, 32, 0, st>>>(L, nboxes, totals);
-    k_lists_warp<true><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, D);
+    k_lists_warp<true><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, Pd, D);
+    vpairs_finish(Pd, st);
 }
 
 }  // namespace sph

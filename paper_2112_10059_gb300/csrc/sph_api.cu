@@ -96,7 +96,7 @@ struct sph_ctx {
     DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
-    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pairs, b_heavy;
+    DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pkeys, b_ppairs, b_heavy;
     DevBuf b_ueq, b_dchk;
     DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf b_err;                // device error flags of the tensor-core tiles
@@ -285,6 +285,23 @@ ListDev list_dev(sph_ctx *c) {
     return L;
 }
 
+// V pairs grouped by (level, offset) key: per-key arrays in b_pkeys (sized at the list count),
+// the pairs and the tile -> key table in b_ppairs (sized at the list fill)
+PairsDev pairs_dev(sph_ctx *c) {
+    PairsDev Pd;
+    const int nkeys = (c->Lmax + 1) * NSLOT;
+    const int nV = std::max(c->list_tot[1], 1);
+    int *pk = P<int>(c->b_pkeys);
+    Pd.nkeys = nkeys;
+    Pd.cnt = pk; Pd.off = pk + nkeys; Pd.cursor = pk + 2 * nkeys + 1;
+    Pd.tile_cnt = pk + 3 * nkeys + 1; Pd.tile_off = pk + 4 * nkeys + 1;
+    Pd.total_tiles = pk + 5 * nkeys + 2;
+    int *pp = P<int>(c->b_ppairs);
+    Pd.trg = pp; Pd.src = pp ? pp + nV : nullptr;
+    Pd.tile_key = pp ? pp + 2 * (size_t)nV : nullptr;
+    return Pd;
+}
+
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
 // [43] scan give-up flag, [44..48) list totals, [48] tensor-core error flags
@@ -348,10 +365,14 @@ int tree_read_count(sph_ctx *c) {
     ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
     ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
     ENS(c->b_heavy, (size_t)nb * sizeof(int));
+    const int nkeys = (Lmax + 1) * NSLOT;
+    ENS(c->b_pkeys, (5 * (size_t)nkeys + 10) * sizeof(int));
+    CK(cudaMemsetAsync(c->b_pkeys.p, 0, (5 * (size_t)nkeys + 10) * sizeof(int), c->stream));
     ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
-    lists_count_launch(tree_dev(c), L, c->nboxes, c->D, Lmax, P<int>(c->b_scan), ltot, ltot - 1, c->stream);
+    lists_count_launch(tree_dev(c), L, pairs_dev(c), c->nboxes, c->D, Lmax, P<int>(c->b_scan), ltot, ltot - 1,
+                       c->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
@@ -367,10 +388,15 @@ int lists_fill(sph_ctx *c) {
     ENS(c->b_vtrg, std::max(1, c->list_tot[1]) * sizeof(int));
     ENS(c->b_wsrc, std::max(1, c->list_tot[2]) * sizeof(int));
     ENS(c->b_xsrc, std::max(1, c->list_tot[3]) * sizeof(int));
+    {
+        const size_t nV = std::max(1, c->list_tot[1]), nkeys = (size_t)(c->Lmax + 1) * NSLOT;
+        ENS(c->b_ppairs, (2 * nV + nV / 64 + nkeys + 1) * sizeof(int));
+    }
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
-    lists_fill_launch(tree_dev(c), L, c->nboxes, c->D, c->Lmax, ltot, c->stream);
-    if (c->nboxes > 0) c->launches += 5;   // classify, count, one scan, close, fill
+    lists_fill_launch(tree_dev(c), L, pairs_dev(c), c->nboxes, c->D, c->Lmax, ltot, c->stream);
+    // classify, count, list and key scans, close, fill, tiles of the V pairs
+    if (c->nboxes > 0) c->launches += 7;
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
@@ -513,11 +539,6 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
     ENS(c->b_work, (3 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
-    const int nV = c->list_tot[1];
-    const int nkeys = (c->Lmax + 1) * NSLOT;
-    const size_t max_tiles = (size_t)std::max(nV, 1) / 64 + nkeys + 1;
-    ENS(c->b_pairs, ((size_t)6 * nkeys + 8 + 2 * (size_t)std::max(nV, 1) + max_tiles) * sizeof(int));
-    ENS(c->b_scan, scan_tmp_ints(nkeys + 1) * sizeof(int) + 64);
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
     F.T = tree_dev(c);
@@ -548,14 +569,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.w_leaf = S.w_src + std::max(nb, 1);
     S.w_p2p = S.w_leaf + std::max(nb, 1);
     S.w_cnt = S.w_p2p + std::max(nb, 1);
-    int *pb = P<int>(c->b_pairs);
-    PairsDev &Pd = S.Pd;
-    Pd.nkeys = nkeys;
-    Pd.cnt = pb; Pd.off = pb + nkeys; Pd.cursor = pb + 2 * nkeys + 1;
-    Pd.tile_cnt = pb + 3 * nkeys + 1; Pd.tile_off = pb + 4 * nkeys + 1;
-    Pd.total_tiles = pb + 5 * nkeys + 2;
-    Pd.trg = pb + 5 * nkeys + 8; Pd.src = Pd.trg + std::max(nV, 1);
-    Pd.tile_key = Pd.src + std::max(nV, 1);
+    S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
     tc_init_attributes();
@@ -598,8 +612,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         // every M2L (all levels) and P2L first, then L2L top-down: d_child += L2L d_parent
         // needs the parent's d complete, which holds once the level above is done.
         const int nV = c->list_tot[1];
-        vpairs_build(F, S.Pd, nV, P<int>(c->b_scan), c->stream);
-        c->launches += 5 + (nV > 0 ? 2 : 0);
+        // (the V pairs were grouped by key with the lists)
         if (tm) tm->mark_at(5, c->stream);
         if (S.tc) {
             CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));
@@ -1382,7 +1395,7 @@ void sph_destroy(sph_ctx *c) {
     DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
-                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pairs, &c->b_heavy,
+                     &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pkeys, &c->b_ppairs, &c->b_heavy,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
                      &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,

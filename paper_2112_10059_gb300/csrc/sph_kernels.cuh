@@ -81,10 +81,13 @@ struct ListDev {
     int *v_trg;                             // target box of each V entry
     int *heavy, *nheavy;                    // boxes that can have list entries ([nboxes]), their count
 };
-void lists_count_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, int *scan_tmp,
-                        int *totals, int *err, cudaStream_t st);
-void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, int Lmax, const int *totals,
-                       cudaStream_t st);
+struct PairsDev;
+// The V pairs are also counted per (level, offset) key by the count pass and bucketed by the
+// fill pass (the grouping the M2L tiles read); `Pd` per-key arrays zeroed before the count.
+void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
+                        int *scan_tmp, int *totals, int *err, cudaStream_t st);
+void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
+                       const int *totals, cudaStream_t st);
 
 // ---------------------------------------------------------------- operators
 // Far-field representation of a box (Section 2.4: artificial source points
@@ -97,6 +100,16 @@ void lists_fill_launch(const TreeDev &T, const ListDev &L, int nboxes, int D, in
 enum FarMethod { FAR_CHEB = 0, FAR_SURFACE = 1 };
 constexpr int MAXPAD = 512;          // largest padded state length (p <= 8, NP <= 10)
 constexpr int NSLOT = 316;           // M2L offsets o in [-3,3]^3 \ [-1,1]^3
+
+// Slot of a V offset (|o|_inf >= 2, components in [-3, 3]): its rank among those offsets in
+// the order of the code (ox + 3) + 7 (oy + 3) + 49 (oz + 3), i.e. the code minus the number of
+// adjacent offsets (components in {-1, 0, 1}) with a smaller code.
+__host__ __device__ __forceinline__ int m2l_slot(int ox, int oy, int oz) {
+    auto below = [](int v) { return v < -1 ? 0 : (v > 1 ? 3 : v + 1); };   // adjacent values < v
+    const bool ny = oy >= -1 && oy <= 1, nz = oz >= -1 && oz <= 1;
+    const int code = (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);
+    return code - (9 * below(oz) + (nz ? 3 * below(oy) + (ny ? below(ox) : 0) : 0));
+}
 constexpr int ETAB_MAX_EDGE = 16;    // surface L2P tables for leaf boxes of edge <= 16 cells
 
 // Surface radii in units of the box half-width: upward equivalent / check,
@@ -211,7 +224,8 @@ struct PairsDev {
     int *total_tiles;     // [1]
     int *tile_key;        // [nV / 64 + nkeys]: key of every tile (one load instead of a search per CTA)
 };
-void vpairs_build(const FmmDev &F, const PairsDev &Pd, int nV, int *scan_tmp, cudaStream_t st);
+// per-key tile counts and offsets, the closing offsets and the tile -> key table (one CTA)
+void vpairs_finish(const PairsDev &Pd, cudaStream_t st);
 void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cudaStream_t st);
 // tensor-core (tcgen05, BF16 x3) translations; require npad == 128
 bool tc_supported(const OpsDev &O);
