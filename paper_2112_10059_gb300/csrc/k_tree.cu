@@ -21,6 +21,8 @@
 //   X: A leaf with sources, coarser than B, A adjacent to parent(B), not to B.
 // k_lists_classify + k_lists_warp<false> count, one scan gives the four CSR offset arrays,
 // k_lists_warp<true> fills.
+#include <algorithm>
+
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -216,15 +218,18 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
 // carried out by the whole block, so that no warp runs them one lane at a time.
 constexpr int RANGE_PER = 4, RANGE_T = 256;
 
-__global__ void __launch_bounds__(RANGE_T) k_tree_ranges(int n, const uint32_t *__restrict__ key, int D, int Lmax,
-                                                         int *__restrict__ beg, int *__restrict__ end) {
+__global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ n_dev, const uint32_t *__restrict__ key,
+                                                         int D, int Lmax, int *__restrict__ beg, int *__restrict__ end) {
     __shared__ uint32_t task_key[2 * RANGE_PER * RANGE_T];
     __shared__ int task_val[2 * RANGE_PER * RANGE_T];
     __shared__ uint8_t task_lvl[2 * RANGE_PER * RANGE_T];   // first level | 0x80 for an end
     __shared__ int ntask;
-    const int t = blockIdx.x * RANGE_T + threadIdx.x;
+    const int n = *n_dev;                 // a negative count (failed selection) reads as none
     const int lane = threadIdx.x & 31;
-    const long long i0 = (long long)t * RANGE_PER;
+    // grid-stride over chunks of RANGE_T * RANGE_PER keys (uniform across the block)
+    for (long long base = (long long)blockIdx.x * RANGE_T * RANGE_PER; base < n;
+         base += (long long)gridDim.x * RANGE_T * RANGE_PER) {
+    const long long i0 = base + (long long)threadIdx.x * RANGE_PER;
     if (threadIdx.x == 0) ntask = 0;
     uint32_t k[RANGE_PER];
     if (i0 + RANGE_PER <= n) {
@@ -272,6 +277,8 @@ __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(int n, const uint32_t *
         int64_t off = dense_off(l0);
         for (int l = l0; l <= Lmax; ++l, off = 8 * off + 1) out[off + (kk >> (3 * (D - l)))] = val;
     }
+    __syncthreads();                      // the task queue is reused by the next chunk
+    }
 }
 
 __device__ __forceinline__ int level_of_slot(int64_t s, int Lmax) {
@@ -304,7 +311,8 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
                                 const int *__restrict__ pos, const int *__restrict__ rsb,
                                 const int *__restrict__ rse, const int *__restrict__ rtb,
                                 const int *__restrict__ rte, const int *__restrict__ total,
-                                const uint32_t *__restrict__ skey, int ns, const uint32_t *__restrict__ tkey, int nt,
+                                const uint32_t *__restrict__ skey, const int *__restrict__ ns_dev,
+                                const uint32_t *__restrict__ tkey, const int *__restrict__ nt_dev,
                                 uint8_t *__restrict__ vsrc) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= Lmax) {       // level table (threads 0..Lmax)
@@ -327,8 +335,8 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
     int sb = rsb[s], se = rse[s], tb = rtb[s], te = rte[s];
     // an empty range starts where the slot's first key would be inserted
     const uint32_t lo = (uint32_t)m << (3 * (D - l));
-    if (se == sb) sb = se = lower_bound_u32(skey, 0, ns, lo);
-    if (te == tb) tb = te = lower_bound_u32(tkey, 0, nt, lo);
+    if (se == sb) sb = se = lower_bound_u32(skey, 0, max(*ns_dev, 0), lo);
+    if (te == tb) tb = te = lower_bound_u32(tkey, 0, max(*nt_dev, 0), lo);
     T.b_level[idx] = l;
     T.b_key[idx] = (uint32_t)m;
     T.b_sb[idx] = sb; T.b_se[idx] = se;
@@ -388,14 +396,15 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
     cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
     constexpr int RB = RANGE_T * RANGE_PER;
-    if (A.ns > 0) k_tree_ranges<<<(A.ns + RB - 1) / RB, RANGE_T, 0, st>>>(A.ns, A.skey, A.D, A.Lmax, A.rsb, A.rse);
-    if (A.nt > 0) k_tree_ranges<<<(A.nt + RB - 1) / RB, RANGE_T, 0, st>>>(A.nt, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
+    const int rg = (int)std::min<int64_t>(((int64_t)A.ncap + RB - 1) / RB, 152 * 8);
+    k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.ns_dev, A.skey, A.D, A.Lmax, A.rsb, A.rse);
+    k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
     k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);
     k_tree_emit_all<<<grid, 256, 0, st>>>(A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
-                                          A.rte, total, A.skey, A.ns, A.tkey, A.nt, A.vsrc);
+                                          A.rte, total, A.skey, A.ns_dev, A.tkey, A.nt_dev, A.vsrc);
     const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
     if (npar > 0 && A.occ && A.near) {
         const int g2 = (int)((npar + 255) / 256);
@@ -439,11 +448,11 @@ __device__ __forceinline__ int lookup(const TreeDev &T, int level, int x, int y,
 // then takes one queued box per warp: the 27 neighbour slots of U / W and of X one per
 // lane, the 216 V candidates 32 at a time, entries placed in slot order by warp prefix
 // sums, so every list comes out exactly as a serial walk of the slots would write it.
-__global__ void k_lists_classify(TreeDev T, ListDev L, int nboxes) {
+__global__ void k_lists_classify(TreeDev T, ListDev L, int cap, const int *__restrict__ nboxes_dev) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nboxes) return;
+    if (b >= cap) return;
     bool heavy = false;
-    if (T.b_te[b] > T.b_tb[b]) {
+    if (b < *nboxes_dev && T.b_te[b] > T.b_tb[b]) {
         const int l = T.b_level[b];
         // nothing with sources anywhere around the parent: every list is empty
         heavy = !(l >= 1 && T.near && !T.near[dense_off(l - 1) + (T.b_key[b] >> 3)]);
@@ -629,14 +638,15 @@ __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, PairsD
 
 constexpr int LISTS_WARP_GRID = 152 * 8;
 
-void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
-                        int *scan_tmp, int *totals /* device [4] */, int *err, cudaStream_t st) {
+void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
+                        int D, int Lmax, int *scan_tmp, int *totals /* device [4] */, int *err, cudaStream_t st) {
+    const int nboxes = cap;   // counts and offsets span every slot; the ones past the last box stay 0
     if (nboxes <= 0) {
         cudaMemsetAsync(totals, 0, 4 * sizeof(int), st);
         return;
     }
     cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
-    k_lists_classify<<<(nboxes + 255) / 256, 256, 0, st>>>(T, L, nboxes);
+    k_lists_classify<<<(nboxes + 255) / 256, 256, 0, st>>>(T, L, cap, nboxes_dev);
     k_lists_warp<false><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, Pd, D);
     ScanSet S{};
     S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;

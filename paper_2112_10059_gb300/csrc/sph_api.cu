@@ -87,6 +87,8 @@ struct sph_ctx {
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     bool l2lp_fused = true;           // deepest level of edge-4 leaves: L2L and L2P in one tensor-core kernel
     bool l2lp_used = false;           // the last eval ran the fused kernel
+    bool defer_sync = true;           // fixed leaf size: one host sync for selection, tree and list counts
+    int list_cap = 0;                 // slots of every tree level: length of the list count / offset arrays
     int near_mode = SPH_NEAR_EXP;     // requested near-field form
     double r_s = 0.0;                 // strategy 3 ratio (0: off)
     DevBuf b_skip;
@@ -272,7 +274,7 @@ TreeDev tree_dev(sph_ctx *c) {
 
 ListDev list_dev(sph_ctx *c) {
     ListDev L;
-    int nb = std::max(c->nboxes, 1);
+    int nb = std::max(c->list_cap, 1);
     int *cnt = P<int>(c->b_lcnt), *off = P<int>(c->b_loff);
     L.u_cnt = cnt; L.v_cnt = cnt + nb; L.w_cnt = cnt + 2 * nb; L.x_cnt = cnt + 3 * nb;
     L.u_off = off; L.v_off = off + (nb + 1); L.w_off = off + 2 * (nb + 1); L.x_off = off + 3 * (nb + 1);
@@ -304,7 +306,9 @@ PairsDev pairs_dev(sph_ctx *c) {
 
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
-// [43] scan give-up flag, [44..48) list totals, [48] tensor-core error flags
+// [43] scan give-up flag, [44..48) list totals, [48] tensor-core error flags.
+// The tree and the list counts read the selection's point counts and the tree's box count
+// from device memory, so selection, tree and list counting need one host sync in all.
 int tree_queue(sph_ctx *c) {
     const int D = c->D;
     int S = c->leaf_eff;
@@ -329,7 +333,10 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_leaf, cap);
     TreeArgs A;
     A.T = tree_dev(c);
-    A.ns = (int)c->ns; A.nt = (int)c->nt; A.S = S; A.D = D; A.Lmax = Lmax;
+    A.ns_dev = P<int>(c->b_tot); A.nt_dev = P<int>(c->b_tot) + 1;
+    A.ncap = (int)std::min<int64_t>((int64_t)c->nx * c->ny * c->nz, INT32_MAX);
+    A.S = S; A.D = D; A.Lmax = Lmax;
+    c->list_cap = (int)dense_total;
     A.skey = P<uint32_t>(c->b_skey); A.tkey = P<uint32_t>(c->b_tkey);
     A.flag = P<int>(c->b_flag); A.pos = P<int>(c->b_pos);
     A.rsb = P<int>(c->b_rng); A.rse = A.rsb + dense_total; A.rtb = A.rse + dense_total; A.rte = A.rtb + dense_total;
@@ -339,17 +346,39 @@ int tree_queue(sph_ctx *c) {
     CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
     // ranges (sources, targets), existence flags, scan, emit, source occupancy and its dilation
-    c->launches += (A.ns > 0) + (A.nt > 0) + 3 + (Lmax >= 1 ? 2 : 0);
+    c->launches += 2 + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->pinned + 43, A.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
-// after a sync: level counts -> box count; queue the list counting
-int tree_read_count(sph_ctx *c) {
+// after tree_queue, no sync: the list counts over every slot (the box count stays on the
+// device), their offsets, the V pairs per key; totals and the scans' flag read back
+int lists_count_queue(sph_ctx *c) {
     const int Lmax = c->Lmax;
-    if (c->pinned[43] != 0) return fail(c, SPH_ETIMEOUT, "the tree scan gave up waiting for a preceding tile");
+    const int cap = std::max(c->list_cap, 1);
+    ENS(c->b_lcnt, 4 * (size_t)cap * sizeof(int));
+    ENS(c->b_loff, 4 * (size_t)(cap + 1) * sizeof(int));
+    ENS(c->b_heavy, (size_t)cap * sizeof(int));
+    const int nkeys = (Lmax + 1) * NSLOT;
+    ENS(c->b_pkeys, (5 * (size_t)nkeys + 10) * sizeof(int));
+    CK(cudaMemsetAsync(c->b_pkeys.p, 0, (5 * (size_t)nkeys + 10) * sizeof(int), c->stream));
+    ENS(c->b_scan, scan_tmp_ints(cap + 1) * sizeof(int) + 64);
+    ListDev L = list_dev(c);
+    int *ltot = P<int>(c->b_tot) + 4;
+    const int *nboxes_dev = P<int>(c->b_pos) + dense_off(Lmax + 1);   // the tree scan's total
+    lists_count_launch(tree_dev(c), L, pairs_dev(c), c->list_cap, nboxes_dev, c->D, Lmax, P<int>(c->b_scan), ltot,
+                       ltot - 1, c->stream);
+    c->launches += 4;   // classify, count, list and key scans
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return SPH_OK;
+}
+
+// after the sync: level counts -> box count (the scans' flag covers the tree and the list counts)
+int tree_levels_read(sph_ctx *c) {
+    const int Lmax = c->Lmax;
+    if (c->pinned[43] != 0) return fail(c, SPH_ETIMEOUT, "a tree or list scan gave up waiting for a preceding tile");
     c->lvl_count.assign(Lmax + 1, 0);
     c->lvl_base.assign(Lmax + 1, 0);
     int64_t tot = 0;
@@ -361,20 +390,6 @@ int tree_read_count(sph_ctx *c) {
     }
     if (tot > dense_off(Lmax + 1)) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
     c->nboxes = (int)tot;
-    int nb = std::max(c->nboxes, 1);
-    ENS(c->b_lcnt, 4 * (size_t)nb * sizeof(int));
-    ENS(c->b_loff, 4 * (size_t)(nb + 1) * sizeof(int));
-    ENS(c->b_heavy, (size_t)nb * sizeof(int));
-    const int nkeys = (Lmax + 1) * NSLOT;
-    ENS(c->b_pkeys, (5 * (size_t)nkeys + 10) * sizeof(int));
-    CK(cudaMemsetAsync(c->b_pkeys.p, 0, (5 * (size_t)nkeys + 10) * sizeof(int), c->stream));
-    ENS(c->b_scan, scan_tmp_ints(nb + 1) * sizeof(int) + 64);
-    ListDev L = list_dev(c);
-    int *ltot = P<int>(c->b_tot) + 4;
-    lists_count_launch(tree_dev(c), L, pairs_dev(c), c->nboxes, c->D, Lmax, P<int>(c->b_scan), ltot, ltot - 1,
-                       c->stream);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
@@ -395,8 +410,7 @@ int lists_fill(sph_ctx *c) {
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
     lists_fill_launch(tree_dev(c), L, pairs_dev(c), c->nboxes, c->D, c->Lmax, ltot, c->stream);
-    // classify, count, list and key scans, close, fill, tiles of the V pairs
-    if (c->nboxes > 0) c->launches += 7;
+    if (c->nboxes > 0) c->launches += 3;   // close, fill, tiles of the V pairs
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;
@@ -404,11 +418,11 @@ int lists_fill(sph_ctx *c) {
 
 int run_tree(sph_ctx *c) {
     int r = tree_queue(c);
+    if (!r) r = lists_count_queue(c);
     if (r) return r;
     CK(cudaStreamSynchronize(c->stream));
-    r = tree_read_count(c);
+    r = tree_levels_read(c);
     if (r) return r;
-    CK(cudaStreamSynchronize(c->stream));
     return lists_fill(c);
 }
 
@@ -777,16 +791,21 @@ int fmm_queue_graph(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
 }
 
 // tree + operators + passes for the current selection (used by eval and by the autotuner)
-int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm) {
-    int r = run_tree(c);
-    if (r) return r;
+// the passes after the tree: operators, pass state, FMM passes (graph)
+int fmm_after_tree(sph_ctx *c, float *out, PhaseTimer *tm) {
     if (tm) tm->mark_at(2, c->stream);
-    r = run_ops(c);
+    int r = run_ops(c);
     if (r) return r;
     PassState S;
     r = fmm_prepare(c, S);
     if (r) return r;
     return c->eval_graph ? fmm_queue_graph(c, S, out, tm) : fmm_queue(c, S, out, tm);
+}
+
+int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm) {
+    int r = run_tree(c);
+    if (r) return r;
+    return fmm_after_tree(c, out, tm);
 }
 
 // Problem class of the autotuner's cache: grid shape, far-field form and arithmetic, and the
@@ -900,6 +919,44 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     c->launches = 0;
     int r = check_previous_tc(c);
     if (r) return r;
+    if (c->defer_sync && c->leaf_size != 0 && c->near_mode != SPH_NEAR_AUTO) {
+        // fixed leaf size: selection, tree and list counts queued back to back, one sync
+        r = select_queue(c);
+        if (r) return r;
+        tm.mark_at(1, c->stream);
+        if ((int64_t)c->nx * c->ny * c->nz > 0)
+            CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
+        c->leaf_eff = c->leaf_size;
+        r = resolve_near(c, out);
+        if (!r) r = tree_queue(c);
+        if (!r) r = lists_count_queue(c);
+        if (r) return r;
+        CK(cudaStreamSynchronize(c->stream));
+        r = select_read(c);
+        if (r) return r;
+        if (c->nt == 0) {
+            c->have_tree = false;
+            if (stats) {
+                memset(stats, 0, sizeof *stats);
+                stats->n_sources = c->ns;
+                stats->depth = c->D;
+                stats->n_launches = c->launches;
+            }
+            return SPH_OK;
+        }
+        r = tree_levels_read(c);
+        if (!r) r = lists_fill(c);
+        if (!r) r = fmm_after_tree(c, out, &tm);
+        if (r) return r;
+        if (stats) {
+            CK(cudaStreamSynchronize(c->stream));
+            if ((c->tc_used && c->pinned[48] != 0) || (c->l2p_tc_used && c->pinned[49] != 0))
+                return fail(c, SPH_ETIMEOUT, "a tensor-core tile gave up waiting (code %d)",
+                            c->pinned[48] | c->pinned[49]);
+            fill_stats(c, stats, &tm);
+        }
+        return SPH_OK;
+    }
     r = run_select(c);
     if (r) return r;
     tm.mark_at(1, c->stream);
@@ -987,6 +1044,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
     sub->l2lp_fused = parent->l2lp_fused;
+    sub->defer_sync = parent->defer_sync;
     sub->near_mode = parent->near_mode;
     sub->r_s = parent->r_s;
     sub->launches = 0;
@@ -1059,19 +1117,16 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
             if (r) return sub_fail(c, sub, r, i);
         }
     }
-    // phases 2-3: trees, list counts, list fills -- two more synchronisations
+    // phases 2-3: trees and list counts, then list fills -- one more synchronisation
     for (int i : live) {
         int r = tree_queue(c->subs[i]);
+        if (!r) r = lists_count_queue(c->subs[i]);
         if (r) return sub_fail(c, c->subs[i], r, i);
     }
     for (int i : live) {
         CK(cudaStreamSynchronize(c->subs[i]->stream));
-        int r = tree_read_count(c->subs[i]);
-        if (r) return sub_fail(c, c->subs[i], r, i);
-    }
-    for (int i : live) {
-        CK(cudaStreamSynchronize(c->subs[i]->stream));
-        int r = lists_fill(c->subs[i]);
+        int r = tree_levels_read(c->subs[i]);
+        if (!r) r = lists_fill(c->subs[i]);
         if (!r) r = run_ops(c->subs[i]);
         if (r) return sub_fail(c, c->subs[i], r, i);
     }
@@ -1365,6 +1420,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;
+    if (const char *e = getenv("SPH_DEFER_SYNC")) c->defer_sync = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_FAR")) {

@@ -60,7 +60,9 @@ struct TreeDev {
 };
 struct TreeArgs {
     TreeDev T;
-    int ns, nt, S, D, Lmax;
+    const int *ns_dev, *nt_dev;   // point counts (device: the selection's totals)
+    int ncap;                     // upper bound of either count (cells of the grid)
+    int S, D, Lmax;
     const uint32_t *skey, *tkey;
     int *flag, *pos;     // dense scratch over every level's slots, dense_off(Lmax + 1) (+1 for pos)
     int *rsb, *rse, *rtb, *rte;   // dense point ranges of every slot of every level
@@ -84,8 +86,10 @@ struct ListDev {
 struct PairsDev;
 // The V pairs are also counted per (level, offset) key by the count pass and bucketed by the
 // fill pass (the grouping the M2L tiles read); `Pd` per-key arrays zeroed before the count.
-void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
-                        int *scan_tmp, int *totals, int *err, cudaStream_t st);
+// cap: slots of every level (upper bound of the box count, the length of the list count and
+// offset arrays); nboxes_dev: the tree's box count on the device
+void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
+                        int D, int Lmax, int *scan_tmp, int *totals, int *err, cudaStream_t st);
 void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
                        const int *totals, cudaStream_t st);
 
