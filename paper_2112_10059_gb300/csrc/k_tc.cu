@@ -21,6 +21,8 @@
 //     DRAM read per element.
 // Every wait is bounded; on expiry the tile records an error code and still
 // releases its TMEM.
+#include <algorithm>
+
 #include "sph_kernels.cuh"
 #include "tc_sm103.cuh"
 
@@ -843,7 +845,7 @@ __device__ __forceinline__ void lp_store(uint8_t *hi, uint8_t *lo, const float4 
 }
 
 __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int parent_begin, int parent_count,
-                                                     const uint16_t *__restrict__ img_e,
+                                                     int ppc, const uint16_t *__restrict__ img_e,
                                                      const uint16_t *__restrict__ img_c, float *__restrict__ out,
                                                      int *err) {
     extern __shared__ uint8_t smem_raw[];
@@ -865,10 +867,10 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     const size_t img_elems = (size_t)2 * 64 * TCK;          // one image: hi then lo
     int any = 0;
     if (tid < TCM) {
-        const int i = blockIdx.x * TCM + tid;
+        const int i = blockIdx.x * ppc + tid;
         const int p = parent_begin + i;
         int P = -1;
-        if (i < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
+        if (tid < ppc && i < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
         spar[tid] = P;
         for (int c = 0; c < 8; ++c) {
             int C = -1, full = 0;
@@ -1031,7 +1033,10 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
                        cudaStream_t st) {
     if (parent_count <= 0 || level < 3 || F.O.l2pc_off < 0 || F.O.l2p_off[level] < 0) return;
     tc_init_attributes();
-    k_l2lp_tc<<<(parent_count + TCM - 1) / TCM, LP_T, LP_SMEM, st>>>(F, level, parent_begin, parent_count,
+    // parents per CTA: up to 128 (the MMA's M), fewer where that spreads the work evenly over
+    // two rounds of one CTA per SM
+    const int ppc = std::max(1, std::min(TCM, (parent_count + 2 * 152 - 1) / (2 * 152)));
+    k_l2lp_tc<<<(parent_count + ppc - 1) / ppc, LP_T, LP_SMEM, st>>>(F, level, parent_begin, parent_count, ppc,
                                                                      F.O.l2p_img + F.O.l2p_off[level],
                                                                      F.O.l2p_img + F.O.l2pc_off, out, err);
 }
