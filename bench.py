@@ -144,10 +144,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-# DRAM bytes (read + write) per launch of the selection kernels from one ncu capture
-# (profiles/k_select_onepass_streamer256_adaptive.md, profiles/k_grid_max_streamer256_adaptive.md);
-# valid for the 256^3 adaptive workload and the kernels as profiled there.
-NCU_TRAFFIC = {"select": (134.320640 + 104.982784 + 134.236928 + 3.904512) * 1e6}
+# DRAM bytes (read + write) per launch from one ncu capture (profiles/k_select_onepass_streamer256_adaptive.md,
+# profiles/k_grid_max_streamer256_adaptive.md, profiles/k_l2lp_tc_streamer256_adaptive.md); valid for the
+# 256^3 adaptive workload and the kernels as profiled there.
+NCU_TRAFFIC = {"select": (134.239488 + 3.42656 + 134.33984 + 103.371776) * 1e6,
+               "l2lp": (161.337088 + 39.760384) * 1e6}
 
 
 def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_headline=True):
