@@ -144,9 +144,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture (profiles/k_select_onepass_streamer256_adaptive.md,
-# profiles/k_grid_max_streamer256_adaptive.md, profiles/k_l2lp_tc_streamer256_adaptive.md); valid for the
-# 256^3 adaptive workload and the kernels as profiled there.
+# DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_grid_max + k_select_onepass, and of k_l2lp_tc);
+# valid for that workload and the kernels as profiled.
 NCU_TRAFFIC = {"select": (134.239488 + 3.42656 + 134.33984 + 103.371776) * 1e6,
                "l2lp": (161.337088 + 39.760384) * 1e6}
 

@@ -161,27 +161,49 @@ void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list
 // Compact work lists: per level the boxes with sources (stored in the level's box range),
 // and the leaves that the leaf kernel has to visit (any without a table L2P, or with a
 // U or W list).
+// Append with one atomic per (warp, counter): lanes with `pred` that share a counter get
+// consecutive slots from the group's leader.  Every lane of `act` must call it.
+__device__ __forceinline__ int warp_append(unsigned act, bool pred, int *counter) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long key = pred ? reinterpret_cast<unsigned long long>(counter) : 0ull;
+    const unsigned grp = __match_any_sync(act, key);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (pred && lane == leader) base = atomicAdd(counter, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
                              int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
                              int *__restrict__ p2p_cnt) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
+    const unsigned act = __activemask();
     const TreeDev &T = F.T;
-    int l = T.b_level[b];
-    if (l >= 2 && T.b_se[b] > T.b_sb[b]) {
-        int i = atomicAdd(src_cnt + l, 1);
-        src_list[T.lvl_base[l] + i] = b;
-    }
-    if (T.b_leaf[b] && T.b_te[b] > T.b_tb[b]) {
+    const int l = T.b_level[b];
+    const bool has_src = l >= 2 && T.b_se[b] > T.b_sb[b];
+    const bool leaf_t = T.b_leaf[b] && T.b_te[b] > T.b_tb[b];
+    bool need = false, p2p = false;
+    if (leaf_t) {
         bool l2p_done = F.leaf_l2p_done && F.O.method == FAR_CHEB && l >= 2 && (F.O.e_off[l] >= 0 || F.l2p_sep);
         bool has_u = F.L.u_off[b] != F.L.u_off[b + 1];
         bool has_w = F.L.w_off[b] != F.L.w_off[b + 1];
         // the separate near-field kernel takes U and (Chebyshev far field) W lists
         bool w_sep = F.p2p_separate && F.O.method == FAR_CHEB;
-        bool need = !l2p_done || ((has_u || has_w) && !F.p2p_separate) || (has_w && !w_sep);
-        if (need) leaf_list[atomicAdd(leaf_cnt, 1)] = b;
-        if (F.p2p_separate && (has_u || (has_w && w_sep))) p2p_list[atomicAdd(p2p_cnt, 1)] = b;
+        need = !l2p_done || ((has_u || has_w) && !F.p2p_separate) || (has_w && !w_sep);
+        p2p = F.p2p_separate && (has_u || (has_w && w_sep));
     }
+    int i = warp_append(act, has_src, src_cnt + l);
+    if (has_src) src_list[T.lvl_base[l] + i] = b;
+    // per level, the leaves with targets (the separable L2P walks these only)
+    const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr;
+    i = warp_append(act, l2p, F.l2p_cnt + l);
+    if (l2p) F.l2p_list[T.lvl_base[l] + i] = b;
+    i = warp_append(act, need, leaf_cnt);
+    if (need) leaf_list[i] = b;
+    i = warp_append(act, p2p, p2p_cnt);
+    if (p2p) p2p_list[i] = b;
 }
 
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
@@ -524,8 +546,9 @@ size_t sep_smem_bytes(int p, int np, int e) {
     return sizeof(float) * ((size_t)np + (size_t)p * e + (size_t)p * p * e + (size_t)p * sep_band_rows(p, e) * e);
 }
 
-__global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, int box_begin, int box_count, int band,
-                                                 float *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, const int *__restrict__ list,
+                                                 const int *__restrict__ count, int band, float *__restrict__ out) {
+    const int box_count = *count;
     extern __shared__ float sm[];
     const int p = F.O.order, n = F.O.n, np = F.O.npad;
     const int e = 1 << (F.D - level);
@@ -538,7 +561,7 @@ __global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, int box_be
     const int z0 = blockIdx.y * SEP_SLAB, z1 = min(e, z0 + SEP_SLAB);
     if (tid < p) tch[tid] = F.O.cheb_t[tid];
     for (int i = blockIdx.x; i < box_count; i += gridDim.x) {
-        const int b = box_begin + i;
+        const int b = list[i];
         const TreeDev &T = F.T;
         if (!T.b_leaf[b] || T.b_te[b] <= T.b_tb[b] || z0 >= e) continue;   // uniform over the CTA
         const bool full = T.b_te[b] - T.b_tb[b] == e * e * e;
@@ -596,8 +619,10 @@ constexpr int SEPW_MAXE = 8;
 constexpr int SEPW_MAXP = 6;           // orders up to 6 (n <= 216, npad <= 224)
 constexpr int SEPW_NP = 224;
 
-__global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int level, int box_begin,
-                                                                   int box_count, float *__restrict__ out) {
+__global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int level, const int *__restrict__ list,
+                                                                   const int *__restrict__ count,
+                                                                   float *__restrict__ out) {
+    const int box_count = *count;
     __shared__ float Sb[SEPW_MAXP * SEPW_MAXE];                                  // [p][e]
     __shared__ __align__(16) float sd[SEPW_WARPS][SEPW_NP];
     __shared__ float T1[SEPW_WARPS][SEPW_MAXP * SEPW_MAXP * SEPW_MAXE];          // [p*p][e]
@@ -629,7 +654,7 @@ __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int
     float4 nd[2];
     auto fetch = [&](int ii, float4 *r) {
         if (ii < box_count) {
-            const float *src = F.dchk + (size_t)(box_begin + ii) * np;
+            const float *src = F.dchk + (size_t)list[ii] * np;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int j = 4 * lane + 128 * k;
@@ -639,7 +664,7 @@ __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int
     };
     fetch(i, nd);
     for (; i < box_count; i += stride) {
-        const int b = box_begin + i;
+        const int b = list[i];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int j = 4 * lane + 128 * k;
@@ -701,13 +726,14 @@ __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int
     (void)n;
 }
 
-void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st) {
+void fmm_l2p_sep_level(const FmmDev &F, int level, const int *list, const int *count, int box_count, float *out,
+                       cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
     if ((1 << (F.D - level)) <= SEPW_MAXE && F.O.order <= SEPW_MAXP && F.O.npad <= SEPW_NP) {
         const int per = SEPW_WARPS;
         int grid = (box_count + per - 1) / per;
         if (grid > 152 * 8) grid = 152 * 8;
-        k_l2p_sep_small<<<grid, SEPW_WARPS * 32, 0, st>>>(F, level, box_begin, box_count, out);
+        k_l2p_sep_small<<<grid, SEPW_WARPS * 32, 0, st>>>(F, level, list, count, out);
         return;
     }
     const int e = 1 << (F.D - level), p = F.O.order;
@@ -715,7 +741,7 @@ void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count,
     const size_t smem = sep_smem_bytes(p, F.O.npad, e);
     const int zs = (e + SEP_SLAB - 1) / SEP_SLAB;
     int gx = box_count < 152 * 4 ? box_count : 152 * 4;
-    k_l2p_sep<<<dim3(gx, zs), 256, smem, st>>>(F, level, box_begin, box_count, band, out);
+    k_l2p_sep<<<dim3(gx, zs), 256, smem, st>>>(F, level, list, count, band, out);
 }
 
 // Shared-memory opt-in of the FMM kernels that may need more than 48 KiB (host, once, before

@@ -552,7 +552,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_work, (3 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    ENS(c->b_work, (4 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
     F.T = tree_dev(c);
@@ -583,6 +583,8 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.w_leaf = S.w_src + std::max(nb, 1);
     S.w_p2p = S.w_leaf + std::max(nb, 1);
     S.w_cnt = S.w_p2p + std::max(nb, 1);
+    F.l2p_list = S.w_cnt + 64;                  // [nb], per level at lvl_base[l]
+    F.l2p_cnt = S.w_cnt + 40;                   // [16]
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
@@ -675,14 +677,14 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             }
             const bool tc_here = l2p_tc && (c->l2p_tc_tables || (1 << (c->D - l)) == 4);
             if (c->lvl_count[l] > 0 && sep_all && !tc_here) {
-                fmm_l2p_sep_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_count[l], out, c->stream);
                 ++c->launches;
             } else if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
                 if (tc_here) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
                 else fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
                 ++c->launches;
             } else if (c->lvl_count[l] > 0 && F.l2p_sep) {
-                fmm_l2p_sep_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
+                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_count[l], out, c->stream);
                 ++c->launches;
             }
         }

@@ -187,6 +187,7 @@ struct FmmDev {
     const float *gtab;      // optional near-field table: g(d2) for integer squared offsets d2 < GTAB_N
     float r_s;              // strategy 3 (skip W boxes whose bounded share is below r_s S_est); 0 = off
     unsigned long long *skip_count;   // (target, W box) pairs skipped by strategy 3
+    int *l2p_list = nullptr, *l2p_cnt = nullptr;   // per level (at lvl_base[l]): leaves with targets, [16] counts
     float wscale;
     KParams kp;
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
@@ -211,7 +212,10 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
 void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, int *err,
                       cudaStream_t st);
 __host__ __device__ int l2p_tile_n(int edge);
-void fmm_l2p_sep_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, cudaStream_t st);
+// separable L2P of the leaves with targets of one level: list / *count (device) from the work
+// lists; box_count (host) bounds the count and sizes the launch
+void fmm_l2p_sep_level(const FmmDev &F, int level, const int *list, const int *count, int box_count, float *out,
+                       cudaStream_t st);
 void fmm_init_attributes();
 constexpr int GTAB_N = 4096;           // table of the scaled kernel for squared cell offsets 0 .. 4095
 void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st);
