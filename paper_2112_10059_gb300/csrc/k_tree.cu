@@ -396,9 +396,11 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
     cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
     constexpr int RB = RANGE_T * RANGE_PER;
-    // enough blocks for every possible point (blocks past the actual count exit at once)
+    // targets: enough blocks for every possible point (blocks past the actual count exit at
+    // once); sources, usually far fewer: a grid-stride loop over 8 blocks per SM
     const int rg = (int)std::min<int64_t>(((int64_t)A.ncap + RB - 1) / RB, 1 << 20);
-    k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.ns_dev, A.skey, A.D, A.Lmax, A.rsb, A.rse);
+    k_tree_ranges<<<std::max(std::min(rg, 152 * 8), 1), RANGE_T, 0, st>>>(A.ns_dev, A.skey, A.D, A.Lmax, A.rsb,
+                                                                           A.rse);
     k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
     k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
