@@ -142,20 +142,24 @@ __device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
 }
 
 // CTAs walk the compact list of this level's boxes that hold sources.
+// leaves_only: the split boxes' M2M runs on the tensor cores (k_m2m_tc)
 __global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, const int *__restrict__ list,
-                                                       const int *__restrict__ count) {
+                                                       const int *__restrict__ count, int leaves_only) {
     const int cnt = *count;
     for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-        upward_box(F, level, list[i]);
+        const int b = list[i];
+        if (leaves_only && !F.T.b_leaf[b]) continue;   // uniform across the CTA
+        upward_box(F, level, b);
         __syncthreads();
     }
 }
 
-void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
-                      cudaStream_t st) {
-    if (box_count <= 0 || level < 2) return;
+int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count, bool leaves_only,
+                     cudaStream_t st) {
+    if (box_count <= 0 || level < 2) return 0;
     int grid = box_count < 152 * 8 ? box_count : 152 * 8;
-    k_upward<<<grid, 2 * F.O.npad, 0, st>>>(F, level, list, count);
+    k_upward<<<grid, 2 * F.O.npad, 0, st>>>(F, level, list, count, leaves_only ? 1 : 0);
+    return 1;
 }
 
 // Compact work lists: per level the boxes with sources (stored in the level's box range),
@@ -196,6 +200,11 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
     }
     int i = warp_append(act, has_src, src_cnt + l);
     if (has_src) src_list[T.lvl_base[l] + i] = b;
+    // split boxes with sources: the tensor-core M2M adds its children's terms into a zeroed row
+    if (has_src && !T.b_leaf[b] && F.O.m2m_img != nullptr) {
+        float4 *u = reinterpret_cast<float4 *>(F.ueq + (size_t)b * F.O.npad);
+        for (int j = 0; j < F.O.npad / 4; ++j) u[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     // per level, the leaves with targets (the separable L2P walks these only)
     const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr;
     i = warp_append(act, l2p, F.l2p_cnt + l);

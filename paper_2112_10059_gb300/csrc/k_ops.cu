@@ -591,6 +591,7 @@ int ops_build(const OpsBuildArgs &A, cudaStream_t st) {
         if (O.m2l_img && tc_supported(O)) {
             make_images(O.m2l_t, O.npad, (A.Lmax + 1) * NSLOT, O.m2l_img, st);
             make_images(O.l2l_t, O.npad, (A.Lmax + 1) * 8, O.l2l_img, st);
+            if (O.m2m_img) make_images(O.m2m_t, O.npad, (A.Lmax + 1) * 8, O.m2m_img, st);
         }
         if (O.l2p_img && O.method == FAR_CHEB && tc_supported(O)) {
             for (int l = 2; l <= A.Lmax && l < 16; ++l)

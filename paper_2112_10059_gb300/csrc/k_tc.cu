@@ -490,6 +490,50 @@ __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_
     tile_teardown(s);
 }
 
+// ---------------------------------------------------------------- M2M, one child slot per CTA
+// Tiles of 64 split boxes with sources of one level (from the level's compact source list)
+// x child slot c = blockIdx.y:  u_P += M2M_c u_{child c of P}, BF16 hi / lo x3, added with
+// reductions into rows that the work-list kernel zeroed.
+__global__ void __launch_bounds__(256) k_m2m_tc(FmmDev F, int level, const int *__restrict__ list,
+                                                const int *__restrict__ count, const uint16_t *__restrict__ images,
+                                                int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem s = carve(smem_raw);
+    const int t0 = blockIdx.x * TCN;
+    const int c = blockIdx.y;
+    const int cnt = *count;
+    if (t0 >= cnt) return;
+    const TreeDev &T = F.T;
+    int any = 0;
+    if (threadIdx.x < TCN) {
+        const int j = t0 + threadIdx.x;
+        int P = -1, C = -1;
+        if (j < cnt) {
+            const int p = list[j];
+            if (!T.b_leaf[p]) {
+                const int ch = T.box_at[dense_off(level + 1) + ((T.b_key[p] << 3) | (uint32_t)c)];
+                if (ch >= 0 && T.b_se[ch] > T.b_sb[ch]) { P = p; C = ch; }
+            }
+        }
+        any = C >= 0;
+        s.col_src[threadIdx.x] = C;
+        s.col_dst[threadIdx.x] = P;
+    }
+    if (!__syncthreads_or(any)) return;
+    tile_setup(s);
+    const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
+    tile_body(s, img, F.ueq, F.ueq, F.O.npad, F.O.n, true, err);
+    tile_teardown(s);
+}
+
+void fmm_m2m_tc_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
+                      const uint16_t *images, int *err, cudaStream_t st) {
+    if (box_count <= 0 || level < 2) return;
+    tc_init_attributes();
+    dim3 grid((box_count + TCN - 1) / TCN, 8);
+    k_m2m_tc<<<grid, 256, TC_SMEM, st>>>(F, level, list, count, images, err);
+}
+
 // ---------------------------------------------------------------- L2L, all 8 children per CTA
 // 64 parents per CTA; their downward states are gathered once (B tile), and the 8 child
 // operators stream through two 64 KiB image buffers: image c + 2 is loaded into the
@@ -1050,6 +1094,7 @@ void tc_init_attributes() {
     if (done) return;
     cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaFuncSetAttribute(k_m2m_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
     cudaFuncSetAttribute(k_l2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2P_SMEM);
     cudaFuncSetAttribute(k_l2lp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);

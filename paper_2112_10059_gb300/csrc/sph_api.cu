@@ -100,7 +100,7 @@ struct sph_ctx {
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
     DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pkeys, b_ppairs, b_heavy;
     DevBuf b_ueq, b_dchk;
-    DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_slot, o_surf, o_cheb, o_self;
+    DevBuf o_work, o_etab, o_m2m, o_l2l, o_m2l, o_m2lbf, o_l2lbf, o_m2mbf, o_slot, o_surf, o_cheb, o_self;
     DevBuf b_err;                // device error flags of the tensor-core tiles
     DevBuf b_work;               // compact work lists: sources per level, leaves for the leaf and P2P kernels
     DevBuf b_tmask;              // [ncell] 1 at targets (written by the selection)
@@ -438,6 +438,7 @@ void fill_ops(sph_ctx *c, OpsDev &O, int D, int L, bool bf) {
     const bool img = bf && O.npad == 128;
     O.m2l_img = img ? P<uint16_t>(c->o_m2lbf) : nullptr;
     O.l2l_img = img ? P<uint16_t>(c->o_l2lbf) : nullptr;
+    O.m2m_img = (img && c->far_method == FAR_CHEB) ? P<uint16_t>(c->o_m2mbf) : nullptr;
     O.l2p_img = (img && c->far_method == FAR_CHEB) ? P<uint16_t>(c->o_l2pimg) : nullptr;
     O.slot_of_code = P<short>(c->o_slot);
     O.nodes = P<float>(c->o_surf);
@@ -465,6 +466,7 @@ int run_ops(sph_ctx *c) {
     if (want_bf && np == 128) {
         ENS(c->o_m2lbf, tc_image_elems((L + 1) * 316) * sizeof(uint16_t));
         ENS(c->o_l2lbf, tc_image_elems((L + 1) * 8) * sizeof(uint16_t));
+        if (c->far_method == FAR_CHEB) ENS(c->o_m2mbf, tc_image_elems((L + 1) * 8) * sizeof(uint16_t));
         if (c->far_method == FAR_CHEB) ENS(c->o_l2pimg, (ops_l2p_img_elems(c->D, L) + 64) * sizeof(uint16_t));
     }
     ENS(c->o_slot, 343 * sizeof(short));
@@ -600,12 +602,21 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
     CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
+    if (S.tc) CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));   // M2M, M2L and L2L tiles' flags
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 33, c->stream);
     c->launches += nb > 0;
     if (tm) tm->mark_at(3, c->stream);
+    // P2M of the leaves (and, without the tensor-core images, M2M) box by box; with them the
+    // split boxes' M2M in tiles on the tensor cores (their rows zeroed by the work lists)
+    const bool m2m_tc = S.tc && F.O.m2m_img != nullptr;
     for (int l = c->Lmax; l >= 2; --l) {
-        fmm_upward_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, c->stream);
-        c->launches += c->lvl_count[l] > 0;
+        c->launches += fmm_upward_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, m2m_tc,
+                                        c->stream);
+        if (m2m_tc && l < c->Lmax && c->lvl_count[l] > 0) {
+            fmm_m2m_tc_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, F.O.m2m_img, S.err,
+                             c->stream);
+            ++c->launches;
+        }
     }
     if (tm) tm->mark_at(4, c->stream);
     // the last L2L and the L2P of the deepest level fused (every box there a leaf of edge 4)
@@ -631,7 +642,6 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         // (the V pairs were grouped by key with the lists)
         if (tm) tm->mark_at(5, c->stream);
         if (S.tc) {
-            CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));
             fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream, c->m2l_pipe);
         } else {
             fmm_m2l_pairs(F, S.Pd, nV, c->m2l_prec, c->stream);
@@ -1455,7 +1465,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pkeys, &c->b_ppairs, &c->b_heavy,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->o_m2mbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)

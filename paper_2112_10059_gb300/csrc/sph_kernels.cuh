@@ -143,6 +143,7 @@ struct OpsDev {
     float *m2l_t;     // [L][316][npad][npad] u_A -> d_B (A at offset o from B)
     uint16_t *m2l_img;    // [L][316] BF16 hi / lo images of M2L for the tensor cores (npad == 128)
     uint16_t *l2l_img;    // [L][8]   BF16 hi / lo images of L2L
+    uint16_t *m2m_img;    // [L][8]   BF16 hi / lo images of M2M
     float *e_tab;     // L2P tables per level: FAR_SURFACE [edge^3][npad] row-major (cells in linear order);
                       // FAR_CHEB [npad][edge^3] (cells in local Morton order)
     long long e_off[16];          // float offset of level l's table in e_tab, -1 if none
@@ -194,8 +195,9 @@ struct FmmDev {
     int D, nx, ny, nz, self_mode;
     float *ueq, *dchk;   // [nboxes][PP]: upward / downward check potentials u_B, d_B
 };
-void fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
-                      cudaStream_t st);
+// returns the number of kernels launched
+int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count, bool leaves_only,
+                     cudaStream_t st);
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
                     int *p2p_list, int *p2p_cnt, cudaStream_t st);
 // near field over the U lists of the leaves in p2p_list (adds into out)
@@ -209,6 +211,10 @@ void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, fl
 // `level` must be a leaf (level == Lmax).  Replaces fmm_l2l_*_level(level) and the L2P of `level`.
 void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, float *out, int *err,
                        cudaStream_t st);
+// M2M of the split boxes with sources of `level` on the tensor cores: tiles of 64 boxes from
+// the level's source list x one child slot per CTA, added into rows zeroed by the work lists
+void fmm_m2m_tc_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
+                      const uint16_t *images, int *err, cudaStream_t st);
 void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, float *out, int *err,
                       cudaStream_t st);
 __host__ __device__ int l2p_tile_n(int edge);
