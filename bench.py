@@ -557,10 +557,10 @@ def main():
         ms = float(t.item())
     value = nt * world / (ms * 1e-3)
 
-    # e2e through the host-buffer entry point
-    qh = p.q
-    eh = p.emag
-    sh = np.empty(p.ncell, np.float32)
+    # e2e through the host-buffer entry point, inputs and output in pinned host memory
+    qh = torch.from_numpy(p.q).pin_memory().numpy()
+    eh = torch.from_numpy(p.emag).pin_memory().numpy()
+    sh = torch.empty(p.ncell, dtype=torch.float32).pin_memory().numpy()
     sph.eval_sph_host(ctx, qh, eh, out=sh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
