@@ -439,11 +439,6 @@ __device__ __forceinline__ bool adjacent(const BoxGeom &a, const BoxGeom &b, int
     return ax <= bx + sb && bx <= ax + sa && ay <= by + sb && by <= ay + sa && az <= bz + sb && bz <= az + sa;
 }
 
-__device__ __forceinline__ int lookup(const TreeDev &T, int level, int x, int y, int z) {
-    int n = 1 << level;
-    if (x < 0 || y < 0 || z < 0 || x >= n || y >= n || z >= n) return -1;
-    return T.box_at[dense_off(level) + morton3(x, y, z)];
-}
 
 // Lists in two steps.  k_lists_classify (thread per box) finds the boxes that can have an
 // entry -- targets, and sources somewhere around the parent -- and queues them (any order:
