@@ -344,6 +344,7 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
     T.b_parent[idx] = l > 0 ? pos[dense_off(l - 1) + (m >> 3)] : -1;
     T.b_leaf[idx] = !(l < D && (se - sb > S || te - tb > S));
     vsrc[s] = se > sb;
+    if (se > sb) atomicAdd(T.lvl_src + l, 1);
 }
 
 // occ[s] = 1 if the slot's region holds a source point, or lies inside a leaf that holds
@@ -403,6 +404,7 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
                                                                            A.rse);
     k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
+    cudaMemsetAsync(A.T.lvl_src, 0, 16 * sizeof(int), st);
     k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);

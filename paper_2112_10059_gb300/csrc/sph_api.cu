@@ -74,7 +74,7 @@ struct sph_ctx {
     // results of the last eval
     int64_t ns = 0, nt = 0;
     int nboxes = 0, Lmax = 0;
-    std::vector<int> lvl_count, lvl_base;
+    std::vector<int> lvl_count, lvl_base, lvl_src;   // boxes, first box, boxes with sources per level
     int list_tot[4] = {0, 0, 0, 0};
     bool have_tree = false;
     int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
@@ -265,6 +265,7 @@ TreeDev tree_dev(sph_ctx *c) {
     T.box_at = P<int>(c->b_boxat);
     T.lvl_base = P<int>(c->b_lvl);
     T.lvl_count = T.lvl_base + 16;
+    T.lvl_src = T.lvl_base + 32;
     T.b_level = P<int>(c->b_level);
     T.b_key = P<uint32_t>(c->b_key);
     T.b_sb = P<int>(c->b_sb); T.b_se = P<int>(c->b_se);
@@ -312,7 +313,8 @@ PairsDev pairs_dev(sph_ctx *c) {
 
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
-// [43] scan give-up flag, [44..48) list totals, [48] tensor-core error flags.
+// [43] scan give-up flag, [44..48) list totals, [48] and [49] tensor-core error flags,
+// [50..50+Lmax] boxes with sources per level.
 // The tree and the list counts read the selection's point counts and the tree's box count
 // from device memory, so selection, tree and list counting need one host sync in all.
 int tree_queue(sph_ctx *c) {
@@ -329,7 +331,7 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_rng, 4 * dense_total * sizeof(int));
     ENS(c->b_near, 3 * dense_total + 16);
     ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
-    ENS(c->b_lvl, 32 * sizeof(int));
+    ENS(c->b_lvl, 48 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
     ENS(c->b_level, cap * sizeof(int));
     ENS(c->b_key, cap * sizeof(uint32_t));
@@ -355,6 +357,7 @@ int tree_queue(sph_ctx *c) {
     c->launches += 2 + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 50, A.T.lvl_src, (Lmax + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
@@ -387,9 +390,13 @@ int tree_levels_read(sph_ctx *c) {
     if (c->pinned[43] != 0) return fail(c, SPH_ETIMEOUT, "a tree or list scan gave up waiting for a preceding tile");
     c->lvl_count.assign(Lmax + 1, 0);
     c->lvl_base.assign(Lmax + 1, 0);
+    c->lvl_src.assign(Lmax + 1, 0);
     int64_t tot = 0;
     for (int l = 0; l <= Lmax; ++l) {
+        c->lvl_src[l] = c->pinned[50 + l];
         c->lvl_count[l] = c->pinned[8 + 16 + l];
+        if (c->lvl_src[l] < 0 || c->lvl_src[l] > c->pinned[8 + 16 + l])
+            return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         if (c->lvl_count[l] < 0) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         c->lvl_base[l] = (int)tot;
         tot += c->lvl_count[l];
@@ -617,10 +624,11 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     // split boxes' M2M in tiles on the tensor cores (their rows zeroed by the work lists)
     const bool m2m_tc = S.tc && F.O.m2m_img != nullptr;
     for (int l = c->Lmax; l >= 2; --l) {
-        c->launches += fmm_upward_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, m2m_tc,
+        // launch sizes from the number of boxes with sources (the kernels read the exact count)
+        c->launches += fmm_upward_level(F, l, c->lvl_src[l], S.w_src + c->lvl_base[l], S.w_cnt + l, m2m_tc,
                                         c->stream);
-        if (m2m_tc && l < c->Lmax && c->lvl_count[l] > 0) {
-            fmm_m2m_tc_level(F, l, c->lvl_count[l], S.w_src + c->lvl_base[l], S.w_cnt + l, F.O.m2m_img, S.err,
+        if (m2m_tc && l < c->Lmax && c->lvl_src[l] > 0) {
+            fmm_m2m_tc_level(F, l, c->lvl_src[l], S.w_src + c->lvl_base[l], S.w_cnt + l, F.O.m2m_img, S.err,
                              c->stream);
             ++c->launches;
         }
@@ -786,6 +794,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(&S, sizeof S);
     put(c->lvl_count.data(), c->lvl_count.size() * sizeof(int));
     put(c->lvl_base.data(), c->lvl_base.size() * sizeof(int));
+    put(c->lvl_src.data(), c->lvl_src.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
                           c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, (int64_t)reinterpret_cast<uintptr_t>(out)};

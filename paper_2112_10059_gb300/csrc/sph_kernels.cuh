@@ -48,6 +48,7 @@ int direct_launch(const DirectArgs &A, cudaStream_t st);
 struct TreeDev {
     int *box_at;         // concatenated dense levels
     int *lvl_base, *lvl_count;   // [Lmax+1]
+    int *lvl_src;                // [Lmax+1] boxes holding sources per level (zeroed before the emit)
     int *b_level;
     uint32_t *b_key;
     int *b_sb, *b_se, *b_tb, *b_te, *b_parent;
