@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __shared__ int ws[16], wt[16];
     __shared__ unsigned rs[16], rt[16];
     __shared__ int s_stop;
-    __shared__ uint32_t st_key[4096], st_pc[4096];
+    // targets staged at brick-local rank j, slot j + j / 32: a thread's consecutive ranks (8 apart
+    // from its neighbours') then fall in distinct banks
+    __shared__ uint32_t st_key[4096 + 128], st_pc[4096 + 128];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_brick = (int)atomicAdd(ticket, 1u);
@@ -484,15 +486,15 @@ __global__ void __launch_bounds__(512) k_select_onepass(
             ++ps;
         }
         if (my_bits[u] & 2) {
-            st_key[lt] = key;
-            st_pc[lt] = pc;
+            st_key[lt + (lt >> 5)] = key;
+            st_pc[lt + (lt >> 5)] = pc;
             ++lt;
         }
     }
     __syncthreads();
     for (int i = tid; i < (int)agg_t; i += blockDim.x) {
-        trg_key[pre_t + i] = st_key[i];
-        trg_pc[pre_t + i] = st_pc[i];
+        trg_key[pre_t + i] = st_key[i + (i >> 5)];
+        trg_pc[pre_t + i] = st_pc[i + (i >> 5)];
     }
 }
 
