@@ -212,11 +212,11 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
 // Point ranges of every dense slot of every level in one pass over the Morton-sorted keys:
 // point i opens the range of its slot at level l when point i-1 lies in another slot of
 // that level, and closes it when point i+1 does.  Untouched slots keep [0, 0).
-// Four keys per thread (one 16-byte load), neighbours through warp shuffles.  A key whose
+// Eight keys per thread (two 16-byte loads), neighbours through warp shuffles.  A key whose
 // finest slot (level Lmax) matches both neighbours' -- all but about one in 8^(D-Lmax) --
 // costs a few integer operations; the boundary writes are queued in shared memory and
 // carried out by the whole block, so that no warp runs them one lane at a time.
-constexpr int RANGE_PER = 4, RANGE_T = 256;
+constexpr int RANGE_PER = 8, RANGE_T = 256;
 
 __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ n_dev, const uint32_t *__restrict__ key,
                                                          int D, int Lmax, int *__restrict__ beg, int *__restrict__ end) {
@@ -226,58 +226,60 @@ __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__
     __shared__ int ntask;
     const int n = *n_dev;                 // a negative count (failed selection) reads as none
     const int lane = threadIdx.x & 31;
-    // grid-stride over chunks of RANGE_T * RANGE_PER keys (uniform across the block)
-    for (long long base = (long long)blockIdx.x * RANGE_T * RANGE_PER; base < n;
-         base += (long long)gridDim.x * RANGE_T * RANGE_PER) {
-    const long long i0 = base + (long long)threadIdx.x * RANGE_PER;
-    if (threadIdx.x == 0) ntask = 0;
-    uint32_t k[RANGE_PER];
-    if (i0 + RANGE_PER <= n) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(key + i0);
-        k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-    } else {
-#pragma unroll
-        for (int u = 0; u < RANGE_PER; ++u) k[u] = i0 + u < n ? key[i0 + u] : 0u;
-    }
-    // every lane takes part in the shuffles; lanes past the end only supply values nobody uses
-    uint32_t prev = __shfl_up_sync(0xffffffffu, k[RANGE_PER - 1], 1);
-    uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
-    if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? key[i0 - 1] : 0u;
-    if (lane == 31) next = (i0 + RANGE_PER < n) ? key[i0 + RANGE_PER] : 0u;
-    __syncthreads();
     const int fine = 3 * (D - Lmax);
     // two keys fall in different slots of level l iff their highest differing bit b (0-based)
     // satisfies b >= 3 (D - l), i.e. for every l >= D - b / 3
     auto first_level = [&](uint32_t x, uint32_t o) { return max(0, D - (31 - __clz(x ^ o)) / 3); };
+    // grid-stride over chunks of RANGE_T * RANGE_PER keys (uniform across the block); point
+    // counts stay below 2^30 (grids of at most 1024^3 cells), so int indices do not overflow
+    for (int base = blockIdx.x * RANGE_T * RANGE_PER; base < n; base += gridDim.x * RANGE_T * RANGE_PER) {
+        const int i0 = base + threadIdx.x * RANGE_PER;
+        if (threadIdx.x == 0) ntask = 0;
+        uint32_t k[RANGE_PER];
+        if (i0 + RANGE_PER <= n) {
+            const uint4 v0 = *reinterpret_cast<const uint4 *>(key + i0);
+            const uint4 v1 = *reinterpret_cast<const uint4 *>(key + i0 + 4);
+            k[0] = v0.x; k[1] = v0.y; k[2] = v0.z; k[3] = v0.w;
+            k[4] = v1.x; k[5] = v1.y; k[6] = v1.z; k[7] = v1.w;
+        } else {
 #pragma unroll
-    for (int u = 0; u < RANGE_PER; ++u) {
-        const long long i = i0 + u;
-        if (i >= n) break;
-        const uint32_t p = u == 0 ? prev : k[u - 1];
-        const uint32_t q = u == RANGE_PER - 1 ? next : k[u + 1];
-        if (i == 0 || ((k[u] ^ p) >> fine) != 0) {
-            const int s = atomicAdd(&ntask, 1);
-            task_key[s] = k[u];
-            task_val[s] = (int)i;
-            task_lvl[s] = (uint8_t)(i == 0 ? 0 : first_level(k[u], p));
+            for (int u = 0; u < RANGE_PER; ++u) k[u] = i0 + u < n ? key[i0 + u] : 0u;
         }
-        if (i + 1 == n || ((k[u] ^ q) >> fine) != 0) {
-            const int s = atomicAdd(&ntask, 1);
-            task_key[s] = k[u];
-            task_val[s] = (int)i + 1;
-            task_lvl[s] = (uint8_t)(0x80 | (i + 1 == n ? 0 : first_level(k[u], q)));
+        // every lane takes part in the shuffles; lanes past the end only supply values nobody uses
+        uint32_t prev = __shfl_up_sync(0xffffffffu, k[RANGE_PER - 1], 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? key[i0 - 1] : 0u;
+        if (lane == 31) next = (i0 + RANGE_PER < n) ? key[i0 + RANGE_PER] : 0u;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RANGE_PER; ++u) {
+            const int i = i0 + u;
+            if (i >= n) break;
+            const uint32_t p = u == 0 ? prev : k[u - 1];
+            const uint32_t q = u == RANGE_PER - 1 ? next : k[u + 1];
+            if (i == 0 || ((k[u] ^ p) >> fine) != 0) {
+                const int s = atomicAdd(&ntask, 1);
+                task_key[s] = k[u];
+                task_val[s] = i;
+                task_lvl[s] = (uint8_t)(i == 0 ? 0 : first_level(k[u], p));
+            }
+            if (i + 1 == n || ((k[u] ^ q) >> fine) != 0) {
+                const int s = atomicAdd(&ntask, 1);
+                task_key[s] = k[u];
+                task_val[s] = i + 1;
+                task_lvl[s] = (uint8_t)(0x80 | (i + 1 == n ? 0 : first_level(k[u], q)));
+            }
         }
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < ntask; s += RANGE_T) {
-        const uint32_t kk = task_key[s];
-        const int val = task_val[s];
-        const int l0 = task_lvl[s] & 0x7f;
-        int *out = (task_lvl[s] & 0x80) ? end : beg;
-        int64_t off = dense_off(l0);
-        for (int l = l0; l <= Lmax; ++l, off = 8 * off + 1) out[off + (kk >> (3 * (D - l)))] = val;
-    }
-    __syncthreads();                      // the task queue is reused by the next chunk
+        __syncthreads();
+        for (int s = threadIdx.x; s < ntask; s += RANGE_T) {
+            const uint32_t kk = task_key[s];
+            const int val = task_val[s];
+            const int l0 = task_lvl[s] & 0x7f;
+            int *out = (task_lvl[s] & 0x80) ? end : beg;
+            int64_t off = dense_off(l0);
+            for (int l = l0; l <= Lmax; ++l, off = 8 * off + 1) out[off + (kk >> (3 * (D - l)))] = val;
+        }
+        __syncthreads();                      // the task queue is reused by the next chunk
     }
 }
 
