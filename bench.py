@@ -147,7 +147,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of k_grid_max + k_select_onepass, and of k_l2lp_tc);
 # valid for that workload and the kernels as profiled.
-NCU_TRAFFIC = {"select": (134.239488 + 3.42656 + 134.33984 + 103.371776) * 1e6,
+NCU_TRAFFIC = {"select": (134.252288 + 3.670272 + 134.298112 + 103.954944) * 1e6,
                "l2lp": (161.337088 + 39.760384) * 1e6}
 
 
