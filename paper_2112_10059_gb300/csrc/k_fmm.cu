@@ -782,21 +782,26 @@ struct P2PConst {
     float k1, k2;        // alpha h log2(e), (beta - alpha) h log2(e)
     float bma_h;         // (beta - alpha) h
     float wself;         // G_self h^3 / C  (self term, in the scaled weight units)
+    float k12;           // k1 + k2 = beta h log2(e)
 };
 
-// the scaled kernel g(s^2) of the near-field sum (see above); d2 > 0
+// the scaled kernel g(s^2) of the near-field sum (see above); d2 >= 1 (distinct cells, or a
+// node of a non-adjacent box).  Where (beta - alpha) h >= 1/2 the factor 1 - e^{-(beta-alpha) s}
+// is at least 0.29, and e^{-alpha s} - e^{-beta s} is formed directly (no cancellation to fear).
 template <bool TAYLOR>
 __device__ __forceinline__ float p2p_g(float d2, const P2PConst &K) {
-    const float rs = rsqrt_approx(fmaxf(d2, 1e-12f));
+    const float rs = rsqrt_approx(d2);
     const float sdist = d2 * rs;
-    const float e1 = ex2_approx(-K.k1 * sdist);
-    const float em = TAYLOR ? one_minus_exp_neg(K.bma_h * sdist, K.k2 * sdist) : 1.f - ex2_approx(-K.k2 * sdist);
-    return e1 * em * (rs * rs * rs);
+    const float diff = TAYLOR ? ex2_approx(-K.k1 * sdist) * one_minus_exp_neg(K.bma_h * sdist, K.k2 * sdist)
+                              : ex2_approx(-K.k1 * sdist) - ex2_approx(-K.k12 * sdist);
+    return diff * (rs * rs * rs);
 }
 
 // TABLE: the offsets of point sources are integers; g is read from the shared-memory table
 // for d2 < GTAB_N (values computed by p2p_g itself, so the sums are the same).
-template <bool TAYLOR, bool TABLE>
+// SELF: the range may hold the target's own cell (d2 = 0: the self term); otherwise every
+// source lies in another cell.
+template <bool TAYLOR, bool TABLE, bool SELF = false>
 __device__ __forceinline__ float p2p_sum(const float4 *__restrict__ pts, int lo, int hi, float tx, float ty,
                                          float tz, const P2PConst &K, const float *__restrict__ tab) {
     float a = 0.f;
@@ -809,9 +814,11 @@ __device__ __forceinline__ float p2p_sum(const float4 *__restrict__ pts, int lo,
         if (TABLE) {
             const int di = (int)d2;
             g = di < GTAB_N ? tab[di] : p2p_g<TAYLOR>(d2, K);
-        } else {
-            const float gv = p2p_g<TAYLOR>(d2, K);      // computed for every pair, then selected
+        } else if (SELF) {
+            const float gv = p2p_g<TAYLOR>(fmaxf(d2, 1.f), K);   // computed for every pair, then selected
             g = d2 > 0.f ? gv : K.wself;
+        } else {
+            g = p2p_g<TAYLOR>(d2, K);
         }
         a = fmaf(g, sp.w, a);
     }
@@ -836,6 +843,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
     if (TABLE)
         for (int j = threadIdx.x; j < GTAB_N; j += blockDim.x) tab[j] = F.gtab[j];
     __shared__ int ub[P2P_MAXU], un[P2P_MAXU], uo[P2P_MAXU + 1];
+    __shared__ int s_own;                  // entry of the leaf itself in the staged U list, or -1
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cnt = *count;
     const TreeDev &T = F.T;
@@ -881,8 +889,11 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
             for (int ub0 = l0; ub0 < l1; ub0 += P2P_MAXU) {
                 const int nu = min(P2P_MAXU, l1 - ub0);
                 __syncthreads();
+                if (tid == 0) s_own = -1;
+                __syncthreads();
                 if (tid < nu) {
                     const int A = pass == 0 ? F.L.u_src[ub0 + tid] : F.L.w_src[ub0 + tid];
+                    if (pass == 0 && A == b) s_own = tid;
                     if (pass == 0) {
                         const int sb = T.b_sb[A];
                         ub[tid] = sb;
@@ -982,9 +993,20 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                         if (TABLE && pass == 0)
                             a = p2p_sum<TAYLOR, true>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
                                                       (float)pc_k(tp), K, tab);
-                        else
-                            a = p2p_sum<TAYLOR, false>(stage, s_lo, s_hi, (float)pc_i(tp), (float)pc_j(tp),
-                                                       (float)pc_k(tp), K, tab);
+                        else {
+                            // only the leaf's own cells can be the target's cell: the self-term
+                            // select runs there alone
+                            const float fx = (float)pc_i(tp), fy = (float)pc_j(tp), fz = (float)pc_k(tp);
+                            const int own = pass == 0 ? s_own : -1;
+                            const int olo = own >= 0 ? max(uo[own] - r0, s_lo) : s_hi;
+                            const int ohi = own >= 0 ? min(uo[own + 1] - r0, s_hi) : s_hi;
+                            if (olo < ohi)
+                                a = p2p_sum<TAYLOR, false>(stage, s_lo, olo, fx, fy, fz, K, tab) +
+                                    p2p_sum<TAYLOR, false, true>(stage, olo, ohi, fx, fy, fz, K, tab) +
+                                    p2p_sum<TAYLOR, false>(stage, ohi, s_hi, fx, fy, fz, K, tab);
+                            else
+                                a = p2p_sum<TAYLOR, false>(stage, s_lo, s_hi, fx, fy, fz, K, tab);
+                        }
                         if (slot < 2) acc[slot] += a;
                         else if (t < te)
                             atomicAdd(out + (int64_t)pc_i(tp) +
@@ -1011,6 +1033,7 @@ static P2PConst p2p_const(const FmmDev &F) {
     K.k1 = F.kp.a2 * h;                       // a2 = alpha log2(e)
     K.k2 = F.kp.b2 * h;                       // b2 = (beta - alpha) log2(e)
     K.bma_h = F.kp.bma * h;
+    K.k12 = K.k1 + K.k2;
     // the self weight multiplies the scaled weight w' = w C / h^3: g_self w = (g_self h^3 / C) w'
     K.wself = F.self_mode ? F.kp.gself * h * h * h / F.kp.C : 0.f;
     return K;
