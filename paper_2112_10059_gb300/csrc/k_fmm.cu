@@ -49,6 +49,26 @@ __device__ __forceinline__ void cheb_basis(int p, const float *t, float x, float
     }
 }
 
+// The same basis from the barycentric weights w_k = 1 / prod_{j != k} (t_k - t_j):
+// S_k(x) = w_k prod_{j < k} (x - t_j) prod_{j > k} (x - t_j), by prefix and suffix products
+// (no division per evaluation).
+__device__ __forceinline__ void cheb_basis_w(int p, const float *t, const float *w, float x, float *S) {
+    float d[8], pre[8];
+    float acc = 1.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {          // fixed trip counts: the arrays stay in registers
+        d[k] = k < p ? x - t[k] : 1.f;
+        pre[k] = acc;
+        acc *= d[k];
+    }
+    float suf = 1.f;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        if (k < p) S[k] = w[k] * pre[k] * suf;
+        suf *= d[k];
+    }
+}
+
 // ------------------------------------------------------------------ upward
 constexpr int UT = 256;   // sources per shared tile
 
@@ -62,7 +82,7 @@ __device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
     __shared__ uint32_t spc[UT];
     __shared__ float sw[UT];
     __shared__ float bas[UT][3][8];
-    __shared__ float tcheb[8];
+    __shared__ float tcheb[8], wcheb[8];
     const int tid = threadIdx.x, pt = tid % np, half = tid / np;
     const int size = 1 << (F.D - level);
     const float w = F.kp.h * size * 0.5f;
@@ -73,7 +93,14 @@ __device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
         box_coords(T, b, bx, by, bz);
         const bool cheb = F.O.method == FAR_CHEB;
         const int p = F.O.order;
-        if (cheb && tid < p) tcheb[tid] = F.O.cheb_t[tid];
+        if (cheb && tid < p) {
+            const float tk = F.O.cheb_t[tid];
+            float w = 1.f;
+            for (int j = 0; j < p; ++j)
+                if (j != tid) w *= tk - F.O.cheb_t[j];
+            tcheb[tid] = tk;
+            wcheb[tid] = 1.f / w;
+        }
         float sx = 0, sy = 0, sz = 0;
         int ia = 0, ib = 0, ic = 0;
         if (pt < n) {
@@ -97,9 +124,9 @@ __device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
                 if (cheb) {
                     float x, y, z;
                     rel_cell(pc_i(pc), pc_j(pc), pc_k(pc), bx, by, bz, size, hh, x, y, z);
-                    cheb_basis(p, tcheb, x * iw, bas[v][0]);
-                    cheb_basis(p, tcheb, y * iw, bas[v][1]);
-                    cheb_basis(p, tcheb, z * iw, bas[v][2]);
+                    cheb_basis_w(p, tcheb, wcheb, x * iw, bas[v][0]);
+                    cheb_basis_w(p, tcheb, wcheb, y * iw, bas[v][1]);
+                    cheb_basis_w(p, tcheb, wcheb, z * iw, bas[v][2]);
                 }
             }
             __syncthreads();
