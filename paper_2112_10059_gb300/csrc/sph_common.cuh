@@ -2,6 +2,7 @@
 // the FP32 evaluation of the photoionization kernel of Eq. gfun.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #ifndef SPH_NP
