@@ -171,11 +171,11 @@ typedef struct sph_problem {
     float *s_dev;                   /* output float[nx*ny*nz], device; 0 at non-targets */
 } sph_problem;
 
-/* Evaluate n independent snapshots (SURVEY's batching row; the paper evaluates S_ph twice per
- * time step of a streamer simulation, Section 5).  Method options (self term, leaf size or
- * autotune, M2L arithmetic, far field) come from the context's set_criteria /
- * sph_set_far_field; the grid, fields and thresholds from each problem.  The snapshots'
- * phases are interleaved so the whole batch needs three host synchronisations, and their
+/* Evaluate n independent snapshots in one call (the paper evaluates S_ph twice per time step
+ * of a streamer simulation, Section 5; a batch is many such evaluations).  Method options
+ * (self term, leaf size or autotune, M2L arithmetic, far field) come from the context's
+ * set_criteria / sph_set_far_field; the grid, fields and thresholds from each problem.  The
+ * snapshots' phases are interleaved so the whole batch needs two host synchronisations, and their
  * FMM passes run concurrently on per-snapshot streams, captured into one CUDA graph.
  * Inputs must be ready on the context's stream; outputs are complete on it when the
  * queued work finishes.  stats (optional) sums counts over the batch; ms_total is the
