@@ -381,6 +381,7 @@ void ops_layout(int D, int Lmax, double *work, OpsDev &O) {
 }
 
 static void offsets_of(int slot, int &ox, int &oy, int &oz) {
+    ox = oy = oz = 0;
     int s = 0;
     for (int code = 0; code < SPH_NOFF; ++code) {
         int x = code % 7 - 3, y = (code / 7) % 7 - 3, z = code / 49 - 3;

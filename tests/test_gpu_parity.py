@@ -96,21 +96,20 @@ def test_selection_threshold_ties_and_mask(sph, ctx):
     assert 150 in J and 250 not in J and 4090 not in J
 
 
-def test_selection_one_pass_equals_two_pass(sph, monkeypatch):
-    """The one-pass look-back selection emits exactly what the count / scan / emit passes do."""
-    import torch
-    p = si.streamer(n=96, box=1.0, chan_len=0.5, i_frac=1e-4, e_frac=0.2, targets_all=False, seed=41,
-                    name="s96")
-    res = []
+@pytest.mark.parametrize("n", [45, 96, 200])
+def test_selection_one_pass_equals_two_pass(sph, monkeypatch, n):
+    """The one-pass look-back selection and the count / scan / emit passes both emit the
+    oracle's sets (odd row pitch at 45; 4096 bricks at 200)."""
+    p = si.streamer(n=n, box=1.0, chan_len=0.5, i_frac=1e-4, e_frac=0.2, targets_all=False, seed=41 + n,
+                    name="s%d" % n)
+    Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
     for flag in ("1", "0"):
         monkeypatch.setenv("SPH_SELECT_TWO_PASS", flag)
         c = sph.Context(0)
         sph.solve(p, c)
-        res.append(sph.get_selection(c))
+        J, T = sph.get_selection(c)
         c.close()
-    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
-    Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
-    assert np.array_equal(res[1][0], Jo) and np.array_equal(res[1][1], To)
+        assert np.array_equal(J, Jo) and np.array_equal(T, To), flag
 
 
 @pytest.mark.parametrize("case", [(16, 16, 16, 0.05, 0.3, 8, 2), (12, 9, 7, 0.2, 0.1, 4, 3),
