@@ -172,6 +172,7 @@ __device__ __forceinline__ void upward_box(const FmmDev &F, int level, int b) {
 // leaves_only: the split boxes' M2M runs on the tensor cores (k_m2m_tc)
 __global__ void __launch_bounds__(2 * MAXPAD) k_upward(FmmDev F, int level, const int *__restrict__ list,
                                                        const int *__restrict__ count, int leaves_only) {
+    pdl_enter();
     const int cnt = *count;
     for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
         const int b = list[i];
@@ -185,7 +186,7 @@ int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list,
                      cudaStream_t st) {
     if (box_count <= 0 || level < 2) return 0;
     int grid = box_count < 152 * 8 ? box_count : 152 * 8;
-    k_upward<<<grid, 2 * F.O.npad, 0, st>>>(F, level, list, count, leaves_only ? 1 : 0);
+    launch_pdl(k_upward, grid, 2 * F.O.npad, 0, st, F, level, list, count, leaves_only ? 1 : 0);
     return 1;
 }
 
@@ -208,6 +209,7 @@ __device__ __forceinline__ int warp_append(unsigned act, bool pred, int *counter
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
                              int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
                              int *__restrict__ p2p_cnt) {
+    pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
     const unsigned act = __activemask();
@@ -245,12 +247,13 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
                     int *p2p_list, int *p2p_cnt, cudaStream_t st) {
     if (nboxes <= 0) return;
-    k_work_lists<<<(nboxes + 255) / 256, 256, 0, st>>>(F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
+    launch_pdl(k_work_lists, (nboxes + 255) / 256, 256, 0, st, F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
                                                        p2p_cnt);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
 __global__ void __launch_bounds__(2 * MAXPAD) k_m2l_simt(FmmDev F, int level, int box_begin, int box_count) {
+    pdl_enter();
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     int v0 = F.L.v_off[b], v1 = F.L.v_off[b + 1];
@@ -278,11 +281,12 @@ __global__ void __launch_bounds__(2 * MAXPAD) k_m2l_simt(FmmDev F, int level, in
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
     (void)m2l_prec;
-    k_m2l_simt<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
+    launch_pdl(k_m2l_simt, box_count, 2 * F.O.npad, 0, st, F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ P2L (X list)
 __global__ void __launch_bounds__(2 * MAXPAD) k_p2l(FmmDev F, int level, int box_begin, int box_count) {
+    pdl_enter();
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     int x0 = F.L.x_off[b], x1 = F.L.x_off[b + 1];
@@ -334,11 +338,12 @@ __global__ void __launch_bounds__(2 * MAXPAD) k_p2l(FmmDev F, int level, int box
 
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
-    k_p2l<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
+    launch_pdl(k_p2l, box_count, 2 * F.O.npad, 0, st, F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ downward: L2L
 __global__ void __launch_bounds__(2 * MAXPAD) k_down(FmmDev F, int level, int box_begin, int box_count) {
+    pdl_enter();
     int b = box_begin + blockIdx.x;
     if (blockIdx.x >= box_count) return;
     const TreeDev &T = F.T;
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(2 * MAXPAD) k_down(FmmDev F, int level, int bo
 
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
     if (box_count <= 0 || level < 3) return;
-    k_down<<<box_count, 2 * F.O.npad, 0, st>>>(F, level, box_begin, box_count);
+    launch_pdl(k_down, box_count, 2 * F.O.npad, 0, st, F, level, box_begin, box_count);
 }
 
 // ------------------------------------------------------------------ leaves
@@ -556,6 +561,7 @@ __device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restri
 // CTAs walk the compact list of leaves that need this kernel.
 __global__ void __launch_bounds__(LT) k_leaf(FmmDev F, const int *__restrict__ list, const int *__restrict__ count,
                                              float *__restrict__ out) {
+    pdl_enter();
     const int cnt = *count;
     for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
         leaf_box(F, list[i], out);
@@ -584,6 +590,7 @@ size_t sep_smem_bytes(int p, int np, int e) {
 
 __global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, const int *__restrict__ list,
                                                  const int *__restrict__ count, int band, float *__restrict__ out) {
+    pdl_enter();
     const int box_count = *count;
     extern __shared__ float sm[];
     const int p = F.O.order, n = F.O.n, np = F.O.npad;
@@ -658,6 +665,7 @@ constexpr int SEPW_NP = 224;
 __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int level, const int *__restrict__ list,
                                                                    const int *__restrict__ count,
                                                                    float *__restrict__ out) {
+    pdl_enter();
     const int box_count = *count;
     __shared__ float Sb[SEPW_MAXP * SEPW_MAXE];                                  // [p][e]
     __shared__ __align__(16) float sd[SEPW_WARPS][SEPW_NP];
@@ -769,7 +777,7 @@ void fmm_l2p_sep_level(const FmmDev &F, int level, const int *list, const int *c
         const int per = SEPW_WARPS;
         int grid = (box_count + per - 1) / per;
         if (grid > 152 * 8) grid = 152 * 8;
-        k_l2p_sep_small<<<grid, SEPW_WARPS * 32, 0, st>>>(F, level, list, count, out);
+        launch_pdl(k_l2p_sep_small, grid, SEPW_WARPS * 32, 0, st, F, level, list, count, out);
         return;
     }
     const int e = 1 << (F.D - level), p = F.O.order;
@@ -777,7 +785,7 @@ void fmm_l2p_sep_level(const FmmDev &F, int level, const int *list, const int *c
     const size_t smem = sep_smem_bytes(p, F.O.npad, e);
     const int zs = (e + SEP_SLAB - 1) / SEP_SLAB;
     int gx = box_count < 152 * 4 ? box_count : 152 * 4;
-    k_l2p_sep<<<dim3(gx, zs), 256, smem, st>>>(F, level, list, count, band, out);
+    launch_pdl(k_l2p_sep, dim3(gx, zs), 256, smem, st, F, level, list, count, band, out);
 }
 
 // Shared-memory opt-in of the FMM kernels that may need more than 48 KiB (host, once, before
@@ -854,6 +862,7 @@ __device__ __forceinline__ float p2p_sum(const float4 *__restrict__ pts, int lo,
 
 template <bool TAYLOR>
 __global__ void k_near_table(P2PConst K, float *tab) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < GTAB_N) tab[i] = i == 0 ? K.wself : p2p_g<TAYLOR>((float)i, K);
 }
@@ -862,6 +871,7 @@ template <bool TAYLOR, bool TABLE>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
                                                          const int *__restrict__ count, float *__restrict__ out,
                                                          P2PConst K) {
+    pdl_enter();
     __shared__ float4 stage[P2P_CAP];
     __shared__ float tab[TABLE ? GTAB_N : 1];
     __shared__ int4 ubox[P2P_MAXU];        // W boxes: lowest cell corner, edge (strategy 3)
@@ -1068,8 +1078,8 @@ static P2PConst p2p_const(const FmmDev &F) {
 
 void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st) {
     const P2PConst K = p2p_const(F);
-    if (K.bma_h >= 0.5f) k_near_table<false><<<(GTAB_N + 255) / 256, 256, 0, st>>>(K, gtab);
-    else k_near_table<true><<<(GTAB_N + 255) / 256, 256, 0, st>>>(K, gtab);
+    if (K.bma_h >= 0.5f) launch_pdl(k_near_table<false>, (GTAB_N + 255) / 256, 256, 0, st, K, gtab);
+    else launch_pdl(k_near_table<true>, (GTAB_N + 255) / 256, 256, 0, st, K, gtab);
 }
 
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st) {
@@ -1077,16 +1087,16 @@ void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cn
     const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
     const P2PConst K = p2p_const(F);
     const bool taylor = K.bma_h < 0.5f, table = F.gtab != nullptr;
-    if (!taylor && !table) k_p2p<false, false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
-    else if (taylor && !table) k_p2p<true, false><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
-    else if (!taylor) k_p2p<false, true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
-    else k_p2p<true, true><<<grid, P2P_WARPS * 32, 0, st>>>(F, p2p_list, p2p_cnt, out, K);
+    if (!taylor && !table) launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
+    else if (taylor && !table) launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
+    else if (!taylor) launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
+    else launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {
     if (nboxes <= 0) return;
     int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
-    k_leaf<<<grid, LT, 0, st>>>(F, list, count, out_dense);
+    launch_pdl(k_leaf, grid, LT, 0, st, F, list, count, out_dense);
 }
 
 }  // namespace sph

@@ -27,6 +27,7 @@ __device__ __forceinline__ float ord2f(unsigned u) {
 
 __global__ void k_grid_max(const float *__restrict__ q, const float *__restrict__ e, int64_t n,
                            unsigned *__restrict__ out /* [2] ordered-uint maxima */) {
+    pdl_enter();
     float mq = -INFINITY, me = -INFINITY;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(512) k_select_brick(
         const int *__restrict__ off_s, const int *__restrict__ off_t,// [nbricks] (emit pass)
         uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc, float *__restrict__ src_q,
         uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc, uint8_t *__restrict__ tmask) {
+    pdl_enter();
     const int b = r.brick_edge_log2;
     const int ncell = 1 << (3 * b);
     const uint32_t brick = blockIdx.x;
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(512) k_select_brick(
 __global__ void __launch_bounds__(1024) k_scan2(const int *__restrict__ a, const int *__restrict__ b,
                                                 int *__restrict__ oa, int *__restrict__ ob, int n,
                                                 int *__restrict__ tot) {
+    pdl_enter();
     __shared__ int sa[1024], sb[1024];
     int per = (n + 1023) / 1024;
     int beg = threadIdx.x * per, end = min(n, beg + per);
@@ -278,6 +281,7 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
         float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
         uint8_t *__restrict__ tmask) {
+    pdl_enter();
     __shared__ int s_brick;
     __shared__ float s_thr_q, s_thr_e;
     __shared__ int s_qpos;
@@ -515,13 +519,13 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     if (gm > 152 * 8) gm = 152 * 8;
     if (gm < 1) gm = 1;
     const float *gq = r.src_all ? nullptr : A.q, *ge = r.trg_mode == 1 ? A.emag : nullptr;
-    if (gq || ge) k_grid_max<<<gm, 256, 0, st>>>(gq, ge, n, A.maxes);
+    if (gq || ge) launch_pdl(k_grid_max, gm, 256, 0, st, gq, ge, n, A.maxes);
     if (A.two_pass) {
-        k_select_brick<false><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
+        launch_pdl(k_select_brick<false>, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                    nullptr);
-        k_scan2<<<1, 1024, 0, st>>>(A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
-        k_select_brick<true><<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
+        launch_pdl(k_scan2, 1, 1024, 0, st, A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
+        launch_pdl(k_select_brick<true>, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
                                                   A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
                                                   A.trg_key, A.trg_pc, A.tmask);
         return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -532,7 +536,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     cudaMemsetAsync(state, 0, sizeof(unsigned long long) * nbr, st);
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
-    k_select_onepass<<<nbr, 512, 0, st>>>(r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
+    launch_pdl(k_select_onepass, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
                                           A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -40,6 +40,7 @@ void tc_init_attributes();
 
 // Operator (FP32, transposed [k][i], stride np) -> BF16 hi / lo images, K-major SW128.
 __global__ void k_make_image(const float *__restrict__ opT, int np, uint16_t *__restrict__ img) {
+    pdl_enter();
     const float *src = opT + (size_t)blockIdx.y * np * np;
     uint16_t *hi = img + (size_t)blockIdx.y * 2 * (A_BYTES / 2);
     uint16_t *lo = hi + A_BYTES / 2;
@@ -56,7 +57,7 @@ __global__ void k_make_image(const float *__restrict__ opT, int np, uint16_t *__
 
 void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st) {
     if (count <= 0) return;
-    k_make_image<<<dim3((TCM * TCK + 255) / 256, count), 256, 0, st>>>(opT, np, img);
+    launch_pdl(k_make_image, dim3((TCM * TCK + 255) / 256, count), 256, 0, st, opT, np, img);
 }
 
 struct TcSmem {
@@ -228,6 +229,7 @@ __device__ __forceinline__ void tile_teardown(const TcSmem &s) {
 // ---------------------------------------------------------------- M2L over offset-grouped V pairs
 __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
                                                 int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     const int tile = blockIdx.x;
     if (tile >= Pd.tile_off[Pd.nkeys]) return;
@@ -271,6 +273,7 @@ __device__ __forceinline__ void m2l_tile_range(const PairsDev &Pd, int key, int 
 
 __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
                                                         int *err) {
+    pdl_enter();
     const int T = Pd.tile_off[Pd.nkeys];
     const int chunk = (T + gridDim.x - 1) / gridDim.x;
     const int t_begin = blockIdx.x * chunk, t_end = min(T, t_begin + chunk);
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
 // ---------------------------------------------------------------- L2L for one level
 __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_begin, int parent_count,
                                                 const uint16_t *__restrict__ images, int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     TcSmem s = carve(smem_raw);
     const int t0 = blockIdx.x * TCN;
@@ -497,6 +501,7 @@ __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_
 __global__ void __launch_bounds__(256) k_m2m_tc(FmmDev F, int level, const int *__restrict__ list,
                                                 const int *__restrict__ count, const uint16_t *__restrict__ images,
                                                 int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     TcSmem s = carve(smem_raw);
     const int t0 = blockIdx.x * TCN;
@@ -531,7 +536,7 @@ void fmm_m2m_tc_level(const FmmDev &F, int level, int box_count, const int *list
     if (box_count <= 0 || level < 2) return;
     tc_init_attributes();
     dim3 grid((box_count + TCN - 1) / TCN, 8);
-    k_m2m_tc<<<grid, 256, TC_SMEM, st>>>(F, level, list, count, images, err);
+    launch_pdl(k_m2m_tc, grid, 256, TC_SMEM, st, F, level, list, count, images, err);
 }
 
 // ---------------------------------------------------------------- L2L, all 8 children per CTA
@@ -543,6 +548,7 @@ constexpr uint32_t L8_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + 64 + 9 * TCN * 4
 
 __global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent_begin, int parent_count,
                                                  const uint16_t *__restrict__ images, int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     uintptr_t pa = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
     uint8_t *base = reinterpret_cast<uint8_t *>(pa);
@@ -682,7 +688,7 @@ void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_
                        int *err, cudaStream_t st) {
     if (parent_count <= 0 || level < 3) return;
     tc_init_attributes();
-    k_l2l_tc8<<<(parent_count + TCN - 1) / TCN, 128, L8_SMEM, st>>>(F, level, parent_begin, parent_count, images,
+    launch_pdl(k_l2l_tc8, (parent_count + TCN - 1) / TCN, 128, L8_SMEM, st, F, level, parent_begin, parent_count, images,
                                                                      err);
 }
 
@@ -699,6 +705,7 @@ constexpr uint32_t L2P_B = 64 * TCK * 2;                // 16 KiB: up to 64 cell
 constexpr uint32_t L2P_SMEM = 1024 + 2 * L2P_A + 2 * L2P_B + 64 + 2 * TCM * 4;
 
 __global__ void k_l2p_image(const float *__restrict__ etab, int e, int n, int N, int ntiles, uint16_t *img) {
+    pdl_enter();
     const int rows = e * e * e;
     const size_t total = (size_t)ntiles * N * TCK;
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -729,7 +736,7 @@ __host__ __device__ int l2p_tile_n(int e) {
 void make_l2p_images(const float *etab, int e, int n, uint16_t *img, cudaStream_t st) {
     const int N = l2p_tile_n(e), ntiles = (e * e * e + N - 1) / N;
     const size_t total = (size_t)ntiles * N * TCK;
-    k_l2p_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(etab, e, n, N, ntiles, img);
+    launch_pdl(k_l2p_image, (unsigned)((total + 255) / 256), 256, 0, st, etab, e, n, N, ntiles, img);
 }
 
 size_t l2p_image_elems(int e) {
@@ -740,6 +747,7 @@ size_t l2p_image_elems(int e) {
 __global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_begin, int box_count,
                                                 const uint16_t *__restrict__ img, float *__restrict__ out,
                                                 int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *a_hi = base, *a_lo = base + L2P_A, *b_hi = base + 2 * L2P_A, *b_lo = b_hi + L2P_B;
@@ -892,6 +900,7 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                                                      int ppc, const uint16_t *__restrict__ img_e,
                                                      const uint16_t *__restrict__ img_c, float *__restrict__ out,
                                                      int *err) {
+    pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *ap_hi = base, *ap_lo = base + LP_A, *ac_hi = base + 2 * LP_A, *ac_lo = base + 3 * LP_A;
@@ -1080,7 +1089,7 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
     // parents per CTA: up to 128 (the MMA's M), fewer where that spreads the work evenly over
     // two rounds of one CTA per SM
     const int ppc = std::max(1, std::min(TCM, (parent_count + 2 * 152 - 1) / (2 * 152)));
-    k_l2lp_tc<<<(parent_count + ppc - 1) / ppc, LP_T, LP_SMEM, st>>>(F, level, parent_begin, parent_count, ppc,
+    launch_pdl(k_l2lp_tc, (parent_count + ppc - 1) / ppc, LP_T, LP_SMEM, st, F, level, parent_begin, parent_count, ppc,
                                                                      F.O.l2p_img + F.O.l2p_off[level],
                                                                      F.O.l2p_img + F.O.l2pc_off, out, err);
 }
@@ -1108,7 +1117,7 @@ void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, 
                       cudaStream_t st) {
     if (box_count <= 0 || level < 2 || F.O.l2p_off[level] < 0) return;
     tc_init_attributes();
-    k_l2p_tc<<<(box_count + TCM - 1) / TCM, 128, L2P_SMEM, st>>>(F, level, box_begin, box_count,
+    launch_pdl(k_l2p_tc, (box_count + TCM - 1) / TCM, 128, L2P_SMEM, st, F, level, box_begin, box_count,
                                                                  F.O.l2p_img + F.O.l2p_off[level], out, err);
 }
 
@@ -1117,11 +1126,11 @@ void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *ima
     if (nV <= 0) return;
     tc_init_attributes();
     if (pipelined) {
-        k_m2l_tc_pipe<<<152, 128, PIPE_SMEM, st>>>(F, Pd, images, err);
+        launch_pdl(k_m2l_tc_pipe, 152, 128, PIPE_SMEM, st, F, Pd, images, err);
         return;
     }
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;
-    k_m2l_tc<<<grid, 256, TC_SMEM, st>>>(F, Pd, images, err);
+    launch_pdl(k_m2l_tc, grid, 256, TC_SMEM, st, F, Pd, images, err);
 }
 
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
@@ -1129,7 +1138,7 @@ void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_c
     if (parent_count <= 0 || level < 3) return;
     tc_init_attributes();
     dim3 grid((parent_count + TCN - 1) / TCN, 8);
-    k_l2l_tc<<<grid, 256, TC_SMEM, st>>>(F, level, parent_begin, parent_count, images, err);
+    launch_pdl(k_l2l_tc, grid, 256, TC_SMEM, st, F, level, parent_begin, parent_count, images, err);
 }
 
 }  // namespace sph

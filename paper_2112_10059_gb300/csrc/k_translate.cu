@@ -101,6 +101,7 @@ __device__ __forceinline__ void scatter_add(float *__restrict__ out, int np, int
 
 // ---------------------------------------------------------------- M2L
 __global__ void __launch_bounds__(256) k_m2l_gemm(FmmDev F, int level, int box_begin, int box_count) {
+    pdl_enter();
     __shared__ __align__(16) float As[TK][TM];
     __shared__ __align__(16) float Bs[TK][TN];
     __shared__ int trg[TN], src[TN];
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(FmmDev F, int level, int box_b
 
 // ---------------------------------------------------------------- L2L
 __global__ void __launch_bounds__(256) k_l2l_gemm(FmmDev F, int level, int parent_begin, int parent_count) {
+    pdl_enter();
     __shared__ __align__(16) float As[TK][TM];
     __shared__ __align__(16) float Bs[TK][TN];
     __shared__ int par[TN], dst[TN];
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(256) k_l2l_gemm(FmmDev F, int level, int paren
 // key's range into tiles of TN pairs: tile counts, their exclusive scan (the tile offsets),
 // the closing offsets and the key of every tile.
 __global__ void __launch_bounds__(1024) k_vpairs_finish(PairsDev Pd) {
+    pdl_enter();
     __shared__ int ws[32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int per = (Pd.nkeys + 1023) / 1024;
@@ -237,10 +240,11 @@ __global__ void __launch_bounds__(1024) k_vpairs_finish(PairsDev Pd) {
     }
 }
 
-void vpairs_finish(const PairsDev &Pd, cudaStream_t st) { k_vpairs_finish<<<1, 1024, 0, st>>>(Pd); }
+void vpairs_finish(const PairsDev &Pd, cudaStream_t st) { launch_pdl(k_vpairs_finish, 1, 1024, 0, st, Pd); }
 
 // One CTA per tile of up to 64 V pairs sharing (level, offset): d_B += M2L_{l,o} u_A, scatter-added.
 __global__ void __launch_bounds__(256) k_m2l_pairs(FmmDev F, PairsDev Pd) {
+    pdl_enter();
     __shared__ __align__(16) float As[TK][TM];
     __shared__ __align__(16) float Bs[TK][TN];
     __shared__ int trg[TN], src[TN];
@@ -278,7 +282,7 @@ void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cu
     if (nV <= 0) return;
     // upper bound on the tile count: every key adds at most one partial tile
     int grid = (nV + TN - 1) / TN + Pd.nkeys;
-    k_m2l_pairs<<<grid, 256, 0, st>>>(F, Pd);
+    launch_pdl(k_m2l_pairs, grid, 256, 0, st, F, Pd);
 }
 
 // ---------------------------------------------------------------- L2P for whole leaf boxes
@@ -289,6 +293,7 @@ void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cu
 // their key.  Writes (=) every target of every leaf of this level.
 __global__ void __launch_bounds__(256) k_l2p_gemm(FmmDev F, int level, int box_begin, int box_count,
                                                   float *__restrict__ out) {
+    pdl_enter();
     __shared__ __align__(16) float As[TK][TM];
     __shared__ __align__(16) float Bs[TK][TN];
     __shared__ float Cs[TM][TN + 1];
@@ -338,19 +343,19 @@ void fmm_l2p_gemm_level(const FmmDev &F, int level, int box_begin, int box_count
     if (box_count <= 0 || level < 2 || F.O.e_off[level] < 0) return;
     int e = 1 << (F.D - level);
     dim3 grid((box_count + TN - 1) / TN, (e * e * e + TM - 1) / TM);
-    k_l2p_gemm<<<grid, 256, 0, st>>>(F, level, box_begin, box_count, out);
+    launch_pdl(k_l2p_gemm, grid, 256, 0, st, F, level, box_begin, box_count, out);
 }
 
 void fmm_m2l_gemm_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st) {
     if (box_count <= 0 || level < 2) return;
     dim3 grid((box_count + TN - 1) / TN, (F.O.npad + TM - 1) / TM);
-    k_m2l_gemm<<<grid, 256, 0, st>>>(F, level, box_begin, box_count);
+    launch_pdl(k_m2l_gemm, grid, 256, 0, st, F, level, box_begin, box_count);
 }
 
 void fmm_l2l_gemm_level(const FmmDev &F, int level, int parent_begin, int parent_count, cudaStream_t st) {
     if (parent_count <= 0 || level < 3) return;
     dim3 grid((parent_count + TN - 1) / TN, (F.O.npad + TM - 1) / TM, 8);
-    k_l2l_gemm<<<grid, 256, 0, st>>>(F, level, parent_begin, parent_count);
+    launch_pdl(k_l2l_gemm, grid, 256, 0, st, F, level, parent_begin, parent_count);
 }
 
 }  // namespace sph

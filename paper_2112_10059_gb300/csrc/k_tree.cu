@@ -103,6 +103,7 @@ __device__ __forceinline__ void tile_store(int *__restrict__ out, int base, int 
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_small(ScanSet S, int n) {
+    pdl_enter();
     __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
     __shared__ int ws[32];
     const int a = blockIdx.y;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_small(ScanSet S, int n) {
 // [0, true prefix], so indices derived from them stay in bounds) and sets bit 0 of *err.
 __global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int ntiles,
                                                          unsigned long long *__restrict__ state, int *err) {
+    pdl_enter();
     __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
     __shared__ int ws[32];
     __shared__ int s_tile, s_pre;
@@ -183,13 +185,13 @@ void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cu
         return;
     }
     if (n <= SCAN_SMALL) {
-        k_scan_small<<<dim3(1, k), SCAN_T, 0, st>>>(S, n);
+        launch_pdl(k_scan_small, dim3(1, k), SCAN_T, 0, st, S, n);
         return;
     }
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     unsigned long long *state = reinterpret_cast<unsigned long long *>(tmp);
     cudaMemsetAsync(state, 0, sizeof(unsigned long long) * k * (ntiles + 1), st);
-    k_scan_onepass<<<dim3(ntiles, k), SCAN_T, 0, st>>>(S, n, ntiles, state, err);
+    launch_pdl(k_scan_onepass, dim3(ntiles, k), SCAN_T, 0, st, S, n, ntiles, state, err);
 }
 
 void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err) {
@@ -220,6 +222,7 @@ constexpr int RANGE_PER = 8, RANGE_T = 256;
 
 __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ n_dev, const uint32_t *__restrict__ key,
                                                          int D, int Lmax, int *__restrict__ beg, int *__restrict__ end) {
+    pdl_enter();
     __shared__ uint32_t task_key[2 * RANGE_PER * RANGE_T];
     __shared__ int task_val[2 * RANGE_PER * RANGE_T];
     __shared__ uint8_t task_lvl[2 * RANGE_PER * RANGE_T];   // first level | 0x80 for an end
@@ -295,6 +298,7 @@ __device__ __forceinline__ int level_of_slot(int64_t s, int Lmax) {
 __global__ void k_tree_exists(int64_t nslot, int Lmax, int D, int S, const int *__restrict__ rsb,
                               const int *__restrict__ rse, const int *__restrict__ rtb, const int *__restrict__ rte,
                               int *__restrict__ flag) {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     const int l = level_of_slot(s, Lmax);
@@ -316,6 +320,7 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
                                 const uint32_t *__restrict__ skey, const int *__restrict__ ns_dev,
                                 const uint32_t *__restrict__ tkey, const int *__restrict__ nt_dev,
                                 uint8_t *__restrict__ vsrc) {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= Lmax) {       // level table (threads 0..Lmax)
         const int l = (int)s;
@@ -353,6 +358,7 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
 // sources (the deepest existing box over the slot); levels 0..Lmax-1.
 __global__ void k_src_occ(TreeDev T, int64_t nslot, int Lmax, const int *__restrict__ rsb,
                           const int *__restrict__ rse, uint8_t *__restrict__ occ) {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     uint8_t o = rse[s] > rsb[s];
@@ -371,6 +377,7 @@ __global__ void k_src_occ(TreeDev T, int64_t nslot, int Lmax, const int *__restr
 }
 
 __global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ occ, uint8_t *__restrict__ near) {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     const int l = level_of_slot(s, Lmax);
@@ -402,21 +409,21 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     // targets: enough blocks for every possible point (blocks past the actual count exit at
     // once); sources, usually far fewer: a grid-stride loop over 8 blocks per SM
     const int rg = (int)std::min<int64_t>(((int64_t)A.ncap + RB - 1) / RB, 1 << 20);
-    k_tree_ranges<<<std::max(std::min(rg, 152 * 8), 1), RANGE_T, 0, st>>>(A.ns_dev, A.skey, A.D, A.Lmax, A.rsb,
+    launch_pdl(k_tree_ranges, std::max(std::min(rg, 152 * 8), 1), RANGE_T, 0, st, A.ns_dev, A.skey, A.D, A.Lmax, A.rsb,
                                                                            A.rse);
-    k_tree_ranges<<<std::max(rg, 1), RANGE_T, 0, st>>>(A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
+    launch_pdl(k_tree_ranges, std::max(rg, 1), RANGE_T, 0, st, A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
     cudaMemsetAsync(A.T.lvl_src, 0, 16 * sizeof(int), st);
-    k_tree_exists<<<grid, 256, 0, st>>>(nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
+    launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);
-    k_tree_emit_all<<<grid, 256, 0, st>>>(A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
+    launch_pdl(k_tree_emit_all, grid, 256, 0, st, A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
                                           A.rte, total, A.skey, A.ns_dev, A.tkey, A.nt_dev, A.vsrc);
     const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
     if (npar > 0 && A.occ && A.near) {
         const int g2 = (int)((npar + 255) / 256);
-        k_src_occ<<<g2, 256, 0, st>>>(A.T, npar, A.Lmax - 1, A.rsb, A.rse, A.occ);
-        k_src_near<<<g2, 256, 0, st>>>(npar, A.Lmax - 1, A.occ, A.near);
+        launch_pdl(k_src_occ, g2, 256, 0, st, A.T, npar, A.Lmax - 1, A.rsb, A.rse, A.occ);
+        launch_pdl(k_src_near, g2, 256, 0, st, npar, A.Lmax - 1, A.occ, A.near);
     }
 }
 
@@ -451,6 +458,7 @@ __device__ __forceinline__ bool adjacent(const BoxGeom &a, const BoxGeom &b, int
 // lane, the 216 V candidates 32 at a time, entries placed in slot order by warp prefix
 // sums, so every list comes out exactly as a serial walk of the slots would write it.
 __global__ void k_lists_classify(TreeDev T, ListDev L, int cap, const int *__restrict__ nboxes_dev) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= cap) return;
     bool heavy = false;
@@ -516,6 +524,7 @@ __device__ __forceinline__ int coarse_leaf_src(const TreeDev &T, int lq, int qx,
 
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, PairsDev Pd, int D) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -648,8 +657,8 @@ void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, 
         return;
     }
     cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
-    k_lists_classify<<<(nboxes + 255) / 256, 256, 0, st>>>(T, L, cap, nboxes_dev);
-    k_lists_warp<false><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, Pd, D);
+    launch_pdl(k_lists_classify, (nboxes + 255) / 256, 256, 0, st, T, L, cap, nboxes_dev);
+    launch_pdl(k_lists_warp<false>, LISTS_WARP_GRID, 256, 0, st, T, L, Pd, D);
     ScanSet S{};
     S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;
     S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
@@ -659,6 +668,7 @@ void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, 
 }
 
 __global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ totals) {
+    pdl_enter();
     if (threadIdx.x == 0) {
         L.u_off[nboxes] = totals[0];
         L.v_off[nboxes] = totals[1];
@@ -670,8 +680,8 @@ __global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ t
 void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
                        const int *totals, cudaStream_t st) {
     if (nboxes <= 0) return;
-    k_close_offsets<<<1, 32, 0, st>>>(L, nboxes, totals);
-    k_lists_warp<true><<<LISTS_WARP_GRID, 256, 0, st>>>(T, L, Pd, D);
+    launch_pdl(k_close_offsets, 1, 32, 0, st, L, nboxes, totals);
+    launch_pdl(k_lists_warp<true>, LISTS_WARP_GRID, 256, 0, st, T, L, Pd, D);
     vpairs_finish(Pd, st);
 }
 

@@ -5,6 +5,44 @@
 #include <math.h>
 #include <stdint.h>
 
+#ifdef __CUDACC__
+#include <cstdlib>
+#include <utility>
+
+// ---------------------------------------------------------------- programmatic dependent launch
+// Kernels of the evaluation are launched with programmatic stream serialization: the CTAs of
+// a kernel may be scheduled while the previous kernel of the stream drains.  Every such kernel
+// begins with pdl_enter(): it waits until the previous kernel has completed and its writes are
+// visible (nothing is read or written before that), then lets the next kernel's launch begin.
+// Both instructions are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// SPH_PDL=0 in the environment launches every kernel in plain stream order.
+inline bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("SPH_PDL");
+        return !e || atoi(e) != 0;
+    }();
+    return on;
+}
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);
+}
+#endif
+
 #ifndef SPH_NP
 #define SPH_NP 6         // surface lattice points per cube edge
 #endif
