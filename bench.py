@@ -147,8 +147,8 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of k_grid_max + k_select_onepass, and of k_l2lp_tc);
 # valid for that workload and the kernels as profiled.
-NCU_TRAFFIC = {"select": (134.252288 + 3.670272 + 134.298112 + 103.954944) * 1e6,
-               "l2lp": (161.337088 + 39.760384) * 1e6}
+NCU_TRAFFIC = {"select": (134.236672 + 3.092224 + 134.303232 + 104.036864) * 1e6,
+               "l2lp": (161.343744 + 40.14208) * 1e6}
 
 
 def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_headline=True):
