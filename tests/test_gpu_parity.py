@@ -589,3 +589,34 @@ def test_strategy3_skips_within_its_bound(sph, r_s):
         assert res[r_s][1] > 0
     with pytest.raises(sph.SphError):
         sph.set_skip_ratio(sph.Context(0), -1.0)
+
+
+_LAUNCH_ORDER_CHILD = r'''
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import paper_2112_10059_gb300 as sph
+import sph_inputs as si
+p = si.streamer(n=96, box=1.0, chan_len=0.5, i_frac=1e-4, e_frac=0.2, targets_all=False, seed=7, name="order")
+ctx, out, _ = sph.solve(p, m2l_precision=sph.M2L_BF16X3)
+np.save(sys.argv[2], out.cpu().numpy() if hasattr(out, "cpu") else np.asarray(out))
+'''
+
+
+def test_launch_order_switch_same_result(sph, tmp_path):
+    """Programmatic dependent launch (the default) and plain stream order (SPH_PDL=0, read once
+    per process, so each mode runs in its own interpreter) give the same S_ph: the kernels are
+    the same, only the reductions of the translations may add in another order."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for flag in ("1", "0"):
+        f = tmp_path / ("s%s.npy" % flag)
+        subprocess.run([sys.executable, "-c", _LAUNCH_ORDER_CHILD, root, str(f)], check=True,
+                       env=dict(os.environ, SPH_PDL=flag), timeout=600)
+        res.append(np.load(f).astype(np.float64))
+    a, b = res
+    assert np.count_nonzero(a) > 0
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)
