@@ -34,6 +34,11 @@
  *  - All work is queued on the stream given to sph_create (NULL = legacy
  *    default stream).  eval_* calls may synchronise that stream internally
  *    (tree sizes are data dependent); they return after the result is queued.
+ *  - The library's kernels are launched with programmatic stream serialization:
+ *    each may be scheduled while the previous kernel of the stream drains, and
+ *    waits at entry until that kernel (the caller's or the library's) has
+ *    completed, so stream order holds as usual.  SPH_PDL=0 in the environment
+ *    (read once per process) launches them in plain stream order.
  *  - A CUDA error poisons the context: every later call returns SPH_ECUDA.
  *  - One context per host thread; contexts are independent.
  */
