@@ -1,0 +1,69 @@
+"""Host arithmetic of the benchmark's rooflines (CPU): the algorithmic work each phase is
+credited with, worked out by hand on a three-box tree.
+
+Tree: box 0 at level 2 (split; targets 0..8, sources 0..4) with two level-3 leaves, box 1
+(targets 0..4, sources 0..2) and box 2 (targets 4..8, sources 2..4); U lists pair each leaf
+with both leaves; no V or W entries.  Chebyshev order 5: n = 125 nodes, rows padded to 128.
+"""
+import os
+import sys
+import types
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+TREE = {
+    "level": np.array([2, 3, 3]),
+    "leaf": np.array([False, True, True]),
+    "trg_begin": np.array([0, 0, 4]), "trg_end": np.array([8, 4, 8]),
+    "src_begin": np.array([0, 0, 2]), "src_end": np.array([4, 2, 4]),
+    "V": [],
+    "U": np.array([[1, 1], [1, 2], [2, 1], [2, 2]]),
+    "W": np.zeros((0, 2), np.int64),
+}
+PEAKS = {"bf16_tflops": 1000.0, "hbm_gbs": 5000.0, "source": "test"}
+ARGS = types.SimpleNamespace(order=5, m2l="bf16x3")
+
+
+def _stats(fused):
+    base = {"ms_m2l": 0.01, "ms_l2l": 0.004, "ms_l2p": 0.006, "ms_l2lp": 0.004 if fused else 0.0,
+            "ms_near": 0.003, "ms_select": 0.002, "l2lp_fused": 1 if fused else 0}
+    other = dict(base, ms_select=0.004, ms_near=0.005)
+    return [base, other]                  # phase times are averaged over the steps
+
+
+def test_fused_deepest_level():
+    r = bench.rooflines(TREE, _stats(True), ARGS, nt=8, ns=4, ncell=1000, f_mhz=2000.0, peaks=PEAKS,
+                        workload_is_headline=False)
+    # fused level: parent box 0 and leaves 1, 2 read 128 x 4 B each, 8 targets written
+    assert r["l2lp"]["work_per_launch"] == 3 * 512 + 8 * 4
+    assert r["l2lp"]["achieved"] == pytest.approx(1568 / 0.004e-3 / 1e9)
+    assert r["l2lp"]["traffic"] is None   # the ncu traffic belongs to the headline workload only
+    # nothing left for the separate L2L (both level-3 boxes are fused) and L2P
+    assert r["l2l"]["work_per_launch"] == 0
+    assert r["l2p"]["work_per_launch"] == 0
+    assert r["l2p"]["ms_per_launch"] == pytest.approx(0.006 - 0.004)
+    # near field: 4 x 2 source cells for each of the 4 (leaf, leaf) pairs
+    assert r["near"]["work_per_launch"] == 32
+    assert r["near"]["achieved"] == pytest.approx(32 / 0.004e-3)
+    assert r["near"]["peak"] == pytest.approx(152 * 16 * 2000e6 / 3)
+    # selection: q and |E| read twice (16 B per cell), 8 B per target, 12 B per source, 1 B mask
+    assert r["select"]["work_per_launch"] == 16 * 1000 + 8 * 8 + 12 * 4 + 1000
+    assert r["select"]["frac"] == pytest.approx(17112 / 0.003e-3 / 1e9 / 5000.0)
+    assert r["m2l"]["work_per_launch"] == 0
+
+
+def test_separate_deepest_level():
+    r = bench.rooflines(TREE, _stats(False), ARGS, nt=8, ns=4, ncell=1000, f_mhz=2000.0, peaks=PEAKS,
+                        workload_is_headline=True)
+    assert "l2lp" not in r
+    # both leaves get an L2L from box 0: 2 n^2 flops each
+    assert r["l2l"]["work_per_launch"] == 2 * 2 * 125 ** 2
+    assert r["l2l"]["achieved"] == pytest.approx(62500 / 0.004e-3 / 1e12)
+    assert r["l2l"]["peak"] == 1000.0
+    # both leaves' expansions read, 8 targets written
+    assert r["l2p"]["work_per_launch"] == 2 * 512 + 8 * 4
+    assert r["select"]["traffic"] == bench.NCU_TRAFFIC["select"]
