@@ -67,3 +67,28 @@ def test_separate_deepest_level():
     # both leaves' expansions read, 8 targets written
     assert r["l2p"]["work_per_launch"] == 2 * 512 + 8 * 4
     assert r["select"]["traffic"] == bench.NCU_TRAFFIC["select"]
+
+
+def test_clock_summary_from_nvidia_smi_rows(tmp_path):
+    """The clock record of the timed region: median SM clock under load, the highest maximum
+    clock seen, and every throttle reason that was active in any sample."""
+    f = tmp_path / "clocks.csv"
+    f.write_text(
+        "0, 2070, 2070, 801.25, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1995, 2070, 1391.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "[N/A], [N/A]\n"
+        "0, 2040, 2070, 1200.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+    s = bench.ClockSampler(0)
+    s.path = str(f)
+    c = s.summary()
+    assert c == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_summary_flags_hardware_slowdown_and_no_samples(tmp_path):
+    f = tmp_path / "clocks.csv"
+    f.write_text("0, 1500, 2070, 900.0, 0x0000000000000008, Active, Not Active, Active, Not Active\n")
+    s = bench.ClockSampler(0)
+    s.path = str(f)
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.path = str(tmp_path / "missing.csv")
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
