@@ -1,5 +1,5 @@
-"""Host arithmetic of the benchmark's rooflines (CPU): the algorithmic work each phase is
-credited with, worked out by hand on a three-box tree.
+"""Host logic of the benchmark (CPU): the algorithmic work each roofline credits a phase with,
+worked out by hand on a three-box tree, and the clock record read from nvidia-smi rows.
 
 Tree: box 0 at level 2 (split; targets 0..8, sources 0..4) with two level-3 leaves, box 1
 (targets 0..4, sources 0..2) and box 2 (targets 4..8, sources 2..4); U lists pair each leaf
