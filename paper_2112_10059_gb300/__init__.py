@@ -176,6 +176,33 @@ def _hptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _cells(device, ncell, t, dtype, name):
+    """Device pointer of a per-cell CUDA tensor, after the checks the C ABI cannot make from a
+    bare pointer: on the context's device, contiguous, of ``dtype``, one element per grid cell.
+    With no grid yet (ncell 0) the size is left to the library's own call-order check."""
+    if t is None:
+        return None
+    p = _ptr(t)
+    if t.dtype != dtype:
+        raise TypeError("%s: expected %s, got %s" % (name, dtype, t.dtype))
+    if device is not None and t.device.index is not None and t.device.index != device:
+        raise ValueError("%s: tensor on cuda:%d, context on cuda:%d" % (name, t.device.index, device))
+    if ncell and t.numel() != ncell:
+        raise ValueError("%s: %d elements for a grid of %d cells" % (name, t.numel(), ncell))
+    return p
+
+
+def _hcells(ncell, a, dtype, name):
+    """Host pointer of a per-cell numpy array, with the same checks as :func:`_cells`."""
+    if a is None:
+        return None
+    if a.dtype != np.dtype(dtype):
+        raise TypeError("%s: expected %s, got %s" % (name, np.dtype(dtype), a.dtype))
+    if ncell and a.size != ncell:
+        raise ValueError("%s: %d elements for a grid of %d cells" % (name, a.size, ncell))
+    return _hptr(a)
+
+
 class Context:
     """Owns one ``sph_ctx``: device memory, operator cache and the last tree."""
 
@@ -224,13 +251,18 @@ def set_grid(ctx: Context, nx, ny, nz, h, pO2, chi_min=0.035, chi_max=2.0, origi
 
 def set_sources(ctx: Context, q, source_scale):
     """q: float32 CUDA tensor of nx*ny*nz cells (kept alive by the context)."""
+    import torch
+    qp = _cells(ctx.device, ctx.ncell, q, torch.float32, "q")
     ctx._keep = [k for k in ctx._keep if k[0] != "q"] + [("q", q)]
-    ctx._ck(ctx.lib.set_sources(ctx.h, _ptr(q), float(source_scale)))
+    ctx._ck(ctx.lib.set_sources(ctx.h, qp, float(source_scale)))
 
 
 def set_targets(ctx: Context, emag=None, mask=None):
+    import torch
+    ep = _cells(ctx.device, ctx.ncell, emag, torch.float32, "emag")
+    mp = _cells(ctx.device, ctx.ncell, mask, torch.uint8, "mask")
     ctx._keep = [k for k in ctx._keep if k[0] not in ("e", "m")] + [("e", emag), ("m", mask)]
-    ctx._ck(ctx.lib.set_targets(ctx.h, _ptr(emag), _ptr(mask)))
+    ctx._ck(ctx.lib.set_targets(ctx.h, ep, mp))
 
 
 def set_criteria(ctx: Context, i_frac=0.0, e_frac=0.0, e_applied=0.0, self_mode=1, leaf_size=64,
@@ -261,7 +293,8 @@ def eval_sph(ctx: Context, out=None, stats: bool = False):
     if out is None:
         out = torch.empty(ctx.ncell, dtype=torch.float32, device="cuda:%d" % ctx.device)
     st = Stats() if stats else None
-    ctx._ck(ctx.lib.eval_sph(ctx.h, _ptr(out), ctypes.byref(st) if st is not None else None))
+    op = _cells(ctx.device, ctx.ncell, out, torch.float32, "out")
+    ctx._ck(ctx.lib.eval_sph(ctx.h, op, ctypes.byref(st) if st is not None else None))
     return out, st
 
 
@@ -296,9 +329,14 @@ class BatchProblem:
                    chi_min=problem.chi_min, chi_max=problem.chi_max)
 
     def c_struct(self):
+        import torch
+        n = self.nx * self.ny * self.nz
+        dev = self.q.device.index if self.q is not None else None
         return Problem(self.nx, self.ny, self.nz, self.h, self.pO2, self.chi_min, self.chi_max,
-                       _ptr(self.q), self.source_scale, _ptr(self.emag), _ptr(self.mask), self.i_frac,
-                       self.e_frac, self.e_applied, _ptr(self.out))
+                       _cells(dev, n, self.q, torch.float32, "q"), self.source_scale,
+                       _cells(dev, n, self.emag, torch.float32, "emag"),
+                       _cells(dev, n, self.mask, torch.uint8, "mask"), self.i_frac,
+                       self.e_frac, self.e_applied, _cells(dev, n, self.out, torch.float32, "out"))
 
 
 def eval_sph_batch(ctx: Context, problems, stats: bool = False):
@@ -319,7 +357,9 @@ def eval_sph_host(ctx: Context, q, emag=None, mask=None, out=None, stats: bool =
     if out is None:
         out = np.empty(ctx.ncell, np.float32)
     st = Stats() if stats else None
-    ctx._ck(ctx.lib.eval_sph_host(ctx.h, _hptr(q), _hptr(emag), _hptr(mask), _hptr(out),
+    n = ctx.ncell
+    ctx._ck(ctx.lib.eval_sph_host(ctx.h, _hcells(n, q, np.float32, "q"), _hcells(n, emag, np.float32, "emag"),
+                                  _hcells(n, mask, np.uint8, "mask"), _hcells(n, out, np.float32, "out"),
                                   ctypes.byref(st) if st is not None else None))
     return out, st
 
@@ -330,7 +370,8 @@ def eval_direct(ctx: Context, fp64=False, out=None):
     if out is None:
         out = torch.empty(ctx.ncell, dtype=torch.float64 if fp64 else torch.float32,
                           device="cuda:%d" % ctx.device)
-    ctx._ck(ctx.lib.eval_direct(ctx.h, 1 if fp64 else 0, _ptr(out)))
+    op = _cells(ctx.device, ctx.ncell, out, torch.float64 if fp64 else torch.float32, "out")
+    ctx._ck(ctx.lib.eval_direct(ctx.h, 1 if fp64 else 0, op))
     return out
 
 
@@ -400,14 +441,15 @@ def solve(problem, ctx: Context | None = None, m2l_precision=M2L_F32, leaf_size=
     ctx = ctx or Context(0)
     set_grid(ctx, problem.nx, problem.ny, problem.nz, problem.h, problem.pO2_torr,
              problem.chi_min, problem.chi_max, problem.origin)
-    q = torch.from_numpy(problem.q).cuda()
+    dev = "cuda:%d" % ctx.device
+    q = torch.from_numpy(problem.q).to(dev)
     set_sources(ctx, q, problem.source_scale)
     if mask is not None:
-        set_targets(ctx, mask=torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).cuda())
+        set_targets(ctx, mask=torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).to(dev))
     elif problem.targets_all or problem.emag is None:
         set_targets(ctx)
     else:
-        set_targets(ctx, emag=torch.from_numpy(problem.emag).cuda())
+        set_targets(ctx, emag=torch.from_numpy(problem.emag).to(dev))
     set_criteria(ctx, problem.i_frac, problem.e_frac, problem.e_applied, 1,
                  problem.leaf_size if leaf_size is None else leaf_size, m2l_precision)
     out, st = eval_sph(ctx, stats=stats)
