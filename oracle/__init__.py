@@ -20,10 +20,13 @@ Contents
   convolution (an independent full-field cross-check).
 * :func:`radial_reference`: the continuum Eq. integral for a spherically
   symmetric source reduced to a 1D integral.
-* :func:`rel_l2`, :func:`e_delta`: the error measures of Eq. relativefun.
+* :func:`rel_l2`, :func:`e_delta`: the error measures of Eq. relativefun, and
+  :func:`max_rel`, the gate's maximum relative error above a floor.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-and ``tests/test_oracle_octree.py``; none is "parity unpinned".
+and ``tests/test_oracle_octree.py`` (the three error measures by hand-worked
+cases, boundaries, empty and all-zero inputs included); none is "parity
+unpinned".
 """
 from __future__ import annotations
 
@@ -187,7 +190,8 @@ def max_rel(num, ref, floor_frac=1e-3):
 
 
 def e_delta(num, ref, pts, x0, delta):
-    """E_delta(x0) / 100: mean relative error over points within ``delta`` of x0."""
+    """E_delta(x0) / 100: mean relative error over the points within ``delta`` of x0 (the
+    boundary included); 0 for an empty ball.  ``ref`` must be positive inside the ball."""
     pts = np.asarray(pts, np.float64)
     sel = np.linalg.norm(pts - np.asarray(x0)[None, :], axis=1) <= delta
     if not np.any(sel):

@@ -312,3 +312,60 @@ def test_truncated_gaussian_far_field_deficit():
         u = math.sqrt(math.log(1 / f))
         expect = math.erfc(u) + 2 * u / math.sqrt(math.pi) * math.exp(-u * u)
         assert np.all(np.abs(drop / expect - 1) < 0.03), (f, drop, expect)
+
+
+# --------------------------------------------------------------------------- error measures
+# Eq. relativefun (Section 4): E_V = ||num - ref||_2 / ||ref||_2 and
+# E_delta(x0) = (1/N_tot) sum_{|x - x0| <= delta} |num - ref| / ref over the N_tot grid points in
+# the ball.  The oracle returns both as fractions (the paper's x 100 %).  max_rel is the gate's
+# second measure: max |num - ref| / ref over the entries with ref > floor * max(ref).  The values
+# below are worked by hand; each case is laid out so that a plausible slip gives another number.
+
+def test_rel_l2_hand_worked():
+    ref = np.array([3.0, 4.0])                       # ||ref|| = 5
+    num = ref + np.array([0.3, 0.4])                 # ||num - ref|| = 0.5
+    assert oracle.rel_l2(num, ref) == pytest.approx(0.1, rel=1e-15)
+    # normalising by ||num|| (= 5.5) instead would give 0.0909...
+    assert oracle.rel_l2(ref, num) == pytest.approx(0.5 / 5.5, rel=1e-15)
+    assert oracle.rel_l2(ref, ref) == 0.0
+    # sign of the difference does not matter; scale does not matter
+    assert oracle.rel_l2(ref - np.array([0.3, 0.4]), ref) == pytest.approx(0.1, rel=1e-15)
+    assert oracle.rel_l2(7.0 * num, 7.0 * ref) == pytest.approx(0.1, rel=1e-14)
+    # all-zero reference: the measure is undefined; the oracle returns the absolute norm of num
+    assert oracle.rel_l2(np.array([1.0, 2.0, 2.0]), np.zeros(3)) == pytest.approx(3.0, rel=1e-15)
+    # empty sets
+    assert oracle.rel_l2(np.zeros(0), np.zeros(0)) == 0.0
+
+
+def test_max_rel_hand_worked():
+    # floor 1e-3 * max(ref) = 0.01: entries 0..2 count, entry 3 (ref 0.001) does not
+    ref = np.array([10.0, 0.02, 1.0, 0.001])
+    num = np.array([10.0, 0.03, 1.1, 100.0])
+    # relative errors over the counted entries: 0, 0.5, 0.1 -> 0.5
+    assert oracle.max_rel(num, ref, 1e-3) == pytest.approx(0.5, rel=1e-14)
+    # a floor taken from max(num) (= 100 -> 0.1) would drop entry 1 and give 0.1; dividing by
+    # num instead of ref would give 0.01/0.03 = 0.333 at entry 1
+    # the comparison is strict: an entry exactly at the floor does not count
+    ref2 = np.array([1000.0, 1.0, 2.0])
+    num2 = np.array([1001.0, 5.0, 2.2])
+    assert oracle.max_rel(num2, ref2, 1e-3) == pytest.approx(0.1, rel=1e-13)
+    # a larger floor leaves only the maximum
+    assert oracle.max_rel(num2, ref2, 0.5) == pytest.approx(1e-3, rel=1e-12)
+    # empty and all-zero references count nothing
+    assert oracle.max_rel(np.zeros(0), np.zeros(0)) == 0.0
+    assert oracle.max_rel(np.ones(3), np.zeros(3)) == 0.0
+
+
+def test_e_delta_hand_worked():
+    pts = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [3.0, 0.0, 0.0]])
+    ref = np.array([1.0, 2.0, 4.0, 8.0])
+    num = np.array([1.1, 2.0, 5.0, 100.0])
+    # ball of radius 2 around the origin holds points 0..2 (point 2 on its boundary, included):
+    # (0.1 + 0 + 0.25) / 3
+    assert oracle.e_delta(num, ref, pts, (0.0, 0.0, 0.0), 2.0) == pytest.approx(0.35 / 3, rel=1e-14)
+    # a strict boundary would give 0.05, dividing by every point (4) 0.0875, and the ball around
+    # another centre other points
+    assert oracle.e_delta(num, ref, pts, (3.0, 0.0, 0.0), 0.5) == pytest.approx(11.5, rel=1e-14)
+    assert oracle.e_delta(num, ref, pts, (3.0, 0.0, 0.0), 2.0) == pytest.approx((0.0 + 11.5) / 2, rel=1e-14)
+    # an empty ball
+    assert oracle.e_delta(num, ref, pts, (10.0, 10.0, 10.0), 1.0) == 0.0
