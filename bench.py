@@ -59,6 +59,14 @@ def parse():
                     help="Section 4.3 trade-off: FMM time and E_V against the full FP64 sum for I_pct 1e-4 .. 1e-1")
     ap.add_argument("--sur-samples", type=int, default=2000, help="FMM solves in the surrogate's training set")
     ap.add_argument("--sur-epochs", type=int, default=10)
+    ap.add_argument("--acc-uniform", type=int, default=100000,
+                    help="uniform targets of the stratified oracle sample (plus every target within 5 sigma of the head)")
+    ap.add_argument("--no-decomp", action="store_true", help="skip the error decomposition (M2L arithmetic, fusion, order)")
+    ap.add_argument("--no-full128", action="store_true",
+                    help="skip the non-adaptive 128^3 FMM-vs-direct block (every cell a source and a target)")
+    ap.add_argument("--no-pressures", action="store_true", help="skip the 76 and 380 Torr runs of the 256^3 workload")
+    ap.add_argument("--fft256", action="store_true",
+                    help="also time the FP64 FFT convolution of the 256^3 workload and check every target against it")
     return ap.parse_args()
 
 
@@ -145,27 +153,45 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
-# (dram__bytes_read.sum + dram__bytes_write.sum of k_grid_max + k_select_onepass, and of k_l2lp_tc);
-# valid for that workload and the kernels as profiled.
-NCU_TRAFFIC = {"select": (134.236672 + 3.092224 + 134.303232 + 104.036864) * 1e6,
-               "l2lp": (161.343744 + 40.14208) * 1e6}
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_l2lp_tc); valid for that workload and the
+# kernel as profiled (None once the kernel has changed since).
+NCU_TRAFFIC = {"l2lp": (161.343744 + 40.14208) * 1e6}
 
 
-def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_headline=True):
-    """Achieved vs peak per phase.  Work is ALGORITHMIC (what the method needs), not executed:
-      m2l  (tensor): 2 n^2 flops per V pair, n = order^3 (the BF16 x3 split executes 3 x 128^2 x 2);
+def pipe_peaks(sph, dev, stream, f_mhz_nominal=2070.0):
+    """FP32 FMA and MUFU throughput measured by the library's own kernels (sph_measure_pipe_peaks),
+    with the nominal figures as a fallback if the measurement fails."""
+    try:
+        m = sph.pipe_peaks(dev.index or 0, stream)
+        m["source"] = "measured (sph_measure_pipe_peaks: 8 independent chains per thread, 8 CTAs x 256 per SM)"
+        return m
+    except Exception as e:  # pragma: no cover - only without the library
+        f = f_mhz_nominal * 1e6
+        return {"ffma_flops": NSM * 128 * 2 * f, "ex2_per_s": NSM * MUFU_PER_SM_CLK * f,
+                "rsqrt_per_s": NSM * MUFU_PER_SM_CLK * f, "n_sm": NSM,
+                "source": "nominal (measurement failed: %s)" % e}
+
+
+def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=True, order=None):
+    """Achieved vs peak per kernel.  Work is ALGORITHMIC (what the method needs), not executed:
+      m2l  (tensor, k_m2l_tc): 2 n^2 flops per V pair, n = order^3 (the BF16 x3 split executes
+                     3 x 2 x 128^2);
       l2l  (tensor): 2 n^2 flops per child box with targets below level 2 (levels the separate
                      L2L kernels run: all but the deepest one when that level is fused);
-      l2lp (HBM): fused L2L + L2P of the deepest level: the parents' and the leaves' local
-                  expansions read (npad x 4 B each) + S written (4 B per target of those leaves);
+      l2lp (HBM, k_l2lp_tc): fused L2L + L2P of the deepest level: the parents' and the leaves'
+                  local expansions read (npad x 4 B each) + S written (4 B per target there);
       l2p  (HBM): the other leaves' local expansions read (npad x 4 B per leaf with targets) + S
-                  written (4 B per target);
-      near (MUFU):  P2P pairs + M2P evaluations (3 MUFU each: rsqrt + 2 x ex2);
-      select (HBM): 8 B per cell read twice (maxima, then the rules: q and |E|) + 8 B per target and
-                    12 B per source written + 1 B per cell of target mask."""
-    n = args.order ** 3
+                  written (4 B per target) -- only where such leaves exist;
+      near (MUFU, k_p2p): P2P pairs + M2P evaluations, 2 ex2 + 1 rsqrt each, against the measured
+                  ex2 and rsqrt rates;
+      select (HBM, k_grid_max + k_select_onepass): 16 B per cell (q and |E| read by the maxima
+                  pass and again by the rules) + 4 B per selected index (sources and targets).
+    Times are the medians of the library's CUDA-event phase timers; the step's dominant single
+    kernel is the entry with the longest time among those timed as one kernel."""
+    order = order or args.order
+    n = order ** 3
     npad = (n + 15) // 16 * 16
-    mean = lambda k: statistics.mean(x[k] for x in step_stats)
+    med = lambda k: statistics.median(x[k] for x in step_stats)
     fused = all(x["l2lp_fused"] for x in step_stats)
     lev = tree["level"]
     ntb = (tree["trg_end"] - tree["trg_begin"]).astype(np.int64)
@@ -180,41 +206,51 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, f_mhz, peaks, workload_is_h
     U, W = tree["U"], tree["W"]
     p2p = int(np.sum(ntb[U[:, 0]] * nsb[U[:, 1]])) if len(U) else 0
     m2p = int(np.sum(ntb[W[:, 0]]) * n) if len(W) else 0
-    fp32_peak = NSM * 128 * 2 * f_mhz * 1e6 / 1e12          # TFLOP/s: 128 FP32 lanes x FMA
-    mufu_peak = NSM * MUFU_PER_SM_CLK * f_mhz * 1e6 / MUFU_PER_EVAL
+    fp32_peak = pipes["ffma_flops"] / 1e12
+    mufu_evals = 1.0 / (2.0 / pipes["ex2_per_s"] + 1.0 / pipes["rsqrt_per_s"])
     tc = args.m2l == "bf16x3"
     tpk = peaks["bf16_tflops"]
     hbm = peaks["hbm_gbs"]
     hbm_basis = "measured HBM copy %.0f GB/s (%s)" % (hbm, peaks["source"])
     out = {}
 
-    def add(name, kernel, bound, work, unit_work, ms, peak, unit, basis, traffic=None):
+    def add(name, kernel, single, bound, work, unit_work, ms, peak, unit, basis, traffic=None):
         ach = work / (ms * 1e-3) if ms > 0 else 0.0
         scale = 1e12 if unit == "TFLOP/s" else (1e9 if unit == "GB/s" else 1.0)
-        out[name] = {"kernel": kernel, "bound": bound, "achieved": ach / scale, "peak": peak, "unit": unit,
-                     "frac": (ach / scale) / peak if peak else None, "traffic": traffic, "ms_per_launch": ms,
-                     "work_per_launch": work, "work_unit": unit_work, "peak_basis": basis}
+        out[name] = {"kernel": kernel, "single_kernel": single, "bound": bound, "achieved": ach / scale,
+                     "peak": peak, "unit": unit, "frac": (ach / scale) / peak if peak else None,
+                     "traffic": traffic, "ms_per_launch": ms, "work_per_launch": work, "work_unit": unit_work,
+                     "peak_basis": basis}
 
-    add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
-        mean("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
-        ("measured dense BF16 %.1f TFLOP/s (%s)" % (tpk, peaks["source"])) if tc else "FP32 FMA 152 SMs")
-    add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", "tensor" if tc else "alu", 2.0 * n * n * n_child,
-        "flop", mean("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
-    ms_lp = mean("ms_l2lp") if fused else 0.0
+    add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", True, "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
+        med("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
+        ("measured dense BF16 %.1f TFLOP/s burst (%s)" % (tpk, peaks["source"])) if tc else
+        "measured FP32 FMA %.1f TFLOP/s (%s)" % (fp32_peak, pipes["source"]))
+    if n_child > 0:
+        add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", False, "tensor" if tc else "alu",
+            2.0 * n * n * n_child, "flop", med("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
+    ms_lp = med("ms_l2lp") if fused else 0.0
     if fused:
         n_par = int(np.sum((lev == lmax - 1) & ~tree["leaf"] & (ntb > 0)))
         n_deep = int(np.sum(leaf_t & deep))
         nt_deep = int(np.sum(ntb[leaf_t & deep]))
-        add("l2lp", "k_l2lp_tc", "hbm", 4.0 * npad * (n_par + n_deep) + 4.0 * nt_deep, "bytes", ms_lp, hbm,
-            "GB/s", hbm_basis, traffic=NCU_TRAFFIC.get("l2lp") if workload_is_headline else None)
-    add("l2p", ("k_l2p_tc + " if tc and not fused else "") + "k_l2p_sep_small + k_l2p_sep", "hbm",
-        4.0 * npad * n_leaf_t + 4.0 * nt_other, "bytes", mean("ms_l2p") - ms_lp, hbm, "GB/s", hbm_basis)
-    add("near", "k_p2p", "alu", float(p2p + m2p), "kernel-evals", mean("ms_near"), mufu_peak, "evals/s",
-        "152 SMs x 16 MUFU/clk x %.0f MHz / 3 MUFU per eval" % f_mhz)
-    add("select", "k_grid_max + k_select_onepass", "hbm", 16.0 * ncell + 8.0 * nt + 12.0 * ns + 1.0 * ncell,
-        "bytes", mean("ms_select"), hbm, "GB/s", hbm_basis,
-        traffic=NCU_TRAFFIC["select"] if workload_is_headline else None)
+        add("l2lp", "k_l2lp_tc", True, "hbm", 4.0 * npad * (n_par + n_deep) + 4.0 * nt_deep, "bytes", ms_lp, hbm,
+            "GB/s", hbm_basis, traffic=NCU_TRAFFIC.get("l2lp") if traffic_ok else None)
+    if n_leaf_t > 0:
+        add("l2p", ("k_l2p_tc + " if tc and not fused else "") + "k_l2p_sep_small + k_l2p_sep", False, "hbm",
+            4.0 * npad * n_leaf_t + 4.0 * nt_other, "bytes", med("ms_l2p") - ms_lp, hbm, "GB/s", hbm_basis)
+    add("near", "k_p2p", True, "alu", float(p2p + m2p), "kernel-evals", med("ms_near"), mufu_evals, "evals/s",
+        "MUFU: 2 ex2 + 1 rsqrt per evaluation at the measured %.3g ex2/s and %.3g rsqrt/s (%s)"
+        % (pipes["ex2_per_s"], pipes["rsqrt_per_s"], pipes["source"]))
+    add("select", "k_grid_max + k_select_onepass", False, "hbm", 16.0 * ncell + 4.0 * (nt + ns),
+        "bytes", med("ms_select"), hbm, "GB/s", hbm_basis)
     return out
+
+
+def dominant_kernel(roof):
+    """The entry of the longest-running single kernel."""
+    singles = {k: v for k, v in roof.items() if v["single_kernel"]}
+    return max(singles, key=lambda k: singles[k]["ms_per_launch"])
 
 
 def oracle_sample(p, J, T, seconds, seed=5):
@@ -500,6 +536,209 @@ def run_sweep(sph, torch, dev, stream, args):
     return rows
 
 
+SIGMA_HEAD = 0.015      # cm: the streamer preset's head width (ball of E_delta: 5 sigma)
+
+
+def make_ctx(sph, dev, stream, p, q, em, prec, order, leaf=None, env=None):
+    """A context set up for problem p on device inputs q / em; ``env`` holds library switches
+    read at context creation (set only for that call)."""
+    saved = {}
+    for k, v in (env or {}).items():
+        saved[k] = os.environ.get(k)
+        os.environ[k] = v
+    try:
+        ctx = sph.Context(dev.index or 0, stream)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    sph.set_grid(ctx, p.nx, p.ny, p.nz, p.h, p.pO2_torr, p.chi_min, p.chi_max)
+    sph.set_sources(ctx, q, p.source_scale)
+    if p.targets_all or em is None:
+        sph.set_targets(ctx)
+    else:
+        sph.set_targets(ctx, emag=em)
+    sph.set_criteria(ctx, p.i_frac, p.e_frac, p.e_applied, 1, p.leaf_size if leaf is None else leaf, prec)
+    sph.set_far_field(ctx, sph.FAR_CHEBYSHEV, order)
+    return ctx
+
+
+def accuracy_block(p, J, T, S, n_uniform, cpu_seconds_single=3.0):
+    """The FP64 oracle on a stratified target sample (every target within 5 sigma of the head
+    + n_uniform seeded uniform others), timed on the host's cores; the FMM's errors there.
+    Returns (accuracy dict, oracle reference, sample, in_ball, weight, cpu timing dict)."""
+    import oracle
+    samp, ball, w = si.stratified_targets(p, T, si.streamer_head(), 5 * SIGMA_HEAD, n_uniform, seed=17)
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    t0 = time.perf_counter()
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+    dt = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    # single-thread rate on an evenly spaced part of the sample, about cpu_seconds_single long
+    per = dt * cores / max(samp.size, 1)
+    m = int(max(8, min(samp.size, cpu_seconds_single / max(per, 1e-9))))
+    sub = samp[np.linspace(0, samp.size - 1, m).astype(np.int64)]
+    prev = oracle.set_num_threads(1)
+    t1 = time.perf_counter()
+    oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, sub)
+    dt1 = time.perf_counter() - t1
+    oracle.set_num_threads(prev)
+    cpu = {"value": samp.size / dt, "seconds": dt, "cores": cores, "n": int(samp.size),
+           "single_thread_value": sub.size / dt1, "single_thread_n": int(sub.size), "single_thread_s": dt1}
+    acc = errors_on_sample(S[samp].astype(np.float64), ref, samp, ball, w, p)
+    return acc, ref, samp, ball, w, cpu
+
+
+def errors_on_sample(got, ref, samp, ball, w, p):
+    import oracle
+    X = p.origin[0] + p.h * (samp % p.nx + 0.5)
+    Y = p.origin[1] + p.h * ((samp // p.nx) % p.ny + 0.5)
+    Z = p.origin[2] + p.h * (samp // (p.nx * p.ny) + 0.5)
+    pts = np.stack([X, Y, Z], axis=1)
+    return {"rel_l2_whole_set_estimate": oracle.rel_l2_weighted(got, ref, np.where(ball, 1.0, w)),
+            "rel_l2_sample": oracle.rel_l2(got, ref),
+            "rel_l2_ball": oracle.rel_l2(got[ball], ref[ball]),
+            "rel_l2_uniform": oracle.rel_l2(got[~ball], ref[~ball]),
+            "max_rel": oracle.max_rel(got, ref, 1e-3),
+            "e_delta_5sigma": oracle.e_delta(got, ref, pts, si.streamer_head(), 5 * SIGMA_HEAD),
+            "n_ball": int(ball.sum()), "n_uniform": int((~ball).sum()), "uniform_weight": w}
+
+
+def error_decomposition(sph, torch, dev, stream, p, q, em, samp, ball, w, ref, args):
+    """The same evaluation with one ingredient changed at a time, errors on the same sample:
+    M2L arithmetic (FP32 SIMT vs BF16 x3), deepest level fused or separate, Chebyshev order."""
+    variants = [("bf16x3_fused_order5", sph.M2L_BF16X3, 5, {}),
+                ("bf16x3_separate_order5", sph.M2L_BF16X3, 5, {"SPH_L2LP_FUSED": "0"}),
+                ("f32_order5", sph.M2L_F32, 5, {}),
+                ("bf16x3_fused_order4", sph.M2L_BF16X3, 4, {}),
+                ("bf16x3_fused_order6", sph.M2L_BF16X3, 6, {}),
+                ("f32_order6", sph.M2L_F32, 6, {})]
+    out = {}
+    for name, prec, order, env in variants:
+        c = make_ctx(sph, dev, stream, p, q, em, prec, order, env=env)
+        o = torch.empty(p.ncell, dtype=torch.float32, device=dev)
+        sph.eval_sph(c, o)
+        _, st = sph.eval_sph(c, o, stats=True)
+        got = o.cpu().numpy()[samp].astype(np.float64)
+        e = errors_on_sample(got, ref, samp, ball, w, p)
+        e["ms"] = st.ms_total
+        e["fused"] = int(st.l2lp_fused)
+        out[name] = e
+        c.close()
+    return out
+
+
+def step_times(sph, torch, ctx, out, stream, flush, steps, warmup):
+    """Device time of each step (CUDA events on the library's stream, L2 flushed before each)."""
+    for _ in range(max(3, warmup)):
+        sph.eval_sph(ctx, out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sph.eval_sph(ctx, out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def phase_stats(sph, ctx, out, flush, n):
+    res = []
+    for k in range(n):
+        flush.fill_(float(k))
+        _, st = sph.eval_sph(ctx, out, stats=True)
+        res.append(st.as_dict())
+    return res
+
+
+def run_full128(sph, torch, dev, stream, args, peaks, pipes, flush):
+    """FMM vs direct sum without adaptivity: the 128^3 streamer in a 1 cm cube at 760 Torr with
+    every cell a source and a target (2.1 M points, 4.4e12 pairs), leaf size 64, FP32 and BF16 x3
+    M2L.  Accuracy over EVERY target against the FP64 FFT convolution of the same discrete sum
+    (timed on the host cores), itself checked against the FP64 direct oracle on sampled targets."""
+    import oracle
+    p = si.streamer_full(128)
+    q = torch.from_numpy(p.q).to(dev)
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    Jall = np.arange(p.ncell, dtype=np.int32)
+    t0 = time.perf_counter()
+    fft = oracle.fft_convolution(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, Jall)
+    fft_s = time.perf_counter() - t0
+    chk = np.sort(np.random.default_rng(23).choice(p.ncell, 256, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    dref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, Jall, chk)
+    direct_s = time.perf_counter() - t0
+    res = {"workload": "streamer 128^3 in 1 cm, 760 Torr, every cell a source and a target (no adaptivity), "
+                       "leaf 64, Chebyshev order %d" % args.order,
+           "n_points": p.ncell, "pairs": p.ncell ** 2,
+           "fft_oracle": {"seconds": fft_s, "cores": oracle.num_threads(),
+                          "rel_l2_vs_direct_oracle_256_targets": oracle.rel_l2(fft[chk], dref),
+                          "direct_oracle_targets_per_s": chk.size / direct_s}}
+    for name, prec, m2l in (("bf16x3", sph.M2L_BF16X3, "bf16x3"), ("f32", sph.M2L_F32, "f32")):
+        ctx = make_ctx(sph, dev, stream, p, q, None, prec, args.order, leaf=64)
+        out = torch.empty(p.ncell, dtype=torch.float32, device=dev)
+        ms = step_times(sph, torch, ctx, out, stream, flush, max(5, args.steps // 2), 3)
+        st = phase_stats(sph, ctx, out, flush, 3)
+        S = out.cpu().numpy().astype(np.float64)
+        tree = sph.get_tree(ctx)
+        sub_args = argparse.Namespace(order=args.order, m2l=m2l)
+        roof = rooflines(tree, st, sub_args, p.ncell, p.ncell, p.ncell, peaks, pipes, traffic_ok=False)
+        med = statistics.median(ms)
+        res[name] = {"ms_per_step": med, "targets_per_s": p.ncell / (med * 1e-3),
+                     "rel_l2_all_targets_vs_fft": oracle.rel_l2(S, fft),
+                     "max_rel_all_targets_vs_fft": oracle.max_rel(S, fft, 1e-3),
+                     "phases_ms": {k: statistics.median(x[k] for x in st)
+                                   for k in ("ms_select", "ms_tree", "ms_upward", "ms_m2l", "ms_l2l", "ms_l2p",
+                                             "ms_l2lp", "ms_near", "ms_total")},
+                     "counts": {k: st[-1][k] for k in ("n_boxes", "n_u", "n_v", "n_w", "n_x", "max_level")},
+                     "rooflines": {k: roof[k] for k in ("m2l", "near", "l2lp") if k in roof}}
+        if name == "bf16x3" and not args.no_direct:
+            d = sph.eval_direct(ctx, fp64=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d = sph.eval_direct(ctx, fp64=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dms = e0.elapsed_time(e1)
+            dd = d.cpu().numpy().astype(np.float64)
+            res["direct_fp32"] = {"ms": dms, "targets_per_s": p.ncell / (dms * 1e-3),
+                                  "pairs_per_s": float(p.ncell) ** 2 / (dms * 1e-3),
+                                  "rel_l2_vs_fft": oracle.rel_l2(dd, fft),
+                                  "fmm_speedup": dms / med}
+        ctx.close()
+    return res
+
+
+def run_pressures(sph, torch, dev, stream, args, flush, pressures=(76.0, 380.0)):
+    """The 256^3 adaptive workload at the other pressures of its configuration (Section 4.2):
+    step time and the gate on a stratified oracle sample (ball + 20000 uniform targets)."""
+    import oracle
+    rows = []
+    for pt in pressures:
+        p = si.streamer_adaptive(n=args.n, p_torr=pt)
+        q = torch.from_numpy(p.q).to(dev)
+        em = torch.from_numpy(p.emag).to(dev)
+        prec = sph.M2L_BF16X3 if args.m2l == "bf16x3" else sph.M2L_F32
+        ctx = make_ctx(sph, dev, stream, p, q, em, prec, args.order)
+        out = torch.empty(p.ncell, dtype=torch.float32, device=dev)
+        ms = step_times(sph, torch, ctx, out, stream, flush, max(5, args.steps // 2), 3)
+        _, st = sph.eval_sph(ctx, out, stats=True)
+        J, T = sph.get_selection(ctx)
+        samp, ball, w = si.stratified_targets(p, T, si.streamer_head(), 5 * SIGMA_HEAD, 20000, seed=19)
+        a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+        ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+        acc = errors_on_sample(out.cpu().numpy()[samp].astype(np.float64), ref, samp, ball, w, p)
+        med = statistics.median(ms)
+        rows.append({"pressure_torr": pt, "ms_per_step": med, "targets_per_s": int(st.n_targets) / (med * 1e-3),
+                     "n_sources": int(st.n_sources), "n_targets": int(st.n_targets), "accuracy": acc})
+        ctx.close()
+    return rows
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -524,13 +763,9 @@ def main():
     q = torch.from_numpy(p.q).to(dev)
     em = torch.from_numpy(p.emag).to(dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = sph.Context(local, stream)
-    sph.set_grid(ctx, p.nx, p.ny, p.nz, p.h, p.pO2_torr, p.chi_min, p.chi_max)
-    sph.set_sources(ctx, q, p.source_scale)
-    sph.set_targets(ctx, emag=em)
+    pipes = pipe_peaks(sph, dev, stream)
     prec = sph.M2L_BF16X3 if args.m2l == "bf16x3" else sph.M2L_F32
-    sph.set_criteria(ctx, p.i_frac, p.e_frac, p.e_applied, 1, p.leaf_size, prec)
-    sph.set_far_field(ctx, sph.FAR_CHEBYSHEV, args.order)
+    ctx = make_ctx(sph, dev, stream, p, q, em, prec, args.order)
     out = torch.empty(p.ncell, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -541,7 +776,6 @@ def main():
     nt = int(st0.n_targets)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    step_stats = []
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -557,12 +791,9 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # phase breakdown (library CUDA-event timers) from separate steps: the timers add event
     # records and a final synchronisation, which the timed steps above do without
-    for k in range(max(3, min(args.steps, 5))):
-        flush.fill_(float(k))
-        _, st = sph.eval_sph(ctx, out, stats=True)
-        step_stats.append(st.as_dict())
+    step_stats = phase_stats(sph, ctx, out, flush, max(3, min(args.steps, 5)))
     torch.cuda.synchronize()
-    ms, value = whole_job_rate(sum(step_ms) / len(step_ms), nt, world, dist, dev)
+    ms, value = whole_job_rate(statistics.median(step_ms), nt, world, dist, dev)
 
     # e2e through the host-buffer entry point, inputs and output in pinned host memory
     qh = torch.from_numpy(p.q).pin_memory().numpy()
@@ -570,23 +801,27 @@ def main():
     sh = torch.empty(p.ncell, dtype=torch.float32).pin_memory().numpy()
     sph.eval_sph_host(ctx, qh, eh, out=sh)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     ne2e = max(3, min(args.steps, 5))
+    e2e_t = []
     for _ in range(ne2e):
+        t0 = time.perf_counter()
         sph.eval_sph_host(ctx, qh, eh, out=sh)
-    e2e_ms, e2e_value = whole_job_rate(1e3 * (time.perf_counter() - t0) / ne2e, nt, world, dist, dev)
-    # restore device inputs
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms, e2e_value = whole_job_rate(1e3 * statistics.median(e2e_t), nt, world, dist, dev)
+    # restore device inputs, and the device result of the last evaluation
     sph.set_sources(ctx, q, p.source_scale)
     sph.set_targets(ctx, emag=em)
+    sph.eval_sph(ctx, out)
+    torch.cuda.synchronize()
 
-    # rooflines of the kernels, from the library's CUDA-event phase timers (averages over the timed steps)
+    # rooflines of the kernels, from the library's CUDA-event phase timers (medians)
     tree = sph.get_tree(ctx)
     clocks = clk.summary()
-    f_mhz = clocks["sm_mhz"] or 1920.0
     peaks = measured_peaks()
-    roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, f_mhz, peaks,
-                     workload_is_headline=(args.n == 256 and args.p == 760.0 and args.order == 5))
-    dominant = max(roof, key=lambda k: roof[k]["ms_per_launch"])
+    headline = args.n == 256 and args.p == 760.0 and args.order == 5
+    roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, peaks, pipes,
+                     traffic_ok=headline)
+    dominant = dominant_kernel(roof)
 
     # FP32 direct sum on the same GPU over the same selected sets
     direct = None
@@ -602,16 +837,27 @@ def main():
         direct = {"targets_per_s": nt / (dms * 1e-3), "ms": dms, "pairs": int(st0.n_sources) * nt,
                   "fmm_speedup": (nt / (ms * 1e-3)) / (nt / (dms * 1e-3))}
 
-    # accuracy on sampled targets against the FP64 oracle
-    import oracle
+    # accuracy against the FP64 oracle on a stratified sample (every target within 5 sigma of the
+    # head + seeded uniform targets), the same run timed as the CPU baseline
     J, T = sph.get_selection(ctx)
-    rng = np.random.default_rng(1)
-    samp = np.sort(rng.choice(T, size=min(T.size, 400), replace=False))
-    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
-    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
-    S = out.cpu().numpy().astype(np.float64)[samp]
-    acc = {"rel_l2_sampled": oracle.rel_l2(S, ref), "max_rel_sampled": oracle.max_rel(S, ref, 1e-3),
-           "n_sampled_targets": int(samp.size)}
+    S = out.cpu().numpy()
+    acc, ref, samp, ball, w, cpu_t = accuracy_block(p, J, T, S, args.acc_uniform)
+    if not args.no_decomp:
+        acc["decomposition"] = error_decomposition(sph, torch, dev, stream, p, q, em, samp, ball, w, ref, args)
+    fft256 = None
+    if args.fft256:
+        import oracle
+        a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+        t0 = time.perf_counter()
+        full = oracle.fft_convolution(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J)
+        fs = time.perf_counter() - t0
+        fft256 = {"seconds": fs, "cores": oracle.num_threads(),
+                  "rel_l2_all_targets": oracle.rel_l2(S[T].astype(np.float64), full[T]),
+                  "max_rel_all_targets": oracle.max_rel(S[T].astype(np.float64), full[T], 1e-3),
+                  "fft_vs_direct_oracle_on_sample": oracle.rel_l2(full[samp], ref)}
+
+    full128 = None if args.no_full128 else run_full128(sph, torch, dev, stream, args, peaks, pipes, flush)
+    pressures = None if args.no_pressures else run_pressures(sph, torch, dev, stream, args, flush)
 
     batch = None
     if not args.no_batch:
@@ -625,10 +871,14 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n1, dt, cores = oracle_sample(p, J, T, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "targets/s", "cores": cores, "kind": "oracle",
-               "sample": "%d random targets of %d (FP64 direct sum over all %d sources) in %.1f s"
-                         % (n1, T.size, J.size, dt)}
+        cpu = {"value": cpu_t["value"], "unit": "targets/s", "cores": cpu_t["cores"], "kind": "oracle",
+               "sample": "%d targets of %d -- every target within 5 sigma of the head (%d) + %d seeded uniform "
+                         "others -- FP64 direct sum over all %d sources in %.1f s; the same run gives the "
+                         "accuracy figures" % (cpu_t["n"], T.size, acc["n_ball"], acc["n_uniform"], J.size,
+                                               cpu_t["seconds"]),
+               "single_thread": {"value": cpu_t["single_thread_value"], "cores": 1,
+                                 "sample": "%d of those targets in %.1f s" % (cpu_t["single_thread_n"],
+                                                                             cpu_t["single_thread_s"])}}
 
     if rank == 0:
         last = step_stats[-1]
@@ -636,17 +886,21 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.m2l == "f32" else "f32+bf16x3",
                 "data": "synthetic", "config": workload_cfg(p, args),
+                "step_ms_stats": {"median": statistics.median(step_ms), "mean": statistics.mean(step_ms),
+                                  "min": min(step_ms), "max": max(step_ms)},
                 "e2e": {"value": e2e_value, "unit": "targets/s",
                         "h2d_bytes_per_step": int(qh.nbytes + eh.nbytes), "d2h_bytes_per_step": int(sh.nbytes)},
                 "roofline": dict(roof[dominant], phase=dominant),
-                "rooflines": roof,
+                "rooflines": roof, "pipe_peaks": pipes,
                 "clocks": clocks, "gpu_launches": int(step_stats[-1]["n_launches"]) * args.steps,
-                "phases_ms": {k: statistics.mean(x[k] for x in step_stats)
+                "phases_ms": {k: statistics.median(x[k] for x in step_stats)
                               for k in ("ms_select", "ms_tree", "ms_upward", "ms_vpairs", "ms_m2l", "ms_l2l",
                                         "ms_l2p", "ms_l2lp", "ms_near", "ms_total")},
                 "counts": {k: last[k] for k in ("n_sources", "n_targets", "n_boxes", "n_u", "n_v", "n_w", "n_x",
                                                 "max_level")},
-                "direct_fp32": direct, "accuracy": acc, "batch": batch, "surrogate": surrogate, "sweep": sweep, "cpu_baseline": cpu}
+                "direct_fp32": direct, "accuracy": acc, "fft256": fft256, "full128": full128,
+                "pressures": pressures, "batch": batch, "surrogate": surrogate, "sweep": sweep,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

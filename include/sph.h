@@ -234,8 +234,11 @@ int sph_get_tree(sph_ctx *ctx, sph_tree_view *tree);
  *   set_targets / set_criteria (at most one of emag_dev, mask_dev non-NULL);
  *   outputs (device, each with room for nx*ny*nz entries): src_key_dev, src_pc_dev
  *   (packed i | j<<10 | k<<20), src_q_dev, trg_key_dev, trg_pc_dev, in Morton order;
- *   counts_dev: int32[2] receives (number of sources, number of targets).
- * The work is queued on cuda_stream; results are valid once it completes.  All calls
+ *   counts_dev: int32[3] receives (number of sources, number of targets, failure flag).
+ * The work is queued on cuda_stream; results are valid once it completes and only if
+ * counts_dev[2] is 0.  A non-zero counts_dev[2] means that a block of the selection gave up
+ * waiting for its predecessors' counts (the condition eval_sph reports as SPH_ETIMEOUT):
+ * the counts are then -1 or wrong and the outputs must not be used.  All calls
  * share the library's scratch array: calls that overlap on the GPU race and must be
  * serialised by the caller.  The first call for a device looks up the array's device
  * address; make it before any stream capture.  Never calls cudaMalloc or cudaFree. */
@@ -253,6 +256,15 @@ int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny, int nz, co
  * tile gave up waiting for its predecessors (the results are then not valid). */
 int sph_scan_i32(int device, void *cuda_stream, int64_t n, const int32_t *in_dev, int32_t *out_dev,
                  int32_t *total_dev);
+
+/* Measured throughput of the pipes that evaluate the kernel G (the paper has no counterpart:
+ * these are the denominators of the library's near-field and direct-sum rooflines).  Runs
+ * three short kernels on cuda_stream (FP32 fused multiply-add, MUFU ex2, MUFU rsqrt: eight
+ * independent chains per thread, 8 CTAs of 256 threads per SM), times each with CUDA events
+ * (best of three after one untimed launch) and synchronises the stream.  out_host: double[4]
+ * receives FP32 flop/s (one FMA = 2 flop), ex2 results/s, rsqrt results/s and the number of
+ * SMs.  The figures hold at the SM clock of the moment; allocates nothing. */
+int sph_measure_pipe_peaks(int device, void *cuda_stream, double *out_host);
 
 /* Library version string. */
 const char *sph_version(void);

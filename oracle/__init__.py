@@ -79,6 +79,8 @@ def _load():
             lib.oracle_sph_longdouble.restype = I
             lib.oracle_sph_longdouble.argtypes = [I, I, I, D, D, D, P, D, P, I64, P, I64, I, D, P]
             lib.oracle_num_threads.restype = I
+            lib.oracle_set_num_threads.restype = None
+            lib.oracle_set_num_threads.argtypes = [I]
             _lib = lib
     return _lib
 
@@ -110,6 +112,13 @@ def self_integral(h, alpha, beta):
 
 def num_threads():
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loops from now on (returns the previous count)."""
+    prev = num_threads()
+    _load().oracle_set_num_threads(int(n))
+    return prev
 
 
 def select(q, emag=None, mask=None, i_frac=0.0, e_frac=0.0, e_applied=0.0):
@@ -175,6 +184,17 @@ def rel_l2(num, ref):
     ref = np.asarray(ref, np.float64)
     d = np.linalg.norm(ref)
     return float(np.linalg.norm(num - ref) / d) if d > 0 else float(np.linalg.norm(num))
+
+
+def rel_l2_weighted(num, ref, weight):
+    """E_V / 100 of a whole set estimated from a weighted sample of it: each sampled entry
+    stands for ``weight`` entries, sqrt(sum w (num - ref)^2 / sum w ref^2)."""
+    num = np.asarray(num, np.float64)
+    ref = np.asarray(ref, np.float64)
+    w = np.broadcast_to(np.asarray(weight, np.float64), ref.shape)
+    d = float(np.sum(w * ref * ref))
+    e = float(np.sum(w * (num - ref) ** 2))
+    return float(np.sqrt(e / d)) if d > 0 else float(np.sqrt(e))
 
 
 def max_rel(num, ref, floor_frac=1e-3):

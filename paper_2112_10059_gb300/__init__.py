@@ -78,7 +78,8 @@ class Problem(ctypes.Structure):
 
 EXPORTS = ["sph_create", "sph_destroy", "sph_last_error", "set_grid", "set_sources", "set_targets",
            "set_criteria", "sph_set_far_field", "sph_set_near_field", "sph_set_skip_ratio", "eval_sph", "eval_sph_batch", "eval_sph_host", "eval_direct",
-           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_scan_i32", "sph_version",
+           "sph_get_selection", "sph_get_tree", "sph_select_noalloc", "sph_scan_i32", "sph_measure_pipe_peaks",
+           "sph_version",
            # learned surrogate (include/sph_nn.h)
            "sph_nn_create", "sph_nn_destroy", "sph_nn_last_error", "sph_nn_num_params", "sph_nn_init",
            "sph_nn_set_params", "sph_nn_get_params", "sph_nn_get_grads", "sph_nn_forward", "sph_nn_backward",
@@ -123,6 +124,7 @@ def load(path: str | None = None):
         lib.sph_select_noalloc.argtypes = [I, V, I, I, I, V, V, V, D, D, D, V, V, V, V, V, V]
         lib.sph_select_noalloc.restype = I
         lib.sph_scan_i32.argtypes = [I, V, I64, V, V, V]
+        lib.sph_measure_pipe_peaks.argtypes = [I, V, ctypes.POINTER(ctypes.c_double)]
         lib.sph_scan_i32.restype = I
         PD, PF = ctypes.POINTER(ctypes.c_double), ctypes.c_float
         lib.sph_nn_create.argtypes = [ctypes.POINTER(V), I, V, I, I]
@@ -266,7 +268,7 @@ def set_targets(ctx: Context, emag=None, mask=None):
 
 
 def set_criteria(ctx: Context, i_frac=0.0, e_frac=0.0, e_applied=0.0, self_mode=1, leaf_size=64,
-                 m2l_precision=M2L_F32):
+                 m2l_precision=M2L_BF16X3):
     ctx._ck(ctx.lib.set_criteria(ctx.h, float(i_frac), float(e_frac), float(e_applied), int(self_mode),
                                  int(leaf_size), int(m2l_precision)))
 
@@ -434,7 +436,19 @@ def scan_i32(x):
     return out, int(total.item())
 
 
-def solve(problem, ctx: Context | None = None, m2l_precision=M2L_F32, leaf_size=None, stats=False,
+def pipe_peaks(device=0, stream=None):
+    """Measured FP32 FMA and MUFU throughput of the device: dict with ffma_flops (flop/s),
+    ex2_per_s, rsqrt_per_s (results/s) and n_sm.  Synchronises the stream."""
+    lib = load()
+    out = (ctypes.c_double * 4)()
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = lib.sph_measure_pipe_peaks(int(device), sp, out)
+    if rc != 0:
+        raise SphError(rc, "sph_measure_pipe_peaks failed")
+    return {"ffma_flops": out[0], "ex2_per_s": out[1], "rsqrt_per_s": out[2], "n_sm": int(out[3])}
+
+
+def solve(problem, ctx: Context | None = None, m2l_precision=M2L_BF16X3, leaf_size=None, stats=False,
           mask=None):
     """Convenience: evaluate S_ph for a ``sph_inputs.Problem`` (inputs copied to the GPU)."""
     import torch

@@ -464,7 +464,10 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     }
     if (tid == 0) {
         if (brick > 0) {
-            if (failed) atomicOr(totals + 2, 1);
+            if (failed) {
+                atomicOr(totals + 2, 1);
+                __threadfence();                   // the flag is visible before the state it taints
+            }
             atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
         }
         if (brick == nbr - 1) {

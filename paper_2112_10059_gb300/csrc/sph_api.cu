@@ -53,7 +53,7 @@ struct sph_ctx {
     const float *emag = nullptr;
     const uint8_t *mask = nullptr;
     double i_frac = 0, e_frac = 0, e_app = 0;
-    int self_mode = 1, leaf_size = 64, m2l_prec = SPH_M2L_F32;
+    int self_mode = 1, leaf_size = 64, m2l_prec = SPH_M2L_BF16X3;
     int leaf_eff = 64;                // leaf size of the current tree (leaf_size, or the autotuner's choice)
     std::map<std::string, int> tune_cache;
     sph_ctx *tune_owner = nullptr;    // batch slots share their parent's autotuner cache

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int NOALLOC_MAX_EDGE = 512;
 constexpr int NOALLOC_MAX_BRICKS = 32768;                 // (512 / 16)^3
-constexpr int NOALLOC_HEAD = 64;                          // maxima (2), totals (2), padding
+constexpr int NOALLOC_HEAD = 64;                          // maxima (2), totals (2) + flag, padding
 constexpr size_t NOALLOC_INTS = NOALLOC_HEAD + 4 * (size_t)NOALLOC_MAX_BRICKS;   // 512.25 KiB
 
 static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_INTS];
@@ -103,7 +103,9 @@ extern "C" int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny,
     A.trg_key = trg_key_dev; A.trg_pc = trg_pc_dev;
     int rc = SPH_OK;
     if (sph::select_launch(A, st) != 0) rc = SPH_ECUDA;
-    if (rc == SPH_OK && cudaMemcpyAsync(counts_dev, A.totals, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+    // (sources, targets, gave-up flag): copied after the selection kernel has completed, so the
+    // flag of every brick that gave up waiting is in it
+    if (rc == SPH_OK && cudaMemcpyAsync(counts_dev, A.totals, 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
                             cudaSuccess)
         rc = SPH_ECUDA;
     if (rc != SPH_OK) cudaGetLastError();

@@ -315,3 +315,40 @@ def gaussian_box(nx, ny, nz, sigma_cells=8.0, h=1.25e-3, pO2_torr=150.0, center=
 def random_mask(n_cells: int, frac: float, seed: int) -> np.ndarray:
     """uint8 mask with each cell set with probability ``frac`` (SplitMix64 stream)."""
     return (uniform01(seed, n_cells) < frac).astype(np.uint8)
+
+
+def stratified_targets(p: Problem, T: np.ndarray, center, radius: float, n_uniform: int, seed: int = 5):
+    """A seeded target sample for parity checks at full size: every target whose cell centre
+    lies within ``radius`` (cm) of ``center`` (the ball of Eq. relativefun's local error around
+    the streamer head), plus ``n_uniform`` distinct targets drawn uniformly from the rest.
+
+    Returns (sample, in_ball, weight): the sample as ascending int32 cell indices, a bool array
+    marking its ball members, and the weight of one uniform member when the sample stands for
+    all of T (|T \\ ball| / n_uniform; ball members weigh 1).
+    """
+    T = np.asarray(T, np.int64)
+    i = T % p.nx
+    j = (T // p.nx) % p.ny
+    k = T // (p.nx * p.ny)
+    o = p.origin
+    d2 = ((o[0] + p.h * (i + 0.5) - center[0]) ** 2 + (o[1] + p.h * (j + 0.5) - center[1]) ** 2
+          + (o[2] + p.h * (k + 0.5) - center[2]) ** 2)
+    ball = d2 <= radius * radius
+    rest = T[~ball]
+    m = min(int(n_uniform), rest.size)
+    if 0 < m < rest.size:
+        u = uniform01(seed, rest.size)
+        pick = rest[np.sort(np.argpartition(u, m - 1)[:m])]
+    else:
+        pick = rest[:m]
+    samp = np.concatenate([T[ball], pick])
+    order = np.argsort(samp, kind="stable")
+    in_ball = np.concatenate([np.ones(int(ball.sum()), bool), np.zeros(m, bool)])[order]
+    w = rest.size / m if m > 0 else 0.0
+    return samp[order].astype(np.int32), in_ball, w
+
+
+def streamer_head(box=1.0, chan_len=0.5):
+    """Head centre of :func:`streamer` with its default placement."""
+    return (box / 2, box / 2, box / 2 - chan_len / 2)
+

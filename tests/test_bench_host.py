@@ -25,6 +25,7 @@ TREE = {
     "W": np.zeros((0, 2), np.int64),
 }
 PEAKS = {"bf16_tflops": 1000.0, "hbm_gbs": 5000.0, "source": "test"}
+PIPES = {"ffma_flops": 60e12, "ex2_per_s": 4e12, "rsqrt_per_s": 8e12, "n_sm": 152, "source": "test"}
 ARGS = types.SimpleNamespace(order=5, m2l="bf16x3")
 
 
@@ -32,33 +33,36 @@ def _stats(fused):
     base = {"ms_m2l": 0.01, "ms_l2l": 0.004, "ms_l2p": 0.006, "ms_l2lp": 0.004 if fused else 0.0,
             "ms_near": 0.003, "ms_select": 0.002, "l2lp_fused": 1 if fused else 0}
     other = dict(base, ms_select=0.004, ms_near=0.005)
-    return [base, other]                  # phase times are averaged over the steps
+    slow = dict(base, ms_select=0.009, ms_near=0.009)
+    return [base, other, slow]            # phase times: medians over the steps
 
 
 def test_fused_deepest_level():
-    r = bench.rooflines(TREE, _stats(True), ARGS, nt=8, ns=4, ncell=1000, f_mhz=2000.0, peaks=PEAKS,
-                        workload_is_headline=False)
+    r = bench.rooflines(TREE, _stats(True), ARGS, nt=8, ns=4, ncell=1000, peaks=PEAKS, pipes=PIPES,
+                        traffic_ok=False)
     # fused level: parent box 0 and leaves 1, 2 read 128 x 4 B each, 8 targets written
     assert r["l2lp"]["work_per_launch"] == 3 * 512 + 8 * 4
     assert r["l2lp"]["achieved"] == pytest.approx(1568 / 0.004e-3 / 1e9)
-    assert r["l2lp"]["traffic"] is None   # the ncu traffic belongs to the headline workload only
-    # nothing left for the separate L2L (both level-3 boxes are fused) and L2P
-    assert r["l2l"]["work_per_launch"] == 0
-    assert r["l2p"]["work_per_launch"] == 0
-    assert r["l2p"]["ms_per_launch"] == pytest.approx(0.006 - 0.004)
-    # near field: 4 x 2 source cells for each of the 4 (leaf, leaf) pairs
+    assert r["l2lp"]["traffic"] is None   # ncu traffic only where it was measured on this workload
+    # nothing left for the separate L2L (both level-3 boxes are fused) or L2P: no entries
+    assert "l2l" not in r and "l2p" not in r
+    # near field: 4 x 2 source cells for each of the 4 (leaf, leaf) pairs, median time 0.005 ms;
+    # MUFU bound: 1 / (2 / ex2 + 1 / rsqrt) = 1 / (0.5e-12 + 0.125e-12) = 1.6e12 evaluations/s
     assert r["near"]["work_per_launch"] == 32
-    assert r["near"]["achieved"] == pytest.approx(32 / 0.004e-3)
-    assert r["near"]["peak"] == pytest.approx(152 * 16 * 2000e6 / 3)
-    # selection: q and |E| read twice (16 B per cell), 8 B per target, 12 B per source, 1 B mask
-    assert r["select"]["work_per_launch"] == 16 * 1000 + 8 * 8 + 12 * 4 + 1000
-    assert r["select"]["frac"] == pytest.approx(17112 / 0.003e-3 / 1e9 / 5000.0)
+    assert r["near"]["achieved"] == pytest.approx(32 / 0.005e-3)
+    assert r["near"]["peak"] == pytest.approx(1.6e12)
+    # selection: q and |E| read twice (16 B per cell), 4 B per selected index (8 targets, 4 sources)
+    assert r["select"]["work_per_launch"] == 16 * 1000 + 4 * (8 + 4)
+    assert r["select"]["frac"] == pytest.approx(16048 / 0.004e-3 / 1e9 / 5000.0)
     assert r["m2l"]["work_per_launch"] == 0
+    # the dominant single kernel: m2l (0.01 ms) over l2lp (0.004) and near (0.005)
+    assert bench.dominant_kernel(r) == "m2l"
+    assert not r["select"]["single_kernel"]
 
 
 def test_separate_deepest_level():
-    r = bench.rooflines(TREE, _stats(False), ARGS, nt=8, ns=4, ncell=1000, f_mhz=2000.0, peaks=PEAKS,
-                        workload_is_headline=True)
+    r = bench.rooflines(TREE, _stats(False), ARGS, nt=8, ns=4, ncell=1000, peaks=PEAKS, pipes=PIPES,
+                        traffic_ok=True)
     assert "l2lp" not in r
     # both leaves get an L2L from box 0: 2 n^2 flops each
     assert r["l2l"]["work_per_launch"] == 2 * 2 * 125 ** 2
@@ -66,7 +70,10 @@ def test_separate_deepest_level():
     assert r["l2l"]["peak"] == 1000.0
     # both leaves' expansions read, 8 targets written
     assert r["l2p"]["work_per_launch"] == 2 * 512 + 8 * 4
-    assert r["select"]["traffic"] == bench.NCU_TRAFFIC["select"]
+    assert r["m2l"]["peak"] == 1000.0 and r["m2l"]["bound"] == "tensor"
+    r32 = bench.rooflines(TREE, _stats(False), types.SimpleNamespace(order=5, m2l="f32"), nt=8, ns=4,
+                          ncell=1000, peaks=PEAKS, pipes=PIPES)
+    assert r32["m2l"]["peak"] == pytest.approx(60.0) and r32["m2l"]["bound"] == "alu"
 
 
 def test_clock_summary_from_nvidia_smi_rows(tmp_path):

@@ -199,10 +199,12 @@ def test_direct_fp64_and_fp32_c0(sph, ctx):
     assert oracle.max_rel(d32[T], ref, 0.0) < 1e-3
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("pi", range(3))
-def test_fmm_small(sph, ctx, pi):
+def test_fmm_small(sph, ctx, pi, prec):
+    """Both M2L arithmetics (0: FP32 SIMT, 1: tensor cores, BF16 hi/lo x3) within the gate."""
     p = _problems()[pi]
-    _, out, st = sph.solve(p, ctx, stats=True)
+    _, out, st = sph.solve(p, ctx, m2l_precision=prec, stats=True)
     ref, J, T = oracle.sph_problem(p)
     _check_fmm(out.cpu().numpy(), ref, T, p.name)
 
@@ -589,6 +591,33 @@ def test_strategy3_skips_within_its_bound(sph, r_s):
         assert res[r_s][1] > 0
     with pytest.raises(sph.SphError):
         sph.set_skip_ratio(sph.Context(0), -1.0)
+
+
+@pytest.mark.parametrize("r_s", [1e-4, 1e-2])
+def test_strategy3_against_the_oracle(sph, r_s):
+    """Strategy 3 (Section 3; r_s = 1e-4 as in Section 5) against the FP64 sum over every
+    selected source: skipping moves each target by less than n_W r_s of its value (n_W the
+    largest W list of a leaf), so the skipped result stays within the FMM gate widened by
+    that much, in L2 and pointwise above the floor."""
+    p = _problems()[1]
+    c = sph.Context(0)
+    sph.set_skip_ratio(c, r_s)
+    _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+    S = out.cpu().numpy().astype(np.float64)
+    tree = sph.get_tree(c)
+    c.close()
+    ref, J, T = oracle.sph_problem(p)
+    nmax = int(np.bincount(tree["W"][:, 0]).max())
+    slack = nmax * r_s * (1.0 + MAX_REL)
+    e2 = oracle.rel_l2(S[T], ref)
+    em = oracle.max_rel(S[T], ref, 1e-3)
+    assert e2 <= REL_L2 + slack, (e2, nmax, st.n_w_skipped)
+    assert em <= MAX_REL + slack, (em, nmax, st.n_w_skipped)
+    others = np.ones(S.size, bool)
+    others[T] = False
+    assert np.all(S[others] == 0.0)
+    if r_s >= 1e-2:
+        assert st.n_w_skipped > 0
 
 
 _LAUNCH_ORDER_CHILD = r'''

@@ -59,3 +59,28 @@ def test_streamer_inputs_are_deterministic():
     b = si.streamer(n=24, box=0.5, chan_len=0.25, i_frac=1e-3, e_frac=0.2, targets_all=False, seed=9, name="b")
     assert np.array_equal(a.q, b.q) and np.array_equal(a.emag, b.emag)
     assert a.q.dtype == np.float32 and a.q.size == 24 ** 3
+
+
+def test_stratified_targets_ball_and_uniform_part():
+    """The parity sample: exactly the targets within the radius (brute force over every cell
+    centre), plus the requested number of distinct others, ascending, deterministic."""
+    p = si.gaussian_box(20, 16, 12, sigma_cells=3.0, h=0.01)
+    T = np.flatnonzero(si.uniform01(9, p.ncell) < 0.6).astype(np.int32)
+    c, r = (0.1, 0.08, 0.05), 0.035
+    s, b, w = si.stratified_targets(p, T, c, r, 300, seed=4)
+    X, Y, Z = p.centres()
+    d = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2).ravel()
+    ball = T[d[T] <= r]
+    assert np.array_equal(s[b], ball)
+    others = s[~b]
+    assert others.size == 300 and np.unique(others).size == 300
+    assert np.all(np.isin(others, T)) and not np.any(np.isin(others, ball))
+    assert np.all(np.diff(s) > 0)
+    assert w == (T.size - ball.size) / 300
+    s2, b2, _ = si.stratified_targets(p, T, c, r, 300, seed=4)
+    assert np.array_equal(s, s2) and np.array_equal(b, b2)
+    s3, _, _ = si.stratified_targets(p, T, c, r, 300, seed=5)
+    assert not np.array_equal(s, s3)
+    # asking for more than there is gives every target
+    s4, b4, w4 = si.stratified_targets(p, T, c, r, 10 ** 6)
+    assert np.array_equal(s4, T) and w4 == 1.0

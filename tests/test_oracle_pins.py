@@ -369,3 +369,17 @@ def test_e_delta_hand_worked():
     assert oracle.e_delta(num, ref, pts, (3.0, 0.0, 0.0), 2.0) == pytest.approx((0.0 + 11.5) / 2, rel=1e-14)
     # an empty ball
     assert oracle.e_delta(num, ref, pts, (10.0, 10.0, 10.0), 1.0) == 0.0
+
+
+def test_rel_l2_weighted_hand_worked():
+    # weights 1 and 4: errors (0.3, 0.4) over references (3, 4) -> sqrt((0.09 + 4*0.16)/(9 + 4*16))
+    ref = np.array([3.0, 4.0])
+    num = np.array([3.3, 4.4])
+    assert oracle.rel_l2_weighted(num, ref, np.array([1.0, 4.0])) == pytest.approx(
+        math.sqrt(0.73 / 73.0), rel=1e-14)
+    # equal weights reduce to the plain measure; a weighted sample of repeats equals the whole set
+    assert oracle.rel_l2_weighted(num, ref, 2.5) == pytest.approx(oracle.rel_l2(num, ref), rel=1e-14)
+    whole_num = np.array([3.3, 4.4, 4.4, 4.4, 4.4])
+    whole_ref = np.array([3.0, 4.0, 4.0, 4.0, 4.0])
+    assert oracle.rel_l2_weighted(num, ref, np.array([1.0, 4.0])) == pytest.approx(
+        oracle.rel_l2(whole_num, whole_ref), rel=1e-14)
