@@ -753,12 +753,19 @@ __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int
                     *reinterpret_cast<float4 *>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
                 }
             } else {
-                for (int j = lane; j < e * e * e; j += 32) {
-                    const int x = j & em, y = (j >> le) & em, z = j >> (2 * le);
-                    const int gx = bx + x, gy = by + y, gz = bz + z;
+                // the mask bytes of this lane's cells (at most 16: e <= 8) first, then the sums and
+                // stores (a byte load placed after a float store would wait for it)
+                uint32_t keep = 0;
+                for (int j = lane, it = 0; j < e * e * e; j += 32, ++it) {
+                    const int gx = bx + (j & em), gy = by + ((j >> le) & em), gz = bz + (j >> (2 * le));
                     if (gx >= F.nx || gy >= F.ny || gz >= F.nz) continue;
                     const int64_t o = (int64_t)gx + (int64_t)F.nx * ((int64_t)gy + (int64_t)F.ny * gz);
-                    if (!full && !F.tmask[o]) continue;
+                    if (full || __ldg(F.tmask + o)) keep |= 1u << it;
+                }
+                for (int j = lane, it = 0; j < e * e * e; j += 32, ++it) {
+                    if (!((keep >> it) & 1u)) continue;
+                    const int x = j & em, y = (j >> le) & em, z = j >> (2 * le);
+                    const int64_t o = (int64_t)(bx + x) + (int64_t)F.nx * ((int64_t)(by + y) + (int64_t)F.ny * (bz + z));
                     float acc = 0.f;
                     for (int c = 0; c < p; ++c) acc = fmaf(t2[(c * e + y) * e + x], Sb[c * e + z], acc);
                     out[o] = acc;

@@ -845,14 +845,21 @@ __global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_beg
                 }
                 continue;
             }
+            // mask bytes first, then the stores (a byte load after a float store would wait for it)
+            bool keep[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int c = t * N + c0 + j;
-                if (c >= rows) break;
                 const int x = bx + c % e, y = by + (c / e) % e, z = bz + c / (e * e);
-                if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
+                const bool inb = c < rows && (full || (x < F.nx && y < F.ny && z < F.nz));
                 const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-                if (full || F.tmask[o]) out[o] = v[j];
+                keep[j] = inb && (full || __ldg(F.tmask + o) != 0);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = t * N + c0 + j;
+                const int x = bx + c % e, y = by + (c / e) % e, z = bz + c / (e * e);
+                if (keep[j]) out[(int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z)] = v[j];
             }
         }
         tc::fence_before_sync();
@@ -896,11 +903,19 @@ __device__ __forceinline__ void lp_store(uint8_t *hi, uint8_t *lo, const float4 
     }
 }
 
+// One persistent CTA per SM: CTA b takes the chunks b, b + gridDim.x, ... of `ppc` parents
+// each (the launch makes every CTA take the same number of chunks), so no SM runs an extra
+// chunk while others idle.  The L2P table E and the TMEM accumulators are set up once per CTA;
+// the composed tables stream through one buffer, the copy of the next one (the next chunk's
+// first one after a chunk's last child) issued as soon as the MMAs that read the current one
+// have completed.  Barrier phases run on across chunks: the k-th wait on bar_t / bar_mma uses
+// parity k & 1.
 __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int parent_begin, int parent_count,
-                                                     int ppc, const uint16_t *__restrict__ img_e,
+                                                     int ppc, int nchunks, const uint16_t *__restrict__ img_e,
                                                      const uint16_t *__restrict__ img_c, float *__restrict__ out,
                                                      int *err) {
     pdl_enter();
+    if ((int)blockIdx.x >= nchunks) return;        // uniform, before any allocation
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *ap_hi = base, *ap_lo = base + LP_A, *ac_hi = base + 2 * LP_A, *ac_lo = base + 3 * LP_A;
@@ -918,28 +933,6 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int np = F.O.npad;
     const size_t img_elems = (size_t)2 * 64 * TCK;          // one image: hi then lo
-    int any = 0;
-    if (tid < TCM) {
-        const int i = blockIdx.x * ppc + tid;
-        const int p = parent_begin + i;
-        int P = -1;
-        if (tid < ppc && i < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
-        spar[tid] = P;
-        for (int c = 0; c < 8; ++c) {
-            int C = -1, full = 0;
-            if (P >= 0) {
-                const int ch = T.box_at[dense_off(level) + ((T.b_key[P] << 3) | (uint32_t)c)];
-                if (ch >= 0 && T.b_leaf[ch] && T.b_te[ch] > T.b_tb[ch]) {
-                    C = ch;
-                    full = T.b_te[ch] - T.b_tb[ch] == 64;
-                }
-            }
-            sch[c * TCM + tid] = C;
-            sfull[c * TCM + tid] = full;
-            any |= C >= 0;
-        }
-    }
-    if (!__syncthreads_or(any)) return;
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(tslot), 512);
         tc::tmem_relinquish();
@@ -966,10 +959,6 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
         t_issued = 1;
     }
     float4 v[LP_V];
-    lp_load(v, spar, F.dchk, np);
-    lp_store(ap_hi, ap_lo, v);
-    lp_load(v, sch, F.dchk, np);
-    lp_store(ac_hi, ac_lo, v);
     const uint32_t idesc = tc::idesc_bf16_f32(TCM, 64);
     const int q = warp & 3, r = q * 32 + lane;              // TMEM lane quadrant, parent row
     const bool vec_ok = (F.nx % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
@@ -984,114 +973,205 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
             demorton3(T.b_key[C], ux, uy, uz);
             bx = (int)ux * 4; by = (int)uy * 4; bz = (int)uz * 4;
         }
+        float w[2][16];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c0 = 32 * (warp >> 2) + 16 * h;
-            float w[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * c + c0), w);
-            if (C < 0) continue;
-            if (full && vec_ok) {   // whole box: one 16-byte store per row of 4 cells
+        for (int h = 0; h < 2; ++h)
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * c + 32 * (warp >> 2) + 16 * h), w[h]);
+        if (C < 0) return;
+        const bool inside = bx + 4 <= F.nx && by + 4 <= F.ny && bz + 4 <= F.nz;
+        if (vec_ok && inside) {
+            // one 16-byte store per row of 4 cells; in a partly selected box the non-target
+            // cells of a row get their zero in the same store (never a partial 32-byte sector,
+            // which the memory system would have to merge), the row's 4 mask bytes read as one
+            // word, every word before the first store
+            uint32_t mw[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) {
-                    const int cell = c0 + j;
+                    const int cell = 32 * (warp >> 2) + 16 * h + j;
                     const int y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
                     const int64_t o = (int64_t)bx + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-                    *reinterpret_cast<float4 *>(out + o) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+                    mw[h][j >> 2] = full ? 0x01010101u : __ldg(reinterpret_cast<const uint32_t *>(F.tmask + o));
                 }
-                continue;
-            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const int cell = 32 * (warp >> 2) + 16 * h + j;
+                    const int y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                    const int64_t o = (int64_t)bx + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+                    const uint32_t m = mw[h][j >> 2];
+                    *reinterpret_cast<float4 *>(out + o) =
+                        make_float4((m & 0xFFu) ? w[h][j] : 0.f, (m & 0xFF00u) ? w[h][j + 1] : 0.f,
+                                    (m & 0xFF0000u) ? w[h][j + 2] : 0.f, (m & 0xFF000000u) ? w[h][j + 3] : 0.f);
+                }
+            return;
+        }
+        // partly selected or overhanging box: every mask byte is fetched before the first
+        // store (a byte load placed after a float store would wait for it)
+        bool keep[2][16];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int cell = c0 + j;
+                const int cell = 32 * (warp >> 2) + 16 * h + j;
                 const int x = bx + (cell & 3), y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
-                if (!full && (x >= F.nx || y >= F.ny || z >= F.nz)) continue;   // box overhangs the grid
+                const bool inb = full || (x < F.nx && y < F.ny && z < F.nz);   // box overhangs the grid
                 const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-                if (full || F.tmask[o]) out[o] = w[j];
+                keep[h][j] = inb && (full || __ldg(F.tmask + o) != 0);
             }
-        }
-    };
-    for (int c = 0; c < 8; ++c) {
-        // (a) operand tiles of child c are in shared memory: MMAs (thread 0)
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0 && *ok_s) {
-            bool ok = e_landed || tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
-            e_landed = ok;
-            ok = ok && tc::mbar_wait_bounded(tc::smem_u32(bar_t), c & 1, WAIT_LIMIT);
-            if (ok) {
-                ++t_landed;
-                tc::fence_after_sync();
-                const uint32_t d = tmem + (uint32_t)(64 * c);
-                const uint32_t aph = tc::smem_u32(ap_hi), apl = tc::smem_u32(ap_lo);
-                const uint32_t ach = tc::smem_u32(ac_hi), acl = tc::smem_u32(ac_lo);
-                const uint32_t th = tc::smem_u32(t_hi), tl = tc::smem_u32(t_lo);
-                const uint32_t eh = tc::smem_u32(e_hi), el = tc::smem_u32(e_lo);
 #pragma unroll
-                for (int ks = 0; ks < TCK / 16; ++ks) {
-                    const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
-                    const uint32_t bo = tc::sw128_offset(0, 16 * ks, 64);
-                    tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(th + bo), idesc, ks > 0);
-                    tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(tl + bo), idesc, 1);
-                    tc::mma_bf16(d, tc::sdesc_sw128(apl + ao), tc::sdesc_sw128(th + bo), idesc, 1);
-                    tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
-                    tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
-                    tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int cell = 32 * (warp >> 2) + 16 * h + j;
+                const int x = bx + (cell & 3), y = by + ((cell >> 2) & 3), z = bz + (cell >> 4);
+                if (keep[h][j]) out[(int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z)] = w[h][j];
+            }
+    };
+    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const bool more = chunk + (int)gridDim.x < nchunks;   // this CTA has another chunk after this one
+        __syncthreads();                                       // previous chunk's epilogue read sch / sfull
+        int any = 0;
+        if (tid < TCM) {
+            const int i = chunk * ppc + tid;
+            const int p = parent_begin + i;
+            int P = -1;
+            if (tid < ppc && i < parent_count && !T.b_leaf[p] && T.b_te[p] > T.b_tb[p]) P = p;
+            spar[tid] = P;
+            for (int c = 0; c < 8; ++c) {
+                int C = -1, full = 0;
+                if (P >= 0) {
+                    const int ch = T.box_at[dense_off(level) + ((T.b_key[P] << 3) | (uint32_t)c)];
+                    if (ch >= 0 && T.b_leaf[ch] && T.b_te[ch] > T.b_tb[ch]) {
+                        C = ch;
+                        full = T.b_te[ch] - T.b_tb[ch] == 64;
+                    }
                 }
-                tc::mma_commit(tc::smem_u32(bar_mma));
-                ++m_issued;
-            } else {
-                atomicOr(err, 4);
-                *ok_s = 0;
+                sch[c * TCM + tid] = C;
+                sfull[c * TCM + tid] = full;
+                any |= C >= 0;
             }
         }
-        // (b) child c+1's rows in flight and child c-1's cells written while the MMAs run
-        if (c + 1 < 8) lp_load(v, sch + (c + 1) * TCM, F.dchk, np);
-        if (c > 0) epilogue(c - 1);
-        // (c) MMAs of child c complete: its accumulator is final (written in the next round),
-        //     the child tile and the table buffer are free; child c+1's table streams in
-        if (tid == 0 && *ok_s) {
-            if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), c & 1, WAIT_LIMIT)) {
-                ++m_done;
-                if (c + 1 < 8) {
-                    tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
-                    const uint16_t *src = img_c + (size_t)(c + 1) * img_elems;
-                    tc::bulk_g2s(tc::smem_u32(t_hi), src, LP_B, tc::smem_u32(bar_t));
-                    tc::bulk_g2s(tc::smem_u32(t_lo), src + LP_B / 2, LP_B, tc::smem_u32(bar_t));
-                    ++t_issued;
+        // a chunk without leaves is skipped; the first composed table stays in flight for the next
+        if (!__syncthreads_or(any)) continue;
+        lp_load(v, spar, F.dchk, np);
+        lp_store(ap_hi, ap_lo, v);
+        lp_load(v, sch, F.dchk, np);
+        lp_store(ac_hi, ac_lo, v);
+        auto round = [&](int c) -> bool {
+            // (a) operand tiles of child c are in shared memory: MMAs (thread 0); the TMEM
+            //     reads of earlier epilogues (the same columns in the previous chunk) are ordered
+            //     before them
+            tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0 && *ok_s) {
+                bool ok = e_landed || tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
+                e_landed = ok;
+                ok = ok && tc::mbar_wait_bounded(tc::smem_u32(bar_t), t_landed & 1, WAIT_LIMIT);
+                if (ok) {
+                    ++t_landed;
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(64 * c);
+                    const uint32_t aph = tc::smem_u32(ap_hi), apl = tc::smem_u32(ap_lo);
+                    const uint32_t ach = tc::smem_u32(ac_hi), acl = tc::smem_u32(ac_lo);
+                    const uint32_t th = tc::smem_u32(t_hi), tl = tc::smem_u32(t_lo);
+                    const uint32_t eh = tc::smem_u32(e_hi), el = tc::smem_u32(e_lo);
+#pragma unroll
+                    for (int ks = 0; ks < TCK / 16; ++ks) {
+                        const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
+                        const uint32_t bo = tc::sw128_offset(0, 16 * ks, 64);
+                        tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(th + bo), idesc, ks > 0);
+                        tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(tl + bo), idesc, 1);
+                        tc::mma_bf16(d, tc::sdesc_sw128(apl + ao), tc::sdesc_sw128(th + bo), idesc, 1);
+                        tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                        tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
+                        tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                    }
+                    tc::mma_commit(tc::smem_u32(bar_mma));
+                    ++m_issued;
+                } else {
+                    atomicOr(err, 4);
+                    *ok_s = 0;
                 }
-            } else {
-                atomicOr(err, 8);
-                *ok_s = 0;
             }
-        }
-        __syncthreads();
+            // (b) child c+1's rows in flight
+            if (c + 1 < 8) lp_load(v, sch + (c + 1) * TCM, F.dchk, np);
+            // (c) MMAs of child c complete: its accumulator is final (written in the next round),
+            //     the child tile and the table buffer are free; the next composed table streams
+            //     in (child c+1's, or after the last child the first one of the next chunk) --
+            //     before thread 0 takes its share of the epilogue, so the copy overlaps it
+            if (tid == 0 && *ok_s) {
+                if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), m_done & 1, WAIT_LIMIT)) {
+                    ++m_done;
+                    if (c + 1 < 8 || more) {
+                        tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
+                        const uint16_t *src = img_c + (size_t)((c + 1) & 7) * img_elems;
+                        tc::bulk_g2s(tc::smem_u32(t_hi), src, LP_B, tc::smem_u32(bar_t));
+                        tc::bulk_g2s(tc::smem_u32(t_lo), src + LP_B / 2, LP_B, tc::smem_u32(bar_t));
+                        ++t_issued;
+                    }
+                } else {
+                    atomicOr(err, 8);
+                    *ok_s = 0;
+                }
+            }
+            // (d) child c-1's cells written while child c's MMAs run and the table streams in
+            if (c > 0) epilogue(c - 1);
+            __syncthreads();
+            if (!*ok_s) return false;
+            tc::fence_after_sync();
+            // (e) child c+1's operand tile
+            if (c + 1 < 8) lp_store(ac_hi, ac_lo, v);
+            return true;
+        };
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c)
+            if (!round(c)) break;
         if (!*ok_s) break;
-        tc::fence_after_sync();
-        // (e) child c+1's operand tile
-        if (c + 1 < 8) lp_store(ac_hi, ac_lo, v);
+        epilogue(7);
     }
-    if (*ok_s) epilogue(7);
     if (tid == 0 && !*ok_s) {
         // let this CTA's own copies and MMAs finish before its memory is released
         if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
         if (t_issued > t_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_issued - 1) & 1, WAIT_LIMIT);
         if (m_issued > m_done) tc::mbar_wait_bounded(tc::smem_u32(bar_mma), (m_issued - 1) & 1, WAIT_LIMIT);
     }
+    if (tid == 0 && *ok_s) {
+        // a table still in flight (the CTA's chunks ended with skipped ones): let it land
+        if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
+        if (t_issued > t_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_issued - 1) & 1, WAIT_LIMIT);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
 }
 
 void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, float *out, int *err,
                        cudaStream_t st) {
     if (parent_count <= 0 || level < 3 || F.O.l2pc_off < 0 || F.O.l2p_off[level] < 0) return;
     tc_init_attributes();
-    // parents per CTA: up to 128 (the MMA's M), fewer where that spreads the work evenly over
-    // two rounds of one CTA per SM
-    const int ppc = std::max(1, std::min(TCM, (parent_count + 2 * 152 - 1) / (2 * 152)));
-    launch_pdl(k_l2lp_tc, (parent_count + ppc - 1) / ppc, LP_T, LP_SMEM, st, F, level, parent_begin, parent_count, ppc,
-                                                                     F.O.l2p_img + F.O.l2p_off[level],
-                                                                     F.O.l2p_img + F.O.l2pc_off, out, err);
+    // one CTA per SM, each taking the same number k of chunks of up to 128 parents (the MMA's M)
+    const int nsm = sm_count();
+    const int k = std::max(1, (parent_count + TCM * nsm - 1) / (TCM * nsm));
+    const int ppc = std::max(1, std::min(TCM, (parent_count + k * nsm - 1) / (k * nsm)));
+    const int nchunks = (parent_count + ppc - 1) / ppc;
+    const int grid = std::min(nchunks, nsm);
+    launch_pdl(k_l2lp_tc, grid, LP_T, LP_SMEM, st, F, level, parent_begin, parent_count, ppc, nchunks,
+                                                         F.O.l2p_img + F.O.l2p_off[level],
+                                                         F.O.l2p_img + F.O.l2pc_off, out, err);
 }
 
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
