@@ -37,6 +37,14 @@ constexpr uint32_t TC_TAIL = 32 + 2 * TCN * 4;                     // 2 mbarrier
 constexpr uint32_t TC_SMEM = 1024 + 2 * A_BYTES + 2 * B_BYTES + TC_TAIL;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 void tc_init_attributes();
+// target-stationary M2L (below): parts of the 216 positions around the parent, positions per part,
+// dynamic shared memory (two operator buffers, the gathered tile, the source table, the tail)
+constexpr int MT_P = 4;
+constexpr int MT_OFFS = 216 / MT_P;
+constexpr uint32_t MT_SMEM = 1024 + 4 * A_BYTES + 2 * A_BYTES + MT_OFFS * TCM * 4 + 1024;
+__global__ void __launch_bounds__(256, 1) k_m2l_tiles(FmmDev F, const int *__restrict__ groups,
+                                                      const int *__restrict__ ngroups, int *__restrict__ counter,
+                                                      const uint16_t *__restrict__ images, int *err);
 
 // Operator (FP32, transposed [k][i], stride np) -> BF16 hi / lo images, K-major SW128.
 __global__ void k_make_image(const float *__restrict__ opT, int np, uint16_t *__restrict__ img) {
@@ -1187,6 +1195,7 @@ void tc_init_attributes() {
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
     cudaFuncSetAttribute(k_l2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L2P_SMEM);
     cudaFuncSetAttribute(k_l2lp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);
+    cudaFuncSetAttribute(k_m2l_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
     cudaFuncSetAttribute(k_m2l_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PIPE_SMEM);
     done = true;
 }
@@ -1199,6 +1208,260 @@ void fmm_l2p_tc_level(const FmmDev &F, int level, int box_begin, int box_count, 
     tc_init_attributes();
     launch_pdl(k_l2p_tc, (box_count + TCM - 1) / TCM, 128, L2P_SMEM, st, F, level, box_begin, box_count,
                                                                  F.O.l2p_img + F.O.l2p_off[level], out, err);
+}
+
+// ---------------------------------------------------------------- M2L, target-stationary tiles
+// A work item is a group of up to 128 target boxes of one level and one octant (child index c
+// within the parent: the 128 children c of 128 consecutive parent slots) and one of MT_P parts
+// of the 216 = 6^3 positions around the parent.  Every box of the group has the same 189 V-list
+// offsets (source minus target: o + c in [-2, 3] per axis, |o|_inf >= 2), so the MMA's columns
+// are the group's boxes and its A operand the operator of one offset.  Per offset, the source of
+// column j is the box at its key + o when that slot holds a box with sources (the V rule of the
+// list kernel, by dense lookup), else a zero column.  The 128 x 128 result accumulates in TMEM
+// over the item's offsets and is added into the boxes' rows once (reductions: the other parts
+// and the X list add into the same rows).  Operators stream through two buffers (the copy of
+// offset k+2 issued once MMA k has read its buffer); the gathered sources of offset k+1 are in
+// registers while MMA k runs.  One persistent CTA per SM takes items from a counter.
+
+__device__ __forceinline__ void mt_offset(int v, int c, int &ox, int &oy, int &oz) {
+    ox = v % 6 - 2 - (c & 1);
+    oy = (v / 6) % 6 - 2 - ((c >> 1) & 1);
+    oz = v / 36 - 2 - (c >> 2);
+}
+
+// member j of group (l, tile, c): the child c of parent slot tile * 128 + j, if it holds
+// targets and has V-list entries (its parent's 3^3 neighbourhood holds sources); else -1
+__device__ __forceinline__ int mt_member(const FmmDev &F, int l, int tile, int c, int j) {
+    const TreeDev &T = F.T;
+    const int P = tile * TCM + j;
+    if (P >= (1 << (3 * (l - 1))) || !T.near[dense_off(l - 1) + P]) return -1;
+    const int b = T.box_at[dense_off(l) + ((uint32_t)P << 3 | (uint32_t)c)];
+    if (b < 0 || T.b_te[b] <= T.b_tb[b] || F.L.v_cnt[b] <= 0) return -1;
+    return b;
+}
+
+__global__ void __launch_bounds__(256) k_m2l_groups(FmmDev F, MtLevels ML, int *__restrict__ groups,
+                                                    int *__restrict__ ngroups) {
+    pdl_enter();
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (g >= ML.gbase[ML.lmax + 1]) return;
+    int l = ML.lmin;
+    while (g >= ML.gbase[l + 1]) ++l;
+    const int r = g - ML.gbase[l], tile = r >> 3, c = r & 7;
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < TCM / 32; ++u) any |= mt_member(F, l, tile, c, lane + 32 * u) >= 0;
+    if (__any_sync(0xffffffffu, any) && lane == 0) groups[atomicAdd(ngroups, 1)] = (l << 24) | (tile << 3) | c;
+}
+
+__global__ void __launch_bounds__(256, 1) k_m2l_tiles(FmmDev F, const int *__restrict__ groups,
+                                                      const int *__restrict__ ngroups, int *__restrict__ counter,
+                                                      const uint16_t *__restrict__ images, int *err) {
+    pdl_enter();
+    const int nitems = MT_P * *ngroups;
+    if ((int)blockIdx.x >= nitems) return;         // uniform, before any allocation
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // operator images at base + 2 A_BYTES buf (buf = 0, 1: hi then lo), then the gathered tile
+    uint8_t *b_hi = base + 4 * A_BYTES, *b_lo = b_hi + A_BYTES;
+    int *tab = reinterpret_cast<int *>(b_lo + A_BYTES);        // [MT_OFFS][128] source box or -1
+    uint8_t *tail = reinterpret_cast<uint8_t *>(tab + MT_OFFS * TCM);
+    uint64_t *bar_a = reinterpret_cast<uint64_t *>(tail);     // [2]
+    uint64_t *bar_mma = bar_a + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tail + 24);
+    int *ctl = reinterpret_cast<int *>(tail + 32);            // [0] item, [1] offsets, [2] ok
+    int *mem = reinterpret_cast<int *>(tail + 64);            // [128] member box or -1
+    int *offs = mem + TCM;                                    // [MT_OFFS] positions with a source
+    int *oflag = offs + MT_OFFS;                              // [MT_OFFS]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int np = F.O.npad, n = F.O.n;
+    const TreeDev &T = F.T;
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tslot), TCM);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) tc::mbar_init(tc::smem_u32(bar_a + k), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ctl[2] = 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(TCM, TCM);
+    // thread 0's barrier bookkeeping: completed waits per operator buffer and on the MMA barrier
+    int a_done[2] = {0, 0}, a_iss[2] = {0, 0}, m_done = 0, m_iss = 0;
+    float4 v[LP_V];
+    auto issue_op = [&](int buf, int l, int c, int vpos) {
+        int ox, oy, oz;
+        mt_offset(vpos, c, ox, oy, oz);
+        const uint16_t *img = images + (size_t)(l * NSLOT + m2l_slot(ox, oy, oz)) * (2 * A_BYTES / 2);
+        tc::mbar_expect_tx(tc::smem_u32(bar_a + buf), 2 * A_BYTES);
+        uint8_t *dst = base + 2 * A_BYTES * buf;
+        tc::bulk_g2s(tc::smem_u32(dst), img, A_BYTES, tc::smem_u32(bar_a + buf));
+        tc::bulk_g2s(tc::smem_u32(dst + A_BYTES), img + A_BYTES / 2, A_BYTES, tc::smem_u32(bar_a + buf));
+        ++a_iss[buf];
+    };
+    while (true) {
+        tc::fence_before_sync();                   // the previous item's TMEM reads
+        __syncthreads();
+        if (tid == 0) ctl[0] = atomicAdd(counter, 1);
+        if (tid < MT_OFFS) oflag[tid] = 0;
+        __syncthreads();
+        const int item = ctl[0];
+        if (item >= nitems || !ctl[2]) break;
+        const int g = groups[item / MT_P], part = item % MT_P;
+        const int l = g >> 24, tile = (g >> 3) & 0x1FFFFF, c = g & 7;
+        if (tid < TCM) mem[tid] = mt_member(F, l, tile, c, tid);
+        __syncthreads();
+        // sources of every (position, member) of this part, by dense lookup
+        const int edge = 1 << l;
+        const uint8_t *vs = T.vsrc + dense_off(l);
+        const int *ba = T.box_at + dense_off(l);
+        // a thread's 27 lookups are independent: every slot is computed first, then both loads of
+        // every lookup are issued before any is used (one round trip instead of 27)
+        {
+            constexpr int PER = MT_OFFS * TCM / 256;           // 27
+            const int j = tid % TCM;                           // the same member in every lookup
+            const int mj = mem[j];
+            uint32_t bx = 0, by = 0, bz = 0;
+            demorton3((uint32_t)(tile * TCM + j) << 3 | (uint32_t)c, bx, by, bz);
+            int slot[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int vi = (tid + 256 * u) / TCM;
+                int ox, oy, oz;
+                mt_offset(part * MT_OFFS + vi, c, ox, oy, oz);
+                const int sx = (int)bx + ox, sy = (int)by + oy, sz = (int)bz + oz;
+                const bool ok = mj >= 0 && !(abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) && sx >= 0 && sy >= 0 &&
+                                sz >= 0 && sx < edge && sy < edge && sz < edge;
+                slot[u] = ok ? (int)morton3((uint32_t)sx, (uint32_t)sy, (uint32_t)sz) : -1;
+            }
+            uint8_t has[PER];
+            int box[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                has[u] = slot[u] >= 0 ? __ldg(vs + slot[u]) : (uint8_t)0;
+                box[u] = slot[u] >= 0 ? __ldg(ba + slot[u]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int e = tid + 256 * u;
+                const int A = has[u] ? box[u] : -1;
+                tab[e] = A;
+                if (A >= 0) oflag[e / TCM] = 1;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int k = 0;
+            for (int vi = 0; vi < MT_OFFS; ++vi)
+                if (oflag[vi]) offs[k++] = vi;
+            ctl[1] = k;
+        }
+        __syncthreads();
+        const int n_off = ctl[1];
+        if (n_off == 0) continue;
+        if (tid == 0) {
+            issue_op(0, l, c, part * MT_OFFS + offs[0]);
+            if (n_off > 1) issue_op(1, l, c, part * MT_OFFS + offs[1]);
+        }
+        lp_load(v, tab + offs[0] * TCM, F.ueq, np);
+        lp_store(b_hi, b_lo, v);
+        for (int k = 0; k < n_off; ++k) {
+            // (a) the gathered sources of offset k are in shared memory: MMAs (thread 0)
+            tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            const int buf = k & 1;
+            if (tid == 0 && ctl[2]) {
+                if (tc::mbar_wait_bounded(tc::smem_u32(bar_a + buf), a_done[buf] & 1, WAIT_LIMIT)) {
+                    ++a_done[buf];
+                    tc::fence_after_sync();
+                    const uint32_t ah = tc::smem_u32(base + 2 * A_BYTES * buf), al = ah + A_BYTES;
+                    const uint32_t bh = tc::smem_u32(b_hi), bl = tc::smem_u32(b_lo);
+#pragma unroll
+                    for (int ks = 0; ks < TCK / 16; ++ks) {
+                        const uint32_t o = tc::sw128_offset(0, 16 * ks, TCM);
+                        tc::mma_bf16(tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bh + o), idesc, (k | ks) > 0);
+                        tc::mma_bf16(tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bl + o), idesc, 1);
+                        tc::mma_bf16(tmem, tc::sdesc_sw128(al + o), tc::sdesc_sw128(bh + o), idesc, 1);
+                    }
+                    tc::mma_commit(tc::smem_u32(bar_mma));
+                    ++m_iss;
+                } else {
+                    atomicOr(err, 16);
+                    ctl[2] = 0;
+                }
+            }
+            // (b) the sources of offset k+1 in flight while the MMAs run
+            if (k + 1 < n_off) lp_load(v, tab + offs[k + 1] * TCM, F.ueq, np);
+            // (c) MMAs of offset k complete: the B tile and operator buffer k % 2 are free; the
+            //     operator of offset k+2 streams into that buffer
+            if (tid == 0 && ctl[2]) {
+                if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), m_done & 1, WAIT_LIMIT)) {
+                    ++m_done;
+                    if (k + 2 < n_off) issue_op(buf, l, c, part * MT_OFFS + offs[k + 2]);
+                } else {
+                    atomicOr(err, 32);
+                    ctl[2] = 0;
+                }
+            }
+            __syncthreads();
+            if (!ctl[2]) break;
+            tc::fence_after_sync();
+            // (e) the B tile of offset k+1
+            if (k + 1 < n_off) lp_store(b_hi, b_lo, v);
+        }
+        if (!ctl[2]) break;
+        // the accumulated check potentials into the members' rows: warps w and w + 4 read TMEM
+        // lanes 32 (w % 4) .. (rows i) and half of the 128 columns each
+        const int q = warp & 3, i = q * 32 + lane;
+#pragma unroll 1
+        for (int c0 = (warp >> 2) * 64; c0 < (warp >> 2) * 64 + 64; c0 += 16) {
+            float r[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+            if (i < n) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int d = mem[c0 + jj];
+                    if (d >= 0) atomicAdd(F.dchk + (size_t)d * np + i, r[jj]);
+                }
+            }
+        }
+    }
+    if (tid == 0 && !ctl[2]) {
+        // let this CTA's own copies and MMAs finish before its memory is released
+        for (int b = 0; b < 2; ++b)
+            if (a_iss[b] > a_done[b]) tc::mbar_wait_bounded(tc::smem_u32(bar_a + b), (a_iss[b] - 1) & 1, WAIT_LIMIT);
+        if (m_iss > m_done) tc::mbar_wait_bounded(tc::smem_u32(bar_mma), (m_iss - 1) & 1, WAIT_LIMIT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TCM);
+}
+
+MtLevels m2l_tile_levels(int Lmax) {
+    MtLevels ML{};
+    ML.lmin = 2;
+    ML.lmax = Lmax;
+    int g = 0;
+    for (int l = 0; l <= Lmax + 1 && l < 18; ++l) {
+        ML.gbase[l] = g;
+        if (l >= 2 && l <= Lmax) g += ((1 << (3 * (l - 1))) + TCM - 1) / TCM * 8;
+    }
+    return ML;
+}
+
+void fmm_m2l_tiles(const FmmDev &F, const MtLevels &ML, int *groups, int *ngroups, int *counter,
+                   const uint16_t *images, int *err, cudaStream_t st) {
+    if (ML.lmax < ML.lmin) return;
+    tc_init_attributes();
+    const int total = ML.gbase[ML.lmax + 1];
+    launch_pdl(k_m2l_groups, (total + 7) / 8, 256, 0, st, F, ML, groups, ngroups);
+    launch_pdl(k_m2l_tiles, sm_count(), 256, MT_SMEM, st, F, (const int *)groups, (const int *)ngroups, counter,
+               images, err);
 }
 
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,

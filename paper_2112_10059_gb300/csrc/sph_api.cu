@@ -87,6 +87,9 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    int m2l_tiles = 2;                // tensor-core M2L in target-stationary tiles: 0 never (tiles of V
+                                      // pairs), 1 always, 2 where the V lists are dense (>= 32 pairs per box)
+    DevBuf b_mtg;                     // groups of the target-stationary M2L
     bool l2lp_fused = true;           // deepest level of edge-4 leaves: L2L and L2P in one tensor-core kernel
     bool l2lp_used = false;           // the last eval ran the fused kernel
     bool defer_sync = true;           // fixed leaf size: one host sync for selection, tree and list counts
@@ -560,6 +563,8 @@ struct PassState {
     PairsDev Pd;
     int *err = nullptr;
     bool tc = false;
+    MtLevels ML;                 // target-stationary M2L: groups per level
+    int *mt_groups = nullptr;    // [groups] scratch of that M2L
 };
 
 // Every buffer the passes need (so that fmm_queue allocates nothing and can be captured).
@@ -604,6 +609,11 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
+    S.ML = m2l_tile_levels(c->Lmax);
+    if (S.tc && c->m2l_tiles) {
+        ENS(c->b_mtg, (size_t)std::max(1, S.ML.gbase[S.ML.lmax + 1]) * sizeof(int));
+        S.mt_groups = P<int>(c->b_mtg);
+    }
     tc_init_attributes();
     fmm_init_attributes();
     return SPH_OK;
@@ -656,12 +666,22 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         const int nV = c->list_tot[1];
         // (the V pairs were grouped by key with the lists)
         if (tm) tm->mark_at(5, c->stream);
-        if (S.tc) {
+        // target-stationary tiles pay a round per (group, offset) whatever the number of pairs in
+        // it, so they are taken where the lists are dense (uniform trees), the pair tiles elsewhere
+        const bool tiles = S.tc && (c->m2l_tiles == 1 || (c->m2l_tiles == 2 && (int64_t)nV >= 32ll * nb));
+        if (tiles) {
+            // w_cnt[36]: number of groups, w_cnt[37]: the work counter (zeroed with the others)
+            if (nV > 0) {
+                fmm_m2l_tiles(F, S.ML, S.mt_groups, S.w_cnt + 36, S.w_cnt + 37, F.O.m2l_img, S.err, c->stream);
+                c->launches += 2;
+            }
+        } else if (S.tc) {
             fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream, c->m2l_pipe);
+            c->launches += nV > 0;
         } else {
             fmm_m2l_pairs(F, S.Pd, nV, c->m2l_prec, c->stream);
+            c->launches += nV > 0;
         }
-        c->launches += nV > 0;
         if (tm) tm->mark_at(6, c->stream);
         for (int l = 2; l <= c->Lmax; ++l)
             if (c->list_tot[3] > 0) {
@@ -797,7 +817,8 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(c->lvl_src.data(), c->lvl_src.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
-                          c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, (int64_t)reinterpret_cast<uintptr_t>(out)};
+                          c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, c->m2l_tiles,
+                          (int64_t)reinterpret_cast<uintptr_t>(out)};
     put(sc, sizeof sc);
     return v;
 }
@@ -1105,6 +1126,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
     sub->l2lp_fused = parent->l2lp_fused;
+    sub->m2l_tiles = parent->m2l_tiles;
     sub->defer_sync = parent->defer_sync;
     sub->near_mode = parent->near_mode;
     sub->r_s = parent->r_s;
@@ -1481,6 +1503,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;
+    if (const char *e = getenv("SPH_M2L_TILES")) c->m2l_tiles = atoi(e);
     if (const char *e = getenv("SPH_DEFER_SYNC")) c->defer_sync = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;
@@ -1514,7 +1537,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pkeys, &c->b_ppairs, &c->b_heavy,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->o_m2mbf, &c->b_err, &c->b_work, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->o_m2mbf, &c->b_err, &c->b_work, &c->b_mtg, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)

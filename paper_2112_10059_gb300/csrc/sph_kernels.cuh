@@ -249,6 +249,17 @@ size_t tc_image_elems(int count);
 void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st);
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
                 bool pipelined = false);
+// M2L of every level in target-stationary tiles (tensor cores): groups of up to 128 boxes of one
+// level and octant, their V-list sources found by dense lookup (no pair list read)
+struct MtLevels {
+    int lmin, lmax;
+    int gbase[18];      // first group of level l; gbase[lmax + 1] = number of groups
+};
+MtLevels m2l_tile_levels(int Lmax);
+// groups: [number of groups] scratch; ngroups, counter: device ints zeroed before the call
+void fmm_m2l_tiles(const FmmDev &F, const MtLevels &ML, int *groups, int *ngroups, int *counter,
+                   const uint16_t *images, int *err, cudaStream_t st);
+int sm_count();
 void fmm_l2l_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,
                       int *err, cudaStream_t st);
 void fmm_l2l_tc8_level(const FmmDev &F, int level, int parent_begin, int parent_count, const uint16_t *images,

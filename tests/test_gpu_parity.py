@@ -649,3 +649,42 @@ def test_launch_order_switch_same_result(sph, tmp_path):
     a, b = res
     assert np.count_nonzero(a) > 0
     assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("pi", [0, 1, 2])
+def test_m2l_target_tiles_equal_pair_tiles(sph, monkeypatch, pi):
+    """The two tensor-core M2L forms give the same far field: tiles of V pairs of one (level,
+    offset) with per-pair reductions (SPH_M2L_TILES=0), and target-stationary tiles that find
+    each target's V-list sources by dense lookup and accumulate every offset in TMEM (default).
+    Same operators, same BF16 x3 arithmetic; only the order of the FP32 sums differs."""
+    p = _problems()[pi]
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SPH_M2L_TILES", flag)
+        c = sph.Context(0)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, stats=True)
+        outs[flag] = out.cpu().numpy().astype(np.float64)
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs["1"][T], outs["0"][T]) < 1e-5
+    _check_fmm(outs["1"], ref, T, p.name)
+
+
+def test_m2l_target_tiles_uniform_tree(sph, monkeypatch):
+    """Every cell a source and a target on a 64^3 grid (a complete tree down to leaves of 4^3
+    cells, every box at every level with its full V list): both M2L forms agree and pass the
+    oracle gate on sampled targets."""
+    p = si.streamer(n=64, box=1.0, chan_len=0.5, i_frac=0.0, targets_all=True, seed=41, name="s64_full")
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SPH_M2L_TILES", flag)
+        c = sph.Context(0)
+        _, out, st = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3, leaf_size=64, stats=True)
+        outs[flag] = out.cpu().numpy().astype(np.float64)
+        c.close()
+    samp = np.sort(np.random.default_rng(3).choice(p.ncell, 3000, replace=False)).astype(np.int32)
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, np.arange(p.ncell, dtype=np.int32), samp)
+    assert oracle.rel_l2(outs["1"], outs["0"]) < 1e-5
+    assert oracle.rel_l2(outs["1"][samp], ref) <= REL_L2
+    assert oracle.max_rel(outs["1"][samp], ref, 1e-3) <= MAX_REL
