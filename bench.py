@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid edge (cells)")
+    ap.add_argument("--workload", default="adaptive", choices=["adaptive", "full"],
+                    help="adaptive: sources I >= 1e-4 max I, targets |E| >= 0.1 max|E|; full: every cell a source "
+                         "and a target (no adaptivity)")
     ap.add_argument("--p", type=float, default=760.0, help="pressure (Torr)")
     ap.add_argument("--m2l", default="bf16x3", choices=["f32", "bf16x3"])
     ap.add_argument("--order", type=int, default=5, help="Chebyshev order of the far field")
@@ -59,24 +62,39 @@ def parse():
                     help="Section 4.3 trade-off: FMM time and E_V against the full FP64 sum for I_pct 1e-4 .. 1e-1")
     ap.add_argument("--sur-samples", type=int, default=2000, help="FMM solves in the surrogate's training set")
     ap.add_argument("--sur-epochs", type=int, default=10)
-    ap.add_argument("--acc-uniform", type=int, default=100000,
-                    help="uniform targets of the stratified oracle sample (plus every target within 5 sigma of the head)")
+    ap.add_argument("--acc-uniform", type=int, default=None,
+                    help="uniform targets of the stratified oracle sample (plus every target within 5 sigma of the head); "
+                         "default 100000 (adaptive workload), 1000 (every cell a source)")
     ap.add_argument("--no-decomp", action="store_true", help="skip the error decomposition (M2L arithmetic, fusion, order)")
     ap.add_argument("--no-full128", action="store_true",
                     help="skip the non-adaptive 128^3 FMM-vs-direct block (every cell a source and a target)")
     ap.add_argument("--no-pressures", action="store_true", help="skip the 76 and 380 Torr runs of the 256^3 workload")
     ap.add_argument("--fft256", action="store_true",
                     help="also time the FP64 FFT convolution of the 256^3 workload and check every target against it")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.acc_uniform is None:
+        a.acc_uniform = 100000 if a.workload == "adaptive" else 1000
+    if a.workload == "full":
+        a.no_full128 = True          # that block is this workload at 128^3
+    return a
 
 
 def workload(args):
+    if args.workload == "full":
+        p = si.streamer_full(args.n)
+        if args.p != 760.0:
+            p = si.streamer(n=args.n, box=1.0, p_torr=args.p, chan_len=0.5, i_frac=0.0, targets_all=True, seed=1001,
+                            with_efield=False, name="streamer_%d_full" % args.n)
+        return p
     return si.streamer_adaptive(n=args.n, p_torr=args.p)
 
 
 def workload_cfg(p, args):
-    return {"workload": "streamer %d^3 in 1 cm, %g Torr, sources I>=1e-4*max, targets |E|>=0.1*max|E|"
-                        % (args.n, args.p),
+    if args.workload == "full":
+        desc = "streamer %d^3 in 1 cm, %g Torr, every cell a source and a target" % (args.n, args.p)
+    else:
+        desc = "streamer %d^3 in 1 cm, %g Torr, sources I>=1e-4*max, targets |E|>=0.1*max|E|" % (args.n, args.p)
+    return {"workload": desc,
             "grid": [p.nx, p.ny, p.nz], "pressure_torr": args.p, "i_frac": p.i_frac, "e_frac": p.e_frac,
             "leaf_size": p.leaf_size, "m2l": args.m2l, "far_field": "chebyshev order %d" % args.order,
             "l2_flush_between_steps": True,
@@ -434,13 +452,28 @@ def run_surrogate(sph, torch, dev, stream, args, peaks):
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 5
     # prediction error on held-out geometries: network vs the coarse estimate alone
-    en, ec = [], []
-    for i in range(0, 16, B):
-        yy = net.forward(Xv[i:i + B].reshape(-1), B).cpu().numpy().reshape(B, -1, 2)
-        tt = Tv[i:i + B].cpu().numpy().reshape(B, -1)
-        en.append(np.abs(np.expm1(yy[..., 0] - tt)))
-        ec.append(np.abs(np.expm1(-tt)))
-    en, ec = np.concatenate(en).ravel(), np.concatenate(ec).ravel()
+    def held_out_errors(nt):
+        en, ec = [], []
+        for i in range(0, 16, B):
+            yy = nt.forward(Xv[i:i + B].reshape(-1), B).cpu().numpy().reshape(B, -1, 2)
+            tt = Tv[i:i + B].cpu().numpy().reshape(B, -1)
+            en.append(np.abs(np.expm1(yy[..., 0] - tt)))
+            ec.append(np.abs(np.expm1(-tt)))
+        return np.concatenate(en).ravel(), np.concatenate(ec).ravel()
+
+    def err_stats(e):
+        return {"mean": float(e.mean()), "median": float(np.median(e)), "p90": float(np.percentile(e, 90)),
+                "frac_below_1e-3": float((e < 1e-3).mean())}
+
+    en, ec = held_out_errors(net)
+    # the spread over initial weights: the same training set and schedule from two more seeds
+    # (training itself is deterministic: gradients are summed in a fixed order)
+    seeds = [{"seed": 11, **err_stats(en)}]
+    for sd in (12, 13):
+        other = sur.Net(edge=D, max_batch=B, seed=sd)
+        sur.train(other, X, T, epochs=args.sur_epochs, batch=B, lr=1e-3, lr_final=1e-4)
+        seeds.append({"seed": sd, **err_stats(held_out_errors(other)[0])})
+        other.close()
     # the streamer-and-cloud configuration: full FMM vs the judged surrogate
     p = si.streamer_cloud(nf)
     q = torch.from_numpy(p.q).to(dev)
@@ -492,11 +525,9 @@ def run_surrogate(sph, torch, dev, stream, args, peaks):
                                                                                          args.sur_epochs, B),
             "params": int(net.P), "generate_s": gen_s, "train_s": train_s, "train_steps": steps,
             "val_loss_before": before, "val_loss_after": hist[-1][2], "train_loss_last": hist[-1][1],
-            "pred_err_network": {"mean": float(en.mean()), "median": float(np.median(en)),
-                                 "p90": float(np.percentile(en, 90)), "frac_below_1e-3": float((en < 1e-3).mean())},
-            "pred_err_coarse_only": {"mean": float(ec.mean()), "median": float(np.median(ec)),
-                                     "p90": float(np.percentile(ec, 90)),
-                                     "frac_below_1e-3": float((ec < 1e-3).mean())},
+            "pred_err_network": err_stats(en),
+            "pred_err_network_seeds": seeds,
+            "pred_err_coarse_only": err_stats(ec),
             "train_step_ms": step_ms, "forward_ms": fwd_ms,
             "conv_roofline": {"bound": "tensor", "achieved_train": fl_step / (step_ms * 1e-3) / 1e12,
                               "achieved_forward": fl_fwd / (fwd_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -761,7 +792,7 @@ def main():
     p = workload(args)
     dev = torch.device("cuda", local)
     q = torch.from_numpy(p.q).to(dev)
-    em = torch.from_numpy(p.emag).to(dev)
+    em = torch.from_numpy(p.emag).to(dev) if p.emag is not None and not p.targets_all else None
     stream = torch.cuda.current_stream(dev)
     pipes = pipe_peaks(sph, dev, stream)
     prec = sph.M2L_BF16X3 if args.m2l == "bf16x3" else sph.M2L_F32
@@ -797,7 +828,7 @@ def main():
 
     # e2e through the host-buffer entry point, inputs and output in pinned host memory
     qh = torch.from_numpy(p.q).pin_memory().numpy()
-    eh = torch.from_numpy(p.emag).pin_memory().numpy()
+    eh = torch.from_numpy(p.emag).pin_memory().numpy() if em is not None else None
     sh = torch.empty(p.ncell, dtype=torch.float32).pin_memory().numpy()
     sph.eval_sph_host(ctx, qh, eh, out=sh)
     torch.cuda.synchronize()
@@ -810,7 +841,10 @@ def main():
     e2e_ms, e2e_value = whole_job_rate(1e3 * statistics.median(e2e_t), nt, world, dist, dev)
     # restore device inputs, and the device result of the last evaluation
     sph.set_sources(ctx, q, p.source_scale)
-    sph.set_targets(ctx, emag=em)
+    if em is not None:
+        sph.set_targets(ctx, emag=em)
+    else:
+        sph.set_targets(ctx)
     sph.eval_sph(ctx, out)
     torch.cuda.synchronize()
 
@@ -818,7 +852,7 @@ def main():
     tree = sph.get_tree(ctx)
     clocks = clk.summary()
     peaks = measured_peaks()
-    headline = args.n == 256 and args.p == 760.0 and args.order == 5
+    headline = args.n == 256 and args.p == 760.0 and args.order == 5 and args.workload == "adaptive"
     roof = rooflines(tree, step_stats, args, nt, int(st0.n_sources), p.ncell, peaks, pipes,
                      traffic_ok=headline)
     dominant = dominant_kernel(roof)
@@ -841,7 +875,8 @@ def main():
     # head + seeded uniform targets), the same run timed as the CPU baseline
     J, T = sph.get_selection(ctx)
     S = out.cpu().numpy()
-    acc, ref, samp, ball, w, cpu_t = accuracy_block(p, J, T, S, args.acc_uniform)
+    acc, ref, samp, ball, w, cpu_t = accuracy_block(p, J, T, S, args.acc_uniform,
+                                                    3.0 if args.workload == "adaptive" else 1.0)
     if not args.no_decomp:
         acc["decomposition"] = error_decomposition(sph, torch, dev, stream, p, q, em, samp, ball, w, ref, args)
     fft256 = None
@@ -889,7 +924,8 @@ def main():
                 "step_ms_stats": {"median": statistics.median(step_ms), "mean": statistics.mean(step_ms),
                                   "min": min(step_ms), "max": max(step_ms)},
                 "e2e": {"value": e2e_value, "unit": "targets/s",
-                        "h2d_bytes_per_step": int(qh.nbytes + eh.nbytes), "d2h_bytes_per_step": int(sh.nbytes)},
+                        "h2d_bytes_per_step": int(qh.nbytes + (eh.nbytes if eh is not None else 0)),
+                        "d2h_bytes_per_step": int(sh.nbytes)},
                 "roofline": dict(roof[dominant], phase=dominant),
                 "rooflines": roof, "pipe_peaks": pipes,
                 "clocks": clocks, "gpu_launches": int(step_stats[-1]["n_launches"]) * args.steps,

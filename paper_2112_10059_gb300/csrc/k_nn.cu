@@ -19,6 +19,8 @@
 // on (the result is then invalid and the host reports it).
 #include <math.h>
 
+#include <algorithm>
+
 #include "nn_kernels.cuh"
 #include "tc_sm103.cuh"
 
@@ -271,13 +273,29 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a) {
     float v[N];
     tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
     if constexpr (N == 32) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16, v + 16);
-    float *dst = a.dw + (size_t)(blockIdx.x * 128 + r) * N;
+    if (a.part) {   // this CTA's partial, summed with the others' in a fixed order by k_wgrad_sum
+        const size_t rows = (size_t)gridDim.x * 128;
+        float4 *dst = reinterpret_cast<float4 *>(a.part + ((size_t)blockIdx.y * rows + blockIdx.x * 128 + r) * N);
 #pragma unroll
-    for (int n = 0; n < N; ++n) atomicAdd(dst + n, v[n]);
+        for (int n = 0; n < N; n += 4) dst[n / 4] = make_float4(v[n], v[n + 1], v[n + 2], v[n + 3]);
+    } else {
+        float *dst = a.dw + (size_t)(blockIdx.x * 128 + r) * N;
+#pragma unroll
+        for (int n = 0; n < N; ++n) atomicAdd(dst + n, v[n]);
+    }
     fence_before_sync();
     __syncthreads();
     if (r == 0 && *eflag) atomicOr(a.err, 1);
     if (r < 32) tmem_dealloc(tmem, 32);
+}
+
+// dw[e] += sum over the splits y = 0, 1, ... of part[y][e], in that order
+__global__ void k_wgrad_sum(const float *__restrict__ part, float *__restrict__ dw, int elems, int splits) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= elems) return;
+    float acc = dw[e];
+    for (int y = 0; y < splits; ++y) acc += part[(size_t)y * elems + e];
+    dw[e] = acc;
 }
 
 template <int C, int N>
@@ -319,9 +337,14 @@ static void launch_wgrad(WgradArgs a, cudaStream_t st) {
     const int target = 4 * 152;
     int cpc = (nchunks * mtiles + target - 1) / target;
     if (cpc < 4) cpc = 4;
+    if (a.part) cpc = std::max(cpc, (nchunks + WGRAD_MAX_SPLIT - 1) / WGRAD_MAX_SPLIT);   // splits fit the scratch
     a.chunks_per_cta = cpc;
     dim3 grid(mtiles, (nchunks + cpc - 1) / cpc);
     k_wgrad_tc<C, N><<<grid, 128, wgrad_smem(N), st>>>(a);
+    if (a.part) {
+        const int elems = wgrad_rows(C) * N;
+        k_wgrad_sum<<<(elems + 255) / 256, 256, 0, st>>>(a.part, a.dw, elems, (int)grid.y);
+    }
 }
 
 int wgrad(const WgradArgs &a, int C, int N, cudaStream_t st) {
@@ -497,7 +520,8 @@ __global__ void k_head_forward(const uint16_t *__restrict__ f, const float *__re
 __global__ void k_head_loss_backward(const uint16_t *__restrict__ f, const float *__restrict__ hw,
                                      const float *__restrict__ hb, const float *__restrict__ t,
                                      uint16_t *__restrict__ g_f, float *__restrict__ hg, double *loss_sum, int nvox,
-                                     float lambda, float eps) {
+                                     float lambda, float eps, float *__restrict__ hpart) {
+    __shared__ float wsum[8][34];
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = m < nvox;
     float a[16];
@@ -533,7 +557,19 @@ __global__ void k_head_loss_backward(const uint16_t *__restrict__ f, const float
         float x = k < 16 ? gr * a[k] : (k < 32 ? ge * a[k - 16] : (k == 32 ? gr : ge));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0 && x != 0.f) atomicAdd(hg + k, x);
+        if (hpart) {
+            if (lane == 0) wsum[threadIdx.x >> 5][k] = x;
+        } else if (lane == 0 && x != 0.f) {
+            atomicAdd(hg + k, x);
+        }
+    }
+    if (hpart) {   // the block's partial (its warps in order); summed over the blocks in order later
+        __syncthreads();
+        if (threadIdx.x < 34) {
+            float b = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w][threadIdx.x];
+            hpart[(size_t)blockIdx.x * 34 + threadIdx.x] = b;
+        }
     }
     double ld = li;
 #pragma unroll
@@ -544,10 +580,23 @@ __global__ void k_head_loss_backward(const uint16_t *__restrict__ f, const float
 void head_forward(const uint16_t *f, const float *hw, const float *hb, float *y, int nvox, cudaStream_t st) {
     if (nvox > 0) k_head_forward<<<blocks_for(nvox), 256, 0, st>>>(f, hw, hb, y, nvox);
 }
+// hg[k] += sum over the blocks b = 0, 1, ... of hpart[b][k], in that order
+__global__ void k_head_sum(const float *__restrict__ hpart, float *__restrict__ hg, int nblocks) {
+    const int k = threadIdx.x;
+    if (k >= 34) return;
+    float acc = hg[k];
+    for (int b = 0; b < nblocks; ++b) acc += hpart[(size_t)b * 34 + k];
+    hg[k] = acc;
+}
+
 void head_loss_backward(const uint16_t *f, const float *hw, const float *hb, const float *t, uint16_t *g_f,
-                        float *hg, double *loss_sum, int nvox, float lambda, float eps, cudaStream_t st) {
-    if (nvox > 0)
-        k_head_loss_backward<<<blocks_for(nvox), 256, 0, st>>>(f, hw, hb, t, g_f, hg, loss_sum, nvox, lambda, eps);
+                        float *hg, double *loss_sum, int nvox, float lambda, float eps, cudaStream_t st,
+                        float *hpart) {
+    if (nvox <= 0) return;
+    const int nb = blocks_for(nvox);
+    if (nb > HEAD_MAX_BLOCKS) hpart = nullptr;   // beyond the scratch: reductions
+    k_head_loss_backward<<<nb, 256, 0, st>>>(f, hw, hb, t, g_f, hg, loss_sum, nvox, lambda, eps, hpart);
+    if (hpart) k_head_sum<<<1, 64, 0, st>>>(hpart, hg, nb);
 }
 
 // ---------------------------------------------------------------- parameters

@@ -270,7 +270,6 @@ __device__ __forceinline__ unsigned long long pack_state(unsigned st, unsigned n
     return ((unsigned long long)st << 62) | ((unsigned long long)ns << 31) | (unsigned long long)nt;
 }
 
-constexpr unsigned LOOKBACK_LIMIT = 1u << 22;
 
 // One pass over the grid: each CTA takes the next brick in dispatch order (ticket), reads
 // it row by row, evaluates both rules, ranks its cells in Morton order, finds its output
@@ -280,7 +279,7 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
         int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
         float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
-        uint8_t *__restrict__ tmask) {
+        uint8_t *__restrict__ tmask, unsigned wait_limit) {
     pdl_enter();
     __shared__ int s_brick;
     __shared__ float s_thr_q, s_thr_e;
@@ -420,7 +419,7 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         unsigned long long v = 0;
         unsigned stt = 2;                          // before brick 0: an inclusive zero
         bool ready = false;
-        for (unsigned k = 0; k < LOOKBACK_LIMIT; ++k) {
+        for (unsigned k = 0; k < wait_limit; ++k) {
             if (idx >= 0) {
                 v = *((volatile unsigned long long *)(state + idx));
                 stt = (unsigned)(v >> 62);
@@ -540,7 +539,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
     launch_pdl(k_select_onepass, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
-                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask);
+                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask, A.wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -34,7 +34,6 @@ namespace sph {
 // short arrays, one CTA per array walks every tile with a running carry.
 constexpr int SCAN_T = 1024, SCAN_PER = 8, SCAN_TILE = SCAN_T * SCAN_PER;
 constexpr int SCAN_SMALL = 4 * SCAN_TILE;          // one CTA per array up to this length
-constexpr unsigned SCAN_WAIT_LIMIT = 1u << 20;
 constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62;
 
 struct ScanSet {
@@ -122,7 +121,8 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_small(ScanSet S, int n) {
 // A tile that gives up waiting for a predecessor counts it as zero (its prefixes stay in
 // [0, true prefix], so indices derived from them stay in bounds) and sets bit 0 of *err.
 __global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int ntiles,
-                                                         unsigned long long *__restrict__ state, int *err) {
+                                                         unsigned long long *__restrict__ state, int *err,
+                                                         unsigned wait_limit) {
     pdl_enter();
     __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
     __shared__ int ws[32];
@@ -144,12 +144,12 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int n
             const int idx = j - tid;
             unsigned long long w = ST_INC;   // before tile 0: an inclusive zero
             unsigned k = 0;
-            for (; k < SCAN_WAIT_LIMIT; ++k) {
+            for (; k < wait_limit; ++k) {
                 if (idx >= 0) w = *((volatile unsigned long long *)(st + idx));
                 if (__all_sync(0xffffffffu, (w >> 62) != 0)) break;
                 __nanosleep(32);
             }
-            if (k == SCAN_WAIT_LIMIT) {
+            if (k == wait_limit) {
                 gave_up = true;
                 break;
             }
@@ -179,7 +179,8 @@ size_t scan_tmp_ints(int n) {
 
 // out_k[i] = sum_{j<i} in_k[j]; *total_k = sum (device), for k <= 4 arrays of length n.
 // tmp: scan_tmp_ints(n) ints, 8-byte aligned; err (optional): bit 0 set if a look-back gave up.
-void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cudaStream_t st) {
+void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cudaStream_t st,
+                          unsigned wait_limit = SCAN_WAIT_LIMIT) {
     if (n <= 0) {
         for (int a = 0; a < k; ++a) cudaMemsetAsync(S.total[a], 0, sizeof(int), st);
         return;
@@ -191,15 +192,16 @@ void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cu
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     unsigned long long *state = reinterpret_cast<unsigned long long *>(tmp);
     cudaMemsetAsync(state, 0, sizeof(unsigned long long) * k * (ntiles + 1), st);
-    launch_pdl(k_scan_onepass, dim3(ntiles, k), SCAN_T, 0, st, S, n, ntiles, state, err);
+    launch_pdl(k_scan_onepass, dim3(ntiles, k), SCAN_T, 0, st, S, n, ntiles, state, err, wait_limit);
 }
 
-void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err) {
+void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err,
+                    unsigned wait_limit) {
     ScanSet S{};
     S.in[0] = in;
     S.out[0] = out;
     S.total[0] = total;
-    scan_exclusive_multi(S, 1, n, tmp, err, st);
+    scan_exclusive_multi(S, 1, n, tmp, err, st, wait_limit);
 }
 
 // ------------------------------------------------------------ tree build

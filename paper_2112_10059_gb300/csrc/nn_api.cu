@@ -46,6 +46,8 @@ struct sph_nn {
     size_t img_f_off[NLAYER] = {}, img_d_off[NLAYER] = {}, dw_off[NLAYER] = {};
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr, *dw = nullptr;
     size_t dw_total = 0;
+    float *wpart = nullptr;      // [WGRAD_MAX_SPLIT][rows][N] partial weight gradients (fixed-order sums)
+    float *hpart = nullptr;      // [HEAD_MAX_BLOCKS][34] partial head gradients
     uint16_t *img = nullptr;
     double *loss = nullptr;
     int *errflag = nullptr;
@@ -133,6 +135,7 @@ int wgrad_layer(sph_nn *n, int L, int batch, const uint16_t *x, const uint16_t *
     a.lg = n->lg0 - S.lvl;
     a.chunks_per_cta = 0;
     a.err = n->errflag;
+    a.part = n->wpart;
     return wgrad(a, S.ci, S.co, n->stream) ? fail(n, SPH_EINTERNAL, "unsupported layer shape") : SPH_OK;
 }
 
@@ -183,7 +186,7 @@ int backward_pass(sph_nn *n, int B, const uint16_t *x, const float *t) {
     NCK(cudaMemsetAsync(n->loss, 0, sizeof(double), st));
     const float *hw = n->params + n->head_off;
     head_loss_backward(n->f, hw, hw + HEAD_W, t, n->g_f, n->grads + n->head_off, n->loss, (int)vox(n, B, 0),
-                       LOSS_LAMBDA, LOSS_EPS, st);
+                       LOSS_LAMBDA, LOSS_EPS, st, n->hpart);
     RUN(wgrad_layer(n, C03, B, n->v0, n->g_f));
     RUN(conv_layer(n, C03, B, n->g_f, n->g_v0, nullptr, true, nullptr));
     mask_mul(n->g_v0, n->d0, n->g_d0, vox(n, B, 0) * 16, st);
@@ -305,6 +308,8 @@ int sph_nn_create(sph_nn **out, int device, void *stream, int edge, int max_batc
     A(n->m, n->P);
     A(n->v, n->P);
     A(n->dw, dwo);
+    A(n->wpart, (size_t)WGRAD_MAX_SPLIT * wgrad_rows(32) * 32);
+    A(n->hpart, (size_t)HEAD_MAX_BLOCKS * 34);
     A(n->img, io);
     A(n->loss, 1);
     A(n->errflag, 1);

@@ -39,11 +39,17 @@ struct ConvArgs {
 struct WgradArgs {
     const uint16_t *x;       // [nvox][C] layer input
     const uint16_t *dz;      // [nvox][N] gradient w.r.t. the layer's pre-activation
-    float *dw;               // [wgrad_rows(C)][N], accumulated with reductions
+    float *dw;               // [wgrad_rows(C)][N]: added into (reductions, or the fixed-order sum below)
     int nvox, lg;
     int chunks_per_cta;      // chunks of 64 voxels per CTA
     int *err;
+    // optional [WGRAD_MAX_SPLIT][wgrad_rows(C)][N] scratch: each CTA stores its partial sum there
+    // and a second kernel adds the partials into dw in a fixed order (training is then
+    // reproducible bit for bit); nullptr: the CTAs add into dw with reductions
+    float *part = nullptr;
 };
+constexpr int WGRAD_MAX_SPLIT = 160;   // voxel splits of one weight gradient (grid.y) at most
+constexpr int HEAD_MAX_BLOCKS = 8192;  // blocks of the head's loss / gradient kernel with partials
 
 // set the shared-memory limits of every instantiation (call once, outside graph capture)
 void init_attributes();
@@ -66,8 +72,11 @@ void pool_back_add_mask(const uint16_t *g_coarse, const uint16_t *add, const uin
 void head_forward(const uint16_t *f, const float *hw, const float *hb, float *y, int nvox, cudaStream_t st);
 // loss of the residual r = y0 against t and of the error head e = y1 against log(|r - t| + eps);
 // writes the masked gradient of f (BF16), accumulates the head's gradient hg[34] and the loss sum
+// hpart (optional, [HEAD_MAX_BLOCKS][34] scratch, nvox <= 256 HEAD_MAX_BLOCKS): per-block partials of the
+// head gradient summed in a fixed order instead of reductions
 void head_loss_backward(const uint16_t *f, const float *hw, const float *hb, const float *t, uint16_t *g_f,
-                        float *hg, double *loss_sum, int nvox, float lambda, float eps, cudaStream_t st);
+                        float *hg, double *loss_sum, int nvox, float lambda, float eps, cudaStream_t st,
+                        float *hpart = nullptr);
 
 // parameters: per layer w [N][27][C] then b [N] (FP32 master copy)
 void collect_grads(const float *dw, int C, int N, float *g, cudaStream_t st);

@@ -87,6 +87,8 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    unsigned select_wait = SELECT_WAIT_LIMIT;   // look-back polls of the selection (SPH_WAIT_LIMIT_SELECT)
+    int fault_alloc = 0;              // > 0: the fault_alloc-th allocation fails (SPH_FAULT=alloc[:k])
     int m2l_tiles = 2;                // tensor-core M2L in target-stationary tiles: 0 never (tiles of V
                                       // pairs), 1 always, 2 where the V lists are dense (>= 32 pairs per box)
     DevBuf b_mtg;                     // groups of the target-stationary M2L
@@ -150,8 +152,21 @@ int cuda_fail(sph_ctx *c, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
     } while (0)
 
+// Wait limit from the environment (tests lower it to make a bounded wait run out), else `dflt`.
+unsigned env_limit(const char *name, unsigned dflt) {
+    const char *e = getenv(name);
+    if (!e || !*e) return dflt;
+    char *end = nullptr;
+    const unsigned long v = strtoul(e, &end, 10);
+    return (end && *end == 0) ? (unsigned)v : dflt;
+}
+
 int ensure(sph_ctx *c, DevBuf &b, size_t bytes) {
     if (bytes <= b.cap && b.p) return SPH_OK;
+    // injected failure (SPH_FAULT=alloc[:k] at context creation): the k-th allocation that
+    // would call cudaMalloc fails as if the device were out of memory, then injection stops
+    if (c->fault_alloc > 0 && --c->fault_alloc == 0)
+        return fail(c, SPH_ENOMEM, "injected allocation failure (SPH_FAULT) for %zu bytes", bytes);
     if (b.p) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "stream sync before realloc");
@@ -234,6 +249,7 @@ int select_queue(sph_ctx *c) {
     A.i_frac = c->i_frac; A.e_frac = c->e_frac; A.e_app = c->e_app;
     A.maxes = P<unsigned>(c->b_maxes);
     A.two_pass = c->select_two_pass;
+    A.wait_limit = c->select_wait;
     A.cnt_s = P<int>(c->b_cnt); A.cnt_t = A.cnt_s + nbr;
     A.off_s = P<int>(c->b_off); A.off_t = A.off_s + nbr;
     A.totals = P<int>(c->b_tot);
@@ -1462,7 +1478,8 @@ int sph_scan_i32(int device, void *cuda_stream, int64_t n, const int32_t *in_dev
     int herr = 0;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e == cudaSuccess) {
-        scan_exclusive(in_dev, out_dev, (int)n, total_dev, tmp, st, err);
+        scan_exclusive(in_dev, out_dev, (int)n, total_dev, tmp, st, err,
+                       env_limit("SPH_WAIT_LIMIT_SCAN", SCAN_WAIT_LIMIT));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1504,6 +1521,10 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_TILES")) c->m2l_tiles = atoi(e);
+    c->select_wait = env_limit("SPH_WAIT_LIMIT_SELECT", SELECT_WAIT_LIMIT);
+    if (const char *e = getenv("SPH_FAULT")) {
+        if (strncmp(e, "alloc", 5) == 0) c->fault_alloc = e[5] == ':' ? std::max(1, atoi(e + 6)) : 1;
+    }
     if (const char *e = getenv("SPH_DEFER_SYNC")) c->defer_sync = atoi(e) != 0;
     if (const char *e = getenv("SPH_BATCH_GRAPH")) c->batch_graph = atoi(e) != 0;
     if (const char *e = getenv("SPH_EVAL_GRAPH")) c->eval_graph = atoi(e) != 0;

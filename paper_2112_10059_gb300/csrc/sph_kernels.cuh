@@ -14,6 +14,11 @@ struct KParams64 {
 };
 
 // ---------------------------------------------------------------- selection
+// Polls of a look-back before a block gives up waiting for its predecessor (selection) or a
+// tile for its predecessors (device scan) and reports it; the host may lower either (tests:
+// 0 gives up at once, deterministically).
+constexpr unsigned SELECT_WAIT_LIMIT = 1u << 22;
+constexpr unsigned SCAN_WAIT_LIMIT = 1u << 20;
 struct SelectArgs {
     int nx, ny, nz, D, brick_log2;
     const float *q, *emag;
@@ -26,6 +31,7 @@ struct SelectArgs {
     uint32_t *src_key, *src_pc, *trg_key, *trg_pc;
     float *src_q;
     uint8_t *tmask = nullptr;        // optional [nx*ny*nz]: 1 where the cell is a target
+    unsigned wait_limit = SELECT_WAIT_LIMIT;   // polls per look-back round before giving up
 };
 int select_launch(const SelectArgs &A, cudaStream_t st);
 
@@ -74,7 +80,8 @@ struct TreeArgs {
 };
 void tree_build_launch(const TreeArgs &A, cudaStream_t st);
 size_t scan_tmp_ints(int n);
-void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err = nullptr);
+void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err = nullptr,
+                    unsigned wait_limit = SCAN_WAIT_LIMIT);
 
 struct ListDev {
     int *u_cnt, *v_cnt, *w_cnt, *x_cnt;     // [nboxes]

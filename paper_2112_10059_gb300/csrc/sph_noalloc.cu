@@ -21,6 +21,7 @@
 //   * the device address of the array is looked up once per device, with that
 //     device current, by the first call made for it (cudaGetSymbolAddress); make
 //     that first call before capturing any stream into a CUDA graph.
+#include <cstdlib>
 #include <mutex>
 
 #include "sph_kernels.cuh"
@@ -101,6 +102,11 @@ extern "C" int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny,
     A.off_t = A.off_s + nbricks;
     A.src_key = src_key_dev; A.src_pc = src_pc_dev; A.src_q = src_q_dev;
     A.trg_key = trg_key_dev; A.trg_pc = trg_pc_dev;
+    if (const char *e = getenv("SPH_WAIT_LIMIT_SELECT")) {   // tests: make the look-back give up
+        char *end = nullptr;
+        const unsigned long v = strtoul(e, &end, 10);
+        if (end && *end == 0) A.wait_limit = (unsigned)v;
+    }
     int rc = SPH_OK;
     if (sph::select_launch(A, st) != 0) rc = SPH_ECUDA;
     // (sources, targets, gave-up flag): copied after the selection kernel has completed, so the

@@ -173,6 +173,26 @@ def test_training_reduces_loss(sur):
     assert last < 0.5 * first, (first, last)
 
 
+def test_training_is_reproducible(sur):
+    """The weight and head gradients are summed in a fixed order (per-CTA partials, then an
+    ordered sum), so two trainings from the same initial weights on the same data end with the
+    same weights, bit for bit; at 64^3 the weight gradient spans many voxel splits per layer."""
+    edge, batch = 64, 2
+    x, _ = _net_inputs(edge, batch, 12)
+    t = 0.3 * x[..., 0] - 0.2 * x[..., 1] * x[..., 2]
+    xd, td = _to_dev_bf16(x), _to_dev_f32(t)
+    finals = []
+    for _ in range(2):
+        net = sur.Net(edge=edge, max_batch=batch, seed=3)
+        for _ in range(12):
+            net.train_step(xd, td, batch, 1e-3, want_loss=False)
+        finals.append(net.get_params())
+        g = net.get_grads()
+        net.close()
+    assert np.array_equal(finals[0], finals[1])
+    assert np.any(g != 0)
+
+
 def test_bad_arguments(sur):
     import torch
     with pytest.raises(Exception):
