@@ -330,7 +330,7 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(sph, torch, dev, stream, args, prec):
+def run_batch(sph, torch, dev, stream, args, prec, flush=None):
     """24 independent snapshots through eval_sph_batch (autotuned leaf sizes), against the same
     snapshots evaluated one eval_sph call at a time on per-snapshot contexts."""
     import oracle
@@ -346,7 +346,8 @@ def run_batch(sph, torch, dev, stream, args, prec):
     for _ in range(2):
         sph.eval_sph_batch(ctx, bps)
     torch.cuda.synchronize()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if flush is None:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     wall, dev_ms, nt = [], [], 0
     for k in range(max(1, args.batch_steps)):
         flush.fill_(float(k))
@@ -404,13 +405,57 @@ def run_batch(sph, torch, dev, stream, args, prec):
     for c in seq_ctx:
         c.close()
     ctx.close()
+    stress = run_stress(sph, torch, dev, stream, args, prec, flush)
     return {"workload": "24 streamer snapshots, grids %s, pressures %s Torr, i_frac 1e-5..1e-3, e_frac 0.05..0.2, "
                         "seed 1003" % (sorted({p.nx for p in probs}), sorted({int(p.p_torr) for p in probs})),
             "value": nt / bw, "unit": "targets/s", "ms_per_batch_wall": 1e3 * bw, "ms_per_batch_gpu": bd,
             "n_targets": nt, "gpu_launches": launches, "graph_captured": True,
             "sequential_ms_wall": 1e3 * sq, "speedup_vs_sequential": sq / bw,
             "max_rel_diff_vs_sequential": same, "first_call_s": first_s, "leaf_sizes": leaf,
-            "rel_l2_sampled_smallest3": errs, "l2_flush": "256 MiB write before each batch"}
+            "rel_l2_sampled_smallest3": errs, "l2_flush": "256 MiB write before each batch", "stress": stress}
+
+
+def run_stress(sph, torch, dev, stream, args, prec, flush):
+    """The wide-channel batch (channel radius 0.2 .. 1 mm, source threshold 1e-5; about three
+    million sources in its last, 256^3 snapshot) in one eval_sph_batch, leaf size and M2L form
+    autotuned; accuracy on 200 sampled targets of every snapshot."""
+    import oracle
+    probs = si.stress_batch(4)
+    bps = [sph.BatchProblem.from_problem(p, device=dev) for p in probs]
+    ctx = sph.Context(dev.index or 0, stream)
+    sph.set_criteria(ctx, 0.0, 0.0, 0.0, 1, 0, prec)
+    sph.set_far_field(ctx, sph.FAR_CHEBYSHEV, args.order)
+    t0 = time.perf_counter()
+    sph.eval_sph_batch(ctx, bps)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    sph.eval_sph_batch(ctx, bps)
+    dev_ms = []
+    for k in range(3):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = sph.eval_sph_batch(ctx, bps, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    rng = np.random.default_rng(29)
+    snaps = []
+    for p, bp in zip(probs, bps):
+        J, T = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+        samp = np.sort(rng.choice(T, size=min(T.size, 200), replace=False))
+        a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+        ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+        S = bp.out.cpu().numpy().astype(np.float64)[samp]
+        snaps.append({"name": p.name, "n_sources": int(J.size), "n_targets": int(T.size),
+                      "rel_l2_sampled": oracle.rel_l2(S, ref), "max_rel_sampled": oracle.max_rel(S, ref, 1e-3)})
+    ctx.close()
+    md = statistics.median(dev_ms)
+    return {"workload": "4 wide-channel snapshots (128^3, 192^3, 256^3, 256^3; channel radius 0.2 .. 1 mm, "
+                        "i_frac 1e-5, seed 1006), leaf size and M2L form autotuned",
+            "ms_per_batch_gpu": md, "targets_per_s": int(st.n_targets) / (md * 1e-3),
+            "n_sources": int(st.n_sources), "n_targets": int(st.n_targets), "first_call_s": first_s,
+            "snapshots": snaps}
 
 
 def run_surrogate(sph, torch, dev, stream, args, peaks):
@@ -896,7 +941,7 @@ def main():
 
     batch = None
     if not args.no_batch:
-        batch = run_batch(sph, torch, dev, stream, args, prec)
+        batch = run_batch(sph, torch, dev, stream, args, prec, flush)
 
     sweep = run_sweep(sph, torch, dev, stream, args) if args.sweep else None
 

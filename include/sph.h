@@ -107,6 +107,9 @@ typedef struct sph_stats {
     int64_t n_w_skipped;       /* (target, W box) pairs skipped by strategy 3 (sph_set_skip_ratio) */
     int32_t l2lp_fused;        /* 1 if the deepest level's L2L and L2P ran as one kernel (leaves of edge 4) */
     float ms_l2lp;             /* its GPU milliseconds (inside ms_l2p), 0 if not fused */
+    int32_t m2l_tiles;         /* tensor-core M2L form of this eval: 1 target-stationary tiles (dense V
+                                  lists), 0 tiles of V pairs; chosen by V-pair density, or by timing both
+                                  when the leaf size is autotuned (set_criteria leaf_size 0) */
 } sph_stats;
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`

@@ -52,7 +52,7 @@ class Stats(ctypes.Structure):
                 ("ms_near", ctypes.c_float), ("ms_total", ctypes.c_float), ("n_launches", ctypes.c_int64),
                 ("far_method", ctypes.c_int32), ("far_order", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("near_table", ctypes.c_int32), ("n_w_skipped", ctypes.c_int64), ("l2lp_fused", ctypes.c_int32),
-                ("ms_l2lp", ctypes.c_float)]
+                ("ms_l2lp", ctypes.c_float), ("m2l_tiles", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

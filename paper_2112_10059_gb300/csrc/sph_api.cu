@@ -92,6 +92,8 @@ struct sph_ctx {
     int m2l_tiles = 2;                // tensor-core M2L in target-stationary tiles: 0 never (tiles of V
                                       // pairs), 1 always, 2 where the V lists are dense (>= 32 pairs per box)
     DevBuf b_mtg;                     // groups of the target-stationary M2L
+    int m2l_form = -1;                // autotuned M2L form for this eval (-1: the density rule)
+    bool m2l_tiles_used = false;      // the last eval ran the target-stationary M2L
     bool l2lp_fused = true;           // deepest level of edge-4 leaves: L2L and L2P in one tensor-core kernel
     bool l2lp_used = false;           // the last eval ran the fused kernel
     bool defer_sync = true;           // fixed leaf size: one host sync for selection, tree and list counts
@@ -684,7 +686,10 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         if (tm) tm->mark_at(5, c->stream);
         // target-stationary tiles pay a round per (group, offset) whatever the number of pairs in
         // it, so they are taken where the lists are dense (uniform trees), the pair tiles elsewhere
-        const bool tiles = S.tc && (c->m2l_tiles == 1 || (c->m2l_tiles == 2 && (int64_t)nV >= 32ll * nb));
+        const bool tiles = S.tc && (c->m2l_tiles == 1 ||
+                                    (c->m2l_tiles == 2 && (c->m2l_form >= 0 ? c->m2l_form == 1
+                                                                            : (int64_t)nV >= 32ll * nb)));
+        c->m2l_tiles_used = tiles;
         if (tiles) {
             // w_cnt[36]: number of groups, w_cnt[37]: the work counter (zeroed with the others)
             if (nV > 0) {
@@ -809,6 +814,7 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
     stats->leaf_size = c->leaf_eff;
     stats->near_table = c->near_table ? 1 : 0;
     stats->l2lp_fused = c->l2lp_used ? 1 : 0;
+    stats->m2l_tiles = c->m2l_tiles_used ? 1 : 0;
     if (c->b_skip.p) {
         unsigned long long k = 0;
         if (cudaMemcpy(&k, c->b_skip.p, sizeof k, cudaMemcpyDeviceToHost) == cudaSuccess) stats->n_w_skipped = (int64_t)k;
@@ -833,7 +839,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(c->lvl_src.data(), c->lvl_src.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
-                          c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, c->m2l_tiles,
+                          c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, c->m2l_tiles, c->m2l_form,
                           (int64_t)reinterpret_cast<uintptr_t>(out)};
     put(sc, sizeof sc);
     return v;
@@ -1011,10 +1017,63 @@ int resolve_near(sph_ctx *c, float *out) {
     return SPH_OK;
 }
 
+// Tensor-core M2L form for this evaluation when the leaf size is autotuned (set_criteria
+// leaf_size 0) and the form is left to the library: the faster of the tiles of V pairs and the
+// target-stationary tiles, timed like the leaf size over the FMM passes and cached per problem
+// class, leaf size and near-field form.  Otherwise the density rule of fmm_queue decides.
+int fmm_after_select(sph_ctx *c, float *out, PhaseTimer *tm);
+int resolve_m2l(sph_ctx *c, float *out) {
+    c->m2l_form = -1;
+    if (c->leaf_size != 0 || c->m2l_tiles != 2 || c->m2l_prec != SPH_M2L_BF16X3) return SPH_OK;
+    const std::string key = tune_key(c) + "|m2l|" + std::to_string(c->leaf_eff) + "|" + std::to_string(c->near_table);
+    std::map<std::string, int> &cache = c->tune_owner ? c->tune_owner->tune_cache : c->tune_cache;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        c->m2l_form = it->second;
+        return SPH_OK;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int choice = 0;
+    for (int form = 0; form < 2; ++form) {
+        c->m2l_form = form;
+        int r = fmm_after_select(c, out, nullptr);
+        float tot = 0.f;
+        for (int rep = 0; rep < 2 && !r; ++rep) {
+            CK(cudaEventRecord(e0, c->stream));
+            r = fmm_after_select(c, out, nullptr);
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (r) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r;
+        }
+        if (tot < best) {
+            best = tot;
+            choice = form;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
+    cache[key] = choice;
+    c->m2l_form = choice;
+    return SPH_OK;
+}
+
+
 int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     PhaseTimer tm;
     tm.start(stats != nullptr, c->stream);
     c->launches = 0;
+    c->m2l_form = -1;                 // the density rule unless the autotuner picks the form below
     int r = check_previous_tc(c);
     if (r) return r;
     if (c->defer_sync && c->leaf_size != 0 && c->near_mode != SPH_NEAR_AUTO) {
@@ -1078,6 +1137,8 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         c->leaf_eff = c->leaf_size;
     }
     r = resolve_near(c, out);
+    if (r) return r;
+    r = resolve_m2l(c, out);
     if (r) return r;
     r = fmm_after_select(c, out, &tm);
     if (r) return r;
@@ -1213,6 +1274,7 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
         }
         {
             int r = resolve_near(sub, probs[i].s_dev);
+            if (!r) r = resolve_m2l(sub, probs[i].s_dev);
             if (r) return sub_fail(c, sub, r, i);
         }
     }

@@ -256,6 +256,27 @@ def snapshot_batch(count=24, seed=1003, sizes=(64, 96, 128, 192, 256), pressures
     return out
 
 
+def stress_batch(count=4, seed=1006, sizes=(128, 192, 256, 256), pressures=(76.0, 380.0, 760.0)):
+    """Snapshots with wide channels (many sources): the channel radius steps log-uniformly from
+    0.2 to 1.0 mm over the batch (snapshot k of n: 0.2 mm x 5^(k / (n - 1))), its length is
+    U[0.6, 0.8] cm and the source threshold 1e-5, so that the last snapshot (256^3, 1 mm) selects
+    about three million sources.  Grid edges from ``sizes`` in order, pressures and target
+    thresholds drawn as in :func:`snapshot_batch`."""
+    u = uniform01(seed, 8 * count).reshape(count, 8)
+    out = []
+    for k in range(count):
+        n = int(sizes[min(k, len(sizes) - 1)])
+        chan = 0.6 + 0.2 * float(u[k, 1])
+        p = float(pressures[min(int(u[k, 2] * len(pressures)), len(pressures) - 1)])
+        radius = float(0.02 * 5.0 ** (k / max(count - 1, 1)))
+        e_frac = 0.05 + 0.15 * float(u[k, 4])
+        head = (0.5 + 0.1 * (u[k, 5] - 0.5), 0.5 + 0.1 * (u[k, 6] - 0.5), 0.5 - chan / 2.0)
+        out.append(streamer(n=n, box=1.0, p_torr=p, chan_len=chan, i_frac=1e-5, e_frac=e_frac,
+                            targets_all=False, seed=seed * 1000 + k, head=head, chan_radius=radius,
+                            name="stress%02d_n%d_p%d_r%.2fmm" % (k, n, int(p), 10 * radius)))
+    return out
+
+
 def streamer_cloud(n=256, box=1.5, p_torr=760.0, i_frac=1e-4, seed=1004):
     """Streamer head approaching a plasma cloud: n^3 grid in a 1.5 cm cube at 760 Torr.
 

@@ -162,3 +162,52 @@ def test_autotuned_leaf_size(sph):
     _, out2, st2 = sph.solve(p, ctx, m2l_precision=1, leaf_size=0, stats=True)
     assert st2.leaf_size == leaf
     _close(out2.cpu().numpy().astype(np.float64), S, "autotune cache")
+
+
+def test_stress_batch_millions_of_sources(sph):
+    """The wide-channel batch (channel radius 0.2 .. 1 mm, source threshold 1e-5; the last
+    snapshot selects about three million sources on a 256^3 grid) in one eval_sph_batch with the
+    leaf size and the M2L form autotuned: every snapshot selects the oracle's sets (counted) and
+    passes the gate on 200 seeded sampled targets, zero at sampled non-targets."""
+    import torch
+    probs = si.stress_batch(4)
+    ctx = sph.Context(0)
+    _configure(sph, ctx, 0, sph.M2L_BF16X3)
+    bps = [sph.BatchProblem.from_problem(p) for p in probs]
+    outs, st = sph.eval_sph_batch(ctx, bps, stats=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(29)
+    ns_total = 0
+    for p, o in zip(probs, outs):
+        S = o.cpu().numpy().astype(np.float64)
+        J, T = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+        ns_total += J.size
+        samp = np.sort(rng.choice(T, size=min(T.size, 200), replace=False))
+        a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+        ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, J, samp)
+        assert oracle.rel_l2(S[samp], ref) <= REL_L2, p.name
+        assert oracle.max_rel(S[samp], ref, 1e-3) <= MAX_REL, p.name
+        others = np.setdiff1d(rng.choice(p.ncell, size=2000, replace=False), T)
+        assert np.all(S[others] == 0.0), p.name
+        assert np.count_nonzero(S) <= T.size, p.name
+    assert st.n_sources == ns_total
+    assert ns_total > 2_500_000
+    ctx.close()
+
+
+def test_m2l_form_autotuned(sph):
+    """With the leaf size autotuned the M2L form is timed too (tiles of V pairs against
+    target-stationary tiles); whichever is kept, the result passes the oracle gate and the
+    choice is cached for the problem class."""
+    p = si.streamer(n=64, box=1.0, chan_len=0.5, i_frac=0.0, targets_all=True, seed=42, name="tune64")
+    ctx = sph.Context(0)
+    _, out, st = sph.solve(p, ctx, m2l_precision=sph.M2L_BF16X3, leaf_size=0, stats=True)
+    assert st.m2l_tiles in (0, 1)
+    _, out2, st2 = sph.solve(p, ctx, m2l_precision=sph.M2L_BF16X3, leaf_size=0, stats=True)
+    assert st2.m2l_tiles == st.m2l_tiles and st2.leaf_size == st.leaf_size
+    S = out2.cpu().numpy().astype(np.float64)
+    samp = np.sort(np.random.default_rng(4).choice(p.ncell, 2000, replace=False)).astype(np.int32)
+    a, b = oracle.alpha_beta(p.pO2_torr, p.chi_min, p.chi_max)
+    ref = oracle.sph(p.nx, p.ny, p.nz, p.h, a, b, p.q, p.source_scale, np.arange(p.ncell, dtype=np.int32), samp)
+    assert oracle.rel_l2(S[samp], ref) <= REL_L2
+    ctx.close()
