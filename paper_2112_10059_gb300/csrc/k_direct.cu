@@ -16,13 +16,13 @@ constexpr int DS = 512;   // sources per shared-memory tile
 
 __global__ void __launch_bounds__(DT) k_direct_f32(const uint32_t *__restrict__ src_pc,
                                                    const float *__restrict__ src_q, float wscale, int ns,
-                                                   const uint32_t *__restrict__ trg_pc, int nt,
+                                                   const uint32_t *__restrict__ trg_key, int nt,
                                                    KParams kp, int self_mode, int nx, int ny,
                                                    float *__restrict__ out_dense) {
     __shared__ uint32_t sp[DS];
     __shared__ float sw[DS];
     int t = blockIdx.x * DT + threadIdx.x;
-    uint32_t tp = t < nt ? trg_pc[t] : 0xffffffffu;
+    uint32_t tp = t < nt ? key_pc(trg_key[t]) : 0xffffffffu;
     int ti = pc_i(tp), tj = pc_j(tp), tk = pc_k(tp);
     float acc = 0.0f;
     for (int s0 = 0; s0 < ns; s0 += DS) {
@@ -47,13 +47,13 @@ __global__ void __launch_bounds__(DT) k_direct_f32(const uint32_t *__restrict__ 
 
 __global__ void __launch_bounds__(DT) k_direct_f64(const uint32_t *__restrict__ src_pc,
                                                    const float *__restrict__ src_q, int ns,
-                                                   const uint32_t *__restrict__ trg_pc, int nt,
+                                                   const uint32_t *__restrict__ trg_key, int nt,
                                                    KParams64 kp, int self_mode, int nx, int ny,
                                                    double *__restrict__ out_dense) {
     __shared__ uint32_t sp[DS];
     __shared__ float sq[DS];
     int t = blockIdx.x * DT + threadIdx.x;
-    uint32_t tp = t < nt ? trg_pc[t] : 0xffffffffu;
+    uint32_t tp = t < nt ? key_pc(trg_key[t]) : 0xffffffffu;
     int ti = pc_i(tp), tj = pc_j(tp), tk = pc_k(tp);
     double acc = 0.0, comp = 0.0;
     for (int s0 = 0; s0 < ns; s0 += DS) {
@@ -89,10 +89,10 @@ int direct_launch(const DirectArgs &A, cudaStream_t st) {
     if (A.nt == 0) return 0;
     int grid = (A.nt + DT - 1) / DT;
     if (A.fp64)
-        k_direct_f64<<<grid, DT, 0, st>>>(A.src_pc, A.src_q, A.ns, A.trg_pc, A.nt, A.kp64, A.self_mode,
+        k_direct_f64<<<grid, DT, 0, st>>>(A.src_pc, A.src_q, A.ns, A.trg_key, A.nt, A.kp64, A.self_mode,
                                           A.nx, A.ny, (double *)A.out);
     else
-        k_direct_f32<<<grid, DT, 0, st>>>(A.src_pc, A.src_q, A.wscale, A.ns, A.trg_pc, A.nt, A.kp, A.self_mode,
+        k_direct_f32<<<grid, DT, 0, st>>>(A.src_pc, A.src_q, A.wscale, A.ns, A.trg_key, A.nt, A.kp, A.self_mode,
                                           A.nx, A.ny, (float *)A.out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

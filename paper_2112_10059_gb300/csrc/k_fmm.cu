@@ -444,7 +444,7 @@ __device__ __forceinline__ void leaf_box(const FmmDev &F, int b, float *__restri
     for (int t0 = tb; t0 < te; t0 += LT) {
         int t = t0 + threadIdx.x;
         bool act = t < te;
-        uint32_t tp = act ? F.trg_pc[t] : 0u;
+        uint32_t tp = act ? key_pc(F.trg_key[t]) : 0u;
         int ti = pc_i(tp), tj = pc_j(tp), tk = pc_k(tp);
         float tx, ty, tz;
         rel_cell(ti, tj, tk, bx, by, bz, size, hh, tx, ty, tz);
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                     const int t = tb + c * 32 + lane;
                     float far = 0.f;
                     if (t < te) {
-                        const uint32_t tp = F.trg_pc[t];
+                        const uint32_t tp = key_pc(F.trg_key[t]);
                         far = out[(int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp))];
                     }
                     sest[sl] = far + usum[c][lane];
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                     int slot = 0;
                     for (int c = warp / G; c < nch; c += groups, ++slot) {
                         const int t = tb + c * 32 + lane;
-                        const uint32_t tp = t < te ? F.trg_pc[t] : 0u;
+                        const uint32_t tp = t < te ? key_pc(F.trg_key[t]) : 0u;
                         if (pass == 1 && skip3) {
                             // W box by W box: a lane drops box j when G(d_min) * sum(I_h) < r_s * S_est
                             const int tx = pc_i(tp), ty = pc_j(tp), tz = pc_k(tp);
@@ -1064,7 +1064,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
         for (int c = warp / G; c < nch && slot < 2; c += groups, ++slot) {
             const int t = tb + c * 32 + lane;
             if (t >= te) continue;
-            const uint32_t tp = F.trg_pc[t];
+            const uint32_t tp = key_pc(F.trg_key[t]);
             atomicAdd(out + (int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
                       acc[slot]);
         }

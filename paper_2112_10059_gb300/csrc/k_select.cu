@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(512) k_select_brick(
         }
         if (my_bits[u] & 2) {
             trg_key[pt] = key;
-            trg_pc[pt] = pc;
+            if (trg_pc) trg_pc[pt] = pc;
             ++pt;
         }
     }
@@ -493,14 +493,14 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         }
         if (my_bits[u] & 2) {
             st_key[lt + (lt >> 5)] = key;
-            st_pc[lt + (lt >> 5)] = pc;
+            if (trg_pc) st_pc[lt + (lt >> 5)] = pc;
             ++lt;
         }
     }
     __syncthreads();
     for (int i = tid; i < (int)agg_t; i += blockDim.x) {
         trg_key[pre_t + i] = st_key[i + (i >> 5)];
-        trg_pc[pre_t + i] = st_pc[i + (i >> 5)];
+        if (trg_pc) trg_pc[pre_t + i] = st_pc[i + (i >> 5)];
     }
 }
 

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) k_l2p_gemm(FmmDev F, int level, int box_b
         for (int t = T.b_tb[b] + lane; t < T.b_te[b]; t += 32) {
             int m = (int)(F.trg_key[t] & lmask) - i0;
             if (m < 0 || m >= TM) continue;
-            uint32_t pc = F.trg_pc[t];
+            uint32_t pc = key_pc(F.trg_key[t]);
             out[(int64_t)pc_i(pc) + (int64_t)F.nx * ((int64_t)pc_j(pc) + (int64_t)F.ny * pc_k(pc))] = Cs[m][c];
         }
     }

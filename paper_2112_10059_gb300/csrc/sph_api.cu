@@ -243,7 +243,6 @@ int select_queue(sph_ctx *c) {
     ENS(c->b_spc, ncell * sizeof(uint32_t));
     ENS(c->b_sq, ncell * sizeof(float));
     ENS(c->b_tkey, ncell * sizeof(uint32_t));
-    ENS(c->b_tpc, ncell * sizeof(uint32_t));
     ENS(c->b_tmask, ncell);
     SelectArgs A;
     A.nx = c->nx; A.ny = c->ny; A.nz = c->nz; A.D = D; A.brick_log2 = b;
@@ -256,7 +255,7 @@ int select_queue(sph_ctx *c) {
     A.off_s = P<int>(c->b_off); A.off_t = A.off_s + nbr;
     A.totals = P<int>(c->b_tot);
     A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
-    A.trg_key = P<uint32_t>(c->b_tkey); A.trg_pc = P<uint32_t>(c->b_tpc);
+    A.trg_key = P<uint32_t>(c->b_tkey);   // targets' cells follow from their keys: no packed copy
     A.tmask = P<uint8_t>(c->b_tmask);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
     c->launches += 2;
@@ -598,7 +597,6 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     F.L = list_dev(c);
     F.O = ops_dev(c);
     F.src_pc = P<uint32_t>(c->b_spc);
-    F.trg_pc = P<uint32_t>(c->b_tpc);
     F.trg_key = P<uint32_t>(c->b_tkey);
     F.src_q = P<float>(c->b_sq);
     F.wscale = (float)(c->source_scale * c->h * c->h * c->h);
@@ -1795,7 +1793,7 @@ int eval_direct(sph_ctx *c, int fp64, void *s_dev) {
     A.src_q = P<float>(c->b_sq);
     A.wscale = (float)(c->source_scale * c->h * c->h * c->h);
     A.ns = (int)c->ns;
-    A.trg_pc = P<uint32_t>(c->b_tpc);
+    A.trg_key = P<uint32_t>(c->b_tkey);
     A.nt = (int)c->nt;
     A.kp = make_kp(c);
     double L = std::log(c->beta / c->alpha);
@@ -1815,19 +1813,22 @@ int sph_get_selection(sph_ctx *c, int32_t *src_host, int64_t *n_src, int32_t *tr
     if (n_trg) *n_trg = c->nt;
     if (!src_host && !trg_host) return SPH_OK;
     CK(cudaStreamSynchronize(c->stream));
-    auto fetch = [&](DevBuf &pcb, int64_t n, int32_t *dst) -> int {
+    // packed cells (sources) or Morton keys (targets, whose cells follow from the key)
+    auto fetch = [&](DevBuf &pcb, int64_t n, int32_t *dst, bool keys) -> int {
         std::vector<uint32_t> pc(n);
         if (n) {
             cudaError_t e = cudaMemcpy(pc.data(), pcb.p, n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) return cuda_fail(c, e, "selection read-back");
         }
-        for (int64_t i = 0; i < n; ++i)
-            dst[i] = pc_i(pc[i]) + c->nx * (pc_j(pc[i]) + c->ny * pc_k(pc[i]));
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t p = keys ? key_pc(pc[i]) : pc[i];
+            dst[i] = pc_i(p) + c->nx * (pc_j(p) + c->ny * pc_k(p));
+        }
         std::sort(dst, dst + n);
         return SPH_OK;
     };
-    if (src_host) { int r = fetch(c->b_spc, c->ns, src_host); if (r) return r; }
-    if (trg_host) { int r = fetch(c->b_tpc, c->nt, trg_host); if (r) return r; }
+    if (src_host) { int r = fetch(c->b_spc, c->ns, src_host, false); if (r) return r; }
+    if (trg_host) { int r = fetch(c->b_tkey, c->nt, trg_host, true); if (r) return r; }
     return SPH_OK;
 }
 

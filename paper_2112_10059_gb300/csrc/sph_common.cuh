@@ -84,6 +84,13 @@ __host__ __device__ __forceinline__ uint32_t pack_ijk(uint32_t i, uint32_t j, ui
     return i | (j << 10) | (k << 20);
 }
 __host__ __device__ __forceinline__ int pc_i(uint32_t p) { return (int)(p & 1023u); }
+// packed cell of a point from its Morton key at the grid's depth (the key interleaves the
+// cell's three indices, so this is the same cell the selection packed)
+__host__ __device__ __forceinline__ uint32_t key_pc(uint32_t key) {
+    uint32_t i, j, k;
+    demorton3(key, i, j, k);
+    return pack_ijk(i, j, k);
+}
 __host__ __device__ __forceinline__ int pc_j(uint32_t p) { return (int)((p >> 10) & 1023u); }
 __host__ __device__ __forceinline__ int pc_k(uint32_t p) { return (int)((p >> 20) & 1023u); }
 

@@ -28,7 +28,8 @@ struct SelectArgs {
     int *cnt_s, *cnt_t, *off_s, *off_t;   // [nbricks]
     int *totals;                     // [3] Ns, Nt, error flag (look-back gave up)
     int two_pass = 0;                // 1: count pass + scan + emit pass instead of the one-pass kernel
-    uint32_t *src_key, *src_pc, *trg_key, *trg_pc;
+    uint32_t *src_key, *src_pc, *trg_key;
+    uint32_t *trg_pc = nullptr;      // optional: targets' packed cells (key_pc of trg_key)
     float *src_q;
     uint8_t *tmask = nullptr;        // optional [nx*ny*nz]: 1 where the cell is a target
     unsigned wait_limit = SELECT_WAIT_LIMIT;   // polls per look-back round before giving up
@@ -41,7 +42,7 @@ struct DirectArgs {
     const float *src_q;
     float wscale;
     int ns;
-    const uint32_t *trg_pc;
+    const uint32_t *trg_key;         // Morton keys of the targets (cells by key_pc)
     int nt;
     KParams kp;
     KParams64 kp64;
@@ -187,7 +188,7 @@ struct FmmDev {
     TreeDev T;
     ListDev L;
     OpsDev O;
-    const uint32_t *src_pc, *trg_pc, *trg_key;
+    const uint32_t *src_pc, *trg_key;   // targets' cells from their keys (key_pc)
     const float *src_q;
     int leaf_l2p_done;   // 1: k_leaf adds near-field terms only where a table L2P already wrote S
     int p2p_separate;    // 1: the U-list near field runs in k_p2p (after k_leaf), not in k_leaf
