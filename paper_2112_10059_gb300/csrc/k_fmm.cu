@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(256) k_l2p_sep(FmmDev F, int level, const int 
                                                  const int *__restrict__ count, int band, float *__restrict__ out) {
     pdl_enter();
     const int box_count = *count;
+    if ((int)blockIdx.x >= box_count) return;   // a CTA without a box of the list (see k_l2p_sep_small)
     extern __shared__ float sm[];
     const int p = F.O.order, n = F.O.n, np = F.O.npad;
     const int e = 1 << (F.D - level);
@@ -667,6 +668,10 @@ __global__ void __launch_bounds__(SEPW_WARPS * 32) k_l2p_sep_small(FmmDev F, int
                                                                    float *__restrict__ out) {
     pdl_enter();
     const int box_count = *count;
+    // the launch is sized by the level's box count; the leaves with targets are often far fewer
+    // (none at all on a level above a fused deepest one): CTAs without a box leave before the
+    // basis set-up
+    if ((int)blockIdx.x * SEPW_WARPS >= box_count) return;
     __shared__ float Sb[SEPW_MAXP * SEPW_MAXE];                                  // [p][e]
     __shared__ __align__(16) float sd[SEPW_WARPS][SEPW_NP];
     __shared__ float T1[SEPW_WARPS][SEPW_MAXP * SEPW_MAXP * SEPW_MAXE];          // [p*p][e]
