@@ -173,7 +173,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of k_l2lp_tc); valid for that workload and the
 # kernel as profiled (None once the kernel has changed since).
-NCU_TRAFFIC = {"l2lp": (160.919040 + 39.509248) * 1e6}
+NCU_TRAFFIC = {}
 
 
 def pipe_peaks(sph, dev, stream, f_mhz_nominal=2070.0):
@@ -196,14 +196,18 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
                      3 x 2 x 128^2);
       l2l  (tensor): 2 n^2 flops per child box with targets below level 2 (levels the separate
                      L2L kernels run: all but the deepest one when that level is fused);
-      l2lp (HBM, k_l2lp_tc): fused L2L + L2P of the deepest level: the parents' and the leaves'
-                  local expansions read (npad x 4 B each) + S written (4 B per target there);
+      l2lp (HBM, k_l2lp_tc): fused L2L + L2P of the deepest level: the parents' local expansions
+                  and the own local terms of the leaves that have V or X entries read (npad x 4 B
+                  each; a leaf without them has none: its expansion is its parent's, translated)
+                  + S written (4 B per target there);
       l2p  (HBM): the other leaves' local expansions read (npad x 4 B per leaf with targets) + S
                   written (4 B per target) -- only where such leaves exist;
       near (MUFU, k_p2p): P2P pairs + M2P evaluations, 2 ex2 + 1 rsqrt each, against the measured
                   ex2 and rsqrt rates;
-      select (HBM, k_grid_max + k_select_onepass): 16 B per cell (q and |E| read by the maxima
-                  pass and again by the rules) + 4 B per selected index (sources and targets).
+      select (HBM, k_brick_stats + k_select_onepass): 8 B per cell (q and |E| read once) + 4 B
+                  per selected index (sources and targets) -- the minimum of the operation: the
+                  maxima pass reads every cell, the rules re-read only the bricks that the
+                  maxima pass's per-brick statistics leave undecided.
     Times are the medians of the library's CUDA-event phase timers; the step's dominant single
     kernel is the entry with the longest time among those timed as one kernel."""
     order = order or args.order
@@ -250,7 +254,11 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
     ms_lp = med("ms_l2lp") if fused else 0.0
     if fused:
         n_par = int(np.sum((lev == lmax - 1) & ~tree["leaf"] & (ntb > 0)))
-        n_deep = int(np.sum(leaf_t & deep))
+        terms = np.zeros(lev.size, bool)
+        for key in ("V", "X"):
+            if len(tree.get(key, ())):
+                terms[np.asarray(tree[key])[:, 0]] = True
+        n_deep = int(np.sum(leaf_t & deep & terms))
         nt_deep = int(np.sum(ntb[leaf_t & deep]))
         add("l2lp", "k_l2lp_tc", True, "hbm", 4.0 * npad * (n_par + n_deep) + 4.0 * nt_deep, "bytes", ms_lp, hbm,
             "GB/s", hbm_basis, traffic=NCU_TRAFFIC.get("l2lp") if traffic_ok else None)
@@ -260,7 +268,7 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
     add("near", "k_p2p", True, "alu", float(p2p + m2p), "kernel-evals", med("ms_near"), mufu_evals, "evals/s",
         "MUFU: 2 ex2 + 1 rsqrt per evaluation at the measured %.3g ex2/s and %.3g rsqrt/s (%s)"
         % (pipes["ex2_per_s"], pipes["rsqrt_per_s"], pipes["source"]))
-    add("select", "k_grid_max + k_select_onepass", False, "hbm", 16.0 * ncell + 4.0 * (nt + ns),
+    add("select", "k_brick_stats + k_select_onepass", False, "hbm", 8.0 * ncell + 4.0 * (nt + ns),
         "bytes", med("ms_select"), hbm, "GB/s", hbm_basis)
     return out
 

@@ -234,6 +234,12 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
         float4 *u = reinterpret_cast<float4 *>(F.ueq + (size_t)b * F.O.npad);
         for (int j = 0; j < F.O.npad / 4; ++j) u[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    // deepest level under the fused L2L + L2P: only the rows that M2L / P2L add into are cleared
+    if (F.d_sparse_from >= 0 && b >= F.d_sparse_from &&
+        (F.L.v_off[b + 1] != F.L.v_off[b] || F.L.x_off[b + 1] != F.L.x_off[b])) {
+        float4 *d = reinterpret_cast<float4 *>(F.dchk + (size_t)b * F.O.npad);
+        for (int j = 0; j < F.O.npad / 4; ++j) d[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     // per level, the leaves with targets (the separable L2P walks these only)
     const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr;
     i = warp_append(act, l2p, F.l2p_cnt + l);

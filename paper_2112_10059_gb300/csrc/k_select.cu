@@ -2,10 +2,12 @@
 // and the electric-field target rule of Section 5) as a GPU stream compaction
 // that emits the selected cells directly in Morton order.
 //
-// Pass 1 (k_grid_max): max q and max |E| over all cells (NaN ignored).
-// Default: k_select_onepass (below) does count, offsets and emit in one pass over the
-// grid with a decoupled look-back across bricks.  The two-pass form that follows is kept
-// as a reference:
+// Pass 1 (k_brick_stats, bricks of 16^3 cells): max q and max |E| over all cells (NaN
+// ignored) and, per brick, the largest q, the smallest and largest |E| and whether an |E| is
+// NaN.  Default: k_select_onepass (below) does count, offsets and emit in one pass over the
+// grid with a decoupled look-back across bricks; a whole brick that those statistics decide
+// (no source, and every cell or no cell a target) is emitted without reading it again.
+// The two-pass form that follows (after k_grid_max, the maxima alone) is kept as a reference:
 // Pass 2 (k_select_count): per 16^3 brick (a Morton-contiguous key range),
 //         count selected sources / targets.
 // Pass 3 (k_scan_bricks): exclusive scan of the brick counts.
@@ -270,6 +272,183 @@ __device__ __forceinline__ unsigned long long pack_state(unsigned st, unsigned n
     return ((unsigned long long)st << 62) | ((unsigned long long)ns << 31) | (unsigned long long)nt;
 }
 
+// Per brick of 16^3 cells (one CTA of 256 threads): bstat[brick] = (max q, min |E|, max |E|,
+// 1 if an |E| is NaN else 0) over the brick's cells inside the grid, NaN values left out of the
+// extremes (q or e nullptr: that part is not computed); the brick's maxima go into `out` (ordered
+// uints, as k_grid_max).  Four threads per row of 16 cells, each one 16-byte load per array and
+// row, four rows per thread: all eight loads in flight at once.
+constexpr int STAT_T = 256;
+__global__ void __launch_bounds__(STAT_T) k_brick_stats(SelRule r, const float *__restrict__ q,
+                                                        const float *__restrict__ e, float4 *__restrict__ bstat,
+                                                        unsigned *__restrict__ out) {
+    pdl_enter();
+    const uint32_t brick = blockIdx.x;
+    uint32_t bx, by, bz;
+    demorton3(brick, bx, by, bz);
+    const int x0 = (int)bx << 4, y0 = (int)by << 4, z0 = (int)bz << 4;
+    const int tid = threadIdx.x, seg = tid & 3;
+    float mq = -INFINITY, lo = INFINITY, hi = -INFINITY;
+    bool nan_e = false;
+    auto take = [&](float vq, float ve, bool in) {
+        if (!in) return;
+        if (q && vq == vq) mq = fmaxf(mq, vq);
+        if (e) {
+            if (ve == ve) {
+                lo = fminf(lo, ve);
+                hi = fmaxf(hi, ve);
+            } else {
+                nan_e = true;
+            }
+        }
+    };
+    const bool vec = x0 + 16 <= r.nx && (r.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(q) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(e) & 15) == 0;
+    if (vec) {
+        float4 a[4], c[4];
+        bool in[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int row = (tid >> 2) + 64 * k, y = y0 + (row & 15), z = z0 + (row >> 4);
+            in[k] = y < r.ny && z < r.nz;
+            const int64_t lin = (int64_t)x0 + 4 * seg + (int64_t)r.nx * ((int64_t)y + (int64_t)r.ny * z);
+            a[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c[k] = a[k];
+            if (in[k] && q) a[k] = __ldg(reinterpret_cast<const float4 *>(q + lin));
+            if (in[k] && e) c[k] = __ldg(reinterpret_cast<const float4 *>(e + lin));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            take(a[k].x, c[k].x, in[k]);
+            take(a[k].y, c[k].y, in[k]);
+            take(a[k].z, c[k].z, in[k]);
+            take(a[k].w, c[k].w, in[k]);
+        }
+    } else {
+        for (int i = tid; i < 4096; i += STAT_T) {
+            const int x = x0 + (i & 15), y = y0 + ((i >> 4) & 15), z = z0 + (i >> 8);
+            const bool in = x < r.nx && y < r.ny && z < r.nz;
+            const int64_t lin = in ? (int64_t)x + (int64_t)r.nx * ((int64_t)y + (int64_t)r.ny * z) : 0;
+            take(in && q ? __ldg(q + lin) : 0.f, in && e ? __ldg(e + lin) : 0.f, in);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    nan_e = __any_sync(0xffffffffu, nan_e);
+    __shared__ float s_mq[STAT_T / 32], s_lo[STAT_T / 32], s_hi[STAT_T / 32];
+    __shared__ int s_nan[STAT_T / 32];
+    const int w = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        s_mq[w] = mq; s_lo[w] = lo; s_hi[w] = hi; s_nan[w] = nan_e;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 1; k < STAT_T / 32; ++k) {
+            mq = fmaxf(mq, s_mq[k]);
+            lo = fminf(lo, s_lo[k]);
+            hi = fmaxf(hi, s_hi[k]);
+            nan_e = nan_e || s_nan[k];
+        }
+        bstat[brick] = make_float4(mq, lo, hi, nan_e ? 1.f : 0.f);
+        if (q) atomicMax(out + 0, f2ord(mq));
+        if (e) atomicMax(out + 1, f2ord(hi));
+    }
+}
+
+// Status of brick `brick` from its statistics (st, as k_brick_stats): 1 if no cell is a source
+// and every cell a target, 2 if no cell is selected at all, 0 if the cells must be read.  Only a
+// brick of 16^3 cells wholly inside the grid is decided this way; the comparisons are those of
+// the per-cell rules (v >= threshold in FP32, NaN never selected).
+__device__ __forceinline__ int brick_mode(const SelRule &r, uint32_t brick, float4 st, float thr_q, float thr_e,
+                                          bool qpos) {
+    uint32_t bx, by, bz;
+    demorton3(brick, bx, by, bz);
+    if (((int)bx << 4) + 16 > r.nx || ((int)by << 4) + 16 > r.ny || ((int)bz << 4) + 16 > r.nz) return 0;
+    if (r.src_all || (qpos && st.x >= thr_q)) return 0;       // a source in the brick
+    if (r.trg_mode == 0) return 1;
+    if (r.trg_mode != 1) return 0;
+    if (st.w == 0.f && st.y >= thr_e) return 1;               // every |E| at or above the threshold
+    if (!(st.z >= thr_e)) return 2;                           // none
+    return 0;
+}
+
+// Decoupled look-back by the whole block: 512 predecessor states per round (every brick in
+// flight is within a round or two); the nearest inclusive state ends the walk.  Adds the
+// preceding bricks' counts into pre_s / pre_t; returns false (uniformly) if a round gave up
+// after wait_limit polls.  rs, rt: [blockDim.x / 32] shared scratch; s_stop: shared int.
+__device__ __forceinline__ bool look_back(const unsigned long long *state, int brick, unsigned wait_limit,
+                                          unsigned &pre_s, unsigned &pre_t, unsigned *rs, unsigned *rt,
+                                          int *s_stop) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int j = brick - 1; j >= 0; j -= (int)blockDim.x) {
+        const int idx = j - tid;
+        unsigned long long v = 0;
+        unsigned stt = 2;                          // before brick 0: an inclusive zero
+        bool ready = false;
+        for (unsigned k = 0; k < wait_limit; ++k) {
+            if (idx >= 0) {
+                v = *((volatile const unsigned long long *)(state + idx));
+                stt = (unsigned)(v >> 62);
+            }
+            if (__syncthreads_and(stt != 0)) {
+                ready = true;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!ready) return false;                  // uniform: every thread saw the same vote
+        if (tid == 0) *s_stop = (int)blockDim.x;
+        __syncthreads();
+        if (stt == 2u) atomicMin(s_stop, tid);
+        __syncthreads();
+        const int stop = *s_stop;
+        unsigned cs = (tid <= stop && idx >= 0) ? (unsigned)((v >> 31) & 0x7FFFFFFFu) : 0u;
+        unsigned ct = (tid <= stop && idx >= 0) ? (unsigned)(v & 0x7FFFFFFFu) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            ct += __shfl_xor_sync(0xffffffffu, ct, o);
+        }
+        if (lane == 0) {
+            rs[w] = cs;
+            rt[w] = ct;
+        }
+        __syncthreads();
+        unsigned sum_s = 0, sum_t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sum_s += rs[k];
+            sum_t += rt[k];
+        }
+        pre_s += sum_s;
+        pre_t += sum_t;
+        __syncthreads();                           // rs / rt / s_stop reused by the next round
+        if (stop < (int)blockDim.x) break;
+    }
+    return true;
+}
+
+// After the look-back (thread 0): the brick's inclusive state (and the gave-up flag), and the
+// totals from the last brick.
+__device__ __forceinline__ void publish(unsigned long long *state, int brick, int nbr, bool failed, unsigned pre_s,
+                                        unsigned pre_t, unsigned agg_s, unsigned agg_t, int *totals) {
+    if (brick > 0) {
+        if (failed) {
+            atomicOr(totals + 2, 1);
+            __threadfence();                       // the flag is visible before the state it taints
+        }
+        atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
+    }
+    if (brick == nbr - 1) {
+        __threadfence();
+        bool bad = atomicOr(totals + 2, 0) != 0;
+        totals[0] = bad ? -1 : (int)(pre_s + agg_s);
+        totals[1] = bad ? -1 : (int)(pre_t + agg_t);
+    }
+}
+
 
 // One pass over the grid: each CTA takes the next brick in dispatch order (ticket), reads
 // it row by row, evaluates both rules, ranks its cells in Morton order, finds its output
@@ -279,9 +458,9 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
         int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
         float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
-        uint8_t *__restrict__ tmask, unsigned wait_limit) {
+        uint8_t *__restrict__ tmask, unsigned wait_limit, const float4 *__restrict__ bstat) {
     pdl_enter();
-    __shared__ int s_brick;
+    __shared__ int s_brick, s_mode;
     __shared__ float s_thr_q, s_thr_e;
     __shared__ int s_qpos;
     __shared__ int ws[16], wt[16];
@@ -299,6 +478,7 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         s_thr_q = ge_threshold_f32(thr_q);
         s_thr_e = ge_threshold_f32(thr_e);
         s_qpos = qpos;
+        s_mode = bstat ? brick_mode(r, (uint32_t)s_brick, bstat[s_brick], s_thr_q, s_thr_e, qpos) : 0;
     }
     __syncthreads();
     const int brick = s_brick;
@@ -309,6 +489,42 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     const int x0 = bx << b, y0 = by << b, z0 = bz << b;
     const float thr_q = s_thr_q, thr_e = s_thr_e;
     const bool qpos = s_qpos;
+    if (s_mode != 0) {
+        // a whole brick decided by its statistics (16^3 cells inside the grid): no source, and
+        // every cell (mode 1) or none (mode 2) a target -- counts known, nothing read
+        const unsigned agg_t = s_mode == 1 ? (unsigned)ncell : 0u;
+        if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, 0u, agg_t));
+        if (tmask) {
+            const uint8_t m = s_mode == 1 ? 1 : 0;
+            if ((r.nx & 15) == 0 && (reinterpret_cast<uintptr_t>(tmask) & 15) == 0) {
+                if (tid < 256) {   // one 16-byte store per row of the brick
+                    const int64_t o = (int64_t)x0 + (int64_t)r.nx * ((int64_t)(y0 + (tid & 15)) +
+                                                                     (int64_t)r.ny * (z0 + (tid >> 4)));
+                    const uint32_t m4 = m * 0x01010101u;
+                    *reinterpret_cast<uint4 *>(tmask + o) = make_uint4(m4, m4, m4, m4);
+                }
+            } else {
+                for (int i = tid; i < ncell; i += blockDim.x)
+                    tmask[(int64_t)(x0 + (i & 15)) +
+                          (int64_t)r.nx * ((int64_t)(y0 + ((i >> 4) & 15)) + (int64_t)r.ny * (z0 + (i >> 8)))] = m;
+            }
+        }
+        unsigned pre_s = 0, pre_t = 0;
+        const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
+        if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, 0u, agg_t, totals);
+        if (s_mode == 1) {
+            for (int i = tid; i < ncell; i += blockDim.x) {
+                const uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)i;
+                trg_key[pre_t + i] = key;
+                if (trg_pc) {
+                    uint32_t lx, ly, lz;
+                    demorton3((uint32_t)i, lx, ly, lz);
+                    trg_pc[pre_t + i] = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
+                }
+            }
+        }
+        return;
+    }
     // Thread t owns the brick's local Morton keys 8t .. 8t+7: a 2x2x2 micro-cube, so the
     // 8 cells follow from one decode; its loads are all issued before any is used (a warp's
     // cells form an 8x8x4 block, whose rows the L1 serves sector by sector).
@@ -408,74 +624,12 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     __syncthreads();
     const int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
     const int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
-    // decoupled look-back by the whole block: 512 predecessor states per round (every
-    // brick in flight is within a round or two); the nearest inclusive state ends the walk
+    // decoupled look-back over the preceding bricks
     const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
     if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, agg_s, agg_t));
     unsigned pre_s = 0, pre_t = 0;
-    bool failed = false;
-    for (int j = brick - 1; j >= 0; j -= (int)blockDim.x) {
-        const int idx = j - tid;
-        unsigned long long v = 0;
-        unsigned stt = 2;                          // before brick 0: an inclusive zero
-        bool ready = false;
-        for (unsigned k = 0; k < wait_limit; ++k) {
-            if (idx >= 0) {
-                v = *((volatile unsigned long long *)(state + idx));
-                stt = (unsigned)(v >> 62);
-            }
-            if (__syncthreads_and(stt != 0)) {
-                ready = true;
-                break;
-            }
-            __nanosleep(64);
-        }
-        if (!ready) {                              // uniform: every thread saw the same vote
-            failed = true;
-            break;
-        }
-        if (tid == 0) s_stop = (int)blockDim.x;
-        __syncthreads();
-        if (stt == 2u) atomicMin(&s_stop, tid);
-        __syncthreads();
-        const int stop = s_stop;
-        unsigned cs = (tid <= stop && idx >= 0) ? (unsigned)((v >> 31) & 0x7FFFFFFFu) : 0u;
-        unsigned ct = (tid <= stop && idx >= 0) ? (unsigned)(v & 0x7FFFFFFFu) : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cs += __shfl_xor_sync(0xffffffffu, cs, o);
-            ct += __shfl_xor_sync(0xffffffffu, ct, o);
-        }
-        if (lane == 0) {
-            rs[w] = cs;
-            rt[w] = ct;
-        }
-        __syncthreads();
-        unsigned sum_s = 0, sum_t = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            sum_s += rs[k];
-            sum_t += rt[k];
-        }
-        pre_s += sum_s;
-        pre_t += sum_t;
-        __syncthreads();                           // rs / rt / s_stop reused by the next round
-        if (stop < (int)blockDim.x) break;
-    }
-    if (tid == 0) {
-        if (brick > 0) {
-            if (failed) {
-                atomicOr(totals + 2, 1);
-                __threadfence();                   // the flag is visible before the state it taints
-            }
-            atomicExch(state + brick, pack_state(2u, pre_s + agg_s, pre_t + agg_t));
-        }
-        if (brick == nbr - 1) {
-            __threadfence();
-            bool bad = atomicOr(totals + 2, 0) != 0;
-            totals[0] = bad ? -1 : (int)(pre_s + agg_s);
-            totals[1] = bad ? -1 : (int)(pre_t + agg_t);
-        }
-    }
+    const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
+    if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, agg_s, agg_t, totals);
     // targets: staged at their brick-local rank (in the space of s_q, read above), then
     // written out by consecutive threads; sources (few) go straight out
     int ps = (int)pre_s + base_s, lt = base_t;
@@ -521,7 +675,10 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     if (gm > 152 * 8) gm = 152 * 8;
     if (gm < 1) gm = 1;
     const float *gq = r.src_all ? nullptr : A.q, *ge = r.trg_mode == 1 ? A.emag : nullptr;
-    if (gq || ge) launch_pdl(k_grid_max, gm, 256, 0, st, gq, ge, n, A.maxes);
+    // one pass over bricks of 16^3 cells: the maxima with the per-brick statistics
+    const bool stats = !A.two_pass && A.bstat != nullptr && b == 4 && (gq || ge);
+    if (stats) launch_pdl(k_brick_stats, nbr, STAT_T, 0, st, r, gq, ge, reinterpret_cast<float4 *>(A.bstat), A.maxes);
+    else if (gq || ge) launch_pdl(k_grid_max, gm, 256, 0, st, gq, ge, n, A.maxes);
     if (A.two_pass) {
         launch_pdl(k_select_brick<false>, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -539,7 +696,8 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
     launch_pdl(k_select_onepass, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
-                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask, A.wait_limit);
+                                          A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask, A.wait_limit,
+                                          stats ? (const float4 *)A.bstat : nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -886,12 +886,14 @@ __global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_beg
 // contractions (parent x composed table, child x table), BF16 hi / lo x3.  Software pipeline
 // per child: the MMAs of child c run while the 256 threads hold child c+1's rows in flight
 // (16 loads each) and write child c's cells; then the rows are split into the operand tile
-// and child c+1's composed table arrives by a bulk copy.
+// and child c+1's composed table arrives by a bulk copy.  d_c is zero where the child has no
+// V or X entry: such rows are neither read (a zero row in the operand tile) nor, where none of
+// the chunk's children in slot c has one, multiplied (only the parent term is issued).
 constexpr uint32_t LP_A = TCM * TCK * 2;               // 32 KiB: 128 rows x 128 coefficients
 constexpr uint32_t LP_B = 64 * TCK * 2;                // 16 KiB: 64 cells x 128 coefficients
 constexpr int LP_T = 256;
 constexpr int LP_V = TCM * (TCK / 4) / LP_T;           // float4 row segments per thread per tile (16)
-constexpr uint32_t LP_SMEM = 1024 + 4 * LP_A + 4 * LP_B + 64 + 17 * TCM * 4;
+constexpr uint32_t LP_SMEM = 1024 + 4 * LP_A + 4 * LP_B + 64 + 25 * TCM * 4;
 
 // rows idx[0..128) of the FP32 state (-1: zero row), 16 float4 per thread, all in flight at once
 __device__ __forceinline__ void lp_load(float4 (&v)[LP_V], const int *idx, const float *__restrict__ state, int np) {
@@ -934,9 +936,11 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     uint64_t *bar_mma = bar_e + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tail + 24);
     int *ok_s = reinterpret_cast<int *>(tail + 28);
+    int *s_own = reinterpret_cast<int *>(tail + 32);        // bit c: a child in slot c has V / X entries
     int *spar = reinterpret_cast<int *>(tail + 64);         // [128] parent box or -1
     int *sch = spar + TCM;                                  // [8][128] child box or -1
     int *sfull = sch + 8 * TCM;                             // [8][128] child has every cell as target
+    int *sld = sfull + 8 * TCM;                             // [8][128] child box if it has V / X entries, or -1
     const TreeDev &T = F.T;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int np = F.O.npad;
@@ -1040,8 +1044,9 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     };
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const bool more = chunk + (int)gridDim.x < nchunks;   // this CTA has another chunk after this one
+        if (tid == 0) *s_own = 0;                              // its last reader passed the last round's barrier
         __syncthreads();                                       // previous chunk's epilogue read sch / sfull
-        int any = 0;
+        int any = 0, own = 0;
         if (tid < TCM) {
             const int i = chunk * ppc + tid;
             const int p = parent_begin + i;
@@ -1057,17 +1062,25 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                         full = T.b_te[ch] - T.b_tb[ch] == 64;
                     }
                 }
+                const bool terms = C >= 0 && (F.L.v_off[C + 1] != F.L.v_off[C] || F.L.x_off[C + 1] != F.L.x_off[C]);
                 sch[c * TCM + tid] = C;
                 sfull[c * TCM + tid] = full;
+                sld[c * TCM + tid] = terms ? C : -1;
                 any |= C >= 0;
+                own |= (int)terms << c;
             }
+            own = __reduce_or_sync(0xffffffffu, own);           // tid < 128: whole warps
+            if (lane == 0 && own) atomicOr(s_own, own);
         }
         // a chunk without leaves is skipped; the first composed table stays in flight for the next
         if (!__syncthreads_or(any)) continue;
+        own = *s_own;
         lp_load(v, spar, F.dchk, np);
         lp_store(ap_hi, ap_lo, v);
-        lp_load(v, sch, F.dchk, np);
-        lp_store(ac_hi, ac_lo, v);
+        if (own & 1) {
+            lp_load(v, sld, F.dchk, np);
+            lp_store(ac_hi, ac_lo, v);
+        }
         auto round = [&](int c) -> bool {
             // (a) operand tiles of child c are in shared memory: MMAs (thread 0); the TMEM
             //     reads of earlier epilogues (the same columns in the previous chunk) are ordered
@@ -1087,6 +1100,7 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                     const uint32_t ach = tc::smem_u32(ac_hi), acl = tc::smem_u32(ac_lo);
                     const uint32_t th = tc::smem_u32(t_hi), tl = tc::smem_u32(t_lo);
                     const uint32_t eh = tc::smem_u32(e_hi), el = tc::smem_u32(e_lo);
+                    const bool child_terms = (own >> c) & 1;
 #pragma unroll
                     for (int ks = 0; ks < TCK / 16; ++ks) {
                         const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
@@ -1094,9 +1108,11 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                         tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(th + bo), idesc, ks > 0);
                         tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(tl + bo), idesc, 1);
                         tc::mma_bf16(d, tc::sdesc_sw128(apl + ao), tc::sdesc_sw128(th + bo), idesc, 1);
-                        tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
-                        tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
-                        tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                        if (child_terms) {
+                            tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                            tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
+                            tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
+                        }
                     }
                     tc::mma_commit(tc::smem_u32(bar_mma));
                     ++m_issued;
@@ -1105,8 +1121,9 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                     *ok_s = 0;
                 }
             }
-            // (b) child c+1's rows in flight
-            if (c + 1 < 8) lp_load(v, sch + (c + 1) * TCM, F.dchk, np);
+            // (b) child c+1's rows in flight (where that slot has own terms)
+            const bool next_terms = c + 1 < 8 && ((own >> (c + 1)) & 1);
+            if (next_terms) lp_load(v, sld + (c + 1) * TCM, F.dchk, np);
             // (c) MMAs of child c complete: its accumulator is final (written in the next round),
             //     the child tile and the table buffer are free; the next composed table streams
             //     in (child c+1's, or after the last child the first one of the next chunk) --
@@ -1131,8 +1148,8 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
             __syncthreads();
             if (!*ok_s) return false;
             tc::fence_after_sync();
-            // (e) child c+1's operand tile
-            if (c + 1 < 8) lp_store(ac_hi, ac_lo, v);
+            // (e) child c+1's operand tile (child c's MMAs, the last to read it, have completed)
+            if (next_terms) lp_store(ac_hi, ac_lo, v);
             return true;
         };
 #pragma unroll 1

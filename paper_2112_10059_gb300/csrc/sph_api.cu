@@ -104,7 +104,7 @@ struct sph_ctx {
     bool near_table = false;          // resolved for the current evaluation
     DevBuf b_gtab;
     // buffers
-    DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc;
+    DevBuf b_maxes, b_cnt, b_off, b_tot, b_skey, b_spc, b_sq, b_tkey, b_tpc, b_bstat;
     DevBuf b_boxat, b_flag, b_pos, b_rng, b_scan, b_lvl;
     DevBuf b_level, b_key, b_sb, b_se, b_tb, b_te, b_parent, b_leaf;
     DevBuf b_lcnt, b_loff, b_usrc, b_vsrc, b_vocs, b_vtrg, b_wsrc, b_xsrc, b_pkeys, b_ppairs, b_heavy;
@@ -244,6 +244,7 @@ int select_queue(sph_ctx *c) {
     ENS(c->b_sq, ncell * sizeof(float));
     ENS(c->b_tkey, ncell * sizeof(uint32_t));
     ENS(c->b_tmask, ncell);
+    ENS(c->b_bstat, nbr * 4 * sizeof(float));
     SelectArgs A;
     A.nx = c->nx; A.ny = c->ny; A.nz = c->nz; A.D = D; A.brick_log2 = b;
     A.q = c->q; A.emag = c->emag; A.mask = c->mask;
@@ -257,6 +258,7 @@ int select_queue(sph_ctx *c) {
     A.src_key = P<uint32_t>(c->b_skey); A.src_pc = P<uint32_t>(c->b_spc); A.src_q = P<float>(c->b_sq);
     A.trg_key = P<uint32_t>(c->b_tkey);   // targets' cells follow from their keys: no packed copy
     A.tmask = P<uint8_t>(c->b_tmask);
+    A.bstat = P<float>(c->b_bstat);
     if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
     c->launches += 2;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -582,7 +584,15 @@ struct PassState {
     bool tc = false;
     MtLevels ML;                 // target-stationary M2L: groups per level
     int *mt_groups = nullptr;    // [groups] scratch of that M2L
+    bool fused = false;          // the last L2L and the L2P of the deepest level in one kernel
 };
+
+// the last L2L and the L2P of the deepest level fused (every box there a leaf of edge 4)
+bool l2lp_fusable(const sph_ctx *c, const PassState &S) {
+    const FmmDev &F = S.F;
+    return S.tc && c->l2lp_fused && F.leaf_l2p_done && F.O.l2p_img != nullptr && !c->l2p_simt &&
+           F.O.l2pc_off >= 0 && c->Lmax >= 3 && c->Lmax == c->D - 2 && F.O.l2p_off[c->Lmax] >= 0;
+}
 
 // Every buffer the passes need (so that fmm_queue allocates nothing and can be captured).
 int fmm_prepare(sph_ctx *c, PassState &S) {
@@ -625,6 +635,10 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
+    // the fused deepest level reads only the d rows of leaves with V or X entries: the rows of
+    // that level are then cleared one by one by the work lists, the levels above by a memset
+    S.fused = l2lp_fusable(c, S);
+    F.d_sparse_from = S.fused && c->lvl_count[c->Lmax - 1] > 0 ? c->lvl_base[c->Lmax] : -1;
     S.ML = m2l_tile_levels(c->Lmax);
     if (S.tc && c->m2l_tiles) {
         ENS(c->b_mtg, (size_t)std::max(1, S.ML.gbase[S.ML.lmax + 1]) * sizeof(int));
@@ -640,7 +654,8 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     FmmDev &F = S.F;
     const int nb = c->nboxes;
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
-    CK(cudaMemsetAsync(c->b_dchk.p, 0, vb, c->stream));
+    const size_t db = F.d_sparse_from >= 0 ? (size_t)F.d_sparse_from * c->npad() * sizeof(float) : vb;
+    if (db > 0) CK(cudaMemsetAsync(c->b_dchk.p, 0, db, c->stream));
     CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
     if (S.tc) CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));   // M2M, M2L and L2L tiles' flags
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 33, c->stream);
@@ -660,9 +675,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         }
     }
     if (tm) tm->mark_at(4, c->stream);
-    // the last L2L and the L2P of the deepest level fused (every box there a leaf of edge 4)
-    const bool fused = S.tc && c->l2lp_fused && F.leaf_l2p_done && F.O.l2p_img != nullptr && !c->l2p_simt &&
-                       F.O.l2pc_off >= 0 && c->Lmax >= 3 && c->Lmax == c->D - 2 && F.O.l2p_off[c->Lmax] >= 0;
+    const bool fused = S.fused;
     c->l2lp_used = fused && c->lvl_count[c->Lmax - 1] > 0;
     if (c->translate_per_box) {
         if (tm) { tm->mark_at(5, c->stream); tm->mark_at(6, c->stream); }
@@ -1613,7 +1626,7 @@ void sph_destroy(sph_ctx *c) {
     c->subs.clear();
     if (c->sur_coarse) sph_destroy(c->sur_coarse);
     if (c->sur_fine) sph_destroy(c->sur_fine);
-    DevBuf *all[] = {&c->b_maxes, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
+    DevBuf *all[] = {&c->b_maxes, &c->b_bstat, &c->b_cnt, &c->b_off, &c->b_tot, &c->b_skey, &c->b_spc, &c->b_sq, &c->b_tkey,
                      &c->b_tpc, &c->b_boxat, &c->b_flag, &c->b_pos, &c->b_rng, &c->b_scan, &c->b_lvl,
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pkeys, &c->b_ppairs, &c->b_heavy,

@@ -33,6 +33,10 @@ struct SelectArgs {
     float *src_q;
     uint8_t *tmask = nullptr;        // optional [nx*ny*nz]: 1 where the cell is a target
     unsigned wait_limit = SELECT_WAIT_LIMIT;   // polls per look-back round before giving up
+    // optional [nbricks] float4 scratch (16-byte aligned): per-brick statistics of the maxima
+    // pass, with which the one-pass selection emits a uniform brick without reading it again;
+    // nullptr: the maxima alone (k_grid_max) and every brick read
+    float *bstat = nullptr;
 };
 int select_launch(const SelectArgs &A, cudaStream_t st);
 
@@ -203,6 +207,10 @@ struct FmmDev {
     double alpha, beta, C64;   // FP64 kernel constants for the FP64 evaluation paths
     int D, nx, ny, nz, self_mode;
     float *ueq, *dchk;   // [nboxes][PP]: upward / downward check potentials u_B, d_B
+    // >= 0: the boxes from this one on (the deepest level, taken by the fused L2L + L2P) have
+    // their d rows cleared by the work-list kernel only where they have V or X entries (the
+    // others are never read); -1: every row cleared before the passes
+    int d_sparse_from = -1;
 };
 // returns the number of kernels launched
 int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count, bool leaves_only,

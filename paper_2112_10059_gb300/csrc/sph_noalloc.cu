@@ -7,7 +7,7 @@
 // device memory), or a harness that checks that a step performs no allocation.
 // sph_create + eval_sph allocate their working buffers on first use and grow them;
 // this entry point instead takes every output from the caller and keeps its small
-// scratch (per-brick counters and offsets, the two maxima, the totals) in one
+// scratch (per-brick counters, offsets and statistics, the two maxima, the totals) in one
 // fixed, file-scope device array that exists from library load to process exit.
 //
 // Limits and behaviour:
@@ -32,7 +32,8 @@ namespace {
 constexpr int NOALLOC_MAX_EDGE = 512;
 constexpr int NOALLOC_MAX_BRICKS = 32768;                 // (512 / 16)^3
 constexpr int NOALLOC_HEAD = 64;                          // maxima (2), totals (2) + flag, padding
-constexpr size_t NOALLOC_INTS = NOALLOC_HEAD + 4 * (size_t)NOALLOC_MAX_BRICKS;   // 512.25 KiB
+// head, four ints per brick (counters, offsets), four floats per brick (statistics): 1 MiB + 256 B
+constexpr size_t NOALLOC_INTS = NOALLOC_HEAD + 8 * (size_t)NOALLOC_MAX_BRICKS;
 
 static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_INTS];
 
@@ -100,6 +101,7 @@ extern "C" int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny,
     A.cnt_t = A.cnt_s + nbricks;
     A.off_s = A.cnt_t + nbricks;
     A.off_t = A.off_s + nbricks;
+    A.bstat = reinterpret_cast<float *>(scratch + NOALLOC_HEAD + 4 * (size_t)NOALLOC_MAX_BRICKS);   // 16-B aligned
     A.src_key = src_key_dev; A.src_pc = src_pc_dev; A.src_q = src_q_dev;
     A.trg_key = trg_key_dev; A.trg_pc = trg_pc_dev;
     if (const char *e = getenv("SPH_WAIT_LIMIT_SELECT")) {   // tests: make the look-back give up

@@ -373,3 +373,48 @@ def streamer_head(box=1.0, chan_len=0.5):
     """Head centre of :func:`streamer` with its default placement."""
     return (box / 2, box / 2, box / 2 - chan_len / 2)
 
+
+
+def brick_structured(nx=64, ny=48, nz=48, seed=1007, h=1e-3, p_torr=760.0):
+    """Fields built brick by brick (bricks of 16^3 cells, brick (i, j, k) = cells 16i .. 16i+15
+    along x, and so on) so that a selection may decide whole bricks at once and every way of
+    deciding one is exercised, with ties at the thresholds.  i_frac = e_frac = 0.5, no applied
+    field: the source threshold is 0.5 (max q = 1) and the |E| threshold 0.5 (max |E| = 1).
+
+      q: 0, except 1.0 at (3, 5, 20), 0.5 (a tie: a source) at (6, 21, 6), NaN at (20, 4, 4)
+         and just below 0.5 (not a source) at (20, 20, 3);
+      |E|: 0.8 + seeded noise in [0, 0.1) with 1.0 at (0, 0, 0), except
+         brick (1, 0, 0): 0.2 everywhere (no target);
+         brick (2, 0, 0): 0.2 except 0.5 (a tie: a target) at its first cell;
+         brick (0, 1, 1): one cell just below 0.5 (the others targets);
+         brick (1, 1, 1): one cell at exactly 0.5 (every cell a target);
+         brick (0, 0, 2): one NaN (never a target);
+         brick (2, 2, 0): NaN everywhere (no target).
+    Bricks that reach past the grid are left as they fall."""
+    n = nx * ny * nz
+    q = np.zeros((nz, ny, nx), np.float32)
+    e = (0.8 + 0.1 * uniform01(seed, n)).astype(np.float32).reshape(nz, ny, nx)
+    below = np.nextafter(np.float32(0.5), np.float32(0.0))
+
+    def put(a, x, y, z, v):
+        if x < nx and y < ny and z < nz:
+            a[z, y, x] = v
+
+    def brick(a, i, j, k, v):
+        a[16 * k:16 * k + 16, 16 * j:16 * j + 16, 16 * i:16 * i + 16] = v
+
+    put(q, 3, 5, 20, 1.0)
+    put(q, 6, 21, 6, 0.5)
+    put(q, 20, 4, 4, np.nan)
+    put(q, 20, 20, 3, below)
+    put(e, 0, 0, 0, 1.0)
+    brick(e, 1, 0, 0, 0.2)
+    brick(e, 2, 0, 0, 0.2)
+    put(e, 32, 0, 0, 0.5)
+    put(e, 5, 17, 18, below)
+    put(e, 19, 21, 30, 0.5)
+    put(e, 7, 9, 35, np.nan)
+    brick(e, 2, 2, 0, np.nan)
+    return Problem("bricks_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, h, (0.0, 0.0, 0.0), p_torr, pO2_of(p_torr),
+                   q.reshape(-1), e.reshape(-1), scale_of(p_torr), i_frac=0.5, e_frac=0.5, e_applied=0.0,
+                   targets_all=False, leaf_size=64, seed=seed)

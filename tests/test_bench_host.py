@@ -40,9 +40,15 @@ def _stats(fused):
 def test_fused_deepest_level():
     r = bench.rooflines(TREE, _stats(True), ARGS, nt=8, ns=4, ncell=1000, peaks=PEAKS, pipes=PIPES,
                         traffic_ok=False)
-    # fused level: parent box 0 and leaves 1, 2 read 128 x 4 B each, 8 targets written
-    assert r["l2lp"]["work_per_launch"] == 3 * 512 + 8 * 4
-    assert r["l2lp"]["achieved"] == pytest.approx(1568 / 0.004e-3 / 1e9)
+    # fused level: parent box 0 read (128 x 4 B); leaves 1, 2 have no V or X entries, so no own
+    # local terms to read; 8 targets written
+    assert r["l2lp"]["work_per_launch"] == 512 + 8 * 4
+    assert r["l2lp"]["achieved"] == pytest.approx(544 / 0.004e-3 / 1e9)
+    # with a V entry into leaf 2 (and one X entry into leaf 2 too) its row is read as well
+    tv = dict(TREE, V=np.array([[2, 1]]), X=np.array([[2, 1]]))
+    r2 = bench.rooflines(tv, _stats(True), ARGS, nt=8, ns=4, ncell=1000, peaks=PEAKS, pipes=PIPES,
+                         traffic_ok=False)
+    assert r2["l2lp"]["work_per_launch"] == 2 * 512 + 8 * 4
     assert r["l2lp"]["traffic"] is None   # ncu traffic only where it was measured on this workload
     # nothing left for the separate L2L (both level-3 boxes are fused) or L2P: no entries
     assert "l2l" not in r and "l2p" not in r
@@ -51,9 +57,9 @@ def test_fused_deepest_level():
     assert r["near"]["work_per_launch"] == 32
     assert r["near"]["achieved"] == pytest.approx(32 / 0.005e-3)
     assert r["near"]["peak"] == pytest.approx(1.6e12)
-    # selection: q and |E| read twice (16 B per cell), 4 B per selected index (8 targets, 4 sources)
-    assert r["select"]["work_per_launch"] == 16 * 1000 + 4 * (8 + 4)
-    assert r["select"]["frac"] == pytest.approx(16048 / 0.004e-3 / 1e9 / 5000.0)
+    # selection: q and |E| read once (8 B per cell), 4 B per selected index (8 targets, 4 sources)
+    assert r["select"]["work_per_launch"] == 8 * 1000 + 4 * (8 + 4)
+    assert r["select"]["frac"] == pytest.approx(8048 / 0.004e-3 / 1e9 / 5000.0)
     assert r["m2l"]["work_per_launch"] == 0
     # the dominant single kernel: m2l (0.01 ms) over l2lp (0.004) and near (0.005)
     assert bench.dominant_kernel(r) == "m2l"

@@ -112,6 +112,27 @@ def test_selection_one_pass_equals_two_pass(sph, monkeypatch, n):
         assert np.array_equal(J, Jo) and np.array_equal(T, To), flag
 
 
+@pytest.mark.parametrize("dims", [(64, 48, 48), (56, 48, 40)])
+def test_selection_whole_bricks(sph, monkeypatch, dims):
+    """Bricks that the maxima pass's per-brick statistics decide (no source, every cell or no
+    cell a target) are emitted without reading them again; ties at both thresholds, a source
+    just below its threshold, NaN in q and |E|, an all-NaN brick and bricks that reach past the
+    grid (row pitch 64: one 16-byte mask store per row; 56: byte stores) give the oracle's sets
+    in both selection forms, and the FMM on them passes the gate with S = 0 off the targets."""
+    p = si.brick_structured(*dims)
+    Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    for flag in ("0", "1"):
+        monkeypatch.setenv("SPH_SELECT_TWO_PASS", flag)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        J, T = sph.get_selection(c)
+        c.close()
+        assert np.array_equal(J, Jo) and np.array_equal(T, To), flag
+        if flag == "0":
+            ref, _, _ = oracle.sph_problem(p)
+            _check_fmm(out.cpu().numpy(), ref, To, p.name)
+
+
 @pytest.mark.parametrize("case", [(16, 16, 16, 0.05, 0.3, 8, 2), (12, 9, 7, 0.2, 0.1, 4, 3),
                                   (20, 10, 13, 0.5, 0.02, 6, 5), (32, 32, 32, 0.02, 0.5, 16, 9)])
 def test_tree_bit_exact(sph, ctx, case):

@@ -6,8 +6,9 @@ row with different inputs must each give exactly the selection of the regular en
 point (eval_sph + sph_get_selection) and of the FP64 oracle's selection rules: the
 same index sets (selection is integer work, so the comparison is bit-exact), the
 same source values, and a zero failure flag.  The cases cover the three target
-modes (|E| rule, explicit mask, every cell) and the capacity edge (512 cells on one
-axis: the scratch's full 32768-brick layout).
+modes (|E| rule, explicit mask, every cell), the capacity edge (512 cells on one
+axis: the scratch's full 32768-brick layout) and bricks decided whole from the
+maxima pass's per-brick statistics (their packed cells written without a read).
 
 This file is collected last on purpose, and it passes both alone in a fresh process
 and after the other tests.
@@ -49,7 +50,8 @@ def _cases():
     masked_mask = si.random_mask(masked.ncell, 0.3, seed=33)
     every = si.gaussian_box(512, 8, 8, sigma_cells=40.0, h=1e-3)
     every.i_frac = 1e-2
-    return [(first, None), (second, None), _edge_case(), (masked, masked_mask), (every, None)]
+    bricks = si.brick_structured(56, 48, 40)
+    return [(first, None), (second, None), _edge_case(), (masked, masked_mask), (every, None), (bricks, None)]
 
 
 def test_select_noalloc_matches_regular_path_and_oracle():
