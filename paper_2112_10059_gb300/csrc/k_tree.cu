@@ -315,14 +315,22 @@ __global__ void k_tree_exists(int64_t nslot, int Lmax, int D, int S, const int *
 }
 
 // Boxes in (level, key) order: box index = exclusive scan of the existence flags.
-__global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S, const int *__restrict__ flag,
-                                const int *__restrict__ pos, const int *__restrict__ rsb,
-                                const int *__restrict__ rse, const int *__restrict__ rtb,
-                                const int *__restrict__ rte, const int *__restrict__ total,
-                                const uint32_t *__restrict__ skey, const int *__restrict__ ns_dev,
-                                const uint32_t *__restrict__ tkey, const int *__restrict__ nt_dev,
-                                uint8_t *__restrict__ vsrc) {
+__global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S,
+                                                      const int *__restrict__ flag, const int *__restrict__ pos,
+                                                      const int *__restrict__ rsb, const int *__restrict__ rse,
+                                                      const int *__restrict__ rtb, const int *__restrict__ rte,
+                                                      const int *__restrict__ total, const uint32_t *__restrict__ skey,
+                                                      const int *__restrict__ ns_dev, const uint32_t *__restrict__ tkey,
+                                                      const int *__restrict__ nt_dev, uint8_t *__restrict__ vsrc) {
     pdl_enter();
+    // per-level counts of the block's boxes with sources and leaves with targets, added into
+    // the level tables once per block and level (the same few counters for every block)
+    __shared__ int s_src[16], s_leaf[16];
+    if (threadIdx.x < 16) {
+        s_src[threadIdx.x] = 0;
+        s_leaf[threadIdx.x] = 0;
+    }
+    __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= Lmax) {       // level table (threads 0..Lmax)
         const int l = (int)s;
@@ -331,29 +339,35 @@ __global__ void k_tree_emit_all(TreeDev T, int64_t nslot, int Lmax, int D, int S
         T.lvl_base[l] = b0;
         T.lvl_count[l] = b1 - b0;
     }
-    if (s >= nslot) return;
-    if (!flag[s]) {
+    if (s < nslot && !flag[s]) {
         T.box_at[s] = -1;
         vsrc[s] = 0;
-        return;
+    } else if (s < nslot) {
+        const int l = level_of_slot(s, Lmax);
+        const int64_t m = s - dense_off(l);
+        const int idx = pos[s];
+        T.box_at[s] = idx;
+        int sb = rsb[s], se = rse[s], tb = rtb[s], te = rte[s];
+        // an empty range starts where the slot's first key would be inserted
+        const uint32_t lo = (uint32_t)m << (3 * (D - l));
+        if (se == sb) sb = se = lower_bound_u32(skey, 0, max(*ns_dev, 0), lo);
+        if (te == tb) tb = te = lower_bound_u32(tkey, 0, max(*nt_dev, 0), lo);
+        T.b_level[idx] = l;
+        T.b_key[idx] = (uint32_t)m;
+        T.b_sb[idx] = sb; T.b_se[idx] = se;
+        T.b_tb[idx] = tb; T.b_te[idx] = te;
+        T.b_parent[idx] = l > 0 ? pos[dense_off(l - 1) + (m >> 3)] : -1;
+        const bool leaf = !(l < D && (se - sb > S || te - tb > S));
+        T.b_leaf[idx] = leaf;
+        vsrc[s] = se > sb;
+        if (se > sb) atomicAdd(s_src + l, 1);
+        if (leaf && te > tb) atomicAdd(s_leaf + l, 1);
     }
-    const int l = level_of_slot(s, Lmax);
-    const int64_t m = s - dense_off(l);
-    const int idx = pos[s];
-    T.box_at[s] = idx;
-    int sb = rsb[s], se = rse[s], tb = rtb[s], te = rte[s];
-    // an empty range starts where the slot's first key would be inserted
-    const uint32_t lo = (uint32_t)m << (3 * (D - l));
-    if (se == sb) sb = se = lower_bound_u32(skey, 0, max(*ns_dev, 0), lo);
-    if (te == tb) tb = te = lower_bound_u32(tkey, 0, max(*nt_dev, 0), lo);
-    T.b_level[idx] = l;
-    T.b_key[idx] = (uint32_t)m;
-    T.b_sb[idx] = sb; T.b_se[idx] = se;
-    T.b_tb[idx] = tb; T.b_te[idx] = te;
-    T.b_parent[idx] = l > 0 ? pos[dense_off(l - 1) + (m >> 3)] : -1;
-    T.b_leaf[idx] = !(l < D && (se - sb > S || te - tb > S));
-    vsrc[s] = se > sb;
-    if (se > sb) atomicAdd(T.lvl_src + l, 1);
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        if (s_src[threadIdx.x]) atomicAdd(T.lvl_src + threadIdx.x, s_src[threadIdx.x]);
+        if (s_leaf[threadIdx.x]) atomicAdd(T.lvl_leaf + threadIdx.x, s_leaf[threadIdx.x]);
+    }
 }
 
 // occ[s] = 1 if the slot's region holds a source point, or lies inside a leaf that holds
@@ -415,7 +429,7 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
                                                                            A.rse);
     launch_pdl(k_tree_ranges, std::max(rg, 1), RANGE_T, 0, st, A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
     const int grid = (int)((nslot + 255) / 256);
-    cudaMemsetAsync(A.T.lvl_src, 0, 16 * sizeof(int), st);
+    cudaMemsetAsync(A.T.lvl_src, 0, 32 * sizeof(int), st);   // lvl_src and lvl_leaf
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);

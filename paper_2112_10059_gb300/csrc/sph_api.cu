@@ -75,6 +75,7 @@ struct sph_ctx {
     int64_t ns = 0, nt = 0;
     int nboxes = 0, Lmax = 0;
     std::vector<int> lvl_count, lvl_base, lvl_src;   // boxes, first box, boxes with sources per level
+    std::vector<int> lvl_leaf;                       // leaves with targets per level
     int list_tot[4] = {0, 0, 0, 0};
     bool have_tree = false;
     int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
@@ -288,6 +289,7 @@ TreeDev tree_dev(sph_ctx *c) {
     T.lvl_base = P<int>(c->b_lvl);
     T.lvl_count = T.lvl_base + 16;
     T.lvl_src = T.lvl_base + 32;
+    T.lvl_leaf = T.lvl_base + 48;
     T.b_level = P<int>(c->b_level);
     T.b_key = P<uint32_t>(c->b_key);
     T.b_sb = P<int>(c->b_sb); T.b_se = P<int>(c->b_se);
@@ -336,7 +338,7 @@ PairsDev pairs_dev(sph_ctx *c) {
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
 // [43] scan give-up flag, [44..48) list totals, [48] and [49] tensor-core error flags,
-// [50..50+Lmax] boxes with sources per level.
+// [64..64+Lmax] boxes with sources per level, [80..80+Lmax] leaves with targets per level.
 // The tree and the list counts read the selection's point counts and the tree's box count
 // from device memory, so selection, tree and list counting need one host sync in all.
 int tree_queue(sph_ctx *c) {
@@ -353,7 +355,7 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_rng, 4 * dense_total * sizeof(int));
     ENS(c->b_near, 3 * dense_total + 16);
     ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
-    ENS(c->b_lvl, 48 * sizeof(int));
+    ENS(c->b_lvl, 64 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
     ENS(c->b_level, cap * sizeof(int));
     ENS(c->b_key, cap * sizeof(uint32_t));
@@ -379,7 +381,7 @@ int tree_queue(sph_ctx *c) {
     c->launches += 2 + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->pinned + 50, A.T.lvl_src, (Lmax + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
@@ -413,11 +415,14 @@ int tree_levels_read(sph_ctx *c) {
     c->lvl_count.assign(Lmax + 1, 0);
     c->lvl_base.assign(Lmax + 1, 0);
     c->lvl_src.assign(Lmax + 1, 0);
+    c->lvl_leaf.assign(Lmax + 1, 0);
     int64_t tot = 0;
     for (int l = 0; l <= Lmax; ++l) {
-        c->lvl_src[l] = c->pinned[50 + l];
+        c->lvl_src[l] = c->pinned[64 + l];
+        c->lvl_leaf[l] = c->pinned[80 + l];
         c->lvl_count[l] = c->pinned[8 + 16 + l];
-        if (c->lvl_src[l] < 0 || c->lvl_src[l] > c->pinned[8 + 16 + l])
+        if (c->lvl_src[l] < 0 || c->lvl_src[l] > c->pinned[8 + 16 + l] || c->lvl_leaf[l] < 0 ||
+            c->lvl_leaf[l] > c->pinned[8 + 16 + l])
             return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         if (c->lvl_count[l] < 0) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         c->lvl_base[l] = (int)tot;
@@ -752,16 +757,19 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                 }
                 continue;
             }
+            // only levels that hold leaves with targets (counted by the tree build) get a launch;
+            // the separable form's launch is sized by that count
+            if (c->lvl_count[l] == 0 || c->lvl_leaf[l] == 0) continue;
             const bool tc_here = l2p_tc && (c->l2p_tc_tables || (1 << (c->D - l)) == 4);
-            if (c->lvl_count[l] > 0 && sep_all && !tc_here) {
-                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_count[l], out, c->stream);
+            if (sep_all && !tc_here) {
+                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_leaf[l], out, c->stream);
                 ++c->launches;
-            } else if (c->lvl_count[l] > 0 && F.O.e_off[l] >= 0) {
+            } else if (F.O.e_off[l] >= 0) {
                 if (tc_here) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
                 else fmm_l2p_gemm_level(F, l, c->lvl_base[l], c->lvl_count[l], out, c->stream);
                 ++c->launches;
-            } else if (c->lvl_count[l] > 0 && F.l2p_sep) {
-                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_count[l], out, c->stream);
+            } else if (F.l2p_sep) {
+                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_leaf[l], out, c->stream);
                 ++c->launches;
             }
         }
@@ -769,8 +777,14 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         c->l2p_tc_used = l2p_tc;
     }
     if (tm) tm->mark_at(8, c->stream);
-    fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
-    c->launches += nb > 0;
+    // the leaf kernel has work only where a leaf's L2P or near field is not taken by the kernels
+    // above: with the Chebyshev far field, the separable L2P and the separate near field that is
+    // the leaves of levels 0 and 1
+    const bool leaf_taken = F.leaf_l2p_done && F.O.method == FAR_CHEB && F.l2p_sep && F.p2p_separate;
+    if (!leaf_taken || c->lvl_leaf[0] + (c->Lmax >= 1 ? c->lvl_leaf[1] : 0) > 0) {
+        fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
+        c->launches += nb > 0;
+    }
     if (F.p2p_separate) {
         CK(cudaMemsetAsync(F.skip_count, 0, sizeof(unsigned long long), c->stream));
         if (F.gtab) {
@@ -848,6 +862,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(c->lvl_count.data(), c->lvl_count.size() * sizeof(int));
     put(c->lvl_base.data(), c->lvl_base.size() * sizeof(int));
     put(c->lvl_src.data(), c->lvl_src.size() * sizeof(int));
+    put(c->lvl_leaf.data(), c->lvl_leaf.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
                           c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, c->m2l_tiles, c->m2l_form,
@@ -1179,7 +1194,7 @@ sph_ctx *make_sub(sph_ctx *parent, bool shared_stream = false) {
         }
         c->own_stream = true;
     }
-    if (cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost(&c->pinned, 96 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
@@ -1579,7 +1594,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (!c) return SPH_ENOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 96 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SPH_ECUDA;

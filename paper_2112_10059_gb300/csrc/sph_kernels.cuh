@@ -60,6 +60,8 @@ struct TreeDev {
     int *box_at;         // concatenated dense levels
     int *lvl_base, *lvl_count;   // [Lmax+1]
     int *lvl_src;                // [Lmax+1] boxes holding sources per level (zeroed before the emit)
+    int *lvl_leaf;               // [Lmax+1] leaves holding targets per level (lvl_src + 16,
+                                 // zeroed with it)
     int *b_level;
     uint32_t *b_key;
     int *b_sb, *b_se, *b_tb, *b_te, *b_parent;
