@@ -40,11 +40,12 @@
  *    completed, so stream order holds as usual.  SPH_PDL=0 in the environment
  *    (read once per process) launches them in plain stream order.
  *  - A CUDA error poisons the context: every later call returns SPH_ECUDA.
- *  - Every spin-wait of the library's kernels is bounded.  The look-back of the selection and
- *    of the device scan give up after a number of polls and report it (SPH_ETIMEOUT, or the
- *    flag of sph_select_noalloc); the context stays usable.  For tests, the environment can
- *    lower those limits and inject a failure: SPH_WAIT_LIMIT_SELECT=<polls> (read by sph_create
- *    and by every sph_select_noalloc call), SPH_WAIT_LIMIT_SCAN=<polls> (read by every
+ *  - Every spin-wait of the library's kernels is bounded.  The look-back of the selection (its
+ *    one-pass form: SPH_SELECT_LOOKBACK=1, or grids without per-brick statistics) and of the
+ *    device scan give up after a number of polls and report it (SPH_ETIMEOUT, or the flag of
+ *    sph_select_noalloc); the context stays usable.  For tests, the environment can lower
+ *    those limits and inject a failure: SPH_WAIT_LIMIT_SELECT=<polls> (read by sph_create
+ *    and by every sph_select_noalloc call, as is SPH_SELECT_LOOKBACK), SPH_WAIT_LIMIT_SCAN=<polls> (read by every
  *    sph_scan_i32 call), SPH_FAULT=alloc[:k] (read by sph_create: the k-th device allocation of
  *    that context, default the first, fails with SPH_ENOMEM; later ones proceed).
  *  - One context per host thread; contexts are independent.

@@ -4,10 +4,12 @@
 //
 // Pass 1 (k_brick_stats, bricks of 16^3 cells): max q and max |E| over all cells (NaN
 // ignored) and, per brick, the largest q, the smallest and largest |E| and whether an |E| is
-// NaN.  Default: k_select_onepass (below) does count, offsets and emit in one pass over the
-// grid with a decoupled look-back across bricks; a whole brick that those statistics decide
-// (no source, and every cell or no cell a target) is emitted without reading it again.
-// The two-pass form that follows (after k_grid_max, the maxima alone) is kept as a reference:
+// NaN.  A whole brick that those statistics decide (no source, and every cell or no cell a
+// target) is emitted without reading it again.  Default: k_select_count (counts: decided
+// bricks at once, the others read), k_scan2 (offsets), k_select_emit (points), no CTA waiting
+// for another.  Alternatives: k_select_onepass does count, offsets and emit in one pass with a
+// decoupled look-back across bricks (also the form without statistics); the two-pass form
+// that follows (after k_grid_max, the maxima alone) is kept as a reference:
 // Pass 2 (k_select_count): per 16^3 brick (a Morton-contiguous key range),
 //         count selected sources / targets.
 // Pass 3 (k_scan_bricks): exclusive scan of the brick counts.
@@ -15,6 +17,8 @@
 //         Morton order inside the brick and write key, packed (i,j,k) and, for
 //         sources, q (consumers scale it to I_h = source_scale * q * h^3).
 // The rules compare in FP64: (double)q >= i_frac * (double)qmax.
+#include <algorithm>
+
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -450,158 +454,88 @@ __device__ __forceinline__ void publish(unsigned long long *state, int brick, in
 }
 
 
-// One pass over the grid: each CTA takes the next brick in dispatch order (ticket), reads
-// it row by row, evaluates both rules, ranks its cells in Morton order, finds its output
-// offset by decoupled look-back over the preceding bricks, and writes its points.
-__global__ void __launch_bounds__(512) k_select_onepass(
-        SelRule r, const float *__restrict__ q, const float *__restrict__ e, const uint8_t *__restrict__ mask,
-        const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
-        int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
-        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
-        uint8_t *__restrict__ tmask, unsigned wait_limit, const float4 *__restrict__ bstat) {
-    pdl_enter();
-    __shared__ int s_brick, s_mode;
-    __shared__ float s_thr_q, s_thr_e;
-    __shared__ int s_qpos;
-    __shared__ int ws[16], wt[16];
-    __shared__ unsigned rs[16], rt[16];
-    __shared__ int s_stop;
-    // targets staged at brick-local rank j, slot j + j / 32: a thread's consecutive ranks (8 apart
-    // from its neighbours') then fall in distinct banks
-    __shared__ uint32_t st_key[4096 + 128], st_pc[4096 + 128];
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        s_brick = (int)atomicAdd(ticket, 1u);
-        double thr_q, thr_e;
-        bool qpos;
-        thresholds(r, maxes, thr_q, thr_e, qpos);
-        s_thr_q = ge_threshold_f32(thr_q);
-        s_thr_e = ge_threshold_f32(thr_e);
-        s_qpos = qpos;
-        s_mode = bstat ? brick_mode(r, (uint32_t)s_brick, bstat[s_brick], s_thr_q, s_thr_e, qpos) : 0;
-    }
-    __syncthreads();
-    const int brick = s_brick;
-    const int b = r.brick_edge_log2;
-    const int ncell = 1 << (3 * b);
-    uint32_t bx, by, bz;
-    demorton3((uint32_t)brick, bx, by, bz);
-    const int x0 = bx << b, y0 = by << b, z0 = bz << b;
-    const float thr_q = s_thr_q, thr_e = s_thr_e;
-    const bool qpos = s_qpos;
-    if (s_mode != 0) {
-        // a whole brick decided by its statistics (16^3 cells inside the grid): no source, and
-        // every cell (mode 1) or none (mode 2) a target -- counts known, nothing read
-        const unsigned agg_t = s_mode == 1 ? (unsigned)ncell : 0u;
-        if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, 0u, agg_t));
-        if (tmask) {
-            const uint8_t m = s_mode == 1 ? 1 : 0;
-            if ((r.nx & 15) == 0 && (reinterpret_cast<uintptr_t>(tmask) & 15) == 0) {
-                if (tid < 256) {   // one 16-byte store per row of the brick
-                    const int64_t o = (int64_t)x0 + (int64_t)r.nx * ((int64_t)(y0 + (tid & 15)) +
-                                                                     (int64_t)r.ny * (z0 + (tid >> 4)));
-                    const uint32_t m4 = m * 0x01010101u;
-                    *reinterpret_cast<uint4 *>(tmask + o) = make_uint4(m4, m4, m4, m4);
-                }
-            } else {
-                for (int i = tid; i < ncell; i += blockDim.x)
-                    tmask[(int64_t)(x0 + (i & 15)) +
-                          (int64_t)r.nx * ((int64_t)(y0 + ((i >> 4) & 15)) + (int64_t)r.ny * (z0 + (i >> 8)))] = m;
-            }
-        }
-        unsigned pre_s = 0, pre_t = 0;
-        const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
-        if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, 0u, agg_t, totals);
-        if (s_mode == 1) {
-            for (int i = tid; i < ncell; i += blockDim.x) {
-                const uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)i;
-                trg_key[pre_t + i] = key;
-                if (trg_pc) {
-                    uint32_t lx, ly, lz;
-                    demorton3((uint32_t)i, lx, ly, lz);
-                    trg_pc[pre_t + i] = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
-                }
-            }
-        }
-        return;
-    }
-    // Thread t owns the brick's local Morton keys 8t .. 8t+7: a 2x2x2 micro-cube, so the
-    // 8 cells follow from one decode; its loads are all issued before any is used (a warp's
-    // cells form an 8x8x4 block, whose rows the L1 serves sector by sector).
-    int my_bits[8];
-    float my_q[8];
-    uint32_t mx, my, mz;
+// ---------------------------------------------------------------- parts shared by the brick kernels
+// (blocks of SEL_T = 512 threads, bricks of up to 16^3 cells)
+constexpr int SEL_T = 512;
+
+// Thread `tid`'s 2x2x2 Morton micro-cube of the brick at (x0, y0, z0): the brick-local Morton
+// keys 8 tid .. 8 tid + 7, so the 8 cells follow from one decode.  Both rules are evaluated for
+// each cell (bit 0 source, bit 1 target; q kept for the sources); all loads are issued before
+// any is used (a warp's cells form an 8x8x4 block, whose rows the L1 serves sector by sector).
+// Cell u sits at (mx + (u & 1), my + ((u >> 1) & 1), mz + (u >> 2)): the pairs (u, u + 1), u
+// even, are x-neighbours at an even x, read as one float2 when the row pitch and the arrays
+// allow it.  The target mask is written if `tmask` (two cells per 2-byte store where aligned).
+__device__ __forceinline__ void cube_rules(const SelRule &r, const float *__restrict__ q, const float *__restrict__ e,
+                                           const uint8_t *__restrict__ mask, int tid, int x0, int y0, int z0,
+                                           int ncell, float thr_q, float thr_e, bool qpos,
+                                           uint8_t *__restrict__ tmask, int (&my_bits)[8], float (&my_q)[8],
+                                           uint32_t &mx, uint32_t &my, uint32_t &mz) {
     demorton3((uint32_t)(8 * tid), mx, my, mz);
-    {
-        // cell u of the micro-cube sits at (mx + (u & 1), my + ((u >> 1) & 1), mz + (u >> 2)):
-        // the pairs (u, u + 1), u even, are x-neighbours at an even x, read as one float2 when
-        // the row pitch and the arrays allow it
-        const bool vec2 = (r.nx & 1) == 0 && (reinterpret_cast<uintptr_t>(q) & 7) == 0 &&
-                          (r.trg_mode != 1 || (reinterpret_cast<uintptr_t>(e) & 7) == 0);
-        float ev[8];
-        uint32_t lin[8];
-        bool in[8];
+    const bool vec2 = (r.nx & 1) == 0 && (reinterpret_cast<uintptr_t>(q) & 7) == 0 &&
+                      (r.trg_mode != 1 || (reinterpret_cast<uintptr_t>(e) & 7) == 0);
+    float ev[8];
+    uint32_t lin[8];
+    bool in[8];
+#pragma unroll
+    for (int v2 = 0; v2 < 4; ++v2) {
+        const int u0 = 2 * v2;
+        const int x = x0 + (int)mx, y = y0 + (int)my + (v2 & 1), z = z0 + (int)mz + (v2 >> 1);
+        const bool row = 8 * tid + u0 < ncell && y < r.ny && z < r.nz;
+        in[u0] = row && x < r.nx;
+        in[u0 + 1] = row && x + 1 < r.nx;
+        const uint32_t l0 = row ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
+        lin[u0] = l0;
+        lin[u0 + 1] = l0 + 1;
+        if (vec2 && in[u0 + 1] && r.trg_mode != 2) {
+            const float2 a = __ldg(reinterpret_cast<const float2 *>(q + l0));
+            my_q[u0] = a.x;
+            my_q[u0 + 1] = a.y;
+            float2 c = make_float2(0.f, 0.f);
+            if (r.trg_mode == 1) c = __ldg(reinterpret_cast<const float2 *>(e + l0));
+            ev[u0] = c.x;
+            ev[u0 + 1] = c.y;
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int u = u0 + h;
+                my_q[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
+                ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
+                if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        int bits = 0;
+        if (in[u]) {
+            if (r.src_all || (qpos && my_q[u] >= thr_q)) bits |= 1;
+            if (r.trg_mode == 0) bits |= 2;
+            else if (r.trg_mode == 1) { if (ev[u] >= thr_e) bits |= 2; }
+            else if (ev[u] != 0.f) bits |= 2;
+        }
+        my_bits[u] = bits;
+    }
+    if (tmask) {
 #pragma unroll
         for (int v2 = 0; v2 < 4; ++v2) {
             const int u0 = 2 * v2;
-            const int x = x0 + (int)mx, y = y0 + (int)my + (v2 & 1), z = z0 + (int)mz + (v2 >> 1);
-            const bool row = 8 * tid + u0 < ncell && y < r.ny && z < r.nz;
-            in[u0] = row && x < r.nx;
-            in[u0 + 1] = row && x + 1 < r.nx;
-            const uint32_t l0 = row ? (uint32_t)x + (uint32_t)r.nx * ((uint32_t)y + (uint32_t)r.ny * (uint32_t)z) : 0u;
-            lin[u0] = l0;
-            lin[u0 + 1] = l0 + 1;
-            if (vec2 && in[u0 + 1] && r.trg_mode != 2) {
-                const float2 a = __ldg(reinterpret_cast<const float2 *>(q + l0));
-                my_q[u0] = a.x;
-                my_q[u0 + 1] = a.y;
-                float2 c = make_float2(0.f, 0.f);
-                if (r.trg_mode == 1) c = __ldg(reinterpret_cast<const float2 *>(e + l0));
-                ev[u0] = c.x;
-                ev[u0 + 1] = c.y;
+            if (vec2 && in[u0 + 1]) {      // even index: one 2-byte store
+                *reinterpret_cast<uint16_t *>(tmask + lin[u0]) =
+                    (uint16_t)((my_bits[u0] >> 1) | ((my_bits[u0 + 1] >> 1) << 8));
             } else {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int u = u0 + h;
-                    my_q[u] = in[u] ? __ldg(q + lin[u]) : 0.f;
-                    ev[u] = (in[u] && r.trg_mode == 1) ? __ldg(e + lin[u]) : 0.f;
-                    if (in[u] && r.trg_mode == 2) ev[u] = __ldg(mask + lin[u]) ? 1.f : 0.f;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            int bits = 0;
-            if (in[u]) {
-                if (r.src_all || (qpos && my_q[u] >= thr_q)) bits |= 1;
-                if (r.trg_mode == 0) bits |= 2;
-                else if (r.trg_mode == 1) { if (ev[u] >= thr_e) bits |= 2; }
-                else if (ev[u] != 0.f) bits |= 2;
-            }
-            my_bits[u] = bits;
-        }
-        if (tmask) {
-#pragma unroll
-            for (int v2 = 0; v2 < 4; ++v2) {
-                const int u0 = 2 * v2;
-                if (vec2 && in[u0 + 1]) {      // even index: one 2-byte store
-                    *reinterpret_cast<uint16_t *>(tmask + lin[u0]) =
-                        (uint16_t)((my_bits[u0] >> 1) | ((my_bits[u0 + 1] >> 1) << 8));
-                } else {
-                    if (in[u0]) tmask[lin[u0]] = (uint8_t)(my_bits[u0] >> 1);
-                    if (in[u0 + 1]) tmask[lin[u0 + 1]] = (uint8_t)(my_bits[u0 + 1] >> 1);
-                }
+                if (in[u0]) tmask[lin[u0]] = (uint8_t)(my_bits[u0] >> 1);
+                if (in[u0 + 1]) tmask[lin[u0 + 1]] = (uint8_t)(my_bits[u0 + 1] >> 1);
             }
         }
     }
-    int ns = 0, nt = 0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        ns += my_bits[u] & 1;
-        nt += (my_bits[u] >> 1) & 1;
-    }
-    // block exclusive scan of (ns, nt)
-    int lane = tid & 31, w = tid >> 5;
+}
+
+// Block exclusive scan of (ns, nt) in thread order; ws, wt: [16] shared.  Gives this thread's
+// exclusive offsets and the block's totals (ends with a barrier; ws / wt stay readable until
+// the caller's next barrier).
+__device__ __forceinline__ void block_scan2(int ns, int nt, int *ws, int *wt, int &base_s, int &base_t,
+                                            unsigned &agg_s, unsigned &agg_t) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int is = ns, it = nt;
     for (int o = 1; o < 32; o <<= 1) {
         int a = __shfl_up_sync(0xffffffffu, is, o);
@@ -622,22 +556,27 @@ __global__ void __launch_bounds__(512) k_select_onepass(
         if (lane < 16) { ws[lane] = a; wt[lane] = c; }
     }
     __syncthreads();
-    const int base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
-    const int base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
-    // decoupled look-back over the preceding bricks
-    const unsigned agg_s = (unsigned)ws[(blockDim.x >> 5) - 1], agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
-    if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, agg_s, agg_t));
-    unsigned pre_s = 0, pre_t = 0;
-    const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
-    if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, agg_s, agg_t, totals);
-    // targets: staged at their brick-local rank (in the space of s_q, read above), then
-    // written out by consecutive threads; sources (few) go straight out
-    int ps = (int)pre_s + base_s, lt = base_t;
+    base_s = (w > 0 ? ws[w - 1] : 0) + is - ns;
+    base_t = (w > 0 ? wt[w - 1] : 0) + it - nt;
+    agg_s = (unsigned)ws[(blockDim.x >> 5) - 1];
+    agg_t = (unsigned)wt[(blockDim.x >> 5) - 1];
+}
+
+// The micro-cube's selected cells written out: sources (few) straight to src_* from index ps;
+// targets staged at their brick-local rank j (slot j + j / 32: a thread's consecutive ranks, 8
+// apart from its neighbours', fall in distinct banks), then written by consecutive threads to
+// trg_key[pt0 ..] (and trg_pc).  Ends after a barrier that follows the staging.
+__device__ __forceinline__ void cube_emit(uint32_t brick, int b, int tid, int x0, int y0, int z0, uint32_t mx,
+                                          uint32_t my, uint32_t mz, const int (&my_bits)[8], const float (&my_q)[8],
+                                          int ps, int lt, unsigned pt0, unsigned agg_t, uint32_t *st_key,
+                                          uint32_t *st_pc, uint32_t *__restrict__ src_key,
+                                          uint32_t *__restrict__ src_pc, float *__restrict__ src_q,
+                                          uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int lk = 8 * tid + u;
         if (!my_bits[u]) continue;
-        const uint32_t key = ((uint32_t)brick << (3 * b)) | (uint32_t)lk;
+        const uint32_t key = (brick << (3 * b)) | (uint32_t)lk;
         const uint32_t pc = pack_ijk(x0 + mx + (u & 1), y0 + my + ((u >> 1) & 1), z0 + mz + (u >> 2));
         if (my_bits[u] & 1) {
             src_key[ps] = key;
@@ -653,8 +592,241 @@ __global__ void __launch_bounds__(512) k_select_onepass(
     }
     __syncthreads();
     for (int i = tid; i < (int)agg_t; i += blockDim.x) {
-        trg_key[pre_t + i] = st_key[i + (i >> 5)];
-        if (trg_pc) trg_pc[pre_t + i] = st_pc[i + (i >> 5)];
+        trg_key[pt0 + i] = st_key[i + (i >> 5)];
+        if (trg_pc) trg_pc[pt0 + i] = st_pc[i + (i >> 5)];
+    }
+}
+
+// A brick of 16^3 cells decided by its statistics (mode 1: every cell a target, mode 2: none;
+// no source either way): its target mask, and for mode 1 its 4096 targets from trg_key[pt0]
+// in Morton order (keys brick << 12 | i).
+__device__ __forceinline__ void brick_emit_decided(const SelRule &r, uint32_t brick, int mode, int tid, int x0,
+                                                   int y0, int z0, unsigned pt0, uint32_t *__restrict__ trg_key,
+                                                   uint32_t *__restrict__ trg_pc, uint8_t *__restrict__ tmask) {
+    if (tmask) {
+        const uint8_t m = mode == 1 ? 1 : 0;
+        if ((r.nx & 15) == 0 && (reinterpret_cast<uintptr_t>(tmask) & 15) == 0) {
+            for (int row = tid; row < 256; row += blockDim.x) {   // one 16-byte store per row
+                const int64_t o = (int64_t)x0 + (int64_t)r.nx * ((int64_t)(y0 + (row & 15)) +
+                                                                 (int64_t)r.ny * (z0 + (row >> 4)));
+                const uint32_t m4 = m * 0x01010101u;
+                *reinterpret_cast<uint4 *>(tmask + o) = make_uint4(m4, m4, m4, m4);
+            }
+        } else {
+            for (int i = tid; i < 4096; i += blockDim.x)
+                tmask[(int64_t)(x0 + (i & 15)) +
+                      (int64_t)r.nx * ((int64_t)(y0 + ((i >> 4) & 15)) + (int64_t)r.ny * (z0 + (i >> 8)))] = m;
+        }
+    }
+    if (mode != 1) return;
+    for (int i = tid; i < 4096; i += blockDim.x) {
+        trg_key[pt0 + i] = (brick << 12) | (uint32_t)i;
+        if (trg_pc) {
+            uint32_t lx, ly, lz;
+            demorton3((uint32_t)i, lx, ly, lz);
+            trg_pc[pt0 + i] = pack_ijk(x0 + lx, y0 + ly, z0 + lz);
+        }
+    }
+}
+
+// Thresholds of both rules in FP32 (thread 0), for the whole block.
+__device__ __forceinline__ void block_thresholds(const SelRule &r, const unsigned *maxes, float *s_thr_q,
+                                                 float *s_thr_e, int *s_qpos) {
+    double thr_q, thr_e;
+    bool qpos;
+    thresholds(r, maxes, thr_q, thr_e, qpos);
+    *s_thr_q = ge_threshold_f32(thr_q);
+    *s_thr_e = ge_threshold_f32(thr_e);
+    *s_qpos = qpos;
+}
+
+// ---------------------------------------------------------------- one pass with look-back
+// Each CTA takes the next brick in dispatch order (ticket), reads it, evaluates both rules,
+// ranks its cells in Morton order, finds its output offset by decoupled look-back over the
+// preceding bricks, and writes its points (a brick decided by its statistics: counts known,
+// nothing read).
+__global__ void __launch_bounds__(SEL_T) k_select_onepass(
+        SelRule r, const float *__restrict__ q, const float *__restrict__ e, const uint8_t *__restrict__ mask,
+        const unsigned *__restrict__ maxes, unsigned long long *__restrict__ state, unsigned *__restrict__ ticket,
+        int nbr, int *__restrict__ totals, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
+        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
+        uint8_t *__restrict__ tmask, unsigned wait_limit, const float4 *__restrict__ bstat) {
+    pdl_enter();
+    __shared__ int s_brick, s_mode;
+    __shared__ float s_thr_q, s_thr_e;
+    __shared__ int s_qpos;
+    __shared__ int ws[16], wt[16];
+    __shared__ unsigned rs[16], rt[16];
+    __shared__ int s_stop;
+    __shared__ uint32_t st_key[4096 + 128], st_pc[4096 + 128];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_brick = (int)atomicAdd(ticket, 1u);
+        block_thresholds(r, maxes, &s_thr_q, &s_thr_e, &s_qpos);
+        s_mode = bstat ? brick_mode(r, (uint32_t)s_brick, bstat[s_brick], s_thr_q, s_thr_e, s_qpos) : 0;
+    }
+    __syncthreads();
+    const int brick = s_brick;
+    const int b = r.brick_edge_log2;
+    const int ncell = 1 << (3 * b);
+    uint32_t bx, by, bz;
+    demorton3((uint32_t)brick, bx, by, bz);
+    const int x0 = bx << b, y0 = by << b, z0 = bz << b;
+    if (s_mode != 0) {
+        const unsigned agg_t = s_mode == 1 ? (unsigned)ncell : 0u;
+        if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, 0u, agg_t));
+        unsigned pre_s = 0, pre_t = 0;
+        const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
+        if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, 0u, agg_t, totals);
+        brick_emit_decided(r, (uint32_t)brick, s_mode, tid, x0, y0, z0, pre_t, trg_key, trg_pc, tmask);
+        return;
+    }
+    int my_bits[8];
+    float my_q[8];
+    uint32_t mx, my, mz;
+    cube_rules(r, q, e, mask, tid, x0, y0, z0, ncell, s_thr_q, s_thr_e, s_qpos, tmask, my_bits, my_q, mx, my, mz);
+    int ns = 0, nt = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        ns += my_bits[u] & 1;
+        nt += (my_bits[u] >> 1) & 1;
+    }
+    int base_s, base_t;
+    unsigned agg_s, agg_t;
+    block_scan2(ns, nt, ws, wt, base_s, base_t, agg_s, agg_t);
+    if (tid == 0) atomicExch(state + brick, pack_state(brick == 0 ? 2u : 1u, agg_s, agg_t));
+    unsigned pre_s = 0, pre_t = 0;
+    const bool ok = look_back(state, brick, wait_limit, pre_s, pre_t, rs, rt, &s_stop);
+    if (tid == 0) publish(state, brick, nbr, !ok, pre_s, pre_t, agg_s, agg_t, totals);
+    cube_emit((uint32_t)brick, b, tid, x0, y0, z0, mx, my, mz, my_bits, my_q, (int)pre_s + base_s, base_t, pre_t,
+              agg_t, st_key, st_pc, src_key, src_pc, src_q, trg_key, trg_pc);
+}
+
+// ---------------------------------------------------------------- count, scan, emit (default)
+// With per-brick statistics most bricks are decided without a read, and the selection runs as
+// a count pass, the scan of the per-brick counts (k_scan2) and an emit pass, none of whose CTAs
+// waits for another.  Both passes are persistent: CTA c takes the bricks c, c + gridDim.x, ...,
+// SEL_T of them at a time (their modes found in parallel, one thread per brick); only the
+// undecided ones are read (in both passes).
+
+// counts of every brick: cnt_s / cnt_t [nbr]
+__global__ void __launch_bounds__(SEL_T) k_select_count(SelRule r, const float *__restrict__ q,
+                                                        const float *__restrict__ e, const uint8_t *__restrict__ mask,
+                                                        const unsigned *__restrict__ maxes,
+                                                        const float4 *__restrict__ bstat, int nbr,
+                                                        int *__restrict__ cnt_s, int *__restrict__ cnt_t) {
+    pdl_enter();
+    __shared__ float s_thr_q, s_thr_e;
+    __shared__ int s_qpos;
+    __shared__ int s_und[SEL_T], s_nund;
+    __shared__ int ws[16], wt[16];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        block_thresholds(r, maxes, &s_thr_q, &s_thr_e, &s_qpos);
+        s_nund = 0;
+    }
+    __syncthreads();
+    const int b = r.brick_edge_log2;
+    const int ncell = 1 << (3 * b);
+    for (int k0 = 0; blockIdx.x + (int64_t)k0 * gridDim.x < nbr; k0 += SEL_T) {
+        const int64_t bk = blockIdx.x + (int64_t)(k0 + tid) * gridDim.x;
+        if (bk < nbr) {
+            const int m = brick_mode(r, (uint32_t)bk, bstat[bk], s_thr_q, s_thr_e, s_qpos);
+            if (m != 0) {
+                cnt_s[bk] = 0;
+                cnt_t[bk] = m == 1 ? ncell : 0;
+            } else {
+                s_und[atomicAdd(&s_nund, 1)] = (int)bk;
+            }
+        }
+        __syncthreads();
+        const int nu = s_nund;
+        for (int i = 0; i < nu; ++i) {
+            const int brick = s_und[i];
+            uint32_t bx, by, bz;
+            demorton3((uint32_t)brick, bx, by, bz);
+            int my_bits[8];
+            float my_q[8];
+            uint32_t mx, my, mz;
+            cube_rules(r, q, e, mask, tid, bx << b, by << b, bz << b, ncell, s_thr_q, s_thr_e, s_qpos, nullptr,
+                       my_bits, my_q, mx, my, mz);
+            int ns = 0, nt = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                ns += my_bits[u] & 1;
+                nt += (my_bits[u] >> 1) & 1;
+            }
+            int base_s, base_t;
+            unsigned agg_s, agg_t;
+            block_scan2(ns, nt, ws, wt, base_s, base_t, agg_s, agg_t);
+            if (tid == 0) {
+                cnt_s[brick] = (int)agg_s;
+                cnt_t[brick] = (int)agg_t;
+            }
+            __syncthreads();                       // ws / wt reused by the next brick
+        }
+        if (tid == 0) s_nund = 0;
+        __syncthreads();
+    }
+}
+
+// every brick's points from the scanned offsets off_s / off_t [nbr]
+__global__ void __launch_bounds__(SEL_T) k_select_emit(
+        SelRule r, const float *__restrict__ q, const float *__restrict__ e, const uint8_t *__restrict__ mask,
+        const unsigned *__restrict__ maxes, const float4 *__restrict__ bstat, int nbr, const int *__restrict__ off_s,
+        const int *__restrict__ off_t, uint32_t *__restrict__ src_key, uint32_t *__restrict__ src_pc,
+        float *__restrict__ src_q, uint32_t *__restrict__ trg_key, uint32_t *__restrict__ trg_pc,
+        uint8_t *__restrict__ tmask) {
+    pdl_enter();
+    __shared__ float s_thr_q, s_thr_e;
+    __shared__ int s_qpos;
+    __shared__ int s_mode[SEL_T], s_os[SEL_T], s_ot[SEL_T];
+    __shared__ int ws[16], wt[16];
+    __shared__ uint32_t st_key[4096 + 128], st_pc[4096 + 128];
+    const int tid = threadIdx.x;
+    if (tid == 0) block_thresholds(r, maxes, &s_thr_q, &s_thr_e, &s_qpos);
+    __syncthreads();
+    const int b = r.brick_edge_log2;
+    const int ncell = 1 << (3 * b);
+    for (int k0 = 0; blockIdx.x + (int64_t)k0 * gridDim.x < nbr; k0 += SEL_T) {
+        const int64_t bk = blockIdx.x + (int64_t)(k0 + tid) * gridDim.x;
+        if (bk < nbr) {
+            s_mode[tid] = brick_mode(r, (uint32_t)bk, bstat[bk], s_thr_q, s_thr_e, s_qpos);
+            s_os[tid] = off_s[bk];
+            s_ot[tid] = off_t[bk];
+        }
+        __syncthreads();
+        const int64_t left = (nbr - 1 - (blockIdx.x + (int64_t)k0 * gridDim.x)) / gridDim.x + 1;
+        const int kn = (int)min((int64_t)SEL_T, left);
+        for (int j = 0; j < kn; ++j) {
+            const uint32_t brick = (uint32_t)(blockIdx.x + (int64_t)(k0 + j) * gridDim.x);
+            uint32_t bx, by, bz;
+            demorton3(brick, bx, by, bz);
+            const int x0 = bx << b, y0 = by << b, z0 = bz << b;
+            const int mode = s_mode[j];
+            if (mode != 0) {
+                brick_emit_decided(r, brick, mode, tid, x0, y0, z0, (unsigned)s_ot[j], trg_key, trg_pc, tmask);
+                continue;
+            }
+            int my_bits[8];
+            float my_q[8];
+            uint32_t mx, my, mz;
+            cube_rules(r, q, e, mask, tid, x0, y0, z0, ncell, s_thr_q, s_thr_e, s_qpos, tmask, my_bits, my_q, mx,
+                       my, mz);
+            int ns = 0, nt = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                ns += my_bits[u] & 1;
+                nt += (my_bits[u] >> 1) & 1;
+            }
+            int base_s, base_t;
+            unsigned agg_s, agg_t;
+            block_scan2(ns, nt, ws, wt, base_s, base_t, agg_s, agg_t);
+            cube_emit(brick, b, tid, x0, y0, z0, mx, my, mz, my_bits, my_q, s_os[j] + base_s, base_t,
+                      (unsigned)s_ot[j], agg_t, st_key, st_pc, src_key, src_pc, src_q, trg_key, trg_pc);
+            __syncthreads();                       // staging and ws / wt reused by the next brick
+        }
+        __syncthreads();                           // s_mode / s_os / s_ot reused
     }
 }
 
@@ -671,12 +843,14 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     r.e_app = A.e_app;
     int64_t n = (int64_t)A.nx * A.ny * A.nz;
     cudaMemsetAsync(A.maxes, 0, 2 * sizeof(unsigned), st);
+    cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
     int gm = (int)((n / 4 + 255) / 256);
     if (gm > 152 * 8) gm = 152 * 8;
     if (gm < 1) gm = 1;
     const float *gq = r.src_all ? nullptr : A.q, *ge = r.trg_mode == 1 ? A.emag : nullptr;
     // one pass over bricks of 16^3 cells: the maxima with the per-brick statistics
     const bool stats = !A.two_pass && A.bstat != nullptr && b == 4 && (gq || ge);
+    const float4 *bstat = reinterpret_cast<const float4 *>(A.bstat);
     if (stats) launch_pdl(k_brick_stats, nbr, STAT_T, 0, st, r, gq, ge, reinterpret_cast<float4 *>(A.bstat), A.maxes);
     else if (gq || ge) launch_pdl(k_grid_max, gm, 256, 0, st, gq, ge, n, A.maxes);
     if (A.two_pass) {
@@ -689,15 +863,24 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
                                                   A.trg_key, A.trg_pc, A.tmask);
         return cudaGetLastError() == cudaSuccess ? 0 : -1;
     }
+    if (stats && !A.lookback) {
+        const int grid = std::max(1, std::min(nbr, 2 * sm_count()));
+        launch_pdl(k_select_count, grid, SEL_T, 0, st, r, A.q, A.emag, A.mask, (const unsigned *)A.maxes, bstat, nbr,
+                   A.cnt_s, A.cnt_t);
+        launch_pdl(k_scan2, 1, 1024, 0, st, A.cnt_s, A.cnt_t, A.off_s, A.off_t, nbr, A.totals);
+        launch_pdl(k_select_emit, grid, SEL_T, 0, st, r, A.q, A.emag, A.mask, (const unsigned *)A.maxes, bstat, nbr,
+                   (const int *)A.off_s, (const int *)A.off_t, A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc,
+                   A.tmask);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
     // one pass: the look-back states live in cnt_s .. cnt_t (2 ints per brick), the ticket in off_s[0]
     unsigned long long *state = reinterpret_cast<unsigned long long *>(A.cnt_s);
     unsigned *ticket = reinterpret_cast<unsigned *>(A.off_s);
     cudaMemsetAsync(state, 0, sizeof(unsigned long long) * nbr, st);
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
-    cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
-    launch_pdl(k_select_onepass, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
+    launch_pdl(k_select_onepass, nbr, SEL_T, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
                                           A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask, A.wait_limit,
-                                          stats ? (const float4 *)A.bstat : nullptr);
+                                          stats ? bstat : nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

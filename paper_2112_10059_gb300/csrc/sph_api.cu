@@ -82,7 +82,8 @@ struct sph_ctx {
     bool translate_per_box = false;   // one CTA per box for M2L / L2L instead of the batched GEMMs
     bool tc_used = false;             // this eval ran the tensor-core translations
     bool l2l_eight = true;            // tensor-core L2L: all 8 children per CTA (else one child per CTA)
-    int select_two_pass = 0;          // 1: two-pass selection instead of the one-pass look-back
+    int select_two_pass = 0;          // 1: the reference two-pass selection (maxima alone, every brick read twice)
+    int select_lookback = 0;          // 1: one-pass look-back selection instead of count / scan / emit
     bool p2p_in_leaf = false;         // near field inside the leaf kernel (reference form)
     bool l2p_simt = false;            // FP32 SIMT L2P even when the tensor-core images exist
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
@@ -252,6 +253,7 @@ int select_queue(sph_ctx *c) {
     A.i_frac = c->i_frac; A.e_frac = c->e_frac; A.e_app = c->e_app;
     A.maxes = P<unsigned>(c->b_maxes);
     A.two_pass = c->select_two_pass;
+    A.lookback = c->select_lookback;
     A.wait_limit = c->select_wait;
     A.cnt_s = P<int>(c->b_cnt); A.cnt_t = A.cnt_s + nbr;
     A.off_s = P<int>(c->b_off); A.off_t = A.off_s + nbr;
@@ -1224,6 +1226,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->radii = parent->radii; sub->pinv_eps = parent->pinv_eps;
     sub->translate_per_box = parent->translate_per_box; sub->l2l_eight = parent->l2l_eight;
     sub->select_two_pass = parent->select_two_pass;
+    sub->select_lookback = parent->select_lookback;
     sub->p2p_in_leaf = parent->p2p_in_leaf;
     sub->l2p_simt = parent->l2p_simt;
     sub->l2p_tc_tables = parent->l2p_tc_tables;
@@ -1603,6 +1606,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_TRANSLATE_PER_BOX")) c->translate_per_box = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2L_ONE_CHILD")) c->l2l_eight = atoi(e) == 0;
     if (const char *e = getenv("SPH_SELECT_TWO_PASS")) c->select_two_pass = atoi(e) != 0;
+    if (const char *e = getenv("SPH_SELECT_LOOKBACK")) c->select_lookback = atoi(e) != 0;
     if (const char *e = getenv("SPH_P2P_IN_LEAF")) c->p2p_in_leaf = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;

@@ -27,7 +27,10 @@ struct SelectArgs {
     unsigned *maxes;                 // [2]
     int *cnt_s, *cnt_t, *off_s, *off_t;   // [nbricks]
     int *totals;                     // [3] Ns, Nt, error flag (look-back gave up)
-    int two_pass = 0;                // 1: count pass + scan + emit pass instead of the one-pass kernel
+    int two_pass = 0;                // 1: the reference form (maxima alone, then count pass + scan + emit
+                                     //    pass, every brick read twice)
+    int lookback = 0;                // 1: one pass with a decoupled look-back even where per-brick
+                                     //    statistics allow the count / scan / emit passes
     uint32_t *src_key, *src_pc, *trg_key;
     uint32_t *trg_pc = nullptr;      // optional: targets' packed cells (key_pc of trg_key)
     float *src_q;

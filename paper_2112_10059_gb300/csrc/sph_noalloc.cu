@@ -104,6 +104,7 @@ extern "C" int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny,
     A.bstat = reinterpret_cast<float *>(scratch + NOALLOC_HEAD + 4 * (size_t)NOALLOC_MAX_BRICKS);   // 16-B aligned
     A.src_key = src_key_dev; A.src_pc = src_pc_dev; A.src_q = src_q_dev;
     A.trg_key = trg_key_dev; A.trg_pc = trg_pc_dev;
+    if (const char *e = getenv("SPH_SELECT_LOOKBACK")) A.lookback = atoi(e) != 0;   // the look-back form
     if (const char *e = getenv("SPH_WAIT_LIMIT_SELECT")) {   // tests: make the look-back give up
         char *end = nullptr;
         const unsigned long v = strtoul(e, &end, 10);

@@ -38,6 +38,7 @@ def _case():
 
 def test_selection_lookback_runs_out(sph, monkeypatch):
     p = _case()
+    monkeypatch.setenv("SPH_SELECT_LOOKBACK", "1")      # the form whose CTAs wait on one another
     monkeypatch.setenv("SPH_WAIT_LIMIT_SELECT", "0")
     c = sph.Context(0)
     with pytest.raises(sph.SphError) as e:
@@ -75,6 +76,7 @@ def test_noalloc_selection_reports_giving_up(sph, monkeypatch):
         torch.cuda.synchronize()
         return rc, counts.cpu().numpy().tolist()
 
+    monkeypatch.setenv("SPH_SELECT_LOOKBACK", "1")
     monkeypatch.setenv("SPH_WAIT_LIMIT_SELECT", "0")
     rc, (ns, nt, failed) = run()
     assert rc == 0 and failed != 0 and ns == -1 and nt == -1

@@ -96,20 +96,25 @@ def test_selection_threshold_ties_and_mask(sph, ctx):
     assert 150 in J and 250 not in J and 4090 not in J
 
 
+SELECT_FORMS = (("0", "0"), ("0", "1"), ("1", "0"))   # (SPH_SELECT_TWO_PASS, SPH_SELECT_LOOKBACK)
+
+
 @pytest.mark.parametrize("n", [45, 96, 200])
 def test_selection_one_pass_equals_two_pass(sph, monkeypatch, n):
-    """The one-pass look-back selection and the count / scan / emit passes both emit the
-    oracle's sets (odd row pitch at 45; 4096 bricks at 200)."""
+    """The three selection forms emit the oracle's sets (odd row pitch at 45; 4096 bricks at
+    200): count / scan / emit with the per-brick statistics (default), the one-pass look-back,
+    and the reference count / scan / emit that reads every brick twice."""
     p = si.streamer(n=n, box=1.0, chan_len=0.5, i_frac=1e-4, e_frac=0.2, targets_all=False, seed=41 + n,
                     name="s%d" % n)
     Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
-    for flag in ("1", "0"):
-        monkeypatch.setenv("SPH_SELECT_TWO_PASS", flag)
+    for two, lb in SELECT_FORMS:
+        monkeypatch.setenv("SPH_SELECT_TWO_PASS", two)
+        monkeypatch.setenv("SPH_SELECT_LOOKBACK", lb)
         c = sph.Context(0)
         sph.solve(p, c)
         J, T = sph.get_selection(c)
         c.close()
-        assert np.array_equal(J, Jo) and np.array_equal(T, To), flag
+        assert np.array_equal(J, Jo) and np.array_equal(T, To), (two, lb)
 
 
 @pytest.mark.parametrize("dims", [(64, 48, 48), (56, 48, 40)])
@@ -118,17 +123,20 @@ def test_selection_whole_bricks(sph, monkeypatch, dims):
     cell a target) are emitted without reading them again; ties at both thresholds, a source
     just below its threshold, NaN in q and |E|, an all-NaN brick and bricks that reach past the
     grid (row pitch 64: one 16-byte mask store per row; 56: byte stores) give the oracle's sets
-    in both selection forms, and the FMM on them passes the gate with S = 0 off the targets."""
+    in all three selection forms, and the FMM on them passes the gate with S = 0 off the
+    targets (the target mask of the decided bricks is read by the L2P of partly selected
+    leaves)."""
     p = si.brick_structured(*dims)
     Jo, To = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
-    for flag in ("0", "1"):
-        monkeypatch.setenv("SPH_SELECT_TWO_PASS", flag)
+    for two, lb in SELECT_FORMS:
+        monkeypatch.setenv("SPH_SELECT_TWO_PASS", two)
+        monkeypatch.setenv("SPH_SELECT_LOOKBACK", lb)
         c = sph.Context(0)
         _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
         J, T = sph.get_selection(c)
         c.close()
-        assert np.array_equal(J, Jo) and np.array_equal(T, To), flag
-        if flag == "0":
+        assert np.array_equal(J, Jo) and np.array_equal(T, To), (two, lb)
+        if two == "0":
             ref, _, _ = oracle.sph_problem(p)
             _check_fmm(out.cpu().numpy(), ref, To, p.name)
 
