@@ -208,7 +208,7 @@ __device__ __forceinline__ int warp_append(unsigned act, bool pred, int *counter
 
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
                              int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
-                             int *__restrict__ p2p_cnt) {
+                             int *__restrict__ p2p_cnt, int p2p_stride) {
     pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
@@ -246,15 +246,33 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
     if (l2p) F.l2p_list[T.lvl_base[l] + i] = b;
     i = warp_append(act, need, leaf_cnt);
     if (need) leaf_list[i] = b;
-    i = warp_append(act, p2p, p2p_cnt);
-    if (p2p) p2p_list[i] = b;
+    // near-field leaves by their number of kernel evaluations (targets x U-list sources and
+    // W-list nodes), in classes of halving size, so that the near field can start the heaviest
+    // first and end on light ones
+    int cls = P2P_CLASSES - 1;
+    if (p2p) {
+        int64_t ns = 0;
+        for (int u = F.L.u_off[b]; u < F.L.u_off[b + 1]; ++u) {
+            const int A = F.L.u_src[u];
+            ns += T.b_se[A] - T.b_sb[A];
+        }
+        if (F.O.method == FAR_CHEB) ns += (int64_t)(F.L.w_off[b + 1] - F.L.w_off[b]) * F.O.n;   // W nodes
+        const int64_t w = ns * (T.b_te[b] - T.b_tb[b]);
+        cls = 0;
+        while (cls < P2P_CLASSES - 1 && w < (P2P_CLASS0 >> cls)) ++cls;
+    }
+    for (int c = 0; c < P2P_CLASSES; ++c) {
+        const bool in = p2p && cls == c;
+        i = warp_append(act, in, p2p_cnt + c);
+        if (in) p2p_list[(size_t)c * p2p_stride + i] = b;
+    }
 }
 
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, cudaStream_t st) {
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, cudaStream_t st) {
     if (nboxes <= 0) return;
     launch_pdl(k_work_lists, (nboxes + 255) / 256, 256, 0, st, F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
-                                                       p2p_cnt);
+                                                       p2p_cnt, p2p_stride);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
@@ -885,10 +903,12 @@ __global__ void k_near_table(P2PConst K, float *tab) {
     if (i < GTAB_N) tab[i] = i == 0 ? K.wself : p2p_g<TAYLOR>((float)i, K);
 }
 
+// list: P2P_CLASSES lists of `stride` slots, count: their lengths; the leaves are taken class
+// by class, the heaviest first
 template <bool TAYLOR, bool TABLE>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
-                                                         const int *__restrict__ count, float *__restrict__ out,
-                                                         P2PConst K) {
+                                                         const int *__restrict__ count, int stride,
+                                                         float *__restrict__ out, P2PConst K) {
     pdl_enter();
     __shared__ float4 stage[P2P_CAP];
     __shared__ float tab[TABLE ? GTAB_N : 1];
@@ -900,14 +920,21 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
     __shared__ int ub[P2P_MAXU], un[P2P_MAXU], uo[P2P_MAXU + 1];
     __shared__ int s_own;                  // entry of the leaf itself in the staged U list, or -1
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cnt = *count;
+    __shared__ int ccnt[P2P_CLASSES];
+    if (tid < P2P_CLASSES) ccnt[tid] = count[tid];
+    __syncthreads();
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < P2P_CLASSES; ++c) cnt += ccnt[c];
     const TreeDev &T = F.T;
     const float h = F.kp.h;
     const float wsc = F.wscale * F.kp.C / (h * h * h);          // source weight -> scaled weight
     const float usc = F.kp.C / (h * h * h);                     // upward weight -> scaled weight
     const int n = F.O.n, np = F.O.npad;
     for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-        const int b = list[i];
+        int c = 0, j = i;
+        while (c < P2P_CLASSES - 1 && j >= ccnt[c]) j -= ccnt[c++];
+        const int b = list[(size_t)c * stride + j];
         const int tb = T.b_tb[b], te = T.b_te[b];
         const int nch = (te - tb + 31) >> 5;
         const int G = nch >= P2P_WARPS ? 1 : P2P_WARPS / nch;     // warps sharing a target chunk
@@ -1100,15 +1127,19 @@ void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st) {
     else launch_pdl(k_near_table<true>, (GTAB_N + 255) / 256, 256, 0, st, K, gtab);
 }
 
-void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st) {
+void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
+             cudaStream_t st) {
     if (nboxes <= 0) return;
     const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
     const P2PConst K = p2p_const(F);
     const bool taylor = K.bma_h < 0.5f, table = F.gtab != nullptr;
-    if (!taylor && !table) launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
-    else if (taylor && !table) launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
-    else if (!taylor) launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
-    else launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, out, K);
+    if (!taylor && !table)
+        launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+    else if (taylor && !table)
+        launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+    else if (!taylor)
+        launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+    else launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {

@@ -607,7 +607,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_work, (4 * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    ENS(c->b_work, ((3 + P2P_CLASSES) * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
     F.T = tree_dev(c);
@@ -635,8 +635,8 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     }
     S.w_src = P<int>(c->b_work);
     S.w_leaf = S.w_src + std::max(nb, 1);
-    S.w_p2p = S.w_leaf + std::max(nb, 1);
-    S.w_cnt = S.w_p2p + std::max(nb, 1);
+    S.w_p2p = S.w_leaf + std::max(nb, 1);                   // P2P_CLASSES lists of max(nb, 1) slots
+    S.w_cnt = S.w_p2p + P2P_CLASSES * std::max(nb, 1);
     F.l2p_list = S.w_cnt + 64;                  // [nb], per level at lvl_base[l]
     F.l2p_cnt = S.w_cnt + 40;                   // [16]
     S.Pd = pairs_dev(c);
@@ -665,7 +665,8 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     if (db > 0) CK(cudaMemsetAsync(c->b_dchk.p, 0, db, c->stream));
     CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
     if (S.tc) CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));   // M2M, M2L and L2L tiles' flags
-    fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 33, c->stream);
+    fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 56, std::max(nb, 1),
+                   c->stream);
     c->launches += nb > 0;
     if (tm) tm->mark_at(3, c->stream);
     // P2M of the leaves (and, without the tensor-core images, M2M) box by box; with them the
@@ -793,7 +794,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             fmm_near_table(F, const_cast<float *>(F.gtab), c->stream);
             ++c->launches;
         }
-        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 33, out, c->stream);
+        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->stream);
         c->launches += nb > 0;
     }
     if (tm) tm->mark_at(9, c->stream);

@@ -220,10 +220,16 @@ struct FmmDev {
 // returns the number of kernels launched
 int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count, bool leaves_only,
                      cudaStream_t st);
+// near-field leaves in classes by their number of kernel evaluations w: class c holds
+// P2P_CLASS0 >> c <= w < P2P_CLASS0 >> (c - 1) (class 0: w >= P2P_CLASS0, the last: the rest)
+constexpr int P2P_CLASSES = 6;
+constexpr int64_t P2P_CLASS0 = 1 << 16;
+// p2p_list: P2P_CLASSES lists of p2p_stride slots, p2p_cnt: their P2P_CLASSES counts
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, cudaStream_t st);
-// near field over the U lists of the leaves in p2p_list (adds into out)
-void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, float *out, cudaStream_t st);
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, cudaStream_t st);
+// near field over the U lists of the leaves in the class lists of p2p_list (adds into out)
+void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
+             cudaStream_t st);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
