@@ -32,8 +32,10 @@ namespace sph {
 // scans a tile of SCAN_TILE ints staged through shared memory; tiles find their offset by
 // decoupled look-back in ticket order (state word: 2-bit status | 32-bit value), or, for
 // short arrays, one CTA per array walks every tile with a running carry.
-constexpr int SCAN_T = 1024, SCAN_PER = 8, SCAN_TILE = SCAN_T * SCAN_PER;
-constexpr int SCAN_SMALL = 4 * SCAN_TILE;          // one CTA per array up to this length
+constexpr int SCAN_PER = 8;
+constexpr int SCAN_T = 256, SCAN_TILE = SCAN_T * SCAN_PER;          // look-back tiles (2048 ints)
+constexpr int SCAN_ST = 1024, SCAN_STILE = SCAN_ST * SCAN_PER;      // the one-CTA form's tiles
+constexpr int SCAN_SMALL = 4 * SCAN_STILE;         // one CTA per array up to this length
 constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62;
 
 struct ScanSet {
@@ -44,14 +46,17 @@ struct ScanSet {
 
 __device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
 
-// Exclusive scan of one tile staged through shared memory: returns the tile's sum (every
-// thread), leaves the thread's exclusive prefix in *pre and its SCAN_PER elements in v.
+// Exclusive scan of one tile of NT * SCAN_PER ints staged through shared memory: returns the
+// tile's sum (every thread), leaves the thread's exclusive prefix in *pre and its SCAN_PER
+// elements in v.  ws: [32] shared.
+template <int NT>
 __device__ __forceinline__ int tile_scan(const int *__restrict__ in, int base, int n, int *sh, int *ws,
                                          int (&v)[SCAN_PER], int *pre) {
+    constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
     for (int u = 0; u < SCAN_PER; ++u) {
-        const int i = u * SCAN_T + tid;
+        const int i = u * NT + tid;
         sh[spad(i)] = base + i < n ? in[base + i] : 0;
     }
     __syncthreads();
@@ -70,20 +75,21 @@ __device__ __forceinline__ int tile_scan(const int *__restrict__ in, int base, i
     if (lane == 31) ws[w] = inc;
     __syncthreads();
     if (w == 0) {
-        int t = ws[lane];
+        int t = lane < NW ? ws[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
-        ws[lane] = t;
+        if (lane < NW) ws[lane] = t;
     }
     __syncthreads();
     *pre = (w ? ws[w - 1] : 0) + inc - s;
-    return ws[31];
+    return ws[NW - 1];
 }
 
 // The tile's exclusive prefixes (offset x added) written back through shared memory, coalesced.
+template <int NT>
 __device__ __forceinline__ void tile_store(int *__restrict__ out, int base, int n, int *sh, const int (&v)[SCAN_PER],
                                            int x) {
     const int tid = threadIdx.x;
@@ -96,21 +102,21 @@ __device__ __forceinline__ void tile_store(int *__restrict__ out, int base, int 
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < SCAN_PER; ++u) {
-        const int i = u * SCAN_T + tid;
+        const int i = u * NT + tid;
         if (base + i < n) out[base + i] = sh[spad(i)];
     }
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_small(ScanSet S, int n) {
+__global__ void __launch_bounds__(SCAN_ST) k_scan_small(ScanSet S, int n) {
     pdl_enter();
-    __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
+    __shared__ int sh[SCAN_STILE + SCAN_STILE / 32];
     __shared__ int ws[32];
     const int a = blockIdx.y;
     int carry = 0;
-    for (int base = 0; base < n; base += SCAN_TILE) {
+    for (int base = 0; base < n; base += SCAN_STILE) {
         int v[SCAN_PER], pre;
-        const int sum = tile_scan(S.in[a], base, n, sh, ws, v, &pre);
-        tile_store(S.out[a], base, n, sh, v, carry + pre);
+        const int sum = tile_scan<SCAN_ST>(S.in[a], base, n, sh, ws, v, &pre);
+        tile_store<SCAN_ST>(S.out[a], base, n, sh, v, carry + pre);
         carry += sum;
         __syncthreads();      // ws / sh are reused by the next tile
     }
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int n
     __syncthreads();
     const int tile = s_tile, base = tile * SCAN_TILE;
     int v[SCAN_PER], pre;
-    const int sum = tile_scan(S.in[a], base, n, sh, ws, v, &pre);
+    const int sum = tile_scan<SCAN_T>(S.in[a], base, n, sh, ws, v, &pre);
     if (tid < 32) {
         if (tid == 0) atomicExch(st + tile, (tile == 0 ? ST_INC : ST_AGG) | (unsigned)sum);
         __syncwarp();
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_onepass(ScanSet S, int n, int n
         }
     }
     __syncthreads();
-    tile_store(S.out[a], base, n, sh, v, s_pre + pre);
+    tile_store<SCAN_T>(S.out[a], base, n, sh, v, s_pre + pre);
 }
 
 size_t scan_tmp_ints(int n) {
@@ -186,7 +192,7 @@ void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cu
         return;
     }
     if (n <= SCAN_SMALL) {
-        launch_pdl(k_scan_small, dim3(1, k), SCAN_T, 0, st, S, n);
+        launch_pdl(k_scan_small, dim3(1, k), SCAN_ST, 0, st, S, n);
         return;
     }
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -222,9 +228,18 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
 // carried out by the whole block, so that no warp runs them one lane at a time.
 constexpr int RANGE_PER = 8, RANGE_T = 256;
 
-__global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ n_dev, const uint32_t *__restrict__ key,
-                                                         int D, int Lmax, int *__restrict__ beg, int *__restrict__ end) {
+// One launch for both point sets: blocks [0, gs) take the sources (grid-stride over gs blocks),
+// the others the targets.
+__global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ ns_dev, const uint32_t *__restrict__ skey,
+                                                         int *__restrict__ sbeg, int *__restrict__ send, int gs,
+                                                         const int *__restrict__ nt_dev, const uint32_t *__restrict__ tkey,
+                                                         int *__restrict__ tbeg, int *__restrict__ tend, int D, int Lmax) {
     pdl_enter();
+    const bool src = (int)blockIdx.x < gs;
+    const int bid = src ? (int)blockIdx.x : (int)blockIdx.x - gs, nblk = src ? gs : (int)gridDim.x - gs;
+    const int *n_dev = src ? ns_dev : nt_dev;
+    const uint32_t *key = src ? skey : tkey;
+    int *beg = src ? sbeg : tbeg, *end = src ? send : tend;
     __shared__ uint32_t task_key[2 * RANGE_PER * RANGE_T];
     __shared__ int task_val[2 * RANGE_PER * RANGE_T];
     __shared__ uint8_t task_lvl[2 * RANGE_PER * RANGE_T];   // first level | 0x80 for an end
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__
     auto first_level = [&](uint32_t x, uint32_t o) { return max(0, D - (31 - __clz(x ^ o)) / 3); };
     // grid-stride over chunks of RANGE_T * RANGE_PER keys (uniform across the block); point
     // counts stay below 2^30 (grids of at most 1024^3 cells), so int indices do not overflow
-    for (int base = blockIdx.x * RANGE_T * RANGE_PER; base < n; base += gridDim.x * RANGE_T * RANGE_PER) {
+    for (int base = bid * RANGE_T * RANGE_PER; base < n; base += nblk * RANGE_T * RANGE_PER) {
         const int i0 = base + threadIdx.x * RANGE_PER;
         if (threadIdx.x == 0) ntask = 0;
         uint32_t k[RANGE_PER];
@@ -417,17 +432,21 @@ __global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ 
 
 void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     const int64_t nslot = dense_off(A.Lmax + 1);
-    cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
-    cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
-    cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
-    cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
+    if (A.rse == A.rsb + nslot && A.rtb == A.rse + nslot && A.rte == A.rtb + nslot) {
+        cudaMemsetAsync(A.rsb, 0, 4 * nslot * sizeof(int), st);
+    } else {
+        cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
+        cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
+        cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
+        cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
+    }
     constexpr int RB = RANGE_T * RANGE_PER;
     // targets: enough blocks for every possible point (blocks past the actual count exit at
     // once); sources, usually far fewer: a grid-stride loop over 8 blocks per SM
     const int rg = (int)std::min<int64_t>(((int64_t)A.ncap + RB - 1) / RB, 1 << 20);
-    launch_pdl(k_tree_ranges, std::max(std::min(rg, 152 * 8), 1), RANGE_T, 0, st, A.ns_dev, A.skey, A.D, A.Lmax, A.rsb,
-                                                                           A.rse);
-    launch_pdl(k_tree_ranges, std::max(rg, 1), RANGE_T, 0, st, A.nt_dev, A.tkey, A.D, A.Lmax, A.rtb, A.rte);
+    const int gs = std::max(std::min(rg, 152 * 8), 1);
+    launch_pdl(k_tree_ranges, gs + std::max(rg, 1), RANGE_T, 0, st, A.ns_dev, A.skey, A.rsb, A.rse, gs, A.nt_dev,
+               A.tkey, A.rtb, A.rte, A.D, A.Lmax);
     const int grid = (int)((nslot + 255) / 256);
     cudaMemsetAsync(A.T.lvl_src, 0, 32 * sizeof(int), st);   // lvl_src and lvl_leaf
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);

@@ -379,8 +379,9 @@ int tree_queue(sph_ctx *c) {
     A.err = P<int>(c->b_tot) + 3;
     CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
-    // ranges (sources, targets), existence flags, scan, emit, source occupancy and its dilation
-    c->launches += 2 + 3 + (Lmax >= 1 ? 2 : 0);
+    // ranges (sources and targets in one launch), existence flags, scan, emit, source occupancy
+    // and its dilation
+    c->launches += 1 + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
