@@ -20,6 +20,8 @@
 //                       FAR_SURFACE FP64 equivalent density of A, then FP64 kernel sums.
 // CTAs of the box kernels have 2 * npad threads: thread t owns state row t % npad
 // and half (t / npad) of the reduction, so each matrix column is read coalesced.
+#include <algorithm>
+
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -904,11 +906,14 @@ __global__ void k_near_table(P2PConst K, float *tab) {
 }
 
 // list: P2P_CLASSES lists of `stride` slots, count: their lengths; the leaves are taken class
-// by class, the heaviest first
+// by class, the heaviest first.  Passes [pass_lo, pass_hi) of 0 (U list) and 1 (W list); a
+// launch of pass 1 alone skips the leaves without W entries and adds to the slots that the
+// pass-0 launch cleared.
 template <bool TAYLOR, bool TABLE>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
                                                          const int *__restrict__ count, int stride,
-                                                         float *__restrict__ out, P2PConst K) {
+                                                         float *__restrict__ out, P2PConst K, int pass_lo,
+                                                         int pass_hi) {
     pdl_enter();
     __shared__ float4 stage[P2P_CAP];
     __shared__ float tab[TABLE ? GTAB_N : 1];
@@ -935,18 +940,30 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
         int c = 0, j = i;
         while (c < P2P_CLASSES - 1 && j >= ccnt[c]) j -= ccnt[c++];
         const int b = list[(size_t)c * stride + j];
+        if (pass_lo == 1 && F.L.w_off[b + 1] == F.L.w_off[b]) continue;     // uniform
         const int tb = T.b_tb[b], te = T.b_te[b];
         const int nch = (te - tb + 31) >> 5;
+        // the leaf's sums: its slots of the scratch (cleared by the launch that starts with the
+        // U list), or the output itself
+        float *nslot = F.near_buf ? F.near_buf + (size_t)i * F.near_s : nullptr;
+        if (nslot && pass_lo == 0) {
+            for (int t = tid; t < te - tb; t += blockDim.x) nslot[t] = 0.f;
+            __syncthreads();
+        }
+        auto add_out = [&](int t, uint32_t tp, float v) {
+            if (nslot) atomicAdd(nslot + (t - tb), v);
+            else atomicAdd(out + (int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)), v);
+        };
         const int G = nch >= P2P_WARPS ? 1 : P2P_WARPS / nch;     // warps sharing a target chunk
         const int groups = P2P_WARPS / G;
         const int k = warp % G;
         float acc[2] = {0.f, 0.f};        // the first two chunks of this warp; further chunks flush per round
         // pass 0: U list (point sources); pass 1: W list (Chebyshev nodes of the W boxes)
-        const int passes = F.O.method == FAR_CHEB ? 2 : 1;     // the surface form keeps M2P in k_leaf
+        const int passes = min(pass_hi, F.O.method == FAR_CHEB ? 2 : 1);   // the surface form keeps M2P in k_leaf
         // strategy 3 applies to leaves whose every chunk stays in this warp's two sum slots
         const bool skip3 = F.r_s > 0.f && nch <= 2 * groups && F.L.w_off[b + 1] > F.L.w_off[b];
         float sest[2] = {0.f, 0.f};
-        for (int pass = 0; pass < passes; ++pass) {
+        for (int pass = pass_lo; pass < passes; ++pass) {
             const int l0 = pass == 0 ? F.L.u_off[b] : F.L.w_off[b];
             const int l1 = pass == 0 ? F.L.u_off[b + 1] : F.L.w_off[b + 1];
             if (pass == 1 && skip3) {
@@ -1064,10 +1081,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                             }
                             if (skipped && F.skip_count) atomicAdd(F.skip_count, skipped);
                             if (slot < 2) acc[slot] += a;
-                            else if (t < te)
-                                atomicAdd(out + (int64_t)pc_i(tp) +
-                                              (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
-                                          a);
+                            else if (t < te) add_out(t, tp, a);
                             continue;
                         }
                         // W-list nodes (pass 1) sit off the lattice: the exp form
@@ -1090,10 +1104,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
                                 a = p2p_sum<TAYLOR, false>(stage, s_lo, s_hi, fx, fy, fz, K, tab);
                         }
                         if (slot < 2) acc[slot] += a;
-                        else if (t < te)
-                            atomicAdd(out + (int64_t)pc_i(tp) +
-                                          (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
-                                      a);
+                        else if (t < te) add_out(t, tp, a);
                     }
                 }
             }
@@ -1102,9 +1113,31 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
         for (int c = warp / G; c < nch && slot < 2; c += groups, ++slot) {
             const int t = tb + c * 32 + lane;
             if (t >= te) continue;
+            add_out(t, nslot ? 0u : key_pc(F.trg_key[t]), acc[slot]);
+        }
+    }
+}
+
+// out[cell of t] += near_buf[slot of t]: one warp per leaf of the class lists (the items in the
+// near field's order); every target belongs to one leaf, so plain read-modify-writes suffice
+__global__ void __launch_bounds__(256) k_near_add(FmmDev F, const int *__restrict__ list,
+                                                  const int *__restrict__ count, int stride,
+                                                  float *__restrict__ out) {
+    pdl_enter();
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < P2P_CLASSES; ++c) cnt += count[c];
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < cnt; i += nw) {
+        int c = 0, j = i;
+        while (c < P2P_CLASSES - 1 && j >= count[c]) j -= count[c++];
+        const int b = list[(size_t)c * stride + j];
+        const int tb = F.T.b_tb[b], te = F.T.b_te[b];
+        const float *ns = F.near_buf + (size_t)i * F.near_s;
+        for (int t = tb + lane; t < te; t += 32) {
             const uint32_t tp = key_pc(F.trg_key[t]);
-            atomicAdd(out + (int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp)),
-                      acc[slot]);
+            out[(int64_t)pc_i(tp) + (int64_t)F.nx * ((int64_t)pc_j(tp) + (int64_t)F.ny * pc_k(tp))] += ns[t - tb];
         }
     }
 }
@@ -1128,18 +1161,31 @@ void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st) {
 }
 
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-             cudaStream_t st) {
+             cudaStream_t st, int pass_lo, int pass_hi, int per_sm) {
     if (nboxes <= 0) return;
-    const int grid = nboxes < 152 * 16 ? nboxes : 152 * 16;
+    const int cap = 152 * per_sm;
+    const int grid = nboxes < cap ? nboxes : cap;
     const P2PConst K = p2p_const(F);
     const bool taylor = K.bma_h < 0.5f, table = F.gtab != nullptr;
     if (!taylor && !table)
-        launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+        launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
+                   pass_hi);
     else if (taylor && !table)
-        launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+        launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
+                   pass_hi);
     else if (!taylor)
-        launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
-    else launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K);
+        launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
+                   pass_hi);
+    else
+        launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
+                   pass_hi);
+}
+
+void fmm_near_add(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
+                  cudaStream_t st) {
+    if (nboxes <= 0 || !F.near_buf) return;
+    const int grid = std::max(1, std::min((nboxes + 7) / 8, 152 * 8));
+    launch_pdl(k_near_add, grid, 256, 0, st, F, p2p_list, p2p_cnt, stride, out);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {

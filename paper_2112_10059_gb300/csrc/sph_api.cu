@@ -89,6 +89,11 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    bool near_overlap = true;         // near field on a second stream beside the far-field passes
+    int near_per_sm = 6;              // its U-list launch: CTAs per SM (room for the far-field CTAs; measured)
+    cudaStream_t near_stream = nullptr;
+    cudaEvent_t near_fork = nullptr, near_join = nullptr, near_up = nullptr;
+    DevBuf b_nearbuf;                 // the near field's per-leaf sums (overlapped form)
     unsigned select_wait = SELECT_WAIT_LIMIT;   // look-back polls of the selection (SPH_WAIT_LIMIT_SELECT)
     int fault_alloc = 0;              // > 0: the fault_alloc-th allocation fails (SPH_FAULT=alloc[:k])
     int m2l_tiles = 2;                // tensor-core M2L in target-stationary tiles: 0 never (tiles of V
@@ -643,6 +648,21 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
     S.tc = c->m2l_prec == SPH_M2L_BF16X3 && F.O.m2l_img != nullptr && !c->translate_per_box;
+    // the near field beside the far-field passes (from the end of the upward pass, whose
+    // equivalent densities its W-list part reads): its sums go to per-leaf slots and are added
+    // into the output after the L2P.  Strategy 3 reads the L2P's far field, so it keeps the
+    // near field after the L2P.
+    if (F.p2p_separate && c->near_overlap && c->r_s == 0.0) {
+        int64_t leaves = 0;
+        for (int l = 0; l <= c->Lmax; ++l) leaves += c->lvl_leaf[l];
+        ENS(c->b_nearbuf, (size_t)std::max<int64_t>(leaves, 1) * c->leaf_eff * sizeof(float));
+        F.near_buf = P<float>(c->b_nearbuf);
+        F.near_s = c->leaf_eff;
+        if (!c->near_stream) CK(cudaStreamCreateWithFlags(&c->near_stream, cudaStreamNonBlocking));
+        if (!c->near_fork) CK(cudaEventCreateWithFlags(&c->near_fork, cudaEventDisableTiming));
+        if (!c->near_join) CK(cudaEventCreateWithFlags(&c->near_join, cudaEventDisableTiming));
+        if (!c->near_up) CK(cudaEventCreateWithFlags(&c->near_up, cudaEventDisableTiming));
+    }
     // the fused deepest level reads only the d rows of leaves with V or X entries: the rows of
     // that level are then cleared one by one by the work lists, the levels above by a memset
     S.fused = l2lp_fusable(c, S);
@@ -669,6 +689,24 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 56, std::max(nb, 1),
                    c->stream);
     c->launches += nb > 0;
+    const bool near_fork = F.near_buf && nb > 0;
+    if (near_fork) {
+        // fork: the near field's U-list part on its own stream from here (it needs the work
+        // lists), beside the upward and far-field passes; its W-list part (M2P, which reads the
+        // upward pass's equivalent densities) after the upward pass; joined before its sums are
+        // added into the output
+        CK(cudaEventRecord(c->near_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->near_stream, c->near_fork, 0));
+        CK(cudaMemsetAsync(F.skip_count, 0, sizeof(unsigned long long), c->near_stream));
+        if (F.gtab) {
+            fmm_near_table(F, const_cast<float *>(F.gtab), c->near_stream);
+            ++c->launches;
+        }
+        if (tm) tm->mark_at(12, c->near_stream);
+        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 0, 1, c->near_per_sm);
+        ++c->launches;
+        if (tm) tm->mark_at(14, c->near_stream);
+    }
     if (tm) tm->mark_at(3, c->stream);
     // P2M of the leaves (and, without the tensor-core images, M2M) box by box; with them the
     // split boxes' M2M in tiles on the tensor cores (their rows zeroed by the work lists)
@@ -684,6 +722,17 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         }
     }
     if (tm) tm->mark_at(4, c->stream);
+    if (near_fork) {
+        CK(cudaEventRecord(c->near_up, c->stream));
+        CK(cudaStreamWaitEvent(c->near_stream, c->near_up, 0));
+        if (tm) tm->mark_at(15, c->near_stream);
+        if (c->list_tot[2] > 0 && F.O.method == FAR_CHEB) {
+            fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 1, 2);
+            ++c->launches;
+        }
+        if (tm) tm->mark_at(13, c->near_stream);
+        CK(cudaEventRecord(c->near_join, c->near_stream));
+    }
     const bool fused = S.fused;
     c->l2lp_used = fused && c->lvl_count[c->Lmax - 1] > 0;
     if (c->translate_per_box) {
@@ -789,7 +838,13 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         fmm_leaf(F, nb, S.w_leaf, S.w_cnt + 32, out, c->stream);
         c->launches += nb > 0;
     }
-    if (F.p2p_separate) {
+    if (F.near_buf) {
+        if (nb > 0) {
+            CK(cudaStreamWaitEvent(c->stream, c->near_join, 0));
+            fmm_near_add(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->stream);
+            ++c->launches;
+        }
+    } else if (F.p2p_separate) {
         CK(cudaMemsetAsync(F.skip_count, 0, sizeof(unsigned long long), c->stream));
         if (F.gtab) {
             fmm_near_table(F, const_cast<float *>(F.gtab), c->stream);
@@ -833,7 +888,8 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
         stats->ms_m2l = tm->ms(5, 6);
         stats->ms_l2l = tm->ms(6, 7);
         stats->ms_l2p = tm->ms(7, 8);
-        stats->ms_near = tm->ms(8, 9);
+        // overlapped near field: its U-list and W-list launches themselves
+        stats->ms_near = tm->rec[12] ? tm->ms(12, 14) + tm->ms(15, 13) : tm->ms(8, 9);
         stats->ms_total = tm->ms(0, 9);
         stats->ms_l2lp = tm->ms(10, 11);
     }
@@ -849,6 +905,18 @@ void fill_stats(sph_ctx *c, sph_stats *stats, PhaseTimer *tm) {
         if (cudaMemcpy(&k, c->b_skip.p, sizeof k, cudaMemcpyDeviceToHost) == cudaSuccess) stats->n_w_skipped = (int64_t)k;
         else cudaGetLastError();
     }
+}
+
+// The context's capture stream, at the device's highest stream priority: where the near field
+// runs beside the far-field passes on a stream of default priority, the CTAs of the far-field
+// chain (the longer one) are scheduled first whenever both wait for a slot.
+cudaError_t make_capture_stream(cudaStream_t *s) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        greatest = 0;
+    }
+    return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
 }
 
 // The passes queued as one CUDA graph: captured on the context's private capture stream (the
@@ -876,7 +944,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
 }
 
 int fmm_queue_graph(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
-    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (!c->cap_stream) CK(make_capture_stream(&c->cap_stream));
     // the same passes with the same arguments as the last captured graph (and no phase events
     // to record): launch that executable again instead of capturing an identical one
     const bool timed = tm && tm->on;   // phase events are recorded inside the graph
@@ -1233,6 +1301,8 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_simt = parent->l2p_simt;
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
+    sub->near_overlap = parent->near_overlap;
+    sub->near_per_sm = parent->near_per_sm;
     sub->l2lp_fused = parent->l2lp_fused;
     sub->m2l_tiles = parent->m2l_tiles;
     sub->defer_sync = parent->defer_sync;
@@ -1330,7 +1400,7 @@ int run_batch(sph_ctx *c, int n, const sph_problem *probs, sph_stats *stats) {
     // phase 4: the FMM passes of every snapshot, concurrently, as one graph
     bool graph = c->batch_graph && !live.empty();
     if (graph) {
-        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (!c->cap_stream) CK(make_capture_stream(&c->cap_stream));
         CK(cudaStreamSynchronize(c->cap_stream));
         // the capture stream starts after the context's stream and every snapshot's pending work
         cudaEvent_t pre = batch_event(c, 1);
@@ -1613,6 +1683,8 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_SIMT")) c->l2p_simt = atoi(e) != 0;
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
+    if (const char *e = getenv("SPH_NEAR_OVERLAP")) c->near_overlap = atoi(e) != 0;
+    if (const char *e = getenv("SPH_NEAR_PER_SM")) c->near_per_sm = std::max(1, atoi(e));
     if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_TILES")) c->m2l_tiles = atoi(e);
     c->select_wait = env_limit("SPH_WAIT_LIMIT_SELECT", SELECT_WAIT_LIMIT);
@@ -1643,6 +1715,13 @@ void sph_destroy(sph_ctx *c) {
     if (c->eval_gexec) cudaGraphExecDestroy(c->eval_gexec);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->near_stream) {
+        cudaStreamSynchronize(c->near_stream);
+        cudaStreamDestroy(c->near_stream);
+    }
+    if (c->near_fork) cudaEventDestroy(c->near_fork);
+    if (c->near_join) cudaEventDestroy(c->near_join);
+    if (c->near_up) cudaEventDestroy(c->near_up);
     for (sph_ctx *sub : c->subs) sph_destroy(sub);
     c->subs.clear();
     if (c->sur_coarse) sph_destroy(c->sur_coarse);
@@ -1652,7 +1731,7 @@ void sph_destroy(sph_ctx *c) {
                      &c->b_level, &c->b_key, &c->b_sb, &c->b_se, &c->b_tb, &c->b_te, &c->b_parent, &c->b_leaf,
                      &c->b_lcnt, &c->b_loff, &c->b_usrc, &c->b_vsrc, &c->b_vocs, &c->b_vtrg, &c->b_wsrc, &c->b_xsrc, &c->b_pkeys, &c->b_ppairs, &c->b_heavy,
                      &c->b_ueq, &c->b_dchk, &c->o_work, &c->o_etab, &c->o_m2m, &c->o_l2l,
-                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->o_m2mbf, &c->b_err, &c->b_work, &c->b_mtg, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
+                     &c->o_m2l, &c->o_m2lbf, &c->o_l2lbf, &c->o_m2mbf, &c->b_err, &c->b_work, &c->b_mtg, &c->b_nearbuf, &c->o_slot, &c->o_surf, &c->o_cheb, &c->o_self, &c->h_q, &c->h_e, &c->h_m,
                      &c->h_s, &c->b_tmask, &c->b_near, &c->b_gtab, &c->b_skip, &c->o_l2pimg, &c->s_qc, &c->s_Sc, &c->s_y, &c->s_Sp, &c->s_x, &c->s_Sf,
                      &c->s_mask, &c->s_svox, &c->s_err, &c->s_pe, &c->s_flags, &c->s_counts};
     for (DevBuf *b : all)

@@ -216,6 +216,11 @@ struct FmmDev {
     // their d rows cleared by the work-list kernel only where they have V or X entries (the
     // others are never read); -1: every row cleared before the passes
     int d_sparse_from = -1;
+    // optional [items][near_s] scratch: the near field sums into its leaf's slots (item i of the
+    // class-walk order, target t - tb) instead of into the output, so that it can run beside the
+    // far-field passes; fmm_near_add adds the slots into the output afterwards
+    float *near_buf = nullptr;
+    int near_s = 0;
 };
 // returns the number of kernels launched
 int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list, const int *count, bool leaves_only,
@@ -227,9 +232,15 @@ constexpr int64_t P2P_CLASS0 = 1 << 16;
 // p2p_list: P2P_CLASSES lists of p2p_stride slots, p2p_cnt: their P2P_CLASSES counts
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
                     int *p2p_list, int *p2p_cnt, int p2p_stride, cudaStream_t st);
-// near field over the U lists of the leaves in the class lists of p2p_list (adds into out)
+// near field over the U lists (pass 0) and W lists (pass 1) of the leaves in the class lists of
+// p2p_list, passes [pass_lo, pass_hi); adds into out, or into F.near_buf where it is set (pass 0
+// clears the leaf's slots; a launch of pass 1 alone must follow the one of pass 0).  At most
+// per_sm CTAs per SM (grid-stride over the leaves).
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-             cudaStream_t st);
+             cudaStream_t st, int pass_lo = 0, int pass_hi = 2, int per_sm = 16);
+// out[cell of t] += F.near_buf[slot of t] for every target of every leaf of those lists
+void fmm_near_add(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
+                  cudaStream_t st);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);

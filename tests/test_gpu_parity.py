@@ -117,6 +117,26 @@ def test_selection_one_pass_equals_two_pass(sph, monkeypatch, n):
         assert np.array_equal(J, Jo) and np.array_equal(T, To), (two, lb)
 
 
+@pytest.mark.parametrize("pi", [0, 1, 2])
+def test_near_field_beside_far_field(sph, monkeypatch, pi):
+    """The near field on its own stream beside the far-field passes (its sums in per-leaf slots,
+    added after the L2P; default) equals the near field after the L2P adding straight into the
+    output (SPH_NEAR_OVERLAP=0): the same terms, added in another order."""
+    p = _problems()[pi]
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SPH_NEAR_OVERLAP", flag)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        outs[flag] = out.cpu().numpy().astype(np.float64)
+        _, again, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)     # graph replay
+        assert oracle.rel_l2(again.cpu().numpy().astype(np.float64), outs[flag]) < 1e-6
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    assert oracle.rel_l2(outs["1"][T], outs["0"][T]) < 1e-6
+    _check_fmm(outs["1"], ref, T, p.name + " near overlapped")
+
+
 @pytest.mark.parametrize("dims", [(64, 48, 48), (56, 48, 40)])
 def test_selection_whole_bricks(sph, monkeypatch, dims):
     """Bricks that the maxima pass's per-brick statistics decide (no source, every cell or no
