@@ -210,7 +210,8 @@ __device__ __forceinline__ int warp_append(unsigned act, bool pred, int *counter
 
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
                              int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
-                             int *__restrict__ p2p_cnt, int p2p_stride) {
+                             int *__restrict__ p2p_cnt, int p2p_stride, int *__restrict__ own_list,
+                             int *__restrict__ own_cnt) {
     pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
@@ -236,12 +237,16 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
         float4 *u = reinterpret_cast<float4 *>(F.ueq + (size_t)b * F.O.npad);
         for (int j = 0; j < F.O.npad / 4; ++j) u[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    // deepest level under the fused L2L + L2P: only the rows that M2L / P2L add into are cleared
-    if (F.d_sparse_from >= 0 && b >= F.d_sparse_from &&
-        (F.L.v_off[b + 1] != F.L.v_off[b] || F.L.x_off[b + 1] != F.L.x_off[b])) {
+    // deepest level under the fused L2L + L2P: only the rows that M2L / P2L add into are
+    // cleared, and those leaves (with targets) listed for the L2P of their own local terms
+    const bool own = F.d_sparse_from >= 0 && b >= F.d_sparse_from &&
+                     (F.L.v_off[b + 1] != F.L.v_off[b] || F.L.x_off[b + 1] != F.L.x_off[b]);
+    if (own) {
         float4 *d = reinterpret_cast<float4 *>(F.dchk + (size_t)b * F.O.npad);
         for (int j = 0; j < F.O.npad / 4; ++j) d[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    i = warp_append(act, own && leaf_t, own_cnt);
+    if (own && leaf_t) own_list[i] = b;
     // per level, the leaves with targets (the separable L2P walks these only)
     const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr;
     i = warp_append(act, l2p, F.l2p_cnt + l);
@@ -271,10 +276,10 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
 }
 
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, int p2p_stride, cudaStream_t st) {
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st) {
     if (nboxes <= 0) return;
     launch_pdl(k_work_lists, (nboxes + 255) / 256, 256, 0, st, F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
-                                                       p2p_cnt, p2p_stride);
+                                                       p2p_cnt, p2p_stride, own_list, own_cnt);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)

@@ -881,19 +881,20 @@ __global__ void __launch_bounds__(128) k_l2p_tc(FmmDev F, int level, int box_beg
 // child c of parent P (cells j of the child, coefficients k)
 //     S(j) = sum_k E[j][k] d_c[k] + sum_k (E L2L_c)[j][k] d_P[k],
 // d_c the child's own local terms (M2L, P2L: its L2L never runs), d_P the parent's complete
-// local expansion.  One CTA takes 128 parents (M = 128, TMEM lane = parent) and all 8
-// children: child c accumulates its 64 cells in TMEM columns [64c, 64c + 64) from two K = 128
-// contractions (parent x composed table, child x table), BF16 hi / lo x3.  Software pipeline
-// per child: the MMAs of child c run while the 256 threads hold child c+1's rows in flight
-// (16 loads each) and write child c's cells; then the rows are split into the operand tile
-// and child c+1's composed table arrives by a bulk copy.  d_c is zero where the child has no
-// V or X entry: such rows are neither read (a zero row in the operand tile) nor, where none of
-// the chunk's children in slot c has one, multiplied (only the parent term is issued).
+// local expansion.  This kernel takes the second sum for every leaf of the level: one CTA takes
+// 128 parents (M = 128, TMEM lane = parent) and all 8 children, child c accumulating its 64
+// cells in TMEM columns [64c, 64c + 64) from one K = 128 contraction (parent x composed
+// table), BF16 hi / lo x3, and stores S at the child's targets.  The first sum is zero unless
+// the child has V or X entries; k_l2p_own adds it for those leaves afterwards.
+// The composed tables stream through two buffers: round g (child g mod 8 of the CTA's g / 8-th
+// chunk) reads buffer g mod 2, and the table of round g + 2 is copied into it as soon as round
+// g's MMAs have completed, so a copy has a whole round to land.  Child c's cells are written
+// while child c+1's MMAs run.
 constexpr uint32_t LP_A = TCM * TCK * 2;               // 32 KiB: 128 rows x 128 coefficients
 constexpr uint32_t LP_B = 64 * TCK * 2;                // 16 KiB: 64 cells x 128 coefficients
 constexpr int LP_T = 256;
 constexpr int LP_V = TCM * (TCK / 4) / LP_T;           // float4 row segments per thread per tile (16)
-constexpr uint32_t LP_SMEM = 1024 + 4 * LP_A + 4 * LP_B + 64 + 25 * TCM * 4;
+constexpr uint32_t LP_SMEM = 1024 + 2 * LP_A + 4 * LP_B + 64 + 17 * TCM * 4;
 
 // rows idx[0..128) of the FP32 state (-1: zero row), 16 float4 per thread, all in flight at once
 __device__ __forceinline__ void lp_load(float4 (&v)[LP_V], const int *idx, const float *__restrict__ state, int np) {
@@ -915,32 +916,27 @@ __device__ __forceinline__ void lp_store(uint8_t *hi, uint8_t *lo, const float4 
 
 // One persistent CTA per SM: CTA b takes the chunks b, b + gridDim.x, ... of `ppc` parents
 // each (the launch makes every CTA take the same number of chunks), so no SM runs an extra
-// chunk while others idle.  The L2P table E and the TMEM accumulators are set up once per CTA;
-// the composed tables stream through one buffer, the copy of the next one (the next chunk's
-// first one after a chunk's last child) issued as soon as the MMAs that read the current one
-// have completed.  Barrier phases run on across chunks: the k-th wait on bar_t / bar_mma uses
-// parity k & 1.
+// chunk while others idle.  The composed tables are the same for every chunk (table of round
+// g: child g mod 8), so the copies run ahead across chunk boundaries; a chunk without leaves
+// has no rounds.  Barrier phases run on across chunks: the k-th use of table buffer j waits on
+// bar_t[j] with parity k & 1, the g-th round's MMAs complete bar_mma's phase g.
 __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int parent_begin, int parent_count,
-                                                     int ppc, int nchunks, const uint16_t *__restrict__ img_e,
-                                                     const uint16_t *__restrict__ img_c, float *__restrict__ out,
-                                                     int *err) {
+                                                     int ppc, int nchunks, const uint16_t *__restrict__ img_c,
+                                                     float *__restrict__ out, int *err) {
     pdl_enter();
     if ((int)blockIdx.x >= nchunks) return;        // uniform, before any allocation
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *ap_hi = base, *ap_lo = base + LP_A, *ac_hi = base + 2 * LP_A, *ac_lo = base + 3 * LP_A;
-    uint8_t *e_hi = base + 4 * LP_A, *e_lo = e_hi + LP_B, *t_hi = e_lo + LP_B, *t_lo = t_hi + LP_B;
-    uint8_t *tail = t_lo + LP_B;
-    uint64_t *bar_e = reinterpret_cast<uint64_t *>(tail);
-    uint64_t *bar_t = bar_e + 1;
-    uint64_t *bar_mma = bar_e + 2;
+    uint8_t *ap_hi = base, *ap_lo = base + LP_A;
+    uint8_t *tbuf = base + 2 * LP_A;                        // table buffer j: hi at tbuf + 2 j LP_B, lo after it
+    uint8_t *tail = base + 2 * LP_A + 4 * LP_B;
+    uint64_t *bar_t = reinterpret_cast<uint64_t *>(tail);   // [2]
+    uint64_t *bar_mma = bar_t + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tail + 24);
     int *ok_s = reinterpret_cast<int *>(tail + 28);
-    int *s_own = reinterpret_cast<int *>(tail + 32);        // bit c: a child in slot c has V / X entries
     int *spar = reinterpret_cast<int *>(tail + 64);         // [128] parent box or -1
     int *sch = spar + TCM;                                  // [8][128] child box or -1
     int *sfull = sch + 8 * TCM;                             // [8][128] child has every cell as target
-    int *sld = sfull + 8 * TCM;                             // [8][128] child box if it has V / X entries, or -1
     const TreeDev &T = F.T;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int np = F.O.npad;
@@ -950,7 +946,7 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int k = 0; k < 3; ++k) tc::mbar_init(tc::smem_u32(bar_e + k), 1);
+        for (int k = 0; k < 3; ++k) tc::mbar_init(tc::smem_u32(bar_t + k), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *ok_s = 1;
     }
@@ -958,17 +954,20 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    // thread 0's record of what is in flight, for a clean exit after a timeout
-    int t_issued = 0, t_landed = 0, m_issued = 0, m_done = 0;
-    bool e_landed = false;
+    // thread 0's record of what is in flight, for a clean exit after a timeout: copies issued /
+    // landed per table buffer (0, 1), MMA commits issued / completed
+    int t_iss0 = 0, t_iss1 = 0, t_land0 = 0, t_land1 = 0, m_issued = 0, m_done = 0;
+    auto copy_table = [&](int j, int child) {           // thread 0
+        const uint32_t hi = tc::smem_u32(tbuf + 2 * (uint32_t)j * LP_B);
+        tc::mbar_expect_tx(tc::smem_u32(bar_t + j), 2 * LP_B);
+        const uint16_t *src = img_c + (size_t)child * img_elems;
+        tc::bulk_g2s(hi, src, LP_B, tc::smem_u32(bar_t + j));
+        tc::bulk_g2s(hi + LP_B, src + LP_B / 2, LP_B, tc::smem_u32(bar_t + j));
+        if (j) ++t_iss1; else ++t_iss0;
+    };
     if (tid == 0) {
-        tc::mbar_expect_tx(tc::smem_u32(bar_e), 2 * LP_B);
-        tc::bulk_g2s(tc::smem_u32(e_hi), img_e, LP_B, tc::smem_u32(bar_e));
-        tc::bulk_g2s(tc::smem_u32(e_lo), img_e + LP_B / 2, LP_B, tc::smem_u32(bar_e));
-        tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
-        tc::bulk_g2s(tc::smem_u32(t_hi), img_c, LP_B, tc::smem_u32(bar_t));
-        tc::bulk_g2s(tc::smem_u32(t_lo), img_c + LP_B / 2, LP_B, tc::smem_u32(bar_t));
-        t_issued = 1;
+        copy_table(0, 0);
+        copy_table(1, 1);
     }
     float4 v[LP_V];
     const uint32_t idesc = tc::idesc_bf16_f32(TCM, 64);
@@ -1042,11 +1041,11 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                 if (keep[h][j]) out[(int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z)] = w[h][j];
             }
     };
+    int g = 0;                                              // rounds of this CTA so far
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const bool more = chunk + (int)gridDim.x < nchunks;   // this CTA has another chunk after this one
-        if (tid == 0) *s_own = 0;                              // its last reader passed the last round's barrier
         __syncthreads();                                       // previous chunk's epilogue read sch / sfull
-        int any = 0, own = 0;
+        int any = 0;
         if (tid < TCM) {
             const int i = chunk * ppc + tid;
             const int p = parent_begin + i;
@@ -1062,45 +1061,32 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                         full = T.b_te[ch] - T.b_tb[ch] == 64;
                     }
                 }
-                const bool terms = C >= 0 && (F.L.v_off[C + 1] != F.L.v_off[C] || F.L.x_off[C + 1] != F.L.x_off[C]);
                 sch[c * TCM + tid] = C;
                 sfull[c * TCM + tid] = full;
-                sld[c * TCM + tid] = terms ? C : -1;
                 any |= C >= 0;
-                own |= (int)terms << c;
             }
-            own = __reduce_or_sync(0xffffffffu, own);           // tid < 128: whole warps
-            if (lane == 0 && own) atomicOr(s_own, own);
         }
-        // a chunk without leaves is skipped; the first composed table stays in flight for the next
+        // a chunk without leaves has no rounds (the tables in flight serve the next chunk's)
         if (!__syncthreads_or(any)) continue;
-        own = *s_own;
         lp_load(v, spar, F.dchk, np);
         lp_store(ap_hi, ap_lo, v);
-        if (own & 1) {
-            lp_load(v, sld, F.dchk, np);
-            lp_store(ac_hi, ac_lo, v);
-        }
-        auto round = [&](int c) -> bool {
-            // (a) operand tiles of child c are in shared memory: MMAs (thread 0); the TMEM
-            //     reads of earlier epilogues (the same columns in the previous chunk) are ordered
-            //     before them
+        bool ok = true;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c, ++g) {
+            const int j = g & 1;
+            // (a) the parent tile (written above) and table g are in shared memory: MMAs (thread
+            //     0); the TMEM reads of earlier epilogues (the same columns in the previous
+            //     chunk) are ordered before them
             tc::fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncthreads();
             if (tid == 0 && *ok_s) {
-                bool ok = e_landed || tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
-                e_landed = ok;
-                ok = ok && tc::mbar_wait_bounded(tc::smem_u32(bar_t), t_landed & 1, WAIT_LIMIT);
-                if (ok) {
-                    ++t_landed;
+                if (tc::mbar_wait_bounded(tc::smem_u32(bar_t + j), (g >> 1) & 1, WAIT_LIMIT)) {
+                    if (j) ++t_land1; else ++t_land0;
                     tc::fence_after_sync();
                     const uint32_t d = tmem + (uint32_t)(64 * c);
                     const uint32_t aph = tc::smem_u32(ap_hi), apl = tc::smem_u32(ap_lo);
-                    const uint32_t ach = tc::smem_u32(ac_hi), acl = tc::smem_u32(ac_lo);
-                    const uint32_t th = tc::smem_u32(t_hi), tl = tc::smem_u32(t_lo);
-                    const uint32_t eh = tc::smem_u32(e_hi), el = tc::smem_u32(e_lo);
-                    const bool child_terms = (own >> c) & 1;
+                    const uint32_t th = tc::smem_u32(tbuf + 2 * (uint32_t)j * LP_B), tl = th + LP_B;
 #pragma unroll
                     for (int ks = 0; ks < TCK / 16; ++ks) {
                         const uint32_t ao = tc::sw128_offset(0, 16 * ks, TCM);
@@ -1108,70 +1094,85 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
                         tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(th + bo), idesc, ks > 0);
                         tc::mma_bf16(d, tc::sdesc_sw128(aph + ao), tc::sdesc_sw128(tl + bo), idesc, 1);
                         tc::mma_bf16(d, tc::sdesc_sw128(apl + ao), tc::sdesc_sw128(th + bo), idesc, 1);
-                        if (child_terms) {
-                            tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
-                            tc::mma_bf16(d, tc::sdesc_sw128(ach + ao), tc::sdesc_sw128(el + bo), idesc, 1);
-                            tc::mma_bf16(d, tc::sdesc_sw128(acl + ao), tc::sdesc_sw128(eh + bo), idesc, 1);
-                        }
                     }
                     tc::mma_commit(tc::smem_u32(bar_mma));
                     ++m_issued;
+                    // (b) round g's MMAs complete: its table buffer is free for round g + 2's
+                    //     table (this chunk's child c + 2, or the next chunk's first ones)
+                    if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), g & 1, WAIT_LIMIT)) {
+                        ++m_done;
+                        if (c + 2 < 8 || more) copy_table(j, (c + 2) & 7);
+                    } else {
+                        atomicOr(err, 8);
+                        *ok_s = 0;
+                    }
                 } else {
                     atomicOr(err, 4);
                     *ok_s = 0;
                 }
             }
-            // (b) child c+1's rows in flight (where that slot has own terms)
-            const bool next_terms = c + 1 < 8 && ((own >> (c + 1)) & 1);
-            if (next_terms) lp_load(v, sld + (c + 1) * TCM, F.dchk, np);
-            // (c) MMAs of child c complete: its accumulator is final (written in the next round),
-            //     the child tile and the table buffer are free; the next composed table streams
-            //     in (child c+1's, or after the last child the first one of the next chunk) --
-            //     before thread 0 takes its share of the epilogue, so the copy overlaps it
-            if (tid == 0 && *ok_s) {
-                if (tc::mbar_wait_bounded(tc::smem_u32(bar_mma), m_done & 1, WAIT_LIMIT)) {
-                    ++m_done;
-                    if (c + 1 < 8 || more) {
-                        tc::mbar_expect_tx(tc::smem_u32(bar_t), 2 * LP_B);
-                        const uint16_t *src = img_c + (size_t)((c + 1) & 7) * img_elems;
-                        tc::bulk_g2s(tc::smem_u32(t_hi), src, LP_B, tc::smem_u32(bar_t));
-                        tc::bulk_g2s(tc::smem_u32(t_lo), src + LP_B / 2, LP_B, tc::smem_u32(bar_t));
-                        ++t_issued;
-                    }
-                } else {
-                    atomicOr(err, 8);
-                    *ok_s = 0;
-                }
-            }
-            // (d) child c-1's cells written while child c's MMAs run and the table streams in
+            // (c) child c-1's cells written while child c's MMAs run
             if (c > 0) epilogue(c - 1);
             __syncthreads();
-            if (!*ok_s) return false;
+            if (!*ok_s) {
+                ok = false;
+                break;
+            }
             tc::fence_after_sync();
-            // (e) child c+1's operand tile (child c's MMAs, the last to read it, have completed)
-            if (next_terms) lp_store(ac_hi, ac_lo, v);
-            return true;
-        };
-#pragma unroll 1
-        for (int c = 0; c < 8; ++c)
-            if (!round(c)) break;
-        if (!*ok_s) break;
+        }
+        if (!ok) break;
         epilogue(7);
     }
-    if (tid == 0 && !*ok_s) {
-        // let this CTA's own copies and MMAs finish before its memory is released
-        if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
-        if (t_issued > t_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_issued - 1) & 1, WAIT_LIMIT);
+    if (tid == 0) {
+        // let this CTA's own copies and MMAs finish before its memory is released (after a
+        // timeout, or copies issued for rounds of chunks that had no leaves)
+        if (t_iss0 > t_land0) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_iss0 - 1) & 1, WAIT_LIMIT);
+        if (t_iss1 > t_land1) tc::mbar_wait_bounded(tc::smem_u32(bar_t + 1), (t_iss1 - 1) & 1, WAIT_LIMIT);
         if (m_issued > m_done) tc::mbar_wait_bounded(tc::smem_u32(bar_mma), (m_issued - 1) & 1, WAIT_LIMIT);
-    }
-    if (tid == 0 && *ok_s) {
-        // a table still in flight (the CTA's chunks ended with skipped ones): let it land
-        if (!e_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_e), 0, WAIT_LIMIT);
-        if (t_issued > t_landed) tc::mbar_wait_bounded(tc::smem_u32(bar_t), (t_issued - 1) & 1, WAIT_LIMIT);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// S += E d_own at the targets of the deepest-level leaves (edge 4) in `list` (count[0] of them:
+// the leaves with V or X entries, whose own local terms the fused kernel leaves out), FP32
+// from the level's interpolation table E ([n][64], cells in local Morton order).  One warp per
+// leaf: lane k takes the cells of local index k and k + 32; every cell belongs to one leaf, so
+// plain read-modify-writes suffice.
+__global__ void __launch_bounds__(256) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
+                                                 const int *__restrict__ count, float *__restrict__ out) {
+    pdl_enter();
+    __shared__ float sd[8][TCK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = *count;
+    const int n = F.O.n, np = F.O.npad;
+    const float *E = F.O.e_tab + F.O.e_off[level];
+    const TreeDev &T = F.T;
+    for (int i = blockIdx.x * 8 + warp; i < cnt; i += gridDim.x * 8) {
+        const int b = list[i];
+        for (int k = lane; k < np && k < TCK; k += 32) sd[warp][k] = F.dchk[(size_t)b * np + k];
+        __syncwarp();
+        float a[2] = {0.f, 0.f};
+        for (int k = 0; k < n; ++k) {
+            const float dk = sd[warp][k];
+            a[0] = fmaf(__ldg(E + (size_t)k * 64 + lane), dk, a[0]);
+            a[1] = fmaf(__ldg(E + (size_t)k * 64 + lane + 32), dk, a[1]);
+        }
+        uint32_t ux, uy, uz;
+        demorton3(T.b_key[b], ux, uy, uz);
+        const bool full = T.b_te[b] - T.b_tb[b] == 64;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t lx, ly, lz;
+            demorton3((uint32_t)(lane + 32 * h), lx, ly, lz);
+            const int x = (int)(ux * 4 + lx), y = (int)(uy * 4 + ly), z = (int)(uz * 4 + lz);
+            if (x >= F.nx || y >= F.ny || z >= F.nz) continue;
+            const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+            if (full || F.tmask[o]) out[o] += a[h];
+        }
+        __syncwarp();
+    }
 }
 
 int sm_count() {
@@ -1195,8 +1196,14 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
     const int nchunks = (parent_count + ppc - 1) / ppc;
     const int grid = std::min(nchunks, nsm);
     launch_pdl(k_l2lp_tc, grid, LP_T, LP_SMEM, st, F, level, parent_begin, parent_count, ppc, nchunks,
-                                                         F.O.l2p_img + F.O.l2p_off[level],
                                                          F.O.l2p_img + F.O.l2pc_off, out, err);
+}
+
+void fmm_l2p_own(const FmmDev &F, int level, const int *list, const int *count, int max_count, float *out,
+                 cudaStream_t st) {
+    if (max_count <= 0 || F.O.e_off[level] < 0 || F.O.npad > TCK || (1 << (F.D - level)) != 4) return;
+    const int grid = std::max(1, std::min((max_count + 7) / 8, 152 * 8));
+    launch_pdl(k_l2p_own, grid, 256, 0, st, F, level, list, count, out);
 }
 
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }

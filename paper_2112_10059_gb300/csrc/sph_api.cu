@@ -591,7 +591,7 @@ struct PhaseTimer {
 // ------------------------------------------------------------------ FMM passes
 struct PassState {
     FmmDev F;
-    int *w_src = nullptr, *w_leaf = nullptr, *w_p2p = nullptr, *w_cnt = nullptr;
+    int *w_src = nullptr, *w_leaf = nullptr, *w_p2p = nullptr, *w_cnt = nullptr, *w_own = nullptr;
     PairsDev Pd;
     int *err = nullptr;
     bool tc = false;
@@ -613,7 +613,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_work, ((3 + P2P_CLASSES) * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    ENS(c->b_work, ((4 + P2P_CLASSES) * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
     F.T = tree_dev(c);
@@ -644,6 +644,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.w_p2p = S.w_leaf + std::max(nb, 1);                   // P2P_CLASSES lists of max(nb, 1) slots
     S.w_cnt = S.w_p2p + P2P_CLASSES * std::max(nb, 1);
     F.l2p_list = S.w_cnt + 64;                  // [nb], per level at lvl_base[l]
+    S.w_own = F.l2p_list + std::max(nb, 1);     // [nb]: deepest-level leaves with V / X entries, count w_cnt[62]
     F.l2p_cnt = S.w_cnt + 40;                   // [16]
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
@@ -687,7 +688,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
     if (S.tc) CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));   // M2M, M2L and L2L tiles' flags
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 56, std::max(nb, 1),
-                   c->stream);
+                   S.w_own, S.w_cnt + 62, c->stream);
     c->launches += nb > 0;
     const bool near_fork = F.near_buf && nb > 0;
     if (near_fork) {
@@ -807,6 +808,11 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                     fmm_l2lp_tc_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], out, S.err + 1, c->stream);
                     if (tm) tm->mark_at(11, c->stream);
                     ++c->launches;
+                    if (c->list_tot[1] + c->list_tot[3] > 0) {
+                        // the own local terms of the leaves with V or X entries
+                        fmm_l2p_own(F, l, S.w_own, S.w_cnt + 62, c->lvl_count[l], out, c->stream);
+                        ++c->launches;
+                    }
                 }
                 continue;
             }

@@ -230,8 +230,10 @@ int fmm_upward_level(const FmmDev &F, int level, int box_count, const int *list,
 constexpr int P2P_CLASSES = 6;
 constexpr int64_t P2P_CLASS0 = 1 << 16;
 // p2p_list: P2P_CLASSES lists of p2p_stride slots, p2p_cnt: their P2P_CLASSES counts
+// own_list / own_cnt: the deepest-level leaves with targets and V or X entries (where
+// F.d_sparse_from >= 0), for fmm_l2p_own
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, int p2p_stride, cudaStream_t st);
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st);
 // near field over the U lists (pass 0) and W lists (pass 1) of the leaves in the class lists of
 // p2p_list, passes [pass_lo, pass_hi); adds into out, or into F.near_buf where it is set (pass 0
 // clears the leaf's slots; a launch of pass 1 alone must follow the one of pass 0).  At most
@@ -250,6 +252,11 @@ void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, fl
 // `level` must be a leaf (level == Lmax).  Replaces fmm_l2l_*_level(level) and the L2P of `level`.
 void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_count, float *out, int *err,
                        cudaStream_t st);
+// the L2P of the own local terms of the leaves in list (count[0] <= max_count of them; leaves of
+// edge 4 at `level`), added into out at their targets (FP32); the part of the deepest level's
+// L2P that fmm_l2lp_tc_level leaves out
+void fmm_l2p_own(const FmmDev &F, int level, const int *list, const int *count, int max_count, float *out,
+                 cudaStream_t st);
 // M2M of the split boxes with sources of `level` on the tensor cores: tiles of 64 boxes from
 // the level's source list x one child slot per CTA, added into rows zeroed by the work lists
 void fmm_m2m_tc_level(const FmmDev &F, int level, int box_count, const int *list, const int *count,
