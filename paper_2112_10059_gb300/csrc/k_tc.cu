@@ -1137,27 +1137,33 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
 
 // S += E d_own at the targets of the deepest-level leaves (edge 4) in `list` (count[0] of them:
 // the leaves with V or X entries, whose own local terms the fused kernel leaves out), FP32
-// from the level's interpolation table E ([n][64], cells in local Morton order).  One warp per
-// leaf: lane k takes the cells of local index k and k + 32; every cell belongs to one leaf, so
-// plain read-modify-writes suffice.
-__global__ void __launch_bounds__(256) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
-                                                 const int *__restrict__ count, float *__restrict__ out) {
+// from the level's interpolation table E ([n][64], cells in local Morton order), staged in
+// shared memory once per CTA.  One warp per leaf: lane k takes the cells of local index k and
+// k + 32; every cell belongs to one leaf, so plain read-modify-writes suffice.
+constexpr int OWN_W = 8;
+__global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
+                                                        const int *__restrict__ count, float *__restrict__ out) {
     pdl_enter();
-    __shared__ float sd[8][TCK];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cnt = *count;
+    if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform, before the table is staged
+    __shared__ float Es[TCK * 64];                          // [n][64]
+    __shared__ float sd[OWN_W][TCK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = F.O.n, np = F.O.npad;
-    const float *E = F.O.e_tab + F.O.e_off[level];
+    const float4 *E4 = reinterpret_cast<const float4 *>(F.O.e_tab + F.O.e_off[level]);
+    for (int j = threadIdx.x; j < n * 16; j += blockDim.x) reinterpret_cast<float4 *>(Es)[j] = __ldg(E4 + j);
+    __syncthreads();
     const TreeDev &T = F.T;
-    for (int i = blockIdx.x * 8 + warp; i < cnt; i += gridDim.x * 8) {
+    for (int i = blockIdx.x * OWN_W + warp; i < cnt; i += gridDim.x * OWN_W) {
         const int b = list[i];
         for (int k = lane; k < np && k < TCK; k += 32) sd[warp][k] = F.dchk[(size_t)b * np + k];
         __syncwarp();
-        float a[2] = {0.f, 0.f};
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll 5
         for (int k = 0; k < n; ++k) {
             const float dk = sd[warp][k];
-            a[0] = fmaf(__ldg(E + (size_t)k * 64 + lane), dk, a[0]);
-            a[1] = fmaf(__ldg(E + (size_t)k * 64 + lane + 32), dk, a[1]);
+            a0 = fmaf(Es[k * 64 + lane], dk, a0);
+            a1 = fmaf(Es[k * 64 + lane + 32], dk, a1);
         }
         uint32_t ux, uy, uz;
         demorton3(T.b_key[b], ux, uy, uz);
@@ -1169,7 +1175,7 @@ __global__ void __launch_bounds__(256) k_l2p_own(FmmDev F, int level, const int 
             const int x = (int)(ux * 4 + lx), y = (int)(uy * 4 + ly), z = (int)(uz * 4 + lz);
             if (x >= F.nx || y >= F.ny || z >= F.nz) continue;
             const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-            if (full || F.tmask[o]) out[o] += a[h];
+            if (full || F.tmask[o]) out[o] += h ? a1 : a0;
         }
         __syncwarp();
     }
@@ -1202,8 +1208,8 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
 void fmm_l2p_own(const FmmDev &F, int level, const int *list, const int *count, int max_count, float *out,
                  cudaStream_t st) {
     if (max_count <= 0 || F.O.e_off[level] < 0 || F.O.npad > TCK || (1 << (F.D - level)) != 4) return;
-    const int grid = std::max(1, std::min((max_count + 7) / 8, 152 * 8));
-    launch_pdl(k_l2p_own, grid, 256, 0, st, F, level, list, count, out);
+    const int grid = std::max(1, std::min((max_count + OWN_W - 1) / OWN_W, 2 * sm_count()));
+    launch_pdl(k_l2p_own, grid, OWN_W * 32, 0, st, F, level, list, count, out);
 }
 
 bool tc_supported(const OpsDev &O) { return O.npad == TCK; }
