@@ -340,10 +340,11 @@ __global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot,
     pdl_enter();
     // per-level counts of the block's boxes with sources and leaves with targets, added into
     // the level tables once per block and level (the same few counters for every block)
-    __shared__ int s_src[16], s_leaf[16];
+    __shared__ int s_src[16], s_leaf[16], s_sleaf[16];
     if (threadIdx.x < 16) {
         s_src[threadIdx.x] = 0;
         s_leaf[threadIdx.x] = 0;
+        s_sleaf[threadIdx.x] = 0;
     }
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,11 +378,13 @@ __global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot,
         vsrc[s] = se > sb;
         if (se > sb) atomicAdd(s_src + l, 1);
         if (leaf && te > tb) atomicAdd(s_leaf + l, 1);
+        if (leaf && se > sb) atomicAdd(s_sleaf + l, 1);
     }
     __syncthreads();
     if (threadIdx.x < 16) {
         if (s_src[threadIdx.x]) atomicAdd(T.lvl_src + threadIdx.x, s_src[threadIdx.x]);
         if (s_leaf[threadIdx.x]) atomicAdd(T.lvl_leaf + threadIdx.x, s_leaf[threadIdx.x]);
+        if (s_sleaf[threadIdx.x]) atomicAdd(T.lvl_sleaf + threadIdx.x, s_sleaf[threadIdx.x]);
     }
 }
 
@@ -448,7 +451,7 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     launch_pdl(k_tree_ranges, gs + std::max(rg, 1), RANGE_T, 0, st, A.ns_dev, A.skey, A.rsb, A.rse, gs, A.nt_dev,
                A.tkey, A.rtb, A.rte, A.D, A.Lmax);
     const int grid = (int)((nslot + 255) / 256);
-    cudaMemsetAsync(A.T.lvl_src, 0, 32 * sizeof(int), st);   // lvl_src and lvl_leaf
+    cudaMemsetAsync(A.T.lvl_src, 0, 48 * sizeof(int), st);   // lvl_src, lvl_leaf and lvl_sleaf
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);

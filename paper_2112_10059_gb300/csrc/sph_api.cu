@@ -76,6 +76,7 @@ struct sph_ctx {
     int nboxes = 0, Lmax = 0;
     std::vector<int> lvl_count, lvl_base, lvl_src;   // boxes, first box, boxes with sources per level
     std::vector<int> lvl_leaf;                       // leaves with targets per level
+    std::vector<int> lvl_sleaf;                      // leaves with sources per level
     int list_tot[4] = {0, 0, 0, 0};
     bool have_tree = false;
     int64_t launches = 0;   // kernels queued by the current eval (operator precompute excluded)
@@ -297,6 +298,7 @@ TreeDev tree_dev(sph_ctx *c) {
     T.lvl_count = T.lvl_base + 16;
     T.lvl_src = T.lvl_base + 32;
     T.lvl_leaf = T.lvl_base + 48;
+    T.lvl_sleaf = T.lvl_base + 64;
     T.b_level = P<int>(c->b_level);
     T.b_key = P<uint32_t>(c->b_key);
     T.b_sb = P<int>(c->b_sb); T.b_se = P<int>(c->b_se);
@@ -345,7 +347,8 @@ PairsDev pairs_dev(sph_ctx *c) {
 // ------------------------------------------------------------------ tree and lists
 // pinned read-back slots: [0..3) selection totals, [8..40) level bases / counts,
 // [43] scan give-up flag, [44..48) list totals, [48] and [49] tensor-core error flags,
-// [64..64+Lmax] boxes with sources per level, [80..80+Lmax] leaves with targets per level.
+// [64..64+Lmax] boxes with sources per level, [80..80+Lmax] leaves with targets per level,
+// [96..96+Lmax] leaves with sources per level.
 // The tree and the list counts read the selection's point counts and the tree's box count
 // from device memory, so selection, tree and list counting need one host sync in all.
 int tree_queue(sph_ctx *c) {
@@ -362,7 +365,7 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_rng, 4 * dense_total * sizeof(int));
     ENS(c->b_near, 3 * dense_total + 16);
     ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
-    ENS(c->b_lvl, 64 * sizeof(int));
+    ENS(c->b_lvl, 80 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
     ENS(c->b_level, cap * sizeof(int));
     ENS(c->b_key, cap * sizeof(uint32_t));
@@ -389,7 +392,7 @@ int tree_queue(sph_ctx *c) {
     c->launches += 1 + 3 + (Lmax >= 1 ? 2 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 48 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
@@ -424,13 +427,15 @@ int tree_levels_read(sph_ctx *c) {
     c->lvl_base.assign(Lmax + 1, 0);
     c->lvl_src.assign(Lmax + 1, 0);
     c->lvl_leaf.assign(Lmax + 1, 0);
+    c->lvl_sleaf.assign(Lmax + 1, 0);
     int64_t tot = 0;
     for (int l = 0; l <= Lmax; ++l) {
         c->lvl_src[l] = c->pinned[64 + l];
         c->lvl_leaf[l] = c->pinned[80 + l];
+        c->lvl_sleaf[l] = c->pinned[96 + l];
         c->lvl_count[l] = c->pinned[8 + 16 + l];
         if (c->lvl_src[l] < 0 || c->lvl_src[l] > c->pinned[8 + 16 + l] || c->lvl_leaf[l] < 0 ||
-            c->lvl_leaf[l] > c->pinned[8 + 16 + l])
+            c->lvl_leaf[l] > c->pinned[8 + 16 + l] || c->lvl_sleaf[l] < 0 || c->lvl_sleaf[l] > c->lvl_src[l])
             return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         if (c->lvl_count[l] < 0) return fail(c, SPH_ETIMEOUT, "inconsistent level counts from the tree build");
         c->lvl_base[l] = (int)tot;
@@ -713,10 +718,13 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     // split boxes' M2M in tiles on the tensor cores (their rows zeroed by the work lists)
     const bool m2m_tc = S.tc && F.O.m2m_img != nullptr;
     for (int l = c->Lmax; l >= 2; --l) {
-        // launch sizes from the number of boxes with sources (the kernels read the exact count)
-        c->launches += fmm_upward_level(F, l, c->lvl_src[l], S.w_src + c->lvl_base[l], S.w_cnt + l, m2m_tc,
-                                        c->stream);
-        if (m2m_tc && l < c->Lmax && c->lvl_src[l] > 0) {
+        // launch sizes from the number of boxes with sources (the kernels read the exact count);
+        // with the tensor-core M2M the box-by-box kernel takes the leaves alone (P2M), and
+        // neither kernel is launched on a level without its kind of box
+        if (!m2m_tc || c->lvl_sleaf[l] > 0)
+            c->launches += fmm_upward_level(F, l, c->lvl_src[l], S.w_src + c->lvl_base[l], S.w_cnt + l, m2m_tc,
+                                            c->stream);
+        if (m2m_tc && l < c->Lmax && c->lvl_src[l] > c->lvl_sleaf[l]) {
             fmm_m2m_tc_level(F, l, c->lvl_src[l], S.w_src + c->lvl_base[l], S.w_cnt + l, F.O.m2m_img, S.err,
                              c->stream);
             ++c->launches;
@@ -941,6 +949,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(c->lvl_base.data(), c->lvl_base.size() * sizeof(int));
     put(c->lvl_src.data(), c->lvl_src.size() * sizeof(int));
     put(c->lvl_leaf.data(), c->lvl_leaf.size() * sizeof(int));
+    put(c->lvl_sleaf.data(), c->lvl_sleaf.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
                           c->l2p_tc_tables, c->m2l_pipe, c->l2lp_fused, c->m2l_tiles, c->m2l_form,
@@ -1272,7 +1281,7 @@ sph_ctx *make_sub(sph_ctx *parent, bool shared_stream = false) {
         }
         c->own_stream = true;
     }
-    if (cudaMallocHost(&c->pinned, 96 * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost(&c->pinned, 128 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
@@ -1675,7 +1684,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (!c) return SPH_ENOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 96 * sizeof(int)) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 128 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SPH_ECUDA;

@@ -65,6 +65,7 @@ struct TreeDev {
     int *lvl_src;                // [Lmax+1] boxes holding sources per level (zeroed before the emit)
     int *lvl_leaf;               // [Lmax+1] leaves holding targets per level (lvl_src + 16,
                                  // zeroed with it)
+    int *lvl_sleaf;              // [Lmax+1] leaves holding sources per level (lvl_src + 32, zeroed with it)
     int *b_level;
     uint32_t *b_key;
     int *b_sb, *b_se, *b_tb, *b_te, *b_parent;
