@@ -160,15 +160,20 @@ __device__ __forceinline__ void issue_mmas(const TcSmem &s, uint32_t tmem) {
 
 // The common body: operator image `img` (hi followed by lo), columns already in smem.
 // Adds D into out[col_dst[j] * np + i] (atomically if `atomic`).  Returns false on a timeout.
-__device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__restrict__ img,
-                                          const float *__restrict__ state, float *__restrict__ out, int np,
-                                          int n, bool atomic, int *err) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Copy of the operator image `img` (hi followed by lo) into the A tile (thread 0).
+__device__ __forceinline__ void tile_issue_image(const TcSmem &s, const uint16_t *__restrict__ img) {
     if (threadIdx.x == 0) {
         tc::mbar_expect_tx(tc::smem_u32(s.bar_a), 2 * A_BYTES);
         tc::bulk_g2s(tc::smem_u32(s.a_hi), img, A_BYTES, tc::smem_u32(s.bar_a));
         tc::bulk_g2s(tc::smem_u32(s.a_lo), img + A_BYTES / 2, A_BYTES, tc::smem_u32(s.bar_a));
     }
+}
+
+__device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__restrict__ img,
+                                          const float *__restrict__ state, float *__restrict__ out, int np,
+                                          int n, bool atomic, int *err, bool image_issued = false) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (!image_issued) tile_issue_image(s, img);
     gather_split(s, state, np);
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -237,7 +242,7 @@ __device__ __forceinline__ void tile_teardown(const TcSmem &s) {
 // ---------------------------------------------------------------- M2L over offset-grouped V pairs
 __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
                                                 int *err) {
-    pdl_enter();
+    // prologue (the V pairs, their tiles and the operator images were written before the passes)
     extern __shared__ uint8_t smem_raw[];
     const int tile = blockIdx.x;
     if (tile >= Pd.tile_off[Pd.nkeys]) return;
@@ -253,9 +258,11 @@ __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
         s.col_src[threadIdx.x] = q < p1 ? Pd.src[q] : -1;
         s.col_dst[threadIdx.x] = q < p1 ? Pd.trg[q] : -1;
     }
-    __syncthreads();
     const uint16_t *img = images + (size_t)key * (2 * A_BYTES / 2);
-    tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err);
+    tile_issue_image(s, img);
+    pdl_enter();
+    __syncthreads();
+    tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err, true);
     tile_teardown(s);
 }
 
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
 // ---------------------------------------------------------------- L2L for one level
 __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_begin, int parent_count,
                                                 const uint16_t *__restrict__ images, int *err) {
-    pdl_enter();
+    // prologue: tree arrays and operator images only
     extern __shared__ uint8_t smem_raw[];
     TcSmem s = carve(smem_raw);
     const int t0 = blockIdx.x * TCN;
@@ -498,7 +505,9 @@ __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_
     if (!__syncthreads_or(any)) return;
     tile_setup(s);
     const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
-    tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err);
+    tile_issue_image(s, img);
+    pdl_enter();
+    tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err, true);
     tile_teardown(s);
 }
 
@@ -509,19 +518,23 @@ __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_
 __global__ void __launch_bounds__(256) k_m2m_tc(FmmDev F, int level, const int *__restrict__ list,
                                                 const int *__restrict__ count, const uint16_t *__restrict__ images,
                                                 int *err) {
-    pdl_enter();
+    // prologue: this CTA's tensor memory, barriers and operator image (the source list and its
+    // count come from the work lists, read after the wait)
     extern __shared__ uint8_t smem_raw[];
     TcSmem s = carve(smem_raw);
     const int t0 = blockIdx.x * TCN;
     const int c = blockIdx.y;
+    tile_setup(s);
+    const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
+    tile_issue_image(s, img);
+    pdl_enter();
     const int cnt = *count;
-    if (t0 >= cnt) return;
-    const TreeDev &T = F.T;
     int any = 0;
+    const TreeDev &T = F.T;
     if (threadIdx.x < TCN) {
         const int j = t0 + threadIdx.x;
         int P = -1, C = -1;
-        if (j < cnt) {
+        if (t0 < cnt && j < cnt) {
             const int p = list[j];
             if (!T.b_leaf[p]) {
                 const int ch = T.box_at[dense_off(level + 1) + ((T.b_key[p] << 3) | (uint32_t)c)];
@@ -532,10 +545,13 @@ __global__ void __launch_bounds__(256) k_m2m_tc(FmmDev F, int level, const int *
         s.col_src[threadIdx.x] = C;
         s.col_dst[threadIdx.x] = P;
     }
-    if (!__syncthreads_or(any)) return;
-    tile_setup(s);
-    const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
-    tile_body(s, img, F.ueq, F.ueq, F.O.npad, F.O.n, true, err);
+    if (!__syncthreads_or(any)) {
+        // nothing to do: let the image copy land before the shared memory is released
+        if (threadIdx.x == 0) tc::mbar_wait_bounded(tc::smem_u32(s.bar_a), 0, WAIT_LIMIT);
+        tile_teardown(s);
+        return;
+    }
+    tile_body(s, img, F.ueq, F.ueq, F.O.npad, F.O.n, true, err, true);
     tile_teardown(s);
 }
 
@@ -556,7 +572,7 @@ constexpr uint32_t L8_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + 64 + 9 * TCN * 4
 
 __global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent_begin, int parent_count,
                                                  const uint16_t *__restrict__ images, int *err) {
-    pdl_enter();
+    // prologue: tree arrays, tensor memory, barriers and the first two operator images
     extern __shared__ uint8_t smem_raw[];
     uintptr_t pa = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
     uint8_t *base = reinterpret_cast<uint8_t *>(pa);
@@ -617,6 +633,7 @@ __global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent
                          tc::smem_u32(bar_a + k));
         }
     }
+    pdl_enter();
     gather_split(s, F.dchk, np);
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -923,8 +940,12 @@ __device__ __forceinline__ void lp_store(uint8_t *hi, uint8_t *lo, const float4 
 __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int parent_begin, int parent_count,
                                                      int ppc, int nchunks, const uint16_t *__restrict__ img_c,
                                                      float *__restrict__ out, int *err) {
-    pdl_enter();
-    if ((int)blockIdx.x >= nchunks) return;        // uniform, before any allocation
+    // prologue: tensor memory, barriers, the first two tables and the first chunk's tree
+    // lookups; the wait comes before the first parent row is read
+    if ((int)blockIdx.x >= nchunks) {              // uniform, before any allocation
+        pdl_enter();
+        return;
+    }
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *ap_hi = base, *ap_lo = base + LP_A;
@@ -1042,6 +1063,7 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
             }
     };
     int g = 0;                                              // rounds of this CTA so far
+    bool waited = false;
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const bool more = chunk + (int)gridDim.x < nchunks;   // this CTA has another chunk after this one
         __syncthreads();                                       // previous chunk's epilogue read sch / sfull
@@ -1068,6 +1090,10 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
         }
         // a chunk without leaves has no rounds (the tables in flight serve the next chunk's)
         if (!__syncthreads_or(any)) continue;
+        if (!waited) {
+            pdl_enter();
+            waited = true;
+        }
         lp_load(v, spar, F.dchk, np);
         lp_store(ap_hi, ap_lo, v);
         bool ok = true;
@@ -1123,6 +1149,7 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
         if (!ok) break;
         epilogue(7);
     }
+    if (!waited) pdl_enter();                   // a CTA whose chunks had no leaves
     if (tid == 0) {
         // let this CTA's own copies and MMAs finish before its memory is released (after a
         // timeout, or copies issued for rounds of chunks that had no leaves)
@@ -1143,15 +1170,20 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
 constexpr int OWN_W = 8;
 __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
                                                         const int *__restrict__ count, float *__restrict__ out) {
-    pdl_enter();
+    // prologue: the leaf list (written by the work-list kernel, several launches back) and the
+    // table; the wait comes before the first local expansion is read
     const int cnt = *count;
-    if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform, before the table is staged
+    if ((int)blockIdx.x * OWN_W >= cnt) {                  // uniform, before the table is staged
+        pdl_enter();
+        return;
+    }
     __shared__ float Es[TCK * 64];                          // [n][64]
     __shared__ float sd[OWN_W][TCK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = F.O.n, np = F.O.npad;
     const float4 *E4 = reinterpret_cast<const float4 *>(F.O.e_tab + F.O.e_off[level]);
     for (int j = threadIdx.x; j < n * 16; j += blockDim.x) reinterpret_cast<float4 *>(Es)[j] = __ldg(E4 + j);
+    pdl_enter();
     __syncthreads();
     const TreeDev &T = F.T;
     for (int i = blockIdx.x * OWN_W + warp; i < cnt; i += gridDim.x * OWN_W) {

@@ -19,6 +19,11 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// pdl_enter() after a prologue: a kernel may first touch what no kernel of the FMM passes
+// writes -- the tree and list arrays, the operator images and tables (written before the passes
+// were queued) -- and set up its own shared memory, barriers and tensor memory, so that this
+// work overlaps the previous kernel's tail.  A grid is released only once every CTA of the
+// previous one has started, so the early CTAs never keep the previous grid's CTAs waiting.
 // SPH_PDL=0 in the environment launches every kernel in plain stream order.
 inline bool pdl_enabled() {
     static const bool on = [] {
