@@ -871,7 +871,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
         launch_pdl(k_select_emit, grid, SEL_T, 0, st, r, A.q, A.emag, A.mask, (const unsigned *)A.maxes, bstat, nbr,
                    (const int *)A.off_s, (const int *)A.off_t, A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc,
                    A.tmask);
-        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+        return cudaGetLastError() == cudaSuccess ? 1 : -1;
     }
     // one pass: the look-back states live in cnt_s .. cnt_t (2 ints per brick), the ticket in off_s[0]
     unsigned long long *state = reinterpret_cast<unsigned long long *>(A.cnt_s);

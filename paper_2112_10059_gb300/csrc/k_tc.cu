@@ -1170,13 +1170,8 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
 constexpr int OWN_W = 8;
 __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
                                                         const int *__restrict__ count, float *__restrict__ out) {
-    // prologue: the leaf list (written by the work-list kernel, several launches back) and the
-    // table; the wait comes before the first local expansion is read
-    const int cnt = *count;
-    if ((int)blockIdx.x * OWN_W >= cnt) {                  // uniform, before the table is staged
-        pdl_enter();
-        return;
-    }
+    // prologue: the table is staged; the list, its count and the local expansions are read
+    // after the wait (the launch is sized by an upper bound of the count)
     __shared__ float Es[TCK * 64];                          // [n][64]
     __shared__ float sd[OWN_W][TCK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1184,6 +1179,8 @@ __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, con
     const float4 *E4 = reinterpret_cast<const float4 *>(F.O.e_tab + F.O.e_off[level]);
     for (int j = threadIdx.x; j < n * 16; j += blockDim.x) reinterpret_cast<float4 *>(Es)[j] = __ldg(E4 + j);
     pdl_enter();
+    const int cnt = *count;
+    if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform
     __syncthreads();
     const TreeDev &T = F.T;
     for (int i = blockIdx.x * OWN_W + warp; i < cnt; i += gridDim.x * OWN_W) {

@@ -228,14 +228,67 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *a, int lo, int hi
 // carried out by the whole block, so that no warp runs them one lane at a time.
 constexpr int RANGE_PER = 8, RANGE_T = 256;
 
+// Target ranges from the selection's per-brick offsets (bricks of 16^3 cells, Morton order,
+// brick b's targets at [boff[b], boff[b + 1]) of the key array, boff[nbr] = nt): a slot of a
+// level at or above the bricks' (D - 4) spans whole bricks; a finer slot lies inside one brick,
+// whose keys are (b << 12) | local index -- consecutive where every cell is a target, found by
+// two binary searches over the brick's keys otherwise.  One thread per dense slot.
+__device__ __forceinline__ void slot_range_from_bricks(int64_t s, int Lmax, int D, const int *__restrict__ boff,
+                                                       int nbr, int nt, const uint32_t *__restrict__ key,
+                                                       int &tb, int &te) {
+    int l = 0;
+    while (l < Lmax && s >= dense_off(l + 1)) ++l;
+    const uint32_t m = (uint32_t)(s - dense_off(l));
+    auto off = [&](uint32_t b) { return b < (uint32_t)nbr ? boff[b] : nt; };
+    if (l <= D - 4) {
+        const int sh = 3 * (D - 4 - l);
+        tb = off(m << sh);
+        te = off((m + 1) << sh);
+        return;
+    }
+    const int sh = 3 * (D - l);
+    const uint32_t k0 = m << sh, b = k0 >> 12;
+    const int ob = off(b), oe = off(b + 1);
+    if (oe - ob == 4096) {
+        tb = ob + (int)(k0 & 4095u);
+        te = tb + (1 << sh);
+        return;
+    }
+    int lo = ob, hi = oe;                                   // first key >= k0
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid] < k0) lo = mid + 1; else hi = mid;
+    }
+    tb = lo;
+    hi = oe;                                                // first key >= k0 + 8^(D-l)
+    const uint32_t k1 = k0 + (1u << sh);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid] < k1) lo = mid + 1; else hi = mid;
+    }
+    te = lo;
+}
+
 // One launch for both point sets: blocks [0, gs) take the sources (grid-stride over gs blocks),
-// the others the targets.
+// the others the targets -- by a pass over the keys, or (boff != nullptr) slot by slot from the
+// selection's per-brick offsets.
 __global__ void __launch_bounds__(RANGE_T) k_tree_ranges(const int *__restrict__ ns_dev, const uint32_t *__restrict__ skey,
                                                          int *__restrict__ sbeg, int *__restrict__ send, int gs,
                                                          const int *__restrict__ nt_dev, const uint32_t *__restrict__ tkey,
-                                                         int *__restrict__ tbeg, int *__restrict__ tend, int D, int Lmax) {
+                                                         int *__restrict__ tbeg, int *__restrict__ tend, int D, int Lmax,
+                                                         const int *__restrict__ boff, int nbr, int64_t nslot) {
     pdl_enter();
     const bool src = (int)blockIdx.x < gs;
+    if (!src && boff) {
+        const int64_t s = (int64_t)(blockIdx.x - gs) * blockDim.x + threadIdx.x;
+        if (s >= nslot) return;
+        const int nt = max(*nt_dev, 0);
+        int tb, te;
+        slot_range_from_bricks(s, Lmax, D, boff, nbr, nt, tkey, tb, te);
+        tbeg[s] = tb;
+        tend[s] = te;
+        return;
+    }
     const int bid = src ? (int)blockIdx.x : (int)blockIdx.x - gs, nblk = src ? gs : (int)gridDim.x - gs;
     const int *n_dev = src ? ns_dev : nt_dev;
     const uint32_t *key = src ? skey : tkey;
@@ -435,7 +488,11 @@ __global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ 
 
 void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     const int64_t nslot = dense_off(A.Lmax + 1);
-    if (A.rse == A.rsb + nslot && A.rtb == A.rse + nslot && A.rte == A.rtb + nslot) {
+    if (A.brick_off_t) {
+        // the target ranges of every slot are written from the brick offsets
+        cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
+        cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
+    } else if (A.rse == A.rsb + nslot && A.rtb == A.rse + nslot && A.rte == A.rtb + nslot) {
         cudaMemsetAsync(A.rsb, 0, 4 * nslot * sizeof(int), st);
     } else {
         cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
@@ -448,8 +505,9 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     // once); sources, usually far fewer: a grid-stride loop over 8 blocks per SM
     const int rg = (int)std::min<int64_t>(((int64_t)A.ncap + RB - 1) / RB, 1 << 20);
     const int gs = std::max(std::min(rg, 152 * 8), 1);
-    launch_pdl(k_tree_ranges, gs + std::max(rg, 1), RANGE_T, 0, st, A.ns_dev, A.skey, A.rsb, A.rse, gs, A.nt_dev,
-               A.tkey, A.rtb, A.rte, A.D, A.Lmax);
+    const int gt = A.brick_off_t ? (int)((nslot + RANGE_T - 1) / RANGE_T) : std::max(rg, 1);
+    launch_pdl(k_tree_ranges, gs + gt, RANGE_T, 0, st, A.ns_dev, A.skey, A.rsb, A.rse, gs, A.nt_dev,
+               A.tkey, A.rtb, A.rte, A.D, A.Lmax, A.brick_off_t, A.nbr, nslot);
     const int grid = (int)((nslot + 255) / 256);
     cudaMemsetAsync(A.T.lvl_src, 0, 48 * sizeof(int), st);   // lvl_src, lvl_leaf and lvl_sleaf
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);

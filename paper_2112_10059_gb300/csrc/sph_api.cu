@@ -90,6 +90,7 @@ struct sph_ctx {
     bool l2p_tc_used = false;         // this eval ran the tensor-core L2P
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
+    bool brick_offsets = false;       // the last selection left every 16^3 brick's target offset in b_off
     bool near_overlap = true;         // near field on a second stream beside the far-field passes
     int near_per_sm = 6;              // its U-list launch: CTAs per SM (room for the far-field CTAs; measured)
     cudaStream_t near_stream = nullptr;
@@ -268,7 +269,9 @@ int select_queue(sph_ctx *c) {
     A.trg_key = P<uint32_t>(c->b_tkey);   // targets' cells follow from their keys: no packed copy
     A.tmask = P<uint8_t>(c->b_tmask);
     A.bstat = P<float>(c->b_bstat);
-    if (select_launch(A, c->stream) != 0) CK(cudaGetLastError());
+    const int sr = select_launch(A, c->stream);
+    if (sr < 0) CK(cudaGetLastError());
+    c->brick_offsets = sr == 1 && b == 4;
     c->launches += 2;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
@@ -385,6 +388,10 @@ int tree_queue(sph_ctx *c) {
     A.occ = P<uint8_t>(c->b_near); A.near = A.occ + dense_total; A.vsrc = A.occ + 2 * dense_total;
     A.scan_tmp = P<int>(c->b_scan);
     A.err = P<int>(c->b_tot) + 3;
+    if (c->brick_offsets && D >= 4) {
+        A.nbr = 1 << (3 * (D - 4));
+        A.brick_off_t = P<int>(c->b_off) + A.nbr;       // off_t follows off_s (select_queue)
+    }
     CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
     // ranges (sources and targets in one launch), existence flags, scan, emit, source occupancy

@@ -41,6 +41,8 @@ struct SelectArgs {
     // nullptr: the maxima alone (k_grid_max) and every brick read
     float *bstat = nullptr;
 };
+// 1: queued, and off_t holds every brick's exclusive target offset (count / scan / emit form);
+// 0: queued without per-brick offsets; -1: a launch failed
 int select_launch(const SelectArgs &A, cudaStream_t st);
 
 // ---------------------------------------------------------------- direct sum
@@ -88,6 +90,12 @@ struct TreeArgs {
     uint8_t *vsrc;                // dense over levels 0..Lmax: box exists and holds sources
     int *scan_tmp;
     int *err = nullptr;           // bit 0 set if a scan's look-back gave up waiting
+    // optional: the selection's exclusive offsets of each 16^3 brick's targets ([nbr], bricks
+    // in Morton order, D >= 4): the target ranges then follow from them slot by slot (a
+    // binary search only inside bricks that are partly selected) instead of from a pass over
+    // the target keys
+    const int *brick_off_t = nullptr;
+    int nbr = 0;
 };
 void tree_build_launch(const TreeArgs &A, cudaStream_t st);
 size_t scan_tmp_ints(int n);

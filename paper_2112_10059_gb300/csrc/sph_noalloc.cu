@@ -111,7 +111,7 @@ extern "C" int sph_select_noalloc(int device, void *cuda_stream, int nx, int ny,
         if (end && *end == 0) A.wait_limit = (unsigned)v;
     }
     int rc = SPH_OK;
-    if (sph::select_launch(A, st) != 0) rc = SPH_ECUDA;
+    if (sph::select_launch(A, st) < 0) rc = SPH_ECUDA;
     // (sources, targets, gave-up flag): copied after the selection kernel has completed, so the
     // flag of every brick that gave up waiting is in it
     if (rc == SPH_OK && cudaMemcpyAsync(counts_dev, A.totals, 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=

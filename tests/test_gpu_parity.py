@@ -188,6 +188,30 @@ def test_tree_bit_exact(sph, ctx, case):
         assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
 
 
+@pytest.mark.parametrize("dims", [(64, 48, 48), (56, 48, 40)])
+@pytest.mark.parametrize("form", SELECT_FORMS)
+def test_tree_bit_exact_whole_bricks(sph, monkeypatch, dims, form):
+    """The tree and its lists on fields built brick by brick: with the default selection the
+    target ranges of the slots follow from the per-brick offsets (whole bricks by arithmetic,
+    partly selected ones by binary search, bricks past the grid); the other forms take the
+    pass over the target keys.  All bit-exact against the oracle's octree."""
+    p = si.brick_structured(*dims)
+    monkeypatch.setenv("SPH_SELECT_TWO_PASS", form[0])
+    monkeypatch.setenv("SPH_SELECT_LOOKBACK", form[1])
+    c = sph.Context(0)
+    sph.solve(p, c, leaf_size=16)
+    g = sph.get_tree(c)
+    c.close()
+    J, T = oracle.select(p.q, p.emag, None, p.i_frac, p.e_frac, p.e_applied)
+    o = oracle.octree(p.nx, p.ny, p.nz, J, T, 16)
+    assert g["depth"] == o["depth"]
+    for k in ("level", "key", "src_begin", "src_end", "trg_begin", "trg_end", "parent"):
+        assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
+    assert np.array_equal(g["leaf"], o["leaf"])
+    for k in ("U", "V", "W", "X"):
+        assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
+
+
 @pytest.mark.parametrize("n", [0, 1, 1000, 32768, 32769, 8192 * 37 + 5, 3_000_001])
 def test_device_scan_exact(sph, n):
     """The one-launch device scan that numbers the boxes and lays out the lists equals the

@@ -2,10 +2,12 @@
 
 A kernel launched with programmatic stream serialization (``launch_pdl``) may be scheduled
 before the previous kernel of its stream has finished, so it must wait (``pdl_enter()``, the
-griddepcontrol wait) before it touches memory.  These tests parse the CUDA sources and check
-that every kernel launched that way opens with that call, that the call waits before it lets
-the next kernel launch, and that the files of the evaluation's kernels launch all of them that
-way.
+griddepcontrol wait) before it touches memory that the preceding kernels write.  These tests
+parse the CUDA sources and check that every kernel launched that way either opens with that
+call or, in a prologue before it, names none of the buffers the passes write (the states, the
+output, the work lists and their counts, the selection's outputs), that the call waits before
+it lets the next kernel launch, and that the files of the evaluation's kernels launch all of
+them that way.
 """
 import os
 import re
@@ -68,6 +70,12 @@ def _pdl_launched(srcs):
     return names
 
 
+# names of what the kernels of the passes write (a prologue must not name them)
+WRITTEN = ["dchk", "ueq", "out", "count", "cnt", "list", "near_buf", "skip_count", "maxes", "totals", "state",
+           "ticket", "src_key", "src_pc", "src_q", "trg_key", "trg_pc", "tmask", "bstat", "w_src", "err_flag"]
+PROLOGUE_KERNELS = {"k_m2l_tc", "k_l2l_tc", "k_m2m_tc", "k_l2l_tc8", "k_l2lp_tc", "k_l2p_own"}
+
+
 def test_every_pdl_kernel_waits_first():
     srcs = {f: _strip_comments(s) for f, s in _sources().items()}
     launched = _pdl_launched(srcs)
@@ -77,8 +85,13 @@ def test_every_pdl_kernel_waits_first():
         bodies.update(_kernel_bodies(s))
     missing = sorted(n for n in launched if n not in bodies)
     assert not missing, "launched with launch_pdl but not defined: %s" % missing
-    bad = sorted(n for n in launched if not bodies[n].lstrip().startswith("pdl_enter();"))
-    assert not bad, "kernels launched with launch_pdl that do not open with pdl_enter(): %s" % bad
+    no_wait = sorted(n for n in launched if "pdl_enter();" not in bodies[n])
+    assert not no_wait, "kernels launched with launch_pdl without pdl_enter(): %s" % no_wait
+    prologues = {n: bodies[n][:bodies[n].index("pdl_enter();")] for n in launched}
+    bad = sorted(n for n, pre in prologues.items() if re.search(r"\b(%s)\b" % "|".join(WRITTEN), pre))
+    assert not bad, "kernels that touch what the passes write before pdl_enter(): %s" % bad
+    # the prologue kernels are the tensor-core translations (set-up that overlaps the previous tail)
+    assert {n for n, pre in prologues.items() if pre.strip()} <= PROLOGUE_KERNELS
 
 
 def test_pdl_enter_waits_before_releasing():
