@@ -853,6 +853,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     const float4 *bstat = reinterpret_cast<const float4 *>(A.bstat);
     if (stats) launch_pdl(k_brick_stats, nbr, STAT_T, 0, st, r, gq, ge, reinterpret_cast<float4 *>(A.bstat), A.maxes);
     else if (gq || ge) launch_pdl(k_grid_max, gm, 256, 0, st, gq, ge, n, A.maxes);
+    A.launched = (stats || gq || ge) ? 1 : 0;
     if (A.two_pass) {
         launch_pdl(k_select_brick<false>, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, A.cnt_s, A.cnt_t,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -861,6 +862,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
         launch_pdl(k_select_brick<true>, nbr, 512, 0, st, r, A.q, A.emag, A.mask, A.maxes, nullptr, nullptr,
                                                   A.off_s, A.off_t, A.src_key, A.src_pc, A.src_q,
                                                   A.trg_key, A.trg_pc, A.tmask);
+        A.launched += 3;
         return cudaGetLastError() == cudaSuccess ? 0 : -1;
     }
     if (stats && !A.lookback) {
@@ -871,6 +873,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
         launch_pdl(k_select_emit, grid, SEL_T, 0, st, r, A.q, A.emag, A.mask, (const unsigned *)A.maxes, bstat, nbr,
                    (const int *)A.off_s, (const int *)A.off_t, A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc,
                    A.tmask);
+        A.launched += 3;
         return cudaGetLastError() == cudaSuccess ? 1 : -1;
     }
     // one pass: the look-back states live in cnt_s .. cnt_t (2 ints per brick), the ticket in off_s[0]
@@ -881,6 +884,7 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     launch_pdl(k_select_onepass, nbr, SEL_T, 0, st, r, A.q, A.emag, A.mask, A.maxes, state, ticket, nbr, A.totals,
                                           A.src_key, A.src_pc, A.src_q, A.trg_key, A.trg_pc, A.tmask, A.wait_limit,
                                           stats ? bstat : nullptr);
+    A.launched += 1;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -92,7 +92,7 @@ struct sph_ctx {
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     bool brick_offsets = false;       // the last selection left every 16^3 brick's target offset in b_off
     bool near_overlap = true;         // near field on a second stream beside the far-field passes
-    int near_per_sm = 6;              // its U-list launch: CTAs per SM (room for the far-field CTAs; measured)
+    int near_per_sm = 0;              // its U-list launch: CTAs per SM (0: by the estimate in fmm_queue)
     cudaStream_t near_stream = nullptr;
     cudaEvent_t near_fork = nullptr, near_join = nullptr, near_up = nullptr;
     DevBuf b_nearbuf;                 // the near field's per-leaf sums (overlapped form)
@@ -272,7 +272,7 @@ int select_queue(sph_ctx *c) {
     const int sr = select_launch(A, c->stream);
     if (sr < 0) CK(cudaGetLastError());
     c->brick_offsets = sr == 1 && b == 4;
-    c->launches += 2;
+    c->launches += A.launched;
     CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
@@ -690,6 +690,29 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     return SPH_OK;
 }
 
+// The M2L form: target-stationary tiles pay a round per (group, offset) whatever the number of
+// pairs in it, so they are taken where the lists are dense (uniform trees), the tiles of V pairs
+// elsewhere (an autotuned choice overrides the density rule).
+bool m2l_target_tiles(const sph_ctx *c, const PassState &S) {
+    const int64_t nV = c->list_tot[1], nb = c->nboxes;
+    return S.tc && (c->m2l_tiles == 1 ||
+                    (c->m2l_tiles == 2 && (c->m2l_form >= 0 ? c->m2l_form == 1 : nV >= 32 * nb)));
+}
+
+// CTAs per SM of the overlapped near field's U-list launch.  Where the far-field chain is the
+// longer of the two, 6 (measured best at the 256^3 headline) leave slots to its kernels; where
+// the near field is the longer one (every cell a source: the uniform 128^3 tree), it gets the
+// whole machine (16; measured best there).  Estimates from the list totals: near-field
+// evaluations at most U entries x leaf size^2 at 1.6e12/s; far field a fixed 150 us plus the
+// M2L at its measured cost per V pair (0.45 ns in pair tiles, 0.19 ns in target tiles).
+int near_cap(const sph_ctx *c, const PassState &S) {
+    if (c->near_per_sm > 0) return c->near_per_sm;
+    const double s = c->leaf_eff;
+    const double near_us = (double)c->list_tot[0] * s * s / 1.6e6;
+    const double far_us = 150.0 + (double)c->list_tot[1] * (m2l_target_tiles(c, S) ? 0.19e-3 : 0.45e-3);
+    return near_us > far_us ? 16 : 6;
+}
+
 // Queue the passes on c->stream: memsets and kernels only (no allocation, no sync).
 int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     FmmDev &F = S.F;
@@ -716,7 +739,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             ++c->launches;
         }
         if (tm) tm->mark_at(12, c->near_stream);
-        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 0, 1, c->near_per_sm);
+        fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 0, 1, near_cap(c, S));
         ++c->launches;
         if (tm) tm->mark_at(14, c->near_stream);
     }
@@ -769,11 +792,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         const int nV = c->list_tot[1];
         // (the V pairs were grouped by key with the lists)
         if (tm) tm->mark_at(5, c->stream);
-        // target-stationary tiles pay a round per (group, offset) whatever the number of pairs in
-        // it, so they are taken where the lists are dense (uniform trees), the pair tiles elsewhere
-        const bool tiles = S.tc && (c->m2l_tiles == 1 ||
-                                    (c->m2l_tiles == 2 && (c->m2l_form >= 0 ? c->m2l_form == 1
-                                                                            : (int64_t)nV >= 32ll * nb)));
+        const bool tiles = m2l_target_tiles(c, S);
         c->m2l_tiles_used = tiles;
         if (tiles) {
             // w_cnt[36]: number of groups, w_cnt[37]: the work counter (zeroed with the others)

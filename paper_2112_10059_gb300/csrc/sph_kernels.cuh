@@ -40,6 +40,7 @@ struct SelectArgs {
     // pass, with which the one-pass selection emits a uniform brick without reading it again;
     // nullptr: the maxima alone (k_grid_max) and every brick read
     float *bstat = nullptr;
+    mutable int launched = 0;        // out: kernels select_launch queued
 };
 // 1: queued, and off_t holds every brick's exclusive target offset (count / scan / emit form);
 // 0: queued without per-brick offsets; -1: a launch failed
