@@ -170,10 +170,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the 256^3 adaptive workload
-# (dram__bytes_read.sum + dram__bytes_write.sum of k_l2lp_tc); valid for that workload and the
-# kernel as profiled (None once the kernel has changed since).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture each of the 256^3 adaptive workload
+# (dram__bytes_read.sum + dram__bytes_write.sum of the kernel); valid for that workload and the
+# kernels as profiled (removed once a kernel has changed since).
+NCU_TRAFFIC = {"m2l": (97.756 + 3.199) * 1e6, "l2lp": (26.381 + 9.930) * 1e6}
 
 
 def pipe_peaks(sph, dev, stream, f_mhz_nominal=2070.0):
@@ -247,7 +247,8 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
     add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", True, "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
         med("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
         ("measured dense BF16 %.1f TFLOP/s burst (%s)" % (tpk, peaks["source"])) if tc else
-        "measured FP32 FMA %.1f TFLOP/s (%s)" % (fp32_peak, pipes["source"]))
+        "measured FP32 FMA %.1f TFLOP/s (%s)" % (fp32_peak, pipes["source"]),
+        traffic=NCU_TRAFFIC.get("m2l") if traffic_ok and tc else None)
     if n_child > 0:
         add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", False, "tensor" if tc else "alu",
             2.0 * n * n * n_child, "flop", med("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
@@ -874,8 +875,17 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # phase breakdown (library CUDA-event timers) from separate steps: the timers add event
-    # records and a final synchronisation, which the timed steps above do without
-    step_stats = phase_stats(sph, ctx, out, flush, max(3, min(args.steps, 5)))
+    # records and a final synchronisation, which the timed steps above do without.  In the timed
+    # steps the near field runs on a second stream beside the far-field passes, so its timer
+    # spans the far field too; the per-kernel attribution (phases, rooflines) therefore comes
+    # from a context with the near field after the far field, each kernel on the GPU alone
+    nph = max(3, min(args.steps, 5))
+    step_stats_overlapped = phase_stats(sph, ctx, out, flush, nph)
+    ctx_seq = make_ctx(sph, dev, stream, p, q, em, prec, args.order, env={"SPH_NEAR_OVERLAP": "0"})
+    for _ in range(2):
+        sph.eval_sph(ctx_seq, out)
+    step_stats = phase_stats(sph, ctx_seq, out, flush, nph)
+    ctx_seq.close()
     torch.cuda.synchronize()
     ms, value = whole_job_rate(statistics.median(step_ms), nt, world, dist, dev)
 
@@ -981,7 +991,10 @@ def main():
                         "d2h_bytes_per_step": int(sh.nbytes)},
                 "roofline": dict(roof[dominant], phase=dominant),
                 "rooflines": roof, "pipe_peaks": pipes,
-                "clocks": clocks, "gpu_launches": int(step_stats[-1]["n_launches"]) * args.steps,
+                "clocks": clocks, "gpu_launches": int(step_stats_overlapped[-1]["n_launches"]) * args.steps,
+                "phases_overlapped_ms": {k: statistics.median(x[k] for x in step_stats_overlapped)
+                                         for k in ("ms_select", "ms_tree", "ms_upward", "ms_m2l", "ms_l2l",
+                                                   "ms_l2p", "ms_l2lp", "ms_near", "ms_total")},
                 "phases_ms": {k: statistics.median(x[k] for x in step_stats)
                               for k in ("ms_select", "ms_tree", "ms_upward", "ms_vpairs", "ms_m2l", "ms_l2l",
                                         "ms_l2p", "ms_l2lp", "ms_near", "ms_total")},

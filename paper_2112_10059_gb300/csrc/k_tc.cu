@@ -1170,17 +1170,15 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
 constexpr int OWN_W = 8;
 __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
                                                         const int *__restrict__ count, float *__restrict__ out) {
-    // prologue: the table is staged; the list, its count and the local expansions are read
-    // after the wait (the launch is sized by an upper bound of the count)
+    pdl_enter();
+    const int cnt = *count;
+    if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform, before the table is staged
     __shared__ float Es[TCK * 64];                          // [n][64]
     __shared__ float sd[OWN_W][TCK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = F.O.n, np = F.O.npad;
     const float4 *E4 = reinterpret_cast<const float4 *>(F.O.e_tab + F.O.e_off[level]);
     for (int j = threadIdx.x; j < n * 16; j += blockDim.x) reinterpret_cast<float4 *>(Es)[j] = __ldg(E4 + j);
-    pdl_enter();
-    const int cnt = *count;
-    if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform
     __syncthreads();
     const TreeDev &T = F.T;
     for (int i = blockIdx.x * OWN_W + warp; i < cnt; i += gridDim.x * OWN_W) {
@@ -1237,7 +1235,7 @@ void fmm_l2lp_tc_level(const FmmDev &F, int level, int parent_begin, int parent_
 void fmm_l2p_own(const FmmDev &F, int level, const int *list, const int *count, int max_count, float *out,
                  cudaStream_t st) {
     if (max_count <= 0 || F.O.e_off[level] < 0 || F.O.npad > TCK || (1 << (F.D - level)) != 4) return;
-    const int grid = std::max(1, std::min((max_count + OWN_W - 1) / OWN_W, 2 * sm_count()));
+    const int grid = std::max(1, std::min((max_count + OWN_W - 1) / OWN_W, 4 * sm_count()));
     launch_pdl(k_l2p_own, grid, OWN_W * 32, 0, st, F, level, list, count, out);
 }
 
