@@ -193,54 +193,10 @@ __global__ void __launch_bounds__(256) k_l2l_gemm(FmmDev F, int level, int paren
 }
 
 // ---------------------------------------------------------------- V pairs grouped by offset
-// key = level * 316 + slot.  The list kernels count the pairs per key, scan the counts and
-// place every pair in its key's range (any order within a key).  One CTA then cuts every
-// key's range into tiles of TN pairs: tile counts, their exclusive scan (the tile offsets),
-// the closing offsets and the key of every tile.
-__global__ void __launch_bounds__(1024) k_vpairs_finish(PairsDev Pd) {
-    pdl_enter();
-    __shared__ int ws[32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int per = (Pd.nkeys + 1023) / 1024;
-    const int k0 = min(tid * per, Pd.nkeys), k1 = min(k0 + per, Pd.nkeys);
-    int s = 0;
-    for (int k = k0; k < k1; ++k) {
-        const int t = (Pd.cnt[k] + TN - 1) / TN;
-        Pd.tile_cnt[k] = t;
-        s += t;
-    }
-    int inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) ws[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int y = ws[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int z = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) y += z;
-        }
-        ws[lane] = y;
-    }
-    __syncthreads();
-    int x = (w ? ws[w - 1] : 0) + inc - s;
-    for (int k = k0; k < k1; ++k) {
-        Pd.tile_off[k] = x;
-        for (int t = 0; t < Pd.tile_cnt[k]; ++t) Pd.tile_key[x + t] = k;
-        x += Pd.tile_cnt[k];
-    }
-    if (tid == 1023) {
-        Pd.tile_off[Pd.nkeys] = ws[31];
-        Pd.total_tiles[0] = ws[31];
-        Pd.off[Pd.nkeys] = Pd.total_tiles[1];
-    }
-}
+// key = level * 316 + slot.  The list kernels count the pairs per key, k_lists_layout (k_tree.cu)
+// scans the counts and cuts every key's range into tiles of VPAIR_TILE pairs, and the list fill
+// places every pair in its key's range (any order within a key) and writes the key of every tile.
 
-void vpairs_finish(const PairsDev &Pd, cudaStream_t st) { launch_pdl(k_vpairs_finish, 1, 1024, 0, st, Pd); }
 
 // One CTA per tile of up to 64 V pairs sharing (level, offset): d_B += M2L_{l,o} u_A, scatter-added.
 __global__ void __launch_bounds__(256) k_m2l_pairs(FmmDev F, PairsDev Pd) {

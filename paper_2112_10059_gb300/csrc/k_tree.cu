@@ -618,9 +618,76 @@ __device__ __forceinline__ int coarse_leaf_src(const TreeDev &T, int lq, int qx,
     return -1;
 }
 
+// After the list counts and their scan (one CTA of 1024 threads): the closing offsets of the four
+// lists (entry nboxes: the list's total), the V pairs' key offsets (exclusive scan of the per-key
+// counts; entry nkeys: the number of pairs) and their tiles of VPAIR_TILE pairs per key (counts,
+// exclusive offsets; entry nkeys: the number of tiles).  The key of every tile is written by the
+// list fill, once the pair buffer has its size.
+__global__ void __launch_bounds__(1024) k_lists_layout(ListDev L, PairsDev Pd, const int *__restrict__ nboxes_dev,
+                                                       const int *__restrict__ totals) {
+    pdl_enter();
+    __shared__ int wp[32], wt[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) {
+        const int nb = *nboxes_dev;
+        L.u_off[nb] = totals[0];
+        L.v_off[nb] = totals[1];
+        L.w_off[nb] = totals[2];
+        L.x_off[nb] = totals[3];
+    }
+    const int per = (Pd.nkeys + 1023) / 1024;
+    const int k0 = min(tid * per, Pd.nkeys), k1 = min(k0 + per, Pd.nkeys);
+    int sp = 0, st = 0;
+    for (int k = k0; k < k1; ++k) {
+        const int c = Pd.cnt[k], t = (c + VPAIR_TILE - 1) / VPAIR_TILE;
+        Pd.tile_cnt[k] = t;
+        sp += c;
+        st += t;
+    }
+    int ip = sp, it = st;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, ip, o), b = __shfl_up_sync(0xffffffffu, it, o);
+        if (lane >= o) { ip += a; it += b; }
+    }
+    if (lane == 31) { wp[w] = ip; wt[w] = it; }
+    __syncthreads();
+    if (w == 0) {
+        int a = wp[lane], b = wt[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a2 = __shfl_up_sync(0xffffffffu, a, o), b2 = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += a2; b += b2; }
+        }
+        wp[lane] = a;
+        wt[lane] = b;
+    }
+    __syncthreads();
+    int xp = (w ? wp[w - 1] : 0) + ip - sp, xt = (w ? wt[w - 1] : 0) + it - st;
+    for (int k = k0; k < k1; ++k) {
+        Pd.off[k] = xp;
+        xp += Pd.cnt[k];
+        Pd.tile_off[k] = xt;
+        xt += Pd.tile_cnt[k];
+    }
+    if (tid == 1023) {
+        Pd.off[Pd.nkeys] = wp[31];
+        Pd.tile_off[Pd.nkeys] = wt[31];
+        Pd.total_tiles[0] = wt[31];
+        Pd.total_tiles[1] = wp[31];
+    }
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, PairsDev Pd, int D) {
     pdl_enter();
+    if (FILL) {
+        // the key of every V-pair tile (k_lists_layout laid the tiles out)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Pd.nkeys; k += gridDim.x * blockDim.x) {
+            const int x = Pd.tile_off[k], t1 = Pd.tile_cnt[k];
+            for (int t = 0; t < t1; ++t) Pd.tile_key[x + t] = k;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -760,25 +827,14 @@ void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, 
     S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
     for (int a = 0; a < 4; ++a) S.total[a] = totals + a;
     scan_exclusive_multi(S, 4, nboxes, scan_tmp, err, st);
-    scan_exclusive(Pd.cnt, Pd.off, Pd.nkeys, Pd.total_tiles + 1, scan_tmp, st, err);
-}
-
-__global__ void k_close_offsets(ListDev L, int nboxes, const int *__restrict__ totals) {
-    pdl_enter();
-    if (threadIdx.x == 0) {
-        L.u_off[nboxes] = totals[0];
-        L.v_off[nboxes] = totals[1];
-        L.w_off[nboxes] = totals[2];
-        L.x_off[nboxes] = totals[3];
-    }
+    launch_pdl(k_lists_layout, 1, 1024, 0, st, L, Pd, nboxes_dev, (const int *)totals);
 }
 
 void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
                        const int *totals, cudaStream_t st) {
     if (nboxes <= 0) return;
-    launch_pdl(k_close_offsets, 1, 32, 0, st, L, nboxes, totals);
+    (void)totals;
     launch_pdl(k_lists_warp<true>, LISTS_WARP_GRID, 256, 0, st, T, L, Pd, D);
-    vpairs_finish(Pd, st);
 }
 
 }  // namespace sph

@@ -420,7 +420,7 @@ int lists_count_queue(sph_ctx *c) {
     const int *nboxes_dev = P<int>(c->b_pos) + dense_off(Lmax + 1);   // the tree scan's total
     lists_count_launch(tree_dev(c), L, pairs_dev(c), c->list_cap, nboxes_dev, c->D, Lmax, P<int>(c->b_scan), ltot,
                        ltot - 1, c->stream);
-    c->launches += 4;   // classify, count, list and key scans
+    c->launches += 4;   // classify, count, list scan, lists / pairs layout
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
@@ -470,7 +470,7 @@ int lists_fill(sph_ctx *c) {
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
     lists_fill_launch(tree_dev(c), L, pairs_dev(c), c->nboxes, c->D, c->Lmax, ltot, c->stream);
-    if (c->nboxes > 0) c->launches += 3;   // close, fill, tiles of the V pairs
+    if (c->nboxes > 0) c->launches += 1;   // fill (with the tiles' keys)
     CK(cudaGetLastError());
     c->have_tree = true;
     return SPH_OK;

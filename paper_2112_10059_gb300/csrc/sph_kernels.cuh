@@ -294,8 +294,7 @@ struct PairsDev {
     int *total_tiles;     // [1]
     int *tile_key;        // [nV / 64 + nkeys]: key of every tile (one load instead of a search per CTA)
 };
-// per-key tile counts and offsets, the closing offsets and the tile -> key table (one CTA)
-void vpairs_finish(const PairsDev &Pd, cudaStream_t st);
+constexpr int VPAIR_TILE = 64;   // V pairs per M2L tile (the tensor-core tile's N)
 void fmm_m2l_pairs(const FmmDev &F, const PairsDev &Pd, int nV, int m2l_prec, cudaStream_t st);
 // tensor-core (tcgen05, BF16 x3) translations; require npad == 128
 bool tc_supported(const OpsDev &O);
