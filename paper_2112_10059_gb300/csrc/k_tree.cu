@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot,
                                                       const int *__restrict__ rtb, const int *__restrict__ rte,
                                                       const int *__restrict__ total, const uint32_t *__restrict__ skey,
                                                       const int *__restrict__ ns_dev, const uint32_t *__restrict__ tkey,
-                                                      const int *__restrict__ nt_dev, uint8_t *__restrict__ vsrc) {
+                                                      const int *__restrict__ nt_dev, uint8_t *__restrict__ vsrc,
+                                                      uint8_t *__restrict__ occ, int64_t npar) {
     pdl_enter();
     // per-level counts of the block's boxes with sources and leaves with targets, added into
     // the level tables once per block and level (the same few counters for every block)
@@ -401,6 +402,25 @@ __global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot,
     }
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (occ && s < npar) {
+        // occ[s], levels 0..Lmax-1: the slot's region holds a source point, or lies inside a leaf
+        // that holds sources (the deepest existing box over the slot, found from the existence
+        // flags and point ranges)
+        uint8_t o = rse[s] > rsb[s];
+        if (!o) {
+            int l = level_of_slot(s, Lmax);
+            int64_t m = s - dense_off(l);
+            for (; l >= 0; --l, m >>= 3) {
+                const int64_t a = dense_off(l) + m;
+                if (flag[a]) {
+                    const int ns = rse[a] - rsb[a], nt = rte[a] - rtb[a];
+                    o = !(l < D && (ns > S || nt > S)) && ns > 0;
+                    break;
+                }
+            }
+        }
+        occ[s] = o;
+    }
     if (s <= Lmax) {       // level table (threads 0..Lmax)
         const int l = (int)s;
         const int b0 = pos[dense_off(l)];
@@ -439,28 +459,6 @@ __global__ void __launch_bounds__(256) k_tree_emit_all(TreeDev T, int64_t nslot,
         if (s_leaf[threadIdx.x]) atomicAdd(T.lvl_leaf + threadIdx.x, s_leaf[threadIdx.x]);
         if (s_sleaf[threadIdx.x]) atomicAdd(T.lvl_sleaf + threadIdx.x, s_sleaf[threadIdx.x]);
     }
-}
-
-// occ[s] = 1 if the slot's region holds a source point, or lies inside a leaf that holds
-// sources (the deepest existing box over the slot); levels 0..Lmax-1.
-__global__ void k_src_occ(TreeDev T, int64_t nslot, int Lmax, const int *__restrict__ rsb,
-                          const int *__restrict__ rse, uint8_t *__restrict__ occ) {
-    pdl_enter();
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nslot) return;
-    uint8_t o = rse[s] > rsb[s];
-    if (!o) {
-        int l = level_of_slot(s, Lmax);
-        int64_t m = s - dense_off(l);
-        for (; l >= 0; --l, m >>= 3) {
-            const int B = T.box_at[dense_off(l) + m];
-            if (B >= 0) {
-                o = T.b_leaf[B] && T.b_se[B] > T.b_sb[B];
-                break;
-            }
-        }
-    }
-    occ[s] = o;
 }
 
 __global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ occ, uint8_t *__restrict__ near) {
@@ -513,12 +511,12 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
     scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);
-    launch_pdl(k_tree_emit_all, grid, 256, 0, st, A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
-                                          A.rte, total, A.skey, A.ns_dev, A.tkey, A.nt_dev, A.vsrc);
     const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
+    launch_pdl(k_tree_emit_all, grid, 256, 0, st, A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
+                                          A.rte, total, A.skey, A.ns_dev, A.tkey, A.nt_dev, A.vsrc,
+                                          (npar > 0 && A.near) ? A.occ : nullptr, npar);
     if (npar > 0 && A.occ && A.near) {
         const int g2 = (int)((npar + 255) / 256);
-        launch_pdl(k_src_occ, g2, 256, 0, st, A.T, npar, A.Lmax - 1, A.rsb, A.rse, A.occ);
         launch_pdl(k_src_near, g2, 256, 0, st, npar, A.Lmax - 1, A.occ, A.near);
     }
 }

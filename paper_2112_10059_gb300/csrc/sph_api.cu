@@ -394,9 +394,9 @@ int tree_queue(sph_ctx *c) {
     }
     CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
-    // ranges (sources and targets in one launch), existence flags, scan, emit, source occupancy
-    // and its dilation
-    c->launches += 1 + 3 + (Lmax >= 1 ? 2 : 0);
+    // ranges (sources and targets in one launch), existence flags, scan, emit (with the source
+    // occupancy), the occupancy's dilation
+    c->launches += 1 + 3 + (Lmax >= 1 ? 1 : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 48 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
