@@ -94,7 +94,7 @@ struct sph_ctx {
     bool near_overlap = true;         // near field on a second stream beside the far-field passes
     int near_per_sm = 0;              // its U-list launch: CTAs per SM (0: by the estimate in fmm_queue)
     cudaStream_t near_stream = nullptr;
-    cudaEvent_t near_fork = nullptr, near_join = nullptr, near_up = nullptr;
+    cudaEvent_t near_fork = nullptr, near_join = nullptr, near_up = nullptr, near_l2l = nullptr;
     DevBuf b_nearbuf;                 // the near field's per-leaf sums (overlapped form)
     unsigned select_wait = SELECT_WAIT_LIMIT;   // look-back polls of the selection (SPH_WAIT_LIMIT_SELECT)
     int fault_alloc = 0;              // > 0: the fault_alloc-th allocation fails (SPH_FAULT=alloc[:k])
@@ -675,6 +675,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
         if (!c->near_fork) CK(cudaEventCreateWithFlags(&c->near_fork, cudaEventDisableTiming));
         if (!c->near_join) CK(cudaEventCreateWithFlags(&c->near_join, cudaEventDisableTiming));
         if (!c->near_up) CK(cudaEventCreateWithFlags(&c->near_up, cudaEventDisableTiming));
+        if (!c->near_l2l) CK(cudaEventCreateWithFlags(&c->near_l2l, cudaEventDisableTiming));
     }
     // the fused deepest level reads only the d rows of leaves with V or X entries: the rows of
     // that level are then cleared one by one by the work lists, the levels above by a memset
@@ -770,7 +771,6 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             ++c->launches;
         }
         if (tm) tm->mark_at(13, c->near_stream);
-        CK(cudaEventRecord(c->near_join, c->near_stream));
     }
     const bool fused = S.fused;
     c->l2lp_used = fused && c->lvl_count[c->Lmax - 1] > 0;
@@ -835,6 +835,15 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         const bool l2p_tc = S.tc && F.O.l2p_img != nullptr && !c->l2p_simt;
         const bool sep_all = F.l2p_sep && !c->l2p_tc_tables;
         if (l2p_tc) CK(cudaMemsetAsync(S.err + 1, 0, sizeof(int), c->stream));
+        // with the near field on its own stream and a fused deepest level, the separable L2P of
+        // the coarser leaves (other leaves than the fused kernel's) joins the near stream once the
+        // L2L passes are done, beside the fused kernel
+        cudaStream_t sep_st = c->stream;
+        if (near_fork && fused) {
+            CK(cudaEventRecord(c->near_l2l, c->stream));
+            CK(cudaStreamWaitEvent(c->near_stream, c->near_l2l, 0));
+            sep_st = c->near_stream;
+        }
         for (int l = 2; l <= c->Lmax; ++l) {
             if (fused && l == c->Lmax) {
                 if (c->lvl_count[l - 1] > 0) {
@@ -855,7 +864,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             if (c->lvl_count[l] == 0 || c->lvl_leaf[l] == 0) continue;
             const bool tc_here = l2p_tc && (c->l2p_tc_tables || (1 << (c->D - l)) == 4);
             if (sep_all && !tc_here) {
-                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_leaf[l], out, c->stream);
+                fmm_l2p_sep_level(F, l, F.l2p_list + c->lvl_base[l], F.l2p_cnt + l, c->lvl_leaf[l], out, sep_st);
                 ++c->launches;
             } else if (F.O.e_off[l] >= 0) {
                 if (tc_here) fmm_l2p_tc_level(F, l, c->lvl_base[l], c->lvl_count[l], out, S.err + 1, c->stream);
@@ -869,6 +878,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         if (l2p_tc) CK(cudaMemcpyAsync(c->pinned + 49, S.err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         c->l2p_tc_used = l2p_tc;
     }
+    if (near_fork) CK(cudaEventRecord(c->near_join, c->near_stream));
     if (tm) tm->mark_at(8, c->stream);
     // the leaf kernel has work only where a leaf's L2P or near field is not taken by the kernels
     // above: with the Chebyshev far field, the separable L2P and the separate near field that is
@@ -1763,6 +1773,7 @@ void sph_destroy(sph_ctx *c) {
     if (c->near_fork) cudaEventDestroy(c->near_fork);
     if (c->near_join) cudaEventDestroy(c->near_join);
     if (c->near_up) cudaEventDestroy(c->near_up);
+    if (c->near_l2l) cudaEventDestroy(c->near_l2l);
     for (sph_ctx *sub : c->subs) sph_destroy(sub);
     c->subs.clear();
     if (c->sur_coarse) sph_destroy(c->sur_coarse);
