@@ -1166,7 +1166,10 @@ __global__ void __launch_bounds__(LP_T, 1) k_l2lp_tc(FmmDev F, int level, int pa
 // the leaves with V or X entries, whose own local terms the fused kernel leaves out), FP32
 // from the level's interpolation table E ([n][64], cells in local Morton order), staged in
 // shared memory once per CTA.  One warp per leaf: lane k takes the cells of local index k and
-// k + 32; every cell belongs to one leaf, so plain read-modify-writes suffice.
+// k + 32; every cell belongs to one leaf, so plain read-modify-writes suffice.  The next
+// leaf's index and expansion are fetched while the current one is evaluated, and the current
+// leaf's cell values (and mask bytes) are read before its contraction, so that a warp's
+// loads overlap its arithmetic instead of following it.
 constexpr int OWN_W = 8;
 __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, const int *__restrict__ list,
                                                         const int *__restrict__ count, float *__restrict__ out) {
@@ -1174,16 +1177,45 @@ __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, con
     const int cnt = *count;
     if ((int)blockIdx.x * OWN_W >= cnt) return;            // uniform, before the table is staged
     __shared__ float Es[TCK * 64];                          // [n][64]
-    __shared__ float sd[OWN_W][TCK];
+    __shared__ __align__(16) float sd[OWN_W][TCK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = F.O.n, np = F.O.npad;
     const float4 *E4 = reinterpret_cast<const float4 *>(F.O.e_tab + F.O.e_off[level]);
     for (int j = threadIdx.x; j < n * 16; j += blockDim.x) reinterpret_cast<float4 *>(Es)[j] = __ldg(E4 + j);
-    __syncthreads();
     const TreeDev &T = F.T;
-    for (int i = blockIdx.x * OWN_W + warp; i < cnt; i += gridDim.x * OWN_W) {
-        const int b = list[i];
-        for (int k = lane; k < np && k < TCK; k += 32) sd[warp][k] = F.dchk[(size_t)b * np + k];
+    const int stride = gridDim.x * OWN_W;
+    int i = blockIdx.x * OWN_W + warp;
+    const bool lane_d = 4 * lane < np;                      // np <= TCK = 128: one float4 per lane
+    auto fetch_d = [&](int b) {
+        return lane_d ? __ldg(reinterpret_cast<const float4 *>(F.dchk + (size_t)b * np) + lane)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    int bn = i < cnt ? list[i] : 0;
+    float4 dn = i < cnt ? fetch_d(bn) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (; i < cnt; i += stride) {
+        const int b = bn;
+        if (lane_d) reinterpret_cast<float4 *>(sd[warp])[lane] = dn;
+        if (i + stride < cnt) {
+            bn = list[i + stride];
+            dn = fetch_d(bn);
+        }
+        uint32_t ux, uy, uz;
+        demorton3(T.b_key[b], ux, uy, uz);
+        const bool full = T.b_te[b] - T.b_tb[b] == 64;
+        int64_t o[2];
+        bool keep[2];
+        float old[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t lx, ly, lz;
+            demorton3((uint32_t)(lane + 32 * h), lx, ly, lz);
+            const int x = (int)(ux * 4 + lx), y = (int)(uy * 4 + ly), z = (int)(uz * 4 + lz);
+            keep[h] = x < F.nx && y < F.ny && z < F.nz;
+            o[h] = keep[h] ? (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z) : 0;
+            keep[h] = keep[h] && (full || F.tmask[o[h]]);
+            old[h] = keep[h] ? out[o[h]] : 0.f;
+        }
         __syncwarp();
         float a0 = 0.f, a1 = 0.f;
 #pragma unroll 5
@@ -1192,18 +1224,8 @@ __global__ void __launch_bounds__(OWN_W * 32) k_l2p_own(FmmDev F, int level, con
             a0 = fmaf(Es[k * 64 + lane], dk, a0);
             a1 = fmaf(Es[k * 64 + lane + 32], dk, a1);
         }
-        uint32_t ux, uy, uz;
-        demorton3(T.b_key[b], ux, uy, uz);
-        const bool full = T.b_te[b] - T.b_tb[b] == 64;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t lx, ly, lz;
-            demorton3((uint32_t)(lane + 32 * h), lx, ly, lz);
-            const int x = (int)(ux * 4 + lx), y = (int)(uy * 4 + ly), z = (int)(uz * 4 + lz);
-            if (x >= F.nx || y >= F.ny || z >= F.nz) continue;
-            const int64_t o = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
-            if (full || F.tmask[o]) out[o] += h ? a1 : a0;
-        }
+        if (keep[0]) out[o[0]] = old[0] + a0;
+        if (keep[1]) out[o[1]] = old[1] + a1;
         __syncwarp();
     }
 }

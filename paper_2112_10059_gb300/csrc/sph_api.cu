@@ -95,6 +95,7 @@ struct sph_ctx {
     int near_per_sm = 0;              // its U-list launch: CTAs per SM (0: by the estimate in fmm_queue)
     cudaStream_t near_stream = nullptr;
     cudaEvent_t near_fork = nullptr, near_join = nullptr, near_up = nullptr, near_l2l = nullptr;
+    cudaEvent_t zero_fork = nullptr, zero_done = nullptr;   // the output's zero fill beside the tree build
     DevBuf b_nearbuf;                 // the near field's per-leaf sums (overlapped form)
     unsigned select_wait = SELECT_WAIT_LIMIT;   // look-back polls of the selection (SPH_WAIT_LIMIT_SELECT)
     int fault_alloc = 0;              // > 0: the fault_alloc-th allocation fails (SPH_FAULT=alloc[:k])
@@ -1230,12 +1231,25 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         r = select_queue(c);
         if (r) return r;
         tm.mark_at(1, c->stream);
-        if ((int64_t)c->nx * c->ny * c->nz > 0)
+        // the output's zero fill (an HBM-bound pass) runs on the side stream beside the tree build
+        // and list counts (latency-bound passes); the context's stream takes it back before the sync
+        const bool zero_side = c->near_overlap && (int64_t)c->nx * c->ny * c->nz > 0;
+        if (zero_side) {
+            if (!c->near_stream) CK(cudaStreamCreateWithFlags(&c->near_stream, cudaStreamNonBlocking));
+            if (!c->zero_fork) CK(cudaEventCreateWithFlags(&c->zero_fork, cudaEventDisableTiming));
+            if (!c->zero_done) CK(cudaEventCreateWithFlags(&c->zero_done, cudaEventDisableTiming));
+            CK(cudaEventRecord(c->zero_fork, c->stream));
+            CK(cudaStreamWaitEvent(c->near_stream, c->zero_fork, 0));
+            CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->near_stream));
+            CK(cudaEventRecord(c->zero_done, c->near_stream));
+        } else if ((int64_t)c->nx * c->ny * c->nz > 0) {
             CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)c->nx * c->ny * c->nz, c->stream));
+        }
         c->leaf_eff = c->leaf_size;
         r = resolve_near(c, out);
         if (!r) r = tree_queue(c);
         if (!r) r = lists_count_queue(c);
+        if (zero_side) CK(cudaStreamWaitEvent(c->stream, c->zero_done, 0));
         if (r) return r;
         CK(cudaStreamSynchronize(c->stream));
         r = select_read(c);
@@ -1774,6 +1788,8 @@ void sph_destroy(sph_ctx *c) {
     if (c->near_join) cudaEventDestroy(c->near_join);
     if (c->near_up) cudaEventDestroy(c->near_up);
     if (c->near_l2l) cudaEventDestroy(c->near_l2l);
+    if (c->zero_fork) cudaEventDestroy(c->zero_fork);
+    if (c->zero_done) cudaEventDestroy(c->zero_done);
     for (sph_ctx *sub : c->subs) sph_destroy(sub);
     c->subs.clear();
     if (c->sur_coarse) sph_destroy(c->sur_coarse);
