@@ -171,7 +171,8 @@ __device__ __forceinline__ void tile_issue_image(const TcSmem &s, const uint16_t
 
 __device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__restrict__ img,
                                           const float *__restrict__ state, float *__restrict__ out, int np,
-                                          int n, bool atomic, int *err, bool image_issued = false) {
+                                          int n, bool atomic, int *err, bool image_issued = false,
+                                          bool bulk = false) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!image_issued) tile_issue_image(s, img);
     gather_split(s, state, np);
@@ -201,6 +202,32 @@ __device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__res
     // warp w reads TMEM lanes 32 (w % 4) ..; with 8 warps, w and w + 4 take half the columns each
     const int q = warp & 3, i = q * 32 + lane;   // TMEM lane = operator row
     const int cw = TCN / ((int)blockDim.x / 128), cbeg = (warp >> 2) * cw;
+    if (bulk) {
+        // each column's np results staged as one contiguous row in the B tiles (free once the
+        // MMAs have completed: TCN x np FP32 = 2 B_BYTES), then added into its target row by one
+        // bulk reduction; padding rows (i >= n) add zeros
+        float *stage = reinterpret_cast<float *>(s.b_hi);
+        for (int c0 = cbeg; c0 < cbeg + cw; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            if (i < np) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) stage[(c0 + j) * np + i] = i < n ? v[j] : 0.f;
+            }
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x < TCN) {
+            const int d = s.col_dst[threadIdx.x];
+            if (d >= 0) {
+                tc::bulk_reduce_add_f32(out + (size_t)d * np, tc::smem_u32(stage + threadIdx.x * np),
+                                        (uint32_t)np * 4u);
+                tc::bulk_commit();
+                tc::bulk_wait_read_all();
+            }
+        }
+        return;
+    }
     for (int c0 = cbeg; c0 < cbeg + cw; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
@@ -262,7 +289,7 @@ __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
     tile_issue_image(s, img);
     pdl_enter();
     __syncthreads();
-    tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err, true);
+    tile_body(s, img, F.ueq, F.dchk, F.O.npad, F.O.n, true, err, true, true);
     tile_teardown(s);
 }
 

@@ -127,6 +127,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void *src, ui
                  : "memory");
 }
 
+// Bulk reduction shared -> global: dst[0..bytes/4) += src[0..bytes/4) (FP32 adds performed at
+// the L2, one request per line instead of one per warp-wide 32-float segment); both addresses
+// 16-byte aligned, bytes a multiple of 16.  Tracked by the issuing thread's bulk group.
+__device__ __forceinline__ void bulk_reduce_add_f32(float *dst, uint32_t src_saddr, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(src_saddr), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// until the source shared memory of every committed bulk operation of this thread has been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
 // 16-byte asynchronous copy global -> shared (generic proxy); src_bytes = 0 writes zeros and
 // reads nothing.  Completion is tracked per thread with commit / wait groups.
 __device__ __forceinline__ void cp_async16(uint32_t dst_saddr, const void *src, uint32_t src_bytes) {
