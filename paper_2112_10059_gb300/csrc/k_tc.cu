@@ -302,11 +302,14 @@ __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
 //   (d, e) tile i+1's pair indices are read and its rows start to stream in (cp.async);
 //   (f) thread 0 issues MMA(i) into accumulator i % 2 and, if tile i+1 needs another
 //       operator, its image into the other A buffer;
-//   (g) all threads add accumulator (i-1) % 2 into the targets (reductions),
+//   (g) all threads stage accumulator (i-1) % 2 as one FP32 row per pair, and one thread per
+//       pair adds its row into the target by a bulk reduction,
 // so the epilogue of one tile runs under the MMAs and loads of the next.  Pair metadata
 // rotates through three slots (i+1 is written while i-1 is still being scattered).
 constexpr uint32_t PIPE_RAW = TCN * TCK * 4;       // 64 rows x 128 FP32
-constexpr uint32_t PIPE_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + PIPE_RAW + 64 + 6 * TCN * 4 + 64;
+constexpr uint32_t PIPE_STG = TCN * TCK * 4;       // staged results, 64 pairs x 128 FP32
+constexpr uint32_t PIPE_SMEM = 1024 + 4 * A_BYTES + 2 * B_BYTES + PIPE_RAW + PIPE_STG + 64 + 6 * TCN * 4 + 64;
+static_assert(PIPE_SMEM <= 227 * 1024, "pipelined M2L: shared memory above the per-CTA limit");
 
 __device__ __forceinline__ void m2l_tile_range(const PairsDev &Pd, int key, int tile, int &p0, int &p1) {
     p0 = Pd.off[key] + (tile - Pd.tile_off[key]) * TCN;
@@ -325,7 +328,8 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
     uint8_t *abuf[2] = {base, base + 2 * A_BYTES};
     uint8_t *b_hi = base + 4 * A_BYTES, *b_lo = b_hi + B_BYTES;
     float *raw = reinterpret_cast<float *>(b_lo + B_BYTES);
-    uint8_t *tail = reinterpret_cast<uint8_t *>(raw) + PIPE_RAW;
+    float *stg = raw + TCN * TCK;
+    uint8_t *tail = reinterpret_cast<uint8_t *>(stg) + PIPE_STG;
     uint64_t *bar_a = reinterpret_cast<uint64_t *>(tail);       // [2]
     uint64_t *bar_mma = bar_a + 2;                              // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_a + 4);
@@ -382,16 +386,23 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
         const int ms = i % 3;
         const uint32_t col = (uint32_t)((i & 1) * TCN);
         const int row = warp * 32 + lane;
+        // the previous tile's bulk reductions have read the staged rows
+        if (tid < TCN) tc::bulk_wait_read_all();
+        __syncthreads();
 #pragma unroll
         for (int c0 = 0; c0 < TCN; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)c0, v);
-            if (row < n) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int d = mdst[ms * TCN + c0 + j];
-                    if (d >= 0) atomicAdd(F.dchk + (size_t)d * np + row, v[j]);
-                }
+            for (int j = 0; j < 16; ++j) stg[(c0 + j) * TCK + row] = row < n ? v[j] : 0.f;
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid < TCN) {
+            const int d = mdst[ms * TCN + tid];
+            if (d >= 0) {
+                tc::bulk_reduce_add_f32(F.dchk + (size_t)d * np, tc::smem_u32(stg + tid * TCK), (uint32_t)np * 4u);
+                tc::bulk_commit();
             }
         }
     };
@@ -503,6 +514,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc_pipe(FmmDev F, PairsDev Pd, c
         }
     }
     tc::cp_async_wait<0>();
+    if (tid < TCN) tc::bulk_wait_read_all();
     tc::fence_before_sync();
     __syncthreads();
     if (tid < 32) tc::tmem_dealloc(tmem, 128);
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(256) k_l2l_tc(FmmDev F, int level, int parent_
     const uint16_t *img = images + ((size_t)level * 8 + c) * (2 * A_BYTES / 2);
     tile_issue_image(s, img);
     pdl_enter();
-    tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err, true);
+    tile_body(s, img, F.dchk, F.dchk, F.O.npad, F.O.n, false, err, true, true);
     tile_teardown(s);
 }
 
@@ -578,7 +590,7 @@ __global__ void __launch_bounds__(256) k_m2m_tc(FmmDev F, int level, const int *
         tile_teardown(s);
         return;
     }
-    tile_body(s, img, F.ueq, F.ueq, F.O.npad, F.O.n, true, err, true);
+    tile_body(s, img, F.ueq, F.ueq, F.O.npad, F.O.n, true, err, true, true);
     tile_teardown(s);
 }
 
