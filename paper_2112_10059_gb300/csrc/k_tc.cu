@@ -193,9 +193,12 @@ __device__ __forceinline__ void tile_body(const TcSmem &s, const uint16_t *__res
     }
     __syncthreads();
     if (!ok_s) return;
-    if (!tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT)) {
-        atomicOr(err, 2);
-        tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);     // let the MMAs finish
+    // every thread waits for the MMAs; the outcome is made uniform over the CTA (the bulk
+    // epilogue below has barriers of its own)
+    const bool mma_ok = tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);
+    if (__syncthreads_or(!mma_ok)) {
+        if (threadIdx.x == 0) atomicOr(err, 2);
+        if (!mma_ok) tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);   // let the MMAs finish
         return;
     }
     tc::fence_after_sync();
@@ -721,27 +724,46 @@ __global__ void __launch_bounds__(128) k_l2l_tc8(FmmDev F, int level, int parent
         ok_s = ok;
     }
     __syncthreads();
-    bool done = ok_s && tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);
-    if (ok_s && !done) atomicOr(err, 8);
-    if (done) {
+    const bool mma_ok = ok_s && tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), 0, WAIT_LIMIT);
+    const bool done = !__syncthreads_or(ok_s && !mma_ok);   // uniform over the CTA
+    if (ok_s && !mma_ok) atomicOr(err, 8);
+    if (ok_s && done) {
         tc::fence_after_sync();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int i = warp * 32 + lane;
+        // each child's results staged as one FP32 row per parent in the operator buffers (free once
+        // every MMA has completed: 4 x 32 KiB, four children at a time), each row added into the
+        // child's downward state by one bulk reduction; padding rows add zeros
+        float *stg = reinterpret_cast<float *>(base);
         for (int c = 0; c < 8; ++c) {
+            if (c == 4) {
+                if (threadIdx.x < TCN) tc::bulk_wait_read_all();
+                __syncthreads();
+            }
+            float *sc = stg + (c & 3) * TCN * TCK;
 #pragma unroll
             for (int c0 = 0; c0 < TCN; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * TCN + c0), v);
-                if (i < n) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        int C = dst[c * TCN + c0 + j];
-                        // a reduction, not a load-add-store: no dependent DRAM round trip per element
-                        if (C >= 0) atomicAdd(F.dchk + (size_t)C * np + i, v[j]);
+                for (int j = 0; j < 16; ++j) sc[(c0 + j) * TCK + i] = i < n ? v[j] : 0.f;
+            }
+            if ((c & 3) == 3) {
+                tc::fence_proxy_async_smem();
+                __syncthreads();
+                if (threadIdx.x < TCN) {
+                    for (int cc = c - 3; cc <= c; ++cc) {
+                        const int C = dst[cc * TCN + threadIdx.x];
+                        if (C >= 0)
+                            tc::bulk_reduce_add_f32(F.dchk + (size_t)C * np,
+                                                    tc::smem_u32(stg + (cc & 3) * TCN * TCK + threadIdx.x * TCK),
+                                                    (uint32_t)np * 4u);
                     }
+                    tc::bulk_commit();
                 }
             }
         }
+        if (threadIdx.x < TCN) tc::bulk_wait_read_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1534,18 +1556,26 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tiles(FmmDev F, const int *__res
         }
         if (!ctl[2]) break;
         // the accumulated check potentials into the members' rows: warps w and w + 4 read TMEM
-        // lanes 32 (w % 4) .. (rows i) and half of the 128 columns each
+        // lanes 32 (w % 4) .. (rows i) and half of the 128 columns each, staged as one FP32 row
+        // per member in the operator buffers (free: every MMA and copy of the item has completed),
+        // each row added into the member's downward state by one bulk reduction
         const int q = warp & 3, i = q * 32 + lane;
+        float *stg = reinterpret_cast<float *>(base);      // [128 members][TCK]
 #pragma unroll 1
         for (int c0 = (warp >> 2) * 64; c0 < (warp >> 2) * 64 + 64; c0 += 16) {
             float r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-            if (i < n) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int d = mem[c0 + jj];
-                    if (d >= 0) atomicAdd(F.dchk + (size_t)d * np + i, r[jj]);
-                }
+            for (int jj = 0; jj < 16; ++jj) stg[(c0 + jj) * TCK + i] = i < n ? r[jj] : 0.f;
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid < TCM) {
+            const int d = mem[tid];
+            if (d >= 0) {
+                tc::bulk_reduce_add_f32(F.dchk + (size_t)d * np, tc::smem_u32(stg + tid * TCK), (uint32_t)np * 4u);
+                tc::bulk_commit();
+                tc::bulk_wait_read_all();   // before the next item's operators land in these buffers
             }
         }
     }
