@@ -196,12 +196,12 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
                      3 x 2 x 128^2);
       l2l  (tensor): 2 n^2 flops per child box with targets below level 2 (levels the separate
                      L2L kernels run: all but the deepest one when that level is fused);
-      l2lp (HBM, k_l2lp_tc): fused L2L + L2P of the deepest level: the parents' local expansions
-                  and the own local terms of the leaves that have V or X entries read (npad x 4 B
-                  each; a leaf without them has none: its expansion is its parent's, translated)
-                  + S written (4 B per target there);
-      l2p  (HBM): the other leaves' local expansions read (npad x 4 B per leaf with targets) + S
-                  written (4 B per target) -- only where such leaves exist;
+      l2lp (HBM, k_l2lp_tc): fused L2L + L2P of the deepest level, parent terms: the parents'
+                  local expansions read (npad x 4 B each) + S written (4 B per target there);
+      l2p  (HBM, k_l2p_own + the separable L2P): the own local terms of the deepest leaves that
+                  have V or X entries read (npad x 4 B each) with S read and written at their
+                  targets (8 B per target), and the other levels' leaves (npad x 4 B per leaf
+                  with targets + 4 B per target written) -- only where such leaves exist;
       near (MUFU, k_p2p): P2P pairs + M2P evaluations, 2 ex2 + 1 rsqrt each, against the measured
                   ex2 and rsqrt rates;
       select (HBM, k_brick_stats + k_select_onepass): 8 B per cell (q and |E| read once) + 4 B
@@ -244,11 +244,13 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
                      "traffic": traffic, "ms_per_launch": ms, "work_per_launch": work, "work_unit": unit_work,
                      "peak_basis": basis}
 
-    add("m2l", "k_m2l_tc" if tc else "k_m2l_pairs", True, "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
+    tiles = tc and all(x.get("m2l_tiles", 0) for x in step_stats)   # target-stationary form ran
+    add("m2l", ("k_m2l_groups + k_m2l_tiles" if tiles else "k_m2l_tc") if tc else "k_m2l_pairs", not tiles,
+        "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
         med("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
         ("measured dense BF16 %.1f TFLOP/s burst (%s)" % (tpk, peaks["source"])) if tc else
         "measured FP32 FMA %.1f TFLOP/s (%s)" % (fp32_peak, pipes["source"]),
-        traffic=NCU_TRAFFIC.get("m2l") if traffic_ok and tc else None)
+        traffic=NCU_TRAFFIC.get("m2l") if traffic_ok and tc and not tiles else None)
     if n_child > 0:
         add("l2l", "k_l2l_tc8 + k_l2l_tc" if tc else "k_l2l_gemm", False, "tensor" if tc else "alu",
             2.0 * n * n * n_child, "flop", med("ms_l2l"), tpk if tc else fp32_peak, "TFLOP/s", "as m2l")
@@ -260,12 +262,17 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
             if len(tree.get(key, ())):
                 terms[np.asarray(tree[key])[:, 0]] = True
         n_deep = int(np.sum(leaf_t & deep & terms))
+        nt_own = int(np.sum(ntb[leaf_t & deep & terms]))
         nt_deep = int(np.sum(ntb[leaf_t & deep]))
-        add("l2lp", "k_l2lp_tc", True, "hbm", 4.0 * npad * (n_par + n_deep) + 4.0 * nt_deep, "bytes", ms_lp, hbm,
+        add("l2lp", "k_l2lp_tc", True, "hbm", 4.0 * npad * n_par + 4.0 * nt_deep, "bytes", ms_lp, hbm,
             "GB/s", hbm_basis, traffic=NCU_TRAFFIC.get("l2lp") if traffic_ok else None)
-    if n_leaf_t > 0:
-        add("l2p", ("k_l2p_tc + " if tc and not fused else "") + "k_l2p_sep_small + k_l2p_sep", False, "hbm",
-            4.0 * npad * n_leaf_t + 4.0 * nt_other, "bytes", med("ms_l2p") - ms_lp, hbm, "GB/s", hbm_basis)
+    else:
+        n_deep = nt_own = 0
+    if n_leaf_t + n_deep > 0:
+        add("l2p", ("k_l2p_own + " if n_deep else "") + ("k_l2p_tc + " if tc and not fused else "") +
+            "k_l2p_sep_small + k_l2p_sep", False, "hbm",
+            4.0 * npad * (n_leaf_t + n_deep) + 4.0 * nt_other + 8.0 * nt_own, "bytes", med("ms_l2p") - ms_lp, hbm,
+            "GB/s", hbm_basis)
     add("near", "k_p2p", True, "alu", float(p2p + m2p), "kernel-evals", med("ms_near"), mufu_evals, "evals/s",
         "MUFU: 2 ex2 + 1 rsqrt per evaluation at the measured %.3g ex2/s and %.3g rsqrt/s (%s)"
         % (pipes["ex2_per_s"], pipes["rsqrt_per_s"], pipes["source"]))

@@ -44,11 +44,16 @@ def test_fused_deepest_level():
     # local terms to read; 8 targets written
     assert r["l2lp"]["work_per_launch"] == 512 + 8 * 4
     assert r["l2lp"]["achieved"] == pytest.approx(544 / 0.004e-3 / 1e9)
-    # with a V entry into leaf 2 (and one X entry into leaf 2 too) its row is read as well
+    # with a V entry into leaf 2 (and one X entry into leaf 2 too) the fused kernel's work is the
+    # same; the own-term L2P reads leaf 2's row and reads and writes S at its 4 targets, in the
+    # L2P phase time left after the fused kernel (0.006 - 0.004 ms)
     tv = dict(TREE, V=np.array([[2, 1]]), X=np.array([[2, 1]]))
     r2 = bench.rooflines(tv, _stats(True), ARGS, nt=8, ns=4, ncell=1000, peaks=PEAKS, pipes=PIPES,
                          traffic_ok=False)
-    assert r2["l2lp"]["work_per_launch"] == 2 * 512 + 8 * 4
+    assert r2["l2lp"]["work_per_launch"] == 512 + 8 * 4
+    assert r2["l2p"]["kernel"].startswith("k_l2p_own")
+    assert r2["l2p"]["work_per_launch"] == 512 + 4 * 8
+    assert r2["l2p"]["ms_per_launch"] == pytest.approx(0.002)
     assert r["l2lp"]["traffic"] is None   # ncu traffic only where it was measured on this workload
     # nothing left for the separate L2L (both level-3 boxes are fused) or L2P: no entries
     assert "l2l" not in r and "l2p" not in r
