@@ -247,8 +247,9 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
     }
     i = warp_append(act, own && leaf_t, own_cnt);
     if (own && leaf_t) own_list[i] = b;
-    // per level, the leaves with targets (the separable L2P walks these only)
-    const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr;
+    // per level, the leaves with targets (the separable L2P walks these only; the fused deepest
+    // level, whose boxes start at d_sparse_from, needs no list)
+    const bool l2p = leaf_t && l >= 2 && F.l2p_list != nullptr && !(F.d_sparse_from >= 0 && b >= F.d_sparse_from);
     i = warp_append(act, l2p, F.l2p_cnt + l);
     if (l2p) F.l2p_list[T.lvl_base[l] + i] = b;
     i = warp_append(act, need, leaf_cnt);

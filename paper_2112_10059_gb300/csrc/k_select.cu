@@ -842,8 +842,10 @@ int select_launch(const SelectArgs &A, cudaStream_t st) {
     r.e_frac = A.e_frac;
     r.e_app = A.e_app;
     int64_t n = (int64_t)A.nx * A.ny * A.nz;
-    cudaMemsetAsync(A.maxes, 0, 2 * sizeof(unsigned), st);
-    cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
+    if (!A.zeroed) {
+        cudaMemsetAsync(A.maxes, 0, 2 * sizeof(unsigned), st);
+        cudaMemsetAsync(A.totals + 2, 0, sizeof(int), st);
+    }
     int gm = (int)((n / 4 + 255) / 256);
     if (gm > 152 * 8) gm = 152 * 8;
     if (gm < 1) gm = 1;

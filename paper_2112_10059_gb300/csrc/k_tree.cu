@@ -185,8 +185,30 @@ size_t scan_tmp_ints(int n) {
 
 // out_k[i] = sum_{j<i} in_k[j]; *total_k = sum (device), for k <= 4 arrays of length n.
 // tmp: scan_tmp_ints(n) ints, 8-byte aligned; err (optional): bit 0 set if a look-back gave up.
+size_t scan_state_bytes(int k, int n) {
+    if (n <= SCAN_SMALL) return 0;
+    const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return sizeof(unsigned long long) * (size_t)k * (size_t)(ntiles + 1);
+}
+
+__global__ void __launch_bounds__(256) k_zero_set(ZeroSet Z) {
+    pdl_enter();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int s = 0; s < Z.n; ++s)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Z.words[s]; i += stride) Z.p[s][i] = 0;
+}
+
+void zero_set_launch(const ZeroSet &Z, cudaStream_t st) {
+    int64_t mx = 0;
+    for (int s = 0; s < Z.n; ++s) mx = std::max(mx, Z.words[s]);
+    if (mx <= 0) return;
+    const int grid = (int)std::min<int64_t>((mx + 255) / 256, 152 * 4);
+    launch_pdl(k_zero_set, grid, 256, 0, st, Z);
+}
+
+// state_zeroed: the look-back state (scan_state_bytes(k, n) at tmp) is already clear
 void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cudaStream_t st,
-                          unsigned wait_limit = SCAN_WAIT_LIMIT) {
+                          unsigned wait_limit = SCAN_WAIT_LIMIT, bool state_zeroed = false) {
     if (n <= 0) {
         for (int a = 0; a < k; ++a) cudaMemsetAsync(S.total[a], 0, sizeof(int), st);
         return;
@@ -197,17 +219,17 @@ void scan_exclusive_multi(const ScanSet &S, int k, int n, int *tmp, int *err, cu
     }
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     unsigned long long *state = reinterpret_cast<unsigned long long *>(tmp);
-    cudaMemsetAsync(state, 0, sizeof(unsigned long long) * k * (ntiles + 1), st);
+    if (!state_zeroed) cudaMemsetAsync(state, 0, sizeof(unsigned long long) * k * (ntiles + 1), st);
     launch_pdl(k_scan_onepass, dim3(ntiles, k), SCAN_T, 0, st, S, n, ntiles, state, err, wait_limit);
 }
 
 void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err,
-                    unsigned wait_limit) {
+                    unsigned wait_limit, bool state_zeroed) {
     ScanSet S{};
     S.in[0] = in;
     S.out[0] = out;
     S.total[0] = total;
-    scan_exclusive_multi(S, 1, n, tmp, err, st, wait_limit);
+    scan_exclusive_multi(S, 1, n, tmp, err, st, wait_limit, state_zeroed);
 }
 
 // ------------------------------------------------------------ tree build
@@ -486,7 +508,14 @@ __global__ void k_src_near(int64_t nslot, int Lmax, const uint8_t *__restrict__ 
 
 void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     const int64_t nslot = dense_off(A.Lmax + 1);
-    if (A.brick_off_t) {
+    if (A.zeroed) {
+        // the source ranges were cleared before the evaluation (zero_set_launch); the target
+        // ranges too need clearing unless the brick offsets write every slot's
+        if (!A.brick_off_t) {
+            cudaMemsetAsync(A.rtb, 0, nslot * sizeof(int), st);
+            cudaMemsetAsync(A.rte, 0, nslot * sizeof(int), st);
+        }
+    } else if (A.brick_off_t) {
         // the target ranges of every slot are written from the brick offsets
         cudaMemsetAsync(A.rsb, 0, nslot * sizeof(int), st);
         cudaMemsetAsync(A.rse, 0, nslot * sizeof(int), st);
@@ -507,10 +536,10 @@ void tree_build_launch(const TreeArgs &A, cudaStream_t st) {
     launch_pdl(k_tree_ranges, gs + gt, RANGE_T, 0, st, A.ns_dev, A.skey, A.rsb, A.rse, gs, A.nt_dev,
                A.tkey, A.rtb, A.rte, A.D, A.Lmax, A.brick_off_t, A.nbr, nslot);
     const int grid = (int)((nslot + 255) / 256);
-    cudaMemsetAsync(A.T.lvl_src, 0, 48 * sizeof(int), st);   // lvl_src, lvl_leaf and lvl_sleaf
+    if (!A.zeroed) cudaMemsetAsync(A.T.lvl_src, 0, 48 * sizeof(int), st);   // lvl_src, lvl_leaf and lvl_sleaf
     launch_pdl(k_tree_exists, grid, 256, 0, st, nslot, A.Lmax, A.D, A.S, A.rsb, A.rse, A.rtb, A.rte, A.flag);
     int *total = A.pos + nslot;
-    scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err);
+    scan_exclusive(A.flag, A.pos, (int)nslot, total, A.scan_tmp, st, A.err, SCAN_WAIT_LIMIT, A.zeroed);
     const int64_t npar = dense_off(A.Lmax);        // slots of levels 0..Lmax-1
     launch_pdl(k_tree_emit_all, grid, 256, 0, st, A.T, nslot, A.Lmax, A.D, A.S, A.flag, A.pos, A.rsb, A.rse, A.rtb,
                                           A.rte, total, A.skey, A.ns_dev, A.tkey, A.nt_dev, A.vsrc,
@@ -622,8 +651,17 @@ __device__ __forceinline__ int coarse_leaf_src(const TreeDev &T, int lq, int qx,
 // exclusive offsets; entry nkeys: the number of tiles).  The key of every tile is written by the
 // list fill, once the pair buffer has its size.
 __global__ void __launch_bounds__(1024) k_lists_layout(ListDev L, PairsDev Pd, const int *__restrict__ nboxes_dev,
-                                                       const int *__restrict__ totals) {
+                                                       const int *__restrict__ totals, ReadBack R) {
     pdl_enter();
+    // the host's read-backs, straight into its mapped buffer (every producer has completed)
+    if (R.dst) {
+        const int tid = threadIdx.x;
+        if (tid < 3) R.dst[tid] = R.sel[tid];
+        else if (tid >= 32 && tid < 64) R.dst[8 + tid - 32] = R.lvl[tid - 32];
+        else if (tid >= 64 && tid < 112) R.dst[tid] = R.lvl[tid - 32];
+        else if (tid >= 128 && tid < 133) R.dst[43 + tid - 128] = R.flag_tot[tid - 128];
+        __threadfence_system();
+    }
     __shared__ int wp[32], wt[32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
@@ -810,22 +848,24 @@ __global__ void __launch_bounds__(256) k_lists_warp(TreeDev T, ListDev L, PairsD
 
 constexpr int LISTS_WARP_GRID = 152 * 8;
 
-void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
-                        int D, int Lmax, int *scan_tmp, int *totals /* device [4] */, int *err, cudaStream_t st) {
+bool lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
+                        int D, int Lmax, int *scan_tmp, int *totals /* device [4] */, int *err, const ReadBack &R,
+                        cudaStream_t st, bool zeroed) {
     const int nboxes = cap;   // counts and offsets span every slot; the ones past the last box stay 0
     if (nboxes <= 0) {
         cudaMemsetAsync(totals, 0, 4 * sizeof(int), st);
-        return;
+        return false;
     }
-    cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
+    if (!zeroed) cudaMemsetAsync(L.nheavy, 0, sizeof(int), st);
     launch_pdl(k_lists_classify, (nboxes + 255) / 256, 256, 0, st, T, L, cap, nboxes_dev);
     launch_pdl(k_lists_warp<false>, LISTS_WARP_GRID, 256, 0, st, T, L, Pd, D);
     ScanSet S{};
     S.in[0] = L.u_cnt; S.in[1] = L.v_cnt; S.in[2] = L.w_cnt; S.in[3] = L.x_cnt;
     S.out[0] = L.u_off; S.out[1] = L.v_off; S.out[2] = L.w_off; S.out[3] = L.x_off;
     for (int a = 0; a < 4; ++a) S.total[a] = totals + a;
-    scan_exclusive_multi(S, 4, nboxes, scan_tmp, err, st);
-    launch_pdl(k_lists_layout, 1, 1024, 0, st, L, Pd, nboxes_dev, (const int *)totals);
+    scan_exclusive_multi(S, 4, nboxes, scan_tmp, err, st, SCAN_WAIT_LIMIT, zeroed);
+    launch_pdl(k_lists_layout, 1, 1024, 0, st, L, Pd, nboxes_dev, (const int *)totals, R);
+    return R.dst != nullptr;
 }
 
 void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,

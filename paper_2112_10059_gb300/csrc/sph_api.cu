@@ -127,6 +127,8 @@ struct sph_ctx {
     DevBuf o_l2pimg;             // BF16 images of the L2P tables (tensor-core L2P)
     DevBuf h_q, h_e, h_m, h_s;   // device copies for eval_sph_host
     int *pinned = nullptr;       // small pinned host buffer for read-backs
+    int *pinned_dev = nullptr;   // its device address (mapped), or null: read-backs then by copies
+    bool chain_zeroed = false;   // chain_zero cleared the counters of the selection, tree and lists queued next
     // operator cache key
     bool ops_valid = false;
     int ops_D = -1, ops_L = -1;
@@ -240,7 +242,9 @@ KParams make_kp(const sph_ctx *c) {
 
 // Selection into Morton-ordered point arrays; reads back (Ns, Nt).
 // ------------------------------------------------------------------ selection
-int select_queue(sph_ctx *c) {
+// copy: read the totals back by a copy (else the list layout kernel writes them into the mapped
+// read-back buffer before the host's sync)
+int select_queue(sph_ctx *c, bool copy = true) {
     const int D = c->D;
     const int b = std::min(4, D);
     const int64_t nbr = 1ll << (3 * (D - b));
@@ -270,11 +274,12 @@ int select_queue(sph_ctx *c) {
     A.trg_key = P<uint32_t>(c->b_tkey);   // targets' cells follow from their keys: no packed copy
     A.tmask = P<uint8_t>(c->b_tmask);
     A.bstat = P<float>(c->b_bstat);
+    A.zeroed = c->chain_zeroed;
     const int sr = select_launch(A, c->stream);
     if (sr < 0) CK(cudaGetLastError());
     c->brick_offsets = sr == 1 && b == 4;
     c->launches += A.launched;
-    CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (copy) CK(cudaMemcpyAsync(c->pinned, A.totals, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SPH_OK;
 }
 
@@ -355,12 +360,24 @@ PairsDev pairs_dev(sph_ctx *c) {
 // [96..96+Lmax] leaves with sources per level.
 // The tree and the list counts read the selection's point counts and the tree's box count
 // from device memory, so selection, tree and list counting need one host sync in all.
+// deepest level: leaves of the effective leaf size hold at most 8^k cells
+int lmax_of(const sph_ctx *c) {
+    int k = 0;
+    while (k < 4 && (1ll << (3 * (k + 1))) <= c->leaf_eff) ++k;
+    return std::max(0, c->D - k);
+}
+
+// The scan scratch: the tree scan's region first, then the list scan's (separate look-back
+// states, so that both can be cleared before the evaluation)
+int64_t scan_list_off(int64_t dense_total) { return (int64_t)scan_tmp_ints((int)(4 * (dense_total + 1))); }
+size_t scan_scratch_bytes(int64_t dense_total) {
+    return (size_t)(scan_list_off(dense_total) + (int64_t)scan_tmp_ints((int)(dense_total + 1))) * sizeof(int) + 64;
+}
+
 int tree_queue(sph_ctx *c) {
     const int D = c->D;
     int S = c->leaf_eff;
-    int k = 0;
-    while (k < 4 && (1ll << (3 * (k + 1))) <= S) ++k;
-    const int Lmax = std::max(0, D - k);
+    const int Lmax = lmax_of(c);
     c->Lmax = Lmax;
     const int64_t dense_total = dense_off(Lmax + 1);
     ENS(c->b_boxat, dense_total * sizeof(int));
@@ -368,7 +385,7 @@ int tree_queue(sph_ctx *c) {
     ENS(c->b_pos, (dense_total + 1) * sizeof(int));
     ENS(c->b_rng, 4 * dense_total * sizeof(int));
     ENS(c->b_near, 3 * dense_total + 16);
-    ENS(c->b_scan, scan_tmp_ints((int)(4 * (dense_total + 1))) * sizeof(int) + 64);
+    ENS(c->b_scan, scan_scratch_bytes(dense_total));
     ENS(c->b_lvl, 80 * sizeof(int));
     const int64_t cap = dense_total;   // every slot of every level could hold a box
     ENS(c->b_level, cap * sizeof(int));
@@ -393,14 +410,17 @@ int tree_queue(sph_ctx *c) {
         A.nbr = 1 << (3 * (D - 4));
         A.brick_off_t = P<int>(c->b_off) + A.nbr;       // off_t follows off_s (select_queue)
     }
-    CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
+    A.zeroed = c->chain_zeroed;
+    if (!A.zeroed) CK(cudaMemsetAsync(A.err, 0, sizeof(int), c->stream));
     tree_build_launch(A, c->stream);
     // ranges (sources and targets in one launch), existence flags, scan, emit (with the source
     // occupancy), the occupancy's dilation
     c->launches += 1 + 3 + (Lmax >= 1 ? 1 : 0);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 48 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (!c->pinned_dev) {   // else written by the list layout kernel (lists_count_queue)
+        CK(cudaMemcpyAsync(c->pinned + 8, A.T.lvl_base, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->pinned + 64, A.T.lvl_src, 48 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
     return SPH_OK;
 }
 
@@ -414,16 +434,62 @@ int lists_count_queue(sph_ctx *c) {
     ENS(c->b_heavy, (size_t)cap * sizeof(int));
     const int nkeys = (Lmax + 1) * NSLOT;
     ENS(c->b_pkeys, (5 * (size_t)nkeys + 10) * sizeof(int));
-    CK(cudaMemsetAsync(c->b_pkeys.p, 0, (5 * (size_t)nkeys + 10) * sizeof(int), c->stream));
-    ENS(c->b_scan, scan_tmp_ints(cap + 1) * sizeof(int) + 64);
+    if (!c->chain_zeroed) CK(cudaMemsetAsync(c->b_pkeys.p, 0, (5 * (size_t)nkeys + 10) * sizeof(int), c->stream));
+    ENS(c->b_scan, scan_scratch_bytes(cap));
     ListDev L = list_dev(c);
     int *ltot = P<int>(c->b_tot) + 4;
     const int *nboxes_dev = P<int>(c->b_pos) + dense_off(Lmax + 1);   // the tree scan's total
-    lists_count_launch(tree_dev(c), L, pairs_dev(c), c->list_cap, nboxes_dev, c->D, Lmax, P<int>(c->b_scan), ltot,
-                       ltot - 1, c->stream);
+    // the layout kernel writes the host's read-backs (selection totals, scan flag, list totals,
+    // level arrays) into the mapped buffer
+    ReadBack R{};
+    R.dst = c->pinned_dev;
+    R.sel = P<int>(c->b_tot);
+    R.flag_tot = ltot - 1;
+    R.lvl = tree_dev(c).lvl_base;
+    const bool rb = lists_count_launch(tree_dev(c), L, pairs_dev(c), c->list_cap, nboxes_dev, c->D, Lmax,
+                                       P<int>(c->b_scan) + scan_list_off(cap), ltot, ltot - 1, R, c->stream,
+                                       c->chain_zeroed);
+    c->chain_zeroed = false;
     c->launches += 4;   // classify, count, list scan, lists / pairs layout
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (!rb) {
+        CK(cudaMemcpyAsync(c->pinned, R.sel, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->pinned + 8, R.lvl, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->pinned + 64, R.lvl + 32, 48 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->pinned + 43, ltot - 1, 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return SPH_OK;
+}
+
+// Before the deferred selection, tree build and list counts: one kernel clears every counter
+// and look-back state they need cleared (the selection's maxima and look-back flag, the tree
+// scans' flag, the per-level source and leaf counts, the slots' source ranges, the heavy-box
+// count, the V-pair key counts and both scans' states) instead of a clearing copy before each
+// user, which would stand between two kernels of the launch sequence.
+int chain_zero(sph_ctx *c) {
+    c->chain_zeroed = false;
+    const int Lmax = lmax_of(c);
+    const int64_t dense_total = dense_off(Lmax + 1);
+    const int nkeys = (Lmax + 1) * NSLOT;
+    ENS(c->b_maxes, 2 * sizeof(unsigned));
+    ENS(c->b_tot, 16 * sizeof(int));
+    ENS(c->b_rng, 4 * dense_total * sizeof(int));
+    ENS(c->b_scan, scan_scratch_bytes(dense_total));
+    ENS(c->b_lvl, 80 * sizeof(int));
+    ENS(c->b_pkeys, (5 * (size_t)nkeys + 10) * sizeof(int));
+    ZeroSet Z;
+    const bool ok =
+        Z.add(P<int>(c->b_maxes), 2) && Z.add(P<int>(c->b_tot) + 2, 2) && Z.add(P<int>(c->b_tot) + 8, 1) &&
+        Z.add(P<int>(c->b_rng), 2 * dense_total) && Z.add(P<int>(c->b_lvl) + 32, 48) &&
+        Z.add(P<int>(c->b_scan), (int64_t)(scan_state_bytes(1, (int)dense_total) / sizeof(int))) &&
+        Z.add(P<int>(c->b_scan) + scan_list_off(dense_total),
+              (int64_t)(scan_state_bytes(4, (int)dense_total) / sizeof(int))) &&
+        Z.add(P<int>(c->b_pkeys), 5 * (int64_t)nkeys + 10);
+    if (!ok) return SPH_OK;   // each user then clears its own
+    zero_set_launch(Z, c->stream);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    c->chain_zeroed = true;
     return SPH_OK;
 }
 
@@ -1223,13 +1289,20 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     PhaseTimer tm;
     tm.start(stats != nullptr, c->stream);
     c->launches = 0;
+    c->chain_zeroed = false;
     c->m2l_form = -1;                 // the density rule unless the autotuner picks the form below
     int r = check_previous_tc(c);
     if (r) return r;
     if (c->defer_sync && c->leaf_size != 0 && c->near_mode != SPH_NEAR_AUTO) {
         // fixed leaf size: selection, tree and list counts queued back to back, one sync
-        r = select_queue(c);
+        c->leaf_eff = c->leaf_size;
+        r = chain_zero(c);
         if (r) return r;
+        r = select_queue(c, false);
+        if (r) {
+            c->chain_zeroed = false;
+            return r;
+        }
         tm.mark_at(1, c->stream);
         // the output's zero fill (an HBM-bound pass) runs on the side stream beside the tree build
         // and list counts (latency-bound passes); the context's stream takes it back before the sync
@@ -1249,6 +1322,7 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
         r = resolve_near(c, out);
         if (!r) r = tree_queue(c);
         if (!r) r = lists_count_queue(c);
+        c->chain_zeroed = false;   // consumed (or abandoned on an error) by the three above
         if (zero_side) CK(cudaStreamWaitEvent(c->stream, c->zero_done, 0));
         if (r) return r;
         CK(cudaStreamSynchronize(c->stream));
@@ -1315,6 +1389,25 @@ int run_fmm(sph_ctx *c, float *out, sph_stats *stats) {
     return SPH_OK;
 }
 
+// The context's read-back buffer: 128 ints of pinned host memory, mapped into the device's
+// address space so that the last kernel before a host sync can write what the host reads
+// there (no copy operations in the stream); without a device address the read-backs are copies.
+bool alloc_pinned(sph_ctx *c) {
+    if (cudaHostAlloc(reinterpret_cast<void **>(&c->pinned), 128 * sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        c->pinned = nullptr;
+        return false;
+    }
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, c->pinned, 0) == cudaSuccess) {
+        c->pinned_dev = static_cast<int *>(d);
+    } else {
+        cudaGetLastError();
+        c->pinned_dev = nullptr;
+    }
+    return true;
+}
+
 // A sub-context of `parent`: its own stream (batch slots) or the parent's (shared_stream).
 sph_ctx *make_sub(sph_ctx *parent, bool shared_stream = false) {
     sph_ctx *c = new (std::nothrow) sph_ctx();
@@ -1331,7 +1424,7 @@ sph_ctx *make_sub(sph_ctx *parent, bool shared_stream = false) {
         }
         c->own_stream = true;
     }
-    if (cudaMallocHost(&c->pinned, 128 * sizeof(int)) != cudaSuccess) {
+    if (!alloc_pinned(c)) {
         cudaGetLastError();
         if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
@@ -1734,7 +1827,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (!c) return SPH_ENOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->pinned, 128 * sizeof(int)) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess || !alloc_pinned(c)) {
         cudaGetLastError();
         delete c;
         return SPH_ECUDA;

@@ -41,6 +41,7 @@ struct SelectArgs {
     // nullptr: the maxima alone (k_grid_max) and every brick read
     float *bstat = nullptr;
     mutable int launched = 0;        // out: kernels select_launch queued
+    bool zeroed = false;             // maxes[0..2) and totals[2] were cleared by zero_set_launch
 };
 // 1: queued, and off_t holds every brick's exclusive target offset (count / scan / emit form);
 // 0: queued without per-brick offsets; -1: a launch failed
@@ -97,11 +98,36 @@ struct TreeArgs {
     // the target keys
     const int *brick_off_t = nullptr;
     int nbr = 0;
+    // the point ranges, the per-level source / leaf counts and the scan's state were cleared by
+    // zero_set_launch before the evaluation (no clearing copies in the launch sequence)
+    bool zeroed = false;
 };
 void tree_build_launch(const TreeArgs &A, cudaStream_t st);
+
+// Up to 12 device ranges of 4-byte words cleared by one launch: the counters and look-back scan
+// states that selection, tree build and list counts need cleared, in one kernel before the
+// selection's first one instead of one clearing copy before each user.
+struct ZeroSet {
+    static constexpr int CAP = 12;
+    int n = 0;
+    int *p[CAP] = {};
+    int64_t words[CAP] = {};
+    bool add(int *q, int64_t w) {
+        if (w <= 0) return true;
+        if (!q || n >= CAP) return false;
+        p[n] = q;
+        words[n] = w;
+        ++n;
+        return true;
+    }
+};
+void zero_set_launch(const ZeroSet &Z, cudaStream_t st);
+// bytes of state a look-back scan of k arrays of length n clears before it runs (0: the
+// single-CTA scan, which keeps no state)
+size_t scan_state_bytes(int k, int n);
 size_t scan_tmp_ints(int n);
 void scan_exclusive(const int *in, int *out, int n, int *total, int *tmp, cudaStream_t st, int *err = nullptr,
-                    unsigned wait_limit = SCAN_WAIT_LIMIT);
+                    unsigned wait_limit = SCAN_WAIT_LIMIT, bool state_zeroed = false);
 
 struct ListDev {
     int *u_cnt, *v_cnt, *w_cnt, *x_cnt;     // [nboxes]
@@ -116,8 +142,20 @@ struct PairsDev;
 // fill pass (the grouping the M2L tiles read); `Pd` per-key arrays zeroed before the count.
 // cap: slots of every level (upper bound of the box count, the length of the list count and
 // offset arrays); nboxes_dev: the tree's box count on the device
-void lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
-                        int D, int Lmax, int *scan_tmp, int *totals, int *err, cudaStream_t st);
+// Values the host reads after its sync, written by the list layout kernel (the last kernel
+// before that sync) into a mapped pinned buffer `dst` (device address; null: not written):
+// dst[0..3) = sel[0..3) (selection totals), dst[8..40) = lvl[0..32) (level first boxes and
+// counts), dst[64..112) = lvl[32..80) (boxes with sources, leaves with targets, leaves with
+// sources per level), dst[43..48) = flag_tot[0..5) (scan flag, the four list totals).
+struct ReadBack {
+    int *dst = nullptr;
+    const int *sel = nullptr, *lvl = nullptr, *flag_tot = nullptr;
+};
+// Returns true when the layout kernel was queued with R.dst (the read-backs are then in flight).
+// zeroed: the heavy-box count and the scan's state were cleared by zero_set_launch
+bool lists_count_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int cap, const int *nboxes_dev,
+                        int D, int Lmax, int *scan_tmp, int *totals, int *err, const ReadBack &R, cudaStream_t st,
+                        bool zeroed = false);
 void lists_fill_launch(const TreeDev &T, const ListDev &L, const PairsDev &Pd, int nboxes, int D, int Lmax,
                        const int *totals, cudaStream_t st);
 
