@@ -1128,8 +1128,13 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
 // near field's order); every target belongs to one leaf, so plain read-modify-writes suffice
 __global__ void __launch_bounds__(256) k_near_add(FmmDev F, const int *__restrict__ list,
                                                   const int *__restrict__ count, int stride,
-                                                  float *__restrict__ out) {
+                                                  float *__restrict__ out, const int *__restrict__ flags,
+                                                  int *flags_host) {
     pdl_enter();
+    if (flags_host && blockIdx.x == 0 && threadIdx.x < 2) {
+        flags_host[threadIdx.x] = flags[threadIdx.x];
+        __threadfence_system();
+    }
     int cnt = 0;
 #pragma unroll
     for (int c = 0; c < P2P_CLASSES; ++c) cnt += count[c];
@@ -1188,10 +1193,11 @@ void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cn
 }
 
 void fmm_near_add(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-                  cudaStream_t st) {
+                  cudaStream_t st,
+                  const int *flags, int *flags_host) {
     if (nboxes <= 0 || !F.near_buf) return;
     const int grid = std::max(1, std::min((nboxes + 7) / 8, 152 * 8));
-    launch_pdl(k_near_add, grid, 256, 0, st, F, p2p_list, p2p_cnt, stride, out);
+    launch_pdl(k_near_add, grid, 256, 0, st, F, p2p_list, p2p_cnt, stride, out, flags, flags_host);
 }
 
 void fmm_leaf(const FmmDev &F, int nboxes, const int *list, const int *count, float *out_dense, cudaStream_t st) {

@@ -787,9 +787,20 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     const int nb = c->nboxes;
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     const size_t db = F.d_sparse_from >= 0 ? (size_t)F.d_sparse_from * c->npad() * sizeof(float) : vb;
-    if (db > 0) CK(cudaMemsetAsync(c->b_dchk.p, 0, db, c->stream));
-    CK(cudaMemsetAsync(S.w_cnt, 0, 64 * sizeof(int), c->stream));
-    if (S.tc) CK(cudaMemsetAsync(S.err, 0, sizeof(int), c->stream));   // M2M, M2L and L2L tiles' flags
+    // one clearing kernel: the downward states (rows the M2L, P2L and L2L add into), the work
+    // list counters, the tensor-core tiles' flags ([0] M2M / M2L / L2L, [1] L2P) and the near
+    // field's skip count
+    {
+        ZeroSet Z;
+        const bool ok = Z.add(P<int>(c->b_dchk), (int64_t)(db / sizeof(int))) && Z.add(S.w_cnt, 64) &&
+                        Z.add(S.err, 2) && Z.add(reinterpret_cast<int *>(F.skip_count), 2);
+        if (!ok) return fail(c, SPH_EINVAL, "internal: clearing set overflow");
+        zero_set_launch(Z, c->stream);
+        ++c->launches;
+    }
+    // the tiles' flags reach the host through the near-field add (the last kernel), written into
+    // the mapped read-back buffer, where that kernel runs; else by copies
+    const bool err_mapped = c->pinned_dev && F.near_buf && nb > 0;
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 56, std::max(nb, 1),
                    S.w_own, S.w_cnt + 62, c->stream);
     c->launches += nb > 0;
@@ -801,7 +812,6 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         // added into the output
         CK(cudaEventRecord(c->near_fork, c->stream));
         CK(cudaStreamWaitEvent(c->near_stream, c->near_fork, 0));
-        CK(cudaMemsetAsync(F.skip_count, 0, sizeof(unsigned long long), c->near_stream));
         if (F.gtab) {
             fmm_near_table(F, const_cast<float *>(F.gtab), c->near_stream);
             ++c->launches;
@@ -891,7 +901,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
             else fmm_l2l_gemm_level(F, l, c->lvl_base[l - 1], c->lvl_count[l - 1], c->stream);
             c->launches += c->lvl_count[l - 1] > 0;
         }
-        if (S.tc) CK(cudaMemcpyAsync(c->pinned + 48, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (S.tc && !err_mapped) CK(cudaMemcpyAsync(c->pinned + 48, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         c->tc_used = S.tc;
     }
     if (tm) tm->mark_at(7, c->stream);
@@ -901,7 +911,6 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         // SPH_L2P_TC=1: tables on the tensor cores at every level; SPH_L2P_SIMT=1: FP32 tables.
         const bool l2p_tc = S.tc && F.O.l2p_img != nullptr && !c->l2p_simt;
         const bool sep_all = F.l2p_sep && !c->l2p_tc_tables;
-        if (l2p_tc) CK(cudaMemsetAsync(S.err + 1, 0, sizeof(int), c->stream));
         // with the near field on its own stream and a fused deepest level, the separable L2P of
         // the coarser leaves (other leaves than the fused kernel's) joins the near stream once the
         // L2L passes are done, beside the fused kernel
@@ -942,7 +951,8 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                 ++c->launches;
             }
         }
-        if (l2p_tc) CK(cudaMemcpyAsync(c->pinned + 49, S.err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (l2p_tc && !err_mapped)
+            CK(cudaMemcpyAsync(c->pinned + 49, S.err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         c->l2p_tc_used = l2p_tc;
     }
     if (near_fork) CK(cudaEventRecord(c->near_join, c->near_stream));
@@ -958,7 +968,8 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     if (F.near_buf) {
         if (nb > 0) {
             CK(cudaStreamWaitEvent(c->stream, c->near_join, 0));
-            fmm_near_add(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->stream);
+            fmm_near_add(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->stream,
+                         err_mapped ? S.err : nullptr, err_mapped ? c->pinned_dev + 48 : nullptr);
             ++c->launches;
         }
     } else if (F.p2p_separate) {

@@ -289,8 +289,11 @@ void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, in
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
              cudaStream_t st, int pass_lo = 0, int pass_hi = 2, int per_sm = 16);
 // out[cell of t] += F.near_buf[slot of t] for every target of every leaf of those lists
+// flags / flags_host (optional): flags[0..2) copied to the mapped host address flags_host once
+// every earlier kernel of the stream has completed
 void fmm_near_add(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-                  cudaStream_t st);
+                  cudaStream_t st,
+                  const int *flags = nullptr, int *flags_host = nullptr);
 void fmm_m2l_level(const FmmDev &F, int level, int box_begin, int box_count, int m2l_prec, cudaStream_t st);
 void fmm_p2l_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
 void fmm_down_level(const FmmDev &F, int level, int box_begin, int box_count, cudaStream_t st);
