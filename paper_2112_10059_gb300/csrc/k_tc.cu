@@ -296,6 +296,126 @@ __global__ void __launch_bounds__(256) k_m2l_tc(FmmDev F, PairsDev Pd, const uin
     tile_teardown(s);
 }
 
+// ---------------------------------------------------------------- M2L, persistent tile loop
+// Two CTAs per SM, each taking tile blockIdx.x first and then the tiles gridDim.x + ticket (a
+// counter, cleared before the passes, so that CTAs that start late beside other kernels take
+// fewer), with the tensor memory and barriers set up once.  Per tile: (1) the previous tile's bulk reductions
+// have read the staged rows (the B tiles), (2) gather and split the 64 source rows, (3) MMAs
+// once the operator image has landed, (4) the next tile's pair indices while they run, (5) the
+// MMAs complete, (6) the next tile's operator image streams into the A tile, (7) the results
+// are staged in the B tiles and added into the targets by bulk reductions that complete under
+// the next tile's steps (1)-(2).  The same sums as k_m2l_tc.
+__global__ void __launch_bounds__(256) k_m2l_tc_loop(FmmDev F, PairsDev Pd, const uint16_t *__restrict__ images,
+                                                     int *err, int *ticket) {
+    // prologue (the V pairs, their tiles and the operator images were written before the passes)
+    extern __shared__ uint8_t smem_raw[];
+    const int ntile = Pd.tile_off[Pd.nkeys];
+    if ((int)blockIdx.x >= ntile) return;                // uniform, before any allocation
+    TcSmem s = carve(smem_raw);
+    __shared__ int s_src[2][TCN], s_dst[2][TCN];
+    __shared__ int s_ok, s_next;
+    const int tid = threadIdx.x;
+    // pair indices of `tile` into slot `slot` (threads < TCN; each finds the tile's key itself)
+    auto tile_meta = [&](int tile, int slot) {
+        const int key = Pd.tile_key[tile];
+        const int p0 = Pd.off[key] + (tile - Pd.tile_off[key]) * TCN;
+        const int p1 = min(p0 + TCN, Pd.off[key + 1]);
+        const int q = p0 + tid;
+        s_src[slot][tid] = q < p1 ? Pd.src[q] : -1;
+        s_dst[slot][tid] = q < p1 ? Pd.trg[q] : -1;
+        return key;
+    };
+    auto issue_image = [&](int key) {
+        const uint16_t *img = images + (size_t)key * (2 * A_BYTES / 2);
+        tc::mbar_expect_tx(tc::smem_u32(s.bar_a), 2 * A_BYTES);
+        tc::bulk_g2s(tc::smem_u32(s.a_hi), img, A_BYTES, tc::smem_u32(s.bar_a));
+        tc::bulk_g2s(tc::smem_u32(s.a_lo), img + A_BYTES / 2, A_BYTES, tc::smem_u32(s.bar_a));
+    };
+    tile_setup(s);
+    if (tid < TCN) {
+        const int key0 = tile_meta(blockIdx.x, 0);
+        if (tid == 0) issue_image(key0);
+    }
+    pdl_enter();
+    const uint32_t tmem = *s.tmem_base;
+    const int np = F.O.npad, n = F.O.n;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, i = q * 32 + lane;           // TMEM lane = operator row
+    const int cbeg = (warp >> 2) * (TCN / 2);
+    float *stage = reinterpret_cast<float *>(s.b_hi);    // TCN rows of TCK FP32 (the two B tiles)
+    int it = 0, flag = 0;
+    bool image_pending = true;                            // an image copy not yet waited for
+    for (int tile = blockIdx.x; tile < ntile; ++it) {
+        const int slot = it & 1;
+        if (tid == 0) s_next = (int)gridDim.x + atomicAdd(ticket, 1);
+        // (1) the previous tile's staged rows have been read (and slot's indices are visible)
+        if (tid < TCN) tc::bulk_wait_read_all();
+        __syncthreads();
+        const int nt = s_next;
+        // (2) the source rows into the B tiles
+        gather_rows_split(s.b_hi, s.b_lo, s_src[slot], TCN, F.ueq, np);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        // (3) MMAs once the image has landed
+        if (tid == 0) {
+            int ok = tc::mbar_wait_bounded(tc::smem_u32(s.bar_a), it & 1, WAIT_LIMIT);
+            if (ok) {
+                image_pending = false;
+                tc::fence_after_sync();
+                issue_mmas(s, tmem);
+            }
+            s_ok = ok;
+        }
+        // (4) the next tile's pair indices while the MMAs run
+        int nkey = 0;
+        if (nt < ntile && tid < TCN) nkey = tile_meta(nt, slot ^ 1);
+        __syncthreads();
+        if (!s_ok) {
+            flag = 1;
+            break;
+        }
+        // (5) the MMAs complete (uniform outcome)
+        const bool mma_ok = tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), it & 1, WAIT_LIMIT);
+        if (__syncthreads_or(!mma_ok)) {
+            flag = 2;
+            if (!mma_ok) tc::mbar_wait_bounded(tc::smem_u32(s.bar_mma), it & 1, WAIT_LIMIT);
+            break;
+        }
+        tc::fence_after_sync();
+        // (6) the next tile's image into the A tile (its readers, the MMAs, have completed)
+        if (tid == 0 && nt < ntile) {
+            issue_image(nkey);
+            image_pending = true;
+        }
+        // (7) results staged as one FP32 row per pair in the B tiles, then one bulk reduction per
+        // pair into its target's row (padding rows add zeros)
+        for (int c0 = cbeg; c0 < cbeg + TCN / 2; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) stage[(c0 + j) * TCK + i] = i < n ? v[j] : 0.f;
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();                         // the TMEM reads before the next tile's MMAs
+        __syncthreads();
+        if (tid < TCN) {
+            const int d = s_dst[slot][tid];
+            if (d >= 0) {
+                tc::bulk_reduce_add_f32(F.dchk + (size_t)d * np, tc::smem_u32(stage + tid * TCK), (uint32_t)np * 4u);
+                tc::bulk_commit();
+            }
+        }
+        tile = nt;
+    }
+    if (tid == 0 && flag) {
+        atomicOr(err, flag);
+        // an image copy in flight lands before this CTA's memory is released
+        if (image_pending) tc::mbar_wait_bounded(tc::smem_u32(s.bar_a), it & 1, WAIT_LIMIT);
+    }
+    if (tid < TCN) tc::bulk_wait_read_all();
+    tile_teardown(s);
+}
+
 // ---------------------------------------------------------------- M2L, persistent and pipelined
 // One CTA per SM walks a contiguous range of tiles (tiles of one (level, offset) group are
 // consecutive, so the operator image is reused while the group lasts).  Per tile i:
@@ -1330,6 +1450,7 @@ void tc_init_attributes() {
     static bool done = false;
     if (done) return;
     cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaFuncSetAttribute(k_m2l_tc_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_m2m_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     cudaFuncSetAttribute(k_l2l_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L8_SMEM);
@@ -1613,11 +1734,16 @@ void fmm_m2l_tiles(const FmmDev &F, const MtLevels &ML, int *groups, int *ngroup
 }
 
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
-                bool pipelined) {
+                bool pipelined, bool tile_loop, int *ticket) {
     if (nV <= 0) return;
     tc_init_attributes();
     if (pipelined) {
         launch_pdl(k_m2l_tc_pipe, 152, 128, PIPE_SMEM, st, F, Pd, images, err);
+        return;
+    }
+    if (tile_loop && ticket) {
+        const int upper = (nV + TCN - 1) / TCN + Pd.nkeys;   // tiles at most
+        launch_pdl(k_m2l_tc_loop, std::min(upper, 2 * sm_count()), 256, TC_SMEM, st, F, Pd, images, err, ticket);
         return;
     }
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;

@@ -73,7 +73,7 @@ def _pdl_launched(srcs):
 # names of what the kernels of the passes write (a prologue must not name them)
 WRITTEN = ["dchk", "ueq", "out", "count", "cnt", "list", "near_buf", "skip_count", "maxes", "totals", "state",
            "ticket", "src_key", "src_pc", "src_q", "trg_key", "trg_pc", "tmask", "bstat", "w_src", "err_flag"]
-PROLOGUE_KERNELS = {"k_m2l_tc", "k_l2l_tc", "k_m2m_tc", "k_l2l_tc8", "k_l2lp_tc"}
+PROLOGUE_KERNELS = {"k_m2l_tc", "k_m2l_tc_loop", "k_l2l_tc", "k_m2m_tc", "k_l2l_tc8", "k_l2lp_tc"}
 
 
 def test_every_pdl_kernel_waits_first():
