@@ -173,7 +173,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch from one ncu capture each of the 256^3 adaptive workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of the kernel); valid for that workload and the
 # kernels as profiled (removed once a kernel has changed since).
-NCU_TRAFFIC = {"m2l": (97.756 + 3.199) * 1e6, "l2lp": (26.381 + 9.930) * 1e6}
+NCU_TRAFFIC = {"l2lp": (26.381 + 9.930) * 1e6}
 
 
 def pipe_peaks(sph, dev, stream, f_mhz_nominal=2070.0):
@@ -245,7 +245,9 @@ def rooflines(tree, step_stats, args, nt, ns, ncell, peaks, pipes, traffic_ok=Tr
                      "peak_basis": basis}
 
     tiles = tc and all(x.get("m2l_tiles", 0) for x in step_stats)   # target-stationary form ran
-    add("m2l", ("k_m2l_groups + k_m2l_tiles" if tiles else "k_m2l_tc") if tc else "k_m2l_pairs", not tiles,
+    # pair tiles: the persistent tile loop unless SPH_M2L_LOOP=0 (one CTA per tile)
+    pairs_k = "k_m2l_tc_loop" if os.environ.get("SPH_M2L_LOOP", "1") != "0" else "k_m2l_tc"
+    add("m2l", ("k_m2l_groups + k_m2l_tiles" if tiles else pairs_k) if tc else "k_m2l_pairs", not tiles,
         "tensor" if tc else "alu", 2.0 * n * n * nV, "flop",
         med("ms_m2l"), tpk if tc else fp32_peak, "TFLOP/s",
         ("measured dense BF16 %.1f TFLOP/s burst (%s)" % (tpk, peaks["source"])) if tc else
