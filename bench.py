@@ -173,7 +173,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch from one ncu capture each of the 256^3 adaptive workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of the kernel); valid for that workload and the
 # kernels as profiled (removed once a kernel has changed since).
-NCU_TRAFFIC = {"l2lp": (26.381 + 9.930) * 1e6}
+NCU_TRAFFIC = {"m2l": (97.748 + 2.976) * 1e6, "l2lp": (26.381 + 9.930) * 1e6}
 
 
 def pipe_peaks(sph, dev, stream, f_mhz_nominal=2070.0):
