@@ -211,7 +211,7 @@ __device__ __forceinline__ int warp_append(unsigned act, bool pred, int *counter
 __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, int *__restrict__ src_cnt,
                              int *__restrict__ leaf_list, int *__restrict__ leaf_cnt, int *__restrict__ p2p_list,
                              int *__restrict__ p2p_cnt, int p2p_stride, int *__restrict__ own_list,
-                             int *__restrict__ own_cnt) {
+                             int *__restrict__ own_cnt, int *__restrict__ w_list, int *__restrict__ w_cnt) {
     pdl_enter();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nboxes) return;
@@ -220,11 +220,11 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
     const int l = T.b_level[b];
     const bool has_src = l >= 2 && T.b_se[b] > T.b_sb[b];
     const bool leaf_t = T.b_leaf[b] && T.b_te[b] > T.b_tb[b];
-    bool need = false, p2p = false;
+    bool need = false, p2p = false, has_w = false;
     if (leaf_t) {
         bool l2p_done = F.leaf_l2p_done && F.O.method == FAR_CHEB && l >= 2 && (F.O.e_off[l] >= 0 || F.l2p_sep);
         bool has_u = F.L.u_off[b] != F.L.u_off[b + 1];
-        bool has_w = F.L.w_off[b] != F.L.w_off[b + 1];
+        has_w = F.L.w_off[b] != F.L.w_off[b + 1];
         // the separate near-field kernel takes U and (Chebyshev far field) W lists
         bool w_sep = F.p2p_separate && F.O.method == FAR_CHEB;
         need = !l2p_done || ((has_u || has_w) && !F.p2p_separate) || (has_w && !w_sep);
@@ -269,18 +269,28 @@ __global__ void k_work_lists(FmmDev F, int nboxes, int *__restrict__ src_list, i
         cls = 0;
         while (cls < P2P_CLASSES - 1 && w < (P2P_CLASS0 >> cls)) ++cls;
     }
+    int my_idx = 0;
     for (int c = 0; c < P2P_CLASSES; ++c) {
         const bool in = p2p && cls == c;
         i = warp_append(act, in, p2p_cnt + c);
-        if (in) p2p_list[(size_t)c * p2p_stride + i] = b;
+        if (in) {
+            p2p_list[(size_t)c * p2p_stride + i] = b;
+            my_idx = i;
+        }
+    }
+    if (w_list) {
+        const bool wl = p2p && has_w && F.O.method == FAR_CHEB;
+        i = warp_append(act, wl, w_cnt);
+        if (wl) w_list[i] = cls * p2p_stride + my_idx;   // the leaf's slot in p2p_list
     }
 }
 
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st) {
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st,
+                    int *w_list, int *w_cnt) {
     if (nboxes <= 0) return;
     launch_pdl(k_work_lists, (nboxes + 255) / 256, 256, 0, st, F, nboxes, src_list, src_cnt, leaf_list, leaf_cnt, p2p_list,
-                                                       p2p_cnt, p2p_stride, own_list, own_cnt);
+                                                       p2p_cnt, p2p_stride, own_list, own_cnt, w_list, w_cnt);
 }
 
 // ------------------------------------------------------------------ M2L (FP32 SIMT)
@@ -919,7 +929,8 @@ template <bool TAYLOR, bool TABLE>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__restrict__ list,
                                                          const int *__restrict__ count, int stride,
                                                          float *__restrict__ out, P2PConst K, int pass_lo,
-                                                         int pass_hi) {
+                                                         int pass_hi, const int *__restrict__ w_list,
+                                                         const int *__restrict__ w_cnt) {
     pdl_enter();
     __shared__ float4 stage[P2P_CAP];
     __shared__ float tab[TABLE ? GTAB_N : 1];
@@ -937,14 +948,25 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p(FmmDev F, const int *__r
     int cnt = 0;
 #pragma unroll
     for (int c = 0; c < P2P_CLASSES; ++c) cnt += ccnt[c];
+    // a W-only launch with the list of the leaves that have W entries walks those alone
+    const int nitems = w_list ? *w_cnt : cnt;
     const TreeDev &T = F.T;
     const float h = F.kp.h;
     const float wsc = F.wscale * F.kp.C / (h * h * h);          // source weight -> scaled weight
     const float usc = F.kp.C / (h * h * h);                     // upward weight -> scaled weight
     const int n = F.O.n, np = F.O.npad;
-    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-        int c = 0, j = i;
-        while (c < P2P_CLASSES - 1 && j >= ccnt[c]) j -= ccnt[c++];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        int c = 0, j = it, i = it;
+        if (w_list) {
+            // slot in the class lists -> (class, index in the class) -> position i in the class order
+            const int e = w_list[it];
+            c = e / stride;
+            j = e - c * stride;
+            i = j;
+            for (int k = 0; k < c; ++k) i += ccnt[k];
+        } else {
+            while (c < P2P_CLASSES - 1 && j >= ccnt[c]) j -= ccnt[c++];
+        }
         const int b = list[(size_t)c * stride + j];
         if (pass_lo == 1 && F.L.w_off[b + 1] == F.L.w_off[b]) continue;     // uniform
         const int tb = T.b_tb[b], te = T.b_te[b];
@@ -1172,24 +1194,28 @@ void fmm_near_table(const FmmDev &F, float *gtab, cudaStream_t st) {
 }
 
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-             cudaStream_t st, int pass_lo, int pass_hi, int per_sm) {
+             cudaStream_t st, int pass_lo, int pass_hi, int per_sm, const int *w_list, const int *w_cnt, int max_w) {
     if (nboxes <= 0) return;
     const int cap = 152 * per_sm;
-    const int grid = nboxes < cap ? nboxes : cap;
+    int grid = nboxes < cap ? nboxes : cap;
+    if (w_list) {
+        if (pass_lo != 1 || max_w <= 0) return;      // the list serves a W-only launch; no W entries
+        grid = std::min(grid, max_w);
+    }
     const P2PConst K = p2p_const(F);
     const bool taylor = K.bma_h < 0.5f, table = F.gtab != nullptr;
     if (!taylor && !table)
         launch_pdl(k_p2p<false, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
-                   pass_hi);
+                   pass_hi, w_list, w_cnt);
     else if (taylor && !table)
         launch_pdl(k_p2p<true, false>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
-                   pass_hi);
+                   pass_hi, w_list, w_cnt);
     else if (!taylor)
         launch_pdl(k_p2p<false, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
-                   pass_hi);
+                   pass_hi, w_list, w_cnt);
     else
         launch_pdl(k_p2p<true, true>, grid, P2P_WARPS * 32, 0, st, F, p2p_list, p2p_cnt, stride, out, K, pass_lo,
-                   pass_hi);
+                   pass_hi, w_list, w_cnt);
 }
 
 void fmm_near_add(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,

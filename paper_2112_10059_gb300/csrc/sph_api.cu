@@ -671,7 +671,7 @@ struct PhaseTimer {
 // ------------------------------------------------------------------ FMM passes
 struct PassState {
     FmmDev F;
-    int *w_src = nullptr, *w_leaf = nullptr, *w_p2p = nullptr, *w_cnt = nullptr, *w_own = nullptr;
+    int *w_src = nullptr, *w_leaf = nullptr, *w_p2p = nullptr, *w_cnt = nullptr, *w_own = nullptr, *w_wl = nullptr;
     PairsDev Pd;
     int *err = nullptr;
     bool tc = false;
@@ -693,7 +693,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     const size_t vb = (size_t)std::max(nb, 1) * c->npad() * sizeof(float);
     ENS(c->b_ueq, vb);
     ENS(c->b_dchk, vb);
-    ENS(c->b_work, ((4 + P2P_CLASSES) * (size_t)std::max(nb, 1) + 64) * sizeof(int));
+    ENS(c->b_work, ((5 + P2P_CLASSES) * (size_t)std::max(nb, 1) + 64) * sizeof(int));
     ENS(c->b_err, 16 * sizeof(int));
     FmmDev &F = S.F;
     F.T = tree_dev(c);
@@ -725,6 +725,7 @@ int fmm_prepare(sph_ctx *c, PassState &S) {
     S.w_cnt = S.w_p2p + P2P_CLASSES * std::max(nb, 1);
     F.l2p_list = S.w_cnt + 64;                  // [nb], per level at lvl_base[l]
     S.w_own = F.l2p_list + std::max(nb, 1);     // [nb]: deepest-level leaves with V / X entries, count w_cnt[62]
+    S.w_wl = S.w_own + std::max(nb, 1);         // [nb]: near-field leaves with W entries, count w_cnt[39]
     F.l2p_cnt = S.w_cnt + 40;                   // [16]
     S.Pd = pairs_dev(c);
     S.err = P<int>(c->b_err);
@@ -803,7 +804,7 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
     // the mapped read-back buffer, where that kernel runs; else by copies
     const bool err_mapped = c->pinned_dev && F.near_buf && nb > 0;
     fmm_work_lists(F, nb, S.w_src, S.w_cnt, S.w_leaf, S.w_cnt + 32, S.w_p2p, S.w_cnt + 56, std::max(nb, 1),
-                   S.w_own, S.w_cnt + 62, c->stream);
+                   S.w_own, S.w_cnt + 62, c->stream, S.w_wl, S.w_cnt + 39);
     c->launches += nb > 0;
     const bool near_fork = F.near_buf && nb > 0;
     if (near_fork) {
@@ -845,7 +846,9 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
         CK(cudaStreamWaitEvent(c->near_stream, c->near_up, 0));
         if (tm) tm->mark_at(15, c->near_stream);
         if (c->list_tot[2] > 0 && F.O.method == FAR_CHEB) {
-            fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 1, 2);
+            // only the leaves with W entries (at most one per W entry)
+            fmm_p2p(F, nb, S.w_p2p, S.w_cnt + 56, std::max(nb, 1), out, c->near_stream, 1, 2, 16, S.w_wl,
+                    S.w_cnt + 39, c->list_tot[2]);
             ++c->launches;
         }
         if (tm) tm->mark_at(13, c->near_stream);

@@ -280,14 +280,20 @@ constexpr int64_t P2P_CLASS0 = 1 << 16;
 // p2p_list: P2P_CLASSES lists of p2p_stride slots, p2p_cnt: their P2P_CLASSES counts
 // own_list / own_cnt: the deepest-level leaves with targets and V or X entries (where
 // F.d_sparse_from >= 0), for fmm_l2p_own
+// w_list / w_cnt (optional): the near-field leaves with W entries, each as its slot in the class
+// lists (class x p2p_stride + index in the class), for a launch of the W-list pass alone
 void fmm_work_lists(const FmmDev &F, int nboxes, int *src_list, int *src_cnt, int *leaf_list, int *leaf_cnt,
-                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st);
+                    int *p2p_list, int *p2p_cnt, int p2p_stride, int *own_list, int *own_cnt, cudaStream_t st,
+                    int *w_list = nullptr, int *w_cnt = nullptr);
 // near field over the U lists (pass 0) and W lists (pass 1) of the leaves in the class lists of
 // p2p_list, passes [pass_lo, pass_hi); adds into out, or into F.near_buf where it is set (pass 0
 // clears the leaf's slots; a launch of pass 1 alone must follow the one of pass 0).  At most
 // per_sm CTAs per SM (grid-stride over the leaves).
+// w_list / w_cnt (a launch of pass 1 alone): walk only those leaves (fmm_work_lists), with a
+// grid of at most max_w CTAs
 void fmm_p2p(const FmmDev &F, int nboxes, const int *p2p_list, const int *p2p_cnt, int stride, float *out,
-             cudaStream_t st, int pass_lo = 0, int pass_hi = 2, int per_sm = 16);
+             cudaStream_t st, int pass_lo = 0, int pass_hi = 2, int per_sm = 16, const int *w_list = nullptr,
+             const int *w_cnt = nullptr, int max_w = 0);
 // out[cell of t] += F.near_buf[slot of t] for every target of every leaf of those lists
 // flags / flags_host (optional): flags[0..2) copied to the mapped host address flags_host once
 // every earlier kernel of the stream has completed
