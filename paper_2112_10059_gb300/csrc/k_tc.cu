@@ -1734,7 +1734,7 @@ void fmm_m2l_tiles(const FmmDev &F, const MtLevels &ML, int *groups, int *ngroup
 }
 
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
-                bool pipelined, bool tile_loop, int *ticket) {
+                bool pipelined, bool tile_loop, int *ticket, int loop_ctas) {
     if (nV <= 0) return;
     tc_init_attributes();
     if (pipelined) {
@@ -1743,7 +1743,8 @@ void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *ima
     }
     if (tile_loop && ticket) {
         const int upper = (nV + TCN - 1) / TCN + Pd.nkeys;   // tiles at most
-        launch_pdl(k_m2l_tc_loop, std::min(upper, 2 * sm_count()), 256, TC_SMEM, st, F, Pd, images, err, ticket);
+        const int ctas = loop_ctas > 0 ? loop_ctas : 2 * sm_count();
+        launch_pdl(k_m2l_tc_loop, std::min(upper, ctas), 256, TC_SMEM, st, F, Pd, images, err, ticket);
         return;
     }
     int grid = (nV + TCN - 1) / TCN + Pd.nkeys;

@@ -91,6 +91,7 @@ struct sph_ctx {
     bool l2p_tc_tables = false;       // interpolation-table L2P (tensor cores) instead of the separable form
     bool m2l_pipe = false;            // tensor-core M2L as one persistent pipelined CTA per SM (measured slower)
     bool m2l_loop = true;             // tensor-core M2L as two persistent CTAs per SM looping over the tiles
+    int m2l_loop_ctas = 0;            // > 0: that many CTAs for the tile loop instead (tests: many tiles per CTA)
     bool brick_offsets = false;       // the last selection left every 16^3 brick's target offset in b_off
     bool near_overlap = true;         // near field on a second stream beside the far-field passes
     int near_per_sm = 0;              // its U-list launch: CTAs per SM (0: by the estimate in fmm_queue)
@@ -882,7 +883,8 @@ int fmm_queue(sph_ctx *c, PassState &S, float *out, PhaseTimer *tm) {
                 c->launches += 2;
             }
         } else if (S.tc) {
-            fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream, c->m2l_pipe, c->m2l_loop, S.w_cnt + 38);
+            fmm_m2l_tc(F, S.Pd, nV, F.O.m2l_img, S.err, c->stream, c->m2l_pipe, c->m2l_loop, S.w_cnt + 38,
+                       c->m2l_loop_ctas);
             c->launches += nV > 0;
         } else {
             fmm_m2l_pairs(F, S.Pd, nV, c->m2l_prec, c->stream);
@@ -1070,7 +1072,7 @@ std::vector<uint8_t> graph_signature(const sph_ctx *c, const PassState &S, const
     put(c->lvl_sleaf.data(), c->lvl_sleaf.size() * sizeof(int));
     put(c->list_tot, sizeof c->list_tot);
     const int64_t sc[] = {c->nboxes, c->Lmax, c->D, c->m2l_prec, c->translate_per_box, c->l2l_eight, c->l2p_simt,
-                          c->l2p_tc_tables, c->m2l_pipe, c->m2l_loop, c->l2lp_fused, c->m2l_tiles, c->m2l_form,
+                          c->l2p_tc_tables, c->m2l_pipe, c->m2l_loop, c->m2l_loop_ctas, c->l2lp_fused, c->m2l_tiles, c->m2l_form,
                           (int64_t)reinterpret_cast<uintptr_t>(out)};
     put(sc, sizeof sc);
     return v;
@@ -1475,6 +1477,7 @@ int configure_sub(sph_ctx *sub, const sph_ctx *parent, const sph_problem &p) {
     sub->l2p_tc_tables = parent->l2p_tc_tables;
     sub->m2l_pipe = parent->m2l_pipe;
     sub->m2l_loop = parent->m2l_loop;
+    sub->m2l_loop_ctas = parent->m2l_loop_ctas;
     sub->near_overlap = parent->near_overlap;
     sub->near_per_sm = parent->near_per_sm;
     sub->l2lp_fused = parent->l2lp_fused;
@@ -1858,6 +1861,7 @@ int sph_create(sph_ctx **out, int device, void *cuda_stream) {
     if (const char *e = getenv("SPH_L2P_TC")) c->l2p_tc_tables = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_PIPE")) c->m2l_pipe = atoi(e) != 0;
     if (const char *e = getenv("SPH_M2L_LOOP")) c->m2l_loop = atoi(e) != 0;
+    if (const char *e = getenv("SPH_M2L_LOOP_CTAS")) c->m2l_loop_ctas = std::max(0, atoi(e));
     if (const char *e = getenv("SPH_NEAR_OVERLAP")) c->near_overlap = atoi(e) != 0;
     if (const char *e = getenv("SPH_NEAR_PER_SM")) c->near_per_sm = std::max(1, atoi(e));
     if (const char *e = getenv("SPH_L2LP_FUSED")) c->l2lp_fused = atoi(e) != 0;

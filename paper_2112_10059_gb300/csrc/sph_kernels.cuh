@@ -350,7 +350,8 @@ size_t tc_image_elems(int count);
 void make_images(const float *opT, int np, int count, uint16_t *img, cudaStream_t st);
 void fmm_m2l_tc(const FmmDev &F, const PairsDev &Pd, int nV, const uint16_t *images, int *err, cudaStream_t st,
                 bool pipelined = false,
-                bool tile_loop = false, int *ticket = nullptr);   // ticket: a cleared counter (tile loop)
+                bool tile_loop = false, int *ticket = nullptr,   // ticket: a cleared counter (tile loop)
+                int loop_ctas = 0);                              // > 0: CTAs of the tile loop (else 2 per SM)
 // M2L of every level in target-stationary tiles (tensor cores): groups of up to 128 boxes of one
 // level and octant, their V-list sources found by dense lookup (no pair list read)
 struct MtLevels {

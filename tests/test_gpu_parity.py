@@ -516,6 +516,29 @@ def test_pipelined_m2l_matches_per_tile(sph, monkeypatch, pi):
     _check_fmm(outs[1], ref, T, "m2l pipelined")
 
 
+@pytest.mark.parametrize("pi", [1, 2])
+def test_m2l_tile_loop_matches_per_tile(sph, monkeypatch, pi):
+    """The persistent tile-loop M2L equals the one-CTA-per-tile kernel (the same products; only
+    the order of the reductions into the targets differs), on its default grid and on 3 CTAs,
+    where every CTA walks many tiles through the ticket with the next tile's pair indices and
+    operator image fetched under the current one.  The pair-tile form is forced (no
+    target-stationary tiles)."""
+    p = _problems()[pi]
+    monkeypatch.setenv("SPH_M2L_TILES", "0")
+    outs = []
+    for loop, ctas in (("0", "0"), ("1", "3"), ("1", "0")):
+        monkeypatch.setenv("SPH_M2L_LOOP", loop)
+        monkeypatch.setenv("SPH_M2L_LOOP_CTAS", ctas)
+        c = sph.Context(0)
+        _, out, _ = sph.solve(p, c, m2l_precision=sph.M2L_BF16X3)
+        outs.append(out.cpu().numpy().astype(np.float64))
+        c.close()
+    ref, J, T = oracle.sph_problem(p)
+    for o in outs[1:]:
+        assert oracle.rel_l2(o[T], outs[0][T]) < 1e-6
+    _check_fmm(outs[1], ref, T, "m2l tile loop")
+
+
 def test_l2l_eight_children_per_cta(sph, monkeypatch):
     """Tensor-core L2L with all 8 child operators streamed through one CTA equals the
     one-child-per-CTA kernel (same products, different scheduling)."""
